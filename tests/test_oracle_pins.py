@@ -1,0 +1,306 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix (no GPU).
+
+Each pin is computed independently of the oracle's own formulation:
+  P1  canonical limit: complete OSVs + one full cluster == brute-force canonical DF-MP2 (Sec. 2.1: OSV-MP2
+      with untruncated OSVs spans the whole virtual space);
+  P2  MBE exactness: all clusters kept and N <= 3 (or decoupled subsystems) == full OSV-MP2 (Eqs. 28-34);
+  P6  brute-force Galerkin solve of the virtual-space pair equations (Eq. 4 projected on each pair domain);
+  P5  invariances (LMO relabelling, orthogonal aux rotation, common energy shift);
+  P10 T_kk is positive semidefinite (Eq. 6 elements are a Schur product of a Gram and a Cauchy matrix);
+  P9  Hylleraas functional error is quadratic in the amplitude error (Eq. 3);
+  P7  autograd gradient == central finite differences; P8 Euler identity sum B dE/dB = 4 E.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2106_06149_gb300.synth import Params, Problem, make_problem
+
+DT = torch.float64
+
+
+def canonical_df_mp2(problem):
+    """E = sum_ijab (ia|jb)[2(ia|jb) - (ib|ja)] / (e_i + e_j - e_a - e_b) in canonical occupied orbitals."""
+    n, nv = problem.n_occ, problem.n_vir
+    Bs = np.stack([problem.B_dense(i) for i in range(n)])               # (n, nv, naux)
+    e_occ, U = np.linalg.eigh(problem.f_occ)
+    Bc = np.einsum("ji,jap->iap", U, Bs)                                # canonical MOs phi_i = sum_j U_ji phi_j
+    iajb = np.einsum("iap,jbp->iajb", Bc, Bc)
+    eps = problem.eps_vir
+    den = e_occ[:, None, None, None] + e_occ[None, None, :, None] - eps[None, :, None, None] - eps[None, None, None, :]
+    return float(np.sum(iajb * (2.0 * iajb - iajb.transpose(0, 3, 2, 1)) / den))
+
+
+def galerkin_energy(problem, Q, clusters_all=True):
+    """Solve the projected pair equations of one full cluster as one dense linear system.
+
+    Unknowns: X_ij in an orthonormal basis Phi_ij of range(Q_i Q_j) (SVD), t_ij = Phi X Phi^T.  Equations:
+    Phi_ij^T [K_ij + eps t_ij + t_ij eps - sum_k (f_kj t_ik + f_ik t_kj)] Phi_ij = 0 for every ordered pair."""
+    n, nv = problem.n_occ, problem.n_vir
+    Bs = [problem.B_dense(i) for i in range(n)]
+    f, eps = problem.f_occ, problem.eps_vir
+    Qn = [q.numpy() for q in Q]
+    pairs = [(i, j) for i in range(n) for j in range(n)]
+    Phi = {}
+    for (i, j) in pairs:
+        P = Qn[i] if i == j else np.concatenate([Qn[i], Qn[j]], axis=1)
+        u, s, _ = np.linalg.svd(P, full_matrices=False)
+        Phi[(i, j)] = u[:, s > 1e-6]
+    off, tot = {}, 0
+    for p in pairs:
+        off[p] = tot
+        tot += Phi[p].shape[1] ** 2
+    A = np.zeros((tot, tot))
+    rhs = np.zeros(tot)
+    E = np.diag(eps)
+    for (i, j) in pairs:
+        Pp = Phi[(i, j)]
+        r = Pp.shape[1]
+        rows = slice(off[(i, j)], off[(i, j)] + r * r)
+        rhs[rows] = -(Pp.T @ Bs[i] @ Bs[j].T @ Pp).ravel()
+
+        def add(q, coef_left, transpose=False):
+            # contribution of t_q (virtual) = Phi_q X_q Phi_q^T mapped through M -> Pp^T op(M) Pp
+            Pq = Phi[q]
+            rq = Pq.shape[1]
+            cols = slice(off[q], off[q] + rq * rq)
+            for a in range(rq):
+                for b in range(rq):
+                    Xu = np.zeros((rq, rq))
+                    Xu[a, b] = 1.0
+                    t = Pq @ Xu @ Pq.T
+                    A[rows, off[q] + a * rq + b] += (Pp.T @ coef_left(t) @ Pp).ravel()
+
+        add((i, j), lambda t: E @ t + t @ E)
+        for k in range(n):
+            add((i, k), lambda t, k=k: -f[k, j] * t)
+            add((k, j), lambda t, k=k: -f[i, k] * t)
+    x = np.linalg.solve(A, rhs)
+    Etot = 0.0
+    for (i, j) in pairs:
+        Pp = Phi[(i, j)]
+        r = Pp.shape[1]
+        t = Pp @ x[off[(i, j)]:off[(i, j)] + r * r].reshape(r, r) @ Pp.T
+        Etot += np.sum((Bs[i] @ Bs[j].T) * (2.0 * t - t.T))
+    return Etot
+
+
+def _cut_all():
+    return dict(r2b=1e9, r3b=1e9)
+
+
+# ------------------------------------------------------------------------------------------------ P1
+@pytest.mark.parametrize("seed", [0, 1])
+def test_canonical_limit_full_cluster(seed):
+    p = make_problem(4, 10, 28, seed=seed)
+    prm = Params(n_osv_fixed=10, mbe_order=0, tol=1e-11, max_iter=400)
+    e = oracle.energy(p, prm)["E"]
+    ref = canonical_df_mp2(p)
+    assert abs(e - ref) <= 1e-10 * max(1.0, abs(ref)), (e, ref)
+
+
+def test_canonical_limit_mbe3_three_lmos():
+    p = make_problem(3, 9, 20, seed=5)
+    prm = Params(n_osv_fixed=9, mbe_order=3, tol=1e-11, max_iter=400, **_cut_all())
+    e = oracle.energy(p, prm)["E"]
+    assert abs(e - canonical_df_mp2(p)) <= 1e-10
+
+
+def test_canonical_limit_local_domains():
+    p = make_problem(4, 8, 40, geometry="cube", box=6.0, dmin=1.4, radius=4.0, seed=7)
+    assert not p.full_domain()
+    prm = Params(n_osv_fixed=8, mbe_order=0, tol=1e-11, max_iter=400)
+    assert abs(oracle.energy(p, prm)["E"] - canonical_df_mp2(p)) <= 1e-10
+
+
+# ------------------------------------------------------------------------------------------------ P2
+@pytest.mark.parametrize("n", [2, 3])
+def test_mbe_exact_for_small_n(n):
+    p = make_problem(n, 14, 30, seed=11 + n)
+    full = oracle.energy(p, Params(n_osv_fixed=5, mbe_order=0, tol=1e-11))
+    mbe = oracle.energy(p, Params(n_osv_fixed=5, mbe_order=3, tol=1e-11, **_cut_all()))
+    assert abs(full["E"] - mbe["E"]) <= 1e-11
+    # collective amplitudes equal the full-cluster amplitudes (Eqs. 28-32)
+    for pr, T in full["amplitudes"][tuple(range(n))].items():
+        assert torch.allclose(mbe["collective"][pr], T, atol=1e-10)
+
+
+def _merge(a: Problem, b: Problem, shift=500.0):
+    """Two problems side by side: disjoint aux sets, no occupied Fock coupling between them."""
+    na, nb = a.n_occ, b.n_occ
+    assert a.n_vir == b.n_vir
+    f = np.zeros((na + nb, na + nb))
+    f[:na, :na] = a.f_occ
+    f[na:, na:] = b.f_occ
+    cb = b.centres.copy()
+    cb[:, 0] += shift
+    blocks, ptr, idx = [], [0], []
+    for src, base in ((a, 0), (b, a.n_aux)):
+        for i in range(src.n_occ):
+            blocks.append(src.B_block(i).ravel())
+            idx.append(src.aux_idx[src.aux_ptr[i]:src.aux_ptr[i + 1]] + base)
+            ptr.append(ptr[-1] + src.a(i))
+    return Problem(centres=np.concatenate([a.centres, cb]), aux_centres=np.concatenate([a.aux_centres, b.aux_centres]),
+                   f_occ=f, eps_vir=a.eps_vir, aux_ptr=np.asarray(ptr, np.int64),
+                   aux_idx=np.concatenate(idx).astype(np.int32), B=np.concatenate(blocks))
+
+
+def test_mbe_exact_for_decoupled_subsystems():
+    a = make_problem(2, 12, 20, seed=21)
+    b = make_problem(2, 12, 20, seed=22)
+    b.eps_vir = a.eps_vir
+    p = _merge(a, b)
+    prm = dict(n_osv_fixed=5, tol=1e-11)
+    full = oracle.energy(p, Params(mbe_order=0, **prm))["E"]
+    mbe = oracle.energy(p, Params(mbe_order=3, **prm, **_cut_all()))
+    assert len(mbe["clusters"]) == 4 + 6 + 4
+    assert abs(full - mbe["E"]) <= 1e-11
+    ea = oracle.energy(a, Params(mbe_order=0, **prm))["E"]
+    eb = oracle.energy(b, Params(mbe_order=0, **prm))["E"]
+    assert abs(full - ea - eb) <= 1e-11
+
+
+def test_mbe_weights_moebius():
+    """sum of w_c over clusters containing any selected set s is 1 (inclusion-exclusion)."""
+    p = make_problem(12, 4, 4, seed=3)
+    cl = oracle.select_clusters(p.centres, 8.0, 6.0, 3)
+    w = oracle.mbe_weights(cl)
+    for s in cl:
+        assert sum(w[c] for c in cl if set(s) <= set(c)) == 1
+    # chain spacing 1.5 A: pairs |i-j| <= 5, triples of span <= 4
+    n = 12
+    assert sum(len(c) == 2 for c in cl) == sum(1 for i in range(n) for j in range(i + 1, n) if j - i <= 5)
+    assert sum(len(c) == 3 for c in cl) == sum(1 for c in itertools.combinations(range(n), 3) if c[2] - c[0] <= 4)
+
+
+# ------------------------------------------------------------------------------------------------ P6
+@pytest.mark.parametrize("seed,asym", [(0, False), (4, False), (8, True)])
+def test_bruteforce_galerkin(seed, asym):
+    p = make_problem(3, 7, 16, seed=seed)
+    if asym:
+        # an asymmetric occupied Fock matrix tells f_kj from f_jk and K_ij from K_ji in Eq. 4
+        p.f_occ = p.f_occ + np.triu(np.full((3, 3), 0.03), 1)
+    prm = Params(n_osv_fixed=3, mbe_order=0, tol=1e-12, max_iter=500)
+    out = oracle.energy(p, prm)
+    ref = galerkin_energy(p, out["Q"])
+    assert abs(out["E"] - ref) <= 1e-11 * max(1.0, abs(ref)), (out["E"], ref)
+
+
+# ------------------------------------------------------------------------------------------------ P5
+def test_invariances():
+    p = make_problem(4, 10, 20, seed=9)
+    prm = Params(n_osv_fixed=4, mbe_order=3, tol=1e-11, **_cut_all())
+    e0 = oracle.energy(p, prm)["E"]
+    # LMO relabelling
+    perm = np.array([2, 0, 3, 1])
+    blocks = [p.B_block(i).ravel() for i in perm]
+    q = Problem(centres=p.centres[perm], aux_centres=p.aux_centres, f_occ=p.f_occ[np.ix_(perm, perm)],
+                eps_vir=p.eps_vir, aux_ptr=p.aux_ptr, aux_idx=p.aux_idx, B=np.concatenate(blocks))
+    assert abs(oracle.energy(q, prm)["E"] - e0) <= 1e-11
+    # common orthogonal rotation of the aux index (full domains)
+    O, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((p.n_aux, p.n_aux)))
+    blocks = [(p.B_block(i) @ O).ravel() for i in range(p.n_occ)]
+    q = Problem(centres=p.centres, aux_centres=p.aux_centres, f_occ=p.f_occ, eps_vir=p.eps_vir,
+                aux_ptr=p.aux_ptr, aux_idx=p.aux_idx, B=np.concatenate(blocks))
+    assert abs(oracle.energy(q, prm)["E"] - e0) <= 1e-11
+    # shift of all orbital energies: (eps + c, F + c 1)
+    c = 0.37
+    q = Problem(centres=p.centres, aux_centres=p.aux_centres, f_occ=p.f_occ + c * np.eye(p.n_occ),
+                eps_vir=p.eps_vir + c, aux_ptr=p.aux_ptr, aux_idx=p.aux_idx, B=p.B)
+    assert abs(oracle.energy(q, prm)["E"] - e0) <= 1e-11
+
+
+def test_osv_selection_keeps_largest_eigenvalues():
+    """Q_k spans the eigenvectors of T_kk with the n_k largest eigenvalues (Sec. 2.1, Eq. 6): the trace of
+    Q^T T_kk Q equals the sum of the n_k largest eigenvalues; T_kk built here element by element."""
+    p = make_problem(3, 12, 20, seed=17)
+    out = oracle.energy(p, Params(n_osv_fixed=4, mbe_order=1))
+    for k in range(p.n_occ):
+        Bk = p.B_dense(k)
+        T = np.empty((p.n_vir, p.n_vir))
+        for a in range(p.n_vir):
+            for b in range(p.n_vir):
+                T[a, b] = np.dot(Bk[a], Bk[b]) / (p.eps_vir[a] + p.eps_vir[b] - 2.0 * p.f_occ[k, k])
+        Q = out["Q"][k].numpy()
+        assert np.allclose(Q.T @ Q, np.eye(4), atol=1e-12)
+        top = np.sort(np.linalg.eigvalsh(T))[::-1][:4].sum()
+        assert abs(np.trace(Q.T @ T @ Q) - top) <= 1e-12 * abs(top)
+
+
+# ----------------------------------------------------------------------------------------------- P10
+def test_tkk_psd_and_negative_energy():
+    p = make_problem(5, 30, 20, seed=2)        # n_aux < n_vir: rank-deficient, still PSD
+    eps = torch.as_tensor(p.eps_vir, dtype=DT)
+    for k in range(p.n_occ):
+        w = torch.linalg.eigvalsh(oracle.tkk(oracle.dense_B(p, k), eps, float(p.f_occ[k, k])))
+        assert float(w.min()) >= -1e-14 * float(w.abs().max())
+    assert oracle.energy(p, Params(n_osv_fixed=6, mbe_order=3))["E"] < 0.0
+
+
+# ------------------------------------------------------------------------------------------------ P9
+def test_hylleraas_error_is_quadratic():
+    p = make_problem(3, 10, 20, seed=6)
+    prm = Params(n_osv_fixed=4, mbe_order=0, tol=1e-13, max_iter=500)
+    out = oracle.energy(p, prm)
+    c = out["clusters"][0]
+    T = out["amplitudes"][c]
+    Fo = torch.as_tensor(p.f_occ, dtype=DT)
+    cs = oracle.ClusterSolver(c, out["blocks"], Fo, prm.tau_red)
+    e0 = float(cs.hylleraas(T))
+    g = torch.Generator().manual_seed(0)
+    X = {k: torch.randn(v.shape, generator=g, dtype=DT) for k, v in T.items()}
+    d = []
+    for h in (1e-3, 5e-4):
+        d.append(float(cs.hylleraas({k: T[k] + h * X[k] for k in T})) - e0)
+    assert abs(d[0] / d[1] - 4.0) < 1e-3, d
+
+
+# --------------------------------------------------------------------------------------------- P7/P8
+def _fd_problem():
+    return make_problem(4, 10, 24, seed=13), Params(n_osv_fixed=4, mbe_order=3, tol=1e-12, max_iter=500, r2b=3.5,
+                                                     r3b=3.1)
+
+
+def test_gradient_matches_central_differences():
+    p, prm = _fd_problem()
+    g = oracle.gradient(p, prm)
+    nosv = g["n_osv"]
+    assert len(g["clusters"]) < 4 + 6 + 4       # a truncated expansion, not the full one
+    h = 1e-5
+    rng = np.random.default_rng(0)
+    worst = 0.0
+    for _ in range(12):
+        i = int(rng.integers(p.n_occ))
+        a = int(rng.integers(p.n_vir))
+        P = int(rng.integers(p.a(i)))
+        off = p.b_offset(i) + a * p.a(i) + P
+        ev = []
+        for s in (+h, -h):
+            q = Problem(**{**p.__dict__})
+            q.B = p.B.copy()
+            q.B[off] += s
+            ev.append(oracle.energy(q, prm, n_osv=nosv)["E"])
+        fd = (ev[0] - ev[1]) / (2 * h)
+        worst = max(worst, abs(fd - g["dB"][i][a, P]))
+    for x in range(p.n_occ):
+        for y in range(p.n_occ):
+            ev = []
+            for s in (+h, -h):
+                q = Problem(**{**p.__dict__})
+                q.f_occ = p.f_occ.copy()
+                q.f_occ[x, y] += s
+                ev.append(oracle.energy(q, prm, n_osv=nosv)["E"])
+            fd = (ev[0] - ev[1]) / (2 * h)
+            worst = max(worst, abs(fd - g["dF"][x, y]))
+    assert worst <= 1e-7, worst
+
+
+def test_euler_identity():
+    """With the OSV counts frozen E is homogeneous of degree 4 in B, so sum B * dE/dB = 4 E."""
+    p, prm = _fd_problem()
+    g = oracle.gradient(p, prm)
+    s = sum(float(np.sum(p.B_block(i) * g["dB"][i])) for i in range(p.n_occ))
+    assert abs(s - 4.0 * g["E"]) <= 1e-12 * max(1.0, abs(g["E"])) * 100
