@@ -1,0 +1,146 @@
+/*
+ * osvmbe.h -- C ABI of libosvmbe: MBE(3)-OSV-MP2 energies and OSV-space analytical gradients on one GPU
+ * (GB300, sm_103a).  Method: Q. Liang and J. Yang, "Third-order many-body expansion of OSV-MP2 wavefunction
+ * for low-order scaling analytical gradient computation" (arXiv 2106.06149).
+ *
+ * Conventions for every entry point
+ *   - Every call returns an osv_status; none aborts, traps or exits.  osv_last_error() gives a message.
+ *   - "DEVICE" pointers are CUDA device pointers owned by the caller; "HOST" pointers are ordinary memory.
+ *     Inputs are read, never written; outputs are written only where stated.
+ *   - Work is enqueued on the stream given to osv_create (NULL = the legacy default stream).  Calls that
+ *     return host values (energy, osv_build with n_osv_out, cluster_residual_solve with n_iter_out) wait
+ *     for the stream; the others only enqueue.
+ *   - Input buffers named in osv_problem must stay valid and unchanged from osv_build until the last
+ *     gradient_backward of that problem has completed on the stream.
+ *   - Matrices are row-major; "n x m" means n rows of m contiguous elements.
+ *   - The context owns all intermediates (OSVs, pair bases, cluster amplitudes, densities) until the next
+ *     clusters_build/osv_build on it or osv_destroy.  One context is used by one host thread at a time.
+ */
+#ifndef OSVMBE_H
+#define OSVMBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct osv_ctx osv_ctx;
+
+typedef enum {
+    OSV_OK = 0,
+    OSV_ERR_INVALID = -1,  /* bad argument, size or call order; nothing was enqueued                     */
+    OSV_ERR_NOCONV = -2,   /* some cluster's residual iterations hit max_iter; results are still written  */
+    OSV_ERR_OOM = -3,      /* a device allocation failed                                                   */
+    OSV_ERR_CUDA = -4,     /* a CUDA runtime call failed                                                   */
+    OSV_ERR_TIMEOUT = -5,  /* a bounded device loop gave up (eigensolver iteration cap)                    */
+    OSV_ERR_NUMERIC = -6   /* non-finite value met (input, energy or gradient)                             */
+} osv_status;
+
+typedef enum {
+    OSV_FP64 = 0,          /* every contraction in FP64                                                    */
+    OSV_MIXED_TF32X3 = 1   /* dense DF contractions in split TF32 on tcgen05 tensor cores, FP32 inside a
+                              k-block and FP64 across k-blocks; eigensolves, residual norms, energy and
+                              gradient accumulation in FP64                                                */
+} osv_precision;
+
+/* Method parameters.  l_osv: OSV cut on the eigenvalues of T_kk (Sec. 2.1, Eq. 6).  r2b/r3b: distance
+ * cutoffs (Angstrom) that select 2b and 3b clusters (Sec. 2.2.1; they replace the OSV-overlap metric of
+ * Eqs. 26-27): a pair is kept iff |r_i - r_j| <= r2b, a triple iff its three pairs are kept and all three
+ * distances are <= r3b.  mbe_order: 1, 2 or 3; 0 = one cluster holding every LMO (plain OSV-MP2). */
+typedef struct {
+    double l_osv;      /* keep eigenvalues > l_osv ...                                                   */
+    int n_osv_max;     /* ... capped at n_osv_max (> 0; at least one OSV is always kept)                 */
+    int n_osv_fixed;   /* > 0: keep exactly this many OSVs per LMO, l_osv ignored                        */
+    double r2b, r3b;
+    int mbe_order;
+    double tau_red;    /* pair-overlap eigenvalues below tau_red are dropped (redundant pair space)      */
+    double tol;        /* converged when max over the cluster's pairs of ||R~_ij||_F <= tol              */
+    int max_iter;      /* residual iteration cap (>= 1)                                                  */
+    int precision;     /* osv_precision                                                                  */
+} osv_params;
+
+/* One problem: n_occ localized occupied orbitals (LMOs), n_vir canonical virtuals, n_aux fitting functions.
+ * B holds, for every LMO i, the DF block B_i^{aP} = (ia|P) restricted to i's local fitting domain A_i
+ * (sorted aux indices aux_idx[aux_ptr[i] .. aux_ptr[i+1]-1]); B_ia^P is zero for P outside A_i
+ * (orbital-specific fitting domains, Sec. 2.3, Eq. 35).  Block i starts at element aux_ptr[i] * n_vir and is
+ * n_vir x a_i row-major, a_i = aux_ptr[i+1] - aux_ptr[i].  (ia|jb) = sum_P B_ia^P B_jb^P. */
+typedef struct {
+    int n_occ, n_vir, n_aux;
+    const double *centres;   /* HOST n_occ x 3, Angstrom (cluster selection only)                         */
+    const int64_t *aux_ptr;  /* HOST n_occ + 1, non-decreasing, aux_ptr[0] = 0                             */
+    const int32_t *aux_idx;  /* HOST aux_ptr[n_occ] entries, each list strictly increasing, in [0, n_aux)  */
+    const double *f_occ;     /* DEVICE n_occ x n_occ occupied Fock matrix in the LMO basis (Eh); must be
+                                symmetric; entries are used as Eq. 4 writes them                          */
+    const double *eps_vir;   /* DEVICE n_vir canonical virtual energies f_aa (Eh)                          */
+    const void *B;           /* DEVICE, B_dtype elements, layout above                                     */
+    int B_dtype;             /* 0 = float64, 1 = float32                                                   */
+} osv_problem;
+
+/* Create a context bound to a CUDA stream (cudaStream_t passed as void*; NULL = legacy default stream).
+ * The current CUDA device at this call is the context's device; later calls switch to it. */
+osv_status osv_create(osv_ctx **ctx, void *cuda_stream);
+osv_status osv_destroy(osv_ctx *ctx);
+/* Message describing the last error on ctx (static storage owned by ctx; "" if none; ctx may be NULL). */
+const char *osv_last_error(const osv_ctx *ctx);
+
+/* Select the 1b/2b/3b clusters and their MBE weights on the host (Sec. 2.2.1).  The weight of cluster c is
+ * w_c = sum over selected supersets c' of c of (-1)^(|c'|-|c|); with it sum_c w_c X^c is the MBE(3)
+ * expansion of Eqs. 28-34.  n_clusters[0..2] (HOST, may be NULL) receive the numbers of 1b, 2b, 3b clusters
+ * (mbe_order 0: n_clusters[0] = 1 full cluster, others 0).  Must precede osv_build. */
+osv_status clusters_build(osv_ctx *ctx, const osv_problem *prob, const osv_params *params, int *n_clusters);
+
+/* Build orbital-specific virtuals and all pair quantities for the selected clusters (steps on the device):
+ *   T_kk = (ka|kb) / (eps_a + eps_b - 2 f_kk), eigendecomposition in FP64, Q_k = eigenvectors of the n_k
+ *   largest eigenvalues (Sec. 2.1, Eqs. 5-6; discarded eigenpairs are kept for the OSV relaxation);
+ *   S, F and K blocks A_(ij,kl) = (Q_i Q_j)^T A (Q_k Q_l) (Eq. 7) with K over the common fitting domain;
+ *   per pair an orthonormal pseudo-canonical basis of (Q_i Q_j).
+ * n_osv_out: HOST n_occ ints receiving n_k (may be NULL; non-NULL synchronises the stream). */
+osv_status osv_build(osv_ctx *ctx, const osv_problem *prob, const osv_params *params, int *n_osv_out);
+
+/* Solve the cluster residual equations (Eq. 4, sum over k restricted to the cluster, Sec. 2.2.1) for every
+ * cluster to max_ij ||R~_ij||_F <= tol, and the cluster Hylleraas energies (Eq. 3).
+ * n_iter_out: HOST int receiving the largest iteration count over clusters (may be NULL; non-NULL
+ * synchronises).  cluster_status: DEVICE int32 per cluster (may be NULL): iterations used, or -1 where the
+ * cluster did not converge.  Returns OSV_ERR_NOCONV (after a synchronisation) if any cluster did not
+ * converge and n_iter_out is non-NULL. */
+osv_status cluster_residual_solve(osv_ctx *ctx, int *n_iter_out, int32_t *cluster_status);
+
+/* Collective pair amplitudes T_(ij,ij) = sum over clusters c containing i, j of w_c T^c_(ij,ij)
+ * (MBE(3), Eqs. 28-32). */
+osv_status mbe3_combine(osv_ctx *ctx);
+
+/* E = sum_c w_c E^c_Hylleraas (Eq. 3 per cluster, MBE-combined) into *E_out (HOST);
+ * E_linear_out (HOST, may be NULL) = sum_ij <K_(ij,ij), 2T - T^T> with the collective amplitudes.
+ * Synchronises the stream.  Returns OSV_ERR_NUMERIC if E is not finite. */
+osv_status energy(osv_ctx *ctx, double *E_out, double *E_linear_out);
+
+/* Adjoint of the energy (amplitudes are variational, Sec. 2.1): accumulate dE_scale * dE/dB into dE_dB
+ * (DEVICE, same layout and dtype as prob->B) and dE_scale * dE/df_occ into dE_dFocc (DEVICE n_occ x n_occ
+ * float64, entrywise derivative with F used as given).  Includes the OSV relaxation through the discarded
+ * eigenvectors of T_kk (Sec. 2.1, Eq. 8) and the MBE(3) combination of the pair densities (Eqs. 33-34).
+ * The buffers are added to (+=), not overwritten; either may be NULL to skip it.  Half-transformed
+ * integrals are recomputed, not stored. */
+osv_status gradient_backward(osv_ctx *ctx, double dE_scale, void *dE_dB, double *dE_dFocc);
+
+/* Diagnostics (all synchronise; HOST outputs):
+ *   osv_cluster_count: number of clusters (all orders).
+ *   osv_cluster_info: members[3*c..3*c+2] (-1 padded; mbe_order 0 reports the first 3 members only),
+ *     weight[c], energy[c] (cluster Hylleraas energy E^c), iters[c] (-1 = not converged); any may be NULL.
+ *   osv_eigenvalues: the n_vir eigenvalues of T_kk of LMO k, decreasing. */
+osv_status osv_cluster_count(osv_ctx *ctx, int *n_clusters);
+osv_status osv_cluster_info(osv_ctx *ctx, int32_t *members, int32_t *weight, double *energy, int32_t *iters);
+osv_status osv_eigenvalues(osv_ctx *ctx, int k, double *w_out);
+
+/* Batched symmetric eigensolver used for Eq. 6 (utility entry point): for b = 0..batch-1, the n x n
+ * symmetric matrix A + b*n*n (DEVICE, read only) gets eigenvalues w + b*n (DEVICE, decreasing) and
+ * eigenvectors as rows of Zt + b*n*n (DEVICE; row mu is the eigenvector of w[mu]).  Householder
+ * tridiagonalisation and implicit QL in FP64.  Allocates 2*batch*n*n doubles of scratch with cudaMalloc per
+ * call and frees it before returning; synchronises the stream.  1 <= n <= 4096. */
+osv_status osv_syev_batched(const double *A, int n, int batch, double *w, double *Zt, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OSVMBE_H */

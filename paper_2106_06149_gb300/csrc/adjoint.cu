@@ -1,0 +1,536 @@
+// Adjoint of the MBE(3)-OSV-MP2 energy (dE/dB, dE/df_occ), FP64.
+//
+// The amplitudes are variational (Sec. 2.1, text around Eq. 9), so dE is the partial derivative of
+// E = sum_c w_c E^c_H at frozen cluster amplitudes.  With T = V T~ V^T in each pair's OSV basis and
+// Tb = 2T - T^T, the per-cluster partials with respect to the pair blocks of Eq. 7 are, in the pseudo-canonical
+// basis of each pair (Lambda = diag(e), m = 2 for i != j from the ordered pairs ij and ji, m = 1 for ii):
+//   d/dS_(ij,ij):  m [Tb Lambda T^T + T^T Lambda Tb - (f_ii + f_jj)(Tb T^T + T^T Tb)]
+//   d/dF_(ij,ij):  m [T^T Tb + Tb T^T]
+//   d/dS_(ij,kl):  -m f [Tb S T'^T + Tb^T S T']            (one per coupling term of Eq. 4)
+//   d/dK_(ij,ij):  2 m Tb_collective                         (linear: only the MBE-combined amplitudes)
+//   d/df_xy:       -<S T' S^T, Tb> per term, -<T, Tb> for the diagonal f of D
+// (these are the OSV-space densities D, D' and N_ij of Eqs. 14-16 in the orthonormal pair basis, MBE-combined
+// as in Eqs. 33-34).  They are mapped back with V, split into LMO-pair blocks s_ab = Q_a^T Q_b,
+// phi_ab = Q_a^T eps Q_b and K sub-blocks W^(i)_a W^(j)T_b, chained to W (recomputed in the forward and kept),
+// Q and B, and the OSV gradient is relaxed through the discarded eigenvectors of T_kk (Eq. 8):
+//   C = Q'^T dE/dQ,  Y = C / (omega_mu - omega'_nu),  G_T = sym(Q' Y Q^T),
+//   dE/dB_k += 2 (G_T / Delta) B_k,  dE/df_kk += 2 sum_ab G_T,ab T_ab / Delta_ab.
+#include "ctx.h"
+#include "launch.h"
+
+namespace osv {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// C (M x N) (+)= alpha * op(A) diag(dk) op(B) with dk optional (scales the k index).
+__device__ void sgemm_d(int M, int N, int K, const double *__restrict__ A, long long lda, bool ta,
+                        const double *__restrict__ dk, const double *__restrict__ B, long long ldb, bool tb,
+                        double *C, long long ldc, double alpha, bool accumulate) {
+    const int mt = (M + 3) >> 2, nt = (N + 3) >> 2;
+    for (int t = threadIdx.x; t < mt * nt; t += blockDim.x) {
+        const int bm = (t / nt) << 2, bn = (t % nt) << 2;
+        double acc[4][4] = {};
+        for (int k = 0; k < K; ++k) {
+            const double sk = dk ? dk[k] : 1.0;
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int m = bm + i;
+                a[i] = m < M ? sk * (ta ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = bn + j;
+                b[j] = n < N ? (tb ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = bm + i;
+            if (m >= M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = bn + j;
+                if (n >= N) continue;
+                double *c = C + (long long)m * ldc + n;
+                *c = accumulate ? *c + alpha * acc[i][j] : alpha * acc[i][j];
+            }
+        }
+    }
+}
+
+struct AdjArgs {
+    const ClusterInfo *clusters;
+    const Slot *slots;
+    const Term *terms;
+    const PairInfo *pairs;
+    const int *rdim;
+    const double *e, *Tslot, *Stil, *focc;
+    int n_occ, ncl;
+    double *GS, *GF, *GSc, *dF;   // accumulators (pair off / coupling offset / n_occ^2)
+    double *scratch;
+    long long sstride, pstride;   // per-CTA scratch, one matrix slot
+};
+
+__global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
+    __shared__ double red[kThreads / 32];
+    double *Tb = A.scratch + (long long)blockIdx.x * A.sstride;
+    double *M1 = Tb + A.pstride, *M2 = M1 + A.pstride, *U1 = M2 + A.pstride, *U2 = U1 + A.pstride;
+    const int tid = threadIdx.x;
+    for (int c = blockIdx.x; c < A.ncl; c += gridDim.x) {
+        const ClusterInfo C = A.clusters[c];
+        if (C.weight == 0) continue;
+        const double w = (double)C.weight;
+        for (int s = C.slot0; s < C.slot1; ++s) {
+            const Slot S = A.slots[s];
+            const PairInfo P = A.pairs[S.pair];
+            const int r = A.rdim[S.pair], np = P.np;
+            const double *T = A.Tslot + S.t_off;
+            const double *e = A.e + P.e_off;
+            const double fii = A.focc[(long long)P.i * A.n_occ + P.i], fjj = A.focc[(long long)P.j * A.n_occ + P.j];
+            double tt = 0.0;
+            for (int idx = tid; idx < r * r; idx += kThreads) {
+                const int a = idx / r, b = idx % r;
+                const double tb = 2.0 * T[(long long)a * np + b] - T[(long long)b * np + a];
+                Tb[(long long)a * np + b] = tb;
+                tt += T[(long long)a * np + b] * tb;
+            }
+            tt = block_sum(tt, red);   // also orders the Tb writes before the products below
+            const double wm = w * S.mult;
+            if (tid == 0) {
+                atomicAdd(&A.dF[(long long)P.i * A.n_occ + P.i], -wm * tt);
+                atomicAdd(&A.dF[(long long)P.j * A.n_occ + P.j], -wm * tt);
+            }
+            // M1 = Tb L T^T + T^T L Tb ;  M2 = Tb T^T + T^T Tb
+            sgemm_d(r, r, r, Tb, np, false, e, T, np, true, M1, np, 1.0, false);
+            sgemm_d(r, r, r, Tb, np, false, nullptr, T, np, true, M2, np, 1.0, false);
+            __syncthreads();
+            sgemm_d(r, r, r, T, np, true, e, Tb, np, false, M1, np, 1.0, true);
+            sgemm_d(r, r, r, T, np, true, nullptr, Tb, np, false, M2, np, 1.0, true);
+            __syncthreads();
+            for (int idx = tid; idx < r * r; idx += kThreads) {
+                const long long o = (long long)(idx / r) * np + idx % r;
+                atomicAdd(&A.GS[P.off + o], wm * (M1[o] - (fii + fjj) * M2[o]));
+                atomicAdd(&A.GF[P.off + o], wm * M2[o]);
+            }
+            __syncthreads();
+        }
+        for (int t = C.term0; t < C.term1; ++t) {
+            const Term T = A.terms[t];
+            const Slot Sd = A.slots[T.dst], Ss = A.slots[T.src];
+            const PairInfo Pd = A.pairs[Sd.pair], Ps = A.pairs[Ss.pair];
+            const int rp = A.rdim[Sd.pair], rq = A.rdim[Ss.pair];
+            const int np = Pd.np, nq = Ps.np;
+            const double f = A.focc[(long long)T.fx * A.n_occ + T.fy];
+            const double *Sb = A.Stil + T.sblk;
+            const long long lds = T.s_trans ? np : nq;
+            const double *Tq = A.Tslot + Ss.t_off;
+            const double *Tp = A.Tslot + Sd.t_off;
+            const double wm = w * Sd.mult;
+            // Tb of the destination pair
+            for (int idx = tid; idx < rp * rp; idx += kThreads) {
+                const int a = idx / rp, b = idx % rp;
+                Tb[(long long)a * np + b] = 2.0 * Tp[(long long)a * np + b] - Tp[(long long)b * np + a];
+            }
+            __syncthreads();
+            // U1 = Tb S (rp x rq), U2 = Tb^T S, M1 = S T' (rp x rq)
+            sgemm_d(rp, rq, rp, Tb, np, false, nullptr, Sb, lds, T.s_trans, U1, nq, 1.0, false);
+            sgemm_d(rp, rq, rp, Tb, np, true, nullptr, Sb, lds, T.s_trans, U2, nq, 1.0, false);
+            sgemm_d(rp, rq, rq, Sb, lds, T.s_trans, nullptr, Tq, nq, T.t_trans, M1, nq, 1.0, false);
+            __syncthreads();
+            // X = <S T', Tb S>
+            double x = 0.0;
+            for (int idx = tid; idx < rp * rq; idx += kThreads) {
+                const long long o = (long long)(idx / rq) * nq + idx % rq;
+                x += M1[o] * U1[o];
+            }
+            x = block_sum(x, red);
+            if (tid == 0) {
+                atomicAdd(&A.dF[(long long)T.fx * A.n_occ + T.fy], -w * x);
+                if (Pd.i != Pd.j) atomicAdd(&A.dF[(long long)T.fy * A.n_occ + T.fx], -w * x);
+            }
+            // M2 = U1 T'^T + U2 T'  (rp x rq)
+            sgemm_d(rp, rq, rq, U1, nq, false, nullptr, Tq, nq, !T.t_trans, M2, nq, 1.0, false);
+            __syncthreads();
+            sgemm_d(rp, rq, rq, U2, nq, false, nullptr, Tq, nq, T.t_trans, M2, nq, 1.0, true);
+            __syncthreads();
+            double *G = A.GSc + T.sblk;
+            for (int idx = tid; idx < rp * rq; idx += kThreads) {
+                const int a = idx / rq, b = idx % rq;
+                const double v = -wm * f * M2[(long long)a * nq + b];
+                if (T.s_trans) atomicAdd(&G[(long long)b * np + a], v);   // stored as (src pair) x (dst pair)
+                else atomicAdd(&G[(long long)a * nq + b], v);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// dE/dK~ per pair: 2 m (2 Tc - Tc^T) (collective amplitudes)
+__global__ void k_gk_tilde(const PairInfo *__restrict__ pairs, const double *__restrict__ Tc,
+                           double *__restrict__ out) {
+    const PairInfo P = pairs[blockIdx.x];
+    const double m = P.i == P.j ? 1.0 : 2.0;
+    const int np = P.np;
+    for (long long idx = threadIdx.x; idx < (long long)np * np; idx += blockDim.x) {
+        const int a = int(idx / np), b = int(idx % np);
+        out[P.off + idx] = 2.0 * m * (2.0 * Tc[P.off + idx] - Tc[P.off + (long long)b * np + a]);
+    }
+}
+
+// Y = C / (omega_mu - omega_nu) on the discarded x kept block, zero elsewhere (Eq. 8, kept-discarded only).
+__global__ void k_relax_y(const double *__restrict__ Cm, const double *__restrict__ omega,
+                          const int *__restrict__ nosv, double *__restrict__ Y, int nv, int nm) {
+    const int k = blockIdx.y;
+    const int nk = nosv[k];
+    const double *w = omega + (long long)k * nv;
+    const double *Ck = Cm + (long long)k * nv * nm;
+    double *Yk = Y + (long long)k * nv * nm;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)nv * nm;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int nu = int(idx / nm), mu = int(idx % nm);
+        Yk[idx] = (nu >= nk && mu < nk) ? Ck[idx] / (w[mu] - w[nu]) : 0.0;
+    }
+}
+
+// G = sym(G_T) / Delta in place, and df_kk += 2 sum_ab sym(G_T)_ab T_ab / Delta_ab.
+__global__ void k_relax_sym(double *__restrict__ GT, const double *__restrict__ Tkk, const double *__restrict__ eps,
+                            const double *__restrict__ focc, int n_occ, int nv, double *__restrict__ dF) {
+    const int k = blockIdx.y;
+    __shared__ double red[kThreads / 32];
+    const double fkk = focc[(long long)k * n_occ + k];
+    double *G = GT + (long long)k * nv * nv;
+    const double *T = Tkk + (long long)k * nv * nv;
+    double acc = 0.0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)nv * nv;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int a = int(idx / nv), b = int(idx % nv);
+        if (b < a) continue;
+        const double g = 0.5 * (G[(long long)a * nv + b] + G[(long long)b * nv + a]);
+        const double den = eps[a] + eps[b] - 2.0 * fkk;
+        const double gm = g / den;
+        G[(long long)a * nv + b] = gm;
+        G[(long long)b * nv + a] = gm;
+        acc += (a == b ? 2.0 : 4.0) * gm * T[(long long)a * nv + b];
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&dF[(long long)k * n_occ + k], acc);
+}
+
+template <class T>
+__global__ void k_out_b(const double *__restrict__ src, T *__restrict__ dst, long long n, double scale) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (T)((double)dst[i] + scale * src[i]);
+}
+
+}  // namespace
+
+void AdjointPlan::release() {
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+    for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2, &gb_z, &gb_db, &gb_dq, &gb_c,
+                         &gb_a1, &gb_gt, &gb_rb}) {
+        gemm_batch_free(*g);
+        g->h.clear();
+    }
+    bc_hs.h.clear();
+    bc_hs.d = nullptr;
+    planned = false;
+}
+
+namespace {
+
+template <class T>
+cudaError_t adj_alloc(AdjointPlan &a, T *&p, size_t count) {
+    p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e == cudaSuccess) a.allocs.push_back((void *)p);
+    return e;
+}
+
+}  // namespace
+
+cudaError_t AdjointPlan::plan(osv_ctx &c) {
+    release();
+    cudaError_t e;
+    const int n = c.n_occ, nv = c.n_vir, nm = c.nmax;
+    const long long npairs = (long long)c.pairs.size();
+#define AL(p, cnt) if ((e = adj_alloc(*this, p, (size_t)(cnt))) != cudaSuccess) return e
+    AL(GS, c.pair_mat);
+    AL(GF, c.pair_mat);
+    AL(GK, c.pair_mat);
+    AL(GSo, c.pair_mat);
+    AL(GFo, c.pair_mat);
+    AL(GKo, c.pair_mat);
+    AL(ptmp, c.pair_mat);
+    AL(GSc, c.coup_mat);
+    AL(GSco, c.coup_mat);
+    AL(ctmp, c.coup_mat);
+    AL(HS, npairs * nm * nm);
+    AL(HF, npairs * nm * nm);
+    AL(Z, c.w_off[n]);
+    AL(dQ, (long long)n * nm * nv);
+    AL(dB64, c.aux_ptr[n] * (long long)nv);
+    AL(dF64, (long long)n * n);
+    AL(Cm, (long long)n * nv * nm);
+    AL(Y, (long long)n * nv * nm);
+    AL(A1, (long long)n * nv * nm);
+    grid = (int)std::min<size_t>(c.cl.size(), 152 * 4);
+    pstride = 4LL * nm * nm;
+    AL(scratch, (long long)std::max(grid, 1) * 5 * pstride);
+#undef AL
+    // V G~ V^T for pair and coupling accumulators, and the K gradient
+    auto vgv = [&](GemmBatch &b1, GemmBatch &b2, const double *G, double *tmp, double *out, const PairInfo &Pa,
+                   const PairInfo &Pb, long long off) {
+        // tmp = G V_b^T (na x nb), out = V_a tmp
+        b1.add(gemm(Pa.np, Pb.np, Pb.np, G + off, Pb.np, 0, c.V + Pb.off, Pb.np, 1, tmp + off, Pb.np));
+        b2.add(gemm(Pa.np, Pb.np, Pa.np, c.V + Pa.off, Pa.np, 0, tmp + off, Pb.np, 0, out + off, Pb.np));
+    };
+    for (size_t p = 0; p < c.pairs.size(); ++p) {
+        const PairInfo &P = c.pinfo.h[p];
+        vgv(gb_kc1, gb_kc2, GS, ptmp, GSo, P, P, P.off);
+    }
+    // the GF and GK transforms reuse ptmp: they go into separate batches run one after the other
+    for (size_t p = 0; p < c.pairs.size(); ++p) {
+        const PairInfo &P = c.pinfo.h[p];
+        gb_f1.add(gemm(P.np, P.np, P.np, GF + P.off, P.np, 0, c.V + P.off, P.np, 1, ptmp + P.off, P.np));
+        gb_f2.add(gemm(P.np, P.np, P.np, c.V + P.off, P.np, 0, ptmp + P.off, P.np, 0, GFo + P.off, P.np));
+        gb_k1.add(gemm(P.np, P.np, P.np, GK + P.off, P.np, 0, c.V + P.off, P.np, 1, ptmp + P.off, P.np));
+        gb_k2.add(gemm(P.np, P.np, P.np, c.V + P.off, P.np, 0, ptmp + P.off, P.np, 0, GKo + P.off, P.np));
+    }
+    for (size_t q = 0; q < c.couplings.size(); ++q) {
+        const PairInfo &Pa = c.pinfo.h[c.couplings[q].first], &Pb = c.pinfo.h[c.couplings[q].second];
+        vgv(gb_c1, gb_c2, GSc, ctmp, GSco, Pa, Pb, c.coup_off[q]);
+    }
+    // scatter OSV-basis blocks into LMO-pair accumulators HS (overlap) and HF (Fock)
+    auto scatter = [&](const double *src, long long ld, int x_lmo, int y_lmo, double *H) {
+        BlockCopy b{};
+        const int q = c.pid(x_lmo, y_lmo);
+        b.dst = H + (long long)q * nm * nm;
+        b.ldd = nm;
+        b.src = src;
+        b.lds = ld;
+        b.rows = b.cols = nm;
+        b.trans = x_lmo > y_lmo ? 1 : 0;
+        b.accumulate = 1;
+        b.scale = 1.0;
+        bc_hs.h.push_back(b);
+    };
+    for (size_t p = 0; p < c.pairs.size(); ++p) {
+        const PairInfo &P = c.pinfo.h[p];
+        const int d[2] = {P.i, P.j}, nd = P.i == P.j ? 1 : 2;
+        for (int x = 0; x < nd; ++x)
+            for (int y = 0; y < nd; ++y) {
+                const long long o = P.off + (long long)x * nm * P.np + (long long)y * nm;
+                scatter(GSo + o, P.np, d[x], d[y], HS);
+                scatter(GFo + o, P.np, d[x], d[y], HF);
+            }
+    }
+    for (size_t q = 0; q < c.couplings.size(); ++q) {
+        const PairInfo &Pa = c.pinfo.h[c.couplings[q].first], &Pb = c.pinfo.h[c.couplings[q].second];
+        const int da[2] = {Pa.i, Pa.j}, db[2] = {Pb.i, Pb.j};
+        const int na = Pa.i == Pa.j ? 1 : 2, nb_ = Pb.i == Pb.j ? 1 : 2;
+        for (int x = 0; x < na; ++x)
+            for (int y = 0; y < nb_; ++y)
+                scatter(GSco + c.coup_off[q] + (long long)x * nm * Pb.np + (long long)y * nm, Pb.np, da[x], db[y], HS);
+    }
+    e = [&]() {
+        if (bc_hs.h.empty()) return cudaSuccess;
+        cudaError_t ee = adj_alloc(*this, bc_hs.d, bc_hs.h.size());
+        if (ee != cudaSuccess) return ee;
+        return cudaMemcpy(bc_hs.d, bc_hs.h.data(), bc_hs.h.size() * sizeof(BlockCopy), cudaMemcpyHostToDevice);
+    }();
+    if (e != cudaSuccess) return e;
+    // Z^(i) from the K gradient (common fitting domain gathers as in the forward K blocks)
+    const bool full = [&]() {
+        for (int i = 0; i < n; ++i)
+            if (c.a_of(i) != c.n_aux) return false;
+        return true;
+    }();
+    std::map<long long, std::pair<const int *, const int *>> kmap;
+    std::map<long long, int> klen;
+    if (!full) {
+        // the forward's gb_k descriptors carry the common-domain lists: reuse them
+        for (const GemmDesc &g : c.gb_k.h)
+            if (g.k_idx_a) {
+                // find the pair from the destination pointer
+                const long long off = g.C - c.Kp;
+                for (size_t p = 0; p < c.pairs.size(); ++p) {
+                    const PairInfo &P = c.pinfo.h[p];
+                    if (off >= P.off && off < P.off + (long long)P.np * P.np) {
+                        kmap[(long long)P.i * n + P.j] = {g.k_idx_a, g.k_idx_b};
+                        klen[(long long)P.i * n + P.j] = g.K;
+                        break;
+                    }
+                }
+            }
+    }
+    for (size_t p = 0; p < c.pairs.size(); ++p) {
+        const PairInfo &P = c.pinfo.h[p];
+        const int i = P.i, j = P.j;
+        const long long ai = c.a_of(i), aj = c.a_of(j);
+        if (i == j) {
+            const long long o = c.w_off[i] + (long long)c.slot_of(i, i) * nm * ai;
+            for (int tr = 0; tr < 2; ++tr) {
+                GemmDesc g = gemm(nm, (int)ai, nm, GKo + P.off, P.np, tr, c.W + o, ai, 0, Z + o, ai);
+                g.atomic = 1;
+                gb_z.add(g);
+            }
+            continue;
+        }
+        const int d[2] = {i, j};
+        for (int x = 0; x < 2; ++x)
+            for (int y = 0; y < 2; ++y) {
+                const double *G = GKo + P.off + (long long)x * nm * P.np + (long long)y * nm;
+                const long long oi = c.w_off[i] + (long long)c.slot_of(i, d[x]) * nm * ai;
+                const long long oj = c.w_off[j] + (long long)c.slot_of(j, d[y]) * nm * aj;
+                // dW^(i)_x += G W^(j)_y ;  dW^(j)_y += G^T W^(i)_x  (columns on the common domain)
+                GemmDesc g1 = gemm(nm, full ? c.n_aux : 0, nm, G, P.np, 0, c.W + oj, aj, 0, Z + oi, ai);
+                GemmDesc g2 = gemm(nm, full ? c.n_aux : 0, nm, G, P.np, 1, c.W + oi, ai, 0, Z + oj, aj);
+                g1.atomic = g2.atomic = 1;
+                if (!full) {
+                    const auto &m = kmap[(long long)i * n + j];
+                    g1.N = g2.N = klen[(long long)i * n + j];
+                    g1.n_idx_b = m.second;
+                    g1.n_idx_c = m.first;
+                    g2.n_idx_b = m.first;
+                    g2.n_idx_c = m.second;
+                }
+                gb_z.add(g1);
+                gb_z.add(g2);
+            }
+    }
+    // dB_i = sum_a Q_a Z^(i)_a  (Q rows gathered with the forward's row maps)
+    {
+        size_t at = 0;
+        for (int i = 0; i < n; ++i) {
+            const long long ai = c.a_of(i);
+            const int kk = (int)c.nb[i].size() * nm;
+            GemmDesc g = gemm(nv, (int)ai, kk, c.Q, nv, 1, Z + c.w_off[i], ai, 0, dB64 + c.b_off(i), ai);
+            g.k_idx_a = c.rows_w.d + at;
+            at += kk;
+            gb_db.add(g);
+        }
+    }
+    // dQ_a (rows) += Z^(i)_a B_i^T ;  HS/HF chains
+    for (int i = 0; i < n; ++i) {
+        const long long ai = c.a_of(i);
+        for (int a : c.nb[i]) {
+            const long long o = c.w_off[i] + (long long)c.slot_of(i, a) * nm * ai;
+            GemmDesc g = gemm(nm, nv, (int)ai, Z + o, ai, 0, c.B64 + c.b_off(i), ai, 1, dQ + (long long)a * nm * nv, nv);
+            g.atomic = 1;
+            gb_dq.add(g);
+        }
+    }
+    for (size_t p = 0; p < c.pairs.size(); ++p) {
+        const int a = c.pairs[p].first, b = c.pairs[p].second;
+        const double *Hs = HS + (long long)p * nm * nm, *Hf = HF + (long long)p * nm * nm;
+        double *dQa = dQ + (long long)a * nm * nv, *dQb = dQ + (long long)b * nm * nv;
+        const double *Qa = c.Q + (long long)a * nm * nv, *Qb = c.Q + (long long)b * nm * nv;
+        const double *Qea = c.Qe + (long long)a * nm * nv, *Qeb = c.Qe + (long long)b * nm * nv;
+        GemmDesc g[4] = {gemm(nm, nv, nm, Hs, nm, 0, Qb, nv, 0, dQa, nv), gemm(nm, nv, nm, Hs, nm, 1, Qa, nv, 0, dQb, nv),
+                         gemm(nm, nv, nm, Hf, nm, 0, Qeb, nv, 0, dQa, nv), gemm(nm, nv, nm, Hf, nm, 1, Qea, nv, 0, dQb, nv)};
+        for (auto &x : g) {
+            x.atomic = 1;
+            gb_dq.add(x);
+        }
+    }
+    // relaxation
+    const long long nv2 = (long long)nv * nv;
+    for (int k = 0; k < n; ++k) {
+        gb_c.add(gemm(nv, nm, nv, c.Awork + k * nv2, nv, 0, dQ + (long long)k * nm * nv, nv, 1, Cm + (long long)k * nv * nm, nm));
+        gb_a1.add(gemm(nv, nm, nv, c.Awork + k * nv2, nv, 1, Y + (long long)k * nv * nm, nm, 0, A1 + (long long)k * nv * nm, nm));
+        gb_gt.add(gemm(nv, nv, nm, A1 + (long long)k * nv * nm, nm, 0, c.Q + (long long)k * nm * nv, nv, 0, c.Zc + k * nv2, nv));
+        gb_rb.add(gemm(nv, (int)c.a_of(k), nv, c.Zc + k * nv2, nv, 0, c.B64 + c.b_off(k), c.a_of(k), 0,
+                       dB64 + c.b_off(k), c.a_of(k), 2.0, 1.0));
+    }
+    for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2, &gb_z, &gb_db, &gb_dq,
+                         &gb_c, &gb_a1, &gb_gt, &gb_rb})
+        if ((e = gemm_batch_upload(*g)) != cudaSuccess) return e;
+    planned = true;
+    return cudaSuccess;
+}
+
+cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std::string &msg) {
+    cudaError_t e;
+    msg = "gradient_backward";
+    if (!planned && (e = plan(c)) != cudaSuccess) {
+        msg = "gradient_backward plan";
+        return e;
+    }
+    cudaStream_t s = c.stream;
+    const int n = c.n_occ, nv = c.n_vir, nm = c.nmax;
+#define CK(x) if ((e = (x)) != cudaSuccess) return e
+    CK(cudaMemsetAsync(GS, 0, c.pair_mat * sizeof(double), s));
+    CK(cudaMemsetAsync(GF, 0, c.pair_mat * sizeof(double), s));
+    CK(cudaMemsetAsync(GSc, 0, c.coup_mat * sizeof(double), s));
+    CK(cudaMemsetAsync(HS, 0, c.pairs.size() * nm * nm * sizeof(double), s));
+    CK(cudaMemsetAsync(HF, 0, c.pairs.size() * nm * nm * sizeof(double), s));
+    CK(cudaMemsetAsync(Z, 0, c.w_off[n] * sizeof(double), s));
+    CK(cudaMemsetAsync(dQ, 0, (size_t)n * nm * nv * sizeof(double), s));
+    CK(cudaMemsetAsync(dF64, 0, (size_t)n * n * sizeof(double), s));
+    AdjArgs a{};
+    a.clusters = c.cinfo.d;
+    a.slots = c.slots.d;
+    a.terms = c.terms.d;
+    a.pairs = c.pinfo.d;
+    a.rdim = c.rdim;
+    a.e = c.pe;
+    a.Tslot = c.Tslot;
+    a.Stil = c.Stil;
+    a.focc = c.focc;
+    a.n_occ = n;
+    a.ncl = (int)c.cl.size();
+    a.GS = GS;
+    a.GF = GF;
+    a.GSc = GSc;
+    a.dF = dF64;
+    a.scratch = scratch;
+    a.sstride = 5 * pstride;
+    a.pstride = pstride;
+    if (grid > 0) k_cluster_adjoint<<<grid, kThreads, 0, s>>>(a);
+    CK(cudaGetLastError());
+    if (!c.pairs.empty()) k_gk_tilde<<<(unsigned)c.pairs.size(), kThreads, 0, s>>>(c.pinfo.d, c.Tc, GK);
+    CK(cudaGetLastError());
+    for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2}) CK(gemm_batch_run(*g, s));
+    CK(launch_block_copy(bc_hs.d, (int)bc_hs.h.size(), s));
+    CK(gemm_batch_run(gb_z, s));
+    CK(gemm_batch_run(gb_db, s));
+    CK(gemm_batch_run(gb_dq, s));
+    CK(gemm_batch_run(gb_c, s));
+    {
+        const int bx = (int)std::min<long long>(((long long)nv * nm + kThreads - 1) / kThreads, 64);
+        k_relax_y<<<dim3(bx, n), kThreads, 0, s>>>(Cm, c.omega, c.nosv, Y, nv, nm);
+        CK(cudaGetLastError());
+    }
+    CK(gemm_batch_run(gb_a1, s));
+    CK(gemm_batch_run(gb_gt, s));
+    {
+        const int bx = (int)std::min<long long>(((long long)nv * nv + kThreads - 1) / kThreads, 64);
+        k_relax_sym<<<dim3(bx, n), kThreads, 0, s>>>(c.Zc, c.Tkk, c.eps, c.focc, n, nv, dF64);
+        CK(cudaGetLastError());
+    }
+    CK(gemm_batch_run(gb_rb, s));
+    const long long nb = c.aux_ptr[n] * (long long)nv;
+    if (dB) {
+        const int blocks = (int)std::min<long long>((nb + 255) / 256, 152LL * 16);
+        if (c.B_dtype == 0) k_out_b<double><<<blocks, 256, 0, s>>>(dB64, (double *)dB, nb, scale);
+        else k_out_b<float><<<blocks, 256, 0, s>>>(dB64, (float *)dB, nb, scale);
+        CK(cudaGetLastError());
+    }
+    if (dF) {
+        k_out_b<double><<<1, 256, 0, s>>>(dF64, dF, (long long)n * n, scale);
+        CK(cudaGetLastError());
+    }
+#undef CK
+    return cudaSuccess;
+}
+
+}  // namespace osv

@@ -1,0 +1,34 @@
+// Adjoint (gradient) of the MBE(3)-OSV-MP2 energy: dE/dB and dE/df_occ (amplitudes variational, Sec. 2.1).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct osv_ctx;
+
+namespace osv {
+
+struct AdjointPlan {
+    bool planned = false;
+    std::vector<void *> allocs;
+    // accumulators in the pseudo-canonical pair bases, their OSV-basis images, LMO-pair blocks
+    double *GS = nullptr, *GF = nullptr, *GK = nullptr, *GSo = nullptr, *GFo = nullptr, *GKo = nullptr,
+           *ptmp = nullptr, *GSc = nullptr, *GSco = nullptr, *ctmp = nullptr, *HS = nullptr, *HF = nullptr;
+    // chain to W, Q, B and the OSV relaxation
+    double *Z = nullptr, *dQ = nullptr, *dB64 = nullptr, *dF64 = nullptr, *Cm = nullptr, *Y = nullptr, *A1 = nullptr;
+    double *scratch = nullptr;
+    long long pstride = 0;
+    int grid = 0;
+    struct {
+        std::vector<BlockCopy> h;
+        BlockCopy *d = nullptr;
+    } bc_hs;
+    GemmBatch gb_kc1, gb_kc2, gb_f1, gb_f2, gb_k1, gb_k2, gb_c1, gb_c2, gb_z, gb_db, gb_dq, gb_c, gb_a1, gb_gt, gb_rb;
+
+    void release();
+    cudaError_t plan(osv_ctx &c);
+    cudaError_t run(osv_ctx &c, double scale, void *dB, double *dF, std::string &msg);
+};
+
+}  // namespace osv

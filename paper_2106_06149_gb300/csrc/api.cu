@@ -1,0 +1,875 @@
+// C ABI of libosvmbe: host planner (cluster selection, pair / coupling / slot layout, GEMM batches) and the
+// launch sequence of the MBE(3)-OSV-MP2 hot path.  All device shapes are planned from the padded OSV width
+// nmax, so no step waits for the device to learn the data-dependent OSV counts: padded OSV rows are zero
+// and padded pair-basis columns are dropped by the overlap eigenvalue test.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ctx.h"
+#include "launch.h"
+
+using namespace osv;
+
+namespace {
+
+thread_local std::string g_noctx_err;
+
+osv_status check_params(osv_ctx *c, const osv_params *p) {
+    if (!p) return c->fail(OSV_ERR_INVALID, "params is NULL");
+    if (!(p->tol > 0.0) || p->max_iter < 1) return c->fail(OSV_ERR_INVALID, "tol must be > 0 and max_iter >= 1");
+    if (p->n_osv_fixed <= 0 && p->n_osv_max <= 0) return c->fail(OSV_ERR_INVALID, "n_osv_max must be > 0");
+    if (p->mbe_order < 0 || p->mbe_order > 3) return c->fail(OSV_ERR_INVALID, "mbe_order must be 0..3");
+    if (!(p->tau_red >= 0.0) || !(p->r2b >= 0.0) || !(p->r3b >= 0.0) || !std::isfinite(p->l_osv))
+        return c->fail(OSV_ERR_INVALID, "tau_red, r2b, r3b must be >= 0 and l_osv finite");
+    if (p->precision != OSV_FP64 && p->precision != OSV_MIXED_TF32X3)
+        return c->fail(OSV_ERR_INVALID, "unknown precision");
+    return OSV_OK;
+}
+
+osv_status check_problem(osv_ctx *c, const osv_problem *pb) {
+    if (!pb) return c->fail(OSV_ERR_INVALID, "problem is NULL");
+    if (pb->n_occ < 1 || pb->n_vir < 1 || pb->n_aux < 1) return c->fail(OSV_ERR_INVALID, "sizes must be >= 1");
+    if (pb->n_vir > 4096) return c->fail(OSV_ERR_INVALID, "n_vir > 4096 is not supported");
+    if (!pb->centres || !pb->aux_ptr || !pb->aux_idx) return c->fail(OSV_ERR_INVALID, "host arrays are NULL");
+    if (pb->aux_ptr[0] != 0) return c->fail(OSV_ERR_INVALID, "aux_ptr[0] must be 0");
+    for (int i = 0; i < pb->n_occ; ++i) {
+        const int64_t a0 = pb->aux_ptr[i], a1 = pb->aux_ptr[i + 1];
+        if (a1 <= a0) return c->fail(OSV_ERR_INVALID, "every fitting domain must be non-empty");
+        for (int64_t q = a0; q < a1; ++q) {
+            if (pb->aux_idx[q] < 0 || pb->aux_idx[q] >= pb->n_aux)
+                return c->fail(OSV_ERR_INVALID, "aux_idx out of range");
+            if (q > a0 && pb->aux_idx[q] <= pb->aux_idx[q - 1])
+                return c->fail(OSV_ERR_INVALID, "aux_idx lists must be strictly increasing");
+        }
+    }
+    for (int i = 0; i < 3 * pb->n_occ; ++i)
+        if (!std::isfinite(pb->centres[i])) return c->fail(OSV_ERR_INVALID, "non-finite centre");
+    if (pb->B_dtype != 0 && pb->B_dtype != 1) return c->fail(OSV_ERR_INVALID, "B_dtype must be 0 or 1");
+    return OSV_OK;
+}
+
+// clusters: sorted member lists; selection rule of clusters_build
+void select_clusters(osv_ctx *c) {
+    const int n = c->n_occ;
+    const osv_params &p = c->prm;
+    c->cl.clear();
+    c->ncl_order[0] = c->ncl_order[1] = c->ncl_order[2] = 0;
+    if (p.mbe_order == 0) {
+        std::vector<int> all(n);
+        std::iota(all.begin(), all.end(), 0);
+        c->cl.push_back(all);
+        c->ncl_order[0] = 1;
+        return;
+    }
+    auto dist = [&](int i, int j) {
+        double s = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            const double d = c->centres[3 * i + x] - c->centres[3 * j + x];
+            s += d * d;
+        }
+        return std::sqrt(s);
+    };
+    for (int i = 0; i < n; ++i) c->cl.push_back({i});
+    c->ncl_order[0] = n;
+    if (p.mbe_order < 2) return;
+    std::vector<char> keep((size_t)n * n, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (dist(i, j) <= p.r2b) {
+                keep[(size_t)i * n + j] = 1;
+                c->cl.push_back({i, j});
+                ++c->ncl_order[1];
+            }
+    if (p.mbe_order < 3) return;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            if (!keep[(size_t)i * n + j]) continue;
+            for (int k = j + 1; k < n; ++k)
+                if (keep[(size_t)i * n + k] && keep[(size_t)j * n + k] && dist(i, j) <= p.r3b && dist(i, k) <= p.r3b &&
+                    dist(j, k) <= p.r3b) {
+                    c->cl.push_back({i, j, k});
+                    ++c->ncl_order[2];
+                }
+        }
+}
+
+// w_c = sum over selected supersets c' of c of (-1)^(|c'|-|c|), accumulated from each selected c' over its
+// selected subsets.
+void mbe_weights(osv_ctx *c) {
+    std::map<std::vector<int>, int> idx;
+    for (size_t q = 0; q < c->cl.size(); ++q) idx[c->cl[q]] = (int)q;
+    c->cl_w.assign(c->cl.size(), 0);
+    for (const auto &big : c->cl) {
+        const int m = (int)big.size();
+        if (m > 3) {   // the single full cluster of mbe_order 0
+            c->cl_w[idx[big]] += 1;
+            continue;
+        }
+        for (int mask = 1; mask < (1 << m); ++mask) {
+            std::vector<int> sub;
+            for (int t = 0; t < m; ++t)
+                if (mask >> t & 1) sub.push_back(big[t]);
+            auto it = idx.find(sub);
+            if (it != idx.end()) c->cl_w[it->second] += ((m - (int)sub.size()) % 2) ? -1 : 1;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *osv_last_error(const osv_ctx *ctx) { return ctx ? ctx->err.c_str() : g_noctx_err.c_str(); }
+
+osv_status osv_create(osv_ctx **ctx, void *cuda_stream) {
+    if (!ctx) return OSV_ERR_INVALID;
+    *ctx = nullptr;
+    osv_ctx *c = new (std::nothrow) osv_ctx();
+    if (!c) return OSV_ERR_OOM;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        g_noctx_err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        delete c;
+        return OSV_ERR_CUDA;
+    }
+    c->stream = (cudaStream_t)cuda_stream;
+    *ctx = c;
+    return OSV_OK;
+}
+
+osv_status osv_destroy(osv_ctx *ctx) {
+    if (!ctx) return OSV_ERR_INVALID;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    ctx->release();
+    delete ctx;
+    return OSV_OK;
+}
+
+osv_status clusters_build(osv_ctx *c, const osv_problem *pb, const osv_params *prm, int *n_clusters) {
+    if (!c) return OSV_ERR_INVALID;
+    osv_status st;
+    if ((st = check_params(c, prm)) != OSV_OK) return st;
+    if ((st = check_problem(c, pb)) != OSV_OK) return st;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->release();
+    c->prm = *prm;
+    c->n_occ = pb->n_occ;
+    c->n_vir = pb->n_vir;
+    c->n_aux = pb->n_aux;
+    c->centres.assign(pb->centres, pb->centres + 3 * pb->n_occ);
+    c->aux_ptr.assign(pb->aux_ptr, pb->aux_ptr + pb->n_occ + 1);
+    c->aux_idx.assign(pb->aux_idx, pb->aux_idx + pb->aux_ptr[pb->n_occ]);
+    select_clusters(c);
+    mbe_weights(c);
+    const int n = c->n_occ;
+    // stored pairs i <= j: every diagonal pair and every pair inside a cluster
+    c->pairs.clear();
+    c->pair_id.clear();
+    for (int i = 0; i < n; ++i) {
+        c->pair_id[(long long)i * n + i] = (int)c->pairs.size();
+        c->pairs.push_back({i, i});
+    }
+    for (const auto &m : c->cl)
+        for (size_t a = 0; a < m.size(); ++a)
+            for (size_t b = a + 1; b < m.size(); ++b) {
+                const long long key = (long long)m[a] * n + m[b];
+                if (!c->pair_id.count(key)) {
+                    c->pair_id[key] = (int)c->pairs.size();
+                    c->pairs.push_back({m[a], m[b]});
+                }
+            }
+    c->nb.assign(n, {});
+    for (int i = 0; i < n; ++i) c->nb[i].push_back(i);
+    for (const auto &pr : c->pairs)
+        if (pr.first != pr.second) {
+            c->nb[pr.first].push_back(pr.second);
+            c->nb[pr.second].push_back(pr.first);
+        }
+    for (auto &v : c->nb) std::sort(v.begin(), v.end());
+    c->have_clusters = true;
+    if (n_clusters) {
+        n_clusters[0] = c->ncl_order[0];
+        n_clusters[1] = c->ncl_order[1];
+        n_clusters[2] = c->ncl_order[2];
+    }
+    return OSV_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Host plan of slots, terms, couplings and combine lists (needs nmax).
+void plan_clusters(osv_ctx *c) {
+    const int n = c->n_occ, nm = c->nmax;
+    // pairs
+    c->pinfo.h.clear();
+    long long off = 0, eoff = 0;
+    for (const auto &pr : c->pairs) {
+        PairInfo P{};
+        P.i = pr.first;
+        P.j = pr.second;
+        P.np = pr.first == pr.second ? nm : 2 * nm;
+        P.off = off;
+        P.e_off = eoff;
+        off += (long long)P.np * P.np;
+        eoff += P.np;
+        c->pinfo.h.push_back(P);
+    }
+    c->pair_mat = off;
+    c->pair_vec = eoff;
+    // slots and terms
+    c->slots.h.clear();
+    c->terms.h.clear();
+    c->cinfo.h.clear();
+    c->couplings.clear();
+    c->coupling_id.clear();
+    long long toff = 0;
+    for (size_t q = 0; q < c->cl.size(); ++q) {
+        const auto &m = c->cl[q];
+        ClusterInfo C{};
+        C.slot0 = (int)c->slots.h.size();
+        C.term0 = (int)c->terms.h.size();
+        C.weight = c->cl_w[q];
+        C.size = (int)m.size();
+        std::map<int, int> slot_of_pair;
+        for (size_t a = 0; a < m.size(); ++a)
+            for (size_t b = a; b < m.size(); ++b) {
+                const int p = c->pid(m[a], m[b]);
+                Slot S{};
+                S.pair = p;
+                S.cluster = (int)q;
+                S.t_off = toff;
+                S.mult = a == b ? 1 : 2;
+                toff += (long long)c->pinfo.h[p].np * c->pinfo.h[p].np;
+                slot_of_pair[p] = (int)c->slots.h.size();
+                c->slots.h.push_back(S);
+            }
+        C.slot1 = (int)c->slots.h.size();
+        for (int s = C.slot0; s < C.slot1; ++s) {
+            const int p = c->slots.h[s].pair;
+            const int i = c->pinfo.h[p].i, j = c->pinfo.h[p].j;
+            auto add = [&](int x, int y, int fx, int fy) {   // amplitude t_xy, coefficient f[fx][fy]
+                const int qp = c->pid(x, y);
+                Term T{};
+                T.dst = s;
+                T.src = slot_of_pair[qp];
+                T.fx = fx;
+                T.fy = fy;
+                T.t_trans = x > y ? 1 : 0;
+                const int pa = std::min(p, qp), pb = std::max(p, qp);
+                const long long key = (long long)pa * (long long)c->pairs.size() + pb;
+                auto it = c->coupling_id.find(key);
+                int cid;
+                if (it == c->coupling_id.end()) {
+                    cid = (int)c->couplings.size();
+                    c->coupling_id[key] = cid;
+                    c->couplings.push_back({pa, pb});
+                } else {
+                    cid = it->second;
+                }
+                T.coupling = cid;
+                T.s_trans = p > qp ? 1 : 0;
+                c->terms.h.push_back(T);
+            };
+            for (int k : m) {
+                if (k != j) add(i, k, k, j);   // -f_kj S t_ik S
+                if (k != i) add(k, j, i, k);   // -f_ik S t_kj S
+            }
+        }
+        C.term1 = (int)c->terms.h.size();
+        c->cinfo.h.push_back(C);
+    }
+    c->slot_mat = toff;
+    // coupling block offsets, then patch the terms
+    c->coup_off.assign(c->couplings.size(), 0);
+    long long coff = 0;
+    for (size_t q = 0; q < c->couplings.size(); ++q) {
+        c->coup_off[q] = coff;
+        coff += (long long)c->pinfo.h[c->couplings[q].first].np * c->pinfo.h[c->couplings[q].second].np;
+    }
+    c->coup_mat = coff;
+    for (auto &T : c->terms.h) T.sblk = c->coup_off[T.coupling];
+    // processing order: most expensive clusters first
+    c->order.h.resize(c->cl.size());
+    std::iota(c->order.h.begin(), c->order.h.end(), 0);
+    std::vector<long long> cost(c->cl.size(), 0);
+    for (size_t q = 0; q < c->cl.size(); ++q)
+        for (int t = c->cinfo.h[q].term0; t < c->cinfo.h[q].term1; ++t) {
+            const long long a = c->pinfo.h[c->slots.h[c->terms.h[t].dst].pair].np;
+            const long long b = c->pinfo.h[c->slots.h[c->terms.h[t].src].pair].np;
+            cost[q] += a * b * (a + b);
+        }
+    std::stable_sort(c->order.h.begin(), c->order.h.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    // combine lists: for each pair, the slots holding it and their cluster weights
+    std::vector<std::vector<std::pair<long long, int>>> lst(c->pairs.size());
+    for (const auto &S : c->slots.h) lst[S.pair].push_back({S.t_off, c->cl_w[S.cluster]});
+    c->comb_ptr.h.assign(1, 0);
+    c->comb_src.h.clear();
+    c->comb_w.h.clear();
+    for (const auto &l : lst) {
+        for (const auto &x : l) {
+            c->comb_src.h.push_back(x.first);
+            c->comb_w.h.push_back(x.second);
+        }
+        c->comb_ptr.h.push_back((int)c->comb_src.h.size());
+    }
+    c->gstride = 4LL * nm * nm;
+    (void)n;
+}
+
+// positions of the common fitting functions of LMOs i and j in their own lists
+void common_domain(const osv_ctx *c, int i, int j, std::vector<int> &pi, std::vector<int> &pj) {
+    pi.clear();
+    pj.clear();
+    int64_t a = c->aux_ptr[i], b = c->aux_ptr[j];
+    const int64_t ae = c->aux_ptr[i + 1], be = c->aux_ptr[j + 1];
+    while (a < ae && b < be) {
+        if (c->aux_idx[a] == c->aux_idx[b]) {
+            pi.push_back(int(a - c->aux_ptr[i]));
+            pj.push_back(int(b - c->aux_ptr[j]));
+            ++a;
+            ++b;
+        } else if (c->aux_idx[a] < c->aux_idx[b]) {
+            ++a;
+        } else {
+            ++b;
+        }
+    }
+}
+
+bool full_domains(const osv_ctx *c) {
+    for (int i = 0; i < c->n_occ; ++i)
+        if (c->a_of(i) != c->n_aux) return false;
+    return true;
+}
+
+osv_status build_plan(osv_ctx *c) {
+    cudaError_t e;
+    const int n = c->n_occ, nv = c->n_vir, nm = c->nmax;
+    const long long nv2 = (long long)nv * nv;
+#define ALLOC(ptr, cnt) \
+    if ((e = c->dalloc(ptr, (size_t)(cnt))) != cudaSuccess) return c->cuda_fail(e, "cudaMalloc " #ptr)
+    ALLOC(c->Tkk, n * nv2);
+    ALLOC(c->Awork, n * nv2);
+    ALLOC(c->Zc, n * nv2);
+    ALLOC(c->omega, (long long)n * nv);
+    ALLOC(c->dsc, (long long)n * nv);
+    ALLOC(c->esc, (long long)n * nv);
+    ALLOC(c->tausc, (long long)n * nv);
+    ALLOC(c->nosv, n);
+    ALLOC(c->derr, 1);
+    ALLOC(c->Q, (long long)n * nm * nv);
+    ALLOC(c->Qe, (long long)n * nm * nv);
+    const long long np_ = (long long)c->pairs.size();
+    ALLOC(c->sblk, np_ * nm * nm);
+    ALLOC(c->fblk, np_ * nm * nm);
+    c->w_off.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) c->w_off[i + 1] = c->w_off[i] + (long long)c->nb[i].size() * nm * c->a_of(i);
+    ALLOC(c->W, c->w_off[n]);
+    ALLOC(c->Kp, c->pair_mat);
+    ALLOC(c->Sp, c->pair_mat);
+    ALLOC(c->Fp, c->pair_mat);
+    ALLOC(c->X, c->pair_mat);
+    ALLOC(c->Fx, c->pair_mat);
+    ALLOC(c->V, c->pair_mat);
+    ALLOC(c->Kt, c->pair_mat);
+    ALLOC(c->ptmp, c->pair_mat);
+    ALLOC(c->Tc, c->pair_mat);
+    ALLOC(c->pz, c->pair_mat);
+    ALLOC(c->sw, c->pair_vec);
+    ALLOC(c->pe, c->pair_vec);
+    ALLOC(c->pd, c->pair_vec);
+    ALLOC(c->pee, c->pair_vec);
+    ALLOC(c->ptau, c->pair_vec);
+    ALLOC(c->rdim, np_);
+    ALLOC(c->Scp, c->coup_mat);
+    ALLOC(c->Stil, c->coup_mat);
+    ALLOC(c->ctmp, c->coup_mat);
+    ALLOC(c->Tslot, c->slot_mat);
+    ALLOC(c->Rslot, c->slot_mat);
+    ALLOC(c->G1, (long long)c->cl.size() * c->gstride);
+    ALLOC(c->Ecl, c->cl.size());
+    ALLOC(c->iters, c->cl.size());
+    ALLOC(c->lin, np_);
+    ALLOC(c->Eout, 2);
+    if (c->B_dtype == 1) {
+        ALLOC(c->B64own, c->aux_ptr[n] * (long long)nv);
+        c->B64 = c->B64own;
+    } else {
+        c->B64 = (const double *)c->B_in;
+    }
+    const bool full = full_domains(c);
+
+    // --- a1: Gram products (ka|kb) = B_k B_k^T
+    for (int k = 0; k < n; ++k) {
+        const long long a = c->a_of(k);
+        c->gb_gram.add(gemm(nv, nv, (int)a, c->B64 + c->b_off(k), a, 0, c->B64 + c->b_off(k), a, 1,
+                            c->Tkk + k * nv2, nv));
+    }
+    // --- a2: OSV eigensolves
+    c->eig_tkk.h.clear();
+    for (int k = 0; k < n; ++k) {
+        EighDesc D{};
+        D.A = c->Awork + k * nv2;
+        D.lda = nv;
+        D.n = nv;
+        D.w = c->omega + (long long)k * nv;
+        D.Zt = c->Awork + k * nv2;
+        D.ldz = nv;
+        D.zwork = c->Zc + k * nv2;
+        D.d = c->dsc + (long long)k * nv;
+        D.e = c->esc + (long long)k * nv;
+        D.tau = c->tausc + (long long)k * nv;
+        c->eig_tkk.h.push_back(D);
+    }
+    // --- a3: LMO-pair blocks s_ij = Q_i Q_j^T, phi_ij = Q_i diag(eps) Q_j^T (rows = OSVs)
+    for (size_t p = 0; p < c->pairs.size(); ++p) {
+        const int i = c->pairs[p].first, j = c->pairs[p].second;
+        const double *Qi = c->Q + (long long)i * nm * nv;
+        c->gb_sf.add(gemm(nm, nm, nv, Qi, nv, 0, c->Q + (long long)j * nm * nv, nv, 1, c->sblk + p * nm * nm, nm));
+        c->gb_sf.add(gemm(nm, nm, nv, Qi, nv, 0, c->Qe + (long long)j * nm * nv, nv, 1, c->fblk + p * nm * nm, nm));
+    }
+    // --- a4: half transforms W^{(i)} = [Q_m]_{m in nb(i)} B_i (stacked rows), then K blocks
+    c->rows_w.h.clear();
+    std::vector<size_t> rows_at(n);
+    for (int i = 0; i < n; ++i) {
+        rows_at[i] = c->rows_w.h.size();
+        for (int m : c->nb[i])
+            for (int mu = 0; mu < nm; ++mu) c->rows_w.h.push_back(m * nm + mu);
+    }
+    c->kidx.h.clear();
+    struct KRef { size_t pi, pj; int len; };
+    std::map<long long, KRef> kref;
+    if (!full) {
+        std::vector<int> pi, pj;
+        for (const auto &pr : c->pairs) {
+            if (pr.first == pr.second) continue;
+            common_domain(c, pr.first, pr.second, pi, pj);
+            KRef r{c->kidx.h.size(), c->kidx.h.size() + pi.size(), (int)pi.size()};
+            c->kidx.h.insert(c->kidx.h.end(), pi.begin(), pi.end());
+            c->kidx.h.insert(c->kidx.h.end(), pj.begin(), pj.end());
+            kref[(long long)pr.first * n + pr.second] = r;
+        }
+    }
+    if ((e = c->upload(c->rows_w)) != cudaSuccess) return c->cuda_fail(e, "upload rows");
+    if ((e = c->upload(c->kidx)) != cudaSuccess) return c->cuda_fail(e, "upload kidx");
+    for (int i = 0; i < n; ++i) {
+        const long long a = c->a_of(i);
+        GemmDesc g = gemm((int)c->nb[i].size() * nm, (int)a, nv, c->Q, nv, 0, c->B64 + c->b_off(i), a, 0,
+                          c->W + c->w_off[i], a);
+        g.a_rows = c->rows_w.d + rows_at[i];
+        c->gb_w.add(g);
+    }
+    for (size_t p = 0; p < c->pairs.size(); ++p) {
+        const int i = c->pairs[p].first, j = c->pairs[p].second;
+        const PairInfo &P = c->pinfo.h[p];
+        const long long ai = c->a_of(i), aj = c->a_of(j);
+        if (i == j) {
+            const double *Wii = c->W + c->w_off[i] + (long long)c->slot_of(i, i) * nm * ai;
+            c->gb_k.add(gemm(nm, nm, (int)ai, Wii, ai, 0, Wii, ai, 1, c->Kp + P.off, P.np));
+            continue;
+        }
+        const int dom[2] = {i, j};
+        for (int x = 0; x < 2; ++x)
+            for (int y = 0; y < 2; ++y) {
+                const double *Wa = c->W + c->w_off[i] + (long long)c->slot_of(i, dom[x]) * nm * ai;
+                const double *Wb = c->W + c->w_off[j] + (long long)c->slot_of(j, dom[y]) * nm * aj;
+                GemmDesc g = gemm(nm, nm, full ? c->n_aux : 0, Wa, ai, 0, Wb, aj, 1,
+                                  c->Kp + P.off + (long long)x * nm * P.np + (long long)y * nm, P.np);
+                if (!full) {
+                    const KRef &r = kref[(long long)i * n + j];
+                    g.K = r.len;
+                    g.k_idx_a = c->kidx.d + r.pi;
+                    g.k_idx_b = c->kidx.d + r.pj;
+                }
+                c->gb_k.add(g);
+            }
+    }
+    // --- a5: pair bases.  S_pp / F_pp assembled from the LMO-pair blocks
+    c->bc_pair.h.clear();
+    auto blk = [&](double *base, int x, int y, bool fock) -> BlockCopy {
+        BlockCopy b{};
+        const int q = c->pid(x, y);
+        b.src = (fock ? c->fblk : c->sblk) + (long long)q * nm * nm;
+        b.trans = x > y ? 1 : 0;
+        b.rows = b.cols = nm;
+        b.lds = nm;
+        b.scale = 1.0;
+        b.dst = base;
+        return b;
+    };
+    for (size_t p = 0; p < c->pairs.size(); ++p) {
+        const PairInfo &P = c->pinfo.h[p];
+        const int dom[2] = {P.i, P.j};
+        const int nd = P.i == P.j ? 1 : 2;
+        for (int x = 0; x < nd; ++x)
+            for (int y = 0; y < nd; ++y)
+                for (int f = 0; f < 2; ++f) {
+                    BlockCopy b = blk((f ? c->Fp : c->Sp) + P.off + (long long)x * nm * P.np + (long long)y * nm,
+                                      dom[x], dom[y], f);
+                    b.ldd = P.np;
+                    c->bc_pair.h.push_back(b);
+                }
+    }
+    c->eig_s.h.clear();
+    c->eig_f.h.clear();
+    for (size_t p = 0; p < c->pairs.size(); ++p) {
+        const PairInfo &P = c->pinfo.h[p];
+        EighDesc D{};
+        D.A = c->Sp + P.off;
+        D.lda = P.np;
+        D.n = P.np;
+        D.w = c->sw + P.e_off;
+        D.Zt = c->Sp + P.off;
+        D.ldz = P.np;
+        D.zwork = c->pz + P.off;
+        D.d = c->pd + P.e_off;
+        D.e = c->pee + P.e_off;
+        D.tau = c->ptau + P.e_off;
+        c->eig_s.h.push_back(D);
+        D.A = c->Fx + P.off;
+        D.Zt = c->Fx + P.off;
+        D.w = c->pe + P.e_off;
+        D.n_dev = nullptr;   // patched after rdim upload below
+        c->eig_f.h.push_back(D);
+    }
+    for (size_t p = 0; p < c->pairs.size(); ++p) {
+        const PairInfo &P = c->pinfo.h[p];
+        c->eig_f.h[p].n_dev = c->rdim + p;
+        // F' = X^T F X
+        c->gb_fx1.add(gemm(P.np, P.np, P.np, c->Fp + P.off, P.np, 0, c->X + P.off, P.np, 0, c->ptmp + P.off, P.np));
+        c->gb_fx2.add(gemm(P.np, P.np, P.np, c->X + P.off, P.np, 1, c->ptmp + P.off, P.np, 0, c->Fx + P.off, P.np));
+        // V = X W  (W(k, c) = Wt[c][k])
+        c->gb_v.add(gemm(P.np, P.np, P.np, c->X + P.off, P.np, 0, c->Fx + P.off, P.np, 1, c->V + P.off, P.np));
+        // K~ = V^T K V
+        c->gb_kt1.add(gemm(P.np, P.np, P.np, c->Kp + P.off, P.np, 0, c->V + P.off, P.np, 0, c->ptmp + P.off, P.np));
+        c->gb_kt2.add(gemm(P.np, P.np, P.np, c->V + P.off, P.np, 1, c->ptmp + P.off, P.np, 0, c->Kt + P.off, P.np));
+    }
+    // coupling blocks S~_(pa,pb) = V_pa^T S_(pa,pb) V_pb
+    c->bc_coup.h.clear();
+    for (size_t q = 0; q < c->couplings.size(); ++q) {
+        const PairInfo &Pa = c->pinfo.h[c->couplings[q].first], &Pb = c->pinfo.h[c->couplings[q].second];
+        const int da[2] = {Pa.i, Pa.j}, db[2] = {Pb.i, Pb.j};
+        const int na = Pa.i == Pa.j ? 1 : 2, nbb = Pb.i == Pb.j ? 1 : 2;
+        for (int x = 0; x < na; ++x)
+            for (int y = 0; y < nbb; ++y) {
+                BlockCopy b = blk(c->Scp + c->coup_off[q] + (long long)x * nm * Pb.np + (long long)y * nm, da[x],
+                                  db[y], false);
+                b.ldd = Pb.np;
+                c->bc_coup.h.push_back(b);
+            }
+        c->gb_c1.add(gemm(Pa.np, Pb.np, Pb.np, c->Scp + c->coup_off[q], Pb.np, 0, c->V + Pb.off, Pb.np, 0,
+                          c->ctmp + c->coup_off[q], Pb.np));
+        c->gb_c2.add(gemm(Pa.np, Pb.np, Pa.np, c->V + Pa.off, Pa.np, 1, c->ctmp + c->coup_off[q], Pb.np, 0,
+                          c->Stil + c->coup_off[q], Pb.np));
+    }
+#undef ALLOC
+    for (HostDev<PairInfo> *h : {&c->pinfo}) if ((e = c->upload(*h)) != cudaSuccess) return c->cuda_fail(e, "upload");
+    if ((e = c->upload(c->slots)) != cudaSuccess) return c->cuda_fail(e, "upload slots");
+    if ((e = c->upload(c->terms)) != cudaSuccess) return c->cuda_fail(e, "upload terms");
+    if ((e = c->upload(c->cinfo)) != cudaSuccess) return c->cuda_fail(e, "upload clusters");
+    if ((e = c->upload(c->order)) != cudaSuccess) return c->cuda_fail(e, "upload order");
+    if ((e = c->upload(c->comb_ptr)) != cudaSuccess) return c->cuda_fail(e, "upload comb");
+    if ((e = c->upload(c->comb_src)) != cudaSuccess) return c->cuda_fail(e, "upload comb");
+    if ((e = c->upload(c->comb_w)) != cudaSuccess) return c->cuda_fail(e, "upload comb");
+    if ((e = c->upload(c->bc_pair)) != cudaSuccess) return c->cuda_fail(e, "upload bc");
+    if ((e = c->upload(c->bc_coup)) != cudaSuccess) return c->cuda_fail(e, "upload bc");
+    if ((e = c->upload(c->eig_tkk)) != cudaSuccess) return c->cuda_fail(e, "upload eig");
+    if ((e = c->upload(c->eig_s)) != cudaSuccess) return c->cuda_fail(e, "upload eig");
+    if ((e = c->upload(c->eig_f)) != cudaSuccess) return c->cuda_fail(e, "upload eig");
+    for (GemmBatch *g : {&c->gb_gram, &c->gb_sf, &c->gb_w, &c->gb_k, &c->gb_fx1, &c->gb_fx2, &c->gb_v, &c->gb_kt1,
+                         &c->gb_kt2, &c->gb_c1, &c->gb_c2})
+        if ((e = gemm_batch_upload(*g)) != cudaSuccess) return c->cuda_fail(e, "upload gemm batch");
+    return OSV_OK;
+}
+
+osv_status run_osv_build(osv_ctx *c) {
+    cudaError_t e;
+    cudaStream_t s = c->stream;
+    const int n = c->n_occ, nv = c->n_vir, nm = c->nmax;
+#define CK(x, what) \
+    if ((e = (x)) != cudaSuccess) return c->cuda_fail(e, what)
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(int), s), "memset");
+    if (c->B_dtype == 1) CK(launch_f32_to_f64((const float *)c->B_in, c->B64own, c->aux_ptr[n] * (long long)nv, s), "f32->f64");
+    CK(gemm_batch_run(c->gb_gram, s), "gram");
+    CK(launch_tkk_scale(c->Tkk, c->Awork, c->eps, c->focc, n, nv, c->derr, s), "tkk");
+    CK(eigh_batched(c->eig_tkk.d, n, nv, 0, c->derr, s), "osv eigh");
+    CK(launch_osv_select(c->Awork, c->omega, c->eps, c->Q, c->Qe, c->nosv, n, nv, nm, c->prm.l_osv,
+                         c->prm.n_osv_fixed, s), "select");
+    CK(gemm_batch_run(c->gb_sf, s), "s/f blocks");
+    CK(gemm_batch_run(c->gb_w, s), "half transform");
+    CK(gemm_batch_run(c->gb_k, s), "K blocks");
+    CK(launch_block_copy(c->bc_pair.d, (int)c->bc_pair.h.size(), s), "pair assemble");
+    CK(eigh_batched(c->eig_s.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair overlap eigh");
+    CK(launch_pair_x(c->pinfo.d, (int)c->pairs.size(), c->Sp, c->sw, c->X, c->rdim, c->prm.tau_red, s), "pair x");
+    CK(gemm_batch_run(c->gb_fx1, s), "fx1");
+    CK(gemm_batch_run(c->gb_fx2, s), "fx2");
+    CK(eigh_batched(c->eig_f.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair fock eigh");
+    CK(launch_clean_w(c->pinfo.d, (int)c->pairs.size(), c->rdim, c->Fx, c->pe, s), "clean");
+    CK(gemm_batch_run(c->gb_v, s), "V");
+    CK(gemm_batch_run(c->gb_kt1, s), "kt1");
+    CK(gemm_batch_run(c->gb_kt2, s), "kt2");
+    CK(launch_block_copy(c->bc_coup.d, (int)c->bc_coup.h.size(), s), "coupling assemble");
+    CK(gemm_batch_run(c->gb_c1, s), "c1");
+    CK(gemm_batch_run(c->gb_c2, s), "c2");
+#undef CK
+    return OSV_OK;
+}
+
+osv_status device_error(osv_ctx *c) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return c->cuda_fail(e, "read error word");
+    if (h == kDevEighNoConv) return c->fail(OSV_ERR_TIMEOUT, "eigensolver hit its iteration cap");
+    if (h == kDevNonFinite) return c->fail(OSV_ERR_NUMERIC, "non-finite value in T_kk (check B, eps, f_occ)");
+    return OSV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+osv_status osv_build(osv_ctx *c, const osv_problem *pb, const osv_params *prm, int *n_osv_out) {
+    if (!c) return OSV_ERR_INVALID;
+    if (!c->have_clusters) return c->fail(OSV_ERR_INVALID, "clusters_build must precede osv_build");
+    osv_status st;
+    if ((st = check_params(c, prm)) != OSV_OK) return st;
+    if ((st = check_problem(c, pb)) != OSV_OK) return st;
+    if (pb->n_occ != c->n_occ || pb->n_vir != c->n_vir || pb->n_aux != c->n_aux ||
+        memcmp(pb->aux_ptr, c->aux_ptr.data(), (c->n_occ + 1) * sizeof(int64_t)) != 0 ||
+        memcmp(pb->aux_idx, c->aux_idx.data(), c->aux_idx.size() * sizeof(int32_t)) != 0 ||
+        prm->mbe_order != c->prm.mbe_order || prm->r2b != c->prm.r2b || prm->r3b != c->prm.r3b)
+        return c->fail(OSV_ERR_INVALID, "problem or cluster parameters differ from clusters_build");
+    if (!pb->f_occ || !pb->eps_vir || !pb->B) return c->fail(OSV_ERR_INVALID, "device arrays are NULL");
+    cudaSetDevice(c->device);
+    const int nmax = prm->n_osv_fixed > 0 ? std::min(prm->n_osv_fixed, pb->n_vir) : std::min(prm->n_osv_max, pb->n_vir);
+    const bool replan = !c->built || nmax != c->nmax || pb->B_dtype != c->B_dtype || pb->B != c->B_in;
+    c->prm = *prm;
+    c->focc = pb->f_occ;
+    c->eps = pb->eps_vir;
+    if (replan) {
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        c->release();
+        c->nmax = nmax;
+        c->B_in = pb->B;
+        c->B_dtype = pb->B_dtype;
+        plan_clusters(c);
+        if ((st = build_plan(c)) != OSV_OK) {
+            c->release();
+            return st;
+        }
+        c->built = true;
+    }
+    c->solved = false;
+    if ((st = run_osv_build(c)) != OSV_OK) return st;
+    if (n_osv_out) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return c->cuda_fail(e, "osv_build");
+        if ((st = device_error(c)) != OSV_OK) return st;
+        e = cudaMemcpy(n_osv_out, c->nosv, c->n_occ * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return c->cuda_fail(e, "copy n_osv");
+    }
+    return OSV_OK;
+}
+
+osv_status cluster_residual_solve(osv_ctx *c, int *n_iter_out, int32_t *cluster_status) {
+    if (!c) return OSV_ERR_INVALID;
+    if (!c->built) return c->fail(OSV_ERR_INVALID, "osv_build must precede cluster_residual_solve");
+    cudaSetDevice(c->device);
+    cudaError_t e;
+    SolveArgs a{};
+    a.clusters = c->cinfo.d;
+    a.order = c->order.d;
+    a.slots = c->slots.d;
+    a.terms = c->terms.d;
+    a.pairs = c->pinfo.d;
+    a.rdim = c->rdim;
+    a.e = c->pe;
+    a.Kt = c->Kt;
+    a.sblk = c->Stil;
+    a.focc = c->focc;
+    a.n_occ = c->n_occ;
+    a.T = c->Tslot;
+    a.R = c->Rslot;
+    a.G1 = c->G1;
+    a.gstride = c->gstride;
+    a.E_cluster = c->Ecl;
+    a.iters = c->iters;
+    a.tol = c->prm.tol;
+    a.max_iter = c->prm.max_iter;
+    if ((e = cudaMemsetAsync(c->Tslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
+        return c->cuda_fail(e, "memset T");
+    if ((e = cudaMemsetAsync(c->Rslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
+        return c->cuda_fail(e, "memset R");
+    if ((e = launch_residual(a, (int)c->cl.size(), c->stream)) != cudaSuccess) return c->cuda_fail(e, "residual");
+    if (cluster_status) {
+        if ((e = cudaMemcpyAsync(cluster_status, c->iters, c->cl.size() * sizeof(int), cudaMemcpyDeviceToDevice,
+                                 c->stream)) != cudaSuccess)
+            return c->cuda_fail(e, "status copy");
+    }
+    c->solved = true;
+    if (n_iter_out) {
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "residual");
+        osv_status st = device_error(c);
+        if (st != OSV_OK) return st;
+        std::vector<int> it(c->cl.size());
+        if ((e = cudaMemcpy(it.data(), c->iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return c->cuda_fail(e, "iters");
+        int mx = 0;
+        bool nc = false;
+        for (int v : it) {
+            if (v < 0) nc = true;
+            mx = std::max(mx, v);
+        }
+        *n_iter_out = nc ? c->prm.max_iter : mx;
+        if (nc) return c->fail(OSV_ERR_NOCONV, "some clusters did not converge");
+    }
+    return OSV_OK;
+}
+
+osv_status mbe3_combine(osv_ctx *c) {
+    if (!c) return OSV_ERR_INVALID;
+    if (!c->solved) return c->fail(OSV_ERR_INVALID, "cluster_residual_solve must precede mbe3_combine");
+    cudaSetDevice(c->device);
+    cudaError_t e = launch_combine(c->pinfo.d, (int)c->pairs.size(), c->comb_ptr.d, c->comb_src.d, c->comb_w.d,
+                                   c->Tslot, c->Tc, c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "combine");
+    return OSV_OK;
+}
+
+osv_status energy(osv_ctx *c, double *E_out, double *E_linear_out) {
+    if (!c || !E_out) return c ? c->fail(OSV_ERR_INVALID, "E_out is NULL") : OSV_ERR_INVALID;
+    if (!c->solved) return c->fail(OSV_ERR_INVALID, "cluster_residual_solve must precede energy");
+    cudaSetDevice(c->device);
+    cudaError_t e = launch_energy(c->pinfo.d, c->rdim, c->Kt, c->Tc, (int)c->pairs.size(), c->lin, c->Ecl,
+                                  c->cinfo.d, (int)c->cl.size(), c->Eout, c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "energy");
+    double h[2];
+    if ((e = cudaMemcpyAsync(h, c->Eout, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return c->cuda_fail(e, "energy copy");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "energy");
+    osv_status st = device_error(c);
+    if (st != OSV_OK) return st;
+    *E_out = h[0];
+    if (E_linear_out) *E_linear_out = h[1];
+    if (!std::isfinite(h[0])) return c->fail(OSV_ERR_NUMERIC, "energy is not finite");
+    return OSV_OK;
+}
+
+osv_status osv_cluster_count(osv_ctx *c, int *n_clusters) {
+    if (!c || !n_clusters) return OSV_ERR_INVALID;
+    *n_clusters = (int)c->cl.size();
+    return OSV_OK;
+}
+
+osv_status osv_cluster_info(osv_ctx *c, int32_t *members, int32_t *weight, double *en, int32_t *iters) {
+    if (!c) return OSV_ERR_INVALID;
+    const size_t nc = c->cl.size();
+    if (members)
+        for (size_t q = 0; q < nc; ++q)
+            for (int t = 0; t < 3; ++t) members[3 * q + t] = t < (int)c->cl[q].size() ? c->cl[q][t] : -1;
+    if (weight)
+        for (size_t q = 0; q < nc; ++q) weight[q] = c->cl_w[q];
+    if ((en || iters) && !c->solved) return c->fail(OSV_ERR_INVALID, "no solved clusters");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sync");
+    if (en && (e = cudaMemcpy(en, c->Ecl, nc * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy");
+    if (iters && (e = cudaMemcpy(iters, c->iters, nc * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy");
+    return OSV_OK;
+}
+
+osv_status osv_eigenvalues(osv_ctx *c, int k, double *w_out) {
+    if (!c || !w_out) return OSV_ERR_INVALID;
+    if (!c->built || k < 0 || k >= c->n_occ) return c->fail(OSV_ERR_INVALID, "bad LMO index or not built");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sync");
+    if ((e = cudaMemcpy(w_out, c->omega + (long long)k * c->n_vir, c->n_vir * sizeof(double),
+                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy");
+    return OSV_OK;
+}
+
+osv_status gradient_backward(osv_ctx *c, double dE_scale, void *dE_dB, double *dE_dFocc) {
+    if (!c) return OSV_ERR_INVALID;
+    if (!c->solved) return c->fail(OSV_ERR_INVALID, "cluster_residual_solve must precede gradient_backward");
+    cudaSetDevice(c->device);
+    std::string msg;
+    cudaError_t e = c->adj.run(*c, dE_scale, dE_dB, dE_dFocc, msg);
+    if (e != cudaSuccess) return c->cuda_fail(e, msg.c_str());
+    return OSV_OK;
+}
+
+osv_status osv_syev_batched(const double *A, int n, int batch, double *w, double *Zt, void *cuda_stream) {
+    if (!A || !w || !Zt || n < 1 || n > 4096 || batch < 1) {
+        g_noctx_err = "osv_syev_batched: bad argument";
+        return OSV_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const long long nn = (long long)n * n;
+    double *work = nullptr, *zw = nullptr, *vec = nullptr;
+    int *err = nullptr;
+    auto cleanup = [&]() {
+        if (work) cudaFree(work);
+        if (zw) cudaFree(zw);
+        if (vec) cudaFree(vec);
+        if (err) cudaFree(err);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&work, batch * nn * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&zw, batch * nn * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&vec, 3LL * batch * n * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&err, sizeof(int))) != cudaSuccess) {
+        cleanup();
+        g_noctx_err = std::string("osv_syev_batched: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? OSV_ERR_OOM : OSV_ERR_CUDA;
+    }
+    std::vector<EighDesc> h(batch);
+    for (int b = 0; b < batch; ++b) {
+        EighDesc &D = h[b];
+        D.A = work + b * nn;
+        D.lda = n;
+        D.n = n;
+        D.w = w + (long long)b * n;
+        D.Zt = Zt + b * nn;
+        D.ldz = n;
+        D.zwork = zw + b * nn;
+        D.d = vec + 3LL * b * n;
+        D.e = D.d + n;
+        D.tau = D.e + n;
+    }
+    EighDesc *dd = nullptr;
+    if ((e = cudaMalloc(&dd, batch * sizeof(EighDesc))) == cudaSuccess &&
+        (e = cudaMemcpyAsync(dd, h.data(), batch * sizeof(EighDesc), cudaMemcpyHostToDevice, s)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(work, A, batch * nn * sizeof(double), cudaMemcpyDeviceToDevice, s)) == cudaSuccess &&
+        (e = cudaMemsetAsync(err, 0, sizeof(int), s)) == cudaSuccess &&
+        (e = eigh_batched(dd, batch, n, 0, err, s)) == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (dd) cudaFree(dd);
+    cleanup();
+    if (e != cudaSuccess) {
+        g_noctx_err = std::string("osv_syev_batched: ") + cudaGetErrorString(e);
+        return OSV_ERR_CUDA;
+    }
+    if (herr) {
+        g_noctx_err = "osv_syev_batched: QL iteration cap reached";
+        return OSV_ERR_TIMEOUT;
+    }
+    return OSV_OK;
+}
+
+}  // extern "C"

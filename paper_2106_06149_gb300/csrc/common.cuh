@@ -1,0 +1,122 @@
+// Shared device/host helpers of libosvmbe (GB300, sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+namespace osv {
+
+constexpr int kWarp = 32;
+
+// Error word written by bounded device loops (never a trap).
+enum DevErr : int { kDevOk = 0, kDevEighNoConv = 1, kDevNonFinite = 2 };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum; every thread gets the result.  `red` holds >= blockDim.x/32 doubles.  Deterministic.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    return s;
+}
+
+__device__ __forceinline__ double block_max(double v, double *red) {
+    v = warp_max(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = red[0];
+    for (int w = 1; w < nw; ++w) s = fmax(s, red[w]);
+    return s;
+}
+
+// ------------------------------------------------------------------------------------ grouped FP64 GEMM
+// C[M x N] = alpha * opA(A)[M x K] * opB(B)[K x N] + beta * C, every matrix row-major.
+//   transA = 0: A(m,k) = A[arow(m) * lda + acol(k)],  transA = 1: A(m,k) = A[acol(k) * lda + m]
+//   transB = 0: B(k,n) = B[brow(k) * ldb + bcol(n)],  transB = 1: B(k,n) = B[bcol(n) * ldb + brow(k)]
+//   arow(m) = a_rows ? a_rows[m] : m;  acol(k) = k_idx_a ? k_idx_a[k] : k
+//   brow(k) = k_idx_b ? k_idx_b[k] : k;  bcol(n) = n_idx_b ? n_idx_b[n] : n
+//   C(m,n) at C[m * ldc + ccol(n)], ccol(n) = n_idx_c ? n_idx_c[n] : n
+//   atomic = 1: C(m,n) += alpha * acc with atomicAdd (beta ignored).
+struct GemmDesc {
+    int M, N, K;
+    int transA, transB, atomic;
+    long long lda, ldb, ldc;
+    const double *A;
+    const double *B;
+    double *C;
+    double alpha, beta;
+    const int *a_rows;
+    const int *k_idx_a;
+    const int *k_idx_b;
+    const int *n_idx_b;
+    const int *n_idx_c;
+};
+
+// Host-side batch of GEMM problems: descriptors and per-problem tile offsets live in device memory.
+struct GemmBatch {
+    std::vector<GemmDesc> h;
+    GemmDesc *d_desc = nullptr;
+    long long *d_tile0 = nullptr;
+    long long tiles = 0;
+    void add(const GemmDesc &g) { h.push_back(g); }
+};
+
+cudaError_t gemm_batch_upload(GemmBatch &b);
+cudaError_t gemm_batch_run(const GemmBatch &b, cudaStream_t s);
+void gemm_batch_free(GemmBatch &b);
+
+inline GemmDesc gemm(int M, int N, int K, const double *A, long long lda, int tA, const double *B,
+                     long long ldb, int tB, double *C, long long ldc, double alpha = 1.0, double beta = 0.0) {
+    GemmDesc g{};
+    g.M = M; g.N = N; g.K = K;
+    g.A = A; g.lda = lda; g.transA = tA;
+    g.B = B; g.ldb = ldb; g.transB = tB;
+    g.C = C; g.ldc = ldc;
+    g.alpha = alpha; g.beta = beta;
+    return g;
+}
+
+// ------------------------------------------------------------------------------------- batched eigh
+// One symmetric matrix A (n x n, row-major, leading dimension lda) to diagonalise.  A is overwritten.
+// n_dev (optional): device int with the actual order (<= n) used instead of n; the rest is left alone.
+// Output: w (decreasing eigenvalues), Zt (eigenvector mu in row mu, leading dimension ldz).
+// zwork: n x n scratch (column-major eigenvector accumulation).
+struct EighDesc {
+    double *A;
+    long long lda;
+    int n;
+    const int *n_dev;
+    double *w;
+    double *Zt;
+    long long ldz;
+    double *zwork;
+    double *d;     // n scratch (diagonal)
+    double *e;     // n scratch (sub-diagonal)
+    double *tau;   // n scratch (Householder scalars)
+};
+
+// Diagonalise every matrix of the batch; err (device int) receives kDevEighNoConv on an iteration cap.
+cudaError_t eigh_batched(const EighDesc *d_desc, int batch, int n_max, int rows_split, int *err,
+                         cudaStream_t s);
+
+}  // namespace osv

@@ -1,0 +1,137 @@
+// Context of libosvmbe (shared by the C ABI in api.cu and the adjoint in adjoint.cu).
+#pragma once
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/osvmbe.h"
+#include "adjoint.h"
+
+namespace osv {
+template <class T>
+struct HostDev {
+    std::vector<T> h;
+    T *d = nullptr;
+};
+}  // namespace osv
+
+struct osv_ctx {
+    template <class T>
+    using HostDev = osv::HostDev<T>;
+    using GemmBatch = osv::GemmBatch;
+    using PairInfo = osv::PairInfo;
+    using Slot = osv::Slot;
+    using Term = osv::Term;
+    using ClusterInfo = osv::ClusterInfo;
+    using BlockCopy = osv::BlockCopy;
+    using EighDesc = osv::EighDesc;
+    using GemmDesc = osv::GemmDesc;
+
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // problem and parameters
+    osv_params prm{};
+    int n_occ = 0, n_vir = 0, n_aux = 0, nmax = 0;
+    std::vector<double> centres;
+    std::vector<int64_t> aux_ptr;
+    std::vector<int32_t> aux_idx;
+    const double *focc = nullptr, *eps = nullptr;
+    const void *B_in = nullptr;
+    int B_dtype = 0;
+    const double *B64 = nullptr;   // fp64 DF blocks (caller's buffer or the internal copy)
+
+    // clusters (host)
+    bool have_clusters = false, built = false, solved = false;
+    std::vector<std::vector<int>> cl;
+    std::vector<int> cl_w;
+    int ncl_order[3] = {0, 0, 0};
+
+    // pairs / neighbours / couplings (host)
+    std::vector<std::pair<int, int>> pairs;
+    std::map<long long, int> pair_id;
+    std::vector<std::vector<int>> nb;
+    std::map<long long, int> coupling_id;
+    std::vector<std::pair<int, int>> couplings;
+
+    // device arrays
+    std::vector<void *> allocs;
+    double *Tkk = nullptr, *Awork = nullptr, *Zc = nullptr, *omega = nullptr, *dsc = nullptr, *esc = nullptr,
+           *tausc = nullptr;
+    int *nosv = nullptr, *derr = nullptr;
+    double *B64own = nullptr;
+    double *Q = nullptr, *Qe = nullptr, *sblk = nullptr, *fblk = nullptr, *W = nullptr;
+    std::vector<long long> w_off;          // per LMO offset of W^{(i)} (doubles)
+    double *Kp = nullptr, *Sp = nullptr, *Fp = nullptr, *X = nullptr, *Fx = nullptr, *V = nullptr, *Kt = nullptr,
+           *ptmp = nullptr, *Tc = nullptr, *sw = nullptr, *pe = nullptr, *pz = nullptr, *pd = nullptr,
+           *pee = nullptr, *ptau = nullptr;
+    int *rdim = nullptr;
+    long long pair_mat = 0, pair_vec = 0;  // totals
+    double *Scp = nullptr, *Stil = nullptr, *ctmp = nullptr;
+    long long coup_mat = 0;
+    double *Tslot = nullptr, *Rslot = nullptr, *G1 = nullptr, *Ecl = nullptr, *lin = nullptr, *Eout = nullptr;
+    int *iters = nullptr;
+    long long slot_mat = 0, gstride = 0;
+
+    HostDev<PairInfo> pinfo;
+    HostDev<Slot> slots;
+    HostDev<Term> terms;
+    HostDev<ClusterInfo> cinfo;
+    HostDev<int> order;
+    HostDev<int> comb_ptr, comb_w;
+    HostDev<long long> comb_src;
+    std::vector<long long> coup_off;       // per coupling offset (doubles) of its n_pa x n_pb blocks
+    HostDev<BlockCopy> bc_pair, bc_coup;
+    HostDev<EighDesc> eig_tkk, eig_s, eig_f;
+    HostDev<int> rows_w;                   // a_rows maps for the half transforms
+    HostDev<int> kidx;                     // common-fitting-domain position lists
+    GemmBatch gb_gram, gb_sf, gb_w, gb_k, gb_fx1, gb_fx2, gb_v, gb_kt1, gb_kt2, gb_c1, gb_c2;
+
+    osv::AdjointPlan adj;
+
+    osv_status fail(osv_status s, const std::string &m) {
+        err = m;
+        return s;
+    }
+    osv_status cuda_fail(cudaError_t e, const char *where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? OSV_ERR_OOM : OSV_ERR_CUDA;
+    }
+    template <class T>
+    cudaError_t dalloc(T *&p, size_t count) {
+        p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e == cudaSuccess) allocs.push_back((void *)p);
+        return e;
+    }
+    template <class T>
+    cudaError_t upload(HostDev<T> &hd) {
+        cudaError_t e = dalloc(hd.d, hd.h.size());
+        if (e != cudaSuccess || hd.h.empty()) return e;
+        return cudaMemcpy(hd.d, hd.h.data(), hd.h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    }
+    void release() {
+        for (void *p : allocs) cudaFree(p);
+        allocs.clear();
+        for (GemmBatch *g : {&gb_gram, &gb_sf, &gb_w, &gb_k, &gb_fx1, &gb_fx2, &gb_v, &gb_kt1, &gb_kt2, &gb_c1, &gb_c2}) {
+            gemm_batch_free(*g);
+            g->h.clear();
+        }
+        adj.release();
+        built = solved = false;
+    }
+    int pid(int i, int j) const {
+        auto it = pair_id.find((long long)std::min(i, j) * n_occ + std::max(i, j));
+        return it == pair_id.end() ? -1 : it->second;
+    }
+    int slot_of(int i, int m) const {   // position of m in nb(i)
+        const auto &v = nb[i];
+        return int(std::lower_bound(v.begin(), v.end(), m) - v.begin());
+    }
+    long long a_of(int i) const { return aux_ptr[i + 1] - aux_ptr[i]; }
+    long long b_off(int i) const { return aux_ptr[i] * (long long)n_vir; }
+};
+

@@ -1,0 +1,149 @@
+// Grouped FP64 GEMM on the CUDA cores: one launch runs every problem of a batch (the FP64 path's dense
+// contractions: T_kk Gram products, half transforms, pair blocks, adjoint products).  64 x 64 output tile per
+// CTA, 256 threads with a 4 x 4 register tile each, K staged through shared memory in steps of 16.
+// Optional row/column index maps let one descriptor read a gathered operand (local fitting domains, stacked
+// OSV sets) without a copy.
+#include "common.cuh"
+
+namespace osv {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__global__ void __launch_bounds__(NT) k_gemm_fp64(const GemmDesc *__restrict__ descs,
+                                                   const long long *__restrict__ tile0, int nprob) {
+    // locate the problem of this tile (tile0 is increasing, tile0[nprob] = total)
+    const long long t = blockIdx.x;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const GemmDesc g = descs[lo];
+    const long long local = t - tile0[lo];
+    const int tiles_n = (g.N + BN - 1) / BN;
+    const int m0 = int(local / tiles_n) * BM, n0 = int(local % tiles_n) * BN;
+
+    __shared__ double As[2][BK][BM + 1];
+    __shared__ double Bs[2][BK][BN + 1];
+
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tc = tid % 16;   // 16 x 16 thread grid, 4 x 4 outputs each (stride 16)
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+    auto load = [&](int buf, int k0) {
+        // A tile: BM x BK elements, 4 per thread
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + r * NT;
+            int mm, kk;
+            if (g.transA == 0) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
+            const int m = m0 + mm, k = k0 + kk;
+            double v = 0.0;
+            if (m < g.M && k < g.K) {
+                const long long kc = g.k_idx_a ? g.k_idx_a[k] : k;
+                if (g.transA == 0) {
+                    const long long mr = g.a_rows ? g.a_rows[m] : m;
+                    v = g.A[mr * g.lda + kc];
+                } else {
+                    v = g.A[kc * g.lda + m];
+                }
+            }
+            As[buf][kk][mm] = v;
+        }
+        // B tile: BK x BN elements
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + r * NT;
+            int kk, nn;
+            if (g.transB == 0) { kk = e / BN; nn = e % BN; } else { nn = e / BK; kk = e % BK; }
+            const int n = n0 + nn, k = k0 + kk;
+            double v = 0.0;
+            if (n < g.N && k < g.K) {
+                const long long kr = g.k_idx_b ? g.k_idx_b[k] : k;
+                const long long nc = g.n_idx_b ? g.n_idx_b[n] : n;
+                v = (g.transB == 0) ? g.B[kr * g.ldb + nc] : g.B[nc * g.ldb + kr];
+            }
+            Bs[buf][kk][nn] = v;
+        }
+    };
+
+    const int nk = (g.K + BK - 1) / BK;
+    if (nk > 0) load(0, 0);
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < nk) load(buf ^ 1, (kt + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tr + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tc + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + tr + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tc + 16 * j;
+            if (n >= g.N) continue;
+            const long long nc = g.n_idx_c ? g.n_idx_c[n] : n;
+            double *c = g.C + (long long)m * g.ldc + nc;
+            if (g.atomic) atomicAdd(c, g.alpha * acc[i][j]);
+            else *c = g.alpha * acc[i][j] + (g.beta != 0.0 ? g.beta * *c : 0.0);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t gemm_batch_upload(GemmBatch &b) {
+    gemm_batch_free(b);
+    if (b.h.empty()) return cudaSuccess;
+    std::vector<long long> t0(b.h.size() + 1, 0);
+    for (size_t i = 0; i < b.h.size(); ++i) {
+        const GemmDesc &g = b.h[i];
+        long long tiles = (g.M > 0 && g.N > 0) ? (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) : 0;
+        t0[i + 1] = t0[i] + tiles;
+    }
+    b.tiles = t0.back();
+    cudaError_t e = cudaMalloc(&b.d_desc, b.h.size() * sizeof(GemmDesc));
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&b.d_tile0, t0.size() * sizeof(long long));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(b.d_desc, b.h.data(), b.h.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(b.d_tile0, t0.data(), t0.size() * sizeof(long long), cudaMemcpyHostToDevice);
+}
+
+cudaError_t gemm_batch_run(const GemmBatch &b, cudaStream_t s) {
+    if (b.tiles == 0) return cudaSuccess;
+    // problems without tiles are skipped by the search: tile0 is non-decreasing and the search picks the
+    // last problem whose first tile is <= t, which is the one owning t.
+    k_gemm_fp64<<<(unsigned)b.tiles, NT, 0, s>>>(b.d_desc, b.d_tile0, (int)b.h.size());
+    return cudaGetLastError();
+}
+
+void gemm_batch_free(GemmBatch &b) {
+    if (b.d_desc) cudaFree(b.d_desc);
+    if (b.d_tile0) cudaFree(b.d_tile0);
+    b.d_desc = nullptr;
+    b.d_tile0 = nullptr;
+    b.tiles = 0;
+}
+
+}  // namespace osv

@@ -1,0 +1,26 @@
+// Host-side launchers of the device kernels (each returns the launch status; none synchronises).
+#pragma once
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace osv {
+
+cudaError_t launch_f32_to_f64(const float *in, double *out, long long n, cudaStream_t s);
+cudaError_t launch_tkk_scale(double *T, double *work, const double *eps, const double *focc, int n_occ, int nv,
+                             int *err, cudaStream_t s);
+cudaError_t launch_osv_select(const double *Zt, const double *omega, const double *eps, double *Q, double *Qe,
+                              int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed, cudaStream_t s);
+cudaError_t launch_block_copy(const BlockCopy *d_bc, int n, cudaStream_t s);
+cudaError_t launch_pair_x(const PairInfo *pairs, int npairs, const double *Ut, const double *sv, double *X,
+                          int *rdim, double tau_red, cudaStream_t s);
+cudaError_t launch_clean_w(const PairInfo *pairs, int npairs, const int *rdim, double *Wt, double *e,
+                           cudaStream_t s);
+cudaError_t launch_residual(const SolveArgs &a, int nclusters, cudaStream_t s);
+cudaError_t launch_combine(const PairInfo *pairs, int npairs, const int *ptr, const long long *src, const int *w,
+                           const double *T, double *Tc, cudaStream_t s);
+cudaError_t launch_energy(const PairInfo *pairs, const int *rdim, const double *Kt, const double *Tc, int npairs,
+                          double *lin, const double *Ec, const ClusterInfo *cl, int ncl, double *out,
+                          cudaStream_t s);
+
+}  // namespace osv

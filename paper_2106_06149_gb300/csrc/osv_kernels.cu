@@ -1,0 +1,159 @@
+// Element-wise and bookkeeping kernels of the OSV build (Sec. 2.1, Eqs. 5-7).
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace osv {
+
+namespace {
+
+__global__ void k_f32_to_f64(const float *__restrict__ in, double *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+// T_kk = (ka|kb) / (eps_a + eps_b - 2 f_kk)  (Eq. 6); the Gram product (ka|kb) is already in T.
+// A copy goes to `work` (overwritten by the eigensolver).  Non-finite entries raise the error word.
+__global__ void k_tkk_scale(double *__restrict__ T, double *__restrict__ work, const double *__restrict__ eps,
+                            const double *__restrict__ focc, int n_occ, int nv, int *err) {
+    const int k = blockIdx.y;
+    const double fkk = focc[(long long)k * n_occ + k];
+    const long long nn = (long long)nv * nv;
+    double *Tk = T + (long long)k * nn;
+    double *Wk = work + (long long)k * nn;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nn;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int a = int(idx / nv), b = int(idx % nv);
+        const double v = Tk[idx] / (eps[a] + eps[b] - 2.0 * fkk);
+        if (!isfinite(v)) atomicExch(err, kDevNonFinite);
+        Tk[idx] = v;
+        Wk[idx] = v;
+    }
+}
+
+// OSV selection: n_k = #(omega > l_osv) capped (or fixed), at least one; Q_k rows = leading eigenvectors,
+// padded rows zero.  Qe = Q scaled by the virtual energies (rows of Q diag(eps)).
+__global__ void k_osv_select(const double *__restrict__ Zt, const double *__restrict__ omega,
+                             const double *__restrict__ eps, double *__restrict__ Q, double *__restrict__ Qe,
+                             int *__restrict__ nosv, int nv, int nmax, double l_osv, int n_fixed) {
+    const int k = blockIdx.x;
+    __shared__ int s_n;
+    if (threadIdx.x == 0) {
+        const double *w = omega + (long long)k * nv;
+        int n;
+        if (n_fixed > 0) {
+            n = min(n_fixed, nv);
+        } else {
+            n = 0;
+            while (n < nv && w[n] > l_osv) ++n;   // eigenvalues are sorted decreasing
+            n = min(n, nmax);
+        }
+        n = max(n, 1);
+        s_n = n;
+        nosv[k] = n;
+    }
+    __syncthreads();
+    const int n = s_n;
+    const double *Z = Zt + (long long)k * nv * nv;
+    double *Qk = Q + (long long)k * nmax * nv;
+    double *Qek = Qe + (long long)k * nmax * nv;
+    for (long long idx = threadIdx.x; idx < (long long)nmax * nv; idx += blockDim.x) {
+        const int mu = int(idx / nv), a = int(idx % nv);
+        const double q = mu < n ? Z[idx] : 0.0;
+        Qk[idx] = q;
+        Qek[idx] = q * eps[a];
+    }
+}
+
+__global__ void k_block_copy(const BlockCopy *__restrict__ bc) {
+    const BlockCopy b = bc[blockIdx.x];
+    const long long nel = (long long)b.rows * b.cols;
+    for (long long idx = threadIdx.x; idx < nel; idx += blockDim.x) {
+        const int r = int(idx / b.cols), c = int(idx % b.cols);
+        const double v = b.scale * (b.trans ? b.src[(long long)c * b.lds + r] : b.src[(long long)r * b.lds + c]);
+        double *d = b.dst + (long long)r * b.ldd + c;
+        if (b.accumulate) atomicAdd(d, v);
+        else *d = v;
+    }
+}
+
+// Orthonormal basis of the pair domain from S_pp = U diag(s) U^T (U in rows of Ut, s decreasing):
+// X[:, c] = U[:, c] / sqrt(s_c) for s_c > tau_red, zero columns otherwise; r_p = number kept.
+__global__ void k_pair_x(const PairInfo *__restrict__ pairs, const double *__restrict__ Ut,
+                         const double *__restrict__ s, double *__restrict__ X, int *__restrict__ rdim,
+                         double tau_red) {
+    const PairInfo P = pairs[blockIdx.x];
+    const int np = P.np;
+    __shared__ int s_r;
+    if (threadIdx.x == 0) {
+        int r = 0;
+        while (r < np && s[P.e_off + r] > tau_red) ++r;
+        s_r = r;
+        rdim[blockIdx.x] = r;
+    }
+    __syncthreads();
+    const int r = s_r;
+    for (long long idx = threadIdx.x; idx < (long long)np * np; idx += blockDim.x) {
+        const int a = int(idx / np), c = int(idx % np);
+        X[P.off + idx] = c < r ? Ut[P.off + (long long)c * np + a] / sqrt(s[P.e_off + c]) : 0.0;
+    }
+}
+
+// After the r_p x r_p pseudo-canonical eigensolve: zero the eigenvector rows/columns beyond r_p and the
+// unused eigenvalue slots, so that V = X W^T has exactly r_p non-zero columns.
+__global__ void k_clean_w(const PairInfo *__restrict__ pairs, const int *__restrict__ rdim,
+                          double *__restrict__ Wt, double *__restrict__ e) {
+    const PairInfo P = pairs[blockIdx.x];
+    const int np = P.np, r = rdim[blockIdx.x];
+    for (long long idx = threadIdx.x; idx < (long long)np * np; idx += blockDim.x) {
+        const int a = int(idx / np), c = int(idx % np);
+        if (a >= r || c >= r) Wt[P.off + idx] = 0.0;
+    }
+    for (int a = r + threadIdx.x; a < np; a += blockDim.x) e[P.e_off + a] = 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_f32_to_f64(const float *in, double *out, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    k_f32_to_f64<<<blocks, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tkk_scale(double *T, double *work, const double *eps, const double *focc, int n_occ, int nv,
+                             int *err, cudaStream_t s) {
+    if (n_occ <= 0) return cudaSuccess;
+    const long long nn = (long long)nv * nv;
+    const int bx = (int)std::min<long long>((nn + 255) / 256, 64);
+    k_tkk_scale<<<dim3(bx, n_occ), 256, 0, s>>>(T, work, eps, focc, n_occ, nv, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_osv_select(const double *Zt, const double *omega, const double *eps, double *Q, double *Qe,
+                              int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed, cudaStream_t s) {
+    if (n_occ <= 0) return cudaSuccess;
+    k_osv_select<<<n_occ, 256, 0, s>>>(Zt, omega, eps, Q, Qe, nosv, nv, nmax, l_osv, n_fixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_copy(const BlockCopy *d_bc, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_block_copy<<<n, 256, 0, s>>>(d_bc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_x(const PairInfo *pairs, int npairs, const double *Ut, const double *sv, double *X,
+                          int *rdim, double tau_red, cudaStream_t s) {
+    if (npairs <= 0) return cudaSuccess;
+    k_pair_x<<<npairs, 256, 0, s>>>(pairs, Ut, sv, X, rdim, tau_red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clean_w(const PairInfo *pairs, int npairs, const int *rdim, double *Wt, double *e,
+                           cudaStream_t s) {
+    if (npairs <= 0) return cudaSuccess;
+    k_clean_w<<<npairs, 256, 0, s>>>(pairs, rdim, Wt, e);
+    return cudaGetLastError();
+}
+
+}  // namespace osv
