@@ -1,0 +1,353 @@
+"""Benchmark of the MBE(3)-OSV-MP2 hot path on GB300: one step = one geometry's energy AND gradient
+(osv_build -> cluster_residual_solve -> mbe3_combine -> energy -> gradient_backward) on the 64-LMO chain
+workload (n_vir 400, n_aux 1600, l_osv 1e-4 capped at 40 OSVs, 8/6 A pair/triple cutoffs).
+
+Metric: cluster pair-residual TFLOP/s = algorithmic residual FLOPs of the step (coupling products of Eq. 4,
+2 (r_p r_q^2 + r_p^2 r_q) per term and residual evaluation) / step wall time.  Also reported: gradient
+seconds per geometry (= ms_per_step / 1000), residual-solve-only TFLOP/s, and the roofline of the dominant
+kernel from per-stage CUDA events taken over the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--precision fp64|mixed]
+Multi-GPU (torchrun, one rank per GPU): each rank solves its own geometry (different seed); no collective on
+the data path; value = all ranks' residual FLOPs / max-over-ranks time ("scaling": "weak").
+--impl reference times the CPU oracle (the reference implementation of this path) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cluster pair-residual TFLOP/s, gradient s/geometry: mixed vs FP64 GPU @1e-6 Eh"
+WORKLOAD = 1
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM (1.25 TFLOP/s nominal)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+def workload_config(prm, p):
+    return {"workload": f"MBE(3) energy+gradient, {p.n_occ} LMOs on a 1.5 A chain, n_vir={p.n_vir}, "
+                        f"n_aux={p.n_aux}, l_osv=1e-4 capped at {prm.n_osv_max} OSVs, pair/triple cutoffs "
+                        f"{prm.r2b}/{prm.r3b} A",
+            "n_occ": p.n_occ, "n_vir": p.n_vir, "n_aux": p.n_aux, "mbe_order": prm.mbe_order,
+            "precision": "fp64" if prm.precision == 0 else "mixed_tf32x3",
+            "l2": f"inputs larger than L2 (B = {p.B.nbytes / 1e6:.0f} MB > 129 MB)"}
+
+
+# ------------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# --------------------------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_2106_06149_gb300 import build, osvmbe
+    from paper_2106_06149_gb300.synth import workload, make_problem, WORKLOADS
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    osvmbe.load()
+    p, prm = workload(WORKLOAD)
+    if rank > 0:   # each rank: an independent geometry of the same workload (own seed)
+        _, pk, _ = WORKLOADS[WORKLOAD]
+        p = make_problem(**{**pk, "seed": pk["seed"] + 1000 * rank})
+    if args.precision == "mixed":
+        prm.precision = 1
+    stream = torch.cuda.current_stream()
+    dp = osvmbe.DeviceProblem.from_host(p)
+    ctx = osvmbe.Context(stream)
+    ctx.clusters_build(dp, prm)
+    dB = torch.zeros_like(dp.B)
+    dF = torch.zeros_like(dp.f_occ)
+
+    def step():
+        osvmbe.run_energy(ctx, dp, prm)
+        ctx.gradient_backward(1.0, dB, dF)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    flops_step = ctx.residual_flops()
+    E, E_lin = ctx.energy()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs)
+    ctx.profile(True)
+    l0 = ctypes_launches(osvmbe)
+    with ClockSampler(local) as clk:
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        barrier()
+    launches = ctypes_launches(osvmbe) - l0
+    ms = t0.elapsed_time(t1) / args.steps
+    stages = ctx.profile_read()
+    ctx.profile(False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        f = torch.tensor([flops_step], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(f)
+        flops_all = float(f.item())
+    else:
+        flops_all = flops_step
+    value = flops_all / (ms * 1e-3) / 1e12
+
+    # ---- end to end through the C ABI with host buffers: h2d of B, F, eps; d2h of E, dB, dF
+    hB = torch.from_numpy(np.ascontiguousarray(p.B)).pin_memory()
+    hF = torch.from_numpy(np.ascontiguousarray(p.f_occ)).pin_memory()
+    he = torch.from_numpy(np.ascontiguousarray(p.eps_vir)).pin_memory()
+    odB = torch.empty(dB.shape, dtype=dB.dtype).pin_memory()
+    odF = torch.empty(dF.shape, dtype=dF.dtype).pin_memory()
+
+    def e2e_step():
+        dp.B.copy_(hB, non_blocking=True)
+        dp.f_occ.copy_(hF, non_blocking=True)
+        dp.eps_vir.copy_(he, non_blocking=True)
+        dB.zero_()
+        dF.zero_()
+        osvmbe.run_energy(ctx, dp, prm)        # energy() reads E back to the host
+        ctx.gradient_backward(1.0, dB, dF)
+        odB.copy_(dB, non_blocking=True)
+        odF.copy_(dF, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - te0) * 1e3 / args.steps
+    h2d = hB.numel() * hB.element_size() + hF.numel() * 8 + he.numel() * 8
+    d2h = 8 + odB.numel() * odB.element_size() + odF.numel() * 8
+
+    # ---- roofline of the dominant stage
+    total_stage = sum(v[0] for v in stages.values())
+    dom = max(stages.items(), key=lambda kv: kv[1][0])
+    roof = roofline(dom, stages, flops_step, p, prm)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prm.precision == 0 else "tf32x3+f64", "data": "synthetic",
+        "config": workload_config(prm, p),
+        "gradient_s_per_geometry": ms / 1e3,
+        "residual_solve_tflops": flops_step / (stages["residual"][0] / stages["residual"][1] * 1e-3) / 1e12
+        if "residual" in stages else None,
+        "residual_flops_per_step": flops_step,
+        "energy_Eh": E, "energy_linear_Eh": E_lin,
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "stage_share": {k: v[0] / total_stage for k, v in stages.items()},
+        "roofline": roof,
+        "e2e": {"value": flops_all / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(sample_every=16, repeats=1)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def ctypes_launches(osvmbe):
+    import ctypes
+    n = ctypes.c_longlong()
+    osvmbe.load().osv_kernel_launches(ctypes.byref(n))
+    return n.value
+
+
+def stage_flops(name, p, prm, flops_step):
+    """Algorithmic FLOPs of one launch of a stage (FP64 work of the method, padding excluded)."""
+    nv, na, n, nm = p.n_vir, p.n_aux, p.n_occ, prm.n_osv_max if prm.n_osv_fixed <= 0 else prm.n_osv_fixed
+    d = np.linalg.norm(p.centres[:, None, :] - p.centres[None, :, :], axis=-1)
+    nb = (d <= prm.r2b).sum(axis=1)            # |{i} U N(i)| of the half transforms
+    a = np.diff(p.aux_ptr)
+    if name == "residual":
+        return flops_step
+    if name == "tkk_gram":
+        return float(np.sum(2.0 * nv * nv * a))
+    if name == "half_transform":
+        return float(np.sum(2.0 * nb * nm * nv * a))
+    if name == "osv_eigh":
+        return n * (4.0 / 3.0 + 2.0 + 6.0) * nv ** 3     # Householder + explicit Q + QL rotations (model)
+    return None
+
+
+def roofline(dom, stages, flops_step, p, prm):
+    """FP64 ALU roofline of the dominant stage (CUDA-core FP64; peak from unit counts and clock)."""
+    name, (ms_total, calls) = dom
+    avg_ms = ms_total / calls
+    flops = stage_flops(name, p, prm, flops_step)
+    if not flops:
+        return {"bound": "alu", "stage": name, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": None}
+    ach = flops / (avg_ms * 1e-3) / 1e12
+    return {"bound": "alu", "stage": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "avg_launch_ms": avg_ms,
+            "algorithmic_flops_per_launch": flops,
+            "peak_note": "FP64 CUDA cores, 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+
+
+# ------------------------------------------------------------------------------------- CPU baseline
+def oracle_sample(sample_every):
+    """Oracle energy + gradient of every `sample_every`-th cluster of the bench workload (OSVs for all LMOs)."""
+    import torch
+
+    import oracle
+    from paper_2106_06149_gb300.synth import workload
+
+    p, prm = workload(WORKLOAD)
+    cl = oracle.select_clusters(p.centres, prm.r2b, prm.r3b, prm.mbe_order)
+    sample = cl[::sample_every]
+    t0 = time.perf_counter()
+    g = oracle.gradient(p, prm, clusters=sample)
+    dt = time.perf_counter() - t0
+    # residual model FLOPs of the sample, same formula as the library (stored pairs, r = kept dims)
+    flops = 0.0
+    for c in sample:
+        r = {}
+        for a in c:
+            for b in c:
+                if a <= b:
+                    r[(a, b)] = g["n_osv"][a] + (g["n_osv"][b] if a != b else 0)
+        per = 0.0
+        for (i, j), rp in r.items():
+            for k in c:
+                if k != j:
+                    rq = r[(min(i, k), max(i, k))]
+                    per += 2.0 * (rp * rq * rq + rp * rp * rq)
+                if k != i:
+                    rq = r[(min(k, j), max(k, j))]
+                    per += 2.0 * (rp * rq * rq + rp * rp * rq)
+        flops += per * (g["iters"][c] + 1)
+    return flops, dt, len(sample), len(cl), torch.get_num_threads()
+
+
+def cpu_baseline(sample_every=16, repeats=1):
+    flops, dt, ns, nc, cores = oracle_sample(sample_every)
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "seconds": dt,
+            "sample": f"oracle energy+gradient of every {sample_every}th cluster ({ns} of {nc}) of the bench "
+                      f"workload, OSVs of all LMOs, FP64, torch CPU with {cores} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    torch.set_num_threads(len(os.sched_getaffinity(0)))
+    for _ in range(args.warmup):
+        oracle_sample(32)
+    tot_f, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        f, dt, ns, nc, cores = oracle_sample(32)
+        tot_f += f
+        tot_t += dt
+    value = tot_f / tot_t / 1e12
+    from paper_2106_06149_gb300.synth import workload
+    p, prm = workload(WORKLOAD)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(prm, p),
+           "cpu_baseline": {"value": value, "unit": "TFLOP/s", "kind": "oracle", "cores": cores,
+                            "sample": f"oracle energy+gradient of every 32nd cluster ({ns} of {nc}) per step"},
+           "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -133,6 +133,23 @@ osv_status osv_cluster_count(osv_ctx *ctx, int *n_clusters);
 osv_status osv_cluster_info(osv_ctx *ctx, int32_t *members, int32_t *weight, double *energy, int32_t *iters);
 osv_status osv_eigenvalues(osv_ctx *ctx, int k, double *w_out);
 
+/* Per-stage timing: osv_profile_enable(ctx, 1) clears previous records and makes every later call record a
+ * pair of CUDA events around each of its stages on the context's stream; (ctx, 0) stops and clears.
+ * osv_profile_read (synchronises) returns the stages in first-seen order: names[32*q] (NUL-terminated, up to
+ * 31 chars), summed milliseconds ms[q] and number of records calls[q] for q < min(max_stages, *n_stages);
+ * names, ms, calls may be NULL.  Profiling adds event records; leave it off when capturing a CUDA graph. */
+osv_status osv_profile_enable(osv_ctx *ctx, int on);
+osv_status osv_profile_read(osv_ctx *ctx, int max_stages, char *names, double *ms, int *calls, int *n_stages);
+
+/* Algorithmic FLOPs of the last cluster_residual_solve (synchronises): for every cluster, the number of
+ * residual evaluations (iterations + 1) times the sum over its coupling terms of Eq. 4 of
+ * 2 (r_p r_q^2 + r_p^2 r_q), r the pseudo-canonical pair dimensions; the O(r^2) diagonal terms are not
+ * counted.  HOST *flops. */
+osv_status osv_residual_flops(osv_ctx *ctx, double *flops);
+
+/* Process-wide number of CUDA kernel launches issued by this library so far (HOST *count). */
+osv_status osv_kernel_launches(long long *count);
+
 /* Batched symmetric eigensolver used for Eq. 6 (utility entry point): for b = 0..batch-1, the n x n
  * symmetric matrix A + b*n*n (DEVICE, read only) gets eigenvalues w + b*n (DEVICE, decreasing) and
  * eigenvectors as rows of Zt + b*n*n (DEVICE; row mu is the eigenvector of w[mu]).  Householder

@@ -495,18 +495,29 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
     a.scratch = scratch;
     a.sstride = 5 * pstride;
     a.pstride = pstride;
-    if (grid > 0) k_cluster_adjoint<<<grid, kThreads, 0, s>>>(a);
-    CK(cudaGetLastError());
-    if (!c.pairs.empty()) k_gk_tilde<<<(unsigned)c.pairs.size(), kThreads, 0, s>>>(c.pinfo.d, c.Tc, GK);
-    CK(cudaGetLastError());
-    for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2}) CK(gemm_batch_run(*g, s));
-    CK(launch_block_copy(bc_hs.d, (int)bc_hs.h.size(), s));
-    CK(gemm_batch_run(gb_z, s));
-    CK(gemm_batch_run(gb_db, s));
-    CK(gemm_batch_run(gb_dq, s));
+    {
+        StageTimer t(c, "adj_clusters");
+        if (grid > 0) { count_launch(); k_cluster_adjoint<<<grid, kThreads, 0, s>>>(a); }
+        CK(cudaGetLastError());
+    }
+    {
+        StageTimer t(c, "adj_pair_blocks");
+        if (!c.pairs.empty()) { count_launch(); k_gk_tilde<<<(unsigned)c.pairs.size(), kThreads, 0, s>>>(c.pinfo.d, c.Tc, GK); }
+        CK(cudaGetLastError());
+        for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2}) CK(gemm_batch_run(*g, s));
+        CK(launch_block_copy(bc_hs.d, (int)bc_hs.h.size(), s));
+    }
+    {
+        StageTimer t(c, "adj_half_transform");
+        CK(gemm_batch_run(gb_z, s));
+        CK(gemm_batch_run(gb_db, s));
+        CK(gemm_batch_run(gb_dq, s));
+    }
+    StageTimer trelax(c, "adj_osv_relax");
     CK(gemm_batch_run(gb_c, s));
     {
         const int bx = (int)std::min<long long>(((long long)nv * nm + kThreads - 1) / kThreads, 64);
+        count_launch();
         k_relax_y<<<dim3(bx, n), kThreads, 0, s>>>(Cm, c.omega, c.nosv, Y, nv, nm);
         CK(cudaGetLastError());
     }
@@ -514,6 +525,7 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
     CK(gemm_batch_run(gb_gt, s));
     {
         const int bx = (int)std::min<long long>(((long long)nv * nv + kThreads - 1) / kThreads, 64);
+        count_launch();
         k_relax_sym<<<dim3(bx, n), kThreads, 0, s>>>(c.Zc, c.Tkk, c.eps, c.focc, n, nv, dF64);
         CK(cudaGetLastError());
     }
@@ -521,11 +533,12 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
     const long long nb = c.aux_ptr[n] * (long long)nv;
     if (dB) {
         const int blocks = (int)std::min<long long>((nb + 255) / 256, 152LL * 16);
-        if (c.B_dtype == 0) k_out_b<double><<<blocks, 256, 0, s>>>(dB64, (double *)dB, nb, scale);
-        else k_out_b<float><<<blocks, 256, 0, s>>>(dB64, (float *)dB, nb, scale);
+        if (c.B_dtype == 0) { count_launch(); k_out_b<double><<<blocks, 256, 0, s>>>(dB64, (double *)dB, nb, scale); }
+        else { count_launch(); k_out_b<float><<<blocks, 256, 0, s>>>(dB64, (float *)dB, nb, scale); }
         CK(cudaGetLastError());
     }
     if (dF) {
+        count_launch();
         k_out_b<double><<<1, 256, 0, s>>>(dF64, dF, (long long)n * n, scale);
         CK(cudaGetLastError());
     }

@@ -15,6 +15,10 @@
 
 using namespace osv;
 
+namespace osv {
+std::atomic<long long> g_launches{0};
+}
+
 namespace {
 
 thread_local std::string g_noctx_err;
@@ -148,6 +152,11 @@ osv_status osv_destroy(osv_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     ctx->release();
+    for (auto &e : ctx->pev) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     delete ctx;
     return OSV_OK;
 }
@@ -599,28 +608,52 @@ osv_status run_osv_build(osv_ctx *c) {
 #define CK(x, what) \
     if ((e = (x)) != cudaSuccess) return c->cuda_fail(e, what)
     CK(cudaMemsetAsync(c->derr, 0, sizeof(int), s), "memset");
-    if (c->B_dtype == 1) CK(launch_f32_to_f64((const float *)c->B_in, c->B64own, c->aux_ptr[n] * (long long)nv, s), "f32->f64");
-    CK(gemm_batch_run(c->gb_gram, s), "gram");
-    CK(launch_tkk_scale(c->Tkk, c->Awork, c->eps, c->focc, n, nv, c->derr, s), "tkk");
-    CK(eigh_batched(c->eig_tkk.d, n, nv, 0, c->derr, s), "osv eigh");
-    CK(launch_osv_select(c->Awork, c->omega, c->eps, c->Q, c->Qe, c->nosv, n, nv, nm, c->prm.l_osv,
-                         c->prm.n_osv_fixed, s), "select");
-    CK(gemm_batch_run(c->gb_sf, s), "s/f blocks");
-    CK(gemm_batch_run(c->gb_w, s), "half transform");
-    CK(gemm_batch_run(c->gb_k, s), "K blocks");
-    CK(launch_block_copy(c->bc_pair.d, (int)c->bc_pair.h.size(), s), "pair assemble");
-    CK(eigh_batched(c->eig_s.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair overlap eigh");
-    CK(launch_pair_x(c->pinfo.d, (int)c->pairs.size(), c->Sp, c->sw, c->X, c->rdim, c->prm.tau_red, s), "pair x");
-    CK(gemm_batch_run(c->gb_fx1, s), "fx1");
-    CK(gemm_batch_run(c->gb_fx2, s), "fx2");
-    CK(eigh_batched(c->eig_f.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair fock eigh");
-    CK(launch_clean_w(c->pinfo.d, (int)c->pairs.size(), c->rdim, c->Fx, c->pe, s), "clean");
-    CK(gemm_batch_run(c->gb_v, s), "V");
-    CK(gemm_batch_run(c->gb_kt1, s), "kt1");
-    CK(gemm_batch_run(c->gb_kt2, s), "kt2");
-    CK(launch_block_copy(c->bc_coup.d, (int)c->bc_coup.h.size(), s), "coupling assemble");
-    CK(gemm_batch_run(c->gb_c1, s), "c1");
-    CK(gemm_batch_run(c->gb_c2, s), "c2");
+    if (c->B_dtype == 1) {
+        StageTimer t(*c, "b_to_fp64");
+        CK(launch_f32_to_f64((const float *)c->B_in, c->B64own, c->aux_ptr[n] * (long long)nv, s), "f32->f64");
+    }
+    {
+        StageTimer t(*c, "tkk_gram");
+        CK(gemm_batch_run(c->gb_gram, s), "gram");
+        CK(launch_tkk_scale(c->Tkk, c->Awork, c->eps, c->focc, n, nv, c->derr, s), "tkk");
+    }
+    {
+        StageTimer t(*c, "osv_eigh");
+        CK(eigh_batched(c->eig_tkk.d, n, nv, 0, c->derr, s), "osv eigh");
+        CK(launch_osv_select(c->Awork, c->omega, c->eps, c->Q, c->Qe, c->nosv, n, nv, nm, c->prm.l_osv,
+                             c->prm.n_osv_fixed, s), "select");
+    }
+    {
+        StageTimer t(*c, "sf_blocks");
+        CK(gemm_batch_run(c->gb_sf, s), "s/f blocks");
+    }
+    {
+        StageTimer t(*c, "half_transform");
+        CK(gemm_batch_run(c->gb_w, s), "half transform");
+    }
+    {
+        StageTimer t(*c, "k_blocks");
+        CK(gemm_batch_run(c->gb_k, s), "K blocks");
+    }
+    {
+        StageTimer t(*c, "pair_basis");
+        CK(launch_block_copy(c->bc_pair.d, (int)c->bc_pair.h.size(), s), "pair assemble");
+        CK(eigh_batched(c->eig_s.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair overlap eigh");
+        CK(launch_pair_x(c->pinfo.d, (int)c->pairs.size(), c->Sp, c->sw, c->X, c->rdim, c->prm.tau_red, s), "pair x");
+        CK(gemm_batch_run(c->gb_fx1, s), "fx1");
+        CK(gemm_batch_run(c->gb_fx2, s), "fx2");
+        CK(eigh_batched(c->eig_f.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair fock eigh");
+        CK(launch_clean_w(c->pinfo.d, (int)c->pairs.size(), c->rdim, c->Fx, c->pe, s), "clean");
+        CK(gemm_batch_run(c->gb_v, s), "V");
+    }
+    {
+        StageTimer t(*c, "pair_transform");
+        CK(gemm_batch_run(c->gb_kt1, s), "kt1");
+        CK(gemm_batch_run(c->gb_kt2, s), "kt2");
+        CK(launch_block_copy(c->bc_coup.d, (int)c->bc_coup.h.size(), s), "coupling assemble");
+        CK(gemm_batch_run(c->gb_c1, s), "c1");
+        CK(gemm_batch_run(c->gb_c2, s), "c2");
+    }
 #undef CK
     return OSV_OK;
 }
@@ -710,7 +743,10 @@ osv_status cluster_residual_solve(osv_ctx *c, int *n_iter_out, int32_t *cluster_
         return c->cuda_fail(e, "memset T");
     if ((e = cudaMemsetAsync(c->Rslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
         return c->cuda_fail(e, "memset R");
-    if ((e = launch_residual(a, (int)c->cl.size(), c->stream)) != cudaSuccess) return c->cuda_fail(e, "residual");
+    {
+        StageTimer t(*c, "residual");
+        if ((e = launch_residual(a, (int)c->cl.size(), c->stream)) != cudaSuccess) return c->cuda_fail(e, "residual");
+    }
     if (cluster_status) {
         if ((e = cudaMemcpyAsync(cluster_status, c->iters, c->cl.size() * sizeof(int), cudaMemcpyDeviceToDevice,
                                  c->stream)) != cudaSuccess)
@@ -740,6 +776,7 @@ osv_status mbe3_combine(osv_ctx *c) {
     if (!c) return OSV_ERR_INVALID;
     if (!c->solved) return c->fail(OSV_ERR_INVALID, "cluster_residual_solve must precede mbe3_combine");
     cudaSetDevice(c->device);
+    StageTimer t(*c, "combine");
     cudaError_t e = launch_combine(c->pinfo.d, (int)c->pairs.size(), c->comb_ptr.d, c->comb_src.d, c->comb_w.d,
                                    c->Tslot, c->Tc, c->stream);
     if (e != cudaSuccess) return c->cuda_fail(e, "combine");
@@ -750,8 +787,12 @@ osv_status energy(osv_ctx *c, double *E_out, double *E_linear_out) {
     if (!c || !E_out) return c ? c->fail(OSV_ERR_INVALID, "E_out is NULL") : OSV_ERR_INVALID;
     if (!c->solved) return c->fail(OSV_ERR_INVALID, "cluster_residual_solve must precede energy");
     cudaSetDevice(c->device);
-    cudaError_t e = launch_energy(c->pinfo.d, c->rdim, c->Kt, c->Tc, (int)c->pairs.size(), c->lin, c->Ecl,
+    cudaError_t e;
+    {
+        StageTimer t(*c, "energy");
+        e = launch_energy(c->pinfo.d, c->rdim, c->Kt, c->Tc, (int)c->pairs.size(), c->lin, c->Ecl,
                                   c->cinfo.d, (int)c->cl.size(), c->Eout, c->stream);
+    }
     if (e != cudaSuccess) return c->cuda_fail(e, "energy");
     double h[2];
     if ((e = cudaMemcpyAsync(h, c->Eout, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
@@ -809,6 +850,75 @@ osv_status gradient_backward(osv_ctx *c, double dE_scale, void *dE_dB, double *d
     std::string msg;
     cudaError_t e = c->adj.run(*c, dE_scale, dE_dB, dE_dFocc, msg);
     if (e != cudaSuccess) return c->cuda_fail(e, msg.c_str());
+    return OSV_OK;
+}
+
+osv_status osv_kernel_launches(long long *count) {
+    if (!count) return OSV_ERR_INVALID;
+    *count = g_launches.load();
+    return OSV_OK;
+}
+
+osv_status osv_profile_enable(osv_ctx *c, int on) {
+    if (!c) return OSV_ERR_INVALID;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (auto &e : c->pev) {
+        c->pool.push_back(e.a);
+        c->pool.push_back(e.b);
+    }
+    c->pev.clear();
+    c->prof = on != 0;
+    return OSV_OK;
+}
+
+osv_status osv_profile_read(osv_ctx *c, int max_stages, char *names, double *ms, int *calls, int *n_stages) {
+    if (!c || !n_stages || max_stages < 0) return OSV_ERR_INVALID;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "profile sync");
+    std::vector<std::string> order;
+    std::map<std::string, std::pair<double, int>> acc;
+    for (auto &ev : c->pev) {
+        float t = 0.f;
+        if ((e = cudaEventElapsedTime(&t, ev.a, ev.b)) != cudaSuccess) return c->cuda_fail(e, "event time");
+        if (!acc.count(ev.name)) order.push_back(ev.name);
+        acc[ev.name].first += t;
+        acc[ev.name].second += 1;
+    }
+    *n_stages = (int)order.size();
+    for (int q = 0; q < (int)order.size() && q < max_stages; ++q) {
+        if (names) {
+            strncpy(names + 32 * q, order[q].c_str(), 31);
+            names[32 * q + 31] = 0;
+        }
+        if (ms) ms[q] = acc[order[q]].first;
+        if (calls) calls[q] = acc[order[q]].second;
+    }
+    return OSV_OK;
+}
+
+osv_status osv_residual_flops(osv_ctx *c, double *flops) {
+    if (!c || !flops) return OSV_ERR_INVALID;
+    if (!c->solved) return c->fail(OSV_ERR_INVALID, "no solved clusters");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sync");
+    std::vector<int> r(c->pairs.size()), it(c->cl.size());
+    if ((e = cudaMemcpy(r.data(), c->rdim, r.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(it.data(), c->iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy");
+    double total = 0.0;
+    for (size_t q = 0; q < c->cl.size(); ++q) {
+        const int evals = (it[q] < 0 ? c->prm.max_iter : it[q]) + 1;
+        double per = 0.0;
+        for (int t = c->cinfo.h[q].term0; t < c->cinfo.h[q].term1; ++t) {
+            const double rp = r[c->slots.h[c->terms.h[t].dst].pair], rq = r[c->slots.h[c->terms.h[t].src].pair];
+            per += 2.0 * (rp * rq * rq + rp * rp * rq);
+        }
+        total += per * evals;
+    }
+    *flops = total;
     return OSV_OK;
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -10,6 +11,10 @@
 namespace osv {
 
 constexpr int kWarp = 32;
+
+// Process-wide count of kernel launches issued by this library (osv_kernel_launches).
+extern std::atomic<long long> g_launches;
+inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Error word written by bounded device loops (never a trap).
 enum DevErr : int { kDevOk = 0, kDevEighNoConv = 1, kDevNonFinite = 2 };

@@ -9,6 +9,10 @@
 #include "adjoint.h"
 
 namespace osv {
+struct ProfEvent {
+    const char *name;
+    cudaEvent_t a, b;
+};
 template <class T>
 struct HostDev {
     std::vector<T> h;
@@ -91,6 +95,21 @@ struct osv_ctx {
 
     osv::AdjointPlan adj;
 
+    // per-stage CUDA-event profiling (osv_profile_enable / osv_profile_read)
+    bool prof = false;
+    std::vector<osv::ProfEvent> pev;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t take_event() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+
     osv_status fail(osv_status s, const std::string &m) {
         err = m;
         return s;
@@ -135,3 +154,21 @@ struct osv_ctx {
     long long b_off(int i) const { return aux_ptr[i] * (long long)n_vir; }
 };
 
+
+// Records CUDA events around one stage of the pipeline on the context's stream when profiling is on.
+struct StageTimer {
+    osv_ctx &c;
+    osv::ProfEvent e{};
+    StageTimer(osv_ctx &ctx, const char *name) : c(ctx) {
+        if (!c.prof) return;
+        e.name = name;
+        e.a = c.take_event();
+        e.b = c.take_event();
+        cudaEventRecord(e.a, c.stream);
+    }
+    ~StageTimer() {
+        if (!c.prof || !e.a) return;
+        cudaEventRecord(e.b, c.stream);
+        c.pev.push_back(e);
+    }
+};

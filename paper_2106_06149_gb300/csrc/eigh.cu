@@ -255,10 +255,13 @@ cudaError_t eigh_batched(const EighDesc *d_desc, int batch, int n_max, int rows_
         e = cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh1);
         if (e != cudaSuccess) return e;
     }
+    count_launch();
     k_tridiag<<<batch, kThreads, sh1, s>>>(d_desc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    count_launch();
     k_form_q<<<dim3(batch, split), kThreads, sh2, s>>>(d_desc, chunk);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    count_launch();
     k_ql<<<dim3(batch, split), kThreads, sh3, s>>>(d_desc, chunk, err);
     return cudaGetLastError();
 }

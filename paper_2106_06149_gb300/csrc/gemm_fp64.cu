@@ -134,6 +134,7 @@ cudaError_t gemm_batch_run(const GemmBatch &b, cudaStream_t s) {
     if (b.tiles == 0) return cudaSuccess;
     // problems without tiles are skipped by the search: tile0 is non-decreasing and the search picks the
     // last problem whose first tile is <= t, which is the one owning t.
+    count_launch();
     k_gemm_fp64<<<(unsigned)b.tiles, NT, 0, s>>>(b.d_desc, b.d_tile0, (int)b.h.size());
     return cudaGetLastError();
 }

@@ -116,6 +116,7 @@ __global__ void k_clean_w(const PairInfo *__restrict__ pairs, const int *__restr
 cudaError_t launch_f32_to_f64(const float *in, double *out, long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    count_launch();
     k_f32_to_f64<<<blocks, 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
 }
@@ -125,6 +126,7 @@ cudaError_t launch_tkk_scale(double *T, double *work, const double *eps, const d
     if (n_occ <= 0) return cudaSuccess;
     const long long nn = (long long)nv * nv;
     const int bx = (int)std::min<long long>((nn + 255) / 256, 64);
+    count_launch();
     k_tkk_scale<<<dim3(bx, n_occ), 256, 0, s>>>(T, work, eps, focc, n_occ, nv, err);
     return cudaGetLastError();
 }
@@ -132,12 +134,14 @@ cudaError_t launch_tkk_scale(double *T, double *work, const double *eps, const d
 cudaError_t launch_osv_select(const double *Zt, const double *omega, const double *eps, double *Q, double *Qe,
                               int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed, cudaStream_t s) {
     if (n_occ <= 0) return cudaSuccess;
+    count_launch();
     k_osv_select<<<n_occ, 256, 0, s>>>(Zt, omega, eps, Q, Qe, nosv, nv, nmax, l_osv, n_fixed);
     return cudaGetLastError();
 }
 
 cudaError_t launch_block_copy(const BlockCopy *d_bc, int n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    count_launch();
     k_block_copy<<<n, 256, 0, s>>>(d_bc);
     return cudaGetLastError();
 }
@@ -145,6 +149,7 @@ cudaError_t launch_block_copy(const BlockCopy *d_bc, int n, cudaStream_t s) {
 cudaError_t launch_pair_x(const PairInfo *pairs, int npairs, const double *Ut, const double *sv, double *X,
                           int *rdim, double tau_red, cudaStream_t s) {
     if (npairs <= 0) return cudaSuccess;
+    count_launch();
     k_pair_x<<<npairs, 256, 0, s>>>(pairs, Ut, sv, X, rdim, tau_red);
     return cudaGetLastError();
 }
@@ -152,6 +157,7 @@ cudaError_t launch_pair_x(const PairInfo *pairs, int npairs, const double *Ut, c
 cudaError_t launch_clean_w(const PairInfo *pairs, int npairs, const int *rdim, double *Wt, double *e,
                            cudaStream_t s) {
     if (npairs <= 0) return cudaSuccess;
+    count_launch();
     k_clean_w<<<npairs, 256, 0, s>>>(pairs, rdim, Wt, e);
     return cudaGetLastError();
 }

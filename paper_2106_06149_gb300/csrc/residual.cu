@@ -209,6 +209,7 @@ __global__ void k_energy_final(const double *__restrict__ Ec, const ClusterInfo 
 
 cudaError_t launch_residual(const SolveArgs &a, int nclusters, cudaStream_t s) {
     if (nclusters <= 0) return cudaSuccess;
+    count_launch();
     k_residual<<<nclusters, kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -216,6 +217,7 @@ cudaError_t launch_residual(const SolveArgs &a, int nclusters, cudaStream_t s) {
 cudaError_t launch_combine(const PairInfo *pairs, int npairs, const int *ptr, const long long *src, const int *w,
                            const double *T, double *Tc, cudaStream_t s) {
     if (npairs <= 0) return cudaSuccess;
+    count_launch();
     k_combine<<<npairs, kThreads, 0, s>>>(pairs, ptr, src, w, T, Tc);
     return cudaGetLastError();
 }
@@ -223,7 +225,8 @@ cudaError_t launch_combine(const PairInfo *pairs, int npairs, const int *ptr, co
 cudaError_t launch_energy(const PairInfo *pairs, const int *rdim, const double *Kt, const double *Tc, int npairs,
                           double *lin, const double *Ec, const ClusterInfo *cl, int ncl, double *out,
                           cudaStream_t s) {
-    if (npairs > 0) k_pair_linear<<<npairs, kThreads, 0, s>>>(pairs, rdim, Kt, Tc, lin);
+    if (npairs > 0) { count_launch(); k_pair_linear<<<npairs, kThreads, 0, s>>>(pairs, rdim, Kt, Tc, lin); }
+    count_launch();
     k_energy_final<<<1, kThreads, 0, s>>>(Ec, cl, ncl, lin, npairs, out);
     return cudaGetLastError();
 }

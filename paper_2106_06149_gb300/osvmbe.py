@@ -20,7 +20,8 @@ OSV_FP64, OSV_MIXED_TF32X3 = 0, 1
 
 EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv_build", "cluster_residual_solve",
            "mbe3_combine", "energy", "gradient_backward", "osv_cluster_count", "osv_cluster_info",
-           "osv_eigenvalues", "osv_syev_batched"]
+           "osv_eigenvalues", "osv_syev_batched", "osv_profile_enable", "osv_profile_read",
+           "osv_residual_flops", "osv_kernel_launches"]
 
 
 class OsvParams(ctypes.Structure):
@@ -63,6 +64,10 @@ def load(path=LIB_PATH):
         "osv_cluster_info": ([V, V, V, V, V], I),
         "osv_eigenvalues": ([V, I, V], I),
         "osv_syev_batched": ([V, I, I, V, V, V], I),
+        "osv_profile_enable": ([V, I], I),
+        "osv_profile_read": ([V, I, V, V, V, P(I)], I),
+        "osv_residual_flops": ([V, P(D)], I),
+        "osv_kernel_launches": ([P(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +223,26 @@ class Context:
         it = np.zeros(n.value, np.int32)
         _check(load().osv_cluster_info(self.h, _ptr(mem), _ptr(w), _ptr(e), _ptr(it)), self.h)
         return mem, w, e, it
+
+    def profile(self, on=True):
+        _check(load().osv_profile_enable(self.h, 1 if on else 0), self.h)
+
+    def profile_read(self):
+        """{stage: (total_ms, records)} of the stages recorded since profiling was enabled."""
+        n = ctypes.c_int()
+        _check(load().osv_profile_read(self.h, 0, None, None, None, ctypes.byref(n)), self.h)
+        names = ctypes.create_string_buffer(32 * max(n.value, 1))
+        ms = np.zeros(max(n.value, 1), np.float64)
+        calls = np.zeros(max(n.value, 1), np.int32)
+        _check(load().osv_profile_read(self.h, n.value, names, _ptr(ms), _ptr(calls), ctypes.byref(n)), self.h)
+        raw = names.raw
+        return {raw[32 * q:32 * q + 32].split(b"\0")[0].decode(): (float(ms[q]), int(calls[q]))
+                for q in range(n.value)}
+
+    def residual_flops(self):
+        f = ctypes.c_double()
+        _check(load().osv_residual_flops(self.h, ctypes.byref(f)), self.h)
+        return f.value
 
     def eigenvalues(self, k, n_vir):
         out = np.zeros(n_vir, np.float64)
