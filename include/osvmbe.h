@@ -157,6 +157,23 @@ osv_status osv_kernel_launches(long long *count);
  * call and frees it before returning; synchronises the stream.  1 <= n <= 4096. */
 osv_status osv_syev_batched(const double *A, int n, int batch, double *w, double *Zt, void *cuda_stream);
 
+/* Allocation-free variant of osv_syev_batched (the paper has no counterpart: this is a service for callers).
+ * For callers that cannot call cudaMalloc: code running under an external memory manager that owns the whole
+ * device memory, where a stray cudaMalloc fails or fragments its pool, and latency-sensitive callers that
+ * cannot take the device-wide synchronisation of cudaFree.  Same arguments, results and error codes as
+ * osv_syev_batched, except:
+ *   - no cudaMalloc / cudaFree: scratch is a static device array of 2^20 doubles (8 MiB) plus 1024 matrix
+ *     descriptors, held by every GPU that loads the library until the process exits;
+ *   - limits: batch <= 1024 and batch*n*n + 3*batch*n <= 1048576; larger requests return OSV_ERR_INVALID with
+ *     the numbers in osv_last_error(NULL);
+ *   - Zt doubles as the working matrix (A may equal Zt for an in-place call);
+ *   - the first call on each device looks up the static array's device address (cudaGetSymbolAddress with that
+ *     device current); make that first call before any stream capture;
+ *   - every call shares the one static array (the error word is cleared on each call): calls that overlap on
+ *     the GPU, from several host threads or streams, race and must be serialised by the caller.
+ * Synchronises the stream. */
+osv_status osv_syev_batched_noalloc(const double *A, int n, int batch, double *w, double *Zt, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

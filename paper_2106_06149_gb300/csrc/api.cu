@@ -15,13 +15,16 @@
 
 using namespace osv;
 
+namespace {
+thread_local std::string g_noctx_err;
+}
+
 namespace osv {
 std::atomic<long long> g_launches{0};
+void set_noctx_error(const std::string &msg) { g_noctx_err = msg; }
 }
 
 namespace {
-
-thread_local std::string g_noctx_err;
 
 osv_status check_params(osv_ctx *c, const osv_params *p) {
     if (!p) return c->fail(OSV_ERR_INVALID, "params is NULL");

@@ -21,7 +21,7 @@ OSV_FP64, OSV_MIXED_TF32X3 = 0, 1
 EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv_build", "cluster_residual_solve",
            "mbe3_combine", "energy", "gradient_backward", "osv_cluster_count", "osv_cluster_info",
            "osv_eigenvalues", "osv_syev_batched", "osv_profile_enable", "osv_profile_read",
-           "osv_residual_flops", "osv_kernel_launches"]
+           "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc"]
 
 
 class OsvParams(ctypes.Structure):
@@ -68,6 +68,7 @@ def load(path=LIB_PATH):
         "osv_profile_read": ([V, I, V, V, V, P(I)], I),
         "osv_residual_flops": ([V, P(D)], I),
         "osv_kernel_launches": ([P(ctypes.c_longlong)], I),
+        "osv_syev_batched_noalloc": ([V, I, I, V, V, V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
