@@ -13,7 +13,8 @@
 // as in Eqs. 33-34).  They are mapped back with V, split into LMO-pair blocks s_ab = Q_a^T Q_b,
 // phi_ab = Q_a^T eps Q_b and K sub-blocks W^(i)_a W^(j)T_b, chained to W (recomputed in the forward and kept),
 // Q and B, and the OSV gradient is relaxed through the discarded eigenvectors of T_kk (Eq. 8):
-//   C = Q'^T dE/dQ,  Y = C / (omega_mu - omega'_nu),  G_T = sym(Q' Y Q^T),
+//   x_mu = sum_nu q'_nu q'_nu^T g_mu / (omega_mu - omega'_nu) (restricted resolvent, no discarded vectors formed),
+//   G_T = sym(sum_mu x_mu q_mu^T),
 //   dE/dB_k += 2 (G_T / Delta) B_k,  dE/df_kk += 2 sum_ab G_T,ab T_ab / Delta_ab.
 #include "ctx.h"
 #include "launch.h"
@@ -184,21 +185,6 @@ __global__ void k_gk_tilde(const PairInfo *__restrict__ pairs, const double *__r
     }
 }
 
-// Y = C / (omega_mu - omega_nu) on the discarded x kept block, zero elsewhere (Eq. 8, kept-discarded only).
-__global__ void k_relax_y(const double *__restrict__ Cm, const double *__restrict__ omega,
-                          const int *__restrict__ nosv, double *__restrict__ Y, int nv, int nm) {
-    const int k = blockIdx.y;
-    const int nk = nosv[k];
-    const double *w = omega + (long long)k * nv;
-    const double *Ck = Cm + (long long)k * nv * nm;
-    double *Yk = Y + (long long)k * nv * nm;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)nv * nm;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int nu = int(idx / nm), mu = int(idx % nm);
-        Yk[idx] = (nu >= nk && mu < nk) ? Ck[idx] / (w[mu] - w[nu]) : 0.0;
-    }
-}
-
 // G = sym(G_T) / Delta in place, and df_kk += 2 sum_ab sym(G_T)_ab T_ab / Delta_ab.
 __global__ void k_relax_sym(double *__restrict__ GT, const double *__restrict__ Tkk, const double *__restrict__ eps,
                             const double *__restrict__ focc, int n_occ, int nv, double *__restrict__ dF) {
@@ -234,8 +220,8 @@ __global__ void k_out_b(const double *__restrict__ src, T *__restrict__ dst, lon
 void AdjointPlan::release() {
     for (void *p : allocs) cudaFree(p);
     allocs.clear();
-    for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2, &gb_z, &gb_db, &gb_dq, &gb_c,
-                         &gb_a1, &gb_gt, &gb_rb}) {
+    for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2, &gb_z, &gb_db, &gb_dq,
+                         &gb_gt, &gb_rb}) {
         gemm_batch_free(*g);
         g->h.clear();
     }
@@ -279,8 +265,6 @@ cudaError_t AdjointPlan::plan(osv_ctx &c) {
     AL(dQ, (long long)n * nm * nv);
     AL(dB64, c.aux_ptr[n] * (long long)nv);
     AL(dF64, (long long)n * n);
-    AL(Cm, (long long)n * nv * nm);
-    AL(Y, (long long)n * nv * nm);
     AL(A1, (long long)n * nv * nm);
     grid = (int)std::min<size_t>(c.cl.size(), 152 * 4);
     pstride = 4LL * nm * nm;
@@ -442,17 +426,15 @@ cudaError_t AdjointPlan::plan(osv_ctx &c) {
             gb_dq.add(x);
         }
     }
-    // relaxation
+    // relaxation: G_T = X^T Q with X the kept x discarded resolvent applied to dE/dQ (rows), then dB += 2 (G_T/Delta) B
     const long long nv2 = (long long)nv * nv;
     for (int k = 0; k < n; ++k) {
-        gb_c.add(gemm(nv, nm, nv, c.Awork + k * nv2, nv, 0, dQ + (long long)k * nm * nv, nv, 1, Cm + (long long)k * nv * nm, nm));
-        gb_a1.add(gemm(nv, nm, nv, c.Awork + k * nv2, nv, 1, Y + (long long)k * nv * nm, nm, 0, A1 + (long long)k * nv * nm, nm));
-        gb_gt.add(gemm(nv, nv, nm, A1 + (long long)k * nv * nm, nm, 0, c.Q + (long long)k * nm * nv, nv, 0, c.Zc + k * nv2, nv));
+        gb_gt.add(gemm(nv, nv, nm, A1 + (long long)k * nm * nv, nv, 1, c.Q + (long long)k * nm * nv, nv, 0, c.Zc + k * nv2, nv));
         gb_rb.add(gemm(nv, (int)c.a_of(k), nv, c.Zc + k * nv2, nv, 0, c.B64 + c.b_off(k), c.a_of(k), 0,
                        dB64 + c.b_off(k), c.a_of(k), 2.0, 1.0));
     }
     for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2, &gb_z, &gb_db, &gb_dq,
-                         &gb_c, &gb_a1, &gb_gt, &gb_rb})
+                         &gb_gt, &gb_rb})
         if ((e = gemm_batch_upload(*g)) != cudaSuccess) return e;
     planned = true;
     return cudaSuccess;
@@ -514,14 +496,12 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
         CK(gemm_batch_run(gb_dq, s));
     }
     StageTimer trelax(c, "adj_osv_relax");
-    CK(gemm_batch_run(gb_c, s));
-    {
-        const int bx = (int)std::min<long long>(((long long)nv * nm + kThreads - 1) / kThreads, 64);
-        count_launch();
-        k_relax_y<<<dim3(bx, n), kThreads, 0, s>>>(Cm, c.omega, c.nosv, Y, nv, nm);
-        CK(cudaGetLastError());
-    }
-    CK(gemm_batch_run(gb_a1, s));
+    // P_perp dE/dQ -> tridiagonal basis -> (Tri - omega_mu)^{-1} -> P_perp -> back to the virtual basis
+    CK(osv_project_out(c.nosv, c.Q, dQ, n, nv, nm, s));
+    CK(osv_reflect(c.tri_osv.d, n, nv, nm, c.nosv, dQ, 1, s));
+    CK(osv_tri_shift_solve(c.tri_osv.d, n, nv, nm, c.nosv, dQ, A1, c.tri_work, s));
+    CK(osv_project_out(c.nosv, c.Ytri, A1, n, nv, nm, s));
+    CK(osv_reflect(c.tri_osv.d, n, nv, nm, c.nosv, A1, 0, s));
     CK(gemm_batch_run(gb_gt, s));
     {
         const int bx = (int)std::min<long long>(((long long)nv * nv + kThreads - 1) / kThreads, 64);

@@ -16,7 +16,7 @@ struct AdjointPlan {
     double *GS = nullptr, *GF = nullptr, *GK = nullptr, *GSo = nullptr, *GFo = nullptr, *GKo = nullptr,
            *ptmp = nullptr, *GSc = nullptr, *GSco = nullptr, *ctmp = nullptr, *HS = nullptr, *HF = nullptr;
     // chain to W, Q, B and the OSV relaxation
-    double *Z = nullptr, *dQ = nullptr, *dB64 = nullptr, *dF64 = nullptr, *Cm = nullptr, *Y = nullptr, *A1 = nullptr;
+    double *Z = nullptr, *dQ = nullptr, *dB64 = nullptr, *dF64 = nullptr, *A1 = nullptr;
     double *scratch = nullptr;
     long long pstride = 0;
     int grid = 0;
@@ -24,7 +24,7 @@ struct AdjointPlan {
         std::vector<BlockCopy> h;
         BlockCopy *d = nullptr;
     } bc_hs;
-    GemmBatch gb_kc1, gb_kc2, gb_f1, gb_f2, gb_k1, gb_k2, gb_c1, gb_c2, gb_z, gb_db, gb_dq, gb_c, gb_a1, gb_gt, gb_rb;
+    GemmBatch gb_kc1, gb_kc2, gb_f1, gb_f2, gb_k1, gb_k2, gb_c1, gb_c2, gb_z, gb_db, gb_dq, gb_gt, gb_rb;
 
     void release();
     cudaError_t plan(osv_ctx &c);

@@ -427,21 +427,20 @@ osv_status build_plan(osv_ctx *c) {
         c->gb_gram.add(gemm(nv, nv, (int)a, c->B64 + c->b_off(k), a, 0, c->B64 + c->b_off(k), a, 1,
                             c->Tkk + k * nv2, nv));
     }
-    // --- a2: OSV eigensolves
-    c->eig_tkk.h.clear();
+    // --- a2: OSV eigenproblems (tridiagonal route: bisection + inverse iteration of the kept vectors)
+    ALLOC(c->Ytri, (long long)n * nm * nv);
+    ALLOC(c->tri_work, 4LL * n * nm * nv);
+    c->tri_osv.h.clear();
     for (int k = 0; k < n; ++k) {
-        EighDesc D{};
+        TriDesc D{};
         D.A = c->Awork + k * nv2;
         D.lda = nv;
         D.n = nv;
-        D.w = c->omega + (long long)k * nv;
-        D.Zt = c->Awork + k * nv2;
-        D.ldz = nv;
-        D.zwork = c->Zc + k * nv2;
         D.d = c->dsc + (long long)k * nv;
         D.e = c->esc + (long long)k * nv;
         D.tau = c->tausc + (long long)k * nv;
-        c->eig_tkk.h.push_back(D);
+        D.w = c->omega + (long long)k * nv;
+        c->tri_osv.h.push_back(D);
     }
     // --- a3: LMO-pair blocks s_ij = Q_i Q_j^T, phi_ij = Q_i diag(eps) Q_j^T (rows = OSVs)
     for (size_t p = 0; p < c->pairs.size(); ++p) {
@@ -595,7 +594,7 @@ osv_status build_plan(osv_ctx *c) {
     if ((e = c->upload(c->comb_w)) != cudaSuccess) return c->cuda_fail(e, "upload comb");
     if ((e = c->upload(c->bc_pair)) != cudaSuccess) return c->cuda_fail(e, "upload bc");
     if ((e = c->upload(c->bc_coup)) != cudaSuccess) return c->cuda_fail(e, "upload bc");
-    if ((e = c->upload(c->eig_tkk)) != cudaSuccess) return c->cuda_fail(e, "upload eig");
+    if ((e = c->upload(c->tri_osv)) != cudaSuccess) return c->cuda_fail(e, "upload tri");
     if ((e = c->upload(c->eig_s)) != cudaSuccess) return c->cuda_fail(e, "upload eig");
     if ((e = c->upload(c->eig_f)) != cudaSuccess) return c->cuda_fail(e, "upload eig");
     for (GemmBatch *g : {&c->gb_gram, &c->gb_sf, &c->gb_w, &c->gb_k, &c->gb_fx1, &c->gb_fx2, &c->gb_v, &c->gb_kt1,
@@ -622,9 +621,14 @@ osv_status run_osv_build(osv_ctx *c) {
     }
     {
         StageTimer t(*c, "osv_eigh");
-        CK(eigh_batched(c->eig_tkk.d, n, nv, 0, c->derr, s), "osv eigh");
-        CK(launch_osv_select(c->Awork, c->omega, c->eps, c->Q, c->Qe, c->nosv, n, nv, nm, c->prm.l_osv,
-                             c->prm.n_osv_fixed, s), "select");
+        CK(osv_tridiag(c->tri_osv.d, n, nv, s), "osv tridiag");
+        CK(osv_tri_eigvals(c->tri_osv.d, n, nv, s), "osv eigenvalues");
+        CK(launch_osv_count(c->omega, c->nosv, n, nv, nm, c->prm.l_osv, c->prm.n_osv_fixed, s), "osv count");
+        CK(cudaMemsetAsync(c->Ytri, 0, (size_t)n * nm * nv * sizeof(double), s), "memset Y");
+        CK(osv_tri_kept_vectors(c->tri_osv.d, n, nv, nm, c->nosv, c->Ytri, c->tri_work, s), "osv vectors");
+        CK(cudaMemcpyAsync(c->Q, c->Ytri, (size_t)n * nm * nv * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy Q");
+        CK(osv_reflect(c->tri_osv.d, n, nv, nm, c->nosv, c->Q, 0, s), "osv back-transform");
+        CK(launch_scale_cols(c->Q, c->eps, c->Qe, (long long)n * nm, nv, s), "Qe");
     }
     {
         StageTimer t(*c, "sf_blocks");
@@ -641,11 +645,19 @@ osv_status run_osv_build(osv_ctx *c) {
     {
         StageTimer t(*c, "pair_basis");
         CK(launch_block_copy(c->bc_pair.d, (int)c->bc_pair.h.size(), s), "pair assemble");
-        CK(eigh_batched(c->eig_s.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair overlap eigh");
+        if (2 * nm <= kJacobiMax) {
+            CK(eigh_small_jacobi(c->eig_s.d, (int)c->pairs.size(), 2 * nm, c->derr, s), "pair overlap eigh");
+        } else {
+            CK(eigh_batched(c->eig_s.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair overlap eigh");
+        }
         CK(launch_pair_x(c->pinfo.d, (int)c->pairs.size(), c->Sp, c->sw, c->X, c->rdim, c->prm.tau_red, s), "pair x");
         CK(gemm_batch_run(c->gb_fx1, s), "fx1");
         CK(gemm_batch_run(c->gb_fx2, s), "fx2");
-        CK(eigh_batched(c->eig_f.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair fock eigh");
+        if (2 * nm <= kJacobiMax) {
+            CK(eigh_small_jacobi(c->eig_f.d, (int)c->pairs.size(), 2 * nm, c->derr, s), "pair fock eigh");
+        } else {
+            CK(eigh_batched(c->eig_f.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair fock eigh");
+        }
         CK(launch_clean_w(c->pinfo.d, (int)c->pairs.size(), c->rdim, c->Fx, c->pe, s), "clean");
         CK(gemm_batch_run(c->gb_v, s), "V");
     }

@@ -7,6 +7,7 @@
 
 #include "../../include/osvmbe.h"
 #include "adjoint.h"
+#include "osv_eig.h"
 
 namespace osv {
 struct ProfEvent {
@@ -88,7 +89,9 @@ struct osv_ctx {
     HostDev<long long> comb_src;
     std::vector<long long> coup_off;       // per coupling offset (doubles) of its n_pa x n_pb blocks
     HostDev<BlockCopy> bc_pair, bc_coup;
-    HostDev<EighDesc> eig_tkk, eig_s, eig_f;
+    HostDev<EighDesc> eig_s, eig_f;
+    HostDev<osv::TriDesc> tri_osv;         // OSV eigenproblems (tridiagonal route)
+    double *Ytri = nullptr, *tri_work = nullptr;
     HostDev<int> rows_w;                   // a_rows maps for the half transforms
     HostDev<int> kidx;                     // common-fitting-domain position lists
     GemmBatch gb_gram, gb_sf, gb_w, gb_k, gb_fx1, gb_fx2, gb_v, gb_kt1, gb_kt2, gb_c1, gb_c2;

@@ -11,6 +11,9 @@ cudaError_t launch_tkk_scale(double *T, double *work, const double *eps, const d
                              int *err, cudaStream_t s);
 cudaError_t launch_osv_select(const double *Zt, const double *omega, const double *eps, double *Q, double *Qe,
                               int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed, cudaStream_t s);
+cudaError_t launch_osv_count(const double *omega, int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed,
+                             cudaStream_t s);
+cudaError_t launch_scale_cols(const double *Q, const double *eps, double *Qe, long long rows, int nv, cudaStream_t s);
 cudaError_t launch_block_copy(const BlockCopy *d_bc, int n, cudaStream_t s);
 cudaError_t launch_pair_x(const PairInfo *pairs, int npairs, const double *Ut, const double *sv, double *X,
                           int *rdim, double tau_red, cudaStream_t s);

@@ -64,6 +64,31 @@ __global__ void k_osv_select(const double *__restrict__ Zt, const double *__rest
     }
 }
 
+// n_k from the decreasing eigenvalues: #(omega > l_osv) capped at nmax (or fixed), at least one (Eq. 6).
+__global__ void k_osv_count(const double *__restrict__ omega, int *__restrict__ nosv, int n_occ, int nv, int nmax,
+                            double l_osv, int n_fixed) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_occ) return;
+    const double *w = omega + (long long)k * nv;
+    int n;
+    if (n_fixed > 0) {
+        n = min(n_fixed, nv);
+    } else {
+        n = 0;
+        while (n < nv && w[n] > l_osv) ++n;
+        n = min(n, nmax);
+    }
+    nosv[k] = max(n, 1);
+}
+
+// Qe[r][a] = Q[r][a] * eps[a] over all rows of all LMOs.
+__global__ void k_scale_cols(const double *__restrict__ Q, const double *__restrict__ eps, double *__restrict__ Qe,
+                             long long rows, int nv) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < rows * nv;
+         idx += (long long)gridDim.x * blockDim.x)
+        Qe[idx] = Q[idx] * eps[idx % nv];
+}
+
 __global__ void k_block_copy(const BlockCopy *__restrict__ bc) {
     const BlockCopy b = bc[blockIdx.x];
     const long long nel = (long long)b.rows * b.cols;
@@ -136,6 +161,22 @@ cudaError_t launch_osv_select(const double *Zt, const double *omega, const doubl
     if (n_occ <= 0) return cudaSuccess;
     count_launch();
     k_osv_select<<<n_occ, 256, 0, s>>>(Zt, omega, eps, Q, Qe, nosv, nv, nmax, l_osv, n_fixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_osv_count(const double *omega, int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed,
+                             cudaStream_t s) {
+    if (n_occ <= 0) return cudaSuccess;
+    count_launch();
+    k_osv_count<<<(n_occ + 127) / 128, 128, 0, s>>>(omega, nosv, n_occ, nv, nmax, l_osv, n_fixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_cols(const double *Q, const double *eps, double *Qe, long long rows, int nv, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    const int blocks = (int)std::min<long long>((rows * nv + 255) / 256, 152LL * 8);
+    count_launch();
+    k_scale_cols<<<blocks, 256, 0, s>>>(Q, eps, Qe, rows, nv);
     return cudaGetLastError();
 }
 
