@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="bf16x4", choices=["fp64", "tf32x3", "bf16x4"],
+                    help="path whose throughput is the headline value; the FP64 path is always timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -55,7 +56,7 @@ def workload_config(prm, p):
                         f"n_aux={p.n_aux}, l_osv=1e-4 capped at {prm.n_osv_max} OSVs, pair/triple cutoffs "
                         f"{prm.r2b}/{prm.r3b} A",
             "n_occ": p.n_occ, "n_vir": p.n_vir, "n_aux": p.n_aux, "mbe_order": prm.mbe_order,
-            "precision": "fp64" if prm.precision == 0 else "mixed_tf32x3",
+            "precision": {0: "fp64", 1: "tf32x3", 2: "bf16x4"}[prm.precision],
             "l2": f"inputs larger than L2 (B = {p.B.nbytes / 1e6:.0f} MB > 129 MB)"}
 
 
@@ -127,8 +128,7 @@ def run_gpu(args):
     if rank > 0:   # each rank: an independent geometry of the same workload (own seed)
         _, pk, _ = WORKLOADS[WORKLOAD]
         p = make_problem(**{**pk, "seed": pk["seed"] + 1000 * rank})
-    if args.precision == "mixed":
-        prm.precision = 1
+    prec = {"fp64": 0, "tf32x3": 1, "bf16x4": 2}[args.precision]
     stream = torch.cuda.current_stream()
     dp = osvmbe.DeviceProblem.from_host(p)
     ctx = osvmbe.Context(stream)
@@ -140,31 +140,51 @@ def run_gpu(args):
         osvmbe.run_energy(ctx, dp, prm)
         ctx.gradient_backward(1.0, dB, dF)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    flops_step = ctx.residual_flops()
-    E, E_lin = ctx.energy()
-
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    def timed_steps(k):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        t0.record(stream)
+        for _ in range(k):
+            step()
+        t1.record(stream)
+        barrier()
+        return t0.elapsed_time(t1) / k
+
+    warm = max(args.warmup, 3)
+    # ---- the plain FP64 GPU path (reference point of the mixed path)
+    prm.precision = 0
+    for _ in range(warm):
+        step()
+    fp64_ms = timed_steps(args.steps)
+    E64, _ = ctx.energy()
+    dB.zero_()
+    step()
+    torch.cuda.synchronize()
+    dB64 = dB.clone()
+    # ---- the headline path
+    prm.precision = prec
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    flops_step = ctx.residual_flops()
+    E, E_lin = ctx.energy()
+    dB.zero_()
+    step()
+    torch.cuda.synchronize()
+    grad_diff = float((dB - dB64).abs().max())
+
     # ---- timed region (device-resident inputs)
     ctx.profile(True)
     l0 = ctypes_launches(osvmbe)
     with ClockSampler(local) as clk:
-        barrier()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        for _ in range(args.steps):
-            step()
-        t1.record(stream)
-        barrier()
+        ms = timed_steps(args.steps)
     launches = ctypes_launches(osvmbe) - l0
-    ms = t0.elapsed_time(t1) / args.steps
     stages = ctx.profile_read()
     ctx.profile(False)
     if world > 1:
@@ -210,20 +230,24 @@ def run_gpu(args):
     total_stage = sum(v[0] for v in stages.values())
     dom = max(stages.items(), key=lambda kv: kv[1][0])
     roof = roofline(dom, stages, flops_step, p, prm)
+    roof_tc = tensor_roofline(stages, p, prm) if prec > 0 else None
 
     out = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if prm.precision == 0 else "tf32x3+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {0: "f64", 1: "tf32x3+f64", 2: "bf16x4+f64"}[prec], "data": "synthetic",
         "config": workload_config(prm, p),
         "gradient_s_per_geometry": ms / 1e3,
         "residual_solve_tflops": flops_step / (stages["residual"][0] / stages["residual"][1] * 1e-3) / 1e12
         if "residual" in stages else None,
         "residual_flops_per_step": flops_step,
         "energy_Eh": E, "energy_linear_Eh": E_lin,
+        "fp64_ms_per_step": fp64_ms, "mixed_vs_fp64": fp64_ms / ms, "energy_fp64_Eh": E64,
+        "abs_dE_vs_fp64_Eh": abs(E - E64), "max_abs_dgradB_vs_fp64": grad_diff,
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "stage_share": {k: v[0] / total_stage for k, v in stages.items()},
         "roofline": roof,
+        "roofline_tensor_gemm": roof_tc,
         "e2e": {"value": flops_all / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -259,6 +283,32 @@ def stage_flops(name, p, prm, flops_step):
     if name == "osv_eigh":
         return n * (4.0 / 3.0 + 2.0 + 6.0) * nv ** 3     # Householder + explicit Q + QL rotations (model)
     return None
+
+
+def tensor_roofline(stages, p, prm):
+    """The tcgen05 GEMM of the T_kk Gram products: issued tensor FLOPs vs the measured dense BF16 peak (each useful
+    multiply-add costs 16 BF16 slice products in the exact-slice mode, 3 TF32 products (at half the BF16 rate)
+    in the split-TF32 mode); useful FLOPs reported beside it."""
+    if "tkk_gram" not in stages:
+        return None
+    ms_total, calls = stages["tkk_gram"]
+    avg = ms_total / calls
+    useful = stage_flops("tkk_gram", p, prm, 0.0)
+    mult = 16.0 if prm.precision == 2 else 6.0
+    peak = measured_peak("bf16_tflops", 1949.0)
+    issued = useful * mult / (avg * 1e-3) / 1e12
+    return {"bound": "tensor", "stage": "tkk_gram", "kernel": "k_gemm_bf16x4" if prm.precision == 2 else "k_gemm_tf32x3",
+            "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak, "traffic": None,
+            "useful_tflops": useful / (avg * 1e-3) / 1e12, "avg_launch_ms": avg,
+            "peak_note": "measured dense bf16 (burst); achieved counts issued BF16-equivalent slice products"}
+
+
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except Exception:
+        return fallback
 
 
 def roofline(dom, stages, flops_step, p, prm):

@@ -40,9 +40,15 @@ typedef enum {
 
 typedef enum {
     OSV_FP64 = 0,          /* every contraction in FP64                                                    */
-    OSV_MIXED_TF32X3 = 1   /* dense DF contractions in split TF32 on tcgen05 tensor cores, FP32 inside a
-                              k-block and FP64 across k-blocks; eigensolves, residual norms, energy and
-                              gradient accumulation in FP64                                                */
+    OSV_MIXED_TF32X3 = 1,  /* dense DF contractions (T_kk Gram, half transform, K blocks, adjoint products) in
+                              split TF32 (hi*hi + hi*lo + lo*hi) on tcgen05 tensor cores with FP32 accumulation
+                              in tensor memory; that accumulation is biased over long K (E error ~1e-5
+                              relative): the fast mode                                                     */
+    OSV_MIXED_BF16X4 = 2   /* the same contractions on tcgen05 with each FP64 operand cut into four signed
+                              8-bit integer slices (exact BF16) under per-row power-of-two scales, all sixteen
+                              slice products accumulated exactly per 128-K chunk: unbiased, ~31 significant
+                              bits.  Eigensolves, pair orthonormalisation, residual iterations, norms, energy
+                              and gradient accumulation stay FP64                                           */
 } osv_precision;
 
 /* Method parameters.  l_osv: OSV cut on the eigenvalues of T_kk (Sec. 2.1, Eq. 6).  r2b/r3b: distance

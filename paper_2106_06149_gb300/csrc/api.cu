@@ -33,7 +33,7 @@ osv_status check_params(osv_ctx *c, const osv_params *p) {
     if (p->mbe_order < 0 || p->mbe_order > 3) return c->fail(OSV_ERR_INVALID, "mbe_order must be 0..3");
     if (!(p->tau_red >= 0.0) || !(p->r2b >= 0.0) || !(p->r3b >= 0.0) || !std::isfinite(p->l_osv))
         return c->fail(OSV_ERR_INVALID, "tau_red, r2b, r3b must be >= 0 and l_osv finite");
-    if (p->precision != OSV_FP64 && p->precision != OSV_MIXED_TF32X3)
+    if (p->precision != OSV_FP64 && p->precision != OSV_MIXED_TF32X3 && p->precision != OSV_MIXED_BF16X4)
         return c->fail(OSV_ERR_INVALID, "unknown precision");
     return OSV_OK;
 }
@@ -600,6 +600,10 @@ osv_status build_plan(osv_ctx *c) {
     for (GemmBatch *g : {&c->gb_gram, &c->gb_sf, &c->gb_w, &c->gb_k, &c->gb_fx1, &c->gb_fx2, &c->gb_v, &c->gb_kt1,
                          &c->gb_kt2, &c->gb_c1, &c->gb_c2})
         if ((e = gemm_batch_upload(*g)) != cudaSuccess) return c->cuda_fail(e, "upload gemm batch");
+    if ((e = tc_batch_prepare(c->gb_gram, c->tc_gram)) != cudaSuccess || (e = tc_batch_prepare(c->gb_w, c->tc_w)) != cudaSuccess ||
+        (e = tc_batch_prepare(c->gb_k, c->tc_k)) != cudaSuccess || (e = bf16x4_batch_prepare(c->gb_gram, c->oz_gram)) != cudaSuccess ||
+        (e = bf16x4_batch_prepare(c->gb_w, c->oz_w)) != cudaSuccess || (e = bf16x4_batch_prepare(c->gb_k, c->oz_k)) != cudaSuccess)
+        return c->cuda_fail(e, "tensor-core tiling");
     return OSV_OK;
 }
 
@@ -616,7 +620,7 @@ osv_status run_osv_build(osv_ctx *c) {
     }
     {
         StageTimer t(*c, "tkk_gram");
-        CK(gemm_batch_run(c->gb_gram, s), "gram");
+        CK(c->run_dense(c->gb_gram, c->tc_gram, c->oz_gram), "gram");
         CK(launch_tkk_scale(c->Tkk, c->Awork, c->eps, c->focc, n, nv, c->derr, s), "tkk");
     }
     {
@@ -636,11 +640,11 @@ osv_status run_osv_build(osv_ctx *c) {
     }
     {
         StageTimer t(*c, "half_transform");
-        CK(gemm_batch_run(c->gb_w, s), "half transform");
+        CK(c->run_dense(c->gb_w, c->tc_w, c->oz_w), "half transform");
     }
     {
         StageTimer t(*c, "k_blocks");
-        CK(gemm_batch_run(c->gb_k, s), "K blocks");
+        CK(c->run_dense(c->gb_k, c->tc_k, c->oz_k), "K blocks");
     }
     {
         StageTimer t(*c, "pair_basis");
@@ -679,6 +683,7 @@ osv_status device_error(osv_ctx *c) {
     if (e != cudaSuccess) return c->cuda_fail(e, "read error word");
     if (h == kDevEighNoConv) return c->fail(OSV_ERR_TIMEOUT, "eigensolver hit its iteration cap");
     if (h == kDevNonFinite) return c->fail(OSV_ERR_NUMERIC, "non-finite value in T_kk (check B, eps, f_occ)");
+    if (h == kDevTimeout) return c->fail(OSV_ERR_TIMEOUT, "a bounded tensor-core wait expired");
     return OSV_OK;
 }
 

@@ -17,7 +17,7 @@ extern std::atomic<long long> g_launches;
 inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Error word written by bounded device loops (never a trap).
-enum DevErr : int { kDevOk = 0, kDevEighNoConv = 1, kDevNonFinite = 2 };
+enum DevErr : int { kDevOk = 0, kDevEighNoConv = 1, kDevNonFinite = 2, kDevTimeout = 3 };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -75,6 +75,8 @@ struct GemmDesc {
     const int *k_idx_b;
     const int *n_idx_b;
     const int *n_idx_c;
+    int *ea;   // row scales of A and column scales of B (exact-slice tensor-core GEMM; set by its prepare step)
+    int *eb;
 };
 
 // Host-side batch of GEMM problems: descriptors and per-problem tile offsets live in device memory.

@@ -8,6 +8,7 @@
 #include "../../include/osvmbe.h"
 #include "adjoint.h"
 #include "osv_eig.h"
+#include "tc_gemm.h"
 
 namespace osv {
 struct ProfEvent {
@@ -95,6 +96,8 @@ struct osv_ctx {
     HostDev<int> rows_w;                   // a_rows maps for the half transforms
     HostDev<int> kidx;                     // common-fitting-domain position lists
     GemmBatch gb_gram, gb_sf, gb_w, gb_k, gb_fx1, gb_fx2, gb_v, gb_kt1, gb_kt2, gb_c1, gb_c2;
+    osv::TcTiles tc_gram, tc_w, tc_k;          // tensor-core tilings of the dense DF contractions (TF32x3)
+    osv::TcTiles oz_gram, oz_w, oz_k;          // exact-slice BF16x4 tilings
 
     osv::AdjointPlan adj;
 
@@ -129,6 +132,13 @@ struct osv_ctx {
         if (e == cudaSuccess) allocs.push_back((void *)p);
         return e;
     }
+    // dense DF contractions: FP64 CUDA cores, split TF32 (biased FP32 accumulation) or exact BF16 slices on the
+    // tcgen05 tensor cores
+    cudaError_t run_dense(const GemmBatch &b, const osv::TcTiles &t, const osv::TcTiles &oz) {
+        if (prm.precision == OSV_MIXED_TF32X3) return osv::tc_batch_run(b, t, derr, stream);
+        if (prm.precision == OSV_MIXED_BF16X4) return osv::bf16x4_batch_run(oz, derr, stream);
+        return osv::gemm_batch_run(b, stream);
+    }
     template <class T>
     cudaError_t upload(HostDev<T> &hd) {
         cudaError_t e = dalloc(hd.d, hd.h.size());
@@ -142,6 +152,7 @@ struct osv_ctx {
             gemm_batch_free(*g);
             g->h.clear();
         }
+        for (osv::TcTiles *t : {&tc_gram, &tc_w, &tc_k, &oz_gram, &oz_w, &oz_k}) osv::tc_tiles_free(*t);
         adj.release();
         built = solved = false;
     }

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libosvmbe.so")
 
 OSV_OK, OSV_ERR_INVALID, OSV_ERR_NOCONV, OSV_ERR_OOM, OSV_ERR_CUDA, OSV_ERR_TIMEOUT, OSV_ERR_NUMERIC = \
     0, -1, -2, -3, -4, -5, -6
-OSV_FP64, OSV_MIXED_TF32X3 = 0, 1
+OSV_FP64, OSV_MIXED_TF32X3, OSV_MIXED_BF16X4 = 0, 1, 2
 
 EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv_build", "cluster_residual_solve",
            "mbe3_combine", "energy", "gradient_backward", "osv_cluster_count", "osv_cluster_info",

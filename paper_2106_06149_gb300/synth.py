@@ -34,7 +34,7 @@ class Params:
     tau_red: float = 1e-8     # drop pair-overlap eigenvalues below this (redundant pair space)
     tol: float = 1e-8         # residual convergence: max_ij ||R~_ij||_F <= tol
     max_iter: int = 100       # residual iteration cap
-    precision: int = 0        # 0 = FP64, 1 = mixed TF32x3 GEMMs
+    precision: int = 0        # 0 = FP64, 1 = split-TF32 tensor-core GEMMs, 2 = exact BF16x4 tensor-core GEMMs
 
     def as_dict(self):
         return dataclasses.asdict(self)
@@ -170,14 +170,14 @@ WORKLOADS = {
     2: ("MBE(3) mixed, 256 LMOs in a 20 A cube, n_vir=1500, n_aux=6000, 7 A fitting domains, B fp32",
         dict(n_occ=256, n_vir=1500, n_aux=6000, geometry="cube", box=20.0, radius=7.0, seed=2,
              dtype=np.float32),
-        dict(mbe_order=3, precision=1)),
+        dict(mbe_order=3, precision=2)),
     3: ("gradient, 128 LMOs in a 14 A cube, n_vir=800, n_aux=3200, 7 A fitting domains",
         dict(n_occ=128, n_vir=800, n_aux=3200, geometry="cube", box=14.0, radius=7.0, seed=3),
         dict(mbe_order=3)),
     4: ("large MBE(3) E+grad, 512 LMOs in a 28 A cube, n_vir=3000, n_aux=12000, ~2000 aux per domain, B fp32",
         dict(n_occ=512, n_vir=3000, n_aux=12000, geometry="cube", box=28.0, radius="mean2000", seed=4,
              dtype=np.float32),
-        dict(mbe_order=3, precision=1)),
+        dict(mbe_order=3, precision=2)),
 }
 
 

@@ -1,0 +1,78 @@
+"""Mixed-precision paths (dense DF contractions on tcgen05 tensor cores, everything else FP64) against the FP64
+GPU path and the oracle.  Exact BF16x4 slices (precision 2) must meet |dE| <= 1e-6 Eh and max |d grad| <= 1e-6;
+the split-TF32 mode (precision 1, biased FP32 accumulation) is checked at a looser bar.  Errors are printed."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2106_06149_gb300.synth import Params, make_problem, workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osvmbe():
+    from paper_2106_06149_gb300 import build, osvmbe as m
+    build.build()
+    m.load()
+    return m
+
+
+def run(m, p, prm, grad=True):
+    dp = m.DeviceProblem.from_host(p)
+    ctx = m.Context()
+    ctx.clusters_build(dp, prm)
+    E, El = m.run_energy(ctx, dp, prm)
+    out = {"E": E}
+    if grad:
+        dB = torch.zeros_like(dp.B)
+        dF = torch.zeros_like(dp.f_occ)
+        ctx.gradient_backward(1.0, dB, dF)
+        torch.cuda.synchronize()
+        out["dB"] = dB.cpu().numpy().astype(np.float64)
+        out["dF"] = dF.cpu().numpy()
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("local", [False, True])
+def test_bf16x4_small_matches_fp64_and_oracle(osvmbe, local):
+    if local:
+        p = make_problem(6, 24, 90, geometry="cube", box=7.0, dmin=1.4, radius=4.5, seed=51)
+    else:
+        p = make_problem(6, 40, 150, seed=52)
+    base = dict(n_osv_fixed=6, mbe_order=3, r2b=6.0, r3b=5.0, tol=1e-11)
+    f = run(osvmbe, p, Params(**base))
+    x = run(osvmbe, p, Params(**base, precision=2))
+    o = oracle.gradient(p, Params(**base))
+    print(f"\nmixed vs fp64: dE = {x['E'] - f['E']:.3e} (E = {f['E']:.6f}); "
+          f"max|d dB| = {np.abs(x['dB'] - f['dB']).max():.3e}; max|d dF| = {np.abs(x['dF'] - f['dF']).max():.3e}")
+    assert abs(f["E"] - o["E"]) <= 1e-9
+    assert abs(x["E"] - f["E"]) <= 1e-6
+    assert np.abs(x["dB"] - f["dB"]).max() <= 1e-6
+    assert np.abs(x["dF"] - f["dF"]).max() <= 1e-6
+
+
+def test_tf32x3_small_is_close(osvmbe):
+    p = make_problem(6, 40, 150, seed=52)
+    base = dict(n_osv_fixed=6, mbe_order=3, r2b=6.0, r3b=5.0, tol=1e-11)
+    f = run(osvmbe, p, Params(**base), grad=False)
+    x = run(osvmbe, p, Params(**base, precision=1), grad=False)
+    print(f"\ntf32x3 vs fp64: dE = {x['E'] - f['E']:.3e} (E = {f['E']:.6f})")
+    assert abs(x["E"] - f["E"]) <= 1e-4 * abs(f["E"])
+
+
+@pytest.mark.slow
+def test_bf16x4_bench_workload(osvmbe):
+    p, prm = workload(1)
+    f = run(osvmbe, p, prm)
+    prm.precision = 2
+    x = run(osvmbe, p, prm)
+    dE = x["E"] - f["E"]
+    gb = np.abs(x["dB"] - f["dB"]).max()
+    gf = np.abs(x["dF"] - f["dF"]).max()
+    print(f"\nbench workload mixed vs fp64: E = {f['E']:.9f}, dE = {dE:.3e} Eh (rel {dE / abs(f['E']):.2e}), "
+          f"max|d dB| = {gb:.3e} (max|dB| {np.abs(f['dB']).max():.3e}), max|d dF| = {gf:.3e}")
+    assert abs(dE) <= 1e-6
+    assert gb <= 1e-6 and gf <= 1e-6
