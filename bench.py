@@ -281,7 +281,7 @@ def stage_flops(name, p, prm, flops_step):
     if name == "half_transform":
         return float(np.sum(2.0 * nb * nm * nv * a))
     if name == "osv_eigh":
-        return n * (4.0 / 3.0 + 2.0 + 6.0) * nv ** 3     # Householder + explicit Q + QL rotations (model)
+        return n * (4.0 / 3.0) * nv ** 3                 # Householder tridiagonalisation (bisection and kept-vector work are O(n^2))
     return None
 
 
