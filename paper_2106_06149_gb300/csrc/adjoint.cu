@@ -26,25 +26,26 @@ namespace {
 constexpr int kThreads = 256;
 
 // C (M x N) (+)= alpha * op(A) diag(dk) op(B) with dk optional (scales the k index).
-__device__ void sgemm_d(int M, int N, int K, const double *__restrict__ A, long long lda, bool ta,
-                        const double *__restrict__ dk, const double *__restrict__ B, long long ldb, bool tb,
-                        double *C, long long ldc, double alpha, bool accumulate) {
+template <class R>
+__device__ void sgemm_d(int M, int N, int K, const R *__restrict__ A, long long lda, bool ta,
+                        const R *__restrict__ dk, const R *__restrict__ B, long long ldb, bool tb,
+                        R *C, long long ldc, R alpha, bool accumulate) {
     const int mt = (M + 3) >> 2, nt = (N + 3) >> 2;
     for (int t = threadIdx.x; t < mt * nt; t += blockDim.x) {
         const int bm = (t / nt) << 2, bn = (t % nt) << 2;
-        double acc[4][4] = {};
+        R acc[4][4] = {};
         for (int k = 0; k < K; ++k) {
-            const double sk = dk ? dk[k] : 1.0;
-            double a[4], b[4];
+            const R sk = dk ? dk[k] : R(1);
+            R a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int m = bm + i;
-                a[i] = m < M ? sk * (ta ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : 0.0;
+                a[i] = m < M ? sk * (ta ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : R(0);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int n = bn + j;
-                b[j] = n < N ? (tb ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : 0.0;
+                b[j] = n < N ? (tb ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : R(0);
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -59,7 +60,7 @@ __device__ void sgemm_d(int M, int N, int K, const double *__restrict__ A, long 
             for (int j = 0; j < 4; ++j) {
                 const int n = bn + j;
                 if (n >= N) continue;
-                double *c = C + (long long)m * ldc + n;
+                R *c = C + (long long)m * ldc + n;
                 *c = accumulate ? *c + alpha * acc[i][j] : alpha * acc[i][j];
             }
         }
@@ -72,17 +73,21 @@ struct AdjArgs {
     const Term *terms;
     const PairInfo *pairs;
     const int *rdim;
-    const double *e, *Tslot, *Stil, *focc;
+    const double *focc;
+    const void *e, *Tslot, *Stil;  // R-typed: pair energies, slot amplitudes, coupling blocks
     int n_occ, ncl;
-    double *GS, *GF, *GSc, *dF;   // accumulators (pair off / coupling offset / n_occ^2)
-    double *scratch;
+    double *GS, *GF, *GSc, *dF;   // FP64 accumulators (pair off / coupling offset / n_occ^2)
+    void *scratch;                // R-typed per-CTA scratch
     long long sstride, pstride;   // per-CTA scratch, one matrix slot
 };
 
+// Per-cluster partials of the weighted Hylleraas functional (products in precision R, FP64 accumulation).
+template <class R>
 __global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
     __shared__ double red[kThreads / 32];
-    double *Tb = A.scratch + (long long)blockIdx.x * A.sstride;
-    double *M1 = Tb + A.pstride, *M2 = M1 + A.pstride, *U1 = M2 + A.pstride, *U2 = U1 + A.pstride;
+    R *Tb = (R *)A.scratch + (long long)blockIdx.x * A.sstride;
+    R *M1 = Tb + A.pstride, *M2 = M1 + A.pstride, *U1 = M2 + A.pstride, *U2 = U1 + A.pstride;
+    const R *Ts = (const R *)A.Tslot, *Ss = (const R *)A.Stil, *Ee = (const R *)A.e;
     const int tid = threadIdx.x;
     for (int c = blockIdx.x; c < A.ncl; c += gridDim.x) {
         const ClusterInfo C = A.clusters[c];
@@ -92,15 +97,15 @@ __global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
             const Slot S = A.slots[s];
             const PairInfo P = A.pairs[S.pair];
             const int r = A.rdim[S.pair], np = P.np;
-            const double *T = A.Tslot + S.t_off;
-            const double *e = A.e + P.e_off;
+            const R *T = Ts + S.t_off;
+            const R *e = Ee + P.e_off;
             const double fii = A.focc[(long long)P.i * A.n_occ + P.i], fjj = A.focc[(long long)P.j * A.n_occ + P.j];
             double tt = 0.0;
             for (int idx = tid; idx < r * r; idx += kThreads) {
                 const int a = idx / r, b = idx % r;
-                const double tb = 2.0 * T[(long long)a * np + b] - T[(long long)b * np + a];
+                const R tb = R(2) * T[(long long)a * np + b] - T[(long long)b * np + a];
                 Tb[(long long)a * np + b] = tb;
-                tt += T[(long long)a * np + b] * tb;
+                tt += (double)T[(long long)a * np + b] * (double)tb;
             }
             tt = block_sum(tt, red);   // also orders the Tb writes before the products below
             const double wm = w * S.mult;
@@ -109,47 +114,47 @@ __global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
                 atomicAdd(&A.dF[(long long)P.j * A.n_occ + P.j], -wm * tt);
             }
             // M1 = Tb L T^T + T^T L Tb ;  M2 = Tb T^T + T^T Tb
-            sgemm_d(r, r, r, Tb, np, false, e, T, np, true, M1, np, 1.0, false);
-            sgemm_d(r, r, r, Tb, np, false, nullptr, T, np, true, M2, np, 1.0, false);
+            sgemm_d<R>(r, r, r, Tb, np, false, e, T, np, true, M1, np, R(1), false);
+            sgemm_d<R>(r, r, r, Tb, np, false, nullptr, T, np, true, M2, np, R(1), false);
             __syncthreads();
-            sgemm_d(r, r, r, T, np, true, e, Tb, np, false, M1, np, 1.0, true);
-            sgemm_d(r, r, r, T, np, true, nullptr, Tb, np, false, M2, np, 1.0, true);
+            sgemm_d<R>(r, r, r, T, np, true, e, Tb, np, false, M1, np, R(1), true);
+            sgemm_d<R>(r, r, r, T, np, true, nullptr, Tb, np, false, M2, np, R(1), true);
             __syncthreads();
             for (int idx = tid; idx < r * r; idx += kThreads) {
                 const long long o = (long long)(idx / r) * np + idx % r;
-                atomicAdd(&A.GS[P.off + o], wm * (M1[o] - (fii + fjj) * M2[o]));
-                atomicAdd(&A.GF[P.off + o], wm * M2[o]);
+                atomicAdd(&A.GS[P.off + o], wm * ((double)M1[o] - (fii + fjj) * (double)M2[o]));
+                atomicAdd(&A.GF[P.off + o], wm * (double)M2[o]);
             }
             __syncthreads();
         }
         for (int t = C.term0; t < C.term1; ++t) {
             const Term T = A.terms[t];
-            const Slot Sd = A.slots[T.dst], Ss = A.slots[T.src];
-            const PairInfo Pd = A.pairs[Sd.pair], Ps = A.pairs[Ss.pair];
-            const int rp = A.rdim[Sd.pair], rq = A.rdim[Ss.pair];
+            const Slot Sd = A.slots[T.dst], Ssl = A.slots[T.src];
+            const PairInfo Pd = A.pairs[Sd.pair], Ps = A.pairs[Ssl.pair];
+            const int rp = A.rdim[Sd.pair], rq = A.rdim[Ssl.pair];
             const int np = Pd.np, nq = Ps.np;
             const double f = A.focc[(long long)T.fx * A.n_occ + T.fy];
-            const double *Sb = A.Stil + T.sblk;
+            const R *Sb = Ss + T.sblk;
             const long long lds = T.s_trans ? np : nq;
-            const double *Tq = A.Tslot + Ss.t_off;
-            const double *Tp = A.Tslot + Sd.t_off;
+            const R *Tq = Ts + Ssl.t_off;
+            const R *Tp = Ts + Sd.t_off;
             const double wm = w * Sd.mult;
             // Tb of the destination pair
             for (int idx = tid; idx < rp * rp; idx += kThreads) {
                 const int a = idx / rp, b = idx % rp;
-                Tb[(long long)a * np + b] = 2.0 * Tp[(long long)a * np + b] - Tp[(long long)b * np + a];
+                Tb[(long long)a * np + b] = R(2) * Tp[(long long)a * np + b] - Tp[(long long)b * np + a];
             }
             __syncthreads();
             // U1 = Tb S (rp x rq), U2 = Tb^T S, M1 = S T' (rp x rq)
-            sgemm_d(rp, rq, rp, Tb, np, false, nullptr, Sb, lds, T.s_trans, U1, nq, 1.0, false);
-            sgemm_d(rp, rq, rp, Tb, np, true, nullptr, Sb, lds, T.s_trans, U2, nq, 1.0, false);
-            sgemm_d(rp, rq, rq, Sb, lds, T.s_trans, nullptr, Tq, nq, T.t_trans, M1, nq, 1.0, false);
+            sgemm_d<R>(rp, rq, rp, Tb, np, false, nullptr, Sb, lds, T.s_trans, U1, nq, R(1), false);
+            sgemm_d<R>(rp, rq, rp, Tb, np, true, nullptr, Sb, lds, T.s_trans, U2, nq, R(1), false);
+            sgemm_d<R>(rp, rq, rq, Sb, lds, T.s_trans, nullptr, Tq, nq, T.t_trans, M1, nq, R(1), false);
             __syncthreads();
             // X = <S T', Tb S>
             double x = 0.0;
             for (int idx = tid; idx < rp * rq; idx += kThreads) {
                 const long long o = (long long)(idx / rq) * nq + idx % rq;
-                x += M1[o] * U1[o];
+                x += (double)M1[o] * (double)U1[o];
             }
             x = block_sum(x, red);
             if (tid == 0) {
@@ -157,14 +162,14 @@ __global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
                 if (Pd.i != Pd.j) atomicAdd(&A.dF[(long long)T.fy * A.n_occ + T.fx], -w * x);
             }
             // M2 = U1 T'^T + U2 T'  (rp x rq)
-            sgemm_d(rp, rq, rq, U1, nq, false, nullptr, Tq, nq, !T.t_trans, M2, nq, 1.0, false);
+            sgemm_d<R>(rp, rq, rq, U1, nq, false, nullptr, Tq, nq, !T.t_trans, M2, nq, R(1), false);
             __syncthreads();
-            sgemm_d(rp, rq, rq, U2, nq, false, nullptr, Tq, nq, T.t_trans, M2, nq, 1.0, true);
+            sgemm_d<R>(rp, rq, rq, U2, nq, false, nullptr, Tq, nq, T.t_trans, M2, nq, R(1), true);
             __syncthreads();
             double *G = A.GSc + T.sblk;
             for (int idx = tid; idx < rp * rq; idx += kThreads) {
                 const int a = idx / rq, b = idx % rq;
-                const double v = -wm * f * M2[(long long)a * nq + b];
+                const double v = -wm * f * (double)M2[(long long)a * nq + b];
                 if (T.s_trans) atomicAdd(&G[(long long)b * np + a], v);   // stored as (src pair) x (dst pair)
                 else atomicAdd(&G[(long long)a * nq + b], v);
             }
@@ -486,7 +491,11 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
     a.pstride = pstride;
     {
         StageTimer t(c, "adj_clusters");
-        if (grid > 0) { count_launch(); k_cluster_adjoint<<<grid, kThreads, 0, s>>>(a); }
+        // FP64 in every mode: FP32 products here cost ~7e-7 relative in dE/dB, too much for a 1e-6 bar
+        if (grid > 0) {
+            count_launch();
+            k_cluster_adjoint<double><<<grid, kThreads, 0, s>>>(a);
+        }
         CK(cudaGetLastError());
     }
     {

@@ -413,6 +413,14 @@ osv_status build_plan(osv_ctx *c) {
     ALLOC(c->iters, c->cl.size());
     ALLOC(c->lin, np_);
     ALLOC(c->Eout, 2);
+    ALLOC(c->e32, c->pair_vec);
+    ALLOC(c->Kt32, c->pair_mat);
+    ALLOC(c->S32, c->coup_mat);
+    ALLOC(c->T32, c->slot_mat);
+    ALLOC(c->R32, c->slot_mat);
+    ALLOC(c->H32, c->slot_mat);
+    ALLOC(c->G1_32, (long long)c->cl.size() * c->gstride);
+    ALLOC(c->evals64, c->cl.size());
     if (c->B_dtype == 1) {
         ALLOC(c->B64own, c->aux_ptr[n] * (long long)nv);
         c->B64 = c->B64own;
@@ -672,6 +680,11 @@ osv_status run_osv_build(osv_ctx *c) {
         CK(launch_block_copy(c->bc_coup.d, (int)c->bc_coup.h.size(), s), "coupling assemble");
         CK(gemm_batch_run(c->gb_c1, s), "c1");
         CK(gemm_batch_run(c->gb_c2, s), "c2");
+        if (c->prm.precision != OSV_FP64) {   // FP32 copies for the mixed residual iterations
+            CK(launch_to_f32(c->pe, c->e32, c->pair_vec, s), "e32");
+            CK(launch_to_f32(c->Kt, c->Kt32, c->pair_mat, s), "Kt32");
+            CK(launch_to_f32(c->Stil, c->S32, c->coup_mat, s), "S32");
+        }
     }
 #undef CK
     return OSV_OK;
@@ -759,13 +772,22 @@ osv_status cluster_residual_solve(osv_ctx *c, int *n_iter_out, int32_t *cluster_
     a.iters = c->iters;
     a.tol = c->prm.tol;
     a.max_iter = c->prm.max_iter;
+    a.e32 = c->e32;
+    a.Kt32 = c->Kt32;
+    a.sblk32 = c->S32;
+    a.T32 = c->T32;
+    a.R32 = c->R32;
+    a.H32 = c->H32;
+    a.G1_32 = c->G1_32;
+    a.evals64 = c->evals64;
     if ((e = cudaMemsetAsync(c->Tslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
         return c->cuda_fail(e, "memset T");
     if ((e = cudaMemsetAsync(c->Rslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
         return c->cuda_fail(e, "memset R");
     {
         StageTimer t(*c, "residual");
-        if ((e = launch_residual(a, (int)c->cl.size(), c->stream)) != cudaSuccess) return c->cuda_fail(e, "residual");
+        if ((e = launch_residual(a, (int)c->cl.size(), c->prm.precision != OSV_FP64, c->stream)) != cudaSuccess)
+            return c->cuda_fail(e, "residual");
     }
     if (cluster_status) {
         if ((e = cudaMemcpyAsync(cluster_status, c->iters, c->cl.size() * sizeof(int), cudaMemcpyDeviceToDevice,

@@ -78,6 +78,9 @@ struct osv_ctx {
     double *Scp = nullptr, *Stil = nullptr, *ctmp = nullptr;
     long long coup_mat = 0;
     double *Tslot = nullptr, *Rslot = nullptr, *G1 = nullptr, *Ecl = nullptr, *lin = nullptr, *Eout = nullptr;
+    // FP32 copies and work arrays of the mixed residual solve
+    float *e32 = nullptr, *Kt32 = nullptr, *S32 = nullptr, *T32 = nullptr, *R32 = nullptr, *H32 = nullptr, *G1_32 = nullptr;
+    int *evals64 = nullptr;
     int *iters = nullptr;
     long long slot_mat = 0, gstride = 0;
 

@@ -70,6 +70,11 @@ struct SolveArgs {
     int *iters;             // per cluster iterations (-1: not converged)
     double tol;
     int max_iter;
+    // mixed mode (FP32 iterations + FP64 refinement): FP32 copies of e, K~ and S~, per-slot FP32 work arrays
+    const float *e32, *Kt32, *sblk32;
+    float *T32, *R32, *H32;   // FP32 amplitudes / corrections, residuals, right-hand sides (per slot)
+    float *G1_32;
+    int *evals64;             // per cluster: FP64 residual evaluations used
 };
 
 }  // namespace osv

@@ -19,7 +19,8 @@ cudaError_t launch_pair_x(const PairInfo *pairs, int npairs, const double *Ut, c
                           int *rdim, double tau_red, cudaStream_t s);
 cudaError_t launch_clean_w(const PairInfo *pairs, int npairs, const int *rdim, double *Wt, double *e,
                            cudaStream_t s);
-cudaError_t launch_residual(const SolveArgs &a, int nclusters, cudaStream_t s);
+cudaError_t launch_residual(const SolveArgs &a, int nclusters, bool mixed, cudaStream_t s);
+cudaError_t launch_to_f32(const double *in, float *out, long long n, cudaStream_t s);
 cudaError_t launch_combine(const PairInfo *pairs, int npairs, const int *ptr, const long long *src, const int *w,
                            const double *T, double *Tc, cudaStream_t s);
 cudaError_t launch_energy(const PairInfo *pairs, const int *rdim, const double *Kt, const double *Tc, int npairs,

@@ -105,15 +105,31 @@ __global__ void __launch_bounds__(kT) k_tridiag_osv(const TriDesc *__restrict__ 
 }
 
 // ------------------------------------------------------------------------------------- 2. bisection
+// Number of eigenvalues below x: sign changes of the leading principal minors p_i = det(T_0..i - x), computed by
+// the three-term recurrence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (no division: on GB300 an FP64
+// division costs ~430 cycles of latency, a multiply-add 64).  Every four steps both carried minors are rescaled
+// by an exact power of two, which keeps them finite without changing any sign.  pivmin stands in for an exactly
+// zero minor.
 __device__ __forceinline__ int sturm_below(const double *d, const double *e2, int n, double x, double pivmin) {
-    int cnt = 0;
-    double q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < 0.0;
+    double pm = 1.0, pc = d[0] - x;
+    if (pc == 0.0) pc = -pivmin;
+    int cnt = pc < 0.0;
     for (int i = 1; i < n; ++i) {
-        q = (d[i] - x) - e2[i - 1] / q;
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += q < 0.0;
+        double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
+        if (pn == 0.0) pn = (pc < 0.0 ? pivmin : -pivmin) * fabs(pc);   // treat as a tiny value of opposite sign
+        cnt += (pn < 0.0) != (pc < 0.0);
+        pm = pc;
+        pc = pn;
+        if ((i & 3) == 0) {
+            const double a = fabs(pc);
+            if (a > 0x1p+600) {
+                pc *= 0x1p-600;
+                pm *= 0x1p-600;
+            } else if (a < 0x1p-600) {
+                pc *= 0x1p+600;
+                pm *= 0x1p+600;
+            }
+        }
     }
     return cnt;
 }
@@ -141,7 +157,8 @@ __global__ void __launch_bounds__(kT) k_tri_bisect(const TriDesc *__restrict__ d
         const double span = fmax(hi - lo, fmax(fabs(lo), fabs(hi)));
         s_lo = lo - 2.0 * DBL_EPSILON * span - 1e-300;
         s_hi = hi + 2.0 * DBL_EPSILON * span + 1e-300;
-        s_piv = fmax(DBL_MIN, 1e-300 + DBL_MIN * emax) * 1e10;
+        s_piv = 1e-30;   // relative size of a stand-in for an exactly vanishing minor
+        (void)emax;
     }
     __syncthreads();
     for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < n; j += gridDim.y * blockDim.x) {

@@ -1,5 +1,5 @@
 // Cluster residual solver (Eq. 4 per cluster, Sec. 2.2.1), MBE(3) combination (Eqs. 28-32) and the
-// Hylleraas energy (Eq. 3), FP64.
+// Hylleraas energy (Eq. 3).  Plain FP64 solve, or FP32 iterations with FP64 iterative refinement (mixed modes).
 //
 // Each pair ij of a cluster works in the orthonormal pseudo-canonical basis Phi_ij = (Q_i Q_j) V_ij of its own
 // domain (V^T S_(ij,ij) V = 1, V^T F_(ij,ij) V = diag(e)).  Projected on it, Eq. 4 reads
@@ -18,28 +18,29 @@ constexpr int kThreads = 256;
 
 // C (M x N) = alpha * op(A) op(B) (+ C if accumulate).  op(A)(m,k) = ta ? A[k*lda+m] : A[m*lda+k],
 // op(B)(k,n) = tb ? B[n*ldb+k] : B[k*ldb+n].  Block-cooperative, 4 x 4 outputs per thread and tile.
-__device__ void blk_gemm(int M, int N, int K, const double *__restrict__ A, long long lda, bool ta,
-                         const double *__restrict__ B, long long ldb, bool tb, double *C, long long ldc,
-                         double alpha, bool accumulate) {
+template <class R>
+__device__ void blk_gemm(int M, int N, int K, const R *__restrict__ A, long long lda, bool ta,
+                         const R *__restrict__ B, long long ldb, bool tb, R *C, long long ldc, R alpha,
+                         bool accumulate) {
     const int mt = (M + 3) >> 2, nt = (N + 3) >> 2;
     for (int t = threadIdx.x; t < mt * nt; t += blockDim.x) {
         const int bm = (t / nt) << 2, bn = (t % nt) << 2;
-        double acc[4][4];
+        R acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+            for (int j = 0; j < 4; ++j) acc[i][j] = R(0);
         for (int k = 0; k < K; ++k) {
-            double a[4], b[4];
+            R a[4], b[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int m = bm + i;
-                a[i] = m < M ? (ta ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : 0.0;
+                a[i] = m < M ? (ta ? A[(long long)k * lda + m] : A[(long long)m * lda + k]) : R(0);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int n = bn + j;
-                b[j] = n < N ? (tb ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : 0.0;
+                b[j] = n < N ? (tb ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : R(0);
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -54,97 +55,99 @@ __device__ void blk_gemm(int M, int N, int K, const double *__restrict__ A, long
             for (int j = 0; j < 4; ++j) {
                 const int n = bn + j;
                 if (n >= N) continue;
-                double *c = C + (long long)m * ldc + n;
+                R *c = C + (long long)m * ldc + n;
                 *c = accumulate ? *c + alpha * acc[i][j] : alpha * acc[i][j];
             }
         }
     }
 }
 
-__device__ __forceinline__ double denom(const double *e, int a, int b, double fii, double fjj) {
-    return e[a] + e[b] - fii - fjj;
-}
+// Per-precision view of the operands of one residual evaluation.
+template <class R>
+struct View {
+    const R *e;      // pair pseudo-canonical energies (pair e_off)
+    const R *rhs;    // right-hand side: K~ by pair (rhs_by_slot = false) or a per-slot array
+    bool rhs_by_slot;
+    const R *S;      // coupling blocks
+    R *T, *Rr, *G1;  // per-slot amplitudes, residuals; per-CTA scratch
+};
 
-__global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
-    const int c = A.order[blockIdx.x];
-    const ClusterInfo C = A.clusters[c];
-    __shared__ double red[kThreads / 32];
-    double *G1 = A.G1 + (long long)blockIdx.x * A.gstride;
+// R~ = rhs + D o T~ - sum_terms f S~ T~' S~^T for every slot of cluster C (Eq. 4 projected on the
+// pseudo-canonical pair bases); returns max over slots of ||R~||_F.
+template <class R>
+__device__ double residual_eval(const SolveArgs &A, const ClusterInfo &C, const View<R> &v, double *red) {
     const int tid = threadIdx.x;
-    bool conv = false;
-    int it = 0;
-    for (;; ++it) {
-        // R~ = K~ + D o T~
-        for (int s = C.slot0; s < C.slot1; ++s) {
-            const Slot S = A.slots[s];
-            const PairInfo P = A.pairs[S.pair];
-            const int r = A.rdim[S.pair], np = P.np;
-            const double fii = A.focc[(long long)P.i * A.n_occ + P.i], fjj = A.focc[(long long)P.j * A.n_occ + P.j];
-            const double *e = A.e + P.e_off;
-            for (int idx = tid; idx < r * r; idx += kThreads) {
-                const int a = idx / r, b = idx % r;
-                const long long o = (long long)a * np + b;
-                A.R[S.t_off + o] = A.Kt[P.off + o] + denom(e, a, b, fii, fjj) * A.T[S.t_off + o];
-            }
+    for (int s = C.slot0; s < C.slot1; ++s) {
+        const Slot S = A.slots[s];
+        const PairInfo P = A.pairs[S.pair];
+        const int r = A.rdim[S.pair], np = P.np;
+        const R fii = (R)A.focc[(long long)P.i * A.n_occ + P.i], fjj = (R)A.focc[(long long)P.j * A.n_occ + P.j];
+        const R *e = v.e + P.e_off;
+        const R *rhs = v.rhs + (v.rhs_by_slot ? S.t_off : P.off);
+        for (int idx = tid; idx < r * r; idx += kThreads) {
+            const int a = idx / r, b = idx % r;
+            const long long o = (long long)a * np + b;
+            v.Rr[S.t_off + o] = rhs[o] + (e[a] + e[b] - fii - fjj) * v.T[S.t_off + o];
         }
+    }
+    __syncthreads();
+    for (int t = C.term0; t < C.term1; ++t) {
+        const Term T = A.terms[t];
+        const Slot Sd = A.slots[T.dst], Ss = A.slots[T.src];
+        const PairInfo Pd = A.pairs[Sd.pair], Ps = A.pairs[Ss.pair];
+        const int rp = A.rdim[Sd.pair], rq = A.rdim[Ss.pair];
+        const R f = (R)A.focc[(long long)T.fx * A.n_occ + T.fy];
+        const R *Sb = v.S + T.sblk;
+        // stored block is (smaller pair id) x (larger pair id)
+        const long long lds = T.s_trans ? Pd.np : Ps.np;
+        // G1 = S~_pq T~'_q   (rp x rq)
+        blk_gemm<R>(rp, rq, rq, Sb, lds, T.s_trans, v.T + Ss.t_off, Ps.np, T.t_trans, v.G1, Ps.np, R(1), false);
         __syncthreads();
-        // coupling terms
-        for (int t = C.term0; t < C.term1; ++t) {
-            const Term T = A.terms[t];
-            const Slot Sd = A.slots[T.dst], Ss = A.slots[T.src];
-            const PairInfo Pd = A.pairs[Sd.pair], Ps = A.pairs[Ss.pair];
-            const int rp = A.rdim[Sd.pair], rq = A.rdim[Ss.pair];
-            const double f = A.focc[(long long)T.fx * A.n_occ + T.fy];
-            const double *Sb = A.sblk + T.sblk;
-            // stored block is (smaller pair id) x (larger pair id)
-            const long long lds = T.s_trans ? Pd.np : Ps.np;
-            // G1 = S~_pq T~'_q   (rp x rq)
-            blk_gemm(rp, rq, rq, Sb, lds, T.s_trans, A.T + Ss.t_off, Ps.np, T.t_trans, G1, Ps.np, 1.0, false);
-            __syncthreads();
-            // R~_p -= f G1 S~_pq^T
-            blk_gemm(rp, rp, rq, G1, Ps.np, false, Sb, lds, !T.s_trans, A.R + Sd.t_off, Pd.np, -f, true);
-            __syncthreads();
-        }
-        // max over pairs of ||R~||_F
-        double rmax = 0.0;
-        for (int s = C.slot0; s < C.slot1; ++s) {
-            const Slot S = A.slots[s];
-            const PairInfo P = A.pairs[S.pair];
-            const int r = A.rdim[S.pair], np = P.np;
-            double ss = 0.0;
-            for (int idx = tid; idx < r * r; idx += kThreads) {
-                const double v = A.R[S.t_off + (long long)(idx / r) * np + idx % r];
-                ss += v * v;
-            }
-            rmax = fmax(rmax, sqrt(block_sum(ss, red)));
-        }
-        if (!(rmax > A.tol)) {   // converged (a NaN norm also stops here and is caught by energy())
-            conv = rmax <= A.tol;
-            break;
-        }
-        if (it >= A.max_iter) break;
-        for (int s = C.slot0; s < C.slot1; ++s) {
-            const Slot S = A.slots[s];
-            const PairInfo P = A.pairs[S.pair];
-            const int r = A.rdim[S.pair], np = P.np;
-            const double fii = A.focc[(long long)P.i * A.n_occ + P.i], fjj = A.focc[(long long)P.j * A.n_occ + P.j];
-            const double *e = A.e + P.e_off;
-            for (int idx = tid; idx < r * r; idx += kThreads) {
-                const int a = idx / r, b = idx % r;
-                const long long o = S.t_off + (long long)a * np + b;
-                A.T[o] -= A.R[o] / denom(e, a, b, fii, fjj);
-            }
-        }
+        // R~_p -= f G1 S~_pq^T
+        blk_gemm<R>(rp, rp, rq, v.G1, Ps.np, false, Sb, lds, !T.s_trans, v.Rr + Sd.t_off, Pd.np, -f, true);
         __syncthreads();
     }
-    // cluster Hylleraas energy: sum over ordered pairs of <K~ + R~, 2T~ - T~^T>
+    double rmax = 0.0;
+    for (int s = C.slot0; s < C.slot1; ++s) {
+        const Slot S = A.slots[s];
+        const int r = A.rdim[S.pair], np = A.pairs[S.pair].np;
+        double ss = 0.0;
+        for (int idx = tid; idx < r * r; idx += kThreads) {
+            const double x = (double)v.Rr[S.t_off + (long long)(idx / r) * np + idx % r];
+            ss += x * x;
+        }
+        rmax = fmax(rmax, sqrt(block_sum(ss, red)));
+    }
+    return rmax;
+}
+
+// Jacobi update T~ -= R~ / (e_a + e_b - f_ii - f_jj) on every slot of cluster C.
+template <class R>
+__device__ void jacobi_update(const SolveArgs &A, const ClusterInfo &C, const View<R> &v) {
+    for (int s = C.slot0; s < C.slot1; ++s) {
+        const Slot S = A.slots[s];
+        const PairInfo P = A.pairs[S.pair];
+        const int r = A.rdim[S.pair], np = P.np;
+        const R fii = (R)A.focc[(long long)P.i * A.n_occ + P.i], fjj = (R)A.focc[(long long)P.j * A.n_occ + P.j];
+        const R *e = v.e + P.e_off;
+        for (int idx = threadIdx.x; idx < r * r; idx += kThreads) {
+            const int a = idx / r, b = idx % r;
+            const long long o = S.t_off + (long long)a * np + b;
+            v.T[o] -= v.Rr[o] / (e[a] + e[b] - fii - fjj);
+        }
+    }
+    __syncthreads();
+}
+
+// Cluster Hylleraas energy: sum over ordered pairs of <K~ + R~, 2T~ - T~^T> (FP64).
+__device__ double hylleraas(const SolveArgs &A, const ClusterInfo &C, double *red) {
     double E = 0.0;
     for (int s = C.slot0; s < C.slot1; ++s) {
         const Slot S = A.slots[s];
         const PairInfo P = A.pairs[S.pair];
         const int r = A.rdim[S.pair], np = P.np;
         double acc = 0.0;
-        for (int idx = tid; idx < r * r; idx += kThreads) {
+        for (int idx = threadIdx.x; idx < r * r; idx += kThreads) {
             const int a = idx / r, b = idx % r;
             const long long o = (long long)a * np + b;
             const double tbar = 2.0 * A.T[S.t_off + o] - A.T[S.t_off + (long long)b * np + a];
@@ -152,9 +155,110 @@ __global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
         }
         E += S.mult * block_sum(acc, red);
     }
-    if (tid == 0) {
+    return E;
+}
+
+// Plain FP64 cluster solve: Jacobi iterations from T~ = 0 until max ||R~||_F <= tol.
+__global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
+    const int c = A.order[blockIdx.x];
+    const ClusterInfo C = A.clusters[c];
+    __shared__ double red[kThreads / 32];
+    View<double> v{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride};
+    bool conv = false;
+    int it = 0;
+    for (;; ++it) {
+        const double rmax = residual_eval<double>(A, C, v, red);
+        if (!(rmax > A.tol)) {   // converged (a NaN norm also stops here and is caught by energy())
+            conv = rmax <= A.tol;
+            break;
+        }
+        if (it >= A.max_iter) break;
+        jacobi_update<double>(A, C, v);
+    }
+    const double E = hylleraas(A, C, red);
+    if (threadIdx.x == 0) {
         A.E_cluster[c] = E;
         A.iters[c] = conv ? it : -1;
+        if (A.evals64) A.evals64[c] = it + 1;
+    }
+}
+
+// FP32 Jacobi solve of L(x) = -rhs from x = 0 until max ||R~||_F <= tol32 or the norm stops falling (by 10 %
+// per iteration: the FP32 floor); returns the number of updates.
+__device__ int solve32(const SolveArgs &A, const ClusterInfo &C, const View<float> &v, double tol32, int max_it,
+                       double *red) {
+    double prev = INFINITY;
+    int it = 0;
+    for (; it < max_it; ++it) {
+        const double r = residual_eval<float>(A, C, v, red);
+        if (!(r > tol32) || r > 0.9 * prev) break;
+        prev = r;
+        jacobi_update<float>(A, C, v);
+    }
+    return it;
+}
+
+// Mixed cluster solve: FP32 Jacobi to the FP32 floor, then FP64 iterative refinement (FP64 residual, FP32
+// correction solve with the FP64 residual as right-hand side, FP64 update) until max ||R~||_F <= tol in FP64.
+// The energy uses the last FP64 residual, so its error is second order in the amplitude error (Eq. 3).
+__global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
+    const int c = A.order[blockIdx.x];
+    const ClusterInfo C = A.clusters[c];
+    __shared__ double red[kThreads / 32];
+    View<float> v32{A.e32, A.Kt32, false, A.sblk32, A.T32, A.R32, A.G1_32 + (long long)blockIdx.x * A.gstride};
+    View<double> v64{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride};
+    const int tid = threadIdx.x;
+    auto zero32 = [&](float *x) {
+        for (int s = C.slot0; s < C.slot1; ++s) {
+            const Slot S = A.slots[s];
+            const long long nn = (long long)A.pairs[S.pair].np * A.pairs[S.pair].np;
+            for (long long i = tid; i < nn; i += kThreads) x[S.t_off + i] = 0.f;
+        }
+        __syncthreads();
+    };
+    zero32(A.T32);
+    int total = solve32(A, C, v32, fmax(A.tol, 1e-6), A.max_iter, red);
+    // T64 = T32
+    for (int s = C.slot0; s < C.slot1; ++s) {
+        const Slot S = A.slots[s];
+        const long long nn = (long long)A.pairs[S.pair].np * A.pairs[S.pair].np;
+        for (long long i = tid; i < nn; i += kThreads) A.T[S.t_off + i] = (double)A.T32[S.t_off + i];
+    }
+    __syncthreads();
+    bool conv = false;
+    int evals = 0;
+    View<float> vc{A.e32, A.H32, true, A.sblk32, A.T32, A.R32, v32.G1};
+    for (int round = 0; round < 8; ++round) {
+        const double r64 = residual_eval<double>(A, C, v64, red);
+        ++evals;
+        if (!(r64 > A.tol)) {
+            conv = r64 <= A.tol;
+            break;
+        }
+        if (round == 7 || total >= A.max_iter) break;
+        // correction: L(d) = -R64 in FP32 (rhs = R64), then T64 += d
+        for (int s = C.slot0; s < C.slot1; ++s) {
+            const Slot S = A.slots[s];
+            const long long nn = (long long)A.pairs[S.pair].np * A.pairs[S.pair].np;
+            for (long long i = tid; i < nn; i += kThreads) {
+                A.H32[S.t_off + i] = (float)A.R[S.t_off + i];
+                A.T32[S.t_off + i] = 0.f;
+            }
+        }
+        __syncthreads();
+        total += solve32(A, C, vc, fmax(1e-7 * r64, 0.1 * A.tol), A.max_iter, red);
+        for (int s = C.slot0; s < C.slot1; ++s) {
+            const Slot S = A.slots[s];
+            const long long nn = (long long)A.pairs[S.pair].np * A.pairs[S.pair].np;
+            for (long long i = tid; i < nn; i += kThreads) A.T[S.t_off + i] += (double)A.T32[S.t_off + i];
+        }
+        __syncthreads();
+    }
+    const double E = hylleraas(A, C, red);
+    if (tid == 0) {
+        A.E_cluster[c] = E;
+        A.iters[c] = conv ? total + evals - 1 : -1;
+        if (A.evals64) A.evals64[c] = evals;
     }
 }
 
@@ -207,10 +311,25 @@ __global__ void k_energy_final(const double *__restrict__ Ec, const ClusterInfo 
 
 }  // namespace
 
-cudaError_t launch_residual(const SolveArgs &a, int nclusters, cudaStream_t s) {
+cudaError_t launch_residual(const SolveArgs &a, int nclusters, bool mixed, cudaStream_t s) {
     if (nclusters <= 0) return cudaSuccess;
     count_launch();
-    k_residual<<<nclusters, kThreads, 0, s>>>(a);
+    if (mixed) k_residual_mixed<<<nclusters, kThreads, 0, s>>>(a);
+    else k_residual<<<nclusters, kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+}  // namespace
+
+cudaError_t launch_to_f32(const double *in, float *out, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    k_to_f32<<<(int)std::min<long long>((n + 255) / 256, 152LL * 8), 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
 }
 
