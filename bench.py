@@ -187,15 +187,7 @@ def run_gpu(args):
     launches = ctypes_launches(osvmbe) - l0
     stages = ctx.profile_read()
     ctx.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        f = torch.tensor([flops_step], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(f)
-        flops_all = float(f.item())
-    else:
-        flops_all = flops_step
+    ms, flops_all = reduce_over_ranks(ms, flops_step, world, "cuda")
     value = flops_all / (ms * 1e-3) / 1e12
 
     # ---- end to end through the C ABI with host buffers: h2d of B, F, eps; d2h of E, dB, dF
@@ -259,6 +251,20 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def reduce_over_ranks(ms, flops, world, device):
+    """Whole-job numbers of a weak-scaling step: the slowest rank's time and the sum of every rank's work (each
+    rank solves its own geometry; this timing reduction is the only collective)."""
+    if world <= 1:
+        return ms, flops
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    f = torch.tensor([flops], device=device, dtype=torch.float64)
+    dist.all_reduce(f)
+    return float(t.item()), float(f.item())
 
 
 def ctypes_launches(osvmbe):

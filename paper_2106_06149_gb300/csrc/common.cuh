@@ -19,6 +19,10 @@ inline void count_launch(long long n = 1) { g_launches.fetch_add(n, std::memory_
 // Error word written by bounded device loops (never a trap).
 enum DevErr : int { kDevOk = 0, kDevEighNoConv = 1, kDevNonFinite = 2, kDevTimeout = 3 };
 
+// Record a device error; the first one recorded since the word was cleared wins, so that a root cause (a
+// non-finite input) is not overwritten by what it causes downstream (an eigensolver that cannot converge).
+__device__ __forceinline__ void raise_err(int *err, int code) { atomicCAS(err, (int)kDevOk, code); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kThreads) k_ql(const EighDesc *__restrict__ de
             __syncthreads();
             if (state == 2) {
                 failed = true;
-                if (tid == 0 && blockIdx.y == 0) atomicExch(err, kDevEighNoConv);
+                if (tid == 0 && blockIdx.y == 0) raise_err(err, kDevEighNoConv);
             }
             if (state != 1) break;
         }

@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_bf16x4(const GemmDesc *__restric
         const int st = sl & 1;
         if (sl >= 2) {
             if (!bwait(&bar[st], (uint32_t)(((sl >> 1) - 1) & 1))) {
-                if (tid == 0) atomicExch(err, kDevTimeout);
+                if (tid == 0) raise_err(err, kDevTimeout);
                 s_fail = 1;
             }
         }
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_bf16x4(const GemmDesc *__restric
         if (last_of_chunk) {
             // every MMA of the chunk (tracked by this stage's commit) must finish before TMEM is read
             if (!bwait(&bar[st], (uint32_t)((issued[st] - 1) & 1))) {
-                if (tid == 0) atomicExch(err, kDevTimeout);
+                if (tid == 0) raise_err(err, kDevTimeout);
                 s_fail = 1;
             }
             __syncthreads();

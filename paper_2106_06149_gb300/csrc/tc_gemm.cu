@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gemm_tf32x3(const GemmDesc *__restri
         if (sl >= 2) {
             // the MMAs that read this stage two slabs ago must be done before it is overwritten
             if (!mbar_wait(&bar_stage[st], (uint32_t)(((sl >> 1) - 1) & 1), kWaitBudget)) {
-                if (tid == 0) atomicExch(err, kDevTimeout);
+                if (tid == 0) raise_err(err, kDevTimeout);
                 s_fail = 1;
             }
         }
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gemm_tf32x3(const GemmDesc *__restri
     if (ok && nslab > 0) {
         const int st = (nslab - 1) & 1;
         if (!mbar_wait(&bar_stage[st], (uint32_t)((issued[st] - 1) & 1), kWaitBudget)) {
-            if (tid == 0) atomicExch(err, kDevTimeout);
+            if (tid == 0) raise_err(err, kDevTimeout);
             ok = false;
         }
     }
