@@ -226,7 +226,7 @@ void AdjointPlan::release() {
     for (void *p : allocs) cudaFree(p);
     allocs.clear();
     for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2, &gb_z, &gb_db, &gb_dq,
-                         &gb_gt, &gb_rb}) {
+                         &gb_gt, &gb_rb, &gb_at}) {
         gemm_batch_free(*g);
         g->h.clear();
     }
@@ -438,9 +438,12 @@ cudaError_t AdjointPlan::plan(osv_ctx &c) {
         gb_gt.add(gemm(nv, nv, nm, A1 + (long long)k * nm * nv, nv, 1, c.Q + (long long)k * nm * nv, nv, 0, c.Zc + k * nv2, nv));
         gb_rb.add(gemm(nv, (int)c.a_of(k), nv, c.Zc + k * nv2, nv, 0, c.B64 + c.b_off(k), c.a_of(k), 0,
                        dB64 + c.b_off(k), c.a_of(k), 2.0, 1.0));
+        if (c.osv_mixed)
+            gb_at.add(gemm(nm, nv, nv, A1 + (long long)k * nm * nv, nv, 0, c.Tkk + k * nv2, nv, 0,
+                           c.refine.AT + (long long)k * nm * nv, nv));
     }
     for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2, &gb_z, &gb_db, &gb_dq,
-                         &gb_gt, &gb_rb})
+                         &gb_gt, &gb_rb, &gb_at})
         if ((e = gemm_batch_upload(*g)) != cudaSuccess) return e;
     if ((e = tc_batch_prepare(gb_z, tc_z)) != cudaSuccess || (e = tc_batch_prepare(gb_db, tc_db)) != cudaSuccess ||
         (e = tc_batch_prepare(gb_dq, tc_dq)) != cudaSuccess || (e = tc_batch_prepare(gb_gt, tc_gt)) != cudaSuccess ||
@@ -448,6 +451,11 @@ cudaError_t AdjointPlan::plan(osv_ctx &c) {
         (e = bf16x4_batch_prepare(gb_db, oz_db)) != cudaSuccess || (e = bf16x4_batch_prepare(gb_dq, oz_dq)) != cudaSuccess ||
         (e = bf16x4_batch_prepare(gb_gt, oz_gt)) != cudaSuccess || (e = bf16x4_batch_prepare(gb_rb, oz_rb)) != cudaSuccess)
         return e;
+    if (c.prm.precision == OSV_MIXED_BF16X4) {
+        long long need = 0;
+        for (const TcTiles *t : {&oz_z, &oz_db, &oz_dq, &oz_gt, &oz_rb}) need = std::max(need, t->scratch_bytes);
+        if ((e = c.oz_reserve((size_t)need)) != cudaSuccess) return e;
+    }
     planned = true;
     return cudaSuccess;
 }
@@ -461,7 +469,10 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
     }
     cudaStream_t s = c.stream;
     const int n = c.n_occ, nv = c.n_vir, nm = c.nmax;
-#define CK(x) if ((e = (x)) != cudaSuccess) return e
+#define CK(x) \
+    do { \
+        if ((e = (x)) != cudaSuccess) return e; \
+    } while (0)
     CK(cudaMemsetAsync(GS, 0, c.pair_mat * sizeof(double), s));
     CK(cudaMemsetAsync(GF, 0, c.pair_mat * sizeof(double), s));
     CK(cudaMemsetAsync(GSc, 0, c.coup_mat * sizeof(double), s));
@@ -512,12 +523,18 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
         CK(c.run_dense(gb_dq, tc_dq, oz_dq));
     }
     StageTimer trelax(c, "adj_osv_relax");
-    // P_perp dE/dQ -> tridiagonal basis -> (Tri - omega_mu)^{-1} -> P_perp -> back to the virtual basis
-    CK(osv_project_out(c.nosv, c.Q, dQ, n, nv, nm, s));
-    CK(osv_reflect(c.tri_osv.d, n, nv, nm, c.nosv, dQ, 1, s));
-    CK(osv_tri_shift_solve(c.tri_osv.d, n, nv, nm, c.nosv, dQ, A1, c.tri_work, s));
-    CK(osv_project_out(c.nosv, c.Ytri, A1, n, nv, nm, s));
-    CK(osv_reflect(c.tri_osv.d, n, nv, nm, c.nosv, A1, 0, s));
+    // A1 = (omega_mu - T)^{-1} P_perp dE/dQ on the discarded space.  FP64: P_perp -> tridiagonal basis ->
+    // (Tri - omega_mu)^{-1} -> P_perp -> back to the virtual basis.  Mixed: the same chain in FP32 as a
+    // preconditioner of FP64 residual corrections.
+    CK(osv_project_out<double>(c.nosv, c.Q, dQ, n, nv, nm, s));
+    if (c.osv_mixed) {
+        CK(osv_mixed_relax(c.refine, gb_at, n, nv, nm, c.Q, c.nosv, dQ, A1, s));
+    } else {
+        CK(osv_reflect<double>(c.tri_osv.d, n, nv, nm, c.nosv, dQ, 1, s));
+        CK(osv_tri_shift_solve<double>(c.tri_osv.d, n, nv, nm, c.nosv, dQ, A1, c.tri_work, nullptr, 0, s));
+        CK(osv_project_out<double>(c.nosv, c.Ytri, A1, n, nv, nm, s));
+        CK(osv_reflect<double>(c.tri_osv.d, n, nv, nm, c.nosv, A1, 0, s));
+    }
     CK(c.run_dense(gb_gt, tc_gt, oz_gt));
     {
         const int bx = (int)std::min<long long>(((long long)nv * nv + kThreads - 1) / kThreads, 64);

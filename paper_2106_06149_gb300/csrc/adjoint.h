@@ -26,6 +26,7 @@ struct AdjointPlan {
         BlockCopy *d = nullptr;
     } bc_hs;
     GemmBatch gb_kc1, gb_kc2, gb_f1, gb_f2, gb_k1, gb_k2, gb_c1, gb_c2, gb_z, gb_db, gb_dq, gb_gt, gb_rb;
+    GemmBatch gb_at;                            // mixed relaxation: A1 T (FP64 residual of the resolvent solve)
     TcTiles tc_z, tc_db, tc_dq, tc_gt, tc_rb;   // tensor-core tilings, TF32x3
     TcTiles oz_z, oz_db, oz_dq, oz_gt, oz_rb;   // tensor-core tilings, exact BF16x4
 

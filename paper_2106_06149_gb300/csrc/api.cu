@@ -371,12 +371,8 @@ osv_status build_plan(osv_ctx *c) {
 #define ALLOC(ptr, cnt) \
     if ((e = c->dalloc(ptr, (size_t)(cnt))) != cudaSuccess) return c->cuda_fail(e, "cudaMalloc " #ptr)
     ALLOC(c->Tkk, n * nv2);
-    ALLOC(c->Awork, n * nv2);
     ALLOC(c->Zc, n * nv2);
     ALLOC(c->omega, (long long)n * nv);
-    ALLOC(c->dsc, (long long)n * nv);
-    ALLOC(c->esc, (long long)n * nv);
-    ALLOC(c->tausc, (long long)n * nv);
     ALLOC(c->nosv, n);
     ALLOC(c->derr, 1);
     ALLOC(c->Q, (long long)n * nm * nv);
@@ -435,20 +431,79 @@ osv_status build_plan(osv_ctx *c) {
         c->gb_gram.add(gemm(nv, nv, (int)a, c->B64 + c->b_off(k), a, 0, c->B64 + c->b_off(k), a, 1,
                             c->Tkk + k * nv2, nv));
     }
-    // --- a2: OSV eigenproblems (tridiagonal route: bisection + inverse iteration of the kept vectors)
-    ALLOC(c->Ytri, (long long)n * nm * nv);
-    ALLOC(c->tri_work, 4LL * n * nm * nv);
+    // --- a2: OSV eigenproblems.  FP64: tridiagonal route (multisection + inverse iteration of the kept vectors).
+    // Mixed: the same route in FP32, then FP64 Rayleigh-Ritz refinement of the n_max leading eigenpairs.
     c->tri_osv.h.clear();
-    for (int k = 0; k < n; ++k) {
-        TriDesc D{};
-        D.A = c->Awork + k * nv2;
-        D.lda = nv;
-        D.n = nv;
-        D.d = c->dsc + (long long)k * nv;
-        D.e = c->esc + (long long)k * nv;
-        D.tau = c->tausc + (long long)k * nv;
-        D.w = c->omega + (long long)k * nv;
-        c->tri_osv.h.push_back(D);
+    if (!c->osv_mixed) {
+        ALLOC(c->Awork, n * nv2);
+        ALLOC(c->dsc, (long long)n * nv);
+        ALLOC(c->esc, (long long)n * nv);
+        ALLOC(c->tausc, (long long)n * nv);
+        ALLOC(c->Ytri, (long long)n * nm * nv);
+        ALLOC(c->tri_work, 4LL * n * nm * nv);
+        for (int k = 0; k < n; ++k) {
+            TriDesc D{};
+            D.A = c->Awork + k * nv2;
+            D.lda = nv;
+            D.n = nv;
+            D.d = c->dsc + (long long)k * nv;
+            D.e = c->esc + (long long)k * nv;
+            D.tau = c->tausc + (long long)k * nv;
+            D.w = c->omega + (long long)k * nv;
+            c->tri_osv.h.push_back(D);
+        }
+    } else {
+        OsvRefine &r = c->refine;
+        const long long blk = (long long)n * nm * nv;
+        ALLOC(r.A32, n * nv2);
+        ALLOC(r.d32, (long long)n * nv);
+        ALLOC(r.e32, (long long)n * nv);
+        ALLOC(r.tau32, (long long)n * nv);
+        ALLOC(r.w32, (long long)n * nv);
+        ALLOC(r.Y32, blk);
+        ALLOC(r.work32, 4 * blk);
+        ALLOC(r.X32, blk);
+        ALLOC(r.Z32, blk);
+        ALLOC(r.QW[0], 2 * blk);
+        ALLOC(r.QW[1], 2 * blk);
+        ALLOC(r.GH, 2LL * n * nm * nm);
+        ALLOC(r.Ct, (long long)n * nm * nm);
+        ALLOC(r.lam, (long long)n * nm);
+        ALLOC(r.AT, blk);
+        ALLOC(r.RS, blk);
+        ALLOC(r.nm_all, n);
+        std::vector<int> all(n, nm);
+        if ((e = cudaMemcpy(r.nm_all, all.data(), n * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return c->cuda_fail(e, "upload n_max");
+        r.tri_h.clear();
+        for (int k = 0; k < n; ++k) {
+            TriDesc32 D{};
+            D.A = r.A32 + k * nv2;
+            D.lda = nv;
+            D.n = nv;
+            D.d = r.d32 + (long long)k * nv;
+            D.e = r.e32 + (long long)k * nv;
+            D.tau = r.tau32 + (long long)k * nv;
+            D.w = r.w32 + (long long)k * nv;
+            r.tri_h.push_back(D);
+        }
+        ALLOC(r.tri_d, n);
+        if ((e = cudaMemcpy(r.tri_d, r.tri_h.data(), n * sizeof(TriDesc32), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return c->cuda_fail(e, "upload tri32");
+        const long long per = (long long)nm * nv;
+        for (int x = 0; x < 2; ++x) {
+            const int y = x ^ 1;
+            for (int k = 0; k < n; ++k) {
+                double *qx = r.QW[x] + 2 * per * k, *qy = r.QW[y] + 2 * per * k;
+                const double *ct = r.Ct + (long long)k * nm * nm;
+                // W = Q T;  [G; H] = [Q; W] Q^T;  [Q; W] <- Ct [Q; W];  final Q = Ct Q
+                r.gb_w[x].add(gemm(nm, nv, nv, qx, nv, 0, c->Tkk + k * nv2, nv, 0, qx + per, nv));
+                r.gb_gh[x].add(gemm(2 * nm, nm, nv, qx, nv, 0, qx, nv, 1, r.GH + 2LL * k * nm * nm, nm));
+                r.gb_rot[x].add(gemm(nm, nv, nm, ct, nm, 0, qx, nv, 0, qy, nv));
+                r.gb_rot[x].add(gemm(nm, nv, nm, ct, nm, 0, qx + per, nv, 0, qy + per, nv));
+                r.gb_fin[x].add(gemm(nm, nv, nm, ct, nm, 0, qx, nv, 0, c->Q + per * k, nv));
+            }
+        }
     }
     // --- a3: LMO-pair blocks s_ij = Q_i Q_j^T, phi_ij = Q_i diag(eps) Q_j^T (rows = OSVs)
     for (size_t p = 0; p < c->pairs.size(); ++p) {
@@ -602,16 +657,24 @@ osv_status build_plan(osv_ctx *c) {
     if ((e = c->upload(c->comb_w)) != cudaSuccess) return c->cuda_fail(e, "upload comb");
     if ((e = c->upload(c->bc_pair)) != cudaSuccess) return c->cuda_fail(e, "upload bc");
     if ((e = c->upload(c->bc_coup)) != cudaSuccess) return c->cuda_fail(e, "upload bc");
-    if ((e = c->upload(c->tri_osv)) != cudaSuccess) return c->cuda_fail(e, "upload tri");
+    if (!c->osv_mixed && (e = c->upload(c->tri_osv)) != cudaSuccess) return c->cuda_fail(e, "upload tri");
     if ((e = c->upload(c->eig_s)) != cudaSuccess) return c->cuda_fail(e, "upload eig");
     if ((e = c->upload(c->eig_f)) != cudaSuccess) return c->cuda_fail(e, "upload eig");
     for (GemmBatch *g : {&c->gb_gram, &c->gb_sf, &c->gb_w, &c->gb_k, &c->gb_fx1, &c->gb_fx2, &c->gb_v, &c->gb_kt1,
                          &c->gb_kt2, &c->gb_c1, &c->gb_c2})
         if ((e = gemm_batch_upload(*g)) != cudaSuccess) return c->cuda_fail(e, "upload gemm batch");
+    if (c->osv_mixed)
+        for (int x = 0; x < 2; ++x)
+            for (GemmBatch *g : {&c->refine.gb_w[x], &c->refine.gb_gh[x], &c->refine.gb_rot[x], &c->refine.gb_fin[x]})
+                if ((e = gemm_batch_upload(*g)) != cudaSuccess) return c->cuda_fail(e, "upload refine batch");
     if ((e = tc_batch_prepare(c->gb_gram, c->tc_gram)) != cudaSuccess || (e = tc_batch_prepare(c->gb_w, c->tc_w)) != cudaSuccess ||
         (e = tc_batch_prepare(c->gb_k, c->tc_k)) != cudaSuccess || (e = bf16x4_batch_prepare(c->gb_gram, c->oz_gram)) != cudaSuccess ||
         (e = bf16x4_batch_prepare(c->gb_w, c->oz_w)) != cudaSuccess || (e = bf16x4_batch_prepare(c->gb_k, c->oz_k)) != cudaSuccess)
         return c->cuda_fail(e, "tensor-core tiling");
+    if (c->prm.precision == OSV_MIXED_BF16X4 &&
+        (e = c->oz_reserve((size_t)std::max({c->oz_gram.scratch_bytes, c->oz_w.scratch_bytes, c->oz_k.scratch_bytes}))) !=
+            cudaSuccess)
+        return c->cuda_fail(e, "slice scratch");
     return OSV_OK;
 }
 
@@ -620,7 +683,9 @@ osv_status run_osv_build(osv_ctx *c) {
     cudaStream_t s = c->stream;
     const int n = c->n_occ, nv = c->n_vir, nm = c->nmax;
 #define CK(x, what) \
-    if ((e = (x)) != cudaSuccess) return c->cuda_fail(e, what)
+    do { \
+        if ((e = (x)) != cudaSuccess) return c->cuda_fail(e, what); \
+    } while (0)
     CK(cudaMemsetAsync(c->derr, 0, sizeof(int), s), "memset");
     if (c->B_dtype == 1) {
         StageTimer t(*c, "b_to_fp64");
@@ -629,17 +694,27 @@ osv_status run_osv_build(osv_ctx *c) {
     {
         StageTimer t(*c, "tkk_gram");
         CK(c->run_dense(c->gb_gram, c->tc_gram, c->oz_gram), "gram");
-        CK(launch_tkk_scale(c->Tkk, c->Awork, c->eps, c->focc, n, nv, c->derr, s), "tkk");
+        if (c->osv_mixed) {
+            CK(launch_tkk_scale<float>(c->Tkk, c->refine.A32, c->eps, c->focc, n, nv, c->derr, s), "tkk");
+        } else {
+            CK(launch_tkk_scale<double>(c->Tkk, c->Awork, c->eps, c->focc, n, nv, c->derr, s), "tkk");
+        }
     }
     {
         StageTimer t(*c, "osv_eigh");
-        CK(osv_tridiag(c->tri_osv.d, n, nv, s), "osv tridiag");
-        CK(osv_tri_eigvals(c->tri_osv.d, n, nv, s), "osv eigenvalues");
-        CK(launch_osv_count(c->omega, c->nosv, n, nv, nm, c->prm.l_osv, c->prm.n_osv_fixed, s), "osv count");
-        CK(cudaMemsetAsync(c->Ytri, 0, (size_t)n * nm * nv * sizeof(double), s), "memset Y");
-        CK(osv_tri_kept_vectors(c->tri_osv.d, n, nv, nm, c->nosv, c->Ytri, c->tri_work, s), "osv vectors");
-        CK(cudaMemcpyAsync(c->Q, c->Ytri, (size_t)n * nm * nv * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy Q");
-        CK(osv_reflect(c->tri_osv.d, n, nv, nm, c->nosv, c->Q, 0, s), "osv back-transform");
+        if (c->osv_mixed) {
+            CK(osv_mixed_eigh(c->refine, n, nv, nm, c->Q, c->omega, c->nosv, c->prm.l_osv, c->prm.n_osv_fixed,
+                              c->derr, s), "osv refine");
+        } else {
+            CK(osv_tridiag<double>(c->tri_osv.d, n, nv, s), "osv tridiag");
+            CK(osv_tri_eigvals<double>(c->tri_osv.d, n, nv, nm, s), "osv eigenvalues");
+            CK(launch_osv_count(c->omega, nv, c->nosv, n, nm, c->prm.l_osv, c->prm.n_osv_fixed, s), "osv count");
+            CK(cudaMemsetAsync(c->Ytri, 0, (size_t)n * nm * nv * sizeof(double), s), "memset Y");
+            CK(osv_tri_kept_vectors<double>(c->tri_osv.d, n, nv, nm, c->nosv, c->Ytri, c->tri_work, s), "osv vectors");
+            CK(cudaMemcpyAsync(c->Q, c->Ytri, (size_t)n * nm * nv * sizeof(double), cudaMemcpyDeviceToDevice, s),
+               "copy Q");
+            CK(osv_reflect<double>(c->tri_osv.d, n, nv, nm, c->nosv, c->Q, 0, s), "osv back-transform");
+        }
         CK(launch_scale_cols(c->Q, c->eps, c->Qe, (long long)n * nm, nv, s), "Qe");
     }
     {
@@ -656,20 +731,21 @@ osv_status run_osv_build(osv_ctx *c) {
     }
     {
         StageTimer t(*c, "pair_basis");
+        // pair eigenproblems: FP32 Jacobi + FP64 polish in the mixed modes, FP64 Jacobi otherwise (large
+        // orders: Householder + QL)
+        const bool pmix = c->prm.precision != OSV_FP64 && 2 * nm <= kJacobiMixedMax;
+        auto pair_eigh = [&](const HostDev<EighDesc> &d) -> cudaError_t {
+            const int np_ = (int)c->pairs.size();
+            if (pmix) return eigh_small_jacobi_mixed(d.d, np_, 2 * nm, c->derr, s);
+            if (2 * nm <= kJacobiMax) return eigh_small_jacobi(d.d, np_, 2 * nm, c->derr, s);
+            return eigh_batched(d.d, np_, 2 * nm, 1, c->derr, s);
+        };
         CK(launch_block_copy(c->bc_pair.d, (int)c->bc_pair.h.size(), s), "pair assemble");
-        if (2 * nm <= kJacobiMax) {
-            CK(eigh_small_jacobi(c->eig_s.d, (int)c->pairs.size(), 2 * nm, c->derr, s), "pair overlap eigh");
-        } else {
-            CK(eigh_batched(c->eig_s.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair overlap eigh");
-        }
+        CK(pair_eigh(c->eig_s), "pair overlap eigh");
         CK(launch_pair_x(c->pinfo.d, (int)c->pairs.size(), c->Sp, c->sw, c->X, c->rdim, c->prm.tau_red, s), "pair x");
         CK(gemm_batch_run(c->gb_fx1, s), "fx1");
         CK(gemm_batch_run(c->gb_fx2, s), "fx2");
-        if (2 * nm <= kJacobiMax) {
-            CK(eigh_small_jacobi(c->eig_f.d, (int)c->pairs.size(), 2 * nm, c->derr, s), "pair fock eigh");
-        } else {
-            CK(eigh_batched(c->eig_f.d, (int)c->pairs.size(), 2 * nm, 1, c->derr, s), "pair fock eigh");
-        }
+        CK(pair_eigh(c->eig_f), "pair fock eigh");
         CK(launch_clean_w(c->pinfo.d, (int)c->pairs.size(), c->rdim, c->Fx, c->pe, s), "clean");
         CK(gemm_batch_run(c->gb_v, s), "V");
     }
@@ -718,7 +794,9 @@ osv_status osv_build(osv_ctx *c, const osv_problem *pb, const osv_params *prm, i
     if (!pb->f_occ || !pb->eps_vir || !pb->B) return c->fail(OSV_ERR_INVALID, "device arrays are NULL");
     cudaSetDevice(c->device);
     const int nmax = prm->n_osv_fixed > 0 ? std::min(prm->n_osv_fixed, pb->n_vir) : std::min(prm->n_osv_max, pb->n_vir);
-    const bool replan = !c->built || nmax != c->nmax || pb->B_dtype != c->B_dtype || pb->B != c->B_in;
+    const bool mixed = prm->precision != OSV_FP64 && nmax <= kRefineMaxN;
+    const bool replan = !c->built || nmax != c->nmax || pb->B_dtype != c->B_dtype || pb->B != c->B_in ||
+                        mixed != c->osv_mixed;
     c->prm = *prm;
     c->focc = pb->f_occ;
     c->eps = pb->eps_vir;
@@ -726,6 +804,7 @@ osv_status osv_build(osv_ctx *c, const osv_problem *pb, const osv_params *prm, i
         if (c->stream) cudaStreamSynchronize(c->stream);
         c->release();
         c->nmax = nmax;
+        c->osv_mixed = mixed;
         c->B_in = pb->B;
         c->B_dtype = pb->B_dtype;
         plan_clusters(c);
@@ -780,6 +859,7 @@ osv_status cluster_residual_solve(osv_ctx *c, int *n_iter_out, int32_t *cluster_
     a.H32 = c->H32;
     a.G1_32 = c->G1_32;
     a.evals64 = c->evals64;
+    a.np_max = 2 * c->nmax;
     if ((e = cudaMemsetAsync(c->Tslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
         return c->cuda_fail(e, "memset T");
     if ((e = cudaMemsetAsync(c->Rslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
@@ -877,11 +957,29 @@ osv_status osv_eigenvalues(osv_ctx *c, int k, double *w_out) {
     if (!c || !w_out) return OSV_ERR_INVALID;
     if (!c->built || k < 0 || k >= c->n_occ) return c->fail(OSV_ERR_INVALID, "bad LMO index or not built");
     cudaSetDevice(c->device);
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return c->cuda_fail(e, "sync");
-    if ((e = cudaMemcpy(w_out, c->omega + (long long)k * c->n_vir, c->n_vir * sizeof(double),
-                        cudaMemcpyDeviceToHost)) != cudaSuccess)
+    // the build computes only the n_max leading eigenvalues: the full spectrum is formed here, on demand
+    const int nv = c->n_vir, nm = c->nmax;
+    cudaError_t e;
+    if (!c->osv_mixed) {
+        if ((e = osv_tri_eigvals<double>(c->tri_osv.d, c->n_occ, nv, nv, c->stream)) != cudaSuccess)
+            return c->cuda_fail(e, "eigenvalues");
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "sync");
+        if ((e = cudaMemcpy(w_out, c->omega + (long long)k * nv, nv * sizeof(double), cudaMemcpyDeviceToHost)) !=
+            cudaSuccess)
+            return c->cuda_fail(e, "copy");
+        return OSV_OK;
+    }
+    // mixed: the leading n_max refined in FP64, the rest from the FP32 tridiagonal
+    if ((e = osv_tri_eigvals<float>(c->refine.tri_d, c->n_occ, nv, nv, c->stream)) != cudaSuccess)
+        return c->cuda_fail(e, "eigenvalues");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "sync");
+    std::vector<float> w32(nv);
+    if ((e = cudaMemcpy(w32.data(), c->refine.w32 + (long long)k * nv, nv * sizeof(float), cudaMemcpyDeviceToHost)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(w_out, c->refine.lam + (long long)k * nm, nm * sizeof(double), cudaMemcpyDeviceToHost)) !=
+            cudaSuccess)
         return c->cuda_fail(e, "copy");
+    for (int i = nm; i < nv; ++i) w_out[i] = w32[i];
     return OSV_OK;
 }
 

@@ -8,6 +8,7 @@
 #include "../../include/osvmbe.h"
 #include "adjoint.h"
 #include "osv_eig.h"
+#include "osv_refine.h"
 #include "tc_gemm.h"
 
 namespace osv {
@@ -94,8 +95,10 @@ struct osv_ctx {
     std::vector<long long> coup_off;       // per coupling offset (doubles) of its n_pa x n_pb blocks
     HostDev<BlockCopy> bc_pair, bc_coup;
     HostDev<EighDesc> eig_s, eig_f;
-    HostDev<osv::TriDesc> tri_osv;         // OSV eigenproblems (tridiagonal route)
+    HostDev<osv::TriDesc> tri_osv;         // OSV eigenproblems (FP64 tridiagonal route)
     double *Ytri = nullptr, *tri_work = nullptr;
+    bool osv_mixed = false;                // mixed precisions: FP32 tridiagonal route + FP64 refinement
+    osv::OsvRefine refine;
     HostDev<int> rows_w;                   // a_rows maps for the half transforms
     HostDev<int> kidx;                     // common-fitting-domain position lists
     GemmBatch gb_gram, gb_sf, gb_w, gb_k, gb_fx1, gb_fx2, gb_v, gb_kt1, gb_kt2, gb_c1, gb_c2;
@@ -139,8 +142,23 @@ struct osv_ctx {
     // tcgen05 tensor cores
     cudaError_t run_dense(const GemmBatch &b, const osv::TcTiles &t, const osv::TcTiles &oz) {
         if (prm.precision == OSV_MIXED_TF32X3) return osv::tc_batch_run(b, t, derr, stream);
-        if (prm.precision == OSV_MIXED_BF16X4) return osv::bf16x4_batch_run(oz, derr, stream);
+        if (prm.precision == OSV_MIXED_BF16X4) return osv::bf16x4_batch_run(oz, oz_scratch, derr, stream);
         return osv::gemm_batch_run(b, stream);
+    }
+    // slice images of the exact-slice GEMM batches (one buffer, grown to the largest batch)
+    unsigned char *oz_scratch = nullptr;
+    size_t oz_cap = 0;
+    cudaError_t oz_reserve(size_t bytes) {
+        if (bytes <= oz_cap) return cudaSuccess;
+        if (oz_scratch) {
+            if (stream) cudaStreamSynchronize(stream);
+            cudaFree(oz_scratch);
+            oz_scratch = nullptr;
+            oz_cap = 0;
+        }
+        cudaError_t e = cudaMalloc(&oz_scratch, bytes);
+        if (e == cudaSuccess) oz_cap = bytes;
+        return e;
     }
     template <class T>
     cudaError_t upload(HostDev<T> &hd) {
@@ -155,6 +173,15 @@ struct osv_ctx {
             gemm_batch_free(*g);
             g->h.clear();
         }
+        for (int x = 0; x < 2; ++x)
+            for (GemmBatch *g : {&refine.gb_w[x], &refine.gb_gh[x], &refine.gb_rot[x], &refine.gb_fin[x]}) {
+                gemm_batch_free(*g);
+                g->h.clear();
+            }
+        refine = osv::OsvRefine{};
+        if (oz_scratch) cudaFree(oz_scratch);
+        oz_scratch = nullptr;
+        oz_cap = 0;
         for (osv::TcTiles *t : {&tc_gram, &tc_w, &tc_k, &oz_gram, &oz_w, &oz_k}) osv::tc_tiles_free(*t);
         adj.release();
         built = solved = false;

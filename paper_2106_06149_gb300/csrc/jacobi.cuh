@@ -1,0 +1,100 @@
+// Cyclic parallel Jacobi sweeps on a small symmetric matrix held in shared memory (a device function shared by
+// the batched small eigensolver, the Rayleigh-Ritz step of the OSV refinement and the mixed pair bases).
+#pragma once
+#include "common.cuh"
+
+namespace osv {
+
+// Round-robin pairing: every round rotates ne/2 disjoint planes (p, q) at once, ne - 1 rounds per sweep.
+// A: ne x ne symmetric (leading dimension ld, ne even; padding rows/columns must be zero), rotated in place;
+// V <- V J accumulates the rotations (start from the identity, or from a basis to be updated).  Sweeps stop
+// when the off-diagonal sum of squares is <= tol2 * the Frobenius sum of squares of A at entry, or after
+// max_sweeps.  Scratch: cs, sn (ne/2 of R), pp, qq (ne/2 ints), red (blockDim/32 doubles), flag (one int).
+// Returns whether the tolerance was met.  Every thread of the block must call it.
+template <class R>
+__device__ bool jacobi_sweeps(R *A, R *V, int ne, int ld, R *cs, R *sn, int *pp, int *qq, double *red, int *flag,
+                              int max_sweeps, double tol2) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const R tiny = sizeof(R) == 8 ? (R)1e-300 : (R)1e-37;
+    double fro = 0.0;
+    for (int idx = tid; idx < ne * ne; idx += nt) {
+        const double a = A[(idx / ne) * ld + idx % ne];
+        fro += a * a;
+    }
+    fro = block_sum(fro, red);
+    const int half = ne / 2;
+    bool conv = false;
+    for (int sweep = 0;; ++sweep) {
+        double off = 0.0;
+        for (int idx = tid; idx < ne * ne; idx += nt) {
+            const int r = idx / ne, c = idx % ne;
+            if (r != c) off += (double)A[r * ld + c] * (double)A[r * ld + c];
+        }
+        off = block_sum(off, red);
+        if (tid == 0) *flag = off <= tol2 * fro || off == 0.0;
+        __syncthreads();
+        conv = *flag;
+        __syncthreads();
+        if (conv || sweep == max_sweeps) break;
+        for (int round = 0; round < ne - 1; ++round) {
+            for (int t = tid; t < half; t += nt) {
+                int a = t == 0 ? 0 : 1 + (t - 1 + round) % (ne - 1);
+                int bb = 1 + (ne - 2 - t + round) % (ne - 1);
+                if (t == 0) bb = 1 + (ne - 2 + round) % (ne - 1);
+                const int p = min(a, bb), q = max(a, bb);
+                pp[t] = p;
+                qq[t] = q;
+                const R apq = A[p * ld + q];
+                R c = 1, s = 0;
+                if (apq != (R)0 && fabs(apq) > tiny) {
+                    const R th = (A[q * ld + q] - A[p * ld + p]) / (2 * apq);
+                    const R tt = (th >= (R)0 ? (R)1 : (R)-1) / (fabs(th) + sqrt(th * th + (R)1));
+                    c = rsqrt(tt * tt + (R)1);
+                    s = tt * c;
+                }
+                cs[t] = c;
+                sn[t] = s;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < half * ne; idx += nt) {   // rows: B = J^T A
+                const int t = idx / ne, k = idx % ne;
+                const int p = pp[t], q = qq[t];
+                const R c = cs[t], s = sn[t];
+                const R ap = A[p * ld + k], aq = A[q * ld + k];
+                A[p * ld + k] = c * ap - s * aq;
+                A[q * ld + k] = s * ap + c * aq;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < half * ne; idx += nt) {   // columns: A' = B J, V' = V J
+                const int t = idx / ne, k = idx % ne;
+                const int p = pp[t], q = qq[t];
+                const R c = cs[t], s = sn[t];
+                const R ap = A[k * ld + p], aq = A[k * ld + q];
+                A[k * ld + p] = c * ap - s * aq;
+                A[k * ld + q] = s * ap + c * aq;
+                const R vp = V[k * ld + p], vq = V[k * ld + q];
+                V[k * ld + p] = c * vp - s * vq;
+                V[k * ld + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+        }
+    }
+    return conv;
+}
+
+// rank[i] = position of diagonal entry i in decreasing order (ties by index), for i < n.
+template <class R>
+__device__ void diag_rank(const R *A, int n, int ld, int *rank) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const R di = A[i * ld + i];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) {
+            const R dj = A[j * ld + j];
+            rk += (dj > di) || (dj == di && j < i);
+        }
+        rank[i] = rk;
+    }
+    __syncthreads();
+}
+
+}  // namespace osv

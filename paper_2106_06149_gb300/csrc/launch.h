@@ -7,11 +7,11 @@
 namespace osv {
 
 cudaError_t launch_f32_to_f64(const float *in, double *out, long long n, cudaStream_t s);
-cudaError_t launch_tkk_scale(double *T, double *work, const double *eps, const double *focc, int n_occ, int nv,
-                             int *err, cudaStream_t s);
-cudaError_t launch_osv_select(const double *Zt, const double *omega, const double *eps, double *Q, double *Qe,
-                              int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed, cudaStream_t s);
-cudaError_t launch_osv_count(const double *omega, int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed,
+// T_kk (FP64, in place over the Gram products) and a working copy in W (double or float) for the eigensolver
+template <class W>
+cudaError_t launch_tkk_scale(double *T, W *work, const double *eps, const double *focc, int n_occ, int nv, int *err,
+                             cudaStream_t s);
+cudaError_t launch_osv_count(const double *omega, int ld, int *nosv, int n_occ, int nmax, double l_osv, int n_fixed,
                              cudaStream_t s);
 cudaError_t launch_scale_cols(const double *Q, const double *eps, double *Qe, long long rows, int nv, cudaStream_t s);
 cudaError_t launch_block_copy(const BlockCopy *d_bc, int n, cudaStream_t s);

@@ -2,17 +2,25 @@
 //
 // Only the n_k kept eigenvectors of T_kk enter the energy, and the OSV relaxation of Eq. 8 needs the discarded
 // eigenvectors only through the restricted resolvent sum_nu q'_nu q'_nu^T / (omega_mu - omega'_nu).  So:
-//   1. Householder tridiagonalisation T = H Tri H^T (one CTA per LMO; reflector k kept contiguous in row k);
-//   2. every eigenvalue of Tri by bisection on the Sturm count, one thread per eigenvalue (parallel, no long
-//      dependent chain: on GB300 a dependent FP64 operation costs ~64 cycles and a division ~430);
+//   1. Householder tridiagonalisation T = H Tri H^T (one CTA per LMO; reflector k kept contiguous in row k).
+//      One pass over the trailing matrix per step: the rank-2 update of step k-1 is applied lazily in the same
+//      pass that forms the product A v_k of step k (warp per row, coalesced, division free);
+//   2. the n_max largest eigenvalues of Tri by 32-point multisection of the Sturm count (one warp per
+//      eigenvalue, FP64 arithmetic): ~11 rounds instead of ~60 bisection steps, each a chain of n dependent
+//      multiply-adds (on GB300 a dependent FP64 operation costs ~64 cycles and a division ~430);
 //   3. the kept eigenvectors by inverse iteration on Tri, one thread per vector, then two classical Gram-Schmidt
 //      passes (CGS2) inside the kept set;
 //   4. back-transformation q = H y through the stored reflectors (warp per vector);
 //   5. (adjoint) x_mu = P_perp (omega_mu - Tri)^{-1} P_perp r_mu by a pivoted tridiagonal solve and a CGS2
 //      projection, which is exactly the kept x discarded block of the perturbed eigenproblem (Eq. 8).
+// Every step is templated on the working precision R: double for the FP64 path, float for the first stage of
+// the mixed path (refined to FP64 accuracy afterwards).
 // Pair overlap / pseudo-canonical eigenproblems (order <= 2 nmax) use a cyclic parallel Jacobi in shared memory.
+#include <algorithm>
 #include <cfloat>
+#include <cstdint>
 
+#include "jacobi.cuh"
 #include "kernels.cuh"
 #include "osv_eig.h"
 
@@ -21,95 +29,161 @@ namespace osv {
 namespace {
 
 constexpr int kT = 256;
+constexpr int kTT = 512;   // tridiagonalisation block
+
+template <class R>
+struct Lim;
+template <>
+struct Lim<double> {
+    static constexpr double eps = DBL_EPSILON;
+    static constexpr double tiny = 1e-300;
+};
+template <>
+struct Lim<float> {
+    static constexpr float eps = FLT_EPSILON;
+    static constexpr float tiny = 1e-37f;
+};
+
+template <class R>
+__device__ __forceinline__ R warp_sum_t(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // ---------------------------------------------------------------------- 1. Householder tridiagonalisation
-// A (n x n, lda) overwritten; d, e (n), tau (n); reflector k stored in row k, columns k+1 .. n-1.
-__global__ void __launch_bounds__(kT) k_tridiag_osv(const TriDesc *__restrict__ descs) {
-    const TriDesc D = descs[blockIdx.x];
+// A (n x n, lda, both triangles stored) overwritten; d, e (n), tau (n); reflector k stored in row k, columns
+// k+1 .. n-1 (H_k = I - tau_k v v^T).  Step k: (a) warp 0 applies the pending update of step k-1 to row k and
+// forms v_k from it; (b) one pass over rows r > k applies the pending update and accumulates p = tau A v_k;
+// (c) p -= (tau/2)(p.v) v; (v_k, p) become the pending update A <- A - v p^T - p v^T.  Below-diagonal column k
+// is not updated (it is never read again).
+template <class R>
+__global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__ descs) {
+    const TriDescT<R> D = descs[blockIdx.x];
     const int n = D.n;
-    extern __shared__ double sh[];
-    double *v = sh, *p = sh + n;
-    __shared__ double red[kT / 32];
-    __shared__ double s_beta;
-    const int tid = threadIdx.x;
-    double *A = D.A;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *v = reinterpret_cast<R *>(smem_raw), *p = v + n, *vo = p + n, *po = vo + n;   // global indices
+    __shared__ double part[kTT / 32];
+    __shared__ R s_beta;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int NW = kTT / 32;
+    R *A = D.A;
     const long long lda = D.lda;
+    for (int i = tid; i < n; i += kTT) {
+        vo[i] = 0;
+        po[i] = 0;
+    }
+    __syncthreads();
     for (int k = 0; k + 2 < n; ++k) {
-        const int m = n - k - 1;
-        double ss = 0.0;
-        // column k below the diagonal equals row k right of the diagonal (symmetric storage, both kept)
-        for (int r = tid; r < m; r += kT) {
-            const double x = A[(long long)k * lda + (k + 1 + r)];
-            v[r] = x;
-            ss += x * x;
-        }
-        ss = block_sum(ss, red);
-        const double alpha = sqrt(ss);
-        if (tid == 0) {
-            const double x0 = v[0];
-            D.d[k] = A[(long long)k * lda + k];
-            if (alpha == 0.0) {
-                D.e[k] = 0.0;
-                s_beta = 0.0;
-            } else {
-                const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
-                v[0] = x0 + sgn * alpha;
-                D.e[k] = -sgn * alpha;
-                s_beta = 1.0 / (alpha * (alpha + fabs(x0)));
+        // (a) row k with the pending update; reflector from its entries right of the diagonal
+        if (wid == 0) {
+            R *row = A + (long long)k * lda;
+            const R vk = vo[k], pk = po[k];
+            R ss = 0;
+            for (int c = k + 1 + lane; c < n; c += 32) {
+                const R x = row[c] - vk * po[c] - pk * vo[c];
+                v[c] = x;
+                ss = fma(x, x, ss);
             }
-            D.tau[k] = s_beta;
-        }
-        __syncthreads();
-        const double beta = s_beta;
-        if (beta != 0.0) {
-            // p = beta A' v with A'(r, c) read as A(c, r) (symmetric), coalesced over r; 4 accumulators
-            for (int r = tid; r < m; r += kT) {
-                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-                const double *col = A + (long long)(k + 1) * lda + (k + 1 + r);
-                int c = 0;
-                for (; c + 3 < m; c += 4) {
-                    a0 = fma(col[(long long)c * lda], v[c], a0);
-                    a1 = fma(col[(long long)(c + 1) * lda], v[c + 1], a1);
-                    a2 = fma(col[(long long)(c + 2) * lda], v[c + 2], a2);
-                    a3 = fma(col[(long long)(c + 3) * lda], v[c + 3], a3);
+            ss = warp_sum_t(ss);
+            if (lane == 0) {
+                D.d[k] = row[k] - 2 * vk * pk;
+                const R x0 = v[k + 1];
+                const R alpha = sqrt(ss);
+                R beta = 0;
+                if (alpha == (R)0) {
+                    D.e[k] = 0;
+                } else {
+                    const R sgn = x0 >= (R)0 ? (R)1 : (R)-1;
+                    v[k + 1] = x0 + sgn * alpha;
+                    D.e[k] = -sgn * alpha;
+                    beta = (R)1 / (alpha * (alpha + fabs(x0)));
                 }
-                for (; c < m; ++c) a0 = fma(col[(long long)c * lda], v[c], a0);
-                p[r] = beta * ((a0 + a1) + (a2 + a3));
+                D.tau[k] = beta;
+                s_beta = beta;
             }
-            __syncthreads();
-            double pv = 0.0;
-            for (int r = tid; r < m; r += kT) pv += p[r] * v[r];
-            const double kc = 0.5 * beta * block_sum(pv, red);
-            for (int r = tid; r < m; r += kT) p[r] -= kc * v[r];
-            __syncthreads();
-            for (long long idx = tid; idx < (long long)m * m; idx += kT) {
-                const int r = int(idx / m), c = int(idx % m);
-                A[(long long)(k + 1 + r) * lda + (k + 1 + c)] -= v[r] * p[c] + p[r] * v[c];
+            __syncwarp();
+            for (int c = k + 1 + lane; c < n; c += 32) row[c] = v[c];   // reflector into row k
+        }
+        __syncthreads();
+        const R beta = s_beta;
+        // (b) pending update of rows r > k (columns > k) fused with p = beta A v; a warp takes four rows at a
+        // time so that several independent loads are in flight per lane
+        double pv = 0.0;
+        for (int r0 = k + 1 + wid; r0 < n; r0 += 4 * NW) {
+            R *row[4];
+            R vr[4], pr[4], acc[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = r0 + q * NW;
+                const bool ok = r < n;
+                row[q] = A + (long long)(ok ? r : r0) * lda;
+                vr[q] = ok ? vo[r] : (R)0;
+                pr[q] = ok ? po[r] : (R)0;
+                acc[q] = 0;
+            }
+            const int nr = min(4, (n - 1 - r0) / NW + 1);
+#pragma unroll 2
+            for (int c = k + 1 + lane; c < n; c += 32) {
+                const R poc = po[c], voc = vo[c], vc = v[c];
+                R a[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < nr) a[q] = row[q][c];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < nr) {
+                        a[q] = a[q] - vr[q] * poc - pr[q] * voc;
+                        row[q][c] = a[q];
+                        acc[q] = fma(a[q], vc, acc[q]);
+                    }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q >= nr) break;
+                const R sum = warp_sum_t(acc[q]) * beta;
+                if (lane == 0) {
+                    p[r0 + q * NW] = sum;
+                    pv += (double)sum * (double)v[r0 + q * NW];
+                }
             }
         }
-        // reflector into row k (the row is not read again by the reduction)
-        for (int r = tid; r < m; r += kT) A[(long long)k * lda + (k + 1 + r)] = beta != 0.0 ? v[r] : 0.0;
+        if (lane == 0) part[wid] = pv;
         __syncthreads();
+        // (c) p -= (beta/2)(p.v) v; swap the pending-update buffers
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += part[w];
+        const R kc = (R)(0.5 * (double)beta * s);
+        for (int r = k + 1 + tid; r < n; r += kTT) p[r] -= kc * v[r];
+        __syncthreads();
+        R *t = vo;
+        vo = v;
+        v = t;
+        t = po;
+        po = p;
+        p = t;
     }
     if (tid == 0) {
         if (n >= 2) {
-            D.d[n - 2] = A[(long long)(n - 2) * lda + (n - 2)];
-            D.e[n - 2] = A[(long long)(n - 1) * lda + (n - 2)];
-            D.tau[n - 2] = 0.0;
+            const int a = n - 2, b = n - 1;
+            D.d[a] = A[(long long)a * lda + a] - 2 * vo[a] * po[a];
+            D.e[a] = A[(long long)b * lda + a] - vo[b] * po[a] - po[b] * vo[a];
+            D.d[b] = A[(long long)b * lda + b] - 2 * vo[b] * po[b];
+            D.tau[a] = 0;
+            A[(long long)a * lda + b] = 0;   // no reflector for the last two rows
+        } else if (n == 1) {
+            D.d[0] = A[0];
         }
-        D.d[n - 1] = A[(long long)(n - 1) * lda + (n - 1)];
-        D.e[n - 1] = 0.0;
-        D.tau[n - 1] = 0.0;
-        if (n >= 2) A[(long long)(n - 2) * lda + (n - 1)] = 0.0;   // no reflector for the last two rows
+        D.e[n - 1] = 0;
+        D.tau[n - 1] = 0;
     }
 }
 
-// ------------------------------------------------------------------------------------- 2. bisection
+// ------------------------------------------------------------------------------------- 2. multisection
 // Number of eigenvalues below x: sign changes of the leading principal minors p_i = det(T_0..i - x), computed by
-// the three-term recurrence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (no division: on GB300 an FP64
-// division costs ~430 cycles of latency, a multiply-add 64).  Every four steps both carried minors are rescaled
-// by an exact power of two, which keeps them finite without changing any sign.  pivmin stands in for an exactly
-// zero minor.
+// the three-term recurrence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (no division).  Every four steps both
+// carried minors are rescaled by an exact power of two, which keeps them finite without changing any sign.
+// pivmin stands in for an exactly zero minor.
 __device__ __forceinline__ int sturm_below(const double *d, const double *e2, int n, double x, double pivmin) {
     double pm = 1.0, pc = d[0] - x;
     if (pc == 0.0) pc = -pivmin;
@@ -134,70 +208,163 @@ __device__ __forceinline__ int sturm_below(const double *d, const double *e2, in
     return cnt;
 }
 
-// All eigenvalues of each tridiagonal matrix, decreasing, into w (one thread per eigenvalue).
-__global__ void __launch_bounds__(kT) k_tri_bisect(const TriDesc *__restrict__ descs) {
-    const TriDesc D = descs[blockIdx.x];
+// The cnt largest eigenvalues of each tridiagonal (decreasing, into w).  Warp j of the grid's y-range finds the
+// j-th largest: each round the 32 lanes count at 32 interior points of the current bracket, and the bracket
+// shrinks to the sub-interval where the count passes the target (33x per round).
+constexpr int kMsWarps = 8;
+template <class R>
+__global__ void __launch_bounds__(kMsWarps * 32) k_tri_multisect(const TriDescT<R> *__restrict__ descs, int cnt) {
+    const TriDescT<R> D = descs[blockIdx.x];
     const int n = D.n;
-    extern __shared__ double sh[];
-    double *d = sh, *e2 = sh + n;
-    __shared__ double s_lo, s_hi, s_piv;
+    extern __shared__ double shd[];
+    double *d = shd, *e2 = shd + n;
+    __shared__ double s_lo, s_hi;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        d[i] = D.d[i];
-        e2[i] = D.e[i] * D.e[i];
+        d[i] = (double)D.d[i];
+        const double ei = (double)D.e[i];
+        e2[i] = ei * ei;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double lo = DBL_MAX, hi = -DBL_MAX, emax = 0.0;
-        for (int i = 0; i < n; ++i) {
-            const double r = (i > 0 ? fabs(D.e[i - 1]) : 0.0) + (i + 1 < n ? fabs(D.e[i]) : 0.0);
+    if (threadIdx.x < 32) {   // Gershgorin bracket
+        double lo = DBL_MAX, hi = -DBL_MAX;
+        for (int i = threadIdx.x; i < n; i += 32) {
+            const double r = (i > 0 ? fabs((double)D.e[i - 1]) : 0.0) + (i + 1 < n ? fabs((double)D.e[i]) : 0.0);
             lo = fmin(lo, d[i] - r);
             hi = fmax(hi, d[i] + r);
-            emax = fmax(emax, e2[i]);
         }
-        const double span = fmax(hi - lo, fmax(fabs(lo), fabs(hi)));
-        s_lo = lo - 2.0 * DBL_EPSILON * span - 1e-300;
-        s_hi = hi + 2.0 * DBL_EPSILON * span + 1e-300;
-        s_piv = 1e-30;   // relative size of a stand-in for an exactly vanishing minor
-        (void)emax;
+        lo = -warp_max(-lo);
+        hi = warp_max(hi);
+        if (threadIdx.x == 0) {
+            const double span = fmax(hi - lo, fmax(fabs(lo), fabs(hi)));
+            s_lo = lo - 2.0 * DBL_EPSILON * span - 1e-300;
+            s_hi = hi + 2.0 * DBL_EPSILON * span + 1e-300;
+        }
     }
     __syncthreads();
-    for (int j = blockIdx.y * blockDim.x + threadIdx.x; j < n; j += gridDim.y * blockDim.x) {
-        const int k = n - 1 - j;          // j-th largest = k-th smallest (0-based)
-        double lo = s_lo, hi = s_hi;
-        for (int it = 0; it < 200; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi) break;
-            if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300) break;
-            if (sturm_below(d, e2, n, mid, s_piv) <= k) lo = mid;
-            else hi = mid;
-        }
-        D.w[j] = 0.5 * (lo + hi);
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.y * kMsWarps + (threadIdx.x >> 5);
+    if (j >= cnt || j >= n) return;
+    const int kk = n - 1 - j;   // j-th largest = kk-th smallest (0-based)
+    const double pivmin = 1e-30;
+    double lo = s_lo, hi = s_hi;
+    for (int round = 0; round < 48; ++round) {
+        const double width = hi - lo;
+        if (!(width > 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + 1e-300)) break;
+        const double x = fma(width, (double)(lane + 1) / 33.0, lo);
+        const unsigned below = __ballot_sync(0xffffffffu, sturm_below(d, e2, n, x, pivmin) <= kk);
+        // lanes 0..f-1 have count <= kk (x <= lambda), lane f the first with count > kk
+        const int f = below == 0xffffffffu ? 32 : __ffs(~below) - 1;
+        const double nlo = f > 0 ? fma(width, (double)f / 33.0, lo) : lo;
+        const double nhi = f < 32 ? fma(width, (double)(f + 1) / 33.0, lo) : hi;
+        if (!(nlo > lo || nhi < hi)) break;   // no progress left at this precision
+        lo = nlo;
+        hi = nhi;
     }
+    if (lane == 0) D.w[j] = (R)(0.5 * (lo + hi));
+}
+
+// FP32 counterpart for the FP32 tridiagonal (the first stage of the mixed path only needs FP32-accurate
+// eigenvalues): d and e^2 are pre-scaled by the Gershgorin bound so every factor is <= 1 in magnitude, and the
+// carried minors are rescaled by 2^+-40 at every step (exact, sign-preserving) to stay inside FP32 range.
+__device__ __forceinline__ int sturm_below_f32(const float *d, const float *e2, int n, float x, float pivmin) {
+    float pm = 1.f, pc = d[0] - x;
+    if (pc == 0.f) pc = -pivmin;
+    int cnt = pc < 0.f;
+    for (int i = 1; i < n; ++i) {
+        float pn = fmaf(d[i] - x, pc, -e2[i - 1] * pm);
+        if (pn == 0.f) pn = (pc < 0.f ? pivmin : -pivmin) * fabsf(pc);
+        cnt += (pn < 0.f) != (pc < 0.f);
+        pm = pc;
+        pc = pn;
+        const float a = fabsf(pc);
+        if (a > 0x1p+40f) {
+            pc *= 0x1p-40f;
+            pm *= 0x1p-40f;
+        } else if (a < 0x1p-40f) {
+            pc *= 0x1p+40f;
+            pm *= 0x1p+40f;
+        }
+    }
+    return cnt;
+}
+
+__global__ void __launch_bounds__(kMsWarps * 32) k_tri_multisect32(const TriDesc32 *__restrict__ descs, int cnt) {
+    const TriDesc32 D = descs[blockIdx.x];
+    const int n = D.n;
+    extern __shared__ float shf[];
+    float *d = shf, *e2 = shf + n;
+    __shared__ float s_lo, s_hi, s_scale;
+    if (threadIdx.x < 32) {   // Gershgorin bracket and scale
+        float lo = FLT_MAX, hi = -FLT_MAX;
+        for (int i = threadIdx.x; i < n; i += 32) {
+            const float r = (i > 0 ? fabsf(D.e[i - 1]) : 0.f) + (i + 1 < n ? fabsf(D.e[i]) : 0.f);
+            lo = fminf(lo, D.d[i] - r);
+            hi = fmaxf(hi, D.d[i] + r);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (threadIdx.x == 0) {
+            const float sc = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), 1e-30f);
+            s_scale = sc;
+            s_lo = lo / sc - 4.f * FLT_EPSILON;
+            s_hi = hi / sc + 4.f * FLT_EPSILON;
+        }
+    }
+    __syncthreads();
+    const float inv = 1.f / s_scale;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        d[i] = D.d[i] * inv;
+        const float ei = D.e[i] * inv;
+        e2[i] = ei * ei;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.y * kMsWarps + (threadIdx.x >> 5);
+    if (j >= cnt || j >= n) return;
+    const int kk = n - 1 - j;
+    float lo = s_lo, hi = s_hi;
+    for (int round = 0; round < 24; ++round) {
+        const float width = hi - lo;
+        if (!(width > 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)) + 1e-30f)) break;
+        const float x = fmaf(width, (float)(lane + 1) / 33.f, lo);
+        const unsigned below = __ballot_sync(0xffffffffu, sturm_below_f32(d, e2, n, x, 1e-30f) <= kk);
+        const int f = below == 0xffffffffu ? 32 : __ffs(~below) - 1;
+        const float nlo = f > 0 ? fmaf(width, (float)f / 33.f, lo) : lo;
+        const float nhi = f < 32 ? fmaf(width, (float)(f + 1) / 33.f, lo) : hi;
+        if (!(nlo > lo || nhi < hi)) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) D.w[j] = 0.5f * (lo + hi) * s_scale;
 }
 
 // ------------------------------------------------------------ pivoted tridiagonal solve (one thread)
 // Solves (Tri - shift) x = rhs.  Work arrays u0,u1,u2 (U rows: diagonal, first and second super-diagonal) and
 // the right-hand side / solution x live in global memory at stride `st` (interleaved across threads).
-__device__ void tri_solve(const double *d, const double *e, int n, double shift, double *x, double *u0,
-                          double *u1, double *u2, long long st, double pivmin) {
+template <class R>
+__device__ void tri_solve(const R *d, const R *e, int n, R shift, R *x, R *u0, R *u1, R *u2, long long st,
+                          R pivmin) {
     // current row i as (p, q) on columns i, i+1 (no fill yet), rhs in x
-    double p = d[0] - shift, q = n > 1 ? e[0] : 0.0;
+    R p = d[0] - shift, q = n > 1 ? e[0] : (R)0;
     for (int i = 0; i + 1 < n; ++i) {
-        const double l = e[i];                       // entry (i+1, i)
-        const double a = d[i + 1] - shift;           // (i+1, i+1)
-        const double b = i + 2 < n ? e[i + 1] : 0.0; // (i+1, i+2)
-        double xi = x[(long long)i * st], xn = x[(long long)(i + 1) * st];
+        const R l = e[i];                        // entry (i+1, i)
+        const R a = d[i + 1] - shift;            // (i+1, i+1)
+        const R b = i + 2 < n ? e[i + 1] : (R)0; // (i+1, i+2)
+        const R xi = x[(long long)i * st], xn = x[(long long)(i + 1) * st];
         if (fabs(p) >= fabs(l)) {
-            if (fabs(p) < pivmin) p = p < 0.0 ? -pivmin : pivmin;
-            const double mlt = l / p;
+            if (fabs(p) < pivmin) p = p < (R)0 ? -pivmin : pivmin;
+            const R mlt = l / p;
             u0[(long long)i * st] = p;
             u1[(long long)i * st] = q;
-            u2[(long long)i * st] = 0.0;
+            u2[(long long)i * st] = 0;
             x[(long long)(i + 1) * st] = xn - mlt * xi;
             p = a - mlt * q;
             q = b;
         } else {
-            const double mlt = p / l;
+            const R mlt = p / l;
             u0[(long long)i * st] = l;
             u1[(long long)i * st] = a;
             u2[(long long)i * st] = b;
@@ -207,91 +374,99 @@ __device__ void tri_solve(const double *d, const double *e, int n, double shift,
             q = -mlt * b;
         }
     }
-    if (fabs(p) < pivmin) p = p < 0.0 ? -pivmin : pivmin;
+    if (fabs(p) < pivmin) p = p < (R)0 ? -pivmin : pivmin;
     u0[(long long)(n - 1) * st] = p;
     // back substitution
-    double x1 = x[(long long)(n - 1) * st] / p, x2 = 0.0;
+    R x1 = x[(long long)(n - 1) * st] / p, x2 = 0;
     x[(long long)(n - 1) * st] = x1;
     for (int i = n - 2; i >= 0; --i) {
-        const double xi = (x[(long long)i * st] - u1[(long long)i * st] * x1 - u2[(long long)i * st] * x2) /
-                          u0[(long long)i * st];
+        const R xi = (x[(long long)i * st] - u1[(long long)i * st] * x1 - u2[(long long)i * st] * x2) /
+                     u0[(long long)i * st];
         x[(long long)i * st] = xi;
         x2 = x1;
         x1 = xi;
     }
 }
 
+template <class R>
+__device__ R tri_pivmin(const TriDescT<R> &D) {
+    R tnorm = 0;
+    for (int i = 0; i < D.n; ++i) tnorm = fmax(tnorm, fabs(D.d[i]) + fabs(D.e[i]) + (i ? fabs(D.e[i - 1]) : (R)0));
+    return fmax(tnorm, Lim<R>::tiny) * Lim<R>::eps * (R)1e-3;
+}
+
 // ------------------------------------------------------------------------ 3. inverse iteration (kept)
-// Thread (matrix b, vector mu < n_k): two inverse-iteration solves from a pseudo-random start; the result (not
+// Thread (matrix b, vector mu < n_k): three inverse-iteration solves from a pseudo-random start; the result (not
 // yet orthogonalised) goes to Y row mu (Y: nmax x n per matrix, row-major).
-__global__ void __launch_bounds__(64) k_tri_invit(const TriDesc *__restrict__ descs, const int *__restrict__ nkeep,
-                                                  double *__restrict__ Y, double *__restrict__ work, int nmax) {
+template <class R>
+__global__ void __launch_bounds__(64) k_tri_invit(const TriDescT<R> *__restrict__ descs,
+                                                  const int *__restrict__ nkeep, R *__restrict__ Y,
+                                                  R *__restrict__ work, int nmax) {
     const int b = blockIdx.x;
-    const TriDesc D = descs[b];
+    const TriDescT<R> D = descs[b];
     const int n = D.n;
     const int mu = blockIdx.y * blockDim.x + threadIdx.x;
     const int nk = nkeep[b];
     if (mu >= nk) return;
     const long long st = nmax;
-    double *base = work + (long long)b * 4 * n * nmax;
-    double *x = base + mu, *u0 = base + (long long)n * nmax + mu, *u1 = base + 2LL * n * nmax + mu,
-           *u2 = base + 3LL * n * nmax + mu;
-    double tnorm = 0.0;
-    for (int i = 0; i < n; ++i) tnorm = fmax(tnorm, fabs(D.d[i]) + fabs(D.e[i]) + (i ? fabs(D.e[i - 1]) : 0.0));
-    const double pivmin = fmax(tnorm, 1e-300) * DBL_EPSILON * 1e-3;
-    const double lam = D.w[mu];
+    R *base = work + (long long)b * 4 * n * nmax;
+    R *x = base + mu, *u0 = base + (long long)n * nmax + mu, *u1 = base + 2LL * n * nmax + mu,
+      *u2 = base + 3LL * n * nmax + mu;
+    const R pivmin = tri_pivmin(D);
+    const R lam = D.w[mu];
     unsigned h = 2166136261u ^ (unsigned)(mu * 7919 + 17);
     for (int i = 0; i < n; ++i) {
         h = (h ^ (unsigned)i) * 16777619u;
-        x[(long long)i * st] = 0.5 + (double)(h % 1000003u) / 1000003.0;
+        x[(long long)i * st] = (R)(0.5 + (double)(h % 1000003u) / 1000003.0);
     }
     for (int rep = 0; rep < 3; ++rep) {
-        tri_solve(D.d, D.e, n, lam, x, u0, u1, u2, st, pivmin);
-        double s0 = 0.0, s1 = 0.0;
+        tri_solve<R>(D.d, D.e, n, lam, x, u0, u1, u2, st, pivmin);
+        R s0 = 0, s1 = 0;
         for (int i = 0; i + 1 < n; i += 2) {
             s0 = fma(x[(long long)i * st], x[(long long)i * st], s0);
             s1 = fma(x[(long long)(i + 1) * st], x[(long long)(i + 1) * st], s1);
         }
         if (n & 1) s0 = fma(x[(long long)(n - 1) * st], x[(long long)(n - 1) * st], s0);
-        const double inv = 1.0 / sqrt(s0 + s1);
+        const R inv = (R)1 / sqrt(s0 + s1);
         for (int i = 0; i < n; ++i) x[(long long)i * st] *= inv;
     }
-    double *y = Y + ((long long)b * nmax + mu) * n;
+    R *y = Y + ((long long)b * nmax + mu) * n;
     for (int i = 0; i < n; ++i) y[i] = x[(long long)i * st];
 }
 
-// Shifted solves of the OSV relaxation: X row mu = (Tri - omega_mu)^{-1} (-R row mu) for mu < n_k, zero otherwise.
-__global__ void __launch_bounds__(64) k_tri_shift_solve(const TriDesc *__restrict__ descs,
-                                                        const int *__restrict__ nkeep, const double *__restrict__ R,
-                                                        double *__restrict__ X, double *__restrict__ work,
-                                                        int nmax) {
+// Shifted solves of the OSV relaxation: X row mu = (Tri - s_mu)^{-1} (-R row mu) for mu < n_k, zero otherwise.
+template <class R>
+__global__ void __launch_bounds__(64) k_tri_shift_solve(const TriDescT<R> *__restrict__ descs,
+                                                        const int *__restrict__ nkeep, const R *__restrict__ Rin,
+                                                        R *__restrict__ X, R *__restrict__ work, int nmax,
+                                                        const double *__restrict__ shift, int shift_ld) {
     const int b = blockIdx.x;
-    const TriDesc D = descs[b];
+    const TriDescT<R> D = descs[b];
     const int n = D.n;
     const int mu = blockIdx.y * blockDim.x + threadIdx.x;
     if (mu >= nmax) return;
     const int nk = nkeep[b];
-    double *xo = X + ((long long)b * nmax + mu) * n;
+    R *xo = X + ((long long)b * nmax + mu) * n;
     if (mu >= nk) {
-        for (int i = 0; i < n; ++i) xo[i] = 0.0;
+        for (int i = 0; i < n; ++i) xo[i] = 0;
         return;
     }
     const long long st = nmax;
-    double *base = work + (long long)b * 4 * n * nmax;
-    double *x = base + mu, *u0 = base + (long long)n * nmax + mu, *u1 = base + 2LL * n * nmax + mu,
-           *u2 = base + 3LL * n * nmax + mu;
-    double tnorm = 0.0;
-    for (int i = 0; i < n; ++i) tnorm = fmax(tnorm, fabs(D.d[i]) + fabs(D.e[i]) + (i ? fabs(D.e[i - 1]) : 0.0));
-    const double pivmin = fmax(tnorm, 1e-300) * DBL_EPSILON * 1e-3;
-    const double *r = R + ((long long)b * nmax + mu) * n;
+    R *base = work + (long long)b * 4 * n * nmax;
+    R *x = base + mu, *u0 = base + (long long)n * nmax + mu, *u1 = base + 2LL * n * nmax + mu,
+      *u2 = base + 3LL * n * nmax + mu;
+    const R pivmin = tri_pivmin(D);
+    const R *r = Rin + ((long long)b * nmax + mu) * n;
     for (int i = 0; i < n; ++i) x[(long long)i * st] = -r[i];
-    tri_solve(D.d, D.e, n, D.w[mu], x, u0, u1, u2, st, pivmin);
+    const R s = shift ? (R)shift[(long long)b * shift_ld + mu] : D.w[mu];
+    tri_solve<R>(D.d, D.e, n, s, x, u0, u1, u2, st, pivmin);
     for (int i = 0; i < n; ++i) xo[i] = x[(long long)i * st];
 }
 
 // ------------------------------------------------------------------------------ CGS2 helpers (per CTA)
-__device__ __forceinline__ double warp_dot(const double *a, const double *b, int n) {
-    double s0 = 0.0, s1 = 0.0;
+template <class R>
+__device__ __forceinline__ R warp_dot(const R *a, const R *b, int n) {
+    R s0 = 0, s1 = 0;
     const int lane = threadIdx.x & 31;
     int i = lane;
     for (; i + 32 < n; i += 64) {
@@ -299,61 +474,63 @@ __device__ __forceinline__ double warp_dot(const double *a, const double *b, int
         s1 = fma(a[i + 32], b[i + 32], s1);
     }
     if (i < n) s0 = fma(a[i], b[i], s0);
-    return warp_sum(s0 + s1);
+    return warp_sum_t(s0 + s1);
 }
 
 // Orthonormalise rows 0..n_k-1 of Y (per matrix) in order with two Gram-Schmidt passes each.
-__global__ void __launch_bounds__(kT) k_orthonormalise(const int *__restrict__ nkeep, double *__restrict__ Y, int n,
+template <class R>
+__global__ void __launch_bounds__(kT) k_orthonormalise(const int *__restrict__ nkeep, R *__restrict__ Y, int n,
                                                        int nmax) {
     const int b = blockIdx.x;
     const int nk = nkeep[b];
-    double *Yb = Y + (long long)b * nmax * n;
-    __shared__ double coef[128];
+    R *Yb = Y + (long long)b * nmax * n;
+    __shared__ R coef[128];
     __shared__ double red[kT / 32];
     const int wid = threadIdx.x >> 5, nw = kT / 32, lane = threadIdx.x & 31;
     for (int mu = 0; mu < nk; ++mu) {
-        double *y = Yb + (long long)mu * n;
+        R *y = Yb + (long long)mu * n;
         for (int pass = 0; pass < 2; ++pass) {
             for (int nu = wid; nu < mu; nu += nw) {
-                const double c = warp_dot(y, Yb + (long long)nu * n, n);
+                const R c = warp_dot<R>(y, Yb + (long long)nu * n, n);
                 if (lane == 0) coef[nu] = c;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += kT) {
-                double s = y[i];
+                R s = y[i];
                 for (int nu = 0; nu < mu; ++nu) s -= coef[nu] * Yb[(long long)nu * n + i];
                 y[i] = s;
             }
             __syncthreads();
         }
         double ss = 0.0;
-        for (int i = threadIdx.x; i < n; i += kT) ss += y[i] * y[i];
+        for (int i = threadIdx.x; i < n; i += kT) ss += (double)y[i] * (double)y[i];
         ss = block_sum(ss, red);
-        const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+        const R inv = ss > 0.0 ? (R)(1.0 / sqrt(ss)) : (R)0;
         for (int i = threadIdx.x; i < n; i += kT) y[i] *= inv;
         __syncthreads();
     }
 }
 
 // X rows mu < nx of each matrix -= projection onto rows 0..n_k-1 of Y (two passes; Y orthonormal).
-__global__ void __launch_bounds__(kT) k_project_out(const int *__restrict__ nkeep, const double *__restrict__ Y,
-                                                    double *__restrict__ X, int n, int nmax) {
+template <class R>
+__global__ void __launch_bounds__(kT) k_project_out(const int *__restrict__ nkeep, const R *__restrict__ Y,
+                                                    R *__restrict__ X, int n, int nmax) {
     const int b = blockIdx.x;
     const int nk = nkeep[b];
-    const double *Yb = Y + (long long)b * nmax * n;
-    double *Xb = X + (long long)b * nmax * n;
+    const R *Yb = Y + (long long)b * nmax * n;
+    R *Xb = X + (long long)b * nmax * n;
     const int wid = threadIdx.x >> 5, nw = kT / 32, lane = threadIdx.x & 31;
     for (int pass = 0; pass < 2; ++pass) {
         for (int mu = wid; mu < nk; mu += nw) {
-            double *x = Xb + (long long)mu * n;
+            R *x = Xb + (long long)mu * n;
             // coefficients against every kept y, then one update (classical Gram-Schmidt, repeated)
-            double cbuf[4];
+            R cbuf[4];
             for (int nu0 = 0; nu0 < nk; nu0 += 4) {
                 const int cnt = min(4, nk - nu0);
-                for (int t = 0; t < cnt; ++t) cbuf[t] = warp_dot(x, Yb + (long long)(nu0 + t) * n, n);
+                for (int t = 0; t < cnt; ++t) cbuf[t] = warp_dot<R>(x, Yb + (long long)(nu0 + t) * n, n);
                 __syncwarp();
                 for (int i = lane; i < n; i += 32) {
-                    double s = x[i];
+                    R s = x[i];
                     for (int t = 0; t < cnt; ++t) s -= cbuf[t] * Yb[(long long)(nu0 + t) * n + i];
                     x[i] = s;
                 }
@@ -367,35 +544,76 @@ __global__ void __launch_bounds__(kT) k_project_out(const int *__restrict__ nkee
 // ------------------------------------------------------------------------------- 4. reflector products
 // rows mu < nrow(b) of V (nmax x n per matrix): forward = 0 applies H = H_0 ... H_{n-3} (q = H y),
 // forward = 1 applies H^T (y = H^T g).  Reflector k: row k of A, columns k+1..n-1, scalar tau[k].
-__global__ void __launch_bounds__(kT) k_reflect(const TriDesc *__restrict__ descs, const int *__restrict__ nrow,
-                                                double *__restrict__ V, int nmax, int forward) {
+// CTA (matrix b, group of G rows): the G rows live in shared memory for the whole reflector sequence (one warp
+// per row: a dot product and an update per reflector), and the next reflector is copied into a second buffer
+// with cp.async while the current one is applied.
+__device__ __forceinline__ void cp_async_elem(void *dst, const void *src, int bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <class R>
+__global__ void __launch_bounds__(kT) k_reflect(const TriDescT<R> *__restrict__ descs, const int *__restrict__ nrow,
+                                                R *__restrict__ V, int nmax, int forward, int G) {
     const int b = blockIdx.x;
-    const TriDesc D = descs[b];
+    const TriDescT<R> D = descs[b];
     const int n = D.n;
     const int nr = nrow ? nrow[b] : nmax;
-    extern __shared__ double v[];
-    double *Vb = V + (long long)b * nmax * n;
-    const int wid = threadIdx.x >> 5, nw = kT / 32, lane = threadIdx.x & 31;
+    const int g0 = blockIdx.y * G;
+    if (g0 >= nr || n < 3) return;
+    const int rows = min(G, nr - g0);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *Vs = reinterpret_cast<R *>(smem_raw);   // rows x n
+    R *vb = Vs + (long long)G * n;               // 2 x n: current and next reflector
+    R *ts = vb + 2 * n;                          // tau
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    R *Vg = V + ((long long)b * nmax + g0) * n;
+    for (int i = tid; i < rows * n; i += kT) Vs[i] = Vg[i];
+    for (int i = tid; i < n; i += kT) ts[i] = D.tau[i];
+    auto fetch = [&](int s, R *dst) {   // reflector of step s -> dst[0 .. m)
+        const int k = forward ? s : n - 3 - s, m = n - k - 1;
+        const R *src = D.A + (long long)k * D.lda + k + 1;
+        for (int i = tid; i < m; i += kT) cp_async_elem(dst + i, src + i, (int)sizeof(R));
+    };
+    fetch(0, vb);
+    cp_async_wait_all();
+    __syncthreads();
     for (int s = 0; s + 2 < n; ++s) {
-        const int k = forward ? s : n - 3 - s;
-        const double beta = D.tau[k];
-        if (beta == 0.0) continue;
-        const int m = n - k - 1;
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += kT) v[i] = D.A[(long long)k * D.lda + k + 1 + i];
-        __syncthreads();
-        for (int mu = wid; mu < nr; mu += nw) {
-            double *y = Vb + (long long)mu * n + k + 1;
-            const double c = beta * warp_dot(y, v, m);
-            for (int i = lane; i < m; i += 32) y[i] -= c * v[i];
+        const int k = forward ? s : n - 3 - s, m = n - k - 1;
+        const R *v = vb + (s & 1) * n;
+        if (s + 3 < n) fetch(s + 1, vb + ((s + 1) & 1) * n);
+        const R beta = ts[k];
+        if (beta != (R)0 && wid < rows) {
+            R *y = Vs + (long long)wid * n + k + 1;
+            R a0 = 0, a1 = 0;
+            int i = lane;
+            for (; i + 32 < m; i += 64) {
+                a0 = fma(y[i], v[i], a0);
+                a1 = fma(y[i + 32], v[i + 32], a1);
+            }
+            if (i < m) a0 = fma(y[i], v[i], a0);
+            const R c = beta * warp_sum_t(a0 + a1);
+            for (int j = lane; j < m; j += 32) y[j] -= c * v[j];
         }
+        cp_async_wait_all();
+        __syncthreads();
     }
+    for (int i = tid; i < rows * n; i += kT) Vg[i] = Vs[i];
+}
+
+// rows per CTA of k_reflect for order n: as many as fit next to the two reflector buffers (at most 8)
+template <class R>
+int reflect_rows(int n) {
+    const long long cap = 200 * 1024, per = (long long)n * sizeof(R);
+    const long long g = (cap - 3 * per) / per;
+    return (int)std::max<long long>(1, std::min<long long>(8, g));
 }
 
 // -------------------------------------------------------------------------------- small dense Jacobi
-// Cyclic parallel Jacobi for symmetric matrices of order <= kJacMax held in shared memory (A and V, padded to
-// even order).  Round-robin pairing: every round rotates n/2 disjoint planes at once.  Eigenvalues decreasing
-// into w, eigenvectors as rows of Zt.  n_dev (optional) gives the order.
+// Cyclic parallel Jacobi for symmetric matrices of order <= kJacobiMax held in shared memory (A and V, padded to
+// even order).  Eigenvalues decreasing into w, eigenvectors as rows of Zt.  n_dev (optional) gives the order.
 __global__ void __launch_bounds__(kT) k_jacobi_small(const EighDesc *__restrict__ descs, int *err) {
     const EighDesc D = descs[blockIdx.x];
     const int n = D.n_dev ? min(*D.n_dev, D.n) : D.n;
@@ -407,7 +625,7 @@ __global__ void __launch_bounds__(kT) k_jacobi_small(const EighDesc *__restrict_
     double *cs = V + (long long)ne * ld, *sn = cs + ne / 2;
     int *pp = reinterpret_cast<int *>(sn + ne / 2), *qq = pp + ne / 2, *rank = qq + ne / 2;
     __shared__ double red[kT / 32];
-    __shared__ int s_done;
+    __shared__ int s_flag;
     const int tid = threadIdx.x;
     for (int idx = tid; idx < ne * ne; idx += kT) {
         const int r = idx / ne, c = idx % ne;
@@ -415,86 +633,130 @@ __global__ void __launch_bounds__(kT) k_jacobi_small(const EighDesc *__restrict_
         V[r * ld + c] = r == c ? 1.0 : 0.0;
     }
     __syncthreads();
-    double fro = 0.0;
-    for (int idx = tid; idx < ne * ne; idx += kT) {
-        const double a = A[(idx / ne) * ld + idx % ne];
-        fro += a * a;
-    }
-    fro = block_sum(fro, red);
-    const int half = ne / 2;
-    bool conv = false;
-    for (int sweep = 0; sweep < 40 && !conv; ++sweep) {
-        for (int round = 0; round < ne - 1; ++round) {
-            // round-robin: index 0 fixed, others rotate
-            for (int t = tid; t < half; t += kT) {
-                int a = t == 0 ? 0 : 1 + (t - 1 + round) % (ne - 1);
-                int bb = 1 + (ne - 2 - t + round) % (ne - 1);
-                if (t == 0) bb = 1 + (ne - 2 + round) % (ne - 1);
-                const int p = min(a, bb), q = max(a, bb);
-                pp[t] = p;
-                qq[t] = q;
-                const double apq = A[p * ld + q];
-                double c = 1.0, s = 0.0;
-                if (apq != 0.0 && fabs(apq) > 1e-300) {
-                    const double th = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
-                    const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                    c = rsqrt(tt * tt + 1.0);
-                    s = tt * c;
-                }
-                cs[t] = c;
-                sn[t] = s;
-            }
-            __syncthreads();
-            // rows: B = J^T A
-            for (int idx = tid; idx < half * ne; idx += kT) {
-                const int t = idx / ne, k = idx % ne;
-                const int p = pp[t], q = qq[t];
-                const double c = cs[t], s = sn[t];
-                const double ap = A[p * ld + k], aq = A[q * ld + k];
-                A[p * ld + k] = c * ap - s * aq;
-                A[q * ld + k] = s * ap + c * aq;
-            }
-            __syncthreads();
-            // columns: A' = B J, and V' = V J
-            for (int idx = tid; idx < half * ne; idx += kT) {
-                const int t = idx / ne, k = idx % ne;
-                const int p = pp[t], q = qq[t];
-                const double c = cs[t], s = sn[t];
-                const double ap = A[k * ld + p], aq = A[k * ld + q];
-                A[k * ld + p] = c * ap - s * aq;
-                A[k * ld + q] = s * ap + c * aq;
-                const double vp = V[k * ld + p], vq = V[k * ld + q];
-                V[k * ld + p] = c * vp - s * vq;
-                V[k * ld + q] = s * vp + c * vq;
-            }
-            __syncthreads();
-        }
-        double off = 0.0;
-        for (int idx = tid; idx < ne * ne; idx += kT) {
-            const int r = idx / ne, c = idx % ne;
-            if (r != c) off += A[r * ld + c] * A[r * ld + c];
-        }
-        off = block_sum(off, red);
-        if (tid == 0) s_done = off <= 1e-30 * fro || off == 0.0;
-        __syncthreads();
-        conv = s_done;
-    }
-    if (!conv && tid == 0) atomicExch(err, kDevEighNoConv);
-    for (int i = tid; i < n; i += kT) {
-        const double di = A[i * ld + i];
-        int rk = 0;
-        for (int j = 0; j < n; ++j) {
-            const double dj = A[j * ld + j];
-            rk += (dj > di) || (dj == di && j < i);
-        }
-        rank[i] = rk;
-    }
-    __syncthreads();
+    const bool conv = jacobi_sweeps<double>(A, V, ne, ld, cs, sn, pp, qq, red, &s_flag, 40, 1e-28);
+    if (!conv && tid == 0) raise_err(err, kDevEighNoConv);
+    diag_rank<double>(A, n, ld, rank);
     for (int i = tid; i < n; i += kT) D.w[rank[i]] = A[i * ld + i];
     for (int idx = tid; idx < n * n; idx += kT) {
         const int c = idx / n, r = idx % n;    // eigenvector c, component r
         D.Zt[(long long)rank[c] * D.ldz + r] = V[r * ld + c];
     }
+}
+
+// Mixed-precision variant for the pair eigenproblems (order <= kJacobiMixedMax): FP32 Jacobi sweeps to the FP32
+// floor give V0; FP64 then re-orthonormalises it by two Newton-Schulz steps V <- V (3I - V^T V)/2, forms
+// A1 = V^T A V (A re-read from global memory, FP64) and finishes with FP64 Jacobi sweeps on A1, which is
+// diagonal to ~1e-7 relative and converges quadratically (one or two sweeps instead of ~8 on A itself).
+// Shared memory: three n x n FP64 buffers (the FP32 A and V alias the first).
+__global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict__ descs, int *err) {
+    const EighDesc D = descs[blockIdx.x];
+    const int n = D.n_dev ? min(*D.n_dev, D.n) : D.n;
+    if (n <= 0) return;
+    const int ne = (n + 1) & ~1;
+    const int ld = ne + 1;
+    const long long sq = (long long)ne * ld;
+    extern __shared__ double sh[];
+    double *B0 = sh, *B1 = sh + sq, *B2 = sh + 2 * sq;
+    double *cs = B2 + sq, *sn = cs + ne / 2, *dg = sn + ne / 2;
+    float *cs32 = reinterpret_cast<float *>(dg + ne), *sn32 = cs32 + ne / 2;
+    int *pp = reinterpret_cast<int *>(sn32 + ne / 2), *qq = pp + ne / 2, *rank = qq + ne / 2;
+    float *A32 = reinterpret_cast<float *>(B0), *V32 = A32 + sq;
+    __shared__ double red[kT / 32];
+    __shared__ int s_flag;
+    const int tid = threadIdx.x;
+    auto Ag = [&](int r, int c) -> double { return (r < n && c < n) ? D.A[(long long)r * D.lda + c] : 0.0; };
+    for (int idx = tid; idx < ne * ne; idx += kT) {
+        const int r = idx / ne, c = idx % ne;
+        A32[r * ld + c] = (float)Ag(r, c);
+        V32[r * ld + c] = r == c ? 1.f : 0.f;
+    }
+    __syncthreads();
+    jacobi_sweeps<float>(A32, V32, ne, ld, cs32, sn32, pp, qq, red, &s_flag, 20, 1e-10);
+    for (int idx = tid; idx < ne * ne; idx += kT) {
+        const int r = idx / ne, c = idx % ne;
+        B1[r * ld + c] = (double)V32[r * ld + c];
+    }
+    __syncthreads();
+    // two Newton-Schulz steps V <- V (3I - V^T V) / 2 (orthonormality error 1e-6 -> 1e-12 -> 1e-16):
+    // V0 in B1 -> B0 -> B1
+    double *Vin = B1, *Vout = B0;
+    for (int step = 0; step < 2; ++step) {
+        for (int idx = tid; idx < ne * ne; idx += kT) {
+            const int r = idx / ne, c = idx % ne;
+            double g = 0.0;
+            for (int k = 0; k < ne; ++k) g = fma(Vin[k * ld + r], Vin[k * ld + c], g);
+            B2[r * ld + c] = 0.5 * ((r == c ? 3.0 : 0.0) - g);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < ne * ne; idx += kT) {
+            const int r = idx / ne, c = idx % ne;
+            double v = 0.0;
+            for (int k = 0; k < ne; ++k) v = fma(Vin[r * ld + k], B2[k * ld + c], v);
+            Vout[r * ld + c] = v;
+        }
+        __syncthreads();
+        double *t = Vin;
+        Vin = Vout;
+        Vout = t;
+    }
+    // V in B1; T = A V (B0), A1 = V^T T (B2)
+    for (int idx = tid; idx < ne * ne; idx += kT) {
+        const int r = idx / ne, c = idx % ne;
+        double t = 0.0;
+        if (r < n)
+            for (int k = 0; k < n; ++k) t = fma(D.A[(long long)r * D.lda + k], B1[k * ld + c], t);
+        B0[r * ld + c] = t;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ne * ne; idx += kT) {
+        const int r = idx / ne, c = idx % ne;
+        if (r > c) continue;
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < ne; ++k) {
+            a = fma(B1[k * ld + r], B0[k * ld + c], a);
+            b = fma(B1[k * ld + c], B0[k * ld + r], b);
+        }
+        const double m = 0.5 * (a + b);
+        B2[r * ld + c] = m;
+        B2[c * ld + r] = m;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < ne * ne; idx += kT) {
+        const int r = idx / ne, c = idx % ne;
+        B0[r * ld + c] = r == c ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // polish: off-diagonal norm <= 1e-14 of the Frobenius norm (the FP32 start leaves ~1e-7; quadratic
+    // convergence gives that in one sweep, two with clustered eigenvalues)
+    const bool conv = jacobi_sweeps<double>(B2, B0, ne, ld, cs, sn, pp, qq, red, &s_flag, 20, 1e-28);
+    if (!conv && tid == 0) raise_err(err, kDevEighNoConv);
+    for (int i = tid; i < ne; i += kT) dg[i] = B2[i * ld + i];
+    __syncthreads();
+    // final eigenvectors V V' (B2)
+    for (int idx = tid; idx < ne * ne; idx += kT) {
+        const int r = idx / ne, c = idx % ne;
+        double v = 0.0;
+        for (int k = 0; k < ne; ++k) v = fma(B1[r * ld + k], B0[k * ld + c], v);
+        B2[r * ld + c] = v;
+    }
+    for (int i = tid; i < n; i += kT) {
+        const double di = dg[i];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) rk += (dg[j] > di) || (dg[j] == di && j < i);
+        rank[i] = rk;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += kT) D.w[rank[i]] = dg[i];
+    for (int idx = tid; idx < n * n; idx += kT) {
+        const int c = idx / n, r = idx % n;    // eigenvector c, component r
+        D.Zt[(long long)rank[c] * D.ldz + r] = B2[r * ld + c];
+    }
+}
+
+template <class K>
+cudaError_t smem_attr(K kernel, size_t sh) {
+    if (sh > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -505,66 +767,108 @@ size_t jacobi_smem_bytes(int n) {
            (size_t)ne * sizeof(int) + 64;
 }
 
-cudaError_t osv_tridiag(const TriDesc *d, int batch, int n, cudaStream_t s) {
+template <class R>
+cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
-    const size_t sh = 2 * (size_t)n * sizeof(double);
+    const size_t sh = 4 * (size_t)n * sizeof(R);
     cudaError_t e;
-    if (sh > 48 * 1024 && (e = cudaFuncSetAttribute(k_tridiag_osv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh)) != cudaSuccess)
-        return e;
+    if ((e = smem_attr(k_tridiag<R>, sh)) != cudaSuccess) return e;
     count_launch();
-    k_tridiag_osv<<<batch, kT, sh, s>>>(d);
+    k_tridiag<R><<<batch, kTT, sh, s>>>(d);
     return cudaGetLastError();
 }
 
-cudaError_t osv_tri_eigvals(const TriDesc *d, int batch, int n, cudaStream_t s) {
-    if (batch <= 0) return cudaSuccess;
-    const size_t sh = 2 * (size_t)n * sizeof(double);
+template <class R>
+cudaError_t osv_tri_eigvals(const TriDescT<R> *d, int batch, int n, int cnt, cudaStream_t s) {
+    if (batch <= 0 || cnt <= 0) return cudaSuccess;
+    cnt = cnt < n ? cnt : n;
+    const dim3 grid(batch, (cnt + kMsWarps - 1) / kMsWarps);
     cudaError_t e;
-    if (sh > 48 * 1024 && (e = cudaFuncSetAttribute(k_tri_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh)) != cudaSuccess)
-        return e;
-    const int gy = (n + kT - 1) / kT;
-    count_launch();
-    k_tri_bisect<<<dim3(batch, gy), kT, sh, s>>>(d);
+    if constexpr (sizeof(R) == 4) {
+        const size_t sh = 2 * (size_t)n * sizeof(float);
+        if ((e = smem_attr(k_tri_multisect32, sh)) != cudaSuccess) return e;
+        count_launch();
+        k_tri_multisect32<<<grid, kMsWarps * 32, sh, s>>>(d, cnt);
+    } else {
+        const size_t sh = 2 * (size_t)n * sizeof(double);
+        if ((e = smem_attr(k_tri_multisect<R>, sh)) != cudaSuccess) return e;
+        count_launch();
+        k_tri_multisect<R><<<grid, kMsWarps * 32, sh, s>>>(d, cnt);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t osv_tri_kept_vectors(const TriDesc *d, int batch, int n, int nmax, const int *nkeep, double *Y,
-                                 double *work, cudaStream_t s) {
+template <class R>
+cudaError_t osv_tri_kept_vectors(const TriDescT<R> *d, int batch, int n, int nmax, const int *nkeep, R *Y, R *work,
+                                 cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
-    count_launch();
-    k_tri_invit<<<dim3(batch, (nmax + 63) / 64), 64, 0, s>>>(d, nkeep, Y, work, nmax);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     if (nmax > 128) return cudaErrorInvalidValue;
     count_launch();
-    k_orthonormalise<<<batch, kT, 0, s>>>(nkeep, Y, n, nmax);
+    k_tri_invit<R><<<dim3(batch, (nmax + 63) / 64), 64, 0, s>>>(d, nkeep, Y, work, nmax);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_orthonormalise<R><<<batch, kT, 0, s>>>(nkeep, Y, n, nmax);
     return cudaGetLastError();
 }
 
-cudaError_t osv_reflect(const TriDesc *d, int batch, int n, int nmax, const int *nrow, double *V, int forward,
+template <class R>
+cudaError_t osv_reflect(const TriDescT<R> *d, int batch, int n, int nmax, const int *nrow, R *V, int forward,
                         cudaStream_t s) {
-    if (batch <= 0) return cudaSuccess;
-    const size_t sh = (size_t)n * sizeof(double);
+    if (batch <= 0 || nmax <= 0) return cudaSuccess;
+    const int G = reflect_rows<R>(n);
+    const size_t sh = (size_t)(G + 3) * n * sizeof(R);
     cudaError_t e;
-    if (sh > 48 * 1024 && (e = cudaFuncSetAttribute(k_reflect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh)) != cudaSuccess)
-        return e;
+    if ((e = smem_attr(k_reflect<R>, sh)) != cudaSuccess) return e;
     count_launch();
-    k_reflect<<<batch, kT, sh, s>>>(d, nrow, V, nmax, forward);
+    k_reflect<R><<<dim3(batch, (nmax + G - 1) / G), kT, sh, s>>>(d, nrow, V, nmax, forward, G);
     return cudaGetLastError();
 }
 
-cudaError_t osv_project_out(const int *nkeep, const double *Y, double *X, int batch, int n, int nmax, cudaStream_t s) {
+template <class R>
+cudaError_t osv_project_out(const int *nkeep, const R *Y, R *X, int batch, int n, int nmax, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
     count_launch();
-    k_project_out<<<batch, kT, 0, s>>>(nkeep, Y, X, n, nmax);
+    k_project_out<R><<<batch, kT, 0, s>>>(nkeep, Y, X, n, nmax);
     return cudaGetLastError();
 }
 
-cudaError_t osv_tri_shift_solve(const TriDesc *d, int batch, int n, int nmax, const int *nkeep, const double *R,
-                                double *X, double *work, cudaStream_t s) {
+template <class R>
+cudaError_t osv_tri_shift_solve(const TriDescT<R> *d, int batch, int n, int nmax, const int *nkeep, const R *Rin,
+                                R *X, R *work, const double *shift, int shift_ld, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
     count_launch();
-    k_tri_shift_solve<<<dim3(batch, (nmax + 63) / 64), 64, 0, s>>>(d, nkeep, R, X, work, nmax);
+    k_tri_shift_solve<R><<<dim3(batch, (nmax + 63) / 64), 64, 0, s>>>(d, nkeep, Rin, X, work, nmax, shift, shift_ld);
+    return cudaGetLastError();
+}
+
+#define OSV_EIG_INST(R)                                                                                            \
+    template cudaError_t osv_tridiag<R>(const TriDescT<R> *, int, int, cudaStream_t);                              \
+    template cudaError_t osv_tri_eigvals<R>(const TriDescT<R> *, int, int, int, cudaStream_t);                     \
+    template cudaError_t osv_tri_kept_vectors<R>(const TriDescT<R> *, int, int, int, const int *, R *, R *,        \
+                                                 cudaStream_t);                                                    \
+    template cudaError_t osv_reflect<R>(const TriDescT<R> *, int, int, int, const int *, R *, int, cudaStream_t);  \
+    template cudaError_t osv_project_out<R>(const int *, const R *, R *, int, int, int, cudaStream_t);             \
+    template cudaError_t osv_tri_shift_solve<R>(const TriDescT<R> *, int, int, int, const int *, const R *, R *,   \
+                                                R *, const double *, int, cudaStream_t);
+OSV_EIG_INST(double)
+OSV_EIG_INST(float)
+#undef OSV_EIG_INST
+
+size_t jacobi_mixed_smem_bytes(int n) {
+    const int ne = (n + 1) & ~1;
+    return (size_t)3 * ne * (ne + 1) * sizeof(double) + (size_t)2 * ne * sizeof(double) + (size_t)ne * sizeof(float) +
+           (size_t)3 * (ne / 2 + 1) * sizeof(int) + (size_t)ne * sizeof(int) + 64;
+}
+
+cudaError_t eigh_small_jacobi_mixed(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s) {
+    if (batch <= 0) return cudaSuccess;
+    if (n_max > kJacobiMixedMax) return cudaErrorInvalidValue;
+    const size_t sh = jacobi_mixed_smem_bytes(n_max);
+    cudaError_t e;
+    if ((e = smem_attr(k_jacobi_mixed, sh)) != cudaSuccess) return e;
+    count_launch();
+    k_jacobi_mixed<<<batch, kT, sh, s>>>(d, err);
     return cudaGetLastError();
 }
 
@@ -572,8 +876,7 @@ cudaError_t eigh_small_jacobi(const EighDesc *d, int batch, int n_max, int *err,
     if (batch <= 0) return cudaSuccess;
     const size_t sh = jacobi_smem_bytes(n_max);
     cudaError_t e;
-    if (sh > 48 * 1024 && (e = cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh)) != cudaSuccess)
-        return e;
+    if ((e = smem_attr(k_jacobi_small, sh)) != cudaSuccess) return e;
     count_launch();
     k_jacobi_small<<<batch, kT, sh, s>>>(d, err);
     return cudaGetLastError();

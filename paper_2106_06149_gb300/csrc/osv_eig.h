@@ -1,5 +1,7 @@
-// OSV eigenproblem (Eq. 6) via tridiagonalisation, bisection and inverse iteration, the OSV-relaxation solves
-// (Eq. 8), and the small parallel-Jacobi eigensolver.
+// OSV eigenproblem (Eq. 6) via tridiagonalisation, multisection and inverse iteration, the OSV-relaxation solves
+// (Eq. 8), and the small parallel-Jacobi eigensolver.  The tridiagonal route is templated on the working
+// precision R (double for the FP64 path; float for the first stage of the mixed path, whose results are then
+// refined in FP64 by osv_refine.cu).
 #pragma once
 #include "kernels.cuh"
 
@@ -7,29 +9,45 @@ namespace osv {
 
 // One symmetric matrix reduced in place: A (n x n, lda) -> reflectors (row k, columns k+1..), tridiagonal
 // d (diagonal), e (sub-diagonal e[k] couples k and k+1), tau (reflector scalars); w: eigenvalues, decreasing.
-struct TriDesc {
-    double *A;
+template <class R>
+struct TriDescT {
+    R *A;
     long long lda;
     int n;
-    double *d, *e, *tau, *w;
+    R *d, *e, *tau, *w;
 };
+using TriDesc = TriDescT<double>;
+using TriDesc32 = TriDescT<float>;
 
-cudaError_t osv_tridiag(const TriDesc *d, int batch, int n, cudaStream_t s);
-cudaError_t osv_tri_eigvals(const TriDesc *d, int batch, int n, cudaStream_t s);
+template <class R>
+cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s);
+// The cnt largest eigenvalues of every tridiagonal (decreasing, into w[0..cnt)), by 32-point multisection in
+// FP64 arithmetic (one warp per eigenvalue).
+template <class R>
+cudaError_t osv_tri_eigvals(const TriDescT<R> *d, int batch, int n, int cnt, cudaStream_t s);
 // Kept eigenvectors (rows mu < nkeep[b] of Y, tridiagonal basis), orthonormalised.  work: 4 n nmax per matrix.
-cudaError_t osv_tri_kept_vectors(const TriDesc *d, int batch, int n, int nmax, const int *nkeep, double *Y,
-                                 double *work, cudaStream_t s);
+template <class R>
+cudaError_t osv_tri_kept_vectors(const TriDescT<R> *d, int batch, int n, int nmax, const int *nkeep, R *Y,
+                                 R *work, cudaStream_t s);
 // rows mu < nrow[b] of V (nmax x n per matrix) <- H V (forward = 0) or H^T V (forward = 1)
-cudaError_t osv_reflect(const TriDesc *d, int batch, int n, int nmax, const int *nrow, double *V, int forward,
+template <class R>
+cudaError_t osv_reflect(const TriDescT<R> *d, int batch, int n, int nmax, const int *nrow, R *V, int forward,
                         cudaStream_t s);
 // rows mu < nkeep[b] of X -= their projection on the orthonormal rows mu < nkeep[b] of Y
-cudaError_t osv_project_out(const int *nkeep, const double *Y, double *X, int batch, int n, int nmax, cudaStream_t s);
-// X row mu = (Tri - w_mu)^{-1} (-R row mu) for mu < nkeep[b], zero rows otherwise
-cudaError_t osv_tri_shift_solve(const TriDesc *d, int batch, int n, int nmax, const int *nkeep, const double *R,
-                                double *X, double *work, cudaStream_t s);
+template <class R>
+cudaError_t osv_project_out(const int *nkeep, const R *Y, R *X, int batch, int n, int nmax, cudaStream_t s);
+// X row mu = (Tri - s_mu)^{-1} (-R row mu) for mu < nkeep[b], zero rows otherwise.  Shift s_mu =
+// shift[b * shift_ld + mu] (FP64) or, with shift == nullptr, the tridiagonal's own w[mu].
+template <class R>
+cudaError_t osv_tri_shift_solve(const TriDescT<R> *d, int batch, int n, int nmax, const int *nkeep, const R *Rin,
+                                R *X, R *work, const double *shift, int shift_ld, cudaStream_t s);
 // Parallel Jacobi eigensolver for symmetric matrices of order <= kJacobiMax (same descriptors and outputs as
 // eigh_batched: w decreasing, eigenvectors as rows of Zt).
 constexpr int kJacobiMax = 112;
 cudaError_t eigh_small_jacobi(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s);
+// Same contract, mixed precisions (FP32 sweeps, FP64 re-orthonormalisation and polishing sweeps) for orders
+// <= kJacobiMixedMax; results to FP64 accuracy.
+constexpr int kJacobiMixedMax = 88;
+cudaError_t eigh_small_jacobi_mixed(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s);
 
 }  // namespace osv

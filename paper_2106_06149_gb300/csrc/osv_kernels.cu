@@ -13,70 +13,37 @@ __global__ void k_f32_to_f64(const float *__restrict__ in, double *__restrict__ 
 
 // T_kk = (ka|kb) / (eps_a + eps_b - 2 f_kk)  (Eq. 6); the Gram product (ka|kb) is already in T.
 // A copy goes to `work` (overwritten by the eigensolver).  Non-finite entries raise the error word.
-__global__ void k_tkk_scale(double *__restrict__ T, double *__restrict__ work, const double *__restrict__ eps,
+template <class W>
+__global__ void k_tkk_scale(double *__restrict__ T, W *__restrict__ work, const double *__restrict__ eps,
                             const double *__restrict__ focc, int n_occ, int nv, int *err) {
     const int k = blockIdx.y;
     const double fkk = focc[(long long)k * n_occ + k];
     const long long nn = (long long)nv * nv;
     double *Tk = T + (long long)k * nn;
-    double *Wk = work + (long long)k * nn;
+    W *Wk = work + (long long)k * nn;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nn;
          idx += (long long)gridDim.x * blockDim.x) {
         const int a = int(idx / nv), b = int(idx % nv);
         const double v = Tk[idx] / (eps[a] + eps[b] - 2.0 * fkk);
-        if (!isfinite(v)) atomicExch(err, kDevNonFinite);
+        if (!isfinite(v)) raise_err(err, kDevNonFinite);
         Tk[idx] = v;
-        Wk[idx] = v;
+        Wk[idx] = (W)v;
     }
 }
 
-// OSV selection: n_k = #(omega > l_osv) capped (or fixed), at least one; Q_k rows = leading eigenvectors,
-// padded rows zero.  Qe = Q scaled by the virtual energies (rows of Q diag(eps)).
-__global__ void k_osv_select(const double *__restrict__ Zt, const double *__restrict__ omega,
-                             const double *__restrict__ eps, double *__restrict__ Q, double *__restrict__ Qe,
-                             int *__restrict__ nosv, int nv, int nmax, double l_osv, int n_fixed) {
-    const int k = blockIdx.x;
-    __shared__ int s_n;
-    if (threadIdx.x == 0) {
-        const double *w = omega + (long long)k * nv;
-        int n;
-        if (n_fixed > 0) {
-            n = min(n_fixed, nv);
-        } else {
-            n = 0;
-            while (n < nv && w[n] > l_osv) ++n;   // eigenvalues are sorted decreasing
-            n = min(n, nmax);
-        }
-        n = max(n, 1);
-        s_n = n;
-        nosv[k] = n;
-    }
-    __syncthreads();
-    const int n = s_n;
-    const double *Z = Zt + (long long)k * nv * nv;
-    double *Qk = Q + (long long)k * nmax * nv;
-    double *Qek = Qe + (long long)k * nmax * nv;
-    for (long long idx = threadIdx.x; idx < (long long)nmax * nv; idx += blockDim.x) {
-        const int mu = int(idx / nv), a = int(idx % nv);
-        const double q = mu < n ? Z[idx] : 0.0;
-        Qk[idx] = q;
-        Qek[idx] = q * eps[a];
-    }
-}
-
-// n_k from the decreasing eigenvalues: #(omega > l_osv) capped at nmax (or fixed), at least one (Eq. 6).
-__global__ void k_osv_count(const double *__restrict__ omega, int *__restrict__ nosv, int n_occ, int nv, int nmax,
+// n_k from the decreasing eigenvalues: #(omega > l_osv) capped at nmax (or fixed), at least one (Eq. 6).  Only
+// the leading nmax eigenvalues (row stride ld) are read.
+__global__ void k_osv_count(const double *__restrict__ omega, int ld, int *__restrict__ nosv, int n_occ, int nmax,
                             double l_osv, int n_fixed) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_occ) return;
-    const double *w = omega + (long long)k * nv;
+    const double *w = omega + (long long)k * ld;
     int n;
     if (n_fixed > 0) {
-        n = min(n_fixed, nv);
+        n = min(n_fixed, nmax);
     } else {
         n = 0;
-        while (n < nv && w[n] > l_osv) ++n;
-        n = min(n, nmax);
+        while (n < nmax && w[n] > l_osv) ++n;
     }
     nosv[k] = max(n, 1);
 }
@@ -146,29 +113,26 @@ cudaError_t launch_f32_to_f64(const float *in, double *out, long long n, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_tkk_scale(double *T, double *work, const double *eps, const double *focc, int n_occ, int nv,
-                             int *err, cudaStream_t s) {
+template <class W>
+cudaError_t launch_tkk_scale(double *T, W *work, const double *eps, const double *focc, int n_occ, int nv, int *err,
+                             cudaStream_t s) {
     if (n_occ <= 0) return cudaSuccess;
     const long long nn = (long long)nv * nv;
     const int bx = (int)std::min<long long>((nn + 255) / 256, 64);
     count_launch();
-    k_tkk_scale<<<dim3(bx, n_occ), 256, 0, s>>>(T, work, eps, focc, n_occ, nv, err);
+    k_tkk_scale<W><<<dim3(bx, n_occ), 256, 0, s>>>(T, work, eps, focc, n_occ, nv, err);
     return cudaGetLastError();
 }
+template cudaError_t launch_tkk_scale<double>(double *, double *, const double *, const double *, int, int, int *,
+                                              cudaStream_t);
+template cudaError_t launch_tkk_scale<float>(double *, float *, const double *, const double *, int, int, int *,
+                                             cudaStream_t);
 
-cudaError_t launch_osv_select(const double *Zt, const double *omega, const double *eps, double *Q, double *Qe,
-                              int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed, cudaStream_t s) {
-    if (n_occ <= 0) return cudaSuccess;
-    count_launch();
-    k_osv_select<<<n_occ, 256, 0, s>>>(Zt, omega, eps, Q, Qe, nosv, nv, nmax, l_osv, n_fixed);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_osv_count(const double *omega, int *nosv, int n_occ, int nv, int nmax, double l_osv, int n_fixed,
+cudaError_t launch_osv_count(const double *omega, int ld, int *nosv, int n_occ, int nmax, double l_osv, int n_fixed,
                              cudaStream_t s) {
     if (n_occ <= 0) return cudaSuccess;
     count_launch();
-    k_osv_count<<<(n_occ + 127) / 128, 128, 0, s>>>(omega, nosv, n_occ, nv, nmax, l_osv, n_fixed);
+    k_osv_count<<<(n_occ + 127) / 128, 128, 0, s>>>(omega, ld, nosv, n_occ, nmax, l_osv, n_fixed);
     return cudaGetLastError();
 }
 

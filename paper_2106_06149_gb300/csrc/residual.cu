@@ -7,6 +7,8 @@
 // with S~ = Phi_ij^T Phi_(other pair) and k running over the cluster's LMOs; the Jacobi update is
 // T~ -= R~ / (e_a + e_b - f_ii - f_jj).  One CTA owns one cluster for all its iterations; the small
 // products run as block-cooperative register-tiled FP64 GEMMs.
+#include <type_traits>
+
 #include "kernels.cuh"
 #include "launch.h"
 
@@ -70,7 +72,87 @@ struct View {
     bool rhs_by_slot;
     const R *S;      // coupling blocks
     R *T, *Rr, *G1;  // per-slot amplitudes, residuals; per-CTA scratch
+    float *sm;       // FP32 path: shared-memory staging (3 x np_max x ld floats)
+    int ld;
 };
+
+// One coupling term in FP32 with its operands staged in shared memory:
+//   R~_p(a, b) -= f sum_c G1(a, c) S~(b, c),  G1 = S~ T~'_q,  S~ = op(Sb) (rp x rq), T~'_q = op(Tq) (rq x rq).
+// sS[c][a] = S~(a, c), sT[c][b] = T~'(c, b), sG[c][a] = G1(a, c); 5 x 5 outputs per thread.
+__device__ void term_f32(int rp, int rq, const float *__restrict__ Sb, long long lds, bool s_trans,
+                         const float *__restrict__ Tq, long long ldt, bool t_trans, float f, float *Rp, long long ldr,
+                         float *sm, int ld) {
+    float *sS = sm, *sT = sm + (long long)ld * ld, *sG = sm + 2LL * ld * ld;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (s_trans) {
+        for (int idx = tid; idx < rp * rq; idx += nt) {
+            const int c = idx / rp, a = idx % rp;
+            sS[c * ld + a] = Sb[(long long)c * lds + a];
+        }
+    } else {
+        for (int idx = tid; idx < rp * rq; idx += nt) {
+            const int a = idx / rq, c = idx % rq;
+            sS[c * ld + a] = Sb[(long long)a * lds + c];
+        }
+    }
+    if (t_trans) {
+        for (int idx = tid; idx < rq * rq; idx += nt) {
+            const int b = idx / rq, c = idx % rq;
+            sT[c * ld + b] = Tq[(long long)b * ldt + c];
+        }
+    } else {
+        for (int idx = tid; idx < rq * rq; idx += nt) {
+            const int c = idx / rq, b = idx % rq;
+            sT[c * ld + b] = Tq[(long long)c * ldt + b];
+        }
+    }
+    __syncthreads();
+    const int ta = (rp + 4) / 5, tq = (rq + 4) / 5;
+    for (int t = tid; t < ta * tq; t += nt) {   // G1 = S~ T~'
+        const int a0 = (t / tq) * 5, b0 = (t % tq) * 5;
+        float acc[5][5] = {};
+        for (int c = 0; c < rq; ++c) {
+            float x[5], y[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                x[i] = sS[c * ld + a0 + i];
+                y[i] = sT[c * ld + b0 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (a0 + i < rp && b0 + j < rq) sG[(b0 + j) * ld + a0 + i] = acc[i][j];
+    }
+    __syncthreads();
+    for (int t = tid; t < ta * ta; t += nt) {   // R~_p -= f G1 S~^T
+        const int a0 = (t / ta) * 5, b0 = (t % ta) * 5;
+        float acc[5][5] = {};
+        for (int c = 0; c < rq; ++c) {
+            float x[5], y[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                x[i] = sG[c * ld + a0 + i];
+                y[i] = sS[c * ld + b0 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (a0 + i < rp && b0 + j < rp) Rp[(long long)(a0 + i) * ldr + b0 + j] -= f * acc[i][j];
+    }
+    __syncthreads();
+}
 
 // R~ = rhs + D o T~ - sum_terms f S~ T~' S~^T for every slot of cluster C (Eq. 4 projected on the
 // pseudo-canonical pair bases); returns max over slots of ||R~||_F.
@@ -100,12 +182,16 @@ __device__ double residual_eval(const SolveArgs &A, const ClusterInfo &C, const 
         const R *Sb = v.S + T.sblk;
         // stored block is (smaller pair id) x (larger pair id)
         const long long lds = T.s_trans ? Pd.np : Ps.np;
-        // G1 = S~_pq T~'_q   (rp x rq)
-        blk_gemm<R>(rp, rq, rq, Sb, lds, T.s_trans, v.T + Ss.t_off, Ps.np, T.t_trans, v.G1, Ps.np, R(1), false);
-        __syncthreads();
-        // R~_p -= f G1 S~_pq^T
-        blk_gemm<R>(rp, rp, rq, v.G1, Ps.np, false, Sb, lds, !T.s_trans, v.Rr + Sd.t_off, Pd.np, -f, true);
-        __syncthreads();
+        if constexpr (std::is_same<R, float>::value) {
+            term_f32(rp, rq, Sb, lds, T.s_trans, v.T + Ss.t_off, Ps.np, T.t_trans, f, v.Rr + Sd.t_off, Pd.np, v.sm, v.ld);
+        } else {
+            // G1 = S~_pq T~'_q   (rp x rq)
+            blk_gemm<R>(rp, rq, rq, Sb, lds, T.s_trans, v.T + Ss.t_off, Ps.np, T.t_trans, v.G1, Ps.np, R(1), false);
+            __syncthreads();
+            // R~_p -= f G1 S~_pq^T
+            blk_gemm<R>(rp, rp, rq, v.G1, Ps.np, false, Sb, lds, !T.s_trans, v.Rr + Sd.t_off, Pd.np, -f, true);
+            __syncthreads();
+        }
     }
     double rmax = 0.0;
     for (int s = C.slot0; s < C.slot1; ++s) {
@@ -163,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
     const int c = A.order[blockIdx.x];
     const ClusterInfo C = A.clusters[c];
     __shared__ double red[kThreads / 32];
-    View<double> v{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride};
+    View<double> v{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride, nullptr, 0};
     bool conv = false;
     int it = 0;
     for (;; ++it) {
@@ -205,8 +291,10 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
     const int c = A.order[blockIdx.x];
     const ClusterInfo C = A.clusters[c];
     __shared__ double red[kThreads / 32];
-    View<float> v32{A.e32, A.Kt32, false, A.sblk32, A.T32, A.R32, A.G1_32 + (long long)blockIdx.x * A.gstride};
-    View<double> v64{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride};
+    extern __shared__ float stage32[];
+    const int ld = (A.np_max + 4) & ~3;
+    View<float> v32{A.e32, A.Kt32, false, A.sblk32, A.T32, A.R32, A.G1_32 + (long long)blockIdx.x * A.gstride, stage32, ld};
+    View<double> v64{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride, nullptr, 0};
     const int tid = threadIdx.x;
     auto zero32 = [&](float *x) {
         for (int s = C.slot0; s < C.slot1; ++s) {
@@ -227,7 +315,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
     __syncthreads();
     bool conv = false;
     int evals = 0;
-    View<float> vc{A.e32, A.H32, true, A.sblk32, A.T32, A.R32, v32.G1};
+    View<float> vc{A.e32, A.H32, true, A.sblk32, A.T32, A.R32, v32.G1, stage32, ld};
     for (int round = 0; round < 8; ++round) {
         const double r64 = residual_eval<double>(A, C, v64, red);
         ++evals;
@@ -314,8 +402,17 @@ __global__ void k_energy_final(const double *__restrict__ Ec, const ClusterInfo 
 cudaError_t launch_residual(const SolveArgs &a, int nclusters, bool mixed, cudaStream_t s) {
     if (nclusters <= 0) return cudaSuccess;
     count_launch();
-    if (mixed) k_residual_mixed<<<nclusters, kThreads, 0, s>>>(a);
-    else k_residual<<<nclusters, kThreads, 0, s>>>(a);
+    if (mixed) {
+        const int ld = (a.np_max + 4) & ~3;
+        const size_t sh = 3 * (size_t)ld * ld * sizeof(float);
+        if (sh > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_residual_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+            if (e != cudaSuccess) return e;
+        }
+        k_residual_mixed<<<nclusters, kThreads, sh, s>>>(a);
+    } else {
+        k_residual<<<nclusters, kThreads, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

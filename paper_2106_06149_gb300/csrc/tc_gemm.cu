@@ -302,11 +302,10 @@ void tc_tiles_free(TcTiles &tt) {
     if (tt.d_tile0) cudaFree(tt.d_tile0);
     if (tt.d_desc) cudaFree(tt.d_desc);
     if (tt.d_exps) cudaFree(tt.d_exps);
-    tt.d_tile0 = nullptr;
-    tt.d_desc = nullptr;
-    tt.d_exps = nullptr;
-    tt.tiles = 0;
-    tt.nprob = 0;
+    if (tt.d_jobs0) cudaFree(tt.d_jobs0);
+    if (tt.d_soff) cudaFree(tt.d_soff);
+    if (tt.d_sjobs0) cudaFree(tt.d_sjobs0);
+    tt = TcTiles{};
 }
 
 }  // namespace osv

@@ -10,6 +10,10 @@ struct TcTiles {
     GemmDesc *d_desc = nullptr;   // exact-slice GEMM: descriptors with scale arrays attached
     int *d_exps = nullptr;
     int nprob = 0;
+    // exact-slice GEMM: slicing jobs (operand tiles) per problem, byte offsets of each problem's A and B slice
+    // images in the scratch buffer, and the scratch size the batch needs
+    long long *d_jobs0 = nullptr, *d_soff = nullptr, *d_sjobs0 = nullptr;
+    long long jobs = 0, scratch_bytes = 0, sjobs = 0;   // sjobs: row-scale jobs (blocks of 32 operand rows)
 };
 
 // per-problem 128 x 64 tile offsets of an uploaded batch
@@ -18,8 +22,9 @@ cudaError_t tc_batch_prepare(GemmBatch &b, TcTiles &tt);
 cudaError_t tc_batch_run(const GemmBatch &b, const TcTiles &tt, int *err, cudaStream_t s);
 void tc_tiles_free(TcTiles &tt);
 
-// Exact-slice BF16x4 GEMM (unbiased, ~24 significant bits): own 128 x 64 tiling, per-row scale arrays.
+// Exact-slice BF16x4 GEMM (unbiased, ~31 significant bits, tc_oz.cu): 128 x 128 tiling, per-row scale arrays,
+// operands pre-sliced into scratch (tt.scratch_bytes, 16-byte aligned, shared by batches run one after another).
 cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt);
-cudaError_t bf16x4_batch_run(const TcTiles &tt, int *err, cudaStream_t s);
+cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err, cudaStream_t s);
 
 }  // namespace osv

@@ -1,0 +1,526 @@
+// Grouped GEMM on tcgen05 tensor cores with exactly accumulated BF16 slices of pre-sliced operands.
+//
+// Each operand row (A: row m over k; B: column n over k) gets a power-of-two scale 2^e with every |element| <=
+// 2^e.  An FP64 element x is rounded (integer arithmetic on its bit pattern, round half away from zero) to
+// N = round(x 2^(31-e)), |N| <= 2^31, and N is cut into four signed base-256 digits
+//   N = s0 2^24 + s1 2^16 + s2 2^8 + s3,   |s_i| <= 128  (exact BF16 values).
+// Slice i is stored as s_i 2^(-8 i) (still exact in BF16), so the product of slices i and j carries its weight
+// 2^(-8 (i + j)) and the tensor core sums the products of one order class directly.  Over a chunk of 256 K:
+//   acc0: i + j = 0      integers, |sum| <= 2^22: exact in FP32;
+//   acc1: i + j = 1      multiples of 2^-8, |sum| <= 2^15: exact;
+//   acc2: i + j = 2      multiples of 2^-16, |sum| < 2^8: exact;
+//   acc3: i + j = 3, 4   (7 products) rounded in FP32 (the tensor core may truncate): an error of a few 2^-24 of
+//                        a term that is itself <= 2^-24 of the result, so below 2^-40 relative even if biased.
+// Products with i + j >= 5 (weight <= 2^-40) are not formed.  After each chunk the accumulators are drained
+// into FP64 registers (exactly for acc0..acc2); the epilogue restores 2^(e_m + e_n - 14).
+//
+// Two kernels per batch: (1) the row scales, then every operand tile (128 rows x 32 K) is sliced once into four
+// 8 KB images already in the canonical no-swizzle K-major shared-memory layout (8 rows x 16 bytes per core
+// matrix; K-adjacent core matrices 128 B apart, 8-row groups 512 B apart); (2) the GEMM: one CTA (256 threads)
+// per 128 x 128 output tile, a three-stage pipeline of 64 KB stages filled by bulk asynchronous copies
+// (cp.async.bulk + mbarrier transaction counts), thread 0 issuing 2 x 13 tcgen05.mma.kind::f16 (M = 128,
+// N = 128, K = 16) per stage into four TMEM accumulators (512 columns).  Every wait is bounded: on expiry the
+// error word is set, in-flight MMAs are waited for (bounded), TMEM is freed and the CTA returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "tc_gemm.h"
+
+namespace osv {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32, NT = 256;
+constexpr int NSLICE = 4;
+constexpr int IMG = BM * BK * 2;                  // 8 KB: one slice of one 128 x 32 tile
+constexpr int TILE_BYTES = NSLICE * IMG;          // 32 KB: the four slices of one operand tile
+constexpr int STAGE = 2 * TILE_BYTES;             // A and B
+constexpr int NSTAGE = 3;
+constexpr int SMEM = NSTAGE * STAGE + 1024;
+constexpr int CHUNK_KT = 8;                       // 256 K per exact chunk
+constexpr int NACC = 4;
+constexpr long long kWaitBudget = 4LL << 30;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t koff(int r, int k) {
+    return (uint32_t)((r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool bwait(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    uint32_t done = 0;
+    while (true) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitBudget) return false;
+    }
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bulk asynchronous copy global -> shared, completion counted on bar (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// exact 2^e as a double for |e| < 1000
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// x = N 2^(e-31) + rounding, N cut into four signed base-256 digits; slice i returned as s_i 2^(-8 i).
+__device__ __forceinline__ void slice4(double x, int e, float *s) {
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    long long n = 0;
+    if (ex != 0) {                                           // zero and subnormal inputs slice to zero
+        const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;   // value = mant 2^(ex-1075)
+        const int sh = 1075 - ex + e - 31;                   // N = mant / 2^sh, sh >= 21 since |x| <= 2^e
+        if (sh < 63) n = (mant + (1LL << (sh - 1))) >> sh;
+        if (bits < 0) n = -n;
+    }
+    const int s0 = (int)((n + (1LL << 23)) >> 24);
+    int r = (int)(n - ((long long)s0 << 24));
+    const int s1 = (r + (1 << 15)) >> 16;
+    r -= s1 << 16;
+    const int s2 = (r + (1 << 7)) >> 8;
+    const int s3 = r - (s2 << 8);
+    s[0] = (float)s0;
+    s[1] = (float)s1 * 3.90625e-3f;
+    s[2] = (float)s2 * 1.52587890625e-5f;
+    s[3] = (float)s3 * 5.9604644775390625e-8f;
+}
+
+__device__ __forceinline__ int scale_exp(double mx) {
+    if (!(mx > 0.0)) return 0;
+    int e;
+    (void)frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1)
+    return e;
+}
+
+__device__ __forceinline__ int find_prob(const long long *__restrict__ pre, int nprob, long long t) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Row / column scales: ea[m] = smallest e with max_k |A(m,k)| <= 2^e (0 for a zero row), eb[n] likewise over
+// B(k, n).  One CTA per block of 32 operand rows (jobs of problem p: its A blocks, then its B blocks unless B
+// shares A's slices).  K-contiguous rows: a warp per row; otherwise the 32 lanes take 32 adjacent rows and the
+// eight warps split K.
+constexpr int SROWS = 32;
+__global__ void __launch_bounds__(256) k_oz_scales(const GemmDesc *__restrict__ descs, const long long *__restrict__ sj0,
+                                                   int nprob) {
+    __shared__ double part[8][SROWS];
+    const long long t = blockIdx.x;
+    const int p = find_prob(sj0, nprob, t);
+    const GemmDesc g = descs[p];
+    const int nba = (g.M + SROWS - 1) / SROWS;
+    int j = (int)(t - sj0[p]);
+    const bool isA = j < nba;
+    if (!isA) j -= nba;
+    const int R = isA ? g.M : g.N;
+    const int r0 = j * SROWS;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const bool kcontig = isA ? g.transA == 0 : g.transB == 1;
+    const int *kidx = isA ? g.k_idx_a : g.k_idx_b;
+    int *out = isA ? g.ea : g.eb;
+    if (kcontig) {
+        for (int r = wid; r < SROWS; r += 8) {
+            const int rr = r0 + r;
+            if (rr >= R) break;
+            const double *row = isA ? g.A + (long long)(g.a_rows ? g.a_rows[rr] : rr) * g.lda
+                                    : g.B + (long long)(g.n_idx_b ? g.n_idx_b[rr] : rr) * g.ldb;
+            double mx = 0.0;
+            for (int k = lane; k < g.K; k += 32) mx = fmax(mx, fabs(row[kidx ? kidx[k] : k]));
+            mx = warp_max(mx);
+            if (lane == 0) out[rr] = scale_exp(mx);
+        }
+        return;
+    }
+    const int rr = r0 + lane;
+    double mx = 0.0;
+    if (rr < R) {
+        const long long rc = isA ? rr : (g.n_idx_b ? g.n_idx_b[rr] : rr);
+        const double *base = isA ? g.A + rc : g.B + rc;
+        const long long ld = isA ? g.lda : g.ldb;
+        for (int k = wid; k < g.K; k += 8) mx = fmax(mx, fabs(base[(long long)(kidx ? kidx[k] : k) * ld]));
+    }
+    part[wid][lane] = mx;
+    __syncthreads();
+    if (wid == 0 && rr < R) {
+        for (int w = 1; w < 8; ++w) mx = fmax(mx, part[w][lane]);
+        out[rr] = scale_exp(mx);
+    }
+}
+
+
+// One CTA per operand tile (128 rows x 32 K): stage the FP64 values in shared memory (coalesced for either
+// operand orientation), then write the four slice images.  Jobs of problem p: its A tiles (row tile major, then
+// K tile), then its B tiles (none when B shares A's slices).
+__global__ void __launch_bounds__(NT) k_oz_slice(const GemmDesc *__restrict__ descs, const long long *__restrict__ jobs0,
+                                                 const long long *__restrict__ soff, int nprob,
+                                                 unsigned char *__restrict__ scratch) {
+    __shared__ double xs[BK][BM + 1];
+    __shared__ int es[BM];
+    const long long t = blockIdx.x;
+    const int p = find_prob(jobs0, nprob, t);
+    const GemmDesc g = descs[p];
+    const int nkt = (g.K + BK - 1) / BK;
+    const int ta = ((g.M + BM - 1) / BM) * nkt;
+    long long j = t - jobs0[p];
+    const bool isA = j < ta;
+    if (!isA) j -= ta;
+    const int rt = (int)(j / nkt), kt = (int)(j % nkt);
+    const int R = isA ? g.M : g.N;
+    const int r0 = rt * BM, k0 = kt * BK;
+    const bool kcontig = isA ? g.transA == 0 : g.transB == 1;
+    const int tid = threadIdx.x;
+    for (int r = tid; r < BM; r += NT) es[r] = r0 + r < R ? (isA ? g.ea[r0 + r] : g.eb[r0 + r]) : 0;
+    auto value = [&](int r, int k) -> double {   // operand element (row r, k) of the tile, zero outside
+        const int rr = r0 + r, kk = k0 + k;
+        if (rr >= R || kk >= g.K) return 0.0;
+        if (isA) {
+            const long long kc = g.k_idx_a ? g.k_idx_a[kk] : kk;
+            return g.transA == 0 ? g.A[(long long)(g.a_rows ? g.a_rows[rr] : rr) * g.lda + kc] : g.A[kc * g.lda + rr];
+        }
+        const long long kr = g.k_idx_b ? g.k_idx_b[kk] : kk;
+        const long long nc = g.n_idx_b ? g.n_idx_b[rr] : rr;
+        return g.transB == 0 ? g.B[kr * g.ldb + nc] : g.B[nc * g.ldb + kr];
+    };
+    if (kcontig) {
+        for (int idx = tid; idx < BM * BK; idx += NT) {   // lanes along k
+            const int r = idx / BK, k = idx % BK;
+            xs[k][r] = value(r, k);
+        }
+    } else {
+        for (int idx = tid; idx < BM * BK; idx += NT) {   // lanes along rows
+            const int k = idx / BM, r = idx % BM;
+            xs[k][r] = value(r, k);
+        }
+    }
+    __syncthreads();
+    unsigned char *img = scratch + soff[2 * p + (isA ? 0 : 1)] + ((long long)rt * nkt + kt) * TILE_BYTES;
+    for (int c = tid; c < BM * (BK / 8); c += NT) {   // one core-matrix row (8 K of one row) per step
+        const int r = c % BM, kg = c / BM;
+        float s[8][NSLICE];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) slice4(xs[kg * 8 + q][r], es[r], s[q]);
+        const uint32_t o = koff(r, kg * 8);
+#pragma unroll
+        for (int i = 0; i < NSLICE; ++i) {
+            __nv_bfloat162 h[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(s[2 * q][i], s[2 * q + 1][i]);
+            *reinterpret_cast<uint4 *>(img + i * IMG + o) = *reinterpret_cast<uint4 *>(h);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ descs,
+                                                  const long long *__restrict__ tile0, const long long *__restrict__ soff,
+                                                  int nprob, const unsigned char *__restrict__ scratch, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], dbar;
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_fail;
+
+    const long long t = blockIdx.x;
+    const int p = find_prob(tile0, nprob, t);
+    const GemmDesc g = descs[p];
+    const long long local = t - tile0[p];
+    const int tiles_n = (g.N + BN - 1) / BN;
+    const int mt = int(local / tiles_n), ntile = int(local % tiles_n);
+    const int m0 = mt * BM, n0 = ntile * BN;
+    const int nkt = (g.K + BK - 1) / BK;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned char *Aimg = scratch + soff[2 * p] + (long long)mt * nkt * TILE_BYTES;
+    const unsigned char *Bimg = scratch + soff[2 * p + 1] + (long long)ntile * nkt * TILE_BYTES;
+
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&dbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_taddr)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t taddr = s_taddr;
+
+    // drain targets: TMEM lanes of warp % 4 (rows), columns 64 * (warp / 4) .. + 63
+    double cacc[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) cacc[j] = 0.0;
+
+    int loaded = 0;   // k-tiles whose copies were issued (thread 0's view)
+    auto load_stage = [&](int kt) {   // thread 0 only
+        const int st = kt % NSTAGE;
+        ++loaded;
+        unsigned char *sA = smem + st * STAGE;
+        expect_tx(&full[st], STAGE);
+        bulk_g2s(sA, Aimg + (long long)kt * TILE_BYTES, TILE_BYTES, &full[st]);
+        bulk_g2s(sA + TILE_BYTES, Bimg + (long long)kt * TILE_BYTES, TILE_BYTES, &full[st]);
+    };
+
+    int issued = 0;   // MMA groups committed (thread 0's view)
+    bool ok = true;
+    if (tid == 0)
+        for (int kt = 0; kt < nkt && kt < NSTAGE - 1; ++kt) load_stage(kt);
+    int chunk = 0;
+    for (int kt = 0; kt < nkt; ++kt) {
+        const int st = kt % NSTAGE;
+        const bool first_of_chunk = (kt % CHUNK_KT) == 0;
+        const bool last_of_chunk = (kt % CHUNK_KT) == CHUNK_KT - 1 || kt == nkt - 1;
+        if (tid == 0 && !s_fail) {
+            if (!bwait(&full[st], (uint32_t)((kt / NSTAGE) & 1))) {
+                raise_err(err, kDevTimeout);
+                s_fail = 1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t a0 = smem_u32(smem + st * STAGE), b0 = a0 + TILE_BYTES;
+#pragma unroll
+                for (int ks = 0; ks < BK / 16; ++ks) {
+                    const uint32_t off = ks * 256;
+                    bool fresh[NACC];
+#pragma unroll
+                    for (int a = 0; a < NACC; ++a) fresh[a] = first_of_chunk && ks == 0;
+#pragma unroll
+                    for (int i = 0; i < NSLICE; ++i)
+#pragma unroll
+                        for (int j = 0; j < NSLICE; ++j) {
+                            const int d = i + j;
+                            if (d > 4) continue;
+                            const int a = d < 3 ? d : 3;
+                            mma_bf16(taddr + (uint32_t)(a * BN), sdesc(a0 + i * IMG + off), sdesc(b0 + j * IMG + off),
+                                     fresh[a] ? 0u : 1u);
+                            fresh[a] = false;
+                        }
+                }
+                commit(&empty[st]);
+                ++issued;
+                // refill the stage that kt - 1 used with kt + 2, once its MMAs are done
+                const int nk = kt + NSTAGE - 1;
+                if (nk < nkt) {
+                    if (kt >= 1 && !bwait(&empty[(kt - 1) % NSTAGE], (uint32_t)(((kt - 1) / NSTAGE) & 1))) {
+                        raise_err(err, kDevTimeout);
+                        s_fail = 1;
+                    } else {
+                        load_stage(nk);
+                    }
+                }
+            }
+        }
+        if (last_of_chunk) {
+            if (tid == 0) commit(&dbar);
+            __syncthreads();
+            if (s_fail) { ok = false; break; }
+            if (!bwait(&dbar, (uint32_t)(chunk & 1))) {
+                raise_err(err, kDevTimeout);
+                s_fail = 1;
+            }
+            __syncthreads();
+            if (s_fail) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t lbase = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
+#pragma unroll
+            for (int a = 0; a < NACC; ++a)
+#pragma unroll
+                for (int c = 0; c < 64; c += 32) {
+                    float v0[16], v1[16];
+                    ld16(lbase + a * BN + c, v0);
+                    ld16(lbase + a * BN + c + 16, v1);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        cacc[c + i] += (double)v0[i];
+                        cacc[c + 16 + i] += (double)v1[i];
+                    }
+                }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            ++chunk;
+        }
+    }
+    if (!ok && tid == 0) {
+        // let every committed MMA group finish before TMEM is released, and every issued copy land before the
+        // shared memory is given up (both bounded)
+        for (int s = 0; s < NSTAGE; ++s) {
+            const int uses = issued / NSTAGE + (s < issued % NSTAGE ? 1 : 0);
+            if (uses > 0) bwait(&empty[s], (uint32_t)((uses - 1) & 1));
+        }
+        for (int kt = issued; kt < loaded; ++kt) bwait(&full[kt % NSTAGE], (uint32_t)((kt / NSTAGE) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr));
+    }
+    if (!ok) return;
+    // epilogue through shared memory (the stage buffers are idle): row-major 128 x 128 tile, coalesced stores
+    double *sC = reinterpret_cast<double *>(smem);
+    constexpr int LDC = BN + 1;
+    {
+        const int r = (warp & 3) * 32 + lane;
+        const int m = m0 + r;
+        const double sa = m < g.M ? pow2(g.ea[m] - 14) : 0.0;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) sC[r * LDC + (warp >> 2) * 64 + j] = cacc[j] * sa;
+    }
+    __syncthreads();
+    for (int r = warp; r < BM; r += NT / 32) {
+        const int m = m0 + r;
+        if (m >= g.M) break;
+        for (int c = lane; c < BN; c += 32) {
+            const int n = n0 + c;
+            if (n >= g.N) break;
+            const double val = g.alpha * (sC[r * LDC + c] * pow2(g.eb[n]));
+            const long long nc = g.n_idx_c ? g.n_idx_c[n] : n;
+            double *cp = g.C + (long long)m * g.ldc + nc;
+            if (g.atomic) atomicAdd(cp, val);
+            else *cp = val + (g.beta != 0.0 ? g.beta * *cp : 0.0);
+        }
+    }
+}
+
+// B shares A's slices when both are the same matrix read with K along its rows: C = X X^T
+bool shares_slices(const GemmDesc &g) {
+    return g.A == g.B && g.M == g.N && g.transA == 0 && g.transB == 1 && g.lda == g.ldb && g.a_rows == nullptr &&
+           g.n_idx_b == nullptr && g.k_idx_a == g.k_idx_b;
+}
+
+}  // namespace
+
+cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
+    tc_tiles_free(tt);
+    if (b.h.empty()) return cudaSuccess;
+    long long tot = 0;
+    for (const GemmDesc &g : b.h) tot += (long long)g.M + g.N;
+    cudaError_t e = cudaMalloc(&tt.d_exps, (size_t)std::max<long long>(tot, 1) * sizeof(int));
+    if (e != cudaSuccess) return e;
+    std::vector<GemmDesc> h = b.h;
+    long long off = 0, bytes = 0;
+    std::vector<long long> t0(h.size() + 1, 0), j0(h.size() + 1, 0), so(2 * h.size(), 0), s0(h.size() + 1, 0);
+    for (size_t i = 0; i < h.size(); ++i) {
+        GemmDesc &g = h[i];
+        const bool share = shares_slices(g);
+        g.ea = tt.d_exps + off;
+        off += g.M;
+        g.eb = share ? g.ea : tt.d_exps + off;
+        off += g.N;
+        const long long nkt = (g.K + BK - 1) / BK;
+        const long long mt = (g.M + BM - 1) / BM, ntl = (g.N + BN - 1) / BN;
+        const long long tiles = (g.M > 0 && g.N > 0) ? mt * ntl : 0;
+        t0[i + 1] = t0[i] + tiles;
+        const long long ja = (g.M > 0 && g.N > 0) ? mt * nkt : 0, jb = (g.M > 0 && g.N > 0 && !share) ? ntl * nkt : 0;
+        j0[i + 1] = j0[i] + ja + jb;
+        s0[i + 1] = s0[i] + (g.M > 0 && g.N > 0 ? (g.M + SROWS - 1) / SROWS + (share ? 0 : (g.N + SROWS - 1) / SROWS) : 0);
+        so[2 * i] = bytes;
+        bytes += ja * TILE_BYTES;
+        so[2 * i + 1] = share ? so[2 * i] : bytes;
+        bytes += jb * TILE_BYTES;
+    }
+    tt.tiles = t0.back();
+    tt.jobs = j0.back();
+    tt.scratch_bytes = bytes;
+    tt.nprob = (int)h.size();
+    if ((e = cudaMalloc(&tt.d_desc, h.size() * sizeof(GemmDesc))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(tt.d_desc, h.data(), h.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&tt.d_tile0, t0.size() * sizeof(long long))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(tt.d_tile0, t0.data(), t0.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&tt.d_jobs0, j0.size() * sizeof(long long))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(tt.d_jobs0, j0.data(), j0.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    if ((e = cudaMalloc(&tt.d_soff, so.size() * sizeof(long long))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(tt.d_soff, so.data(), so.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    tt.sjobs = s0.back();
+    if ((e = cudaMalloc(&tt.d_sjobs0, s0.size() * sizeof(long long))) != cudaSuccess) return e;
+    return cudaMemcpy(tt.d_sjobs0, s0.data(), s0.size() * sizeof(long long), cudaMemcpyHostToDevice);
+}
+
+cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err, cudaStream_t s) {
+    if (tt.tiles == 0) return cudaSuccess;
+    if (!scratch) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    cudaError_t e;
+    if (tt.sjobs > 0) {
+        count_launch();
+        k_oz_scales<<<(unsigned)tt.sjobs, 256, 0, s>>>(tt.d_desc, tt.d_sjobs0, tt.nprob);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (tt.jobs > 0) {
+        count_launch();
+        k_oz_slice<<<(unsigned)tt.jobs, NT, 0, s>>>(tt.d_desc, tt.d_jobs0, tt.d_soff, tt.nprob, scratch);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    count_launch();
+    k_oz_gemm<<<(unsigned)tt.tiles, NT, SMEM, s>>>(tt.d_desc, tt.d_tile0, tt.d_soff, tt.nprob, scratch, err);
+    return cudaGetLastError();
+}
+
+}  // namespace osv

@@ -76,3 +76,30 @@ def test_bf16x4_bench_workload(osvmbe):
           f"max|d dB| = {gb:.3e} (max|dB| {np.abs(f['dB']).max():.3e}), max|d dF| = {gf:.3e}")
     assert abs(dE) <= 1e-6
     assert gb <= 1e-6 and gf <= 1e-6
+
+
+@pytest.mark.parametrize("fixed", [0, 7])
+def test_mixed_osv_eigenpairs_match_fp64(osvmbe, fixed):
+    """FP32 tridiagonal route + FP64 Rayleigh-Ritz refinement: the n_max leading eigenvalues of every T_kk and
+    the OSV counts equal the FP64 route's to the accuracy of the mixed T_kk itself (its Gram products come from
+    the exact-slice BF16x4 GEMM: ~2^-31 relative per entry, hence ~1e-9 of the largest eigenvalue); the
+    remaining eigenvalues are FP32-accurate."""
+    p = make_problem(8, 120, 300, seed=61)
+    prm = dict(n_osv_max=20, n_osv_fixed=fixed, l_osv=3e-3, mbe_order=3, r2b=6.0, r3b=5.0)
+    out = {}
+    for prec in (0, 2):
+        dp = osvmbe.DeviceProblem.from_host(p)
+        ctx = osvmbe.Context()
+        ctx.clusters_build(dp, Params(**prm, precision=prec))
+        counts = ctx.osv_build(dp, Params(**prm, precision=prec), want_counts=True)
+        out[prec] = (counts, np.array([ctx.eigenvalues(k, p.n_vir) for k in range(p.n_occ)]))
+        ctx.close()
+    nm = fixed if fixed else 20
+    assert (out[0][0] == out[2][0]).all()
+    w64, wmx = out[0][1], out[2][1]
+    scale = np.abs(w64).max()
+    lead = np.abs(wmx[:, :nm] - w64[:, :nm]).max() / scale
+    rest = np.abs(wmx[:, nm:] - w64[:, nm:]).max() / scale
+    print(f"\nleading eigenvalues rel diff {lead:.2e}; rest {rest:.2e}; counts {out[0][0]}")
+    assert lead <= 2e-9
+    assert rest <= 1e-5
