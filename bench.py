@@ -228,7 +228,7 @@ def run_gpu(args):
     # ---- roofline of the dominant stage
     total_stage = sum(v[0] for v in stages.values())
     dom = max(stages.items(), key=lambda kv: kv[1][0])
-    roof = roofline(dom, stages, flops_step, p, prm)
+    roof = roofline(dom, stages, flops_step, p, prm, ctx.adjoint_flops())
     roof_tc = tensor_roofline(stages, p, prm) if prec > 0 else None
 
     out = {
@@ -283,7 +283,7 @@ def ctypes_launches(osvmbe):
     return n.value
 
 
-def stage_flops(name, p, prm, flops_step):
+def stage_flops(name, p, prm, flops_step, adj_flops=None):
     """Algorithmic FLOPs of one launch of a stage (FP64 work of the method, padding excluded)."""
     nv, na, n, nm = p.n_vir, p.n_aux, p.n_occ, prm.n_osv_max if prm.n_osv_fixed <= 0 else prm.n_osv_fixed
     d = np.linalg.norm(p.centres[:, None, :] - p.centres[None, :, :], axis=-1)
@@ -291,6 +291,8 @@ def stage_flops(name, p, prm, flops_step):
     a = np.diff(p.aux_ptr)
     if name == "residual":
         return flops_step
+    if name == "adj_clusters":
+        return adj_flops
     if name == "tkk_gram":
         return float(np.sum(2.0 * nv * nv * a))
     if name == "half_transform":
@@ -302,17 +304,17 @@ def stage_flops(name, p, prm, flops_step):
 
 def tensor_roofline(stages, p, prm):
     """The tcgen05 GEMM of the T_kk Gram products: issued tensor FLOPs vs the measured dense BF16 peak (each useful
-    multiply-add costs 16 BF16 slice products in the exact-slice mode, 3 TF32 products (at half the BF16 rate)
-    in the split-TF32 mode); useful FLOPs reported beside it."""
+    multiply-add costs 13 BF16 slice products in the exact-slice mode, 3 TF32 products (at half the BF16 rate)
+    in the split-TF32 mode); useful FLOPs reported beside it.  The stage time includes the slicing passes."""
     if "tkk_gram" not in stages:
         return None
     ms_total, calls = stages["tkk_gram"]
     avg = ms_total / calls
     useful = stage_flops("tkk_gram", p, prm, 0.0)
-    mult = 16.0 if prm.precision == 2 else 6.0
+    mult = 13.0 if prm.precision == 2 else 6.0
     peak = measured_peak("bf16_tflops", 1949.0)
     issued = useful * mult / (avg * 1e-3) / 1e12
-    return {"bound": "tensor", "stage": "tkk_gram", "kernel": "k_gemm_bf16x4" if prm.precision == 2 else "k_gemm_tf32x3",
+    return {"bound": "tensor", "stage": "tkk_gram", "kernel": "k_oz_gemm" if prm.precision == 2 else "k_gemm_tf32x3",
             "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak, "traffic": None,
             "useful_tflops": useful / (avg * 1e-3) / 1e12, "avg_launch_ms": avg,
             "peak_note": "measured dense bf16 (burst); achieved counts issued BF16-equivalent slice products"}
@@ -326,11 +328,11 @@ def measured_peak(key, fallback):
         return fallback
 
 
-def roofline(dom, stages, flops_step, p, prm):
+def roofline(dom, stages, flops_step, p, prm, adj_flops=None):
     """FP64 ALU roofline of the dominant stage (CUDA-core FP64; peak from unit counts and clock)."""
     name, (ms_total, calls) = dom
     avg_ms = ms_total / calls
-    flops = stage_flops(name, p, prm, flops_step)
+    flops = stage_flops(name, p, prm, flops_step, adj_flops)
     if not flops:
         return {"bound": "alu", "stage": name, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": None, "traffic": None}

@@ -153,6 +153,12 @@ osv_status osv_profile_read(osv_ctx *ctx, int max_stages, char *names, double *m
  * counted.  HOST *flops. */
 osv_status osv_residual_flops(osv_ctx *ctx, double *flops);
 
+/* Algorithmic FLOPs of the per-cluster partials of gradient_backward (the densities of Eqs. 14-16, 33-34 in
+ * the pseudo-canonical pair bases), for the clusters of the last solve with a non-zero MBE weight: per pair of
+ * order r, 8 r^3 (Tb L T^T + T^T L Tb and Tb T^T + T^T Tb); per coupling term (r_p, r_q),
+ * 4 r_p^2 r_q + 6 r_p r_q^2.  Synchronises.  HOST *flops. */
+osv_status osv_adjoint_flops(osv_ctx *ctx, double *flops);
+
 /* Process-wide number of CUDA kernel launches issued by this library so far (HOST *count). */
 osv_status osv_kernel_launches(long long *count);
 

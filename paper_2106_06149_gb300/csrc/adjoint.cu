@@ -178,6 +178,213 @@ __global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
     }
 }
 
+// ------------------------------------------------------------------------ double-float (FP32 pair) version
+// The same partials in "double-float" arithmetic on the FP32 pipe (on GB300 an FP64 multiply-add issues at 1/64
+// of the FP32 rate): every operand is split once into a pair of FP32 numbers (hi + lo, ~48 significant bits),
+// a product is formed exactly (hi*hi and its FMA error term) plus the cross terms, and sums are kept as
+// (hi, lo) pairs with an error-free two-sum.  ~12 FP32 operations per FP64 multiply-add, relative error
+// ~2^-44 per partial (the FP64 version: 2^-53; the gradient bar is ~1e-7 relative).
+// Shared memory: four np_max x ld buffers of float2: slot phase B0 = T, B1 = Tb, B2 = Tb L, B3 = L T (L =
+// diag(e)); term phase B0 = S~, B1 = Tb_p then T~'_q, B2 = U1 = Tb S~, B3 = U2 = Tb^T S~.
+constexpr int kAT = 256;
+
+struct AdjArgsS {
+    const ClusterInfo *clusters;
+    const int *order;
+    const Slot *slots;
+    const Term *terms;
+    const PairInfo *pairs;
+    const int *rdim;
+    const double *focc, *e, *Tslot, *Stil;
+    int n_occ, ncl, ld;
+    double *GS, *GF, *GSc, *dF;
+};
+
+__global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
+    extern __shared__ float2 smf[];
+    const int ld = A.ld;
+    const long long sq = (long long)ld * ld;
+    float2 *B0 = smf, *B1 = smf + sq, *B2 = smf + 2 * sq, *B3 = smf + 3 * sq;
+    __shared__ double red[kAT / 32];
+    const int tid = threadIdx.x;
+    for (int q = blockIdx.x; q < A.ncl; q += gridDim.x) {
+        const int c = A.order[q];
+        const ClusterInfo C = A.clusters[c];
+        if (C.weight == 0) continue;
+        const double w = (double)C.weight;
+        for (int s = C.slot0; s < C.slot1; ++s) {
+            const Slot S = A.slots[s];
+            const PairInfo P = A.pairs[S.pair];
+            const int r = A.rdim[S.pair], np = P.np;
+            const double *T = A.Tslot + S.t_off;
+            const double *e = A.e + P.e_off;
+            const double fii = A.focc[(long long)P.i * A.n_occ + P.i], fjj = A.focc[(long long)P.j * A.n_occ + P.j];
+            double tt = 0.0;
+            for (int idx = tid; idx < r * r; idx += kAT) {
+                const int a = idx / r, b = idx % r;
+                const double t = T[(long long)a * np + b], tb = 2.0 * t - T[(long long)b * np + a];
+                B0[a * ld + b] = split_df(t);
+                B1[a * ld + b] = split_df(tb);
+                B2[a * ld + b] = split_df(tb * e[b]);   // Tb L
+                B3[a * ld + b] = split_df(e[a] * t);    // L T
+                tt += t * tb;
+            }
+            tt = block_sum(tt, red);   // also orders the staging writes before the products
+            const double wm = w * S.mult;
+            if (tid == 0) {
+                atomicAdd(&A.dF[(long long)P.i * A.n_occ + P.i], -wm * tt);
+                atomicAdd(&A.dF[(long long)P.j * A.n_occ + P.j], -wm * tt);
+            }
+            // M1 = (Tb L) T^T + (L T)^T Tb ;  M2 = Tb T^T + T^T Tb
+            const int tr = (r + 3) >> 2;
+            for (int t = tid; t < tr * tr; t += kAT) {
+                const int a0 = (t / tr) << 2, b0 = (t % tr) << 2;
+                float m1h[4][4] = {}, m1l[4][4] = {}, m2h[4][4] = {}, m2l[4][4] = {};
+                for (int k = 0; k < r; ++k) {
+                    float2 x[4], xl[4], y[4], u[4], ul[4], v[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int a = min(a0 + i, r - 1), b = min(b0 + i, r - 1);
+                        x[i] = B1[a * ld + k];    // Tb(a, k)
+                        xl[i] = B2[a * ld + k];   // (Tb L)(a, k)
+                        y[i] = B0[b * ld + k];    // T(b, k)
+                        u[i] = B0[k * ld + a];    // T(k, a)
+                        ul[i] = B3[k * ld + a];   // (L T)(k, a)
+                        v[i] = B1[k * ld + b];    // Tb(k, b)
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            df_fma(m1h[i][j], m1l[i][j], xl[i], y[j]);
+                            df_fma(m1h[i][j], m1l[i][j], ul[i], v[j]);
+                            df_fma(m2h[i][j], m2l[i][j], x[i], y[j]);
+                            df_fma(m2h[i][j], m2l[i][j], u[i], v[j]);
+                        }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int a = a0 + i, b = b0 + j;
+                        if (a >= r || b >= r) continue;
+                        const long long o = (long long)a * np + b;
+                        const double m1 = df_val(m1h[i][j], m1l[i][j]), m2 = df_val(m2h[i][j], m2l[i][j]);
+                        atomicAdd(&A.GS[P.off + o], wm * (m1 - (fii + fjj) * m2));
+                        atomicAdd(&A.GF[P.off + o], wm * m2);
+                    }
+            }
+            __syncthreads();
+        }
+        for (int t = C.term0; t < C.term1; ++t) {
+            const Term Tm = A.terms[t];
+            const Slot Sd = A.slots[Tm.dst], Ssl = A.slots[Tm.src];
+            const PairInfo Pd = A.pairs[Sd.pair], Ps = A.pairs[Ssl.pair];
+            const int rp = A.rdim[Sd.pair], rq = A.rdim[Ssl.pair];
+            const int np = Pd.np, nq = Ps.np;
+            const double f = A.focc[(long long)Tm.fx * A.n_occ + Tm.fy];
+            const double *Sb = A.Stil + Tm.sblk;
+            const long long lds = Tm.s_trans ? np : nq;
+            const double *Tq = A.Tslot + Ssl.t_off, *Tp = A.Tslot + Sd.t_off;
+            const double wm = w * Sd.mult;
+            // B0 = S~ (rp x rq), B1 = Tb_p
+            for (int idx = tid; idx < rp * rq; idx += kAT) {
+                const int a = idx / rq, b = idx % rq;
+                B0[a * ld + b] = split_df(Tm.s_trans ? Sb[(long long)b * lds + a] : Sb[(long long)a * lds + b]);
+            }
+            for (int idx = tid; idx < rp * rp; idx += kAT) {
+                const int a = idx / rp, b = idx % rp;
+                B1[a * ld + b] = split_df(2.0 * Tp[(long long)a * np + b] - Tp[(long long)b * np + a]);
+            }
+            __syncthreads();
+            // U1 = Tb S (B2), U2 = Tb^T S (B3)
+            const int ta = (rp + 3) >> 2, tq = (rq + 3) >> 2;
+            for (int t2 = tid; t2 < ta * tq; t2 += kAT) {
+                const int a0 = (t2 / tq) << 2, b0 = (t2 % tq) << 2;
+                float u1h[4][4] = {}, u1l[4][4] = {}, u2h[4][4] = {}, u2l[4][4] = {};
+                for (int k = 0; k < rp; ++k) {
+                    float2 x[4], xt[4], y[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int a = min(a0 + i, rp - 1), b = min(b0 + i, rq - 1);
+                        x[i] = B1[a * ld + k];
+                        xt[i] = B1[k * ld + a];
+                        y[i] = B0[k * ld + b];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            df_fma(u1h[i][j], u1l[i][j], x[i], y[j]);
+                            df_fma(u2h[i][j], u2l[i][j], xt[i], y[j]);
+                        }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (a0 + i < rp && b0 + j < rq) {   // renormalised pairs
+                            const float h1 = __fadd_rn(u1h[i][j], u1l[i][j]), h2 = __fadd_rn(u2h[i][j], u2l[i][j]);
+                            B2[(a0 + i) * ld + b0 + j] = make_float2(h1, __fsub_rn(u1l[i][j], __fsub_rn(h1, u1h[i][j])));
+                            B3[(a0 + i) * ld + b0 + j] = make_float2(h2, __fsub_rn(u2l[i][j], __fsub_rn(h2, u2h[i][j])));
+                        }
+            }
+            __syncthreads();
+            // B1 = T~'_q (rq x rq)
+            for (int idx = tid; idx < rq * rq; idx += kAT) {
+                const int a = idx / rq, b = idx % rq;
+                B1[a * ld + b] = split_df(Tm.t_trans ? Tq[(long long)b * nq + a] : Tq[(long long)a * nq + b]);
+            }
+            __syncthreads();
+            // x = <S T', U1>;  M2 = U1 T'^T + U2 T'
+            double xs = 0.0;
+            double *G = A.GSc + Tm.sblk;
+            for (int t2 = tid; t2 < ta * tq; t2 += kAT) {
+                const int a0 = (t2 / tq) << 2, b0 = (t2 % tq) << 2;
+                float m1h[4][4] = {}, m1l[4][4] = {}, m2h[4][4] = {}, m2l[4][4] = {};
+                for (int k = 0; k < rq; ++k) {
+                    float2 sv[4], p1[4], p2[4], tv[4], tw[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int a = min(a0 + i, rp - 1), b = min(b0 + i, rq - 1);
+                        sv[i] = B0[a * ld + k];   // S(a, k)
+                        p1[i] = B2[a * ld + k];   // U1(a, k)
+                        p2[i] = B3[a * ld + k];   // U2(a, k)
+                        tv[i] = B1[k * ld + b];   // T'(k, b)
+                        tw[i] = B1[b * ld + k];   // T'(b, k)
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            df_fma(m1h[i][j], m1l[i][j], sv[i], tv[j]);
+                            df_fma(m2h[i][j], m2l[i][j], p1[i], tw[j]);
+                            df_fma(m2h[i][j], m2l[i][j], p2[i], tv[j]);
+                        }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int a = a0 + i, b = b0 + j;
+                        if (a >= rp || b >= rq) continue;
+                        const float2 u1 = B2[a * ld + b];
+                        xs += df_val(m1h[i][j], m1l[i][j]) * df_val(u1.x, u1.y);
+                        const double v = -wm * f * df_val(m2h[i][j], m2l[i][j]);
+                        if (Tm.s_trans) atomicAdd(&G[(long long)b * np + a], v);   // stored as (src pair) x (dst pair)
+                        else atomicAdd(&G[(long long)a * nq + b], v);
+                    }
+            }
+            xs = block_sum(xs, red);
+            if (tid == 0) {
+                atomicAdd(&A.dF[(long long)Tm.fx * A.n_occ + Tm.fy], -w * xs);
+                if (Pd.i != Pd.j) atomicAdd(&A.dF[(long long)Tm.fy * A.n_occ + Tm.fx], -w * xs);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // dE/dK~ per pair: 2 m (2 Tc - Tc^T) (collective amplitudes)
 __global__ void k_gk_tilde(const PairInfo *__restrict__ pairs, const double *__restrict__ Tc,
                            double *__restrict__ out) {
@@ -503,7 +710,16 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
     {
         StageTimer t(c, "adj_clusters");
         // FP64 in every mode: FP32 products here cost ~7e-7 relative in dE/dB, too much for a 1e-6 bar
-        if (grid > 0) {
+        const int ld = 2 * nm + 1;
+        const size_t sh = 4 * (size_t)ld * ld * sizeof(float2);
+        if (c.osv_mixed && !c.cl.empty() && sh <= 216 * 1024) {
+            // mixed modes: double-float products on the FP32 pipe
+            CK(cudaFuncSetAttribute(k_cluster_adjoint_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+            AdjArgsS as{c.cinfo.d, c.order.d, c.slots.d, c.terms.d, c.pinfo.d, c.rdim, c.focc, c.pe, c.Tslot, c.Stil,
+                        n, (int)c.cl.size(), ld, GS, GF, GSc, dF64};
+            count_launch();
+            k_cluster_adjoint_df<<<(int)std::min<size_t>(c.cl.size(), 152), kAT, sh, s>>>(as);
+        } else if (grid > 0) {
             count_launch();
             k_cluster_adjoint<double><<<grid, kThreads, 0, s>>>(a);
         }
@@ -513,7 +729,7 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
         StageTimer t(c, "adj_pair_blocks");
         if (!c.pairs.empty()) { count_launch(); k_gk_tilde<<<(unsigned)c.pairs.size(), kThreads, 0, s>>>(c.pinfo.d, c.Tc, GK); }
         CK(cudaGetLastError());
-        for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2}) CK(gemm_batch_run(*g, s));
+        for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2}) CK(c.run_small(*g));
         CK(launch_block_copy(bc_hs.d, (int)bc_hs.h.size(), s));
     }
     {

@@ -719,7 +719,7 @@ osv_status run_osv_build(osv_ctx *c) {
     }
     {
         StageTimer t(*c, "sf_blocks");
-        CK(gemm_batch_run(c->gb_sf, s), "s/f blocks");
+        CK(c->run_small(c->gb_sf), "s/f blocks");
     }
     {
         StageTimer t(*c, "half_transform");
@@ -743,19 +743,19 @@ osv_status run_osv_build(osv_ctx *c) {
         CK(launch_block_copy(c->bc_pair.d, (int)c->bc_pair.h.size(), s), "pair assemble");
         CK(pair_eigh(c->eig_s), "pair overlap eigh");
         CK(launch_pair_x(c->pinfo.d, (int)c->pairs.size(), c->Sp, c->sw, c->X, c->rdim, c->prm.tau_red, s), "pair x");
-        CK(gemm_batch_run(c->gb_fx1, s), "fx1");
-        CK(gemm_batch_run(c->gb_fx2, s), "fx2");
+        CK(c->run_small(c->gb_fx1), "fx1");
+        CK(c->run_small(c->gb_fx2), "fx2");
         CK(pair_eigh(c->eig_f), "pair fock eigh");
         CK(launch_clean_w(c->pinfo.d, (int)c->pairs.size(), c->rdim, c->Fx, c->pe, s), "clean");
-        CK(gemm_batch_run(c->gb_v, s), "V");
+        CK(c->run_small(c->gb_v), "V");
     }
     {
         StageTimer t(*c, "pair_transform");
-        CK(gemm_batch_run(c->gb_kt1, s), "kt1");
-        CK(gemm_batch_run(c->gb_kt2, s), "kt2");
+        CK(c->run_small(c->gb_kt1), "kt1");
+        CK(c->run_small(c->gb_kt2), "kt2");
         CK(launch_block_copy(c->bc_coup.d, (int)c->bc_coup.h.size(), s), "coupling assemble");
-        CK(gemm_batch_run(c->gb_c1, s), "c1");
-        CK(gemm_batch_run(c->gb_c2, s), "c2");
+        CK(c->run_small(c->gb_c1), "c1");
+        CK(c->run_small(c->gb_c2), "c2");
         if (c->prm.precision != OSV_FP64) {   // FP32 copies for the mixed residual iterations
             CK(launch_to_f32(c->pe, c->e32, c->pair_vec, s), "e32");
             CK(launch_to_f32(c->Kt, c->Kt32, c->pair_mat, s), "Kt32");
@@ -1057,6 +1057,32 @@ osv_status osv_residual_flops(osv_ctx *c, double *flops) {
             per += 2.0 * (rp * rq * rq + rp * rp * rq);
         }
         total += per * evals;
+    }
+    *flops = total;
+    return OSV_OK;
+}
+
+osv_status osv_adjoint_flops(osv_ctx *c, double *flops) {
+    if (!c || !flops) return OSV_ERR_INVALID;
+    if (!c->solved) return c->fail(OSV_ERR_INVALID, "no solved clusters");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sync");
+    std::vector<int> r(c->pairs.size());
+    if ((e = cudaMemcpy(r.data(), c->rdim, r.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy");
+    double total = 0.0;
+    for (size_t q = 0; q < c->cl.size(); ++q) {
+        const ClusterInfo &C = c->cinfo.h[q];
+        if (C.weight == 0) continue;
+        for (int s = C.slot0; s < C.slot1; ++s) {
+            const double rp = r[c->slots.h[s].pair];
+            total += 8.0 * rp * rp * rp;
+        }
+        for (int t = C.term0; t < C.term1; ++t) {
+            const double rp = r[c->slots.h[c->terms.h[t].dst].pair], rq = r[c->slots.h[c->terms.h[t].src].pair];
+            total += 4.0 * rp * rp * rq + 6.0 * rp * rq * rq;
+        }
     }
     *flops = total;
     return OSV_OK;

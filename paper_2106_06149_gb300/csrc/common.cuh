@@ -58,6 +58,56 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     return s;
 }
 
+// ---------------------------------------------------------------------------- double-float arithmetic
+// "Double-float": a value held as an unevaluated sum of two FP32 numbers (hi + lo, ~48 significant bits).  On
+// GB300 an FP64 multiply-add issues at 1/64 of the FP32 rate, so FP64-accurate products of the mixed path run
+// as double-float on the FP32 pipe (~12 FP32 operations per multiply-add).
+// x ~ hi + lo with hi = x cut to 24 significant bits and lo the rest rounded to FP32, by integer operations
+// (a double -> float conversion runs on the FP64 pipe).  Zero / subnormal / out-of-FP32-range values use the
+// plain conversion.
+__device__ __forceinline__ float2 split_df(double x) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    const int ef = ex - 1023 + 127;
+    if (ex == 0 || ef < 53 || ef > 254) return make_float2((float)x, 0.f);   // |x| < 2^-74: lo negligible
+    const unsigned sign = (unsigned)((unsigned long long)b >> 63) << 31;
+    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7FFFFF));
+    const long long mlo = b & ((1LL << 29) - 1);   // value mlo 2^(ex - 1075)
+    float lo = __ll2float_rn(mlo) * __uint_as_float((unsigned)(ef - 52) << 23);
+    if (sign) lo = -lo;
+    return make_float2(hi, lo);
+}
+
+// (sh, sl) += a * b for double-float a, b
+__device__ __forceinline__ void df_fma(float &sh, float &sl, const float2 a, const float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    const float e = fmaf(a.x, b.x, -p);
+    const float c = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    const float t = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, c));
+}
+
+// (hi, lo) += x with Knuth's two-sum (exact error term)
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+__device__ __forceinline__ float2 df_mul(const float2 a, const float2 b) {
+    float h = 0.f, l = 0.f;
+    df_fma(h, l, a, b);
+    return make_float2(h, l);
+}
+
+__device__ __forceinline__ double df_val(float h, float l) { return (double)h + (double)l; }
+
+
 // ------------------------------------------------------------------------------------ grouped FP64 GEMM
 // C[M x N] = alpha * opA(A)[M x K] * opB(B)[K x N] + beta * C, every matrix row-major.
 //   transA = 0: A(m,k) = A[arow(m) * lda + acol(k)],  transA = 1: A(m,k) = A[acol(k) * lda + m]
@@ -94,6 +144,8 @@ struct GemmBatch {
 
 cudaError_t gemm_batch_upload(GemmBatch &b);
 cudaError_t gemm_batch_run(const GemmBatch &b, cudaStream_t s);
+// the same batch in double-float arithmetic on the FP32 pipe (~2^-44 relative)
+cudaError_t gemm_batch_run_df(const GemmBatch &b, cudaStream_t s);
 void gemm_batch_free(GemmBatch &b);
 
 inline GemmDesc gemm(int M, int N, int K, const double *A, long long lda, int tA, const double *B,

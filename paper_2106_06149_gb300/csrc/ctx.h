@@ -145,6 +145,12 @@ struct osv_ctx {
         if (prm.precision == OSV_MIXED_BF16X4) return osv::bf16x4_batch_run(oz, oz_scratch, derr, stream);
         return osv::gemm_batch_run(b, stream);
     }
+    // the small FP64-accurate GEMM batches (pair and refinement blocks): FP64 CUDA cores, or double-float on the
+    // FP32 pipe in the mixed modes
+    cudaError_t run_small(const GemmBatch &b) {
+        if (prm.precision != OSV_FP64) return osv::gemm_batch_run_df(b, stream);
+        return osv::gemm_batch_run(b, stream);
+    }
     // slice images of the exact-slice GEMM batches (one buffer, grown to the largest batch)
     unsigned char *oz_scratch = nullptr;
     size_t oz_cap = 0;

@@ -109,7 +109,113 @@ __global__ void __launch_bounds__(NT) k_gemm_fp64(const GemmDesc *__restrict__ d
     }
 }
 
+// The same grouped GEMM in double-float arithmetic (mixed modes): operands split into FP32 (hi, lo) pairs by
+// integer operations while staged, products and sums on the FP32 pipe (common.cuh); ~2^-44 relative.  Same
+// descriptors and tiling as k_gemm_fp64.
+__global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ descs,
+                                                 const long long *__restrict__ tile0, int nprob) {
+    const long long t = blockIdx.x;
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const GemmDesc g = descs[lo];
+    const long long local = t - tile0[lo];
+    const int tiles_n = (g.N + BN - 1) / BN;
+    const int m0 = int(local / tiles_n) * BM, n0 = int(local % tiles_n) * BN;
+
+    __shared__ float2 As[2][BK][BM + 1];
+    __shared__ float2 Bs[2][BK][BN + 1];
+
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tc = tid % 16;
+    float ah[4][4], al[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ah[a][b] = al[a][b] = 0.f;
+
+    auto load = [&](int buf, int k0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + r * NT;
+            int mm, kk;
+            if (g.transA == 0) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
+            const int m = m0 + mm, k = k0 + kk;
+            double v = 0.0;
+            if (m < g.M && k < g.K) {
+                const long long kc = g.k_idx_a ? g.k_idx_a[k] : k;
+                if (g.transA == 0) {
+                    const long long mr = g.a_rows ? g.a_rows[m] : m;
+                    v = g.A[mr * g.lda + kc];
+                } else {
+                    v = g.A[kc * g.lda + m];
+                }
+            }
+            As[buf][kk][mm] = split_df(v);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = tid + r * NT;
+            int kk, nn;
+            if (g.transB == 0) { kk = e / BN; nn = e % BN; } else { nn = e / BK; kk = e % BK; }
+            const int n = n0 + nn, k = k0 + kk;
+            double v = 0.0;
+            if (n < g.N && k < g.K) {
+                const long long kr = g.k_idx_b ? g.k_idx_b[k] : k;
+                const long long nc = g.n_idx_b ? g.n_idx_b[n] : n;
+                v = (g.transB == 0) ? g.B[kr * g.ldb + nc] : g.B[nc * g.ldb + kr];
+            }
+            Bs[buf][kk][nn] = split_df(v);
+        }
+    };
+
+    const int nk = (g.K + BK - 1) / BK;
+    if (nk > 0) load(0, 0);
+    __syncthreads();
+    for (int kt = 0; kt < nk; ++kt) {
+        const int buf = kt & 1;
+        if (kt + 1 < nk) load(buf ^ 1, (kt + 1) * BK);
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tr + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tc + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) df_fma(ah[i][j], al[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + tr + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tc + 16 * j;
+            if (n >= g.N) continue;
+            const long long nc = g.n_idx_c ? g.n_idx_c[n] : n;
+            double *c = g.C + (long long)m * g.ldc + nc;
+            const double v = df_val(ah[i][j], al[i][j]);
+            if (g.atomic) atomicAdd(c, g.alpha * v);
+            else *c = g.alpha * v + (g.beta != 0.0 ? g.beta * *c : 0.0);
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t gemm_batch_run_df(const GemmBatch &b, cudaStream_t s) {
+    if (b.tiles == 0) return cudaSuccess;
+    count_launch();
+    k_gemm_df<<<(unsigned)b.tiles, NT, 0, s>>>(b.d_desc, b.d_tile0, (int)b.h.size());
+    return cudaGetLastError();
+}
 
 cudaError_t gemm_batch_upload(GemmBatch &b) {
     gemm_batch_free(b);

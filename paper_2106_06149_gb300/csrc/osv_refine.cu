@@ -214,8 +214,8 @@ cudaError_t apply_precond(const OsvRefine &r, int n, int nv, int nm, const int *
 
 cudaError_t rayleigh_ritz(const OsvRefine &r, int x, int n, int nm, int *err, cudaStream_t s) {
     cudaError_t e;
-    if ((e = gemm_batch_run(r.gb_w[x], s)) != cudaSuccess) return e;
-    if ((e = gemm_batch_run(r.gb_gh[x], s)) != cudaSuccess) return e;
+    if ((e = gemm_batch_run_df(r.gb_w[x], s)) != cudaSuccess) return e;
+    if ((e = gemm_batch_run_df(r.gb_gh[x], s)) != cudaSuccess) return e;
     const size_t sh = rr_smem_bytes(nm);
     if (sh > 48 * 1024 && (e = cudaFuncSetAttribute(k_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh)) != cudaSuccess)
         return e;
@@ -248,7 +248,7 @@ cudaError_t osv_mixed_eigh(const OsvRefine &r, int n, int nv, int nm, double *Q,
     for (int it = 0; it < steps; ++it) {
         const int x = it & 1, y = x ^ 1;
         CK(rayleigh_ritz(r, x, n, nm, err, s));
-        CK(gemm_batch_run(r.gb_rot[x], s));
+        CK(gemm_batch_run_df(r.gb_rot[x], s));
         count_launch();
         k_ritz_residual<<<grid, kT, 0, s>>>(r.QW[y], r.lam, r.X32, nm, nv, tot);
         CK(cudaGetLastError());
@@ -259,7 +259,7 @@ cudaError_t osv_mixed_eigh(const OsvRefine &r, int n, int nv, int nm, double *Q,
     }
     const int x = steps & 1;
     CK(rayleigh_ritz(r, x, n, nm, err, s));
-    CK(gemm_batch_run(r.gb_fin[x], s));
+    CK(gemm_batch_run_df(r.gb_fin[x], s));
     count_launch();
     k_osv_finish<<<n, kT, 0, s>>>(r.lam, omega, nosv, Q, nm, nv, l_osv, n_fixed);
     CK(cudaGetLastError());
@@ -285,7 +285,7 @@ cudaError_t osv_mixed_relax(const OsvRefine &r, const GemmBatch &gb_at, int n, i
     k_acc_f64<<<grid, kT, 0, s>>>(a, r.Z32, tot, 1);
     CK(cudaGetLastError());
     for (int it = 0; it < kRelaxRefineSteps; ++it) {
-        CK(gemm_batch_run(gb_at, s));
+        CK(gemm_batch_run_df(gb_at, s));
         count_launch();
         k_relax_resid<<<grid, kT, 0, s>>>(g, a, r.AT, r.lam, nosv, r.RS, nm, nv, tot);
         CK(cudaGetLastError());

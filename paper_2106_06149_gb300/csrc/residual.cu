@@ -72,9 +72,81 @@ struct View {
     bool rhs_by_slot;
     const R *S;      // coupling blocks
     R *T, *Rr, *G1;  // per-slot amplitudes, residuals; per-CTA scratch
-    float *sm;       // FP32 path: shared-memory staging (3 x np_max x ld floats)
+    float *sm;       // mixed kernel: shared-memory staging (3 x ld^2 floats or 2 x ld^2 float pairs)
     int ld;
+    bool df;         // FP64 evaluation in double-float arithmetic (mixed kernel)
 };
+
+// One coupling term of an FP64-accurate evaluation in double-float arithmetic on the FP32 pipe:
+//   G1 = S~ T~'_q (written to the per-CTA FP64 scratch), then R~_p -= f G1 S~^T.
+// Shared memory: sS[c][a] = S~(a, c) and sX[c][.] = T~'(c, .), later G1(., c), as (hi, lo) pairs.
+__device__ void term_df(int rp, int rq, const double *__restrict__ Sb, long long lds, bool s_trans,
+                        const double *__restrict__ Tq, long long ldt, bool t_trans, double f, double *Rp,
+                        long long ldr, double *G1, long long ldg, float2 *sm, int ld) {
+    float2 *sS = sm, *sX = sm + (long long)ld * ld;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int idx = tid; idx < rp * rq; idx += nt) {
+        int a, c;
+        if (s_trans) { c = idx / rp; a = idx % rp; } else { a = idx / rq; c = idx % rq; }
+        sS[c * ld + a] = split_df(s_trans ? Sb[(long long)c * lds + a] : Sb[(long long)a * lds + c]);
+    }
+    for (int idx = tid; idx < rq * rq; idx += nt) {
+        int c, b;
+        if (t_trans) { b = idx / rq; c = idx % rq; } else { c = idx / rq; b = idx % rq; }
+        sX[c * ld + b] = split_df(t_trans ? Tq[(long long)b * ldt + c] : Tq[(long long)c * ldt + b]);
+    }
+    __syncthreads();
+    const int ta = (rp + 4) / 5, tq = (rq + 4) / 5;
+    for (int t = tid; t < ta * tq; t += nt) {   // G1 = S~ T~'
+        const int a0 = (t / tq) * 5, b0 = (t % tq) * 5;
+        float hh[5][5] = {}, ll[5][5] = {};
+        for (int c = 0; c < rq; ++c) {
+            float2 x[5], y[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                x[i] = sS[c * ld + min(a0 + i, rp - 1)];
+                y[i] = sX[c * ld + min(b0 + i, rq - 1)];
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) df_fma(hh[i][j], ll[i][j], x[i], y[j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (a0 + i < rp && b0 + j < rq) G1[(long long)(a0 + i) * ldg + b0 + j] = df_val(hh[i][j], ll[i][j]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < rp * rq; idx += nt) {   // sX[c][a] = G1(a, c)
+        const int a = idx / rq, c = idx % rq;
+        sX[c * ld + a] = split_df(G1[(long long)a * ldg + c]);
+    }
+    __syncthreads();
+    for (int t = tid; t < ta * ta; t += nt) {   // R~_p -= f G1 S~^T
+        const int a0 = (t / ta) * 5, b0 = (t % ta) * 5;
+        float hh[5][5] = {}, ll[5][5] = {};
+        for (int c = 0; c < rq; ++c) {
+            float2 x[5], y[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                x[i] = sX[c * ld + min(a0 + i, rp - 1)];
+                y[i] = sS[c * ld + min(b0 + i, rp - 1)];
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) df_fma(hh[i][j], ll[i][j], x[i], y[j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (a0 + i < rp && b0 + j < rp) Rp[(long long)(a0 + i) * ldr + b0 + j] -= f * df_val(hh[i][j], ll[i][j]);
+    }
+    __syncthreads();
+}
 
 // One coupling term in FP32 with its operands staged in shared memory:
 //   R~_p(a, b) -= f sum_c G1(a, c) S~(b, c),  G1 = S~ T~'_q,  S~ = op(Sb) (rp x rq), T~'_q = op(Tq) (rq x rq).
@@ -184,6 +256,9 @@ __device__ double residual_eval(const SolveArgs &A, const ClusterInfo &C, const 
         const long long lds = T.s_trans ? Pd.np : Ps.np;
         if constexpr (std::is_same<R, float>::value) {
             term_f32(rp, rq, Sb, lds, T.s_trans, v.T + Ss.t_off, Ps.np, T.t_trans, f, v.Rr + Sd.t_off, Pd.np, v.sm, v.ld);
+        } else if (v.df) {
+            term_df(rp, rq, Sb, lds, T.s_trans, v.T + Ss.t_off, Ps.np, T.t_trans, f, v.Rr + Sd.t_off, Pd.np, v.G1, Ps.np,
+                    reinterpret_cast<float2 *>(v.sm), v.ld);
         } else {
             // G1 = S~_pq T~'_q   (rp x rq)
             blk_gemm<R>(rp, rq, rq, Sb, lds, T.s_trans, v.T + Ss.t_off, Ps.np, T.t_trans, v.G1, Ps.np, R(1), false);
@@ -249,7 +324,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
     const int c = A.order[blockIdx.x];
     const ClusterInfo C = A.clusters[c];
     __shared__ double red[kThreads / 32];
-    View<double> v{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride, nullptr, 0};
+    View<double> v{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride, nullptr, 0, false};
     bool conv = false;
     int it = 0;
     for (;; ++it) {
@@ -292,9 +367,10 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
     const ClusterInfo C = A.clusters[c];
     __shared__ double red[kThreads / 32];
     extern __shared__ float stage32[];
-    const int ld = (A.np_max + 4) & ~3;
-    View<float> v32{A.e32, A.Kt32, false, A.sblk32, A.T32, A.R32, A.G1_32 + (long long)blockIdx.x * A.gstride, stage32, ld};
-    View<double> v64{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride, nullptr, 0};
+    const int ld = A.np_max + 1;
+    View<float> v32{A.e32, A.Kt32, false, A.sblk32, A.T32, A.R32, A.G1_32 + (long long)blockIdx.x * A.gstride, stage32, ld,
+                    false};
+    View<double> v64{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride, stage32, ld, true};
     const int tid = threadIdx.x;
     auto zero32 = [&](float *x) {
         for (int s = C.slot0; s < C.slot1; ++s) {
@@ -315,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
     __syncthreads();
     bool conv = false;
     int evals = 0;
-    View<float> vc{A.e32, A.H32, true, A.sblk32, A.T32, A.R32, v32.G1, stage32, ld};
+    View<float> vc{A.e32, A.H32, true, A.sblk32, A.T32, A.R32, v32.G1, stage32, ld, false};
     for (int round = 0; round < 8; ++round) {
         const double r64 = residual_eval<double>(A, C, v64, red);
         ++evals;
@@ -403,8 +479,8 @@ cudaError_t launch_residual(const SolveArgs &a, int nclusters, bool mixed, cudaS
     if (nclusters <= 0) return cudaSuccess;
     count_launch();
     if (mixed) {
-        const int ld = (a.np_max + 4) & ~3;
-        const size_t sh = 3 * (size_t)ld * ld * sizeof(float);
+        const int ld = a.np_max + 1;
+        const size_t sh = std::max(3 * (size_t)ld * ld * sizeof(float), 2 * (size_t)ld * ld * sizeof(float2));
         if (sh > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(k_residual_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
             if (e != cudaSuccess) return e;

@@ -78,7 +78,7 @@ __device__ __forceinline__ bool bwait(uint64_t *bar, uint32_t parity) {
     uint32_t done = 0;
     while (true) {
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done)
             : "r"(smem_u32(bar)), "r"(parity)
@@ -94,7 +94,7 @@ __device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
 
 // bulk asynchronous copy global -> shared, completion counted on bar (16-byte aligned, size % 16 == 0)
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
@@ -111,6 +111,15 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// (hi, lo) += x with Knuth's two-sum (exact error term; FP32 only)
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
 // exact 2^e as a double for |e| < 1000
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
@@ -118,6 +127,10 @@ __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((lon
 __device__ __forceinline__ void slice4(double x, int e, float *s) {
     const long long bits = __double_as_longlong(x);
     const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0x7FF) {                                       // Inf / NaN: propagate a NaN through the products
+        s[0] = s[1] = s[2] = s[3] = __int_as_float(0x7FC00000);
+        return;
+    }
     long long n = 0;
     if (ex != 0) {                                           // zero and subnormal inputs slice to zero
         const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;   // value = mant 2^(ex-1075)
@@ -137,11 +150,25 @@ __device__ __forceinline__ void slice4(double x, int e, float *s) {
     s[3] = (float)s3 * 5.9604644775390625e-8f;
 }
 
-__device__ __forceinline__ int scale_exp(double mx) {
-    if (!(mx > 0.0)) return 0;
-    int e;
-    (void)frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1)
-    return e;
+// Largest |x| tracked as the bit pattern of |x| (for finite non-negative doubles the integer order of the bit
+// patterns is the numeric order): integer ALU instead of the slow FP64 pipe.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+// e with max |x| = f 2^e, f in [0.5, 1) (the frexp exponent) from the bit pattern; 0 for a zero row, the
+// smallest normal exponent for subnormal maxima (which slice to zero).
+__device__ __forceinline__ int scale_exp_bits(unsigned long long b) {
+    if (b == 0ULL) return 0;
+    const int ex = (int)(b >> 52);
+    return ex == 0 ? -1021 : ex - 1022;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
 }
 
 __device__ __forceinline__ int find_prob(const long long *__restrict__ pre, int nprob, long long t) {
@@ -160,7 +187,7 @@ __device__ __forceinline__ int find_prob(const long long *__restrict__ pre, int 
 constexpr int SROWS = 32;
 __global__ void __launch_bounds__(256) k_oz_scales(const GemmDesc *__restrict__ descs, const long long *__restrict__ sj0,
                                                    int nprob) {
-    __shared__ double part[8][SROWS];
+    __shared__ unsigned long long part[8][SROWS];
     const long long t = blockIdx.x;
     const int p = find_prob(sj0, nprob, t);
     const GemmDesc g = descs[p];
@@ -180,26 +207,32 @@ __global__ void __launch_bounds__(256) k_oz_scales(const GemmDesc *__restrict__ 
             if (rr >= R) break;
             const double *row = isA ? g.A + (long long)(g.a_rows ? g.a_rows[rr] : rr) * g.lda
                                     : g.B + (long long)(g.n_idx_b ? g.n_idx_b[rr] : rr) * g.ldb;
-            double mx = 0.0;
-            for (int k = lane; k < g.K; k += 32) mx = fmax(mx, fabs(row[kidx ? kidx[k] : k]));
-            mx = warp_max(mx);
-            if (lane == 0) out[rr] = scale_exp(mx);
+            unsigned long long mx = 0ULL;
+            for (int k = lane; k < g.K; k += 32) {
+                const unsigned long long b = abs_bits(row[kidx ? kidx[k] : k]);
+                mx = b > mx ? b : mx;
+            }
+            mx = warp_max_u64(mx);
+            if (lane == 0) out[rr] = scale_exp_bits(mx);
         }
         return;
     }
     const int rr = r0 + lane;
-    double mx = 0.0;
+    unsigned long long mx = 0ULL;
     if (rr < R) {
         const long long rc = isA ? rr : (g.n_idx_b ? g.n_idx_b[rr] : rr);
         const double *base = isA ? g.A + rc : g.B + rc;
         const long long ld = isA ? g.lda : g.ldb;
-        for (int k = wid; k < g.K; k += 8) mx = fmax(mx, fabs(base[(long long)(kidx ? kidx[k] : k) * ld]));
+        for (int k = wid; k < g.K; k += 8) {
+            const unsigned long long b = abs_bits(base[(long long)(kidx ? kidx[k] : k) * ld]);
+            mx = b > mx ? b : mx;
+        }
     }
     part[wid][lane] = mx;
     __syncthreads();
     if (wid == 0 && rr < R) {
-        for (int w = 1; w < 8; ++w) mx = fmax(mx, part[w][lane]);
-        out[rr] = scale_exp(mx);
+        for (int w = 1; w < 8; ++w) mx = part[w][lane] > mx ? part[w][lane] : mx;
+        out[rr] = scale_exp_bits(mx);
     }
 }
 
@@ -305,10 +338,16 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t taddr = s_taddr;
 
-    // drain targets: TMEM lanes of warp % 4 (rows), columns 64 * (warp / 4) .. + 63
-    double cacc[64];
+    // drain targets: TMEM lanes of warp % 4 (rows), columns 64 * (warp / 4) .. + 63.  The chunk sums are added
+    // into FP32 double-float pairs (hi, lo) with an error-free two-sum: FP32 ALU only (an FP64 add runs at 1/64 of
+    // the FP32 rate on this part and made the drain the bottleneck); ~48 significant bits, ample for the
+    // ~31-bit products.
+    float chi[64], clo[64];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) cacc[j] = 0.0;
+    for (int j = 0; j < 64; ++j) {
+        chi[j] = 0.f;
+        clo[j] = 0.f;
+    }
 
     int loaded = 0;   // k-tiles whose copies were issued (thread 0's view)
     auto load_stage = [&](int kt) {   // thread 0 only
@@ -316,8 +355,11 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         ++loaded;
         unsigned char *sA = smem + st * STAGE;
         expect_tx(&full[st], STAGE);
-        bulk_g2s(sA, Aimg + (long long)kt * TILE_BYTES, TILE_BYTES, &full[st]);
-        bulk_g2s(sA + TILE_BYTES, Bimg + (long long)kt * TILE_BYTES, TILE_BYTES, &full[st]);
+#pragma unroll
+        for (int i = 0; i < NSLICE; ++i) {   // one copy per slice image keeps several requests in flight
+            bulk_g2s(sA + i * IMG, Aimg + (long long)kt * TILE_BYTES + i * IMG, IMG, &full[st]);
+            bulk_g2s(sA + TILE_BYTES + i * IMG, Bimg + (long long)kt * TILE_BYTES + i * IMG, IMG, &full[st]);
+        }
     };
 
     int issued = 0;   // MMA groups committed (thread 0's view)
@@ -390,8 +432,8 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
                     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        cacc[c + i] += (double)v0[i];
-                        cacc[c + 16 + i] += (double)v1[i];
+                        two_sum_acc(chi[c + i], clo[c + i], v0[i]);
+                        two_sum_acc(chi[c + 16 + i], clo[c + 16 + i], v1[i]);
                     }
                 }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -415,24 +457,27 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr));
     }
     if (!ok) return;
-    // epilogue through shared memory (the stage buffers are idle): row-major 128 x 128 tile, coalesced stores
-    double *sC = reinterpret_cast<double *>(smem);
+    // epilogue through shared memory (the stage buffers are idle): the (hi, lo) pairs of the row-major 128 x 128
+    // tile, then coalesced stores; the only FP64 operations are one add and one or two multiplies per element
+    float2 *sC = reinterpret_cast<float2 *>(smem);
     constexpr int LDC = BN + 1;
     {
         const int r = (warp & 3) * 32 + lane;
-        const int m = m0 + r;
-        const double sa = m < g.M ? pow2(g.ea[m] - 14) : 0.0;
 #pragma unroll
-        for (int j = 0; j < 64; ++j) sC[r * LDC + (warp >> 2) * 64 + j] = cacc[j] * sa;
+        for (int j = 0; j < 64; ++j) sC[r * LDC + (warp >> 2) * 64 + j] = make_float2(chi[j], clo[j]);
     }
     __syncthreads();
+    const bool unit_alpha = g.alpha == 1.0;
     for (int r = warp; r < BM; r += NT / 32) {
         const int m = m0 + r;
         if (m >= g.M) break;
+        const int em = g.ea[m] - 14;
         for (int c = lane; c < BN; c += 32) {
             const int n = n0 + c;
             if (n >= g.N) break;
-            const double val = g.alpha * (sC[r * LDC + c] * pow2(g.eb[n]));
+            const float2 hl = sC[r * LDC + c];
+            double val = ((double)hl.x + (double)hl.y) * pow2(em + g.eb[n]);
+            if (!unit_alpha) val *= g.alpha;
             const long long nc = g.n_idx_c ? g.n_idx_c[n] : n;
             double *cp = g.C + (long long)m * g.ldc + nc;
             if (g.atomic) atomicAdd(cp, val);

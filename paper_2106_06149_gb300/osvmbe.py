@@ -21,7 +21,7 @@ OSV_FP64, OSV_MIXED_TF32X3, OSV_MIXED_BF16X4 = 0, 1, 2
 EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv_build", "cluster_residual_solve",
            "mbe3_combine", "energy", "gradient_backward", "osv_cluster_count", "osv_cluster_info",
            "osv_eigenvalues", "osv_syev_batched", "osv_profile_enable", "osv_profile_read",
-           "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc"]
+           "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops"]
 
 
 class OsvParams(ctypes.Structure):
@@ -69,6 +69,7 @@ def load(path=LIB_PATH):
         "osv_residual_flops": ([V, P(D)], I),
         "osv_kernel_launches": ([P(ctypes.c_longlong)], I),
         "osv_syev_batched_noalloc": ([V, I, I, V, V, V], I),
+        "osv_adjoint_flops": ([V, P(D)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -243,6 +244,11 @@ class Context:
     def residual_flops(self):
         f = ctypes.c_double()
         _check(load().osv_residual_flops(self.h, ctypes.byref(f)), self.h)
+        return f.value
+
+    def adjoint_flops(self):
+        f = ctypes.c_double()
+        _check(load().osv_adjoint_flops(self.h, ctypes.byref(f)), self.h)
         return f.value
 
     def eigenvalues(self, k, n_vir):
