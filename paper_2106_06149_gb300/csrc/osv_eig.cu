@@ -644,10 +644,124 @@ __global__ void __launch_bounds__(kT) k_jacobi_small(const EighDesc *__restrict_
 }
 
 // Mixed-precision variant for the pair eigenproblems (order <= kJacobiMixedMax): FP32 Jacobi sweeps to the FP32
-// floor give V0; FP64 then re-orthonormalises it by two Newton-Schulz steps V <- V (3I - V^T V)/2, forms
-// A1 = V^T A V (A re-read from global memory, FP64) and finishes with FP64 Jacobi sweeps on A1, which is
-// diagonal to ~1e-7 relative and converges quadratically (one or two sweeps instead of ~8 on A itself).
-// Shared memory: three n x n FP64 buffers (the FP32 A and V alias the first).
+// floor give V0; then, in double-float arithmetic on the FP32 pipe (common.cuh; an FP64 operation issues at 1/64
+// of the FP32 rate on GB300): two Newton-Schulz steps V <- V (3I - V^T V)/2 (orthonormality 1e-6 -> 1e-12 ->
+// 1e-16), A1 = V^T A V, and Jacobi polishing sweeps on A1, which is diagonal to ~1e-7 relative and converges
+// quadratically (one sweep, two with close eigenvalues).  Shared memory: four n x n double-float buffers (the
+// FP32 A and V of the first stage alias the first).
+
+__device__ __forceinline__ float2 df_renorm(float h, float l) {
+    const float s = __fadd_rn(h, l);
+    return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+
+// C = op(A) op(B) for ne x ne double-float matrices in shared memory (leading dimension ld), 5 x 5 outputs per
+// thread; op = transpose when TA / TB.
+template <bool TA, bool TB>
+__device__ void df_gemm_sm(int ne, int ld, const float2 *A, const float2 *B, float2 *C) {
+    const int t5 = (ne + 4) / 5;
+    for (int t = threadIdx.x; t < t5 * t5; t += blockDim.x) {
+        const int r0 = (t / t5) * 5, c0 = (t % t5) * 5;
+        float h[5][5] = {}, l[5][5] = {};
+        for (int k = 0; k < ne; ++k) {
+            float2 a[5], b[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const int r = min(r0 + i, ne - 1), c = min(c0 + i, ne - 1);
+                a[i] = TA ? A[k * ld + r] : A[r * ld + k];
+                b[i] = TB ? B[c * ld + k] : B[k * ld + c];
+            }
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j) df_fma(h[i][j], l[i][j], a[i], b[j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (r0 + i < ne && c0 + j < ne) C[(r0 + i) * ld + c0 + j] = df_renorm(h[i][j], l[i][j]);
+    }
+}
+
+// (x, y) <- (c x - s y, s x + c y) in double-float
+__device__ __forceinline__ void df_rot(float2 &x, float2 &y, const float2 c, const float2 sn) {
+    float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    const float2 ms = make_float2(-sn.x, -sn.y);
+    df_fma(h1, l1, c, x);
+    df_fma(h1, l1, ms, y);
+    df_fma(h2, l2, sn, x);
+    df_fma(h2, l2, c, y);
+    x = df_renorm(h1, l1);
+    y = df_renorm(h2, l2);
+}
+
+// Cyclic round-robin Jacobi sweeps in double-float (A, V: ne x ne pairs in shared memory; same pairing and
+// stopping rule as jacobi_sweeps, the rotation angle from FP64 values of the three entries).
+__device__ bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, float2 *cs, float2 *sn, int *pp, int *qq,
+                                 double *red, int *flag, int max_sweeps, double tol2) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double fro = 0.0;
+    for (int idx = tid; idx < ne * ne; idx += nt) {
+        const double a = A[(idx / ne) * ld + idx % ne].x;
+        fro += a * a;
+    }
+    fro = block_sum(fro, red);
+    const int half = ne / 2;
+    bool conv = false;
+    for (int sweep = 0;; ++sweep) {
+        double off = 0.0;
+        for (int idx = tid; idx < ne * ne; idx += nt) {
+            const int r = idx / ne, c = idx % ne;
+            if (r != c) {
+                const double a = A[r * ld + c].x;
+                off += a * a;
+            }
+        }
+        off = block_sum(off, red);
+        if (tid == 0) *flag = off <= tol2 * fro || off == 0.0;
+        __syncthreads();
+        conv = *flag;
+        __syncthreads();
+        if (conv || sweep == max_sweeps) break;
+        for (int round = 0; round < ne - 1; ++round) {
+            for (int t = tid; t < half; t += nt) {
+                int a = t == 0 ? 0 : 1 + (t - 1 + round) % (ne - 1);
+                int bb = 1 + (ne - 2 - t + round) % (ne - 1);
+                if (t == 0) bb = 1 + (ne - 2 + round) % (ne - 1);
+                const int p = min(a, bb), q = max(a, bb);
+                pp[t] = p;
+                qq[t] = q;
+                const float2 apq2 = A[p * ld + q];
+                const double apq = df_val(apq2.x, apq2.y);
+                double c = 1.0, s = 0.0;
+                if (apq != 0.0 && fabs(apq) > 1e-300) {
+                    const float2 aq = A[q * ld + q], ap = A[p * ld + p];
+                    const double th = (df_val(aq.x, aq.y) - df_val(ap.x, ap.y)) / (2.0 * apq);
+                    const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                    c = rsqrt(tt * tt + 1.0);
+                    s = tt * c;
+                }
+                cs[t] = split_df(c);
+                sn[t] = split_df(s);
+            }
+            __syncthreads();
+            for (int idx = tid; idx < half * ne; idx += nt) {   // rows: B = J^T A
+                const int t = idx / ne, k = idx % ne;
+                df_rot(A[pp[t] * ld + k], A[qq[t] * ld + k], cs[t], sn[t]);
+            }
+            __syncthreads();
+            for (int idx = tid; idx < half * ne; idx += nt) {   // columns: A' = B J, V' = V J
+                const int t = idx / ne, k = idx % ne;
+                df_rot(A[k * ld + pp[t]], A[k * ld + qq[t]], cs[t], sn[t]);
+                df_rot(V[k * ld + pp[t]], V[k * ld + qq[t]], cs[t], sn[t]);
+            }
+            __syncthreads();
+        }
+    }
+    return conv;
+}
+
 __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict__ descs, int *err) {
     const EighDesc D = descs[blockIdx.x];
     const int n = D.n_dev ? min(*D.n_dev, D.n) : D.n;
@@ -656,8 +770,9 @@ __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict_
     const int ld = ne + 1;
     const long long sq = (long long)ne * ld;
     extern __shared__ double sh[];
-    double *B0 = sh, *B1 = sh + sq, *B2 = sh + 2 * sq;
-    double *cs = B2 + sq, *sn = cs + ne / 2, *dg = sn + ne / 2;
+    float2 *B0 = reinterpret_cast<float2 *>(sh), *B1 = B0 + sq, *B2 = B1 + sq, *B3 = B2 + sq;
+    float2 *cs = B3 + sq, *sn = cs + ne / 2;
+    double *dg = reinterpret_cast<double *>(sn + ne / 2);
     float *cs32 = reinterpret_cast<float *>(dg + ne), *sn32 = cs32 + ne / 2;
     int *pp = reinterpret_cast<int *>(sn32 + ne / 2), *qq = pp + ne / 2, *rank = qq + ne / 2;
     float *A32 = reinterpret_cast<float *>(B0), *V32 = A32 + sq;
@@ -667,78 +782,68 @@ __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict_
     auto Ag = [&](int r, int c) -> double { return (r < n && c < n) ? D.A[(long long)r * D.lda + c] : 0.0; };
     for (int idx = tid; idx < ne * ne; idx += kT) {
         const int r = idx / ne, c = idx % ne;
-        A32[r * ld + c] = (float)Ag(r, c);
+        const double a = Ag(r, c);
+        A32[r * ld + c] = (float)a;
         V32[r * ld + c] = r == c ? 1.f : 0.f;
+        B3[r * ld + c] = split_df(a);   // A as double-float for A1 = V^T A V
     }
     __syncthreads();
     jacobi_sweeps<float>(A32, V32, ne, ld, cs32, sn32, pp, qq, red, &s_flag, 20, 1e-10);
     for (int idx = tid; idx < ne * ne; idx += kT) {
         const int r = idx / ne, c = idx % ne;
-        B1[r * ld + c] = (double)V32[r * ld + c];
+        B1[r * ld + c] = make_float2(V32[r * ld + c], 0.f);
     }
     __syncthreads();
-    // two Newton-Schulz steps V <- V (3I - V^T V) / 2 (orthonormality error 1e-6 -> 1e-12 -> 1e-16):
-    // V0 in B1 -> B0 -> B1
-    double *Vin = B1, *Vout = B0;
+    // two Newton-Schulz steps: V in B1 -> B0 -> B1
+    float2 *Vin = B1, *Vout = B0;
     for (int step = 0; step < 2; ++step) {
-        for (int idx = tid; idx < ne * ne; idx += kT) {
+        df_gemm_sm<true, false>(ne, ld, Vin, Vin, B2);   // G = V^T V
+        __syncthreads();
+        for (int idx = tid; idx < ne * ne; idx += kT) {   // M = (3I - G)/2
             const int r = idx / ne, c = idx % ne;
-            double g = 0.0;
-            for (int k = 0; k < ne; ++k) g = fma(Vin[k * ld + r], Vin[k * ld + c], g);
-            B2[r * ld + c] = 0.5 * ((r == c ? 3.0 : 0.0) - g);
+            const float2 g = B2[r * ld + c];
+            if (r == c) {   // 1.5 - g/2 with an exact two-sum (g ~ 1: a plain FP32 subtraction would round)
+                float h = 1.5f, l = -0.5f * g.y;
+                df_add(h, l, -0.5f * g.x);
+                B2[r * ld + c] = df_renorm(h, l);
+            } else {
+                B2[r * ld + c] = make_float2(-0.5f * g.x, -0.5f * g.y);
+            }
         }
         __syncthreads();
-        for (int idx = tid; idx < ne * ne; idx += kT) {
-            const int r = idx / ne, c = idx % ne;
-            double v = 0.0;
-            for (int k = 0; k < ne; ++k) v = fma(Vin[r * ld + k], B2[k * ld + c], v);
-            Vout[r * ld + c] = v;
-        }
+        df_gemm_sm<false, false>(ne, ld, Vin, B2, Vout);   // V M
         __syncthreads();
-        double *t = Vin;
+        float2 *t = Vin;
         Vin = Vout;
         Vout = t;
     }
-    // V in B1; T = A V (B0), A1 = V^T T (B2)
-    for (int idx = tid; idx < ne * ne; idx += kT) {
-        const int r = idx / ne, c = idx % ne;
-        double t = 0.0;
-        if (r < n)
-            for (int k = 0; k < n; ++k) t = fma(D.A[(long long)r * D.lda + k], B1[k * ld + c], t);
-        B0[r * ld + c] = t;
-    }
+    // V in B1: T = A V (B0), A1 = V^T T (B2, symmetrised)
+    df_gemm_sm<false, false>(ne, ld, B3, B1, B0);
     __syncthreads();
-    for (int idx = tid; idx < ne * ne; idx += kT) {
+    df_gemm_sm<true, false>(ne, ld, B1, B0, B2);
+    __syncthreads();
+    for (int idx = tid; idx < ne * ne; idx += kT) {   // symmetrise: (x + y) / 2 with a two-sum
         const int r = idx / ne, c = idx % ne;
-        if (r > c) continue;
-        double a = 0.0, b = 0.0;
-        for (int k = 0; k < ne; ++k) {
-            a = fma(B1[k * ld + r], B0[k * ld + c], a);
-            b = fma(B1[k * ld + c], B0[k * ld + r], b);
+        if (r < c) {
+            const float2 x = B2[r * ld + c], y = B2[c * ld + r];
+            float h = x.x, l = __fadd_rn(x.y, y.y);
+            df_add(h, l, y.x);
+            const float2 m = df_renorm(0.5f * h, 0.5f * l);
+            B2[r * ld + c] = m;
+            B2[c * ld + r] = m;
         }
-        const double m = 0.5 * (a + b);
-        B2[r * ld + c] = m;
-        B2[c * ld + r] = m;
     }
     __syncthreads();
-    for (int idx = tid; idx < ne * ne; idx += kT) {
+    for (int idx = tid; idx < ne * ne; idx += kT) {   // polish rotations accumulate from the identity
         const int r = idx / ne, c = idx % ne;
-        B0[r * ld + c] = r == c ? 1.0 : 0.0;
+        B3[r * ld + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
     }
     __syncthreads();
-    // polish: off-diagonal norm <= 1e-14 of the Frobenius norm (the FP32 start leaves ~1e-7; quadratic
-    // convergence gives that in one sweep, two with clustered eigenvalues)
-    const bool conv = jacobi_sweeps<double>(B2, B0, ne, ld, cs, sn, pp, qq, red, &s_flag, 20, 1e-28);
+    const bool conv = jacobi_sweeps_df(B2, B3, ne, ld, cs, sn, pp, qq, red, &s_flag, 20, 1e-28);
     if (!conv && tid == 0) raise_err(err, kDevEighNoConv);
-    for (int i = tid; i < ne; i += kT) dg[i] = B2[i * ld + i];
+    for (int i = tid; i < ne; i += kT) dg[i] = df_val(B2[i * ld + i].x, B2[i * ld + i].y);
     __syncthreads();
-    // final eigenvectors V V' (B2)
-    for (int idx = tid; idx < ne * ne; idx += kT) {
-        const int r = idx / ne, c = idx % ne;
-        double v = 0.0;
-        for (int k = 0; k < ne; ++k) v = fma(B1[r * ld + k], B0[k * ld + c], v);
-        B2[r * ld + c] = v;
-    }
+    df_gemm_sm<false, false>(ne, ld, B1, B3, B0);   // eigenvectors V V'
     for (int i = tid; i < n; i += kT) {
         const double di = dg[i];
         int rk = 0;
@@ -749,7 +854,8 @@ __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict_
     for (int i = tid; i < n; i += kT) D.w[rank[i]] = dg[i];
     for (int idx = tid; idx < n * n; idx += kT) {
         const int c = idx / n, r = idx % n;    // eigenvector c, component r
-        D.Zt[(long long)rank[c] * D.ldz + r] = B2[r * ld + c];
+        const float2 z = B0[r * ld + c];
+        D.Zt[(long long)rank[c] * D.ldz + r] = df_val(z.x, z.y);
     }
 }
 
@@ -857,8 +963,8 @@ OSV_EIG_INST(float)
 
 size_t jacobi_mixed_smem_bytes(int n) {
     const int ne = (n + 1) & ~1;
-    return (size_t)3 * ne * (ne + 1) * sizeof(double) + (size_t)2 * ne * sizeof(double) + (size_t)ne * sizeof(float) +
-           (size_t)3 * (ne / 2 + 1) * sizeof(int) + (size_t)ne * sizeof(int) + 64;
+    return (size_t)4 * ne * (ne + 1) * sizeof(float2) + (size_t)ne * sizeof(float2) + (size_t)ne * sizeof(double) +
+           (size_t)ne * sizeof(float) + (size_t)3 * (ne / 2 + 1) * sizeof(int) + (size_t)ne * sizeof(int) + 64;
 }
 
 cudaError_t eigh_small_jacobi_mixed(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s) {

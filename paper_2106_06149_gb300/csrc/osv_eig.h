@@ -47,7 +47,7 @@ constexpr int kJacobiMax = 112;
 cudaError_t eigh_small_jacobi(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s);
 // Same contract, mixed precisions (FP32 sweeps, FP64 re-orthonormalisation and polishing sweeps) for orders
 // <= kJacobiMixedMax; results to FP64 accuracy.
-constexpr int kJacobiMixedMax = 88;
+constexpr int kJacobiMixedMax = 82;
 cudaError_t eigh_small_jacobi_mixed(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s);
 
 }  // namespace osv
