@@ -305,6 +305,7 @@ void tc_tiles_free(TcTiles &tt) {
     if (tt.d_jobs0) cudaFree(tt.d_jobs0);
     if (tt.d_soff) cudaFree(tt.d_soff);
     if (tt.d_sjobs0) cudaFree(tt.d_sjobs0);
+    if (tt.d_ops) cudaFree(tt.d_ops);
     tt = TcTiles{};
 }
 

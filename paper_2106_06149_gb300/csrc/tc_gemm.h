@@ -14,6 +14,8 @@ struct TcTiles {
     // images in the scratch buffer, and the scratch size the batch needs
     long long *d_jobs0 = nullptr, *d_soff = nullptr, *d_sjobs0 = nullptr;
     long long jobs = 0, scratch_bytes = 0, sjobs = 0;   // sjobs: row-scale jobs (blocks of 32 operand rows)
+    void *d_ops = nullptr;                              // distinct operands (shared by problems that read them)
+    int nops = 0;
 };
 
 // per-problem 128 x 64 tile offsets of an uploaded batch

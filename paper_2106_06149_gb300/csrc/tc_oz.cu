@@ -24,6 +24,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -180,121 +183,108 @@ __device__ __forceinline__ int find_prob(const long long *__restrict__ pre, int 
     return lo;
 }
 
-// Row / column scales: ea[m] = smallest e with max_k |A(m,k)| <= 2^e (0 for a zero row), eb[n] likewise over
-// B(k, n).  One CTA per block of 32 operand rows (jobs of problem p: its A blocks, then its B blocks unless B
-// shares A's slices).  K-contiguous rows: a warp per row; otherwise the 32 lanes take 32 adjacent rows and the
+// One GEMM operand as the slicing passes see it: R rows over K, element (r, k) = ptr[row(r) ld + kk(k)] when the
+// rows are K-contiguous (A, transA = 0; B, transB = 1), ptr[kk(k) ld + row(r)] otherwise, with optional row and
+// K index maps.  Problems that read the same operand (same pointer, layout, maps and sizes) share one entry: its
+// row scales and slice images are computed once per batch.
+struct OzOperand {
+    const double *ptr;
+    long long ld;
+    const int *rowmap, *kmap;
+    int R, K, kcontig;
+    int *exps;         // row scale exponents (R)
+    long long soff;    // byte offset of its slice images in the scratch
+};
+
+__device__ __forceinline__ double oz_elem(const OzOperand &o, int r, int k) {
+    const long long rr = o.rowmap ? o.rowmap[r] : r, kk = o.kmap ? o.kmap[k] : k;
+    return o.kcontig ? o.ptr[rr * o.ld + kk] : o.ptr[kk * o.ld + rr];
+}
+
+// Row scales: exps[r] = e with max_k |X(r,k)| = f 2^e, f in [0.5, 1) (0 for a zero row).  One CTA per block of
+// 32 operand rows.  K-contiguous rows: a warp per row; otherwise the 32 lanes take 32 adjacent rows and the
 // eight warps split K.
 constexpr int SROWS = 32;
-__global__ void __launch_bounds__(256) k_oz_scales(const GemmDesc *__restrict__ descs, const long long *__restrict__ sj0,
-                                                   int nprob) {
+__global__ void __launch_bounds__(256) k_oz_scales(const OzOperand *__restrict__ ops, const long long *__restrict__ sj0,
+                                                   int nops) {
     __shared__ unsigned long long part[8][SROWS];
     const long long t = blockIdx.x;
-    const int p = find_prob(sj0, nprob, t);
-    const GemmDesc g = descs[p];
-    const int nba = (g.M + SROWS - 1) / SROWS;
-    int j = (int)(t - sj0[p]);
-    const bool isA = j < nba;
-    if (!isA) j -= nba;
-    const int R = isA ? g.M : g.N;
-    const int r0 = j * SROWS;
+    const int p = find_prob(sj0, nops, t);
+    const OzOperand o = ops[p];
+    const int r0 = (int)(t - sj0[p]) * SROWS;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const bool kcontig = isA ? g.transA == 0 : g.transB == 1;
-    const int *kidx = isA ? g.k_idx_a : g.k_idx_b;
-    int *out = isA ? g.ea : g.eb;
-    if (kcontig) {
+    if (o.kcontig) {
         for (int r = wid; r < SROWS; r += 8) {
             const int rr = r0 + r;
-            if (rr >= R) break;
-            const double *row = isA ? g.A + (long long)(g.a_rows ? g.a_rows[rr] : rr) * g.lda
-                                    : g.B + (long long)(g.n_idx_b ? g.n_idx_b[rr] : rr) * g.ldb;
+            if (rr >= o.R) break;
+            const double *row = o.ptr + (long long)(o.rowmap ? o.rowmap[rr] : rr) * o.ld;
             unsigned long long mx = 0ULL;
-            for (int k = lane; k < g.K; k += 32) {
-                const unsigned long long b = abs_bits(row[kidx ? kidx[k] : k]);
+            for (int k = lane; k < o.K; k += 32) {
+                const unsigned long long b = abs_bits(row[o.kmap ? o.kmap[k] : k]);
                 mx = b > mx ? b : mx;
             }
             mx = warp_max_u64(mx);
-            if (lane == 0) out[rr] = scale_exp_bits(mx);
+            if (lane == 0) o.exps[rr] = scale_exp_bits(mx);
         }
         return;
     }
     const int rr = r0 + lane;
     unsigned long long mx = 0ULL;
-    if (rr < R) {
-        const long long rc = isA ? rr : (g.n_idx_b ? g.n_idx_b[rr] : rr);
-        const double *base = isA ? g.A + rc : g.B + rc;
-        const long long ld = isA ? g.lda : g.ldb;
-        for (int k = wid; k < g.K; k += 8) {
-            const unsigned long long b = abs_bits(base[(long long)(kidx ? kidx[k] : k) * ld]);
+    if (rr < o.R) {
+        const double *base = o.ptr + (o.rowmap ? o.rowmap[rr] : rr);
+        for (int k = wid; k < o.K; k += 8) {
+            const unsigned long long b = abs_bits(base[(long long)(o.kmap ? o.kmap[k] : k) * o.ld]);
             mx = b > mx ? b : mx;
         }
     }
     part[wid][lane] = mx;
     __syncthreads();
-    if (wid == 0 && rr < R) {
+    if (wid == 0 && rr < o.R) {
         for (int w = 1; w < 8; ++w) mx = part[w][lane] > mx ? part[w][lane] : mx;
-        out[rr] = scale_exp_bits(mx);
+        o.exps[rr] = scale_exp_bits(mx);
     }
 }
 
-
 // One CTA per operand tile (128 rows x 32 K): stage the FP64 values in shared memory (coalesced for either
-// operand orientation), then write the four slice images.  Jobs of problem p: its A tiles (row tile major, then
-// K tile), then its B tiles (none when B shares A's slices).
-__global__ void __launch_bounds__(NT) k_oz_slice(const GemmDesc *__restrict__ descs, const long long *__restrict__ jobs0,
-                                                 const long long *__restrict__ soff, int nprob,
-                                                 unsigned char *__restrict__ scratch) {
+// orientation), then write the four slice images (row tile major, then K tile).
+__global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ ops, const long long *__restrict__ jobs0,
+                                                 int nops, unsigned char *__restrict__ scratch) {
     __shared__ double xs[BK][BM + 1];
     __shared__ int es[BM];
     const long long t = blockIdx.x;
-    const int p = find_prob(jobs0, nprob, t);
-    const GemmDesc g = descs[p];
-    const int nkt = (g.K + BK - 1) / BK;
-    const int ta = ((g.M + BM - 1) / BM) * nkt;
-    long long j = t - jobs0[p];
-    const bool isA = j < ta;
-    if (!isA) j -= ta;
+    const int p = find_prob(jobs0, nops, t);
+    const OzOperand o = ops[p];
+    const int nkt = (o.K + BK - 1) / BK;
+    const long long j = t - jobs0[p];
     const int rt = (int)(j / nkt), kt = (int)(j % nkt);
-    const int R = isA ? g.M : g.N;
     const int r0 = rt * BM, k0 = kt * BK;
-    const bool kcontig = isA ? g.transA == 0 : g.transB == 1;
     const int tid = threadIdx.x;
-    for (int r = tid; r < BM; r += NT) es[r] = r0 + r < R ? (isA ? g.ea[r0 + r] : g.eb[r0 + r]) : 0;
-    auto value = [&](int r, int k) -> double {   // operand element (row r, k) of the tile, zero outside
-        const int rr = r0 + r, kk = k0 + k;
-        if (rr >= R || kk >= g.K) return 0.0;
-        if (isA) {
-            const long long kc = g.k_idx_a ? g.k_idx_a[kk] : kk;
-            return g.transA == 0 ? g.A[(long long)(g.a_rows ? g.a_rows[rr] : rr) * g.lda + kc] : g.A[kc * g.lda + rr];
-        }
-        const long long kr = g.k_idx_b ? g.k_idx_b[kk] : kk;
-        const long long nc = g.n_idx_b ? g.n_idx_b[rr] : rr;
-        return g.transB == 0 ? g.B[kr * g.ldb + nc] : g.B[nc * g.ldb + kr];
-    };
-    if (kcontig) {
+    for (int r = tid; r < BM; r += NT) es[r] = r0 + r < o.R ? o.exps[r0 + r] : 0;
+    if (o.kcontig) {
         for (int idx = tid; idx < BM * BK; idx += NT) {   // lanes along k
             const int r = idx / BK, k = idx % BK;
-            xs[k][r] = value(r, k);
+            xs[k][r] = (r0 + r < o.R && k0 + k < o.K) ? oz_elem(o, r0 + r, k0 + k) : 0.0;
         }
     } else {
         for (int idx = tid; idx < BM * BK; idx += NT) {   // lanes along rows
             const int k = idx / BM, r = idx % BM;
-            xs[k][r] = value(r, k);
+            xs[k][r] = (r0 + r < o.R && k0 + k < o.K) ? oz_elem(o, r0 + r, k0 + k) : 0.0;
         }
     }
     __syncthreads();
-    unsigned char *img = scratch + soff[2 * p + (isA ? 0 : 1)] + ((long long)rt * nkt + kt) * TILE_BYTES;
+    unsigned char *img = scratch + o.soff + ((long long)rt * nkt + kt) * TILE_BYTES;
     for (int c = tid; c < BM * (BK / 8); c += NT) {   // one core-matrix row (8 K of one row) per step
         const int r = c % BM, kg = c / BM;
-        float s[8][NSLICE];
+        float sl[8][NSLICE];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) slice4(xs[kg * 8 + q][r], es[r], s[q]);
-        const uint32_t o = koff(r, kg * 8);
+        for (int q = 0; q < 8; ++q) slice4(xs[kg * 8 + q][r], es[r], sl[q]);
+        const uint32_t off = koff(r, kg * 8);
 #pragma unroll
         for (int i = 0; i < NSLICE; ++i) {
             __nv_bfloat162 h[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(s[2 * q][i], s[2 * q + 1][i]);
-            *reinterpret_cast<uint4 *>(img + i * IMG + o) = *reinterpret_cast<uint4 *>(h);
+            for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(sl[2 * q][i], sl[2 * q + 1][i]);
+            *reinterpret_cast<uint4 *>(img + i * IMG + off) = *reinterpret_cast<uint4 *>(h);
         }
     }
 }
@@ -486,61 +476,98 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
     }
 }
 
-// B shares A's slices when both are the same matrix read with K along its rows: C = X X^T
-bool shares_slices(const GemmDesc &g) {
-    return g.A == g.B && g.M == g.N && g.transA == 0 && g.transB == 1 && g.lda == g.ldb && g.a_rows == nullptr &&
-           g.n_idx_b == nullptr && g.k_idx_a == g.k_idx_b;
-}
-
 }  // namespace
 
 cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
     tc_tiles_free(tt);
     if (b.h.empty()) return cudaSuccess;
-    long long tot = 0;
-    for (const GemmDesc &g : b.h) tot += (long long)g.M + g.N;
-    cudaError_t e = cudaMalloc(&tt.d_exps, (size_t)std::max<long long>(tot, 1) * sizeof(int));
-    if (e != cudaSuccess) return e;
     std::vector<GemmDesc> h = b.h;
-    long long off = 0, bytes = 0;
-    std::vector<long long> t0(h.size() + 1, 0), j0(h.size() + 1, 0), so(2 * h.size(), 0), s0(h.size() + 1, 0);
+    // distinct operands (A of every problem, B of every problem), identified by pointer, layout, maps and sizes
+    struct Key {
+        const double *ptr;
+        long long ld;
+        const int *rowmap, *kmap;
+        int R, K, kcontig;
+        bool operator<(const Key &o) const {
+            return std::tie(ptr, ld, rowmap, kmap, R, K, kcontig) < std::tie(o.ptr, o.ld, o.rowmap, o.kmap, o.R, o.K, o.kcontig);
+        }
+    };
+    std::map<Key, int> index;
+    std::vector<OzOperand> ops;
+    std::vector<int> opA(h.size()), opB(h.size());
+    auto add = [&](const Key &k) -> int {
+        auto it = index.find(k);
+        if (it != index.end()) return it->second;
+        OzOperand o{};
+        o.ptr = k.ptr;
+        o.ld = k.ld;
+        o.rowmap = k.rowmap;
+        o.kmap = k.kmap;
+        o.R = k.R;
+        o.K = k.K;
+        o.kcontig = k.kcontig;
+        ops.push_back(o);
+        index[k] = (int)ops.size() - 1;
+        return (int)ops.size() - 1;
+    };
+    for (size_t i = 0; i < h.size(); ++i) {
+        const GemmDesc &g = h[i];
+        if (g.M <= 0 || g.N <= 0) {
+            opA[i] = opB[i] = -1;
+            continue;
+        }
+        opA[i] = add(Key{g.A, g.lda, g.transA == 0 ? g.a_rows : nullptr, g.k_idx_a, g.M, g.K, g.transA == 0 ? 1 : 0});
+        opB[i] = add(Key{g.B, g.ldb, g.n_idx_b, g.k_idx_b, g.N, g.K, g.transB == 1 ? 1 : 0});
+    }
+    // scale arrays, slice regions and job prefixes per operand
+    long long nexp = 0, bytes = 0;
+    std::vector<long long> j0(ops.size() + 1, 0), s0(ops.size() + 1, 0), eoff(ops.size());
+    for (size_t q = 0; q < ops.size(); ++q) {
+        OzOperand &o = ops[q];
+        const long long nkt = (o.K + BK - 1) / BK, rt = (o.R + BM - 1) / BM;
+        eoff[q] = nexp;
+        nexp += o.R;
+        o.soff = bytes;
+        bytes += rt * nkt * TILE_BYTES;
+        j0[q + 1] = j0[q] + rt * nkt;
+        s0[q + 1] = s0[q] + (o.R + SROWS - 1) / SROWS;
+    }
+    cudaError_t e = cudaMalloc(&tt.d_exps, (size_t)std::max<long long>(nexp, 1) * sizeof(int));
+    if (e != cudaSuccess) return e;
+    for (size_t q = 0; q < ops.size(); ++q) ops[q].exps = tt.d_exps + eoff[q];
+    std::vector<long long> t0(h.size() + 1, 0), so(2 * h.size(), 0);
     for (size_t i = 0; i < h.size(); ++i) {
         GemmDesc &g = h[i];
-        const bool share = shares_slices(g);
-        g.ea = tt.d_exps + off;
-        off += g.M;
-        g.eb = share ? g.ea : tt.d_exps + off;
-        off += g.N;
-        const long long nkt = (g.K + BK - 1) / BK;
-        const long long mt = (g.M + BM - 1) / BM, ntl = (g.N + BN - 1) / BN;
-        const long long tiles = (g.M > 0 && g.N > 0) ? mt * ntl : 0;
+        long long tiles = 0;
+        if (opA[i] >= 0) {
+            g.ea = ops[opA[i]].exps;
+            g.eb = ops[opB[i]].exps;
+            so[2 * i] = ops[opA[i]].soff;
+            so[2 * i + 1] = ops[opB[i]].soff;
+            tiles = (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
+        }
         t0[i + 1] = t0[i] + tiles;
-        const long long ja = (g.M > 0 && g.N > 0) ? mt * nkt : 0, jb = (g.M > 0 && g.N > 0 && !share) ? ntl * nkt : 0;
-        j0[i + 1] = j0[i] + ja + jb;
-        s0[i + 1] = s0[i] + (g.M > 0 && g.N > 0 ? (g.M + SROWS - 1) / SROWS + (share ? 0 : (g.N + SROWS - 1) / SROWS) : 0);
-        so[2 * i] = bytes;
-        bytes += ja * TILE_BYTES;
-        so[2 * i + 1] = share ? so[2 * i] : bytes;
-        bytes += jb * TILE_BYTES;
     }
     tt.tiles = t0.back();
     tt.jobs = j0.back();
+    tt.sjobs = s0.back();
     tt.scratch_bytes = bytes;
     tt.nprob = (int)h.size();
-    if ((e = cudaMalloc(&tt.d_desc, h.size() * sizeof(GemmDesc))) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(tt.d_desc, h.data(), h.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&tt.d_tile0, t0.size() * sizeof(long long))) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(tt.d_tile0, t0.data(), t0.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
-    if ((e = cudaMalloc(&tt.d_jobs0, j0.size() * sizeof(long long))) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(tt.d_jobs0, j0.data(), j0.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
-    if ((e = cudaMalloc(&tt.d_soff, so.size() * sizeof(long long))) != cudaSuccess) return e;
-    if ((e = cudaMemcpy(tt.d_soff, so.data(), so.size() * sizeof(long long), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return e;
-    tt.sjobs = s0.back();
-    if ((e = cudaMalloc(&tt.d_sjobs0, s0.size() * sizeof(long long))) != cudaSuccess) return e;
-    return cudaMemcpy(tt.d_sjobs0, s0.data(), s0.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    tt.nops = (int)ops.size();
+    auto up = [](auto *&dst, const auto &v) -> cudaError_t {
+        cudaError_t ee = cudaMalloc(&dst, std::max<size_t>(v.size(), 1) * sizeof(v[0]));
+        if (ee != cudaSuccess || v.empty()) return ee;
+        return cudaMemcpy(dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
+    };
+    if ((e = up(tt.d_desc, h)) != cudaSuccess) return e;
+    if ((e = up(tt.d_tile0, t0)) != cudaSuccess) return e;
+    if ((e = up(tt.d_soff, so)) != cudaSuccess) return e;
+    if ((e = up(tt.d_jobs0, j0)) != cudaSuccess) return e;
+    if ((e = up(tt.d_sjobs0, s0)) != cudaSuccess) return e;
+    OzOperand *dops = nullptr;
+    if ((e = up(dops, ops)) != cudaSuccess) return e;
+    tt.d_ops = dops;
+    return cudaSuccess;
 }
 
 cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err, cudaStream_t s) {
@@ -553,14 +580,15 @@ cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err
         attr = true;
     }
     cudaError_t e;
+    const OzOperand *ops = static_cast<const OzOperand *>(tt.d_ops);
     if (tt.sjobs > 0) {
         count_launch();
-        k_oz_scales<<<(unsigned)tt.sjobs, 256, 0, s>>>(tt.d_desc, tt.d_sjobs0, tt.nprob);
+        k_oz_scales<<<(unsigned)tt.sjobs, 256, 0, s>>>(ops, tt.d_sjobs0, tt.nops);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (tt.jobs > 0) {
         count_launch();
-        k_oz_slice<<<(unsigned)tt.jobs, NT, 0, s>>>(tt.d_desc, tt.d_jobs0, tt.d_soff, tt.nprob, scratch);
+        k_oz_slice<<<(unsigned)tt.jobs, NT, 0, s>>>(ops, tt.d_jobs0, tt.nops, scratch);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     count_launch();
