@@ -177,6 +177,7 @@ def run_gpu(args):
         step()
     torch.cuda.synchronize()
     flops_exec = ctx.residual_flops()
+    upd32, ev64, uncv = ctx.solve_counts()
     # the metric's work per step: the residual FLOPs of the FP64 solve to tol (the iterations the problem
     # needs); the mixed solve's own count (FP32 iterations + FP64 evaluations) is reported beside it
     flops_step = flops64
@@ -241,6 +242,8 @@ def run_gpu(args):
         if "residual" in stages else None,
         "residual_flops_per_step": flops_step,
         "residual_flops_executed_per_step": flops_exec,
+        "residual_iterations": {"fp32_updates": upd32, "fp64_evals": ev64, "unconverged": uncv,
+                                "clusters": len(ctx.cluster_info()[0])},
         "fp64_stage_ms": {k: v[0] for k, v in stages64.items()},
         "energy_Eh": E, "energy_linear_Eh": E_lin,
         "fp64_ms_per_step": fp64_ms, "mixed_vs_fp64": fp64_ms / ms, "energy_fp64_Eh": E64,

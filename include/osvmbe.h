@@ -156,8 +156,14 @@ osv_status osv_residual_flops(osv_ctx *ctx, double *flops);
 /* Algorithmic FLOPs of the per-cluster partials of gradient_backward (the densities of Eqs. 14-16, 33-34 in
  * the pseudo-canonical pair bases), for the clusters of the last solve with a non-zero MBE weight: per pair of
  * order r, 8 r^3 (Tb L T^T + T^T L Tb and Tb T^T + T^T Tb); per coupling term (r_p, r_q),
- * 4 r_p^2 r_q + 6 r_p r_q^2.  Synchronises.  HOST *flops. */
+ * 4 r_p^2 r_q + 4 r_p r_q^2 (Tb S~, Tb^T S~, then those times T~' and T~'^T).  Synchronises.  HOST *flops. */
 osv_status osv_adjoint_flops(osv_ctx *ctx, double *flops);
+
+/* Iteration statistics of the last cluster_residual_solve (synchronises), summed over clusters:
+ * *updates32 = FP32 Jacobi updates (mixed modes: first solve and correction solves; 0 in FP64 mode),
+ * *evals64 = FP64-accurate residual evaluations (FP64 mode: iterations + 1 per cluster), *unconverged =
+ * clusters that hit max_iter (their FP32 updates are not counted).  HOST outputs. */
+osv_status osv_solve_counts(osv_ctx *ctx, long long *updates32, long long *evals64, int *unconverged);
 
 /* Process-wide number of CUDA kernel launches issued by this library so far (HOST *count). */
 osv_status osv_kernel_launches(long long *count);

@@ -145,25 +145,24 @@ __global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
                 Tb[(long long)a * np + b] = R(2) * Tp[(long long)a * np + b] - Tp[(long long)b * np + a];
             }
             __syncthreads();
-            // U1 = Tb S (rp x rq), U2 = Tb^T S, M1 = S T' (rp x rq)
+            // U1 = Tb S (rp x rq), U2 = Tb^T S
             sgemm_d<R>(rp, rq, rp, Tb, np, false, nullptr, Sb, lds, T.s_trans, U1, nq, R(1), false);
             sgemm_d<R>(rp, rq, rp, Tb, np, true, nullptr, Sb, lds, T.s_trans, U2, nq, R(1), false);
-            sgemm_d<R>(rp, rq, rq, Sb, lds, T.s_trans, nullptr, Tq, nq, T.t_trans, M1, nq, R(1), false);
             __syncthreads();
-            // X = <S T', Tb S>
+            // M2 = U1 T'^T (+ U2 T' below), rp x rq;  X = <S T', Tb S> = tr(T'^T S^T Tb S) = <S, U1 T'^T>
+            sgemm_d<R>(rp, rq, rq, U1, nq, false, nullptr, Tq, nq, !T.t_trans, M2, nq, R(1), false);
+            __syncthreads();
             double x = 0.0;
             for (int idx = tid; idx < rp * rq; idx += kThreads) {
-                const long long o = (long long)(idx / rq) * nq + idx % rq;
-                x += (double)M1[o] * (double)U1[o];
+                const int a = idx / rq, b = idx % rq;
+                const double sab = T.s_trans ? (double)Sb[(long long)b * lds + a] : (double)Sb[(long long)a * lds + b];
+                x += sab * (double)M2[(long long)a * nq + b];
             }
-            x = block_sum(x, red);
+            x = block_sum(x, red);   // also orders every read of M2 above before the accumulation below
             if (tid == 0) {
                 atomicAdd(&A.dF[(long long)T.fx * A.n_occ + T.fy], -w * x);
                 if (Pd.i != Pd.j) atomicAdd(&A.dF[(long long)T.fy * A.n_occ + T.fx], -w * x);
             }
-            // M2 = U1 T'^T + U2 T'  (rp x rq)
-            sgemm_d<R>(rp, rq, rq, U1, nq, false, nullptr, Tq, nq, !T.t_trans, M2, nq, R(1), false);
-            __syncthreads();
             sgemm_d<R>(rp, rq, rq, U2, nq, false, nullptr, Tq, nq, T.t_trans, M2, nq, R(1), true);
             __syncthreads();
             double *G = A.GSc + T.sblk;
@@ -336,18 +335,17 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                 B1[a * ld + b] = split_df(Tm.t_trans ? Tq[(long long)b * nq + a] : Tq[(long long)a * nq + b]);
             }
             __syncthreads();
-            // x = <S T', U1>;  M2 = U1 T'^T + U2 T'
+            // M2 = M2a + M2b with M2a = U1 T'^T, M2b = U2 T';  x = <S T', U1> = tr(T'^T S^T Tb S) = <S, M2a>
             double xs = 0.0;
             double *G = A.GSc + Tm.sblk;
             for (int t2 = tid; t2 < ta * tq; t2 += kAT) {
                 const int a0 = (t2 / tq) << 2, b0 = (t2 % tq) << 2;
-                float m1h[4][4] = {}, m1l[4][4] = {}, m2h[4][4] = {}, m2l[4][4] = {};
+                float mah[4][4] = {}, mal[4][4] = {}, mbh[4][4] = {}, mbl[4][4] = {};
                 for (int k = 0; k < rq; ++k) {
-                    float2 sv[4], p1[4], p2[4], tv[4], tw[4];
+                    float2 p1[4], p2[4], tv[4], tw[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int a = min(a0 + i, rp - 1), b = min(b0 + i, rq - 1);
-                        sv[i] = B0[a * ld + k];   // S(a, k)
                         p1[i] = B2[a * ld + k];   // U1(a, k)
                         p2[i] = B3[a * ld + k];   // U2(a, k)
                         tv[i] = B1[k * ld + b];   // T'(k, b)
@@ -357,9 +355,8 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            df_fma(m1h[i][j], m1l[i][j], sv[i], tv[j]);
-                            df_fma(m2h[i][j], m2l[i][j], p1[i], tw[j]);
-                            df_fma(m2h[i][j], m2l[i][j], p2[i], tv[j]);
+                            df_fma(mah[i][j], mal[i][j], p1[i], tw[j]);
+                            df_fma(mbh[i][j], mbl[i][j], p2[i], tv[j]);
                         }
                 }
 #pragma unroll
@@ -368,9 +365,10 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                     for (int j = 0; j < 4; ++j) {
                         const int a = a0 + i, b = b0 + j;
                         if (a >= rp || b >= rq) continue;
-                        const float2 u1 = B2[a * ld + b];
-                        xs += df_val(m1h[i][j], m1l[i][j]) * df_val(u1.x, u1.y);
-                        const double v = -wm * f * df_val(m2h[i][j], m2l[i][j]);
+                        const float2 sab = B0[a * ld + b];
+                        const double ma = df_val(mah[i][j], mal[i][j]);
+                        xs += df_val(sab.x, sab.y) * ma;
+                        const double v = -wm * f * (ma + df_val(mbh[i][j], mbl[i][j]));
                         if (Tm.s_trans) atomicAdd(&G[(long long)b * np + a], v);   // stored as (src pair) x (dst pair)
                         else atomicAdd(&G[(long long)a * nq + b], v);
                     }
@@ -742,7 +740,8 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
     // A1 = (omega_mu - T)^{-1} P_perp dE/dQ on the discarded space.  FP64: P_perp -> tridiagonal basis ->
     // (Tri - omega_mu)^{-1} -> P_perp -> back to the virtual basis.  Mixed: the same chain in FP32 as a
     // preconditioner of FP64 residual corrections.
-    CK(osv_project_out<double>(c.nosv, c.Q, dQ, n, nv, nm, s));
+    if (c.osv_mixed && osv_project_rows_fits(nv, nm)) CK(osv_project_rows<double>(c.nosv, c.Q, dQ, n, nv, nm, s));
+    else CK(osv_project_out<double>(c.nosv, c.Q, dQ, n, nv, nm, s));
     if (c.osv_mixed) {
         CK(osv_mixed_relax(c.refine, gb_at, n, nv, nm, c.Q, c.nosv, dQ, A1, s));
     } else {

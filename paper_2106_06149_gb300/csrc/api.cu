@@ -472,6 +472,7 @@ osv_status build_plan(osv_ctx *c) {
         ALLOC(r.AT, blk);
         ALLOC(r.RS, blk);
         ALLOC(r.nm_all, n);
+        ALLOC(r.Twy, (long long)osv_wy_floats(n, nv));
         std::vector<int> all(n, nm);
         if ((e = cudaMemcpy(r.nm_all, all.data(), n * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
             return c->cuda_fail(e, "upload n_max");
@@ -1081,10 +1082,33 @@ osv_status osv_adjoint_flops(osv_ctx *c, double *flops) {
         }
         for (int t = C.term0; t < C.term1; ++t) {
             const double rp = r[c->slots.h[c->terms.h[t].dst].pair], rq = r[c->slots.h[c->terms.h[t].src].pair];
-            total += 4.0 * rp * rp * rq + 6.0 * rp * rq * rq;
+            total += 4.0 * rp * rp * rq + 4.0 * rp * rq * rq;
         }
     }
     *flops = total;
+    return OSV_OK;
+}
+
+osv_status osv_solve_counts(osv_ctx *c, long long *updates32, long long *evals64, int *unconverged) {
+    if (!c || !updates32 || !evals64 || !unconverged) return OSV_ERR_INVALID;
+    if (!c->solved) return c->fail(OSV_ERR_INVALID, "no solved clusters");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sync");
+    std::vector<int> it(c->cl.size()), ev(c->cl.size());
+    if ((e = cudaMemcpy(it.data(), c->iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(ev.data(), c->evals64, ev.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy");
+    long long u = 0, f = 0;
+    int bad = 0;
+    for (size_t q = 0; q < it.size(); ++q) {
+        f += ev[q];
+        if (it[q] < 0) ++bad;
+        else if (c->prm.precision != OSV_FP64) u += it[q] - ev[q] + 1;   // iters = FP32 updates + FP64 evals - 1
+    }
+    *updates32 = u;
+    *evals64 = f;
+    *unconverged = bad;
     return OSV_OK;
 }
 

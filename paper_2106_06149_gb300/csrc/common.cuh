@@ -139,6 +139,8 @@ struct GemmBatch {
     GemmDesc *d_desc = nullptr;
     long long *d_tile0 = nullptr;
     long long tiles = 0;
+    long long *d_tile0_80 = nullptr;   // 80 x 80 tile offsets (double-float kernel)
+    long long tiles80 = 0;
     void add(const GemmDesc &g) { h.push_back(g); }
 };
 

@@ -5,6 +5,55 @@
 
 namespace osv {
 
+// One round's rotations J (planes (pp[t], qq[t]), cosines cs, sines sn) applied as A <- J^T A J by 2 x 2 blocks
+// (rows p_t, q_t x columns p_u, q_u: the row rotation, then the column rotation, as two separate passes would)
+// and V <- V J; each element is read and written once, by one thread.  Thread work is stepped without divisions.
+template <class R>
+__device__ __forceinline__ void jacobi_apply_round(R *A, R *V, int ne, int ld, int half, const R *cs, const R *sn,
+                                                   const int *pp, const int *qq) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int dt = nt / half, du = nt - dt * half;
+    {
+        int t = tid / half, u = tid - (tid / half) * half;
+        while (t < half) {
+            const int p = pp[t], q = qq[t], p2 = pp[u], q2 = qq[u];
+            const R ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
+            R *rp = A + p * ld, *rq = A + q * ld;
+            const R a = rp[p2], b = rp[q2], c = rq[p2], d = rq[q2];
+            const R ra = ct * a - st * c, rc = st * a + ct * c;   // rows
+            const R rb = ct * b - st * d, rd = st * b + ct * d;
+            rp[p2] = cu * ra - su * rb;                             // columns
+            rp[q2] = su * ra + cu * rb;
+            rq[p2] = cu * rc - su * rd;
+            rq[q2] = su * rc + cu * rd;
+            u += du;
+            t += dt;
+            if (u >= half) {
+                u -= half;
+                ++t;
+            }
+        }
+    }
+    {
+        const int dv = nt / ne, dk = nt - dv * ne;   // V: consecutive threads take consecutive rows k
+        int u = tid / ne, k = tid - (tid / ne) * ne;
+        while (u < half) {
+            const int p2 = pp[u], q2 = qq[u];
+            const R cu = cs[u], su = sn[u];
+            R *vk = V + k * ld;
+            const R vp = vk[p2], vq = vk[q2];
+            vk[p2] = cu * vp - su * vq;
+            vk[q2] = su * vp + cu * vq;
+            k += dk;
+            u += dv;
+            if (k >= ne) {
+                k -= ne;
+                ++u;
+            }
+        }
+    }
+}
+
 // Round-robin pairing: every round rotates ne/2 disjoint planes (p, q) at once, ne - 1 rounds per sweep.
 // A: ne x ne symmetric (leading dimension ld, ne even; padding rows/columns must be zero), rotated in place;
 // V <- V J accumulates the rotations (start from the identity, or from a basis to be updated).  Sweeps stop
@@ -56,26 +105,7 @@ __device__ bool jacobi_sweeps(R *A, R *V, int ne, int ld, R *cs, R *sn, int *pp,
                 sn[t] = s;
             }
             __syncthreads();
-            for (int idx = tid; idx < half * ne; idx += nt) {   // rows: B = J^T A
-                const int t = idx / ne, k = idx % ne;
-                const int p = pp[t], q = qq[t];
-                const R c = cs[t], s = sn[t];
-                const R ap = A[p * ld + k], aq = A[q * ld + k];
-                A[p * ld + k] = c * ap - s * aq;
-                A[q * ld + k] = s * ap + c * aq;
-            }
-            __syncthreads();
-            for (int idx = tid; idx < half * ne; idx += nt) {   // columns: A' = B J, V' = V J
-                const int t = idx / ne, k = idx % ne;
-                const int p = pp[t], q = qq[t];
-                const R c = cs[t], s = sn[t];
-                const R ap = A[k * ld + p], aq = A[k * ld + q];
-                A[k * ld + p] = c * ap - s * aq;
-                A[k * ld + q] = s * ap + c * aq;
-                const R vp = V[k * ld + p], vq = V[k * ld + q];
-                V[k * ld + p] = c * vp - s * vq;
-                V[k * ld + q] = s * vp + c * vq;
-            }
+            jacobi_apply_round(A, V, ne, ld, half, cs, sn, pp, qq);
             __syncthreads();
         }
     }

@@ -348,19 +348,22 @@ template <class R>
 __device__ void tri_solve(const R *d, const R *e, int n, R shift, R *x, R *u0, R *u1, R *u2, long long st,
                           R pivmin) {
     // current row i as (p, q) on columns i, i+1 (no fill yet), rhs in x
+    // the eliminated rhs entry of row i is carried in xi (row i + 1 is still the original when it is read)
     R p = d[0] - shift, q = n > 1 ? e[0] : (R)0;
+    R xi = x[0];
     for (int i = 0; i + 1 < n; ++i) {
         const R l = e[i];                        // entry (i+1, i)
         const R a = d[i + 1] - shift;            // (i+1, i+1)
         const R b = i + 2 < n ? e[i + 1] : (R)0; // (i+1, i+2)
-        const R xi = x[(long long)i * st], xn = x[(long long)(i + 1) * st];
+        const R xn = x[(long long)(i + 1) * st];
         if (fabs(p) >= fabs(l)) {
             if (fabs(p) < pivmin) p = p < (R)0 ? -pivmin : pivmin;
             const R mlt = l / p;
             u0[(long long)i * st] = p;
             u1[(long long)i * st] = q;
             u2[(long long)i * st] = 0;
-            x[(long long)(i + 1) * st] = xn - mlt * xi;
+            x[(long long)i * st] = xi;
+            xi = xn - mlt * xi;
             p = a - mlt * q;
             q = b;
         } else {
@@ -369,7 +372,7 @@ __device__ void tri_solve(const R *d, const R *e, int n, R shift, R *x, R *u0, R
             u1[(long long)i * st] = a;
             u2[(long long)i * st] = b;
             x[(long long)i * st] = xn;
-            x[(long long)(i + 1) * st] = xi - mlt * xn;
+            xi = xi - mlt * xn;
             p = q - mlt * a;
             q = -mlt * b;
         }
@@ -377,7 +380,7 @@ __device__ void tri_solve(const R *d, const R *e, int n, R shift, R *x, R *u0, R
     if (fabs(p) < pivmin) p = p < (R)0 ? -pivmin : pivmin;
     u0[(long long)(n - 1) * st] = p;
     // back substitution
-    R x1 = x[(long long)(n - 1) * st] / p, x2 = 0;
+    R x1 = xi / p, x2 = 0;
     x[(long long)(n - 1) * st] = x1;
     for (int i = n - 2; i >= 0; --i) {
         const R xi = (x[(long long)i * st] - u1[(long long)i * st] * x1 - u2[(long long)i * st] * x2) /
@@ -746,15 +749,42 @@ __device__ bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, float2 *c
                 sn[t] = split_df(s);
             }
             __syncthreads();
-            for (int idx = tid; idx < half * ne; idx += nt) {   // rows: B = J^T A
-                const int t = idx / ne, k = idx % ne;
-                df_rot(A[pp[t] * ld + k], A[qq[t] * ld + k], cs[t], sn[t]);
-            }
-            __syncthreads();
-            for (int idx = tid; idx < half * ne; idx += nt) {   // columns: A' = B J, V' = V J
-                const int t = idx / ne, k = idx % ne;
-                df_rot(A[k * ld + pp[t]], A[k * ld + qq[t]], cs[t], sn[t]);
-                df_rot(V[k * ld + pp[t]], V[k * ld + qq[t]], cs[t], sn[t]);
+            // A <- J^T A J by 2 x 2 blocks (row rotation, then column rotation), V <- V J; division-free stepping
+            {
+                const int dt = nt / half, du = nt - dt * half;
+                int t = tid / half, u = tid - (tid / half) * half;
+                while (t < half) {
+                    const int p = pp[t], q = qq[t], p2 = pp[u], q2 = qq[u];
+                    const float2 ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
+                    float2 *rp = A + p * ld, *rq = A + q * ld;
+                    float2 a = rp[p2], b = rp[q2], c = rq[p2], d = rq[q2];
+                    df_rot(a, c, ct, st);
+                    df_rot(b, d, ct, st);
+                    df_rot(a, b, cu, su);
+                    df_rot(c, d, cu, su);
+                    rp[p2] = a;
+                    rp[q2] = b;
+                    rq[p2] = c;
+                    rq[q2] = d;
+                    u += du;
+                    t += dt;
+                    if (u >= half) {
+                        u -= half;
+                        ++t;
+                    }
+                }
+                const int dv = nt / ne, dk = nt - dv * ne;
+                int w = tid / ne, k = tid - (tid / ne) * ne;
+                while (w < half) {
+                    float2 *vk = V + k * ld;
+                    df_rot(vk[pp[w]], vk[qq[w]], cs[w], sn[w]);
+                    k += dk;
+                    w += dv;
+                    if (k >= ne) {
+                        k -= ne;
+                        ++w;
+                    }
+                }
             }
             __syncthreads();
         }

@@ -201,15 +201,28 @@ __global__ void __launch_bounds__(kT) k_osv_finish(const double *__restrict__ la
 
 // X (FP32 rows, virtual basis) -> Z = M(shift) X: H^T, remove the FP32 kept vectors, (shift - Tri)^{-1},
 // remove them again, H.  Rows >= nkeep[b] of Z are zero.
+// H or H^T on FP32 rows: blocked (compact WY) when its shared-memory tiles fit, else reflector by reflector
+cudaError_t reflect32(const OsvRefine &r, int n, int nv, int nm, const int *nrow, float *V, int forward,
+                      cudaStream_t s) {
+    if (r.Twy && osv_reflect_wy_fits(nv)) return osv_reflect_wy(r.tri_d, r.Twy, n, nv, nm, nrow, V, forward, s);
+    return osv_reflect<float>(r.tri_d, n, nv, nm, nrow, V, forward, s);
+}
+
+template <class R>
+cudaError_t project(const int *nkeep, const R *Y, R *X, int n, int nv, int nm, cudaStream_t s) {
+    if (osv_project_rows_fits(nv, nm)) return osv_project_rows<R>(nkeep, Y, X, n, nv, nm, s);
+    return osv_project_out<R>(nkeep, Y, X, n, nv, nm, s);
+}
+
 cudaError_t apply_precond(const OsvRefine &r, int n, int nv, int nm, const int *nkeep, const double *shift,
                           cudaStream_t s) {
     cudaError_t e;
-    if ((e = osv_reflect<float>(r.tri_d, n, nv, nm, nkeep, r.X32, 1, s)) != cudaSuccess) return e;
-    if ((e = osv_project_out<float>(nkeep, r.Y32, r.X32, n, nv, nm, s)) != cudaSuccess) return e;
+    if ((e = reflect32(r, n, nv, nm, nkeep, r.X32, 1, s)) != cudaSuccess) return e;
+    if ((e = project<float>(nkeep, r.Y32, r.X32, n, nv, nm, s)) != cudaSuccess) return e;
     if ((e = osv_tri_shift_solve<float>(r.tri_d, n, nv, nm, nkeep, r.X32, r.Z32, r.work32, shift, nm, s)) != cudaSuccess)
         return e;
-    if ((e = osv_project_out<float>(nkeep, r.Y32, r.Z32, n, nv, nm, s)) != cudaSuccess) return e;
-    return osv_reflect<float>(r.tri_d, n, nv, nm, nkeep, r.Z32, 0, s);
+    if ((e = project<float>(nkeep, r.Y32, r.Z32, n, nv, nm, s)) != cudaSuccess) return e;
+    return reflect32(r, n, nv, nm, nkeep, r.Z32, 0, s);
 }
 
 cudaError_t rayleigh_ritz(const OsvRefine &r, int x, int n, int nm, int *err, cudaStream_t s) {
@@ -238,10 +251,11 @@ cudaError_t osv_mixed_eigh(const OsvRefine &r, int n, int nv, int nm, double *Q,
     const long long per = (long long)nm * nv, tot = per * n;
     const int grid = grid_for(tot);
     CK(osv_tridiag<float>(r.tri_d, n, nv, s));
+    if (r.Twy) CK(osv_wy_prepare(r.tri_d, n, nv, r.Twy, s));
     CK(osv_tri_eigvals<float>(r.tri_d, n, nv, nm, s));
     CK(osv_tri_kept_vectors<float>(r.tri_d, n, nv, nm, r.nm_all, r.Y32, r.work32, s));
     CK(cudaMemcpyAsync(r.X32, r.Y32, tot * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    CK(osv_reflect<float>(r.tri_d, n, nv, nm, r.nm_all, r.X32, 0, s));
+    CK(reflect32(r, n, nv, nm, r.nm_all, r.X32, 0, s));
     count_launch();
     k_pack_q<<<grid, kT, 0, s>>>(r.X32, r.QW[0], per, tot);
     CK(cudaGetLastError());
@@ -289,7 +303,7 @@ cudaError_t osv_mixed_relax(const OsvRefine &r, const GemmBatch &gb_at, int n, i
         count_launch();
         k_relax_resid<<<grid, kT, 0, s>>>(g, a, r.AT, r.lam, nosv, r.RS, nm, nv, tot);
         CK(cudaGetLastError());
-        CK(osv_project_out<double>(nosv, Q, r.RS, n, nv, nm, s));
+        CK(project<double>(nosv, Q, r.RS, n, nv, nm, s));
         count_launch();
         k_cast_f32<<<grid, kT, 0, s>>>(r.RS, r.X32, tot);
         CK(cudaGetLastError());
@@ -298,7 +312,7 @@ cudaError_t osv_mixed_relax(const OsvRefine &r, const GemmBatch &gb_at, int n, i
         k_acc_f64<<<grid, kT, 0, s>>>(a, r.Z32, tot, 0);
         CK(cudaGetLastError());
     }
-    CK(osv_project_out<double>(nosv, Q, a, n, nv, nm, s));
+    CK(project<double>(nosv, Q, a, n, nv, nm, s));
 #undef CK
     return cudaSuccess;
 }

@@ -25,6 +25,7 @@ struct OsvRefine {
     double *QW[2] = {nullptr, nullptr}, *GH = nullptr, *Ct = nullptr, *lam = nullptr;
     double *AT = nullptr, *RS = nullptr;   // relaxation: a T and the FP64 residual (nm x n_vir per LMO)
     int *nm_all = nullptr;                 // n_max for every LMO (rows refined)
+    float *Twy = nullptr;                  // compact-WY T factors of the FP32 reflectors (osv_wy_floats)
     GemmBatch gb_w[2], gb_gh[2], gb_rot[2], gb_fin[2];
 };
 
@@ -38,5 +39,17 @@ cudaError_t osv_mixed_eigh(const OsvRefine &r, int n_occ, int nv, int nm, double
 // r.AT = a T.  Rows >= nosv of a are zero.
 cudaError_t osv_mixed_relax(const OsvRefine &r, const GemmBatch &gb_at, int n_occ, int nv, int nm, const double *Q,
                             const int *nosv, const double *g, double *a, cudaStream_t s);
+
+// Blocked FP32 reflector products: T factors of every block of kNB reflectors (osv_wy_floats(batch, n) floats),
+// then rows mu < nrow[b] of V <- H V (forward = 0) or H^T V (forward = 1), same contract as osv_reflect<float>.
+size_t osv_wy_floats(int batch, int n);
+cudaError_t osv_wy_prepare(const TriDesc32 *d, int batch, int n, float *T, cudaStream_t s);
+bool osv_reflect_wy_fits(int n);
+cudaError_t osv_reflect_wy(const TriDesc32 *d, const float *T, int batch, int n, int nmax, const int *nrow, float *V,
+                           int forward, cudaStream_t s);
+// Same contract as osv_project_out, for nmax <= 64: FP32 arithmetic for float, double-float for double.
+bool osv_project_rows_fits(int n, int nmax);
+template <class R>
+cudaError_t osv_project_rows(const int *nkeep, const R *Y, R *X, int batch, int n, int nmax, cudaStream_t s);
 
 }  // namespace osv

@@ -1,0 +1,336 @@
+// Blocked reflector products and row projections of the mixed-precision OSV solves (Eq. 6 and Eq. 8).
+//
+// The FP32 preconditioner of the mixed route applies H^T, a projection, a tridiagonal solve, a projection and H
+// to n_max rows per LMO.  Applied one reflector at a time, H costs n - 2 dependent dot-product / update rounds
+// per row; here the reflectors are grouped in blocks of kNB and each block acts as one compact-WY factor
+// B_j = H_k0 ... H_{k0+kNB-1} = I - V_j T_j V_j^T (T_j upper triangular), so a row sees (n - 2) / kNB
+// block steps whose inner work is a small matrix product on data held in shared memory.  The projections
+// x <- x - Y^T (Y x) (classical Gram-Schmidt, twice) likewise run as two small products per pass with Y streamed
+// through shared memory; the FP64 variant computes in double-float (FP32 pipe, ~48-bit significands).
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
+#include "osv_refine.h"
+
+namespace osv {
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kNB = 32;       // reflectors per compact-WY block (one per lane)
+constexpr int kWyRows = 8;    // rows of V per CTA of the blocked product (one warp each)
+constexpr int kPoRows = 8;    // rows of X per CTA of the projection (one warp each)
+constexpr int kPoCW = 64;     // Y column chunk of the projection
+constexpr int kPoMaxY = 64;   // projection onto at most 64 rows (two per lane)
+
+// element copies global -> shared that stay in flight together (src_bytes = 0: zero fill, nothing read)
+__device__ __forceinline__ void cp_async_zfill(void *dst, const void *src, int bytes, int src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__host__ __device__ __forceinline__ int wy_blocks(int n) { return n < 3 ? 0 : (n - 2 + kNB - 1) / kNB; }
+
+// T_j of every block j of every matrix (kNB x kNB row-major, zero outside the upper triangle of the block's kb
+// reflectors).  With G = V^T V, the columns follow T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i], T[i][i] = tau_i.
+__global__ void __launch_bounds__(kT) k_wy_t(const TriDesc32 *__restrict__ descs, float *__restrict__ Tall, int J) {
+    const int b = blockIdx.x, j = blockIdx.y;
+    const TriDesc32 D = descs[b];
+    const int n = D.n;
+    float *T = Tall + ((long long)b * J + j) * kNB * kNB;
+    const int tid = threadIdx.x;
+    const int k0 = j * kNB;
+    const int kb = j < wy_blocks(n) ? min(kNB, n - 2 - k0) : 0;
+    if (kb <= 0) {
+        for (int i = tid; i < kNB * kNB; i += kT) T[i] = 0.f;
+        return;
+    }
+    const int m0 = n - k0 - 1, ld = m0 | 1;
+    extern __shared__ __align__(16) float wsm[];
+    float *Vs = wsm;                      // kb x ld: reflector i at columns k0+1+c, zero for c < i
+    float *Gs = Vs + (long long)kNB * ld;  // kNB x (kNB + 1)
+    float *Ts = Gs + kNB * (kNB + 1);      // kNB x (kNB + 1)
+    for (int idx = tid; idx < kb * m0; idx += kT) {
+        const int i = idx / m0, c = idx - i * m0;
+        Vs[i * ld + c] = c >= i ? D.A[(long long)(k0 + i) * D.lda + k0 + 1 + c] : 0.f;
+    }
+    for (int idx = tid; idx < kNB * (kNB + 1); idx += kT) Ts[idx] = 0.f;
+    __syncthreads();
+    for (int p = tid; p < kb * kb; p += kT) {
+        const int l = p / kb, i = p - l * kb;
+        if (l < i) {
+            const float *vl = Vs + l * ld, *vi = Vs + i * ld;
+            float s0 = 0.f, s1 = 0.f;
+            int c = i;
+            for (; c + 1 < m0; c += 2) {
+                s0 = fmaf(vl[c], vi[c], s0);
+                s1 = fmaf(vl[c + 1], vi[c + 1], s1);
+            }
+            if (c < m0) s0 = fmaf(vl[c], vi[c], s0);
+            Gs[l * (kNB + 1) + i] = s0 + s1;
+        }
+    }
+    __syncthreads();
+    for (int i = 0; i < kb; ++i) {
+        const float tau = D.tau[k0 + i];
+        if (tid < i) {
+            float s = 0.f;
+            for (int m = tid; m < i; ++m) s = fmaf(Ts[tid * (kNB + 1) + m], Gs[m * (kNB + 1) + i], s);
+            Ts[tid * (kNB + 1) + i] = -tau * s;
+        } else if (tid == i) {
+            Ts[i * (kNB + 1) + i] = tau;
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < kNB * kNB; idx += kT) {
+        const int i = idx / kNB, l = idx - i * kNB;
+        T[idx] = Ts[i * (kNB + 1) + l];
+    }
+}
+
+// rows mu < nrow[b] of V (nmax x n per matrix) <- H V (forward = 0: B_{J-1} first) or H^T V (forward = 1:
+// B_0^T first).  Per block: W = V_j^T y (lane i: reflector i), Z = T_j W or T_j^T W through warp shuffles,
+// y -= V_j Z; the block's reflectors and T_j are shared by the CTA's kWyRows rows.
+__global__ void __launch_bounds__(kT) k_reflect_wy(const TriDesc32 *__restrict__ descs, const float *__restrict__ Tall,
+                                                   int J, const int *__restrict__ nrow, float *__restrict__ V, int nmax,
+                                                   int forward) {
+    const int b = blockIdx.x;
+    const TriDesc32 D = descs[b];
+    const int n = D.n;
+    const int nr = nrow ? nrow[b] : nmax;
+    const int g0 = blockIdx.y * kWyRows;
+    const int Jb = wy_blocks(n);
+    if (g0 >= nr || Jb == 0) return;
+    const int rows = min(kWyRows, nr - g0);
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int ldv = (n - 1) | 1;
+    extern __shared__ __align__(16) float wsm[];
+    float *Ys = wsm;                             // kWyRows x n
+    float *Vs = Ys + (long long)kWyRows * n;     // kNB x ldv
+    float *Ts = Vs + (long long)kNB * ldv;       // kNB x (kNB + 1)
+    float *Vg = V + ((long long)b * nmax + g0) * n;
+    for (int i = tid; i < rows * n; i += kT) cp_async_zfill(Ys + i, Vg + i, 4, 4);
+    for (int s = 0; s < Jb; ++s) {
+        const int j = forward ? s : Jb - 1 - s;
+        const int k0 = j * kNB, kb = min(kNB, n - 2 - k0), m0 = n - k0 - 1, c0 = k0 + 1;
+        __syncthreads();   // previous block fully applied
+        // reflector i of the block: row k0 + i of A from column k0 + 1 + i on, zeros before (and for i >= kb)
+        for (int i = wid; i < kNB; i += kT / 32) {
+            const float *src = D.A + (long long)min(k0 + i, n - 1) * D.lda + c0;
+            for (int c = lane; c < m0; c += 32) cp_async_zfill(Vs + i * ldv + c, src + c, 4, (i < kb && c >= i) ? 4 : 0);
+        }
+        const float *Tg = Tall + ((long long)b * J + j) * kNB * kNB;
+        for (int idx = tid; idx < kNB * kNB; idx += kT) {
+            const int i = idx >> 5, l = idx & 31;
+            cp_async_zfill(Ts + i * (kNB + 1) + l, Tg + idx, 4, 4);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (wid < rows) {
+            float *y = Ys + (long long)wid * n + c0;
+            const float *vr = Vs + lane * ldv;
+            float w0 = 0.f, w1 = 0.f;
+            int c = 0;
+            for (; c + 1 < m0; c += 2) {
+                w0 = fmaf(y[c], vr[c], w0);
+                w1 = fmaf(y[c + 1], vr[c + 1], w1);
+            }
+            if (c < m0) w0 = fmaf(y[c], vr[c], w0);
+            const float w = w0 + w1;
+            float z = 0.f;
+#pragma unroll
+            for (int l = 0; l < kNB; ++l) {
+                const float wl = __shfl_sync(0xffffffffu, w, l);
+                z = fmaf(wl, forward ? Ts[l * (kNB + 1) + lane] : Ts[lane * (kNB + 1) + l], z);
+            }
+            float zr[kNB];
+#pragma unroll
+            for (int i = 0; i < kNB; ++i) zr[i] = __shfl_sync(0xffffffffu, z, i);
+            for (int cc = lane; cc < m0; cc += 32) {
+                float acc = y[cc];
+#pragma unroll
+                for (int i = 0; i < kNB; ++i) acc = fmaf(-zr[i], Vs[i * ldv + cc], acc);
+                y[cc] = acc;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < rows * n; i += kT) Vg[i] = Ys[i];
+}
+
+// Arithmetic of the projection: FP32, or double-float for FP64 data.
+struct ProjF32 {
+    using In = float;
+    using S = float;
+    static __device__ __forceinline__ S load(float x) { return x; }
+    static __device__ __forceinline__ float store(S x) { return x; }
+    static __device__ __forceinline__ S zero() { return 0.f; }
+    static __device__ __forceinline__ S neg(S x) { return -x; }
+    static __device__ __forceinline__ void fma(S &acc, S a, S b) { acc = fmaf(a, b, acc); }
+};
+struct ProjDF {
+    using In = double;
+    using S = float2;
+    static __device__ __forceinline__ S load(double x) { return split_df(x); }
+    static __device__ __forceinline__ double store(S x) { return df_val(x.x, x.y); }
+    static __device__ __forceinline__ S zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ S neg(S x) { return make_float2(-x.x, -x.y); }
+    static __device__ __forceinline__ void fma(S &acc, S a, S b) { df_fma(acc.x, acc.y, a, b); }
+};
+
+// rows mu < nk = nkeep[b] of X -= their projection on the orthonormal rows 0..nk-1 of Y (two passes of
+// C = X Y^T, X -= C Y).  CTA: kPoRows rows of X kept in shared memory; Y streamed in column chunks.
+template <class P>
+__global__ void __launch_bounds__(kT) k_project_rows(const int *__restrict__ nkeep, const typename P::In *__restrict__ Y,
+                                                     typename P::In *__restrict__ X, int n, int nmax) {
+    using S = typename P::S;
+    const int b = blockIdx.x;
+    const int nk = nkeep[b];
+    const int g0 = blockIdx.y * kPoRows;
+    if (g0 >= nk) return;
+    const int rows = min(kPoRows, nk - g0);
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    constexpr int ldy = kPoCW + 1;
+    extern __shared__ __align__(16) unsigned char praw[];
+    S *Xs = reinterpret_cast<S *>(praw);        // kPoRows x n
+    S *Ys = Xs + (long long)kPoRows * n;        // nk x ldy (one chunk)
+    S *Cs = Ys + (long long)kPoMaxY * ldy;      // kPoRows x kPoMaxY: -C
+    const typename P::In *Yb = Y + (long long)b * nmax * n;
+    typename P::In *Xg = X + ((long long)b * nmax + g0) * n;
+    // rows of X and chunks of Y arrive by asynchronous element copies into their shared slots (a double in the
+    // 8-byte slot of its (hi, lo) pair), then each thread converts the elements it copied
+    constexpr int E = (int)sizeof(typename P::In);
+    auto convert_own = [&](S *base, int cnt, int ld_s, int w) {
+        if constexpr (E == 8) {
+            for (int r = wid; r < cnt; r += kT / 32)
+                for (int c = lane; c < w; c += 32) {
+                    S *p = base + (long long)r * ld_s + c;
+                    *p = P::load(*reinterpret_cast<const double *>(p));
+                }
+        }
+    };
+    for (int r = wid; r < rows; r += kT / 32)
+        for (int c = lane; c < n; c += 32) cp_async_zfill(Xs + (long long)r * n + c, Xg + (long long)r * n + c, E, E);
+    cp_async_wait_all();
+    convert_own(Xs, rows, n, n);
+    auto load_chunk = [&](int ch, int w) {
+        for (int nu = wid; nu < nk; nu += kT / 32)
+            for (int c = lane; c < w; c += 32) cp_async_zfill(Ys + nu * ldy + c, Yb + (long long)nu * n + ch + c, E, E);
+        cp_async_wait_all();
+        convert_own(Ys, nk, ldy, w);
+    };
+    for (int pass = 0; pass < 2; ++pass) {
+        S c0 = P::zero(), c1 = P::zero();
+        for (int ch = 0; ch < n; ch += kPoCW) {
+            const int w = min(kPoCW, n - ch);
+            __syncthreads();
+            load_chunk(ch, w);
+            __syncthreads();
+            if (wid < rows) {
+                const S *x = Xs + (long long)wid * n + ch;
+                if (lane < nk) {
+                    const S *yr = Ys + lane * ldy;
+                    for (int c = 0; c < w; ++c) P::fma(c0, x[c], yr[c]);
+                }
+                if (lane + 32 < nk) {
+                    const S *yr = Ys + (lane + 32) * ldy;
+                    for (int c = 0; c < w; ++c) P::fma(c1, x[c], yr[c]);
+                }
+            }
+        }
+        if (wid < rows) {
+            if (lane < nk) Cs[wid * kPoMaxY + lane] = P::neg(c0);
+            if (lane + 32 < nk) Cs[wid * kPoMaxY + lane + 32] = P::neg(c1);
+        }
+        for (int ch = 0; ch < n; ch += kPoCW) {
+            const int w = min(kPoCW, n - ch);
+            __syncthreads();
+            load_chunk(ch, w);
+            __syncthreads();
+            if (wid < rows) {
+                S *x = Xs + (long long)wid * n + ch;
+                const S *cr = Cs + wid * kPoMaxY;
+                for (int c = lane; c < w; c += 32) {
+                    S acc = x[c];
+                    for (int nu = 0; nu < nk; ++nu) P::fma(acc, cr[nu], Ys[nu * ldy + c]);
+                    x[c] = acc;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < rows * n; i += kT) Xg[i] = P::store(Xs[i]);
+}
+
+template <class K>
+cudaError_t smem_attr(K kernel, size_t sh) {
+    if (sh > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+    return cudaSuccess;
+}
+
+constexpr size_t kSmemCap = 227 * 1024;
+
+size_t reflect_wy_smem(int n) {
+    return ((size_t)kWyRows * n + (size_t)kNB * ((n - 1) | 1) + (size_t)kNB * (kNB + 1)) * sizeof(float);
+}
+
+template <class P>
+size_t project_rows_smem(int n) {
+    return ((size_t)kPoRows * n + (size_t)kPoMaxY * (kPoCW + 1) + (size_t)kPoRows * kPoMaxY) * sizeof(typename P::S);
+}
+
+}  // namespace
+
+size_t osv_wy_floats(int batch, int n) { return (size_t)batch * std::max(wy_blocks(n), 1) * kNB * kNB; }
+
+cudaError_t osv_wy_prepare(const TriDesc32 *d, int batch, int n, float *T, cudaStream_t s) {
+    const int J = wy_blocks(n);
+    if (batch <= 0 || J == 0) return cudaSuccess;
+    const size_t sh = ((size_t)kNB * ((n - 1) | 1) + 2 * (size_t)kNB * (kNB + 1)) * sizeof(float);
+    if (sh > kSmemCap) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = smem_attr(k_wy_t, sh)) != cudaSuccess) return e;
+    count_launch();
+    k_wy_t<<<dim3(batch, J), kT, sh, s>>>(d, T, J);
+    return cudaGetLastError();
+}
+
+bool osv_reflect_wy_fits(int n) { return reflect_wy_smem(n) <= kSmemCap; }
+
+cudaError_t osv_reflect_wy(const TriDesc32 *d, const float *T, int batch, int n, int nmax, const int *nrow, float *V,
+                           int forward, cudaStream_t s) {
+    if (batch <= 0 || nmax <= 0 || wy_blocks(n) == 0) return cudaSuccess;
+    const size_t sh = reflect_wy_smem(n);
+    if (sh > kSmemCap) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = smem_attr(k_reflect_wy, sh)) != cudaSuccess) return e;
+    count_launch();
+    k_reflect_wy<<<dim3(batch, (nmax + kWyRows - 1) / kWyRows), kT, sh, s>>>(d, T, wy_blocks(n), nrow, V, nmax,
+                                                                             forward);
+    return cudaGetLastError();
+}
+
+bool osv_project_rows_fits(int n, int nmax) {
+    return nmax <= kPoMaxY && project_rows_smem<ProjDF>(n) <= kSmemCap;
+}
+
+template <class R>
+cudaError_t osv_project_rows(const int *nkeep, const R *Y, R *X, int batch, int n, int nmax, cudaStream_t s) {
+    using P = std::conditional_t<sizeof(R) == 4, ProjF32, ProjDF>;
+    if (batch <= 0 || nmax <= 0) return cudaSuccess;
+    const size_t sh = project_rows_smem<P>(n);
+    if (nmax > kPoMaxY || sh > kSmemCap) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = smem_attr(k_project_rows<P>, sh)) != cudaSuccess) return e;
+    count_launch();
+    k_project_rows<P><<<dim3(batch, (nmax + kPoRows - 1) / kPoRows), kT, sh, s>>>(nkeep, Y, X, n, nmax);
+    return cudaGetLastError();
+}
+
+template cudaError_t osv_project_rows<float>(const int *, const float *, float *, int, int, int, cudaStream_t);
+template cudaError_t osv_project_rows<double>(const int *, const double *, double *, int, int, int, cudaStream_t);
+
+}  // namespace osv

@@ -21,7 +21,8 @@ OSV_FP64, OSV_MIXED_TF32X3, OSV_MIXED_BF16X4 = 0, 1, 2
 EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv_build", "cluster_residual_solve",
            "mbe3_combine", "energy", "gradient_backward", "osv_cluster_count", "osv_cluster_info",
            "osv_eigenvalues", "osv_syev_batched", "osv_profile_enable", "osv_profile_read",
-           "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops"]
+           "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops",
+           "osv_solve_counts"]
 
 
 class OsvParams(ctypes.Structure):
@@ -70,6 +71,7 @@ def load(path=LIB_PATH):
         "osv_kernel_launches": ([P(ctypes.c_longlong)], I),
         "osv_syev_batched_noalloc": ([V, I, I, V, V, V], I),
         "osv_adjoint_flops": ([V, P(D)], I),
+        "osv_solve_counts": ([V, P(ctypes.c_longlong), P(ctypes.c_longlong), P(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -250,6 +252,12 @@ class Context:
         f = ctypes.c_double()
         _check(load().osv_adjoint_flops(self.h, ctypes.byref(f)), self.h)
         return f.value
+
+    def solve_counts(self):
+        """(FP32 Jacobi updates, FP64-accurate residual evaluations, unconverged clusters) of the last solve."""
+        u, f, bad = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+        _check(load().osv_solve_counts(self.h, ctypes.byref(u), ctypes.byref(f), ctypes.byref(bad)), self.h)
+        return u.value, f.value, bad.value
 
     def eigenvalues(self, k, n_vir):
         out = np.zeros(n_vir, np.float64)
