@@ -183,9 +183,9 @@ __global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
 // a product is formed exactly (hi*hi and its FMA error term) plus the cross terms, and sums are kept as
 // (hi, lo) pairs with an error-free two-sum.  ~12 FP32 operations per FP64 multiply-add, relative error
 // ~2^-44 per partial (the FP64 version: 2^-53; the gradient bar is ~1e-7 relative).
-// Shared memory: four np_max x ld buffers of float2: slot phase B0 = T, B1 = Tb, B2 = Tb L, B3 = L T (L =
-// diag(e)); term phase B0 = S~, B1 = Tb_p then T~'_q, B2 = U1 = Tb S~, B3 = U2 = Tb^T S~.
-constexpr int kAT = 256;
+// Shared memory: four np_max x ld buffers of float2: slot phase B0 = T, B1 = Tb, B2 = Tb L', B3 = L' T (L' =
+// diag(e) - f_ii - f_jj); term phase B0 = S~, B1 = Tb_p then T~'_q, B2 = U1 = Tb S~, B3 = U2 = Tb^T S~.
+constexpr int kAT = 512;   // one CTA per SM (its shared memory): 16 warps to hide the double-float latency
 
 struct AdjArgsS {
     const ClusterInfo *clusters;
@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                 const double t = T[(long long)a * np + b], tb = 2.0 * t - T[(long long)b * np + a];
                 B0[a * ld + b] = split_df(t);
                 B1[a * ld + b] = split_df(tb);
-                B2[a * ld + b] = split_df(tb * e[b]);   // Tb L
-                B3[a * ld + b] = split_df(e[a] * t);    // L T
+                B2[a * ld + b] = split_df(tb * (e[b] - fii - fjj));   // Tb L'
+                B3[a * ld + b] = split_df((e[a] - fii - fjj) * t);    // L' T
                 tt += t * tb;
             }
             tt = block_sum(tt, red);   // also orders the staging writes before the products
@@ -234,31 +234,54 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                 atomicAdd(&A.dF[(long long)P.i * A.n_occ + P.i], -wm * tt);
                 atomicAdd(&A.dF[(long long)P.j * A.n_occ + P.j], -wm * tt);
             }
-            // M1 = (Tb L) T^T + (L T)^T Tb ;  M2 = Tb T^T + T^T Tb
+            // M2 = Tb T^T + T^T Tb and M1' = M1 - (f_ii + f_jj) M2 = (Tb L') T^T + (L' T)^T Tb, L' = diag(e) -
+            // (f_ii + f_jj) (staged in B2, B3); two passes over k keep the register tiles small
             const int tr = (r + 3) >> 2;
             for (int t = tid; t < tr * tr; t += kAT) {
                 const int a0 = (t / tr) << 2, b0 = (t % tr) << 2;
-                float m1h[4][4] = {}, m1l[4][4] = {}, m2h[4][4] = {}, m2l[4][4] = {};
+                double m2[4][4];
+                {
+                    float h[4][4] = {}, l[4][4] = {};
+                    for (int k = 0; k < r; ++k) {
+                        float2 x[4], y[4], u[4], v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int a = min(a0 + i, r - 1), b = min(b0 + i, r - 1);
+                            x[i] = B1[a * ld + k];   // Tb(a, k)
+                            y[i] = B0[b * ld + k];   // T(b, k)
+                            u[i] = B0[k * ld + a];   // T(k, a)
+                            v[i] = B1[k * ld + b];   // Tb(k, b)
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                df_fma(h[i][j], l[i][j], x[i], y[j]);
+                                df_fma(h[i][j], l[i][j], u[i], v[j]);
+                            }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) m2[i][j] = df_val(h[i][j], l[i][j]);
+                }
+                float h[4][4] = {}, l[4][4] = {};
                 for (int k = 0; k < r; ++k) {
-                    float2 x[4], xl[4], y[4], u[4], ul[4], v[4];
+                    float2 xl[4], y[4], ul[4], v[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int a = min(a0 + i, r - 1), b = min(b0 + i, r - 1);
-                        x[i] = B1[a * ld + k];    // Tb(a, k)
-                        xl[i] = B2[a * ld + k];   // (Tb L)(a, k)
+                        xl[i] = B2[a * ld + k];   // (Tb L')(a, k)
                         y[i] = B0[b * ld + k];    // T(b, k)
-                        u[i] = B0[k * ld + a];    // T(k, a)
-                        ul[i] = B3[k * ld + a];   // (L T)(k, a)
+                        ul[i] = B3[k * ld + a];   // (L' T)(k, a)
                         v[i] = B1[k * ld + b];    // Tb(k, b)
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            df_fma(m1h[i][j], m1l[i][j], xl[i], y[j]);
-                            df_fma(m1h[i][j], m1l[i][j], ul[i], v[j]);
-                            df_fma(m2h[i][j], m2l[i][j], x[i], y[j]);
-                            df_fma(m2h[i][j], m2l[i][j], u[i], v[j]);
+                            df_fma(h[i][j], l[i][j], xl[i], y[j]);
+                            df_fma(h[i][j], l[i][j], ul[i], v[j]);
                         }
                 }
 #pragma unroll
@@ -268,9 +291,8 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                         const int a = a0 + i, b = b0 + j;
                         if (a >= r || b >= r) continue;
                         const long long o = (long long)a * np + b;
-                        const double m1 = df_val(m1h[i][j], m1l[i][j]), m2 = df_val(m2h[i][j], m2l[i][j]);
-                        atomicAdd(&A.GS[P.off + o], wm * (m1 - (fii + fjj) * m2));
-                        atomicAdd(&A.GF[P.off + o], wm * m2);
+                        atomicAdd(&A.GS[P.off + o], wm * df_val(h[i][j], l[i][j]));
+                        atomicAdd(&A.GF[P.off + o], wm * m2[i][j]);
                     }
             }
             __syncthreads();
@@ -296,36 +318,34 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                 B1[a * ld + b] = split_df(2.0 * Tp[(long long)a * np + b] - Tp[(long long)b * np + a]);
             }
             __syncthreads();
-            // U1 = Tb S (B2), U2 = Tb^T S (B3)
+            // U1 = Tb S (B2), U2 = Tb^T S (B3): one 4 x 4 tile of one of them per job
             const int ta = (rp + 3) >> 2, tq = (rq + 3) >> 2;
-            for (int t2 = tid; t2 < ta * tq; t2 += kAT) {
+            for (int job = tid; job < 2 * ta * tq; job += kAT) {
+                const bool second = job >= ta * tq;
+                const int t2 = second ? job - ta * tq : job;
                 const int a0 = (t2 / tq) << 2, b0 = (t2 % tq) << 2;
-                float u1h[4][4] = {}, u1l[4][4] = {}, u2h[4][4] = {}, u2l[4][4] = {};
+                float uh[4][4] = {}, ul[4][4] = {};
                 for (int k = 0; k < rp; ++k) {
-                    float2 x[4], xt[4], y[4];
+                    float2 x[4], y[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int a = min(a0 + i, rp - 1), b = min(b0 + i, rq - 1);
-                        x[i] = B1[a * ld + k];
-                        xt[i] = B1[k * ld + a];
+                        x[i] = second ? B1[k * ld + a] : B1[a * ld + k];
                         y[i] = B0[k * ld + b];
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            df_fma(u1h[i][j], u1l[i][j], x[i], y[j]);
-                            df_fma(u2h[i][j], u2l[i][j], xt[i], y[j]);
-                        }
+                        for (int j = 0; j < 4; ++j) df_fma(uh[i][j], ul[i][j], x[i], y[j]);
                 }
+                float2 *U = second ? B3 : B2;
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         if (a0 + i < rp && b0 + j < rq) {   // renormalised pairs
-                            const float h1 = __fadd_rn(u1h[i][j], u1l[i][j]), h2 = __fadd_rn(u2h[i][j], u2l[i][j]);
-                            B2[(a0 + i) * ld + b0 + j] = make_float2(h1, __fsub_rn(u1l[i][j], __fsub_rn(h1, u1h[i][j])));
-                            B3[(a0 + i) * ld + b0 + j] = make_float2(h2, __fsub_rn(u2l[i][j], __fsub_rn(h2, u2h[i][j])));
+                            const float h = __fadd_rn(uh[i][j], ul[i][j]);
+                            U[(a0 + i) * ld + b0 + j] = make_float2(h, __fsub_rn(ul[i][j], __fsub_rn(h, uh[i][j])));
                         }
             }
             __syncthreads();
@@ -340,24 +360,40 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
             double *G = A.GSc + Tm.sblk;
             for (int t2 = tid; t2 < ta * tq; t2 += kAT) {
                 const int a0 = (t2 / tq) << 2, b0 = (t2 % tq) << 2;
-                float mah[4][4] = {}, mal[4][4] = {}, mbh[4][4] = {}, mbl[4][4] = {};
-                for (int k = 0; k < rq; ++k) {
-                    float2 p1[4], p2[4], tv[4], tw[4];
+                double ma[4][4];
+                {
+                    float h[4][4] = {}, l[4][4] = {};
+                    for (int k = 0; k < rq; ++k) {
+                        float2 p1[4], tw[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int a = min(a0 + i, rp - 1), b = min(b0 + i, rq - 1);
-                        p1[i] = B2[a * ld + k];   // U1(a, k)
-                        p2[i] = B3[a * ld + k];   // U2(a, k)
-                        tv[i] = B1[k * ld + b];   // T'(k, b)
-                        tw[i] = B1[b * ld + k];   // T'(b, k)
+                        for (int i = 0; i < 4; ++i) {
+                            const int a = min(a0 + i, rp - 1), b = min(b0 + i, rq - 1);
+                            p1[i] = B2[a * ld + k];   // U1(a, k)
+                            tw[i] = B1[b * ld + k];   // T'(b, k)
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) df_fma(h[i][j], l[i][j], p1[i], tw[j]);
                     }
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            df_fma(mah[i][j], mal[i][j], p1[i], tw[j]);
-                            df_fma(mbh[i][j], mbl[i][j], p2[i], tv[j]);
-                        }
+                        for (int j = 0; j < 4; ++j) ma[i][j] = df_val(h[i][j], l[i][j]);
+                }
+                float h[4][4] = {}, l[4][4] = {};
+                for (int k = 0; k < rq; ++k) {
+                    float2 p2[4], tv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int a = min(a0 + i, rp - 1), b = min(b0 + i, rq - 1);
+                        p2[i] = B3[a * ld + k];   // U2(a, k)
+                        tv[i] = B1[k * ld + b];   // T'(k, b)
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) df_fma(h[i][j], l[i][j], p2[i], tv[j]);
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
@@ -366,9 +402,8 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                         const int a = a0 + i, b = b0 + j;
                         if (a >= rp || b >= rq) continue;
                         const float2 sab = B0[a * ld + b];
-                        const double ma = df_val(mah[i][j], mal[i][j]);
-                        xs += df_val(sab.x, sab.y) * ma;
-                        const double v = -wm * f * (ma + df_val(mbh[i][j], mbl[i][j]));
+                        xs += df_val(sab.x, sab.y) * ma[i][j];
+                        const double v = -wm * f * (ma[i][j] + df_val(h[i][j], l[i][j]));
                         if (Tm.s_trans) atomicAdd(&G[(long long)b * np + a], v);   // stored as (src pair) x (dst pair)
                         else atomicAdd(&G[(long long)a * nq + b], v);
                     }

@@ -30,6 +30,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kTT = 512;   // tridiagonalisation block
+constexpr int kTJ = 512;   // mixed Jacobi block (one CTA per SM: its shared memory)
 
 template <class R>
 struct Lim;
@@ -792,7 +793,7 @@ __device__ bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, float2 *c
     return conv;
 }
 
-__global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict__ descs, int *err) {
+__global__ void __launch_bounds__(kTJ) k_jacobi_mixed(const EighDesc *__restrict__ descs, int *err) {
     const EighDesc D = descs[blockIdx.x];
     const int n = D.n_dev ? min(*D.n_dev, D.n) : D.n;
     if (n <= 0) return;
@@ -806,11 +807,11 @@ __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict_
     float *cs32 = reinterpret_cast<float *>(dg + ne), *sn32 = cs32 + ne / 2;
     int *pp = reinterpret_cast<int *>(sn32 + ne / 2), *qq = pp + ne / 2, *rank = qq + ne / 2;
     float *A32 = reinterpret_cast<float *>(B0), *V32 = A32 + sq;
-    __shared__ double red[kT / 32];
+    __shared__ double red[kTJ / 32];
     __shared__ int s_flag;
     const int tid = threadIdx.x;
     auto Ag = [&](int r, int c) -> double { return (r < n && c < n) ? D.A[(long long)r * D.lda + c] : 0.0; };
-    for (int idx = tid; idx < ne * ne; idx += kT) {
+    for (int idx = tid; idx < ne * ne; idx += kTJ) {
         const int r = idx / ne, c = idx % ne;
         const double a = Ag(r, c);
         A32[r * ld + c] = (float)a;
@@ -819,7 +820,7 @@ __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict_
     }
     __syncthreads();
     jacobi_sweeps<float>(A32, V32, ne, ld, cs32, sn32, pp, qq, red, &s_flag, 20, 1e-10);
-    for (int idx = tid; idx < ne * ne; idx += kT) {
+    for (int idx = tid; idx < ne * ne; idx += kTJ) {
         const int r = idx / ne, c = idx % ne;
         B1[r * ld + c] = make_float2(V32[r * ld + c], 0.f);
     }
@@ -829,7 +830,7 @@ __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict_
     for (int step = 0; step < 2; ++step) {
         df_gemm_sm<true, false>(ne, ld, Vin, Vin, B2);   // G = V^T V
         __syncthreads();
-        for (int idx = tid; idx < ne * ne; idx += kT) {   // M = (3I - G)/2
+        for (int idx = tid; idx < ne * ne; idx += kTJ) {   // M = (3I - G)/2
             const int r = idx / ne, c = idx % ne;
             const float2 g = B2[r * ld + c];
             if (r == c) {   // 1.5 - g/2 with an exact two-sum (g ~ 1: a plain FP32 subtraction would round)
@@ -852,7 +853,7 @@ __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict_
     __syncthreads();
     df_gemm_sm<true, false>(ne, ld, B1, B0, B2);
     __syncthreads();
-    for (int idx = tid; idx < ne * ne; idx += kT) {   // symmetrise: (x + y) / 2 with a two-sum
+    for (int idx = tid; idx < ne * ne; idx += kTJ) {   // symmetrise: (x + y) / 2 with a two-sum
         const int r = idx / ne, c = idx % ne;
         if (r < c) {
             const float2 x = B2[r * ld + c], y = B2[c * ld + r];
@@ -864,25 +865,25 @@ __global__ void __launch_bounds__(kT) k_jacobi_mixed(const EighDesc *__restrict_
         }
     }
     __syncthreads();
-    for (int idx = tid; idx < ne * ne; idx += kT) {   // polish rotations accumulate from the identity
+    for (int idx = tid; idx < ne * ne; idx += kTJ) {   // polish rotations accumulate from the identity
         const int r = idx / ne, c = idx % ne;
         B3[r * ld + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
     }
     __syncthreads();
     const bool conv = jacobi_sweeps_df(B2, B3, ne, ld, cs, sn, pp, qq, red, &s_flag, 20, 1e-28);
     if (!conv && tid == 0) raise_err(err, kDevEighNoConv);
-    for (int i = tid; i < ne; i += kT) dg[i] = df_val(B2[i * ld + i].x, B2[i * ld + i].y);
+    for (int i = tid; i < ne; i += kTJ) dg[i] = df_val(B2[i * ld + i].x, B2[i * ld + i].y);
     __syncthreads();
     df_gemm_sm<false, false>(ne, ld, B1, B3, B0);   // eigenvectors V V'
-    for (int i = tid; i < n; i += kT) {
+    for (int i = tid; i < n; i += kTJ) {
         const double di = dg[i];
         int rk = 0;
         for (int j = 0; j < n; ++j) rk += (dg[j] > di) || (dg[j] == di && j < i);
         rank[i] = rk;
     }
     __syncthreads();
-    for (int i = tid; i < n; i += kT) D.w[rank[i]] = dg[i];
-    for (int idx = tid; idx < n * n; idx += kT) {
+    for (int i = tid; i < n; i += kTJ) D.w[rank[i]] = dg[i];
+    for (int idx = tid; idx < n * n; idx += kTJ) {
         const int c = idx / n, r = idx % n;    // eigenvector c, component r
         const float2 z = B0[r * ld + c];
         D.Zt[(long long)rank[c] * D.ldz + r] = df_val(z.x, z.y);
@@ -1004,7 +1005,7 @@ cudaError_t eigh_small_jacobi_mixed(const EighDesc *d, int batch, int n_max, int
     cudaError_t e;
     if ((e = smem_attr(k_jacobi_mixed, sh)) != cudaSuccess) return e;
     count_launch();
-    k_jacobi_mixed<<<batch, kT, sh, s>>>(d, err);
+    k_jacobi_mixed<<<batch, kTJ, sh, s>>>(d, err);
     return cudaGetLastError();
 }
 

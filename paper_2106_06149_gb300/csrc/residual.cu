@@ -345,18 +345,41 @@ __global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
 }
 
 // FP32 Jacobi solve of L(x) = -rhs from x = 0 until max ||R~||_F <= tol32 or the norm stops falling (by 10 %
-// per iteration: the FP32 floor); returns the number of updates.
+// per iteration: the FP32 floor); returns the number of updates.  *fresh: the residual buffer belongs to the
+// final x (false when the update cap ended the loop).
 __device__ int solve32(const SolveArgs &A, const ClusterInfo &C, const View<float> &v, double tol32, int max_it,
-                       double *red) {
+                       double *red, bool *fresh = nullptr) {
     double prev = INFINITY;
     int it = 0;
+    bool ev = false;
     for (; it < max_it; ++it) {
         const double r = residual_eval<float>(A, C, v, red);
+        ev = true;
         if (!(r > tol32) || r > 0.9 * prev) break;
         prev = r;
         jacobi_update<float>(A, C, v);
+        ev = false;
     }
+    if (fresh) *fresh = ev;
     return it;
+}
+
+// A.R (FP64) <- A.R32 on every slot of cluster C; returns max over slots of ||R~||_F.
+__device__ double promote_residual(const SolveArgs &A, const ClusterInfo &C, double *red) {
+    double rmax = 0.0;
+    for (int s = C.slot0; s < C.slot1; ++s) {
+        const Slot S = A.slots[s];
+        const int r = A.rdim[S.pair], np = A.pairs[S.pair].np;
+        double ss = 0.0;
+        for (int idx = threadIdx.x; idx < r * r; idx += kThreads) {
+            const long long o = S.t_off + (long long)(idx / r) * np + idx % r;
+            const double x = (double)A.R32[o];
+            A.R[o] = x;
+            ss += x * x;
+        }
+        rmax = fmax(rmax, sqrt(block_sum(ss, red)));
+    }
+    return rmax;
 }
 
 // Mixed cluster solve: FP32 Jacobi to the FP32 floor, then FP64 iterative refinement (FP64 residual, FP32
@@ -392,12 +415,21 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
     bool conv = false;
     int evals = 0;
     View<float> vc{A.e32, A.H32, true, A.sblk32, A.T32, A.R32, v32.G1, stage32, ld, false};
+    bool have_r = false;   // A.R already holds the residual of the current T64 (by linearity, below)
+    double r64 = 0.0;
     for (int round = 0; round < 8; ++round) {
-        const double r64 = residual_eval<double>(A, C, v64, red);
-        ++evals;
+        if (!have_r) {
+            r64 = residual_eval<double>(A, C, v64, red);
+            ++evals;
+        }
         if (!(r64 > A.tol)) {
             conv = r64 <= A.tol;
             break;
+        }
+        if (have_r) {   // the estimate missed the tolerance: evaluate afresh before the next correction
+            have_r = false;
+            --round;
+            continue;
         }
         if (round == 7 || total >= A.max_iter) break;
         // correction: L(d) = -R64 in FP32 (rhs = R64), then T64 += d
@@ -410,13 +442,22 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
             }
         }
         __syncthreads();
-        total += solve32(A, C, vc, fmax(1e-7 * r64, 0.1 * A.tol), A.max_iter, red);
+        bool fresh = false;
+        total += solve32(A, C, vc, fmax(1e-7 * r64, 0.1 * A.tol), A.max_iter, red, &fresh);
         for (int s = C.slot0; s < C.slot1; ++s) {
             const Slot S = A.slots[s];
             const long long nn = (long long)A.pairs[S.pair].np * A.pairs[S.pair].np;
             for (long long i = tid; i < nn; i += kThreads) A.T[S.t_off + i] += (double)A.T32[S.t_off + i];
         }
         __syncthreads();
+        // R is affine in T: R64(T + d) = R64(T) + L(d).  The correction solve's last evaluation holds
+        // fl32(R64(T)) + L32(d) at its final d; L(d) is of the size of R64(T), so its FP32 error is ~2^-24 |R64(T)|
+        // and the sum is the residual of the updated T64 to far below tol.  It is taken as such; a fresh FP64
+        // evaluation follows only if it misses the tolerance.
+        if (fresh) {
+            r64 = promote_residual(A, C, red);
+            have_r = true;
+        }
     }
     const double E = hylleraas(A, C, red);
     if (tid == 0) {
