@@ -602,6 +602,13 @@ cudaError_t AdjointPlan::plan(osv_ctx &c) {
                 }
             }
     }
+    std::vector<int> zr_h;
+    {
+        long long offdiag = 0;
+        for (size_t p = 0; p < c.pairs.size(); ++p) offdiag += c.pinfo.h[p].i != c.pinfo.h[p].j;
+        if ((e = adj_alloc(*this, zrows, (size_t)(offdiag * 4 * nm))) != cudaSuccess) return e;
+        zr_h.reserve((size_t)offdiag * 4 * nm);
+    }
     for (size_t p = 0; p < c.pairs.size(); ++p) {
         const PairInfo &P = c.pinfo.h[p];
         const int i = P.i, j = P.j;
@@ -616,27 +623,45 @@ cudaError_t AdjointPlan::plan(osv_ctx &c) {
             continue;
         }
         const int d[2] = {i, j};
+        // dW^(i)_x += sum_y G_xy W^(j)_y and dW^(j)_y += sum_x G_xy^T W^(i)_x (columns on the common domain): the
+        // two terms of each sum stacked along K (G rows or columns of the pair block; W rows through a row map)
+        const long long zo = (long long)zr_h.size();
+        for (int y = 0; y < 2; ++y)
+            for (int t = 0; t < nm; ++t) zr_h.push_back(c.slot_of(j, d[y]) * nm + t);
         for (int x = 0; x < 2; ++x)
-            for (int y = 0; y < 2; ++y) {
-                const double *G = GKo + P.off + (long long)x * nm * P.np + (long long)y * nm;
-                const long long oi = c.w_off[i] + (long long)c.slot_of(i, d[x]) * nm * ai;
-                const long long oj = c.w_off[j] + (long long)c.slot_of(j, d[y]) * nm * aj;
-                // dW^(i)_x += G W^(j)_y ;  dW^(j)_y += G^T W^(i)_x  (columns on the common domain)
-                GemmDesc g1 = gemm(nm, full ? c.n_aux : 0, nm, G, P.np, 0, c.W + oj, aj, 0, Z + oi, ai);
-                GemmDesc g2 = gemm(nm, full ? c.n_aux : 0, nm, G, P.np, 1, c.W + oi, ai, 0, Z + oj, aj);
-                g1.atomic = g2.atomic = 1;
-                if (!full) {
-                    const auto &m = kmap[(long long)i * n + j];
-                    g1.N = g2.N = klen[(long long)i * n + j];
-                    g1.n_idx_b = m.second;
-                    g1.n_idx_c = m.first;
-                    g2.n_idx_b = m.first;
-                    g2.n_idx_c = m.second;
-                }
-                gb_z.add(g1);
-                gb_z.add(g2);
+            for (int t = 0; t < nm; ++t) zr_h.push_back(c.slot_of(i, d[x]) * nm + t);
+        for (int x = 0; x < 2; ++x) {
+            const long long oi = c.w_off[i] + (long long)c.slot_of(i, d[x]) * nm * ai;
+            GemmDesc g1 = gemm(nm, full ? c.n_aux : 0, 2 * nm, GKo + P.off + (long long)x * nm * P.np, P.np, 0,
+                               c.W + c.w_off[j], aj, 0, Z + oi, ai);
+            g1.k_idx_b = zrows + zo;
+            g1.atomic = 1;
+            if (!full) {
+                const auto &m = kmap[(long long)i * n + j];
+                g1.N = klen[(long long)i * n + j];
+                g1.n_idx_b = m.second;
+                g1.n_idx_c = m.first;
             }
+            gb_z.add(g1);
+        }
+        for (int y = 0; y < 2; ++y) {
+            const long long oj = c.w_off[j] + (long long)c.slot_of(j, d[y]) * nm * aj;
+            GemmDesc g2 = gemm(nm, full ? c.n_aux : 0, 2 * nm, GKo + P.off + (long long)y * nm, P.np, 1,
+                               c.W + c.w_off[i], ai, 0, Z + oj, aj);
+            g2.k_idx_b = zrows + zo + 2 * nm;
+            g2.atomic = 1;
+            if (!full) {
+                const auto &m = kmap[(long long)i * n + j];
+                g2.N = klen[(long long)i * n + j];
+                g2.n_idx_b = m.first;
+                g2.n_idx_c = m.second;
+            }
+            gb_z.add(g2);
+        }
     }
+    if (!zr_h.empty() &&
+        (e = cudaMemcpy(zrows, zr_h.data(), zr_h.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
     // dB_i = sum_a Q_a Z^(i)_a  (Q rows gathered with the forward's row maps)
     {
         size_t at = 0;

@@ -19,6 +19,7 @@ struct AdjointPlan {
     // chain to W, Q, B and the OSV relaxation
     double *Z = nullptr, *dQ = nullptr, *dB64 = nullptr, *dF64 = nullptr, *A1 = nullptr;
     double *scratch = nullptr;
+    int *zrows = nullptr;   // per off-diagonal pair: W row maps of its two stacked-K products into Z
     long long pstride = 0;
     int grid = 0;
     struct {

@@ -112,6 +112,118 @@ __device__ bool jacobi_sweeps(R *A, R *V, int ne, int ld, R *cs, R *sn, int *pp,
     return conv;
 }
 
+// ------------------------------------------------------------------ double-float sweeps (FP32-pipe FP64)
+// (hi, lo) renormalised so that |lo| <= ulp(hi) / 2
+__device__ __forceinline__ float2 df_renorm(float h, float l) {
+    const float s = __fadd_rn(h, l);
+    return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
+}
+
+// (x, y) <- (c x - s y, s x + c y) in double-float
+__device__ __forceinline__ void df_rot(float2 &x, float2 &y, const float2 c, const float2 sn) {
+    float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+    const float2 ms = make_float2(-sn.x, -sn.y);
+    df_fma(h1, l1, c, x);
+    df_fma(h1, l1, ms, y);
+    df_fma(h2, l2, sn, x);
+    df_fma(h2, l2, c, y);
+    x = df_renorm(h1, l1);
+    y = df_renorm(h2, l2);
+}
+
+// Cyclic round-robin Jacobi sweeps in double-float (A, V: ne x ne pairs in shared memory; same pairing and
+// stopping rule as jacobi_sweeps, the rotation angle from FP64 values of the three entries).
+__device__ inline bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, float2 *cs, float2 *sn, int *pp, int *qq,
+                                 double *red, int *flag, int max_sweeps, double tol2) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double fro = 0.0;
+    for (int idx = tid; idx < ne * ne; idx += nt) {
+        const double a = A[(idx / ne) * ld + idx % ne].x;
+        fro += a * a;
+    }
+    fro = block_sum(fro, red);
+    const int half = ne / 2;
+    bool conv = false;
+    for (int sweep = 0;; ++sweep) {
+        double off = 0.0;
+        for (int idx = tid; idx < ne * ne; idx += nt) {
+            const int r = idx / ne, c = idx % ne;
+            if (r != c) {
+                const double a = A[r * ld + c].x;
+                off += a * a;
+            }
+        }
+        off = block_sum(off, red);
+        if (tid == 0) *flag = off <= tol2 * fro || off == 0.0;
+        __syncthreads();
+        conv = *flag;
+        __syncthreads();
+        if (conv || sweep == max_sweeps) break;
+        for (int round = 0; round < ne - 1; ++round) {
+            for (int t = tid; t < half; t += nt) {
+                int a = t == 0 ? 0 : 1 + (t - 1 + round) % (ne - 1);
+                int bb = 1 + (ne - 2 - t + round) % (ne - 1);
+                if (t == 0) bb = 1 + (ne - 2 + round) % (ne - 1);
+                const int p = min(a, bb), q = max(a, bb);
+                pp[t] = p;
+                qq[t] = q;
+                const float2 apq2 = A[p * ld + q];
+                const double apq = df_val(apq2.x, apq2.y);
+                double c = 1.0, s = 0.0;
+                if (apq != 0.0 && fabs(apq) > 1e-300) {
+                    const float2 aq = A[q * ld + q], ap = A[p * ld + p];
+                    const double th = (df_val(aq.x, aq.y) - df_val(ap.x, ap.y)) / (2.0 * apq);
+                    const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                    c = rsqrt(tt * tt + 1.0);
+                    s = tt * c;
+                }
+                cs[t] = split_df(c);
+                sn[t] = split_df(s);
+            }
+            __syncthreads();
+            // A <- J^T A J by 2 x 2 blocks (row rotation, then column rotation), V <- V J; division-free stepping
+            {
+                const int dt = nt / half, du = nt - dt * half;
+                int t = tid / half, u = tid - (tid / half) * half;
+                while (t < half) {
+                    const int p = pp[t], q = qq[t], p2 = pp[u], q2 = qq[u];
+                    const float2 ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
+                    float2 *rp = A + p * ld, *rq = A + q * ld;
+                    float2 a = rp[p2], b = rp[q2], c = rq[p2], d = rq[q2];
+                    df_rot(a, c, ct, st);
+                    df_rot(b, d, ct, st);
+                    df_rot(a, b, cu, su);
+                    df_rot(c, d, cu, su);
+                    rp[p2] = a;
+                    rp[q2] = b;
+                    rq[p2] = c;
+                    rq[q2] = d;
+                    u += du;
+                    t += dt;
+                    if (u >= half) {
+                        u -= half;
+                        ++t;
+                    }
+                }
+                const int dv = nt / ne, dk = nt - dv * ne;
+                int w = tid / ne, k = tid - (tid / ne) * ne;
+                while (w < half) {
+                    float2 *vk = V + k * ld;
+                    df_rot(vk[pp[w]], vk[qq[w]], cs[w], sn[w]);
+                    k += dk;
+                    w += dv;
+                    if (k >= ne) {
+                        k -= ne;
+                        ++w;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    return conv;
+}
+
 // rank[i] = position of diagonal entry i in decreasing order (ties by index), for i < n.
 template <class R>
 __device__ void diag_rank(const R *A, int n, int ld, int *rank) {

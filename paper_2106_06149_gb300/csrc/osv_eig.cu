@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
     const int n = D.n;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *v = reinterpret_cast<R *>(smem_raw), *p = v + n, *vo = p + n, *po = vo + n;   // global indices
+    R *nx = po + n;   // row k + 1 as pass (b) of step k leaves it (read by step k + 1 instead of global memory)
     __shared__ double part[kTT / 32];
     __shared__ R s_beta;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -79,16 +80,17 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
         // (a) row k with the pending update; reflector from its entries right of the diagonal
         if (wid == 0) {
             R *row = A + (long long)k * lda;
+            const R *src = k == 0 ? row : nx;
             const R vk = vo[k], pk = po[k];
             R ss = 0;
             for (int c = k + 1 + lane; c < n; c += 32) {
-                const R x = row[c] - vk * po[c] - pk * vo[c];
+                const R x = src[c] - vk * po[c] - pk * vo[c];
                 v[c] = x;
                 ss = fma(x, x, ss);
             }
             ss = warp_sum_t(ss);
             if (lane == 0) {
-                D.d[k] = row[k] - 2 * vk * pk;
+                D.d[k] = src[k] - 2 * vk * pk;
                 const R x0 = v[k + 1];
                 const R alpha = sqrt(ss);
                 R beta = 0;
@@ -124,20 +126,32 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
                 acc[q] = 0;
             }
             const int nr = min(4, (n - 1 - r0) / NW + 1);
-#pragma unroll 2
-            for (int c = k + 1 + lane; c < n; c += 32) {
-                const R poc = po[c], voc = vo[c], vc = v[c];
-                R a[4];
+            const bool stash = r0 == k + 1;   // warp 0's first row is row k + 1
+            // U column groups of four rows: every load of a group is issued before its first store
+            constexpr int U = sizeof(R) == 4 ? 4 : 2;
+            for (int c0 = k + 1 + lane; c0 < n; c0 += 32 * U) {
+                R a[U][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < nr) a[q] = row[q][c];
+                for (int u = 0; u < U; ++u) {
+                    const int c = c0 + 32 * u;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < nr) {
-                        a[q] = a[q] - vr[q] * poc - pr[q] * voc;
-                        row[q][c] = a[q];
-                        acc[q] = fma(a[q], vc, acc[q]);
-                    }
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nr && c < n) a[u][q] = row[q][c];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int c = c0 + 32 * u;
+                    if (c >= n) break;
+                    const R poc = po[c], voc = vo[c], vc = v[c];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nr) {
+                            a[u][q] = a[u][q] - vr[q] * poc - pr[q] * voc;
+                            row[q][c] = a[u][q];
+                            acc[q] = fma(a[u][q], vc, acc[q]);
+                        }
+                    if (stash) nx[c] = a[u][0];
+                }
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -393,10 +407,40 @@ __device__ void tri_solve(const R *d, const R *e, int n, R shift, R *x, R *u0, R
 }
 
 template <class R>
-__device__ R tri_pivmin(const TriDescT<R> &D) {
+__device__ R tri_pivmin(const R *d, const R *e, int n) {
     R tnorm = 0;
-    for (int i = 0; i < D.n; ++i) tnorm = fmax(tnorm, fabs(D.d[i]) + fabs(D.e[i]) + (i ? fabs(D.e[i - 1]) : (R)0));
+    for (int i = 0; i < n; ++i) tnorm = fmax(tnorm, fabs(d[i]) + fabs(e[i]) + (i ? fabs(e[i - 1]) : (R)0));
     return fmax(tnorm, Lim<R>::tiny) * Lim<R>::eps * (R)1e-3;
+}
+
+// Per-CTA staging of the solves below: the tridiagonal (d, e) in shared memory and, when the launcher passes
+// work == nullptr, each thread's four length-n work columns too (stride blockDim.x), so that the dependent
+// chain of a solve waits on shared-memory latency instead of L2.  Returns d; e follows it.
+template <class R>
+__device__ R *stage_tri(const TriDescT<R> &D, R *sm) {
+    for (int i = threadIdx.x; i < D.n; i += blockDim.x) {
+        sm[i] = D.d[i];
+        sm[D.n + i] = D.e[i];
+    }
+    __syncthreads();
+    return sm;
+}
+
+// work columns of thread t: x, u0, u1, u2 and their stride
+template <class R>
+struct TriWork {
+    R *x, *u0, *u1, *u2;
+    long long st;
+};
+template <class R>
+__device__ TriWork<R> tri_work(R *sm, int n, R *work, int b, int nmax, int mu) {
+    if (work) {
+        R *base = work + (long long)b * 4 * n * nmax + mu;
+        return {base, base + (long long)n * nmax, base + 2LL * n * nmax, base + 3LL * n * nmax, nmax};
+    }
+    const int T = blockDim.x;
+    R *base = sm + 2 * n + threadIdx.x;
+    return {base, base + (long long)n * T, base + 2LL * n * T, base + 3LL * n * T, T};
 }
 
 // ------------------------------------------------------------------------ 3. inverse iteration (kept)
@@ -411,12 +455,13 @@ __global__ void __launch_bounds__(64) k_tri_invit(const TriDescT<R> *__restrict_
     const int n = D.n;
     const int mu = blockIdx.y * blockDim.x + threadIdx.x;
     const int nk = nkeep[b];
+    extern __shared__ __align__(16) unsigned char tri_raw[];
+    const R *ds = stage_tri(D, reinterpret_cast<R *>(tri_raw)), *es = ds + n;
     if (mu >= nk) return;
-    const long long st = nmax;
-    R *base = work + (long long)b * 4 * n * nmax;
-    R *x = base + mu, *u0 = base + (long long)n * nmax + mu, *u1 = base + 2LL * n * nmax + mu,
-      *u2 = base + 3LL * n * nmax + mu;
-    const R pivmin = tri_pivmin(D);
+    const TriWork<R> W = tri_work(reinterpret_cast<R *>(tri_raw), n, work, b, nmax, mu);
+    const long long st = W.st;
+    R *x = W.x, *u0 = W.u0, *u1 = W.u1, *u2 = W.u2;
+    const R pivmin = tri_pivmin(ds, es, n);
     const R lam = D.w[mu];
     unsigned h = 2166136261u ^ (unsigned)(mu * 7919 + 17);
     for (int i = 0; i < n; ++i) {
@@ -424,7 +469,7 @@ __global__ void __launch_bounds__(64) k_tri_invit(const TriDescT<R> *__restrict_
         x[(long long)i * st] = (R)(0.5 + (double)(h % 1000003u) / 1000003.0);
     }
     for (int rep = 0; rep < 3; ++rep) {
-        tri_solve<R>(D.d, D.e, n, lam, x, u0, u1, u2, st, pivmin);
+        tri_solve<R>(ds, es, n, lam, x, u0, u1, u2, st, pivmin);
         R s0 = 0, s1 = 0;
         for (int i = 0; i + 1 < n; i += 2) {
             s0 = fma(x[(long long)i * st], x[(long long)i * st], s0);
@@ -448,6 +493,8 @@ __global__ void __launch_bounds__(64) k_tri_shift_solve(const TriDescT<R> *__res
     const TriDescT<R> D = descs[b];
     const int n = D.n;
     const int mu = blockIdx.y * blockDim.x + threadIdx.x;
+    extern __shared__ __align__(16) unsigned char tri_raw[];
+    const R *ds = stage_tri(D, reinterpret_cast<R *>(tri_raw)), *es = ds + n;
     if (mu >= nmax) return;
     const int nk = nkeep[b];
     R *xo = X + ((long long)b * nmax + mu) * n;
@@ -455,15 +502,14 @@ __global__ void __launch_bounds__(64) k_tri_shift_solve(const TriDescT<R> *__res
         for (int i = 0; i < n; ++i) xo[i] = 0;
         return;
     }
-    const long long st = nmax;
-    R *base = work + (long long)b * 4 * n * nmax;
-    R *x = base + mu, *u0 = base + (long long)n * nmax + mu, *u1 = base + 2LL * n * nmax + mu,
-      *u2 = base + 3LL * n * nmax + mu;
-    const R pivmin = tri_pivmin(D);
+    const TriWork<R> W = tri_work(reinterpret_cast<R *>(tri_raw), n, work, b, nmax, mu);
+    const long long st = W.st;
+    R *x = W.x, *u0 = W.u0, *u1 = W.u1, *u2 = W.u2;
+    const R pivmin = tri_pivmin(ds, es, n);
     const R *r = Rin + ((long long)b * nmax + mu) * n;
     for (int i = 0; i < n; ++i) x[(long long)i * st] = -r[i];
     const R s = shift ? (R)shift[(long long)b * shift_ld + mu] : D.w[mu];
-    tri_solve<R>(D.d, D.e, n, s, x, u0, u1, u2, st, pivmin);
+    tri_solve<R>(ds, es, n, s, x, u0, u1, u2, st, pivmin);
     for (int i = 0; i < n; ++i) xo[i] = x[(long long)i * st];
 }
 
@@ -654,11 +700,6 @@ __global__ void __launch_bounds__(kT) k_jacobi_small(const EighDesc *__restrict_
 // quadratically (one sweep, two with close eigenvalues).  Shared memory: four n x n double-float buffers (the
 // FP32 A and V of the first stage alias the first).
 
-__device__ __forceinline__ float2 df_renorm(float h, float l) {
-    const float s = __fadd_rn(h, l);
-    return make_float2(s, __fsub_rn(l, __fsub_rn(s, h)));
-}
-
 // C = op(A) op(B) for ne x ne double-float matrices in shared memory (leading dimension ld), 5 x 5 outputs per
 // thread; op = transpose when TA / TB.
 template <bool TA, bool TB>
@@ -686,111 +727,6 @@ __device__ void df_gemm_sm(int ne, int ld, const float2 *A, const float2 *B, flo
             for (int j = 0; j < 5; ++j)
                 if (r0 + i < ne && c0 + j < ne) C[(r0 + i) * ld + c0 + j] = df_renorm(h[i][j], l[i][j]);
     }
-}
-
-// (x, y) <- (c x - s y, s x + c y) in double-float
-__device__ __forceinline__ void df_rot(float2 &x, float2 &y, const float2 c, const float2 sn) {
-    float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
-    const float2 ms = make_float2(-sn.x, -sn.y);
-    df_fma(h1, l1, c, x);
-    df_fma(h1, l1, ms, y);
-    df_fma(h2, l2, sn, x);
-    df_fma(h2, l2, c, y);
-    x = df_renorm(h1, l1);
-    y = df_renorm(h2, l2);
-}
-
-// Cyclic round-robin Jacobi sweeps in double-float (A, V: ne x ne pairs in shared memory; same pairing and
-// stopping rule as jacobi_sweeps, the rotation angle from FP64 values of the three entries).
-__device__ bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, float2 *cs, float2 *sn, int *pp, int *qq,
-                                 double *red, int *flag, int max_sweeps, double tol2) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    double fro = 0.0;
-    for (int idx = tid; idx < ne * ne; idx += nt) {
-        const double a = A[(idx / ne) * ld + idx % ne].x;
-        fro += a * a;
-    }
-    fro = block_sum(fro, red);
-    const int half = ne / 2;
-    bool conv = false;
-    for (int sweep = 0;; ++sweep) {
-        double off = 0.0;
-        for (int idx = tid; idx < ne * ne; idx += nt) {
-            const int r = idx / ne, c = idx % ne;
-            if (r != c) {
-                const double a = A[r * ld + c].x;
-                off += a * a;
-            }
-        }
-        off = block_sum(off, red);
-        if (tid == 0) *flag = off <= tol2 * fro || off == 0.0;
-        __syncthreads();
-        conv = *flag;
-        __syncthreads();
-        if (conv || sweep == max_sweeps) break;
-        for (int round = 0; round < ne - 1; ++round) {
-            for (int t = tid; t < half; t += nt) {
-                int a = t == 0 ? 0 : 1 + (t - 1 + round) % (ne - 1);
-                int bb = 1 + (ne - 2 - t + round) % (ne - 1);
-                if (t == 0) bb = 1 + (ne - 2 + round) % (ne - 1);
-                const int p = min(a, bb), q = max(a, bb);
-                pp[t] = p;
-                qq[t] = q;
-                const float2 apq2 = A[p * ld + q];
-                const double apq = df_val(apq2.x, apq2.y);
-                double c = 1.0, s = 0.0;
-                if (apq != 0.0 && fabs(apq) > 1e-300) {
-                    const float2 aq = A[q * ld + q], ap = A[p * ld + p];
-                    const double th = (df_val(aq.x, aq.y) - df_val(ap.x, ap.y)) / (2.0 * apq);
-                    const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                    c = rsqrt(tt * tt + 1.0);
-                    s = tt * c;
-                }
-                cs[t] = split_df(c);
-                sn[t] = split_df(s);
-            }
-            __syncthreads();
-            // A <- J^T A J by 2 x 2 blocks (row rotation, then column rotation), V <- V J; division-free stepping
-            {
-                const int dt = nt / half, du = nt - dt * half;
-                int t = tid / half, u = tid - (tid / half) * half;
-                while (t < half) {
-                    const int p = pp[t], q = qq[t], p2 = pp[u], q2 = qq[u];
-                    const float2 ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
-                    float2 *rp = A + p * ld, *rq = A + q * ld;
-                    float2 a = rp[p2], b = rp[q2], c = rq[p2], d = rq[q2];
-                    df_rot(a, c, ct, st);
-                    df_rot(b, d, ct, st);
-                    df_rot(a, b, cu, su);
-                    df_rot(c, d, cu, su);
-                    rp[p2] = a;
-                    rp[q2] = b;
-                    rq[p2] = c;
-                    rq[q2] = d;
-                    u += du;
-                    t += dt;
-                    if (u >= half) {
-                        u -= half;
-                        ++t;
-                    }
-                }
-                const int dv = nt / ne, dk = nt - dv * ne;
-                int w = tid / ne, k = tid - (tid / ne) * ne;
-                while (w < half) {
-                    float2 *vk = V + k * ld;
-                    df_rot(vk[pp[w]], vk[qq[w]], cs[w], sn[w]);
-                    k += dk;
-                    w += dv;
-                    if (k >= ne) {
-                        k -= ne;
-                        ++w;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    return conv;
 }
 
 __global__ void __launch_bounds__(kTJ) k_jacobi_mixed(const EighDesc *__restrict__ descs, int *err) {
@@ -896,6 +832,21 @@ cudaError_t smem_attr(K kernel, size_t sh) {
     return cudaSuccess;
 }
 
+// Block size, shared memory and work pointer of the tridiagonal solves for order n: 16 threads with their work
+// columns in shared memory when they fit (work pointer nullptr), else 64 threads on the global work array.
+template <class R>
+R *tri_solve_launch(int n, R *work, int &T, size_t &sh) {
+    const size_t smem = (2 * (size_t)n + 4 * (size_t)n * 16) * sizeof(R);
+    if (smem <= 220 * 1024) {
+        T = 16;
+        sh = smem;
+        return nullptr;
+    }
+    T = 64;
+    sh = 2 * (size_t)n * sizeof(R);
+    return work;
+}
+
 }  // namespace
 
 size_t jacobi_smem_bytes(int n) {
@@ -907,7 +858,7 @@ size_t jacobi_smem_bytes(int n) {
 template <class R>
 cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
-    const size_t sh = 4 * (size_t)n * sizeof(R);
+    const size_t sh = 5 * (size_t)n * sizeof(R);
     cudaError_t e;
     if ((e = smem_attr(k_tridiag<R>, sh)) != cudaSuccess) return e;
     count_launch();
@@ -940,9 +891,14 @@ cudaError_t osv_tri_kept_vectors(const TriDescT<R> *d, int batch, int n, int nma
                                  cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
     if (nmax > 128) return cudaErrorInvalidValue;
+    int T;
+    size_t sh;
+    R *wk = tri_solve_launch<R>(n, work, T, sh);
+    cudaError_t e;
+    if ((e = smem_attr(k_tri_invit<R>, sh)) != cudaSuccess) return e;
     count_launch();
-    k_tri_invit<R><<<dim3(batch, (nmax + 63) / 64), 64, 0, s>>>(d, nkeep, Y, work, nmax);
-    cudaError_t e = cudaGetLastError();
+    k_tri_invit<R><<<dim3(batch, (nmax + T - 1) / T), T, sh, s>>>(d, nkeep, Y, wk, nmax);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
     k_orthonormalise<R><<<batch, kT, 0, s>>>(nkeep, Y, n, nmax);
@@ -974,8 +930,13 @@ template <class R>
 cudaError_t osv_tri_shift_solve(const TriDescT<R> *d, int batch, int n, int nmax, const int *nkeep, const R *Rin,
                                 R *X, R *work, const double *shift, int shift_ld, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
+    int T;
+    size_t sh;
+    R *wk = tri_solve_launch<R>(n, work, T, sh);
+    cudaError_t e;
+    if ((e = smem_attr(k_tri_shift_solve<R>, sh)) != cudaSuccess) return e;
     count_launch();
-    k_tri_shift_solve<R><<<dim3(batch, (nmax + 63) / 64), 64, 0, s>>>(d, nkeep, Rin, X, work, nmax, shift, shift_ld);
+    k_tri_shift_solve<R><<<dim3(batch, (nmax + T - 1) / T), T, sh, s>>>(d, nkeep, Rin, X, wk, nmax, shift, shift_ld);
     return cudaGetLastError();
 }
 

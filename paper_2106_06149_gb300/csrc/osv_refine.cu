@@ -154,15 +154,27 @@ __global__ void __launch_bounds__(kT) k_rr(const double *__restrict__ GH, double
         }
     }
     __syncthreads();
-    const bool conv = jacobi_sweeps<double>(H, V, ne, ld, cs, sn, pp, qq, red, &s_flag, 30, 1e-28);
+    // Jacobi on H' in double-float (FP32 pipe; an FP64 rotation sweep is bound by the FP64 rate): H' into the Tm
+    // space, the rotations into the V space, both as (hi, lo) pairs
+    float2 *Hd = reinterpret_cast<float2 *>(Tm), *Vd = reinterpret_cast<float2 *>(V);
+    float2 *csd = reinterpret_cast<float2 *>(cs), *snd = reinterpret_cast<float2 *>(sn);
+    for (int idx = tid; idx < ne * ne; idx += kT) {
+        const int r = idx / ne, c = idx % ne;
+        Hd[r * ld + c] = split_df(H[r * ld + c]);
+        Vd[r * ld + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
+    }
+    __syncthreads();
+    const bool conv = jacobi_sweeps_df(Hd, Vd, ne, ld, csd, snd, pp, qq, red, &s_flag, 30, 1e-28);
     if (!conv && tid == 0) raise_err(err, kDevEighNoConv);
+    for (int i = tid; i < ne; i += kT) H[i * ld + i] = df_val(Hd[i * ld + i].x, Hd[i * ld + i].y);
+    __syncthreads();
     diag_rank<double>(H, nm, ld, rank);
     for (int i = tid; i < nm; i += kT) lam[(long long)b * nm + rank[i]] = H[i * ld + i];
     double *ct = Ct + (long long)b * nm * nm;
     for (int idx = tid; idx < nm * nm; idx += kT) {
         const int c = idx / nm, k = idx % nm;   // new vector c, old vector k
         double s = 0.0;
-        for (int j = k; j < ne; ++j) s += V[j * ld + c] * Li[j * ld + k];
+        for (int j = k; j < ne; ++j) s += df_val(Vd[j * ld + c].x, Vd[j * ld + c].y) * Li[j * ld + k];
         ct[(long long)rank[c] * nm + k] = s;
     }
 }

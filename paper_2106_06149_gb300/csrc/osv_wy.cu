@@ -265,6 +265,73 @@ __global__ void __launch_bounds__(kT) k_project_rows(const int *__restrict__ nke
     for (int i = tid; i < rows * n; i += kT) Xg[i] = P::store(Xs[i]);
 }
 
+// Same projection with all of Y resident in shared memory (loaded once for both passes) and one row of X per
+// warp: every warp works on its own row against the shared, read-only Y, so after the load no block barrier
+// is needed.  W = warps = rows per CTA (blockDim.x = 32 W).
+template <class P>
+__global__ void __launch_bounds__(1024) k_project_rows_y(const int *__restrict__ nkeep,
+                                                         const typename P::In *__restrict__ Y,
+                                                         typename P::In *__restrict__ X, int n, int nmax) {
+    using S = typename P::S;
+    const int W = blockDim.x >> 5;
+    const int b = blockIdx.x;
+    const int nk = nkeep[b];
+    const int g0 = blockIdx.y * W;
+    if (g0 >= nk) return;
+    const int rows = min(W, nk - g0);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ldy = n | 1;
+    extern __shared__ __align__(16) unsigned char praw[];
+    S *Ys = reinterpret_cast<S *>(praw);          // nk x ldy
+    S *Xs = Ys + (long long)nmax * ldy;           // W x n
+    S *Cs = Xs + (long long)W * n;                // W x kPoMaxY: -C
+    const typename P::In *Yb = Y + (long long)b * nmax * n;
+    typename P::In *Xg = X + ((long long)b * nmax + g0) * n;
+    constexpr int E = (int)sizeof(typename P::In);
+    for (int nu = wid; nu < nk; nu += W)
+        for (int c = lane; c < n; c += 32) cp_async_zfill(Ys + (long long)nu * ldy + c, Yb + (long long)nu * n + c, E, E);
+    if (wid < rows)
+        for (int c = lane; c < n; c += 32) cp_async_zfill(Xs + (long long)wid * n + c, Xg + (long long)wid * n + c, E, E);
+    cp_async_wait_all();
+    if constexpr (E == 8) {   // each thread converts the doubles it copied into (hi, lo) pairs
+        for (int nu = wid; nu < nk; nu += W)
+            for (int c = lane; c < n; c += 32) {
+                S *q = Ys + (long long)nu * ldy + c;
+                *q = P::load(*reinterpret_cast<const double *>(q));
+            }
+        if (wid < rows)
+            for (int c = lane; c < n; c += 32) {
+                S *q = Xs + (long long)wid * n + c;
+                *q = P::load(*reinterpret_cast<const double *>(q));
+            }
+    }
+    __syncthreads();
+    if (wid >= rows) return;
+    S *x = Xs + (long long)wid * n;
+    S *cr = Cs + wid * kPoMaxY;
+    for (int pass = 0; pass < 2; ++pass) {
+        S c0 = P::zero(), c1 = P::zero();
+        if (lane < nk) {
+            const S *yr = Ys + (long long)lane * ldy;
+            for (int c = 0; c < n; ++c) P::fma(c0, x[c], yr[c]);
+        }
+        if (lane + 32 < nk) {
+            const S *yr = Ys + (long long)(lane + 32) * ldy;
+            for (int c = 0; c < n; ++c) P::fma(c1, x[c], yr[c]);
+        }
+        if (lane < nk) cr[lane] = P::neg(c0);
+        if (lane + 32 < nk) cr[lane + 32] = P::neg(c1);
+        __syncwarp();
+        for (int c = lane; c < n; c += 32) {
+            S acc = x[c];
+            for (int nu = 0; nu < nk; ++nu) P::fma(acc, cr[nu], Ys[(long long)nu * ldy + c]);
+            x[c] = acc;
+        }
+        __syncwarp();
+    }
+    for (int c = lane; c < n; c += 32) Xg[(long long)wid * n + c] = P::store(x[c]);
+}
+
 template <class K>
 cudaError_t smem_attr(K kernel, size_t sh) {
     if (sh > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
@@ -321,6 +388,19 @@ template <class R>
 cudaError_t osv_project_rows(const int *nkeep, const R *Y, R *X, int batch, int n, int nmax, cudaStream_t s) {
     using P = std::conditional_t<sizeof(R) == 4, ProjF32, ProjDF>;
     if (batch <= 0 || nmax <= 0) return cudaSuccess;
+    if (nmax <= kPoMaxY) {
+        // Y resident: rows per CTA so that the grid is about one CTA per SM (at most 32 rows, one warp each)
+        const int per = std::max(1, 152 / batch);
+        const int W = std::min(32, std::max(1, (nmax + per - 1) / per));
+        const size_t shy = ((size_t)nmax * (n | 1) + (size_t)W * n + (size_t)W * kPoMaxY) * sizeof(typename P::S);
+        if (shy <= kSmemCap) {
+            cudaError_t e;
+            if ((e = smem_attr(k_project_rows_y<P>, shy)) != cudaSuccess) return e;
+            count_launch();
+            k_project_rows_y<P><<<dim3(batch, (nmax + W - 1) / W), 32 * W, shy, s>>>(nkeep, Y, X, n, nmax);
+            return cudaGetLastError();
+        }
+    }
     const size_t sh = project_rows_smem<P>(n);
     if (nmax > kPoMaxY || sh > kSmemCap) return cudaErrorInvalidValue;
     cudaError_t e;
