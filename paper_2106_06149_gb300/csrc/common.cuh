@@ -139,8 +139,9 @@ struct GemmBatch {
     GemmDesc *d_desc = nullptr;
     long long *d_tile0 = nullptr;
     long long tiles = 0;
-    long long *d_tile0_80 = nullptr;   // 80 x 80 tile offsets (double-float kernel)
-    long long tiles80 = 0;
+    long long *d_tile0_df = nullptr;   // tile offsets of the double-float kernel's shape
+    long long tiles_df = 0;
+    int df_shape = 0;                  // 0: 64 x 64, 1: 80 x 80, 2: 48 x 80, 3: 80 x 48, 4: 48 x 48
     void add(const GemmDesc &g) { h.push_back(g); }
 };
 
@@ -174,7 +175,7 @@ struct EighDesc {
     double *w;
     double *Zt;
     long long ldz;
-    double *zwork;
+    double *zwork;   // n x n scratch (the mixed small Jacobi keeps its FP32 first-stage vectors here)
     double *d;     // n scratch (diagonal)
     double *e;     // n scratch (sub-diagonal)
     double *tau;   // n scratch (Householder scalars)

@@ -3,6 +3,8 @@
 // CTA, 256 threads with a 4 x 4 register tile each, K staged through shared memory in steps of 16.
 // Optional row/column index maps let one descriptor read a gathered operand (local fitting domains, stacked
 // OSV sets) without a copy.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace osv {
@@ -111,15 +113,15 @@ __global__ void __launch_bounds__(NT) k_gemm_fp64(const GemmDesc *__restrict__ d
 
 // The same grouped GEMM in double-float arithmetic (mixed modes): operands split into FP32 (hi, lo) pairs by
 // integer operations while staged, products and sums on the FP32 pipe (common.cuh); ~2^-44 relative.
-// TM x TM outputs per thread and a (16 TM) x (16 TM) tile per CTA: TM = 4 (64 x 64) for general batches,
-// TM = 5 (80 x 80) where it pads less (pair-domain products of order <= 80 fill one tile).  The next K step's
-// operands are loaded into registers before the current step's products, and staged after them.
-template <int TM>
+// TM x TN outputs per thread and a (16 TM) x (16 TN) tile per CTA, the shape chosen per batch (64 x 64 in
+// general, 80 x 80 for pair-domain products of order <= 80, 48-row or 48-column tiles for 40-row / 40-column
+// problems).  The next K step's operands are loaded into registers before the current step's
+// products, and staged after them.
+template <int TM, int TN>
 __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ descs,
                                                  const long long *__restrict__ tile0, int nprob) {
-    constexpr int TB = 16 * TM;                 // tile edge
-    constexpr int LA = TB * BK / NT;            // operand elements per thread and K step
-    static_assert(TB * BK % NT == 0, "tile");
+    constexpr int TBM = 16 * TM, TBN = 16 * TN;   // tile edges
+    constexpr int LA = TBM * BK / NT, LB = TBN * BK / NT;   // operand elements per thread and K step
     const long long t = blockIdx.x;
     int lo = 0, hi = nprob - 1;
     while (lo < hi) {
@@ -128,27 +130,27 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ des
     }
     const GemmDesc g = descs[lo];
     const long long local = t - tile0[lo];
-    const int tiles_n = (g.N + TB - 1) / TB;
-    const int m0 = int(local / tiles_n) * TB, n0 = int(local % tiles_n) * TB;
+    const int tiles_n = (g.N + TBN - 1) / TBN;
+    const int m0 = int(local / tiles_n) * TBM, n0 = int(local % tiles_n) * TBN;
 
-    __shared__ float2 As[2][BK][TB + 1];
-    __shared__ float2 Bs[2][BK][TB + 1];
+    __shared__ float2 As[2][BK][TBM + 1];
+    __shared__ float2 Bs[2][BK][TBN + 1];
 
     const int tid = threadIdx.x;
     const int tr = tid / 16, tc = tid % 16;
-    float ah[TM][TM], al[TM][TM];
+    float ah[TM][TN], al[TM][TN];
 #pragma unroll
     for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < TM; ++b) ah[a][b] = al[a][b] = 0.f;
+        for (int b = 0; b < TN; ++b) ah[a][b] = al[a][b] = 0.f;
 
-    double ra[LA], rb[LA];
+    double ra[LA], rb[LB];
     auto fetch = [&](int k0) {
 #pragma unroll
         for (int r = 0; r < LA; ++r) {
             const int e = tid + r * NT;
             int mm, kk;
-            if (g.transA == 0) { mm = e / BK; kk = e % BK; } else { kk = e / TB; mm = e % TB; }
+            if (g.transA == 0) { mm = e / BK; kk = e % BK; } else { kk = e / TBM; mm = e % TBM; }
             const int m = m0 + mm, k = k0 + kk;
             double v = 0.0;
             if (m < g.M && k < g.K) {
@@ -163,10 +165,10 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ des
             ra[r] = v;
         }
 #pragma unroll
-        for (int r = 0; r < LA; ++r) {
+        for (int r = 0; r < LB; ++r) {
             const int e = tid + r * NT;
             int kk, nn;
-            if (g.transB == 0) { kk = e / TB; nn = e % TB; } else { nn = e / BK; kk = e % BK; }
+            if (g.transB == 0) { kk = e / TBN; nn = e % TBN; } else { nn = e / BK; kk = e % BK; }
             const int n = n0 + nn, k = k0 + kk;
             double v = 0.0;
             if (n < g.N && k < g.K) {
@@ -182,14 +184,14 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ des
         for (int r = 0; r < LA; ++r) {
             const int e = tid + r * NT;
             int mm, kk;
-            if (g.transA == 0) { mm = e / BK; kk = e % BK; } else { kk = e / TB; mm = e % TB; }
+            if (g.transA == 0) { mm = e / BK; kk = e % BK; } else { kk = e / TBM; mm = e % TBM; }
             As[buf][kk][mm] = split_df(ra[r]);
         }
 #pragma unroll
-        for (int r = 0; r < LA; ++r) {
+        for (int r = 0; r < LB; ++r) {
             const int e = tid + r * NT;
             int kk, nn;
-            if (g.transB == 0) { kk = e / TB; nn = e % TB; } else { nn = e / BK; kk = e % BK; }
+            if (g.transB == 0) { kk = e / TBN; nn = e % TBN; } else { nn = e / BK; kk = e % BK; }
             Bs[buf][kk][nn] = split_df(rb[r]);
         }
     };
@@ -205,15 +207,15 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ des
         if (kt + 1 < nk) fetch((kt + 1) * BK);
 #pragma unroll 2
         for (int kk = 0; kk < BK; ++kk) {
-            float2 a[TM], b[TM];
+            float2 a[TM], b[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][tr + 16 * i];
 #pragma unroll
-            for (int j = 0; j < TM; ++j) b[j] = Bs[buf][kk][tc + 16 * j];
+            for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tc + 16 * j];
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TM; ++j) df_fma(ah[i][j], al[i][j], a[i], b[j]);
+                for (int j = 0; j < TN; ++j) df_fma(ah[i][j], al[i][j], a[i], b[j]);
         }
         if (kt + 1 < nk) stage(buf ^ 1);
         __syncthreads();
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ des
         const int m = m0 + tr + 16 * i;
         if (m >= g.M) continue;
 #pragma unroll
-        for (int j = 0; j < TM; ++j) {
+        for (int j = 0; j < TN; ++j) {
             const int n = n0 + tc + 16 * j;
             if (n >= g.N) continue;
             const long long nc = g.n_idx_c ? g.n_idx_c[n] : n;
@@ -240,37 +242,61 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ des
 cudaError_t gemm_batch_run_df(const GemmBatch &b, cudaStream_t s) {
     if (b.tiles == 0) return cudaSuccess;
     count_launch();
-    if (b.tiles80 > 0 && b.tiles80 * 80LL * 80 < b.tiles * 64LL * 64)
-        k_gemm_df<5><<<(unsigned)b.tiles80, NT, 0, s>>>(b.d_desc, b.d_tile0_80, (int)b.h.size());
-    else
-        k_gemm_df<4><<<(unsigned)b.tiles, NT, 0, s>>>(b.d_desc, b.d_tile0, (int)b.h.size());
+    const int c = b.df_shape;
+    const GemmDesc *d = b.d_desc;
+    const long long *t0 = b.d_tile0_df;
+    const unsigned grid = (unsigned)b.tiles_df;
+    const int np = (int)b.h.size();
+    switch (c) {
+        case 1: k_gemm_df<5, 5><<<grid, NT, 0, s>>>(d, t0, np); break;
+        case 2: k_gemm_df<3, 5><<<grid, NT, 0, s>>>(d, t0, np); break;
+        case 3: k_gemm_df<5, 3><<<grid, NT, 0, s>>>(d, t0, np); break;
+        case 4: k_gemm_df<3, 3><<<grid, NT, 0, s>>>(d, t0, np); break;
+        default: k_gemm_df<4, 4><<<grid, NT, 0, s>>>(d, t0, np); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t gemm_batch_upload(GemmBatch &b) {
     gemm_batch_free(b);
     if (b.h.empty()) return cudaSuccess;
-    // per-problem tile offsets for 64 x 64 tiles and, for the double-float kernel, 80 x 80 tiles
-    std::vector<long long> t0(b.h.size() + 1, 0), t80(b.h.size() + 1, 0);
-    for (size_t i = 0; i < b.h.size(); ++i) {
-        const GemmDesc &g = b.h[i];
-        const bool live = g.M > 0 && g.N > 0;
-        t0[i + 1] = t0[i] + (live ? (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN) : 0);
-        t80[i + 1] = t80[i] + (live ? (long long)((g.M + 79) / 80) * ((g.N + 79) / 80) : 0);
+    // 64 x 64 tile offsets (FP64 kernel) and the double-float kernel's tile shape: the one with the least
+    // max(1, waves of two CTAs per SM) x (tile area), i.e. the least padded work on the critical path
+    constexpr int kShapes = 5;
+    const int sm[kShapes] = {64, 80, 48, 80, 48}, sn[kShapes] = {64, 80, 80, 48, 48};
+    std::vector<long long> t[kShapes];
+    for (int c = 0; c < kShapes; ++c) {
+        t[c].assign(b.h.size() + 1, 0);
+        for (size_t i = 0; i < b.h.size(); ++i) {
+            const GemmDesc &g = b.h[i];
+            const bool live = g.M > 0 && g.N > 0;
+            t[c][i + 1] = t[c][i] + (live ? (long long)((g.M + sm[c] - 1) / sm[c]) * ((g.N + sn[c] - 1) / sn[c]) : 0);
+        }
     }
-    b.tiles = t0.back();
-    b.tiles80 = t80.back();
+    int best = 0;
+    double best_cost = 0.0;
+    for (int c = 0; c < kShapes; ++c) {
+        const double waves = std::max(1.0, (double)t[c].back() / (2 * 152));
+        const double cost = waves * sm[c] * sn[c];
+        if (c == 0 || cost < best_cost) {
+            best = c;
+            best_cost = cost;
+        }
+    }
+    b.tiles = t[0].back();
+    b.df_shape = best;
+    b.tiles_df = t[best].back();
     cudaError_t e = cudaMalloc(&b.d_desc, b.h.size() * sizeof(GemmDesc));
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&b.d_tile0, t0.size() * sizeof(long long));
+    e = cudaMalloc(&b.d_tile0, t[0].size() * sizeof(long long));
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&b.d_tile0_80, t80.size() * sizeof(long long));
+    e = cudaMalloc(&b.d_tile0_df, t[best].size() * sizeof(long long));
     if (e != cudaSuccess) return e;
     e = cudaMemcpy(b.d_desc, b.h.data(), b.h.size() * sizeof(GemmDesc), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    e = cudaMemcpy(b.d_tile0_80, t80.data(), t80.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(b.d_tile0_df, t[best].data(), t[best].size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return e;
-    return cudaMemcpy(b.d_tile0, t0.data(), t0.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    return cudaMemcpy(b.d_tile0, t[0].data(), t[0].size() * sizeof(long long), cudaMemcpyHostToDevice);
 }
 
 cudaError_t gemm_batch_run(const GemmBatch &b, cudaStream_t s) {
@@ -285,11 +311,12 @@ cudaError_t gemm_batch_run(const GemmBatch &b, cudaStream_t s) {
 void gemm_batch_free(GemmBatch &b) {
     if (b.d_desc) cudaFree(b.d_desc);
     if (b.d_tile0) cudaFree(b.d_tile0);
-    if (b.d_tile0_80) cudaFree(b.d_tile0_80);
+    if (b.d_tile0_df) cudaFree(b.d_tile0_df);
     b.d_desc = nullptr;
     b.d_tile0 = nullptr;
-    b.d_tile0_80 = nullptr;
-    b.tiles = b.tiles80 = 0;
+    b.d_tile0_df = nullptr;
+    b.tiles = b.tiles_df = 0;
+    b.df_shape = 0;
 }
 
 }  // namespace osv

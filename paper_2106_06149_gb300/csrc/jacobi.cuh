@@ -168,14 +168,18 @@ __device__ inline bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, fl
                 pp[t] = p;
                 qq[t] = q;
                 const float2 apq2 = A[p * ld + q];
-                const double apq = df_val(apq2.x, apq2.y);
                 double c = 1.0, s = 0.0;
-                if (apq != 0.0 && fabs(apq) > 1e-300) {
+                if (apq2.x != 0.f) {
+                    // the angle in FP32 (a rotation within ~1e-7 of the annihilating one still leaves only ~1e-7 of
+                    // a_pq, and the sweeps converge as fast); c and s from it in FP64 so that c^2 + s^2 = 1 to
+                    // FP64 rounding and the rotation stays orthogonal.  An FP64 division or square root is a
+                    // ~500-cycle dependent chain on GB300; one rotation round would otherwise wait on four.
                     const float2 aq = A[q * ld + q], ap = A[p * ld + p];
-                    const double th = (df_val(aq.x, aq.y) - df_val(ap.x, ap.y)) / (2.0 * apq);
-                    const double tt = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                    c = rsqrt(tt * tt + 1.0);
-                    s = tt * c;
+                    const float diff = __fadd_rn(__fsub_rn(aq.x, ap.x), __fsub_rn(aq.y, ap.y));
+                    const float th = diff / (2.f * apq2.x);
+                    const float tt = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+                    c = rsqrt(fma((double)tt, (double)tt, 1.0));
+                    s = (double)tt * c;
                 }
                 cs[t] = split_df(c);
                 sn[t] = split_df(s);

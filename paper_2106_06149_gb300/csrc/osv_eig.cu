@@ -29,7 +29,7 @@ namespace osv {
 namespace {
 
 constexpr int kT = 256;
-constexpr int kTT = 512;   // tridiagonalisation block
+constexpr int kTT = 1024;   // tridiagonalisation block
 constexpr int kTJ = 512;   // mixed Jacobi block (one CTA per SM: its shared memory)
 
 template <class R>
@@ -729,6 +729,35 @@ __device__ void df_gemm_sm(int ne, int ld, const float2 *A, const float2 *B, flo
     }
 }
 
+// zwork holds D.n x D.n doubles: room for the ne x ne FP32 first-stage vectors unless n = 1
+__device__ __forceinline__ bool jacobi_z_fits(const EighDesc &D, int n) {
+    const long long ne = (n + 1) & ~1;
+    return D.zwork != nullptr && ne * ne <= 2LL * D.n * D.n;
+}
+
+// First stage of the mixed small Jacobi on its own (small shared memory, several CTAs per SM): FP32 sweeps on
+// A from the identity; the vectors (columns) go to zwork as ne x ne floats.
+__global__ void __launch_bounds__(kT) k_jacobi32(const EighDesc *__restrict__ descs) {
+    const EighDesc D = descs[blockIdx.x];
+    const int n = D.n_dev ? min(*D.n_dev, D.n) : D.n;
+    if (n <= 0 || !jacobi_z_fits(D, n)) return;
+    const int ne = (n + 1) & ~1, ld = ne + 1;
+    extern __shared__ __align__(16) float j32[];
+    float *A32 = j32, *V32 = A32 + (long long)ne * ld, *cs = V32 + (long long)ne * ld, *sn = cs + ne / 2;
+    int *pp = reinterpret_cast<int *>(sn + ne / 2), *qq = pp + ne / 2;
+    __shared__ double red[kT / 32];
+    __shared__ int s_flag;
+    for (int idx = threadIdx.x; idx < ne * ne; idx += kT) {
+        const int r = idx / ne, c = idx % ne;
+        A32[r * ld + c] = (r < n && c < n) ? (float)D.A[(long long)r * D.lda + c] : 0.f;
+        V32[r * ld + c] = r == c ? 1.f : 0.f;
+    }
+    __syncthreads();
+    jacobi_sweeps<float>(A32, V32, ne, ld, cs, sn, pp, qq, red, &s_flag, 20, 1e-10);
+    float *Vz = reinterpret_cast<float *>(D.zwork);
+    for (int idx = threadIdx.x; idx < ne * ne; idx += kT) Vz[idx] = V32[(idx / ne) * ld + idx % ne];
+}
+
 __global__ void __launch_bounds__(kTJ) k_jacobi_mixed(const EighDesc *__restrict__ descs, int *err) {
     const EighDesc D = descs[blockIdx.x];
     const int n = D.n_dev ? min(*D.n_dev, D.n) : D.n;
@@ -747,18 +776,27 @@ __global__ void __launch_bounds__(kTJ) k_jacobi_mixed(const EighDesc *__restrict
     __shared__ int s_flag;
     const int tid = threadIdx.x;
     auto Ag = [&](int r, int c) -> double { return (r < n && c < n) ? D.A[(long long)r * D.lda + c] : 0.0; };
-    for (int idx = tid; idx < ne * ne; idx += kTJ) {
-        const int r = idx / ne, c = idx % ne;
-        const double a = Ag(r, c);
-        A32[r * ld + c] = (float)a;
-        V32[r * ld + c] = r == c ? 1.f : 0.f;
-        B3[r * ld + c] = split_df(a);   // A as double-float for A1 = V^T A V
-    }
-    __syncthreads();
-    jacobi_sweeps<float>(A32, V32, ne, ld, cs32, sn32, pp, qq, red, &s_flag, 20, 1e-10);
-    for (int idx = tid; idx < ne * ne; idx += kTJ) {
-        const int r = idx / ne, c = idx % ne;
-        B1[r * ld + c] = make_float2(V32[r * ld + c], 0.f);
+    if (jacobi_z_fits(D, n)) {   // first stage done by k_jacobi32
+        const float *Vz = reinterpret_cast<const float *>(D.zwork);
+        for (int idx = tid; idx < ne * ne; idx += kTJ) {
+            const int r = idx / ne, c = idx % ne;
+            B3[r * ld + c] = split_df(Ag(r, c));   // A as double-float for A1 = V^T A V
+            B1[r * ld + c] = make_float2(Vz[idx], 0.f);
+        }
+    } else {
+        for (int idx = tid; idx < ne * ne; idx += kTJ) {
+            const int r = idx / ne, c = idx % ne;
+            const double a = Ag(r, c);
+            A32[r * ld + c] = (float)a;
+            V32[r * ld + c] = r == c ? 1.f : 0.f;
+            B3[r * ld + c] = split_df(a);   // A as double-float for A1 = V^T A V
+        }
+        __syncthreads();
+        jacobi_sweeps<float>(A32, V32, ne, ld, cs32, sn32, pp, qq, red, &s_flag, 20, 1e-10);
+        for (int idx = tid; idx < ne * ne; idx += kTJ) {
+            const int r = idx / ne, c = idx % ne;
+            B1[r * ld + c] = make_float2(V32[r * ld + c], 0.f);
+        }
     }
     __syncthreads();
     // two Newton-Schulz steps: V in B1 -> B0 -> B1
@@ -962,10 +1000,15 @@ size_t jacobi_mixed_smem_bytes(int n) {
 cudaError_t eigh_small_jacobi_mixed(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
     if (n_max > kJacobiMixedMax) return cudaErrorInvalidValue;
+    const int ne = (n_max + 1) & ~1;
+    const size_t sh32 = (2 * (size_t)ne * (ne + 1) + ne) * sizeof(float) + (size_t)ne * sizeof(int);
     const size_t sh = jacobi_mixed_smem_bytes(n_max);
     cudaError_t e;
+    if ((e = smem_attr(k_jacobi32, sh32)) != cudaSuccess) return e;
     if ((e = smem_attr(k_jacobi_mixed, sh)) != cudaSuccess) return e;
-    count_launch();
+    count_launch(2);
+    k_jacobi32<<<batch, kT, sh32, s>>>(d);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_jacobi_mixed<<<batch, kTJ, sh, s>>>(d, err);
     return cudaGetLastError();
 }

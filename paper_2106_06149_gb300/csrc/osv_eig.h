@@ -46,7 +46,8 @@ cudaError_t osv_tri_shift_solve(const TriDescT<R> *d, int batch, int n, int nmax
 constexpr int kJacobiMax = 112;
 cudaError_t eigh_small_jacobi(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s);
 // Same contract, mixed precisions (FP32 sweeps, FP64 re-orthonormalisation and polishing sweeps) for orders
-// <= kJacobiMixedMax; results to FP64 accuracy.
+// <= kJacobiMixedMax; results to FP64 accuracy.  A descriptor's zwork (>= ne^2 / 2 doubles, ne = n rounded up
+// to even) carries the FP32 stage's vectors between its two kernels; with zwork null one kernel does both.
 constexpr int kJacobiMixedMax = 82;
 cudaError_t eigh_small_jacobi_mixed(const EighDesc *d, int batch, int n_max, int *err, cudaStream_t s);
 
