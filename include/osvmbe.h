@@ -165,6 +165,12 @@ osv_status osv_adjoint_flops(osv_ctx *ctx, double *flops);
  * clusters that hit max_iter (their FP32 updates are not counted).  HOST outputs. */
 osv_status osv_solve_counts(osv_ctx *ctx, long long *updates32, long long *evals64, int *unconverged);
 
+/* Coupling-term FLOPs of the last cluster_residual_solve split by arithmetic (synchronises): per cluster the
+ * per-evaluation count of osv_residual_flops times its FP32 evaluations (*flops32; 0 in FP64 mode) and times its
+ * FP64-accurate evaluations (*flops64: FP64 units in FP64 mode, double-float on the FP32 pipe in the mixed
+ * modes).  HOST outputs. */
+osv_status osv_residual_work(osv_ctx *ctx, double *flops32, double *flops64);
+
 /* Process-wide number of CUDA kernel launches issued by this library so far (HOST *count). */
 osv_status osv_kernel_launches(long long *count);
 

@@ -200,7 +200,7 @@ struct AdjArgsS {
 };
 
 __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
-    extern __shared__ float2 smf[];
+    extern __shared__ __align__(16) float2 smf[];
     const int ld = A.ld;
     const long long sq = (long long)ld * ld;
     float2 *B0 = smf, *B1 = smf + sq, *B2 = smf + 2 * sq, *B3 = smf + 3 * sq;
@@ -218,15 +218,27 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
             const double *T = A.Tslot + S.t_off;
             const double *e = A.e + P.e_off;
             const double fii = A.focc[(long long)P.i * A.n_occ + P.i], fjj = A.focc[(long long)P.j * A.n_occ + P.j];
+            // T lands raw (FP64) in B3's slots by asynchronous copies, all in flight together; then B0..B2, then B3
             double tt = 0.0;
             for (int idx = tid; idx < r * r; idx += kAT) {
                 const int a = idx / r, b = idx % r;
-                const double t = T[(long long)a * np + b], tb = 2.0 * t - T[(long long)b * np + a];
+                cpa_elem(B3 + a * ld + b, T + (long long)a * np + b, 8);
+            }
+            cpa_wait();
+            __syncthreads();
+            const double *Tr = reinterpret_cast<const double *>(B3);
+            for (int idx = tid; idx < r * r; idx += kAT) {
+                const int a = idx / r, b = idx % r;
+                const double t = Tr[a * ld + b], tb = 2.0 * t - Tr[b * ld + a];
                 B0[a * ld + b] = split_df(t);
                 B1[a * ld + b] = split_df(tb);
                 B2[a * ld + b] = split_df(tb * (e[b] - fii - fjj));   // Tb L'
-                B3[a * ld + b] = split_df((e[a] - fii - fjj) * t);    // L' T
                 tt += t * tb;
+            }
+            __syncthreads();
+            for (int idx = tid; idx < r * r; idx += kAT) {
+                const int a = idx / r, b = idx % r;
+                B3[a * ld + b] = split_df((e[a] - fii - fjj) * Tr[a * ld + b]);   // L' T (own element, in place)
             }
             tt = block_sum(tt, red);   // also orders the staging writes before the products
             const double wm = w * S.mult;
@@ -308,14 +320,28 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
             const long long lds = Tm.s_trans ? np : nq;
             const double *Tq = A.Tslot + Ssl.t_off, *Tp = A.Tslot + Sd.t_off;
             const double wm = w * Sd.mult;
-            // B0 = S~ (rp x rq), B1 = Tb_p
+            // B0 = S~ (rp x rq), B1 = Tb_p: S~ into B0's slots and T_p into B2's (raw FP64, asynchronous copies all
+            // in flight together), then split in place / combined into B1
             for (int idx = tid; idx < rp * rq; idx += kAT) {
                 const int a = idx / rq, b = idx % rq;
-                B0[a * ld + b] = split_df(Tm.s_trans ? Sb[(long long)b * lds + a] : Sb[(long long)a * lds + b]);
+                cpa_elem(B0 + a * ld + b, Tm.s_trans ? Sb + (long long)b * lds + a : Sb + (long long)a * lds + b, 8);
             }
             for (int idx = tid; idx < rp * rp; idx += kAT) {
                 const int a = idx / rp, b = idx % rp;
-                B1[a * ld + b] = split_df(2.0 * Tp[(long long)a * np + b] - Tp[(long long)b * np + a]);
+                cpa_elem(B2 + a * ld + b, Tp + (long long)a * np + b, 8);
+            }
+            cpa_wait();
+            for (int idx = tid; idx < rp * rq; idx += kAT) {   // own elements
+                const int a = idx / rq, b = idx % rq;
+                B0[a * ld + b] = split_df(*reinterpret_cast<const double *>(B0 + a * ld + b));
+            }
+            __syncthreads();
+            {
+                const double *Tpr = reinterpret_cast<const double *>(B2);
+                for (int idx = tid; idx < rp * rp; idx += kAT) {
+                    const int a = idx / rp, b = idx % rp;
+                    B1[a * ld + b] = split_df(2.0 * Tpr[a * ld + b] - Tpr[b * ld + a]);
+                }
             }
             __syncthreads();
             // U1 = Tb S (B2), U2 = Tb^T S (B3): one 4 x 4 tile of one of them per job
@@ -349,10 +375,15 @@ __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
                         }
             }
             __syncthreads();
-            // B1 = T~'_q (rq x rq)
+            // B1 = T~'_q (rq x rq): asynchronous copies, then each thread splits its own elements
             for (int idx = tid; idx < rq * rq; idx += kAT) {
                 const int a = idx / rq, b = idx % rq;
-                B1[a * ld + b] = split_df(Tm.t_trans ? Tq[(long long)b * nq + a] : Tq[(long long)a * nq + b]);
+                cpa_elem(B1 + a * ld + b, Tm.t_trans ? Tq + (long long)b * nq + a : Tq + (long long)a * nq + b, 8);
+            }
+            cpa_wait();
+            for (int idx = tid; idx < rq * rq; idx += kAT) {
+                const int a = idx / rq, b = idx % rq;
+                B1[a * ld + b] = split_df(*reinterpret_cast<const double *>(B1 + a * ld + b));
             }
             __syncthreads();
             // M2 = M2a + M2b with M2a = U1 T'^T, M2b = U2 T';  x = <S T', U1> = tr(T'^T S^T Tb S) = <S, M2a>

@@ -417,6 +417,7 @@ osv_status build_plan(osv_ctx *c) {
     ALLOC(c->H32, c->slot_mat);
     ALLOC(c->G1_32, (long long)c->cl.size() * c->gstride);
     ALLOC(c->evals64, c->cl.size());
+    ALLOC(c->evals32, c->cl.size());
     if (c->B_dtype == 1) {
         ALLOC(c->B64own, c->aux_ptr[n] * (long long)nv);
         c->B64 = c->B64own;
@@ -860,6 +861,7 @@ osv_status cluster_residual_solve(osv_ctx *c, int *n_iter_out, int32_t *cluster_
     a.H32 = c->H32;
     a.G1_32 = c->G1_32;
     a.evals64 = c->evals64;
+    a.evals32 = c->evals32;
     a.np_max = 2 * c->nmax;
     if ((e = cudaMemsetAsync(c->Tslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
         return c->cuda_fail(e, "memset T");
@@ -1086,6 +1088,32 @@ osv_status osv_adjoint_flops(osv_ctx *c, double *flops) {
         }
     }
     *flops = total;
+    return OSV_OK;
+}
+
+osv_status osv_residual_work(osv_ctx *c, double *flops32, double *flops64) {
+    if (!c || !flops32 || !flops64) return OSV_ERR_INVALID;
+    if (!c->solved) return c->fail(OSV_ERR_INVALID, "no solved clusters");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sync");
+    std::vector<int> r(c->pairs.size()), e32(c->cl.size()), e64(c->cl.size());
+    if ((e = cudaMemcpy(r.data(), c->rdim, r.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(e32.data(), c->evals32, e32.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(e64.data(), c->evals64, e64.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy");
+    double f32 = 0.0, f64 = 0.0;
+    for (size_t q = 0; q < c->cl.size(); ++q) {
+        double per = 0.0;
+        for (int t = c->cinfo.h[q].term0; t < c->cinfo.h[q].term1; ++t) {
+            const double rp = r[c->slots.h[c->terms.h[t].dst].pair], rq = r[c->slots.h[c->terms.h[t].src].pair];
+            per += 2.0 * (rp * rq * rq + rp * rp * rq);
+        }
+        f32 += per * (c->prm.precision != OSV_FP64 ? e32[q] : 0);
+        f64 += per * e64[q];
+    }
+    *flops32 = f32;
+    *flops64 = f64;
     return OSV_OK;
 }
 

@@ -4,7 +4,9 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -105,7 +107,64 @@ __device__ __forceinline__ float2 df_mul(const float2 a, const float2 b) {
     return make_float2(h, l);
 }
 
+
+// (hi + lo) 2^E as an FP64 number without the FP64 pipe (conversions and adds there run at 1/64 of the FP32
+// rate on GB300): the pair is renormalised with an FP32 two-sum (|lo| <= ulp(hi) / 2), then sign, exponent and the
+// significand (hi's 24 bits and lo's bits below them, in an int64) are assembled with integer operations.  Bits
+// of lo more than 29 binades below hi's leading bit are truncated (< 1 ulp of the result).  Zero, subnormal and
+// non-finite pairs and results outside the normal FP64 range take the FP64 route.
+__host__ __device__ __forceinline__ double df_to_double(float hi, float lo, int E) {
+#ifdef __CUDA_ARCH__
+    const float s = __fadd_rn(hi, lo);
+    const float bp = __fsub_rn(s, hi);
+    const float l = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(lo, bp));
+    const unsigned bh = __float_as_uint(s), bl = __float_as_uint(l);
+#else
+    const float s = hi + lo;
+    const float bp = s - hi;
+    const float l = (hi - (s - bp)) + (lo - bp);
+    unsigned bh, bl;
+    memcpy(&bh, &s, 4);
+    memcpy(&bl, &l, 4);
+#endif
+    const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);
+    int e = eh - 127 + 1023 + E;   // biased FP64 exponent of the leading bit
+    if (eh == 0 || eh == 255 || el == 255 || (el == 0 && (bl & 0x7FFFFFu)) || e <= 1 || e >= 2046)
+        return ldexp((double)s + (double)l, E);
+    long long M = (long long)((bh & 0x7FFFFFu) | 0x800000u) << 29;
+    if (el != 0) {
+        const long long ml = (long long)((bl & 0x7FFFFFu) | 0x800000u);
+        const int d = eh - el;   // >= 24 after the renormalisation
+        const long long lv = d <= 29 ? ml << (29 - d) : (d < 54 ? ml >> (d - 29) : 0);
+        if ((bh ^ bl) >> 31) M -= lv; else M += lv;
+        if (M < (1LL << 52)) {   // hi a power of two, lo of the other sign
+            M <<= 1;
+            --e;
+        }
+    }
+    const unsigned long long bits = ((unsigned long long)(bh >> 31) << 63) | ((unsigned long long)e << 52) |
+                                    ((unsigned long long)M & ((1ULL << 52) - 1));
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)bits);
+#else
+    double r;
+    memcpy(&r, &bits, 8);
+    return r;
+#endif
+}
+
+// h + l in FP64 on the FP64 pipe (kernels whose FP32 pipe is the bottleneck; df_to_double where FP64 is)
 __device__ __forceinline__ double df_val(float h, float l) { return (double)h + (double)l; }
+
+// Element copies global -> shared (4 or 8 bytes) that stay in flight together: a staging loop issues all of its
+// copies before any completes, instead of one load latency per element.  src_bytes = 0 zero-fills.
+__device__ __forceinline__ void cpa_elem(void *dst, const void *src, int bytes, int src_bytes = -1) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const int sb = src_bytes < 0 ? bytes : src_bytes;
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(sb) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(sb) : "memory");
+}
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 
 // ------------------------------------------------------------------------------------ grouped FP64 GEMM

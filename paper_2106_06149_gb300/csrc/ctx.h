@@ -82,6 +82,7 @@ struct osv_ctx {
     // FP32 copies and work arrays of the mixed residual solve
     float *e32 = nullptr, *Kt32 = nullptr, *S32 = nullptr, *T32 = nullptr, *R32 = nullptr, *H32 = nullptr, *G1_32 = nullptr;
     int *evals64 = nullptr;
+    int *evals32 = nullptr;
     int *iters = nullptr;
     long long slot_mat = 0, gstride = 0;
 

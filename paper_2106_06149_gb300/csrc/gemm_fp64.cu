@@ -231,8 +231,9 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ des
             const long long nc = g.n_idx_c ? g.n_idx_c[n] : n;
             double *c = g.C + (long long)m * g.ldc + nc;
             const double v = df_val(ah[i][j], al[i][j]);
-            if (g.atomic) atomicAdd(c, g.alpha * v);
-            else *c = g.alpha * v + (g.beta != 0.0 ? g.beta * *c : 0.0);
+            const double av = g.alpha == 1.0 ? v : g.alpha * v;
+            if (g.atomic) atomicAdd(c, av);
+            else *c = g.beta != 0.0 ? av + g.beta * *c : av;
         }
     }
 }

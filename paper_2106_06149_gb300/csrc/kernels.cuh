@@ -75,6 +75,7 @@ struct SolveArgs {
     float *T32, *R32, *H32;   // FP32 amplitudes / corrections, residuals, right-hand sides (per slot)
     float *G1_32;
     int *evals64;             // per cluster: FP64 residual evaluations used
+    int *evals32;             // per cluster: FP32 residual evaluations (mixed solve)
     int np_max;               // largest padded pair order (shared-memory staging of the FP32 terms)
 };
 

@@ -29,7 +29,7 @@ namespace osv {
 namespace {
 
 constexpr int kT = 256;
-constexpr int kTT = 1024;   // tridiagonalisation block
+constexpr int kTT = 512;   // tridiagonalisation block
 constexpr int kTJ = 512;   // mixed Jacobi block (one CTA per SM: its shared memory)
 
 template <class R>
@@ -65,8 +65,8 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *v = reinterpret_cast<R *>(smem_raw), *p = v + n, *vo = p + n, *po = vo + n;   // global indices
     R *nx = po + n;   // row k + 1 as pass (b) of step k leaves it (read by step k + 1 instead of global memory)
-    __shared__ double part[kTT / 32];
-    __shared__ R s_beta;
+    __shared__ R part[kTT / 32];   // in the working precision: FP64 conversions and adds are slow on GB300
+    __shared__ R s_beta, s_kc;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     constexpr int NW = kTT / 32;
     R *A = D.A;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
         const R beta = s_beta;
         // (b) pending update of rows r > k (columns > k) fused with p = beta A v; a warp takes four rows at a
         // time so that several independent loads are in flight per lane
-        double pv = 0.0;
+        R pv = 0;
         for (int r0 = k + 1 + wid; r0 < n; r0 += 4 * NW) {
             R *row[4];
             R vr[4], pr[4], acc[4];
@@ -159,16 +159,19 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
                 const R sum = warp_sum_t(acc[q]) * beta;
                 if (lane == 0) {
                     p[r0 + q * NW] = sum;
-                    pv += (double)sum * (double)v[r0 + q * NW];
+                    pv = fma(sum, v[r0 + q * NW], pv);
                 }
             }
         }
         if (lane == 0) part[wid] = pv;
         __syncthreads();
-        // (c) p -= (beta/2)(p.v) v; swap the pending-update buffers
-        double s = 0.0;
-        for (int w = 0; w < NW; ++w) s += part[w];
-        const R kc = (R)(0.5 * (double)beta * s);
+        // (c) p -= (beta/2)(p.v) v (the partial sums reduced by warp 0); swap the pending-update buffers
+        if (wid == 0) {
+            const R t = warp_sum_t(lane < NW ? part[lane] : (R)0);
+            if (lane == 0) s_kc = (R)0.5 * beta * t;
+        }
+        __syncthreads();
+        const R kc = s_kc;
         for (int r = k + 1 + tid; r < n; r += kTT) p[r] -= kc * v[r];
         __syncthreads();
         R *t = vo;

@@ -85,21 +85,33 @@ __device__ void term_df(int rp, int rq, const double *__restrict__ Sb, long long
                         long long ldr, double *G1, long long ldg, float2 *sm, int ld) {
     float2 *sS = sm, *sX = sm + (long long)ld * ld;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int idx = tid; idx < rp * rq; idx += nt) {
-        int a, c;
-        if (s_trans) { c = idx / rp; a = idx % rp; } else { a = idx / rq; c = idx % rq; }
-        sS[c * ld + a] = split_df(s_trans ? Sb[(long long)c * lds + a] : Sb[(long long)a * lds + c]);
-    }
-    for (int idx = tid; idx < rq * rq; idx += nt) {
-        int c, b;
-        if (t_trans) { b = idx / rq; c = idx % rq; } else { c = idx / rq; b = idx % rq; }
-        sX[c * ld + b] = split_df(t_trans ? Tq[(long long)b * ldt + c] : Tq[(long long)c * ldt + b]);
-    }
+    // the FP64 operands land in the 8-byte slots of their (hi, lo) pairs by asynchronous copies; each thread then
+    // splits the elements it copied
+    auto stage = [&](bool conv) {
+        for (int idx = tid; idx < rp * rq; idx += nt) {
+            int a, c;
+            if (s_trans) { c = idx / rp; a = idx % rp; } else { a = idx / rq; c = idx % rq; }
+            float2 *dst = sS + c * ld + a;
+            if (conv) *dst = split_df(*reinterpret_cast<const double *>(dst));
+            else cpa_elem(dst, s_trans ? Sb + (long long)c * lds + a : Sb + (long long)a * lds + c, 8);
+        }
+        for (int idx = tid; idx < rq * rq; idx += nt) {
+            int c, b;
+            if (t_trans) { b = idx / rq; c = idx % rq; } else { c = idx / rq; b = idx % rq; }
+            float2 *dst = sX + c * ld + b;
+            if (conv) *dst = split_df(*reinterpret_cast<const double *>(dst));
+            else cpa_elem(dst, t_trans ? Tq + (long long)b * ldt + c : Tq + (long long)c * ldt + b, 8);
+        }
+    };
+    stage(false);
+    cpa_wait();
+    stage(true);
     __syncthreads();
     const int ta = (rp + 4) / 5, tq = (rq + 4) / 5;
-    for (int t = tid; t < ta * tq; t += nt) {   // G1 = S~ T~'
+    // G1 = S~ T~'.  When every tile has its own thread, the tiles stay in registers across one barrier and go to
+    // sX (in place of T~') as (hi, lo) pairs; otherwise through the FP64 scratch.
+    auto g1_tile = [&](int t, float (&hh)[5][5], float (&ll)[5][5]) {
         const int a0 = (t / tq) * 5, b0 = (t % tq) * 5;
-        float hh[5][5] = {}, ll[5][5] = {};
         for (int c = 0; c < rq; ++c) {
             float2 x[5], y[5];
 #pragma unroll
@@ -112,18 +124,42 @@ __device__ void term_df(int rp, int rq, const double *__restrict__ Sb, long long
 #pragma unroll
                 for (int j = 0; j < 5; ++j) df_fma(hh[i][j], ll[i][j], x[i], y[j]);
         }
+    };
+    if (ta * tq <= nt) {
+        float hh[5][5] = {}, ll[5][5] = {};
+        const bool mine = tid < ta * tq;
+        if (mine) g1_tile(tid, hh, ll);
+        __syncthreads();
+        if (mine) {
+            const int a0 = (tid / tq) * 5, b0 = (tid % tq) * 5;
 #pragma unroll
-        for (int i = 0; i < 5; ++i)
+            for (int i = 0; i < 5; ++i)
 #pragma unroll
-            for (int j = 0; j < 5; ++j)
-                if (a0 + i < rp && b0 + j < rq) G1[(long long)(a0 + i) * ldg + b0 + j] = df_val(hh[i][j], ll[i][j]);
+                for (int j = 0; j < 5; ++j)
+                    if (a0 + i < rp && b0 + j < rq) {
+                        const float h = __fadd_rn(hh[i][j], ll[i][j]);
+                        sX[(b0 + j) * ld + a0 + i] = make_float2(h, __fsub_rn(ll[i][j], __fsub_rn(h, hh[i][j])));
+                    }
+        }
+        __syncthreads();
+    } else {
+        for (int t = tid; t < ta * tq; t += nt) {
+            float hh[5][5] = {}, ll[5][5] = {};
+            g1_tile(t, hh, ll);
+            const int a0 = (t / tq) * 5, b0 = (t % tq) * 5;
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    if (a0 + i < rp && b0 + j < rq) G1[(long long)(a0 + i) * ldg + b0 + j] = df_val(hh[i][j], ll[i][j]);
+        }
+        __syncthreads();
+        for (int idx = tid; idx < rp * rq; idx += nt) {   // sX[c][a] = G1(a, c)
+            const int a = idx / rq, c = idx % rq;
+            sX[c * ld + a] = split_df(G1[(long long)a * ldg + c]);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int idx = tid; idx < rp * rq; idx += nt) {   // sX[c][a] = G1(a, c)
-        const int a = idx / rq, c = idx % rq;
-        sX[c * ld + a] = split_df(G1[(long long)a * ldg + c]);
-    }
-    __syncthreads();
     for (int t = tid; t < ta * ta; t += nt) {   // R~_p -= f G1 S~^T
         const int a0 = (t / ta) * 5, b0 = (t % ta) * 5;
         float hh[5][5] = {}, ll[5][5] = {};
@@ -143,7 +179,10 @@ __device__ void term_df(int rp, int rq, const double *__restrict__ Sb, long long
         for (int i = 0; i < 5; ++i)
 #pragma unroll
             for (int j = 0; j < 5; ++j)
-                if (a0 + i < rp && b0 + j < rp) Rp[(long long)(a0 + i) * ldr + b0 + j] -= f * df_val(hh[i][j], ll[i][j]);
+                if (a0 + i < rp && b0 + j < rp) {
+                    double *rp_ = Rp + (long long)(a0 + i) * ldr + b0 + j;
+                    *rp_ = fma(-f, df_val(hh[i][j], ll[i][j]), *rp_);
+                }
     }
     __syncthreads();
 }
@@ -156,28 +195,30 @@ __device__ void term_f32(int rp, int rq, const float *__restrict__ Sb, long long
                          float *sm, int ld) {
     float *sS = sm, *sT = sm + (long long)ld * ld, *sG = sm + 2LL * ld * ld;
     const int tid = threadIdx.x, nt = blockDim.x;
+    // asynchronous element copies into the transposed staging layouts (all in flight together)
     if (s_trans) {
         for (int idx = tid; idx < rp * rq; idx += nt) {
             const int c = idx / rp, a = idx % rp;
-            sS[c * ld + a] = Sb[(long long)c * lds + a];
+            cpa_elem(sS + c * ld + a, Sb + (long long)c * lds + a, 4);
         }
     } else {
         for (int idx = tid; idx < rp * rq; idx += nt) {
             const int a = idx / rq, c = idx % rq;
-            sS[c * ld + a] = Sb[(long long)a * lds + c];
+            cpa_elem(sS + c * ld + a, Sb + (long long)a * lds + c, 4);
         }
     }
     if (t_trans) {
         for (int idx = tid; idx < rq * rq; idx += nt) {
             const int b = idx / rq, c = idx % rq;
-            sT[c * ld + b] = Tq[(long long)b * ldt + c];
+            cpa_elem(sT + c * ld + b, Tq + (long long)b * ldt + c, 4);
         }
     } else {
         for (int idx = tid; idx < rq * rq; idx += nt) {
             const int c = idx / rq, b = idx % rq;
-            sT[c * ld + b] = Tq[(long long)c * ldt + b];
+            cpa_elem(sT + c * ld + b, Tq + (long long)c * ldt + b, 4);
         }
     }
+    cpa_wait();
     __syncthreads();
     const int ta = (rp + 4) / 5, tq = (rq + 4) / 5;
     for (int t = tid; t < ta * tq; t += nt) {   // G1 = S~ T~'
@@ -236,12 +277,15 @@ __device__ double residual_eval(const SolveArgs &A, const ClusterInfo &C, const 
         const PairInfo P = A.pairs[S.pair];
         const int r = A.rdim[S.pair], np = P.np;
         const R fii = (R)A.focc[(long long)P.i * A.n_occ + P.i], fjj = (R)A.focc[(long long)P.j * A.n_occ + P.j];
-        const R *e = v.e + P.e_off;
-        const R *rhs = v.rhs + (v.rhs_by_slot ? S.t_off : P.off);
+        const R *__restrict__ e = v.e + P.e_off;
+        const R *__restrict__ rhs = v.rhs + (v.rhs_by_slot ? S.t_off : P.off);
+        const R *__restrict__ Ts = v.T + S.t_off;
+        R *__restrict__ Rs = v.Rr + S.t_off;
+#pragma unroll 4
         for (int idx = tid; idx < r * r; idx += kThreads) {
             const int a = idx / r, b = idx % r;
             const long long o = (long long)a * np + b;
-            v.Rr[S.t_off + o] = rhs[o] + (e[a] + e[b] - fii - fjj) * v.T[S.t_off + o];
+            Rs[o] = rhs[o] + (e[a] + e[b] - fii - fjj) * Ts[o];
         }
     }
     __syncthreads();
@@ -290,11 +334,14 @@ __device__ void jacobi_update(const SolveArgs &A, const ClusterInfo &C, const Vi
         const PairInfo P = A.pairs[S.pair];
         const int r = A.rdim[S.pair], np = P.np;
         const R fii = (R)A.focc[(long long)P.i * A.n_occ + P.i], fjj = (R)A.focc[(long long)P.j * A.n_occ + P.j];
-        const R *e = v.e + P.e_off;
+        const R *__restrict__ e = v.e + P.e_off;
+        R *__restrict__ Ts = v.T + S.t_off;
+        const R *__restrict__ Rs = v.Rr + S.t_off;
+#pragma unroll 4
         for (int idx = threadIdx.x; idx < r * r; idx += kThreads) {
             const int a = idx / r, b = idx % r;
-            const long long o = S.t_off + (long long)a * np + b;
-            v.T[o] -= v.Rr[o] / (e[a] + e[b] - fii - fjj);
+            const long long o = (long long)a * np + b;
+            Ts[o] -= Rs[o] / (e[a] + e[b] - fii - fjj);
         }
     }
     __syncthreads();
@@ -341,6 +388,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
         A.E_cluster[c] = E;
         A.iters[c] = conv ? it : -1;
         if (A.evals64) A.evals64[c] = it + 1;
+        if (A.evals32) A.evals32[c] = 0;
     }
 }
 
@@ -348,7 +396,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
 // per iteration: the FP32 floor); returns the number of updates.  *fresh: the residual buffer belongs to the
 // final x (false when the update cap ended the loop).
 __device__ int solve32(const SolveArgs &A, const ClusterInfo &C, const View<float> &v, double tol32, int max_it,
-                       double *red, bool *fresh = nullptr) {
+                       double *red, bool *fresh = nullptr, int *nevals = nullptr) {
     double prev = INFINITY;
     int it = 0;
     bool ev = false;
@@ -361,6 +409,7 @@ __device__ int solve32(const SolveArgs &A, const ClusterInfo &C, const View<floa
         ev = false;
     }
     if (fresh) *fresh = ev;
+    if (nevals) *nevals += ev ? it + 1 : it;
     return it;
 }
 
@@ -389,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
     const int c = A.order[blockIdx.x];
     const ClusterInfo C = A.clusters[c];
     __shared__ double red[kThreads / 32];
-    extern __shared__ float stage32[];
+    extern __shared__ __align__(16) float stage32[];
     const int ld = A.np_max + 1;
     View<float> v32{A.e32, A.Kt32, false, A.sblk32, A.T32, A.R32, A.G1_32 + (long long)blockIdx.x * A.gstride, stage32, ld,
                     false};
@@ -404,7 +453,8 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
         __syncthreads();
     };
     zero32(A.T32);
-    int total = solve32(A, C, v32, fmax(A.tol, 1e-6), A.max_iter, red);
+    int ev32 = 0;
+    int total = solve32(A, C, v32, fmax(A.tol, 1e-6), A.max_iter, red, nullptr, &ev32);
     // T64 = T32
     for (int s = C.slot0; s < C.slot1; ++s) {
         const Slot S = A.slots[s];
@@ -443,7 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
         }
         __syncthreads();
         bool fresh = false;
-        total += solve32(A, C, vc, fmax(1e-7 * r64, 0.1 * A.tol), A.max_iter, red, &fresh);
+        total += solve32(A, C, vc, fmax(1e-7 * r64, 0.1 * A.tol), A.max_iter, red, &fresh, &ev32);
         for (int s = C.slot0; s < C.slot1; ++s) {
             const Slot S = A.slots[s];
             const long long nn = (long long)A.pairs[S.pair].np * A.pairs[S.pair].np;
@@ -464,6 +514,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
         A.E_cluster[c] = E;
         A.iters[c] = conv ? total + evals - 1 : -1;
         if (A.evals64) A.evals64[c] = evals;
+        if (A.evals32) A.evals32[c] = ev32;
     }
 }
 

@@ -457,17 +457,23 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         for (int j = 0; j < 64; ++j) sC[r * LDC + (warp >> 2) * 64 + j] = make_float2(chi[j], clo[j]);
     }
     __syncthreads();
-    const bool unit_alpha = g.alpha == 1.0;
+    // alpha = +-2^k folds into the exponent (no FP64 multiply); the value itself is assembled with integer
+    // operations (df_to_double)
+    const unsigned long long abits = (unsigned long long)__double_as_longlong(g.alpha);
+    const int aexp = (int)((abits >> 52) & 0x7FF);
+    const bool alpha_p2 = (abits & 0xFFFFFFFFFFFFFULL) == 0 && aexp > 0 && aexp < 0x7FF;
+    const int ashift = alpha_p2 ? aexp - 1023 : 0;
+    const unsigned long long asign = alpha_p2 ? (abits & 0x8000000000000000ULL) : 0ULL;
     for (int r = warp; r < BM; r += NT / 32) {
         const int m = m0 + r;
         if (m >= g.M) break;
-        const int em = g.ea[m] - 14;
+        const int em = g.ea[m] - 14 + ashift;
         for (int c = lane; c < BN; c += 32) {
             const int n = n0 + c;
             if (n >= g.N) break;
             const float2 hl = sC[r * LDC + c];
-            double val = ((double)hl.x + (double)hl.y) * pow2(em + g.eb[n]);
-            if (!unit_alpha) val *= g.alpha;
+            double val = __longlong_as_double(__double_as_longlong(df_to_double(hl.x, hl.y, em + g.eb[n])) ^ (long long)asign);
+            if (!alpha_p2) val *= g.alpha;
             const long long nc = g.n_idx_c ? g.n_idx_c[n] : n;
             double *cp = g.C + (long long)m * g.ldc + nc;
             if (g.atomic) atomicAdd(cp, val);

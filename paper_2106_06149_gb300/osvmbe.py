@@ -22,7 +22,7 @@ EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv
            "mbe3_combine", "energy", "gradient_backward", "osv_cluster_count", "osv_cluster_info",
            "osv_eigenvalues", "osv_syev_batched", "osv_profile_enable", "osv_profile_read",
            "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops",
-           "osv_solve_counts"]
+           "osv_solve_counts", "osv_residual_work"]
 
 
 class OsvParams(ctypes.Structure):
@@ -72,6 +72,7 @@ def load(path=LIB_PATH):
         "osv_syev_batched_noalloc": ([V, I, I, V, V, V], I),
         "osv_adjoint_flops": ([V, P(D)], I),
         "osv_solve_counts": ([V, P(ctypes.c_longlong), P(ctypes.c_longlong), P(I)], I),
+        "osv_residual_work": ([V, P(D), P(D)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -258,6 +259,12 @@ class Context:
         u, f, bad = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
         _check(load().osv_solve_counts(self.h, ctypes.byref(u), ctypes.byref(f), ctypes.byref(bad)), self.h)
         return u.value, f.value, bad.value
+
+    def residual_work(self):
+        """(FLOPs of FP32 residual evaluations, FLOPs of FP64-accurate evaluations) of the last solve."""
+        f32, f64 = ctypes.c_double(), ctypes.c_double()
+        _check(load().osv_residual_work(self.h, ctypes.byref(f32), ctypes.byref(f64)), self.h)
+        return f32.value, f64.value
 
     def eigenvalues(self, k, n_vir):
         out = np.zeros(n_vir, np.float64)
