@@ -187,18 +187,6 @@ __global__ void __launch_bounds__(kThreads) k_cluster_adjoint(AdjArgs A) {
 // diag(e) - f_ii - f_jj); term phase B0 = S~, B1 = Tb_p then T~'_q, B2 = U1 = Tb S~, B3 = U2 = Tb^T S~.
 constexpr int kAT = 512;   // one CTA per SM (its shared memory): 16 warps to hide the double-float latency
 
-struct AdjArgsS {
-    const ClusterInfo *clusters;
-    const int *order;
-    const Slot *slots;
-    const Term *terms;
-    const PairInfo *pairs;
-    const int *rdim;
-    const double *focc, *e, *Tslot, *Stil;
-    int n_occ, ncl, ld;
-    double *GS, *GF, *GSc, *dF;
-};
-
 __global__ void __launch_bounds__(kAT, 1) k_cluster_adjoint_df(AdjArgsS A) {
     extern __shared__ __align__(16) float2 smf[];
     const int ld = A.ld;
@@ -801,11 +789,14 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
         // FP64 in every mode: FP32 products here cost ~7e-7 relative in dE/dB, too much for a 1e-6 bar
         const int ld = 2 * nm + 1;
         const size_t sh = 4 * (size_t)ld * ld * sizeof(float2);
-        if (c.osv_mixed && !c.cl.empty() && sh <= 216 * 1024) {
+        const AdjArgsS as{c.cinfo.d, c.order.d, c.slots.d, c.terms.d, c.pinfo.d, c.rdim, c.focc, c.pe, c.Tslot,
+                          c.Stil, n, (int)c.cl.size(), ld, GS, GF, GSc, dF64};
+        if (c.osv_mixed && !c.cl.empty() && 2 * nm <= kAdjTcMaxOrder) {
+            // mixed modes, pair orders <= 80: exact BF16 slices on the tensor cores
+            CK(launch_cluster_adjoint_tc(as, (int)c.cl.size(), c.derr, s));
+        } else if (c.osv_mixed && !c.cl.empty() && sh <= 216 * 1024) {
             // mixed modes: double-float products on the FP32 pipe
             CK(cudaFuncSetAttribute(k_cluster_adjoint_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-            AdjArgsS as{c.cinfo.d, c.order.d, c.slots.d, c.terms.d, c.pinfo.d, c.rdim, c.focc, c.pe, c.Tslot, c.Stil,
-                        n, (int)c.cl.size(), ld, GS, GF, GSc, dF64};
             count_launch();
             k_cluster_adjoint_df<<<(int)std::min<size_t>(c.cl.size(), 152), kAT, sh, s>>>(as);
         } else if (grid > 0) {

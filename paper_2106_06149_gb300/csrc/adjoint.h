@@ -10,6 +10,27 @@ struct osv_ctx;
 
 namespace osv {
 
+// What the per-cluster partial kernels read and accumulate (device pointers): cluster / slot / term lists, pair
+// dimensions, occupied Fock, pair energies, slot amplitudes, coupling blocks; accumulators dE/dS~ and dE/dF~ per
+// pair (GS, GF), dE/dS~ per coupling block (GSc), dE/df_occ (dF).  ld: shared-memory leading dimension of the
+// double-float kernel.
+struct AdjArgsS {
+    const ClusterInfo *clusters;
+    const int *order;
+    const Slot *slots;
+    const Term *terms;
+    const PairInfo *pairs;
+    const int *rdim;
+    const double *focc, *e, *Tslot, *Stil;
+    int n_occ, ncl, ld;
+    double *GS, *GF, *GSc, *dF;
+};
+
+// The same partials on the tensor cores (exact BF16 slices of every operand, tcgen05 with the sums in tensor
+// memory) for pair orders <= kAdjTcMaxOrder; err receives kDevTimeout if a bounded wait expires.
+constexpr int kAdjTcMaxOrder = 80;
+cudaError_t launch_cluster_adjoint_tc(const AdjArgsS &a, int ncl, int *err, cudaStream_t s);
+
 struct AdjointPlan {
     bool planned = false;
     std::vector<void *> allocs;

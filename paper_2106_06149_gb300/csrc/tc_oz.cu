@@ -30,6 +30,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "tc_common.cuh"
 #include "tc_gemm.h"
 
 namespace osv {
@@ -44,52 +45,12 @@ constexpr int STAGE = 2 * TILE_BYTES;             // A and B
 constexpr int NSTAGE = 3;
 constexpr int SMEM = NSTAGE * STAGE + 1024;
 constexpr int CHUNK_KT = 8;                       // 256 K per exact chunk
+constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
+
+__device__ __forceinline__ uint32_t koff(int r, int k) { return kmajor_off(r, k, BK); }
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return smem_desc(saddr, 16 * BK); }
 constexpr int NACC = 4;
-constexpr long long kWaitBudget = 4LL << 30;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t koff(int r, int k) {
-    return (uint32_t)((r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, K-major, N = 128, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
-}
-
-__device__ __forceinline__ void commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool bwait(uint64_t *bar, uint32_t parity) {
-    const long long t0 = clock64();
-    uint32_t done = 0;
-    while (true) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kWaitBudget) return false;
-    }
-}
 
 __device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
@@ -103,76 +64,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// (hi, lo) += x with Knuth's two-sum (exact error term; FP32 only)
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
-    const float s = hi + x;
-    const float bp = s - hi;
-    const float err = (hi - (s - bp)) + (x - bp);
-    hi = s;
-    lo += err;
-}
-
-// exact 2^e as a double for |e| < 1000
-__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
-
-// x = N 2^(e-31) + rounding, N cut into four signed base-256 digits; slice i returned as s_i 2^(-8 i).
-__device__ __forceinline__ void slice4(double x, int e, float *s) {
-    const long long bits = __double_as_longlong(x);
-    const int ex = (int)((bits >> 52) & 0x7FF);
-    if (ex == 0x7FF) {                                       // Inf / NaN: propagate a NaN through the products
-        s[0] = s[1] = s[2] = s[3] = __int_as_float(0x7FC00000);
-        return;
-    }
-    long long n = 0;
-    if (ex != 0) {                                           // zero and subnormal inputs slice to zero
-        const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;   // value = mant 2^(ex-1075)
-        const int sh = 1075 - ex + e - 31;                   // N = mant / 2^sh, sh >= 21 since |x| <= 2^e
-        if (sh < 63) n = (mant + (1LL << (sh - 1))) >> sh;
-        if (bits < 0) n = -n;
-    }
-    const int s0 = (int)((n + (1LL << 23)) >> 24);
-    int r = (int)(n - ((long long)s0 << 24));
-    const int s1 = (r + (1 << 15)) >> 16;
-    r -= s1 << 16;
-    const int s2 = (r + (1 << 7)) >> 8;
-    const int s3 = r - (s2 << 8);
-    s[0] = (float)s0;
-    s[1] = (float)s1 * 3.90625e-3f;
-    s[2] = (float)s2 * 1.52587890625e-5f;
-    s[3] = (float)s3 * 5.9604644775390625e-8f;
-}
-
-// Largest |x| tracked as the bit pattern of |x| (for finite non-negative doubles the integer order of the bit
-// patterns is the numeric order): integer ALU instead of the slow FP64 pipe.
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
-}
-// e with max |x| = f 2^e, f in [0.5, 1) (the frexp exponent) from the bit pattern; 0 for a zero row, the
-// smallest normal exponent for subnormal maxima (which slice to zero).
-__device__ __forceinline__ int scale_exp_bits(unsigned long long b) {
-    if (b == 0ULL) return 0;
-    const int ex = (int)(b >> 52);
-    return ex == 0 ? -1021 : ex - 1022;
-}
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
-}
 
 __device__ __forceinline__ int find_prob(const long long *__restrict__ pre, int nprob, long long t) {
     int lo = 0, hi = nprob - 1;
@@ -220,11 +111,11 @@ __global__ void __launch_bounds__(256) k_oz_scales(const OzOperand *__restrict__
             const double *row = o.ptr + (long long)(o.rowmap ? o.rowmap[rr] : rr) * o.ld;
             unsigned long long mx = 0ULL;
             for (int k = lane; k < o.K; k += 32) {
-                const unsigned long long b = abs_bits(row[o.kmap ? o.kmap[k] : k]);
+                const unsigned long long b = abs_bits64(row[o.kmap ? o.kmap[k] : k]);
                 mx = b > mx ? b : mx;
             }
-            mx = warp_max_u64(mx);
-            if (lane == 0) o.exps[rr] = scale_exp_bits(mx);
+            mx = warp_max_bits(mx);
+            if (lane == 0) o.exps[rr] = scale_exp_of_bits(mx);
         }
         return;
     }
@@ -233,7 +124,7 @@ __global__ void __launch_bounds__(256) k_oz_scales(const OzOperand *__restrict__
     if (rr < o.R) {
         const double *base = o.ptr + (o.rowmap ? o.rowmap[rr] : rr);
         for (int k = wid; k < o.K; k += 8) {
-            const unsigned long long b = abs_bits(base[(long long)(o.kmap ? o.kmap[k] : k) * o.ld]);
+            const unsigned long long b = abs_bits64(base[(long long)(o.kmap ? o.kmap[k] : k) * o.ld]);
             mx = b > mx ? b : mx;
         }
     }
@@ -241,7 +132,7 @@ __global__ void __launch_bounds__(256) k_oz_scales(const OzOperand *__restrict__
     __syncthreads();
     if (wid == 0 && rr < o.R) {
         for (int w = 1; w < 8; ++w) mx = part[w][lane] > mx ? part[w][lane] : mx;
-        o.exps[rr] = scale_exp_bits(mx);
+        o.exps[rr] = scale_exp_of_bits(mx);
     }
 }
 
@@ -277,7 +168,7 @@ __global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ o
         const int r = c % BM, kg = c / BM;
         float sl[8][NSLICE];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) slice4(xs[kg * 8 + q][r], es[r], sl[q]);
+        for (int q = 0; q < 8; ++q) slice4_exact(xs[kg * 8 + q][r], es[r], sl[q]);
         const uint32_t off = koff(r, kg * 8);
 #pragma unroll
         for (int i = 0; i < NSLICE; ++i) {
@@ -362,7 +253,7 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         const bool first_of_chunk = (kt % CHUNK_KT) == 0;
         const bool last_of_chunk = (kt % CHUNK_KT) == CHUNK_KT - 1 || kt == nkt - 1;
         if (tid == 0 && !s_fail) {
-            if (!bwait(&full[st], (uint32_t)((kt / NSTAGE) & 1))) {
+            if (!tc_wait(&full[st], (uint32_t)((kt / NSTAGE) & 1))) {
                 raise_err(err, kDevTimeout);
                 s_fail = 1;
             } else {
@@ -381,17 +272,17 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
                             const int d = i + j;
                             if (d > 4) continue;
                             const int a = d < 3 ? d : 3;
-                            mma_bf16(taddr + (uint32_t)(a * BN), sdesc(a0 + i * IMG + off), sdesc(b0 + j * IMG + off),
-                                     fresh[a] ? 0u : 1u);
+                            tc_mma_bf16(taddr + (uint32_t)(a * BN), sdesc(a0 + i * IMG + off), sdesc(b0 + j * IMG + off),
+                                        kIdesc, !fresh[a]);
                             fresh[a] = false;
                         }
                 }
-                commit(&empty[st]);
+                tc_commit(&empty[st]);
                 ++issued;
                 // refill the stage that kt - 1 used with kt + 2, once its MMAs are done
                 const int nk = kt + NSTAGE - 1;
                 if (nk < nkt) {
-                    if (kt >= 1 && !bwait(&empty[(kt - 1) % NSTAGE], (uint32_t)(((kt - 1) / NSTAGE) & 1))) {
+                    if (kt >= 1 && !tc_wait(&empty[(kt - 1) % NSTAGE], (uint32_t)(((kt - 1) / NSTAGE) & 1))) {
                         raise_err(err, kDevTimeout);
                         s_fail = 1;
                     } else {
@@ -401,10 +292,10 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
             }
         }
         if (last_of_chunk) {
-            if (tid == 0) commit(&dbar);
+            if (tid == 0) tc_commit(&dbar);
             __syncthreads();
             if (s_fail) { ok = false; break; }
-            if (!bwait(&dbar, (uint32_t)(chunk & 1))) {
+            if (!tc_wait(&dbar, (uint32_t)(chunk & 1))) {
                 raise_err(err, kDevTimeout);
                 s_fail = 1;
             }
@@ -417,13 +308,13 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
 #pragma unroll
                 for (int c = 0; c < 64; c += 32) {
                     float v0[16], v1[16];
-                    ld16(lbase + a * BN + c, v0);
-                    ld16(lbase + a * BN + c + 16, v1);
+                    tc_ld16(lbase + a * BN + c, v0);
+                    tc_ld16(lbase + a * BN + c + 16, v1);
                     asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        two_sum_acc(chi[c + i], clo[c + i], v0[i]);
-                        two_sum_acc(chi[c + 16 + i], clo[c + 16 + i], v1[i]);
+                        two_sum_f32(chi[c + i], clo[c + i], v0[i]);
+                        two_sum_f32(chi[c + 16 + i], clo[c + 16 + i], v1[i]);
                     }
                 }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -436,9 +327,9 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         // shared memory is given up (both bounded)
         for (int s = 0; s < NSTAGE; ++s) {
             const int uses = issued / NSTAGE + (s < issued % NSTAGE ? 1 : 0);
-            if (uses > 0) bwait(&empty[s], (uint32_t)((uses - 1) & 1));
+            if (uses > 0) tc_wait(&empty[s], (uint32_t)((uses - 1) & 1));
         }
-        for (int kt = issued; kt < loaded; ++kt) bwait(&full[kt % NSTAGE], (uint32_t)((kt / NSTAGE) & 1));
+        for (int kt = issued; kt < loaded; ++kt) tc_wait(&full[kt % NSTAGE], (uint32_t)((kt / NSTAGE) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
