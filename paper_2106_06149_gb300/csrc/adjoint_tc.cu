@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
     __shared__ int s_fail;
     __shared__ unsigned long long s_red[kTC / 32];
     __shared__ double s_dred[kTC / 32];
+    __shared__ double s_ep[kR];   // slot phase: e' = e - f_ii - f_jj (zero beyond the pair order)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
@@ -193,6 +194,8 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
             const double *e = A.e + P.e_off;
             const double fii = A.focc[(long long)P.i * A.n_occ + P.i], fjj = A.focc[(long long)P.j * A.n_occ + P.j];
             const double wm = w * S.mult;
+            const float2 wmd = split_df(wm);
+            for (int k = tid; k < kR; k += kTC) s_ep[k] = k < r ? e[k] - fii - fjj : 0.0;   // read after barriers below
             // item (a, k0): T(a, k), T(k, a) for k = k0 .. k0 + 7 (zero outside r x r)
             auto load = [&](int it, int &a, int &k0, double *x, double *xt) {
                 a = it % kR;
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                 load(it, a, k0, x, xt);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const double ep = k0 + j < r ? e[k0 + j] - fii - fjj : 0.0;
+                    const double ep = s_ep[k0 + j];
                     m3 = max(m3, abs_bits64((2.0 * x[j] - xt[j]) * ep));
                     m4 = max(m4, abs_bits64(ep * xt[j]));
                 }
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                 load(it, a, k0, x, xt);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const double ep = k0 + j < r ? e[k0 + j] - fii - fjj : 0.0;
+                    const double ep = s_ep[k0 + j];
                     v3[j] = (2.0 * x[j] - xt[j]) * ep;
                     v4[j] = ep * xt[j];
                 }
@@ -288,8 +291,9 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                         const int b = ch * 8 + i;
                         if (b >= r) break;
                         const long long o = P.off + (long long)row * np + b;
-                        atomicAdd(&A.GS[o], wm * df_to_double(h1[i], l1[i], E1));
-                        atomicAdd(&A.GF[o], wm * df_to_double(h2[i], l2[i], E2));
+                        // w m times the sums in double-float, then integer FP64 assembly (no FP64-pipe work)
+                        atomicAdd(&A.GS[o], df_to_double_mul(h1[i], l1[i], wmd, E1));
+                        atomicAdd(&A.GF[o], df_to_double_mul(h2[i], l2[i], wmd, E2));
                     }
                 }
             }
@@ -402,7 +406,8 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
             double xs = 0.0;
             {
                 const int EM = eU + eTq - 14;
-                const double g = -wm * f;
+                const float2 gd = split_df(-wm * f);
+                float xh = 0.f, xl = 0.f;   // <S~, M2a> in double-float, exponent EM
                 double *G = A.GSc + Tm.sblk;
                 for (int ch = ch0; ch < kR / 8; ch += 4) {
                     float h[8], l[8], h2[8], l2[8];
@@ -413,14 +418,15 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                     for (int i = 0; i < 8; ++i) {
                         const int b = ch * 8 + i;
                         if (b >= rq) break;
-                        xs = fma(sval(row, b), df_to_double(h[i], l[i], EM), xs);
+                        df_fma(xh, xl, split_df(sval(row, b)), make_float2(h[i], l[i]));
                         two_sum_f32(h[i], l[i], h2[i]);   // M2a + M2b (same exponent)
                         l[i] = __fadd_rn(l[i], l2[i]);
-                        const double v = g * df_to_double(h[i], l[i], EM);
+                        const double v = df_to_double_mul(h[i], l[i], gd, EM);
                         if (Tm.s_trans) atomicAdd(&G[(long long)b * np + row], v);   // stored (src pair) x (dst pair)
                         else atomicAdd(&G[(long long)row * nq + b], v);
                     }
                 }
+                xs = df_to_double(xh, xl, EM);
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             xs = block_sum(xs, s_dred);

@@ -153,6 +153,13 @@ __host__ __device__ __forceinline__ double df_to_double(float hi, float lo, int 
 #endif
 }
 
+// (h + l) g 2^E for a double-float g: the product in double-float on the FP32 pipe, then integer assembly
+__device__ __forceinline__ double df_to_double_mul(float h, float l, float2 g, int E) {
+    float ph = 0.f, pl = 0.f;
+    df_fma(ph, pl, make_float2(h, l), g);
+    return df_to_double(ph, pl, E);
+}
+
 // h + l in FP64 on the FP64 pipe (kernels whose FP32 pipe is the bottleneck; df_to_double where FP64 is)
 __device__ __forceinline__ double df_val(float h, float l) { return (double)h + (double)l; }
 
