@@ -260,7 +260,7 @@ def run_gpu(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sample_every=16, repeats=1)
+        out["cpu_baseline"] = cpu_baseline(sample_every=4, repeats=1)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -410,7 +410,7 @@ def oracle_sample(sample_every):
     return flops, dt, len(sample), len(cl), torch.get_num_threads()
 
 
-def cpu_baseline(sample_every=16, repeats=1):
+def cpu_baseline(sample_every=4, repeats=1):
     flops, dt, ns, nc, cores = oracle_sample(sample_every)
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
             "seconds": dt,

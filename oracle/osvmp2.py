@@ -294,7 +294,8 @@ def gradient(problem, params, n_osv=None, clusters=None):
     dB = []
     for i in range(problem.n_occ):
         idx = problem.aux_idx[problem.aux_ptr[i]:problem.aux_ptr[i + 1]].astype(np.int64)
-        dB.append(Bd[i].grad[:, idx].numpy().copy())
+        g = Bd[i].grad   # None when no selected cluster touches LMO i: its derivative is zero
+        dB.append(g[:, idx].numpy().copy() if g is not None else np.zeros((Bd[i].shape[0], len(idx))))
     out["dB"] = dB
     out["dF"] = F.grad.numpy().copy()
     return out

@@ -103,3 +103,19 @@ def test_mixed_osv_eigenpairs_match_fp64(osvmbe, fixed):
     print(f"\nleading eigenvalues rel diff {lead:.2e}; rest {rest:.2e}; counts {out[0][0]}")
     assert lead <= 2e-9
     assert rest <= 1e-5
+
+
+@pytest.mark.parametrize("nosv", [6, 41])
+def test_bf16x4_adjoint_kernels_match_fp64(osvmbe, nosv):
+    """The mixed cluster partials take the tensor-core kernel for pair orders <= 80 (6 OSVs per LMO: orders <= 12)
+    and the double-float kernel above (41 OSVs: orders 82); both must give the FP64 path's gradient to the
+    mixed path's bar."""
+    p = make_problem(5, 60, 200, seed=71)
+    base = dict(n_osv_fixed=nosv, mbe_order=3, r2b=6.0, r3b=5.0, tol=1e-11)
+    f = run(osvmbe, p, Params(**base))
+    x = run(osvmbe, p, Params(**base, precision=2))
+    gb = np.abs(x["dB"] - f["dB"]).max()
+    gf = np.abs(x["dF"] - f["dF"]).max()
+    print(f"\nn_osv {nosv}: dE = {x['E'] - f['E']:.3e}; max|d dB| = {gb:.3e}; max|d dF| = {gf:.3e}")
+    assert abs(x["E"] - f["E"]) <= 1e-6
+    assert gb <= 1e-6 and gf <= 1e-6
