@@ -92,6 +92,22 @@ __device__ __forceinline__ void df_fma(float &sh, float &sl, const float2 a, con
     sl = __fadd_rn(sl, __fadd_rn(err, c));
 }
 
+// Two double-float multiply-adds at once on packed FP32 pairs (the f32x2 instructions of sm_100+: half the issue
+// slots of two df_fma calls, bit-identical results): lane x of every float2 is one accumulation, lane y the
+// other; (sh, sl) += a * (bh, bl) with a = (ah, al) shared by both.  The product error and cross terms are
+// formed negated (fma with -a), so that no separate negation is needed.
+__device__ __forceinline__ void df_fma2(float2 &sh, float2 &sl, float ah, float al, float2 bh, float2 bl) {
+    const float2 nah = make_float2(-ah, -ah), nal = make_float2(-al, -al), m1 = make_float2(-1.f, -1.f);
+    const float2 p = __fmul2_rn(make_float2(ah, ah), bh);
+    const float2 en = __ffma2_rn(nah, bh, p);                          // -(p's rounding error)
+    const float2 cn = __ffma2_rn(nah, bl, __ffma2_rn(nal, bh, en));    // -(error + cross terms)
+    const float2 t = __fadd2_rn(sh, p);
+    const float2 bp = __ffma2_rn(sh, m1, t);                           // t - sh
+    const float2 err = __fadd2_rn(__ffma2_rn(__ffma2_rn(bp, m1, t), m1, sh), __ffma2_rn(bp, m1, p));
+    sh = t;
+    sl = __fadd2_rn(sl, __ffma2_rn(cn, m1, err));                      // sl + (err + c)
+}
+
 // (hi, lo) += x with Knuth's two-sum (exact error term)
 __device__ __forceinline__ void df_add(float &hi, float &lo, float x) {
     const float s = __fadd_rn(hi, x);
