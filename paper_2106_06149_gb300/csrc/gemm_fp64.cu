@@ -212,10 +212,14 @@ __global__ void __launch_bounds__(NT) k_gemm_df(const GemmDesc *__restrict__ des
             for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][tr + 16 * i];
 #pragma unroll
             for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tc + 16 * j];
+            if constexpr (TM == 5 && TN == 5) {
+                df_tile5(ah, al, a, b);
+            } else {
 #pragma unroll
-            for (int i = 0; i < TM; ++i)
+                for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; ++j) df_fma(ah[i][j], al[i][j], a[i], b[j]);
+                    for (int j = 0; j < TN; ++j) df_fma(ah[i][j], al[i][j], a[i], b[j]);
+            }
         }
         if (kt + 1 < nk) stage(buf ^ 1);
         __syncthreads();

@@ -77,22 +77,6 @@ struct View {
     bool df;         // FP64 evaluation in double-float arithmetic (mixed kernel)
 };
 
-// 5 x 5 double-float tile update (h, l)[i][j] += x[i] y[j]: columns (0, 1) and (2, 3) as packed f32x2 pairs
-__device__ __forceinline__ void df_tile5(float (&hh)[5][5], float (&ll)[5][5], const float2 *x, const float2 *y) {
-    const float2 y01h = make_float2(y[0].x, y[1].x), y01l = make_float2(y[0].y, y[1].y);
-    const float2 y23h = make_float2(y[2].x, y[3].x), y23l = make_float2(y[2].y, y[3].y);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        float2 h0 = make_float2(hh[i][0], hh[i][1]), l0 = make_float2(ll[i][0], ll[i][1]);
-        float2 h1 = make_float2(hh[i][2], hh[i][3]), l1 = make_float2(ll[i][2], ll[i][3]);
-        df_fma2(h0, l0, x[i].x, x[i].y, y01h, y01l);
-        df_fma2(h1, l1, x[i].x, x[i].y, y23h, y23l);
-        hh[i][0] = h0.x; hh[i][1] = h0.y; ll[i][0] = l0.x; ll[i][1] = l0.y;
-        hh[i][2] = h1.x; hh[i][3] = h1.y; ll[i][2] = l1.x; ll[i][3] = l1.y;
-        df_fma(hh[i][4], ll[i][4], x[i], y[4]);
-    }
-}
-
 // One coupling term of an FP64-accurate evaluation in double-float arithmetic on the FP32 pipe:
 //   G1 = S~ T~'_q (written to the per-CTA FP64 scratch), then R~_p -= f G1 S~^T.
 // Shared memory: sS[c][a] = S~(a, c) and sX[c][.] = T~'(c, .), later G1(., c), as (hi, lo) pairs.
