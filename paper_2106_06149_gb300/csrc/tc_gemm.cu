@@ -302,8 +302,9 @@ void tc_tiles_free(TcTiles &tt) {
     if (tt.d_tile0) cudaFree(tt.d_tile0);
     if (tt.d_desc) cudaFree(tt.d_desc);
     if (tt.d_exps) cudaFree(tt.d_exps);
-    if (tt.d_jobs0) cudaFree(tt.d_jobs0);
-    if (tt.d_soff) cudaFree(tt.d_soff);
+    if (tt.d_jobs) cudaFree(tt.d_jobs);
+    if (tt.d_otiles) cudaFree(tt.d_otiles);
+    if (tt.d_rows) cudaFree(tt.d_rows);
     if (tt.d_sjobs0) cudaFree(tt.d_sjobs0);
     if (tt.d_ops) cudaFree(tt.d_ops);
     tt = TcTiles{};

@@ -87,11 +87,6 @@ struct OzOperand {
     long long soff;    // byte offset of its slice images in the scratch
 };
 
-__device__ __forceinline__ double oz_elem(const OzOperand &o, int r, int k) {
-    const long long rr = o.rowmap ? o.rowmap[r] : r, kk = o.kmap ? o.kmap[k] : k;
-    return o.kcontig ? o.ptr[rr * o.ld + kk] : o.ptr[kk * o.ld + rr];
-}
-
 // Row scales: exps[r] = e with max_k |X(r,k)| = f 2^e, f in [0.5, 1) (0 for a zero row).  One CTA per block of
 // 32 operand rows.  K-contiguous rows: a warp per row; otherwise the 32 lanes take 32 adjacent rows and the
 // eight warps split K.
@@ -136,34 +131,83 @@ __global__ void __launch_bounds__(256) k_oz_scales(const OzOperand *__restrict__
     }
 }
 
-// One CTA per operand tile (128 rows x 32 K): stage the FP64 values in shared memory (coalesced for either
-// orientation), then write the four slice images (row tile major, then K tile).
-__global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ ops, const long long *__restrict__ jobs0,
-                                                 int nops, unsigned char *__restrict__ scratch) {
+// Output tile of the GEMM kernel: byte offsets of the first k tile of its A and B slice images, the problem and
+// tile origin, its k-tile count, and for a packed tile (rt >= 0) the row table naming each row's problem.
+struct OzTile {
+    long long aoff, boff;
+    int p, m0, n0, nkt, rt;
+};
+// Row r of a packed tile: problem p (-1: empty row), its A operand q and the row m of that problem.
+struct OzRow {
+    int p, q, m;
+};
+// Slicing job: the 128 x 32 tile kt of operand q, row tile rt (packed < 0), or of packed tile `packed`.
+struct OzJob {
+    long long dst;
+    int q, rt, kt, packed;
+};
+
+// One CTA per slicing job: stage the FP64 values in shared memory (coalesced for either orientation of the
+// rows' operand), then write the four slice images.  Rows are addressed through per-row (base, k stride, k map)
+// triples, so a packed tile gathers the rows of several problems.
+__global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ ops, const OzJob *__restrict__ jobs,
+                                                 const OzRow *__restrict__ rows, unsigned char *__restrict__ scratch) {
     __shared__ double xs[BK][BM + 1];
-    __shared__ int es[BM];
-    const long long t = blockIdx.x;
-    const int p = find_prob(jobs0, nops, t);
-    const OzOperand o = ops[p];
-    const int nkt = (o.K + BK - 1) / BK;
-    const long long j = t - jobs0[p];
-    const int rt = (int)(j / nkt), kt = (int)(j % nkt);
-    const int r0 = rt * BM, k0 = kt * BK;
+    __shared__ int es[BM], kn[BM];
+    __shared__ const double *rbase[BM];
+    __shared__ const int *rkmap[BM];
+    __shared__ long long rks[BM];
+    __shared__ int s_along_k;
+    const OzJob J = jobs[blockIdx.x];
+    const int k0 = J.kt * BK;
     const int tid = threadIdx.x;
-    for (int r = tid; r < BM; r += NT) es[r] = r0 + r < o.R ? o.exps[r0 + r] : 0;
-    if (o.kcontig) {
+    for (int r = tid; r < BM; r += NT) {
+        int q = -1, m = 0;
+        if (J.packed < 0) {
+            q = J.q;
+            m = J.rt * BM + r;
+            if (m >= ops[q].R) q = -1;
+        } else {
+            const OzRow x = rows[(long long)J.packed * BM + r];
+            if (x.p >= 0) { q = x.q; m = x.m; }
+        }
+        if (q >= 0) {
+            const OzOperand &o = ops[q];
+            const long long rr = o.rowmap ? o.rowmap[m] : m;
+            rbase[r] = o.kcontig ? o.ptr + rr * o.ld : o.ptr + rr;
+            rks[r] = o.kcontig ? 1 : o.ld;
+            rkmap[r] = o.kmap;
+            kn[r] = o.K;
+            es[r] = o.exps[m];
+        } else {
+            rbase[r] = nullptr;
+            rks[r] = 0;
+            rkmap[r] = nullptr;
+            kn[r] = 0;
+            es[r] = 0;
+        }
+        if (r == 0) s_along_k = q >= 0 ? ops[q].kcontig : 1;
+    }
+    __syncthreads();
+    auto elem = [&](int r, int k) -> double {
+        const int kk = k0 + k;
+        if (kk >= kn[r]) return 0.0;
+        const long long kc = rkmap[r] ? rkmap[r][kk] : kk;
+        return rbase[r][kc * rks[r]];
+    };
+    if (s_along_k) {
         for (int idx = tid; idx < BM * BK; idx += NT) {   // lanes along k
             const int r = idx / BK, k = idx % BK;
-            xs[k][r] = (r0 + r < o.R && k0 + k < o.K) ? oz_elem(o, r0 + r, k0 + k) : 0.0;
+            xs[k][r] = elem(r, k);
         }
     } else {
         for (int idx = tid; idx < BM * BK; idx += NT) {   // lanes along rows
             const int k = idx / BM, r = idx % BM;
-            xs[k][r] = (r0 + r < o.R && k0 + k < o.K) ? oz_elem(o, r0 + r, k0 + k) : 0.0;
+            xs[k][r] = elem(r, k);
         }
     }
     __syncthreads();
-    unsigned char *img = scratch + o.soff + ((long long)rt * nkt + kt) * TILE_BYTES;
+    unsigned char *img = scratch + J.dst;
     for (int c = tid; c < BM * (BK / 8); c += NT) {   // one core-matrix row (8 K of one row) per step
         const int r = c % BM, kg = c / BM;
         float sl[8][NSLICE];
@@ -180,26 +224,20 @@ __global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ o
     }
 }
 
-__global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ descs,
-                                                  const long long *__restrict__ tile0, const long long *__restrict__ soff,
-                                                  int nprob, const unsigned char *__restrict__ scratch, int *err) {
+__global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ descs, const OzTile *__restrict__ tiles,
+                                                  const OzRow *__restrict__ rows,
+                                                  const unsigned char *__restrict__ scratch, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], dbar;
     __shared__ uint32_t s_taddr;
     __shared__ int s_fail;
 
-    const long long t = blockIdx.x;
-    const int p = find_prob(tile0, nprob, t);
-    const GemmDesc g = descs[p];
-    const long long local = t - tile0[p];
-    const int tiles_n = (g.N + BN - 1) / BN;
-    const int mt = int(local / tiles_n), ntile = int(local % tiles_n);
-    const int m0 = mt * BM, n0 = ntile * BN;
-    const int nkt = (g.K + BK - 1) / BK;
+    const OzTile T = tiles[blockIdx.x];
+    const int m0 = T.m0, n0 = T.n0, nkt = T.nkt;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const unsigned char *Aimg = scratch + soff[2 * p] + (long long)mt * nkt * TILE_BYTES;
-    const unsigned char *Bimg = scratch + soff[2 * p + 1] + (long long)ntile * nkt * TILE_BYTES;
+    const unsigned char *Aimg = scratch + T.aoff;
+    const unsigned char *Bimg = scratch + T.boff;
 
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
@@ -348,27 +386,38 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         for (int j = 0; j < 64; ++j) sC[r * LDC + (warp >> 2) * 64 + j] = make_float2(chi[j], clo[j]);
     }
     __syncthreads();
-    // alpha = +-2^k folds into the exponent (no FP64 multiply); the value itself is assembled with integer
-    // operations (df_to_double)
-    const unsigned long long abits = (unsigned long long)__double_as_longlong(g.alpha);
-    const int aexp = (int)((abits >> 52) & 0x7FF);
-    const bool alpha_p2 = (abits & 0xFFFFFFFFFFFFFULL) == 0 && aexp > 0 && aexp < 0x7FF;
-    const int ashift = alpha_p2 ? aexp - 1023 : 0;
-    const unsigned long long asign = alpha_p2 ? (abits & 0x8000000000000000ULL) : 0ULL;
+    // each row's problem: the tile's own, or the packed tile's row table.  alpha = +-2^k folds into the exponent
+    // (no FP64 multiply); the value itself is assembled with integer operations (df_to_double)
     for (int r = warp; r < BM; r += NT / 32) {
-        const int m = m0 + r;
+        int p = T.p, m = m0 + r;
+        if (T.rt >= 0) {
+            const OzRow x = rows[(long long)T.rt * BM + r];
+            if (x.p < 0) continue;
+            p = x.p;
+            m = x.m;
+        }
+        const GemmDesc &g = descs[p];
         if (m >= g.M) break;
+        const double alpha = g.alpha, beta = g.beta;
+        const unsigned long long abits = (unsigned long long)__double_as_longlong(alpha);
+        const int aexp = (int)((abits >> 52) & 0x7FF);
+        const bool alpha_p2 = (abits & 0xFFFFFFFFFFFFFULL) == 0 && aexp > 0 && aexp < 0x7FF;
+        const int ashift = alpha_p2 ? aexp - 1023 : 0;
+        const unsigned long long asign = alpha_p2 ? (abits & 0x8000000000000000ULL) : 0ULL;
         const int em = g.ea[m] - 14 + ashift;
+        const int N = g.N, atomic = g.atomic;
+        const int *__restrict__ eb = g.eb;
+        const int *__restrict__ nmap = g.n_idx_c;
+        double *crow = g.C + (long long)m * g.ldc;
         for (int c = lane; c < BN; c += 32) {
             const int n = n0 + c;
-            if (n >= g.N) break;
+            if (n >= N) break;
             const float2 hl = sC[r * LDC + c];
-            double val = __longlong_as_double(__double_as_longlong(df_to_double(hl.x, hl.y, em + g.eb[n])) ^ (long long)asign);
-            if (!alpha_p2) val *= g.alpha;
-            const long long nc = g.n_idx_c ? g.n_idx_c[n] : n;
-            double *cp = g.C + (long long)m * g.ldc + nc;
-            if (g.atomic) atomicAdd(cp, val);
-            else *cp = val + (g.beta != 0.0 ? g.beta * *cp : 0.0);
+            double val = __longlong_as_double(__double_as_longlong(df_to_double(hl.x, hl.y, em + eb[n])) ^ (long long)asign);
+            if (!alpha_p2) val *= alpha;
+            double *cp = crow + (nmap ? nmap[n] : n);
+            if (atomic) atomicAdd(cp, val);
+            else *cp = val + (beta != 0.0 ? beta * *cp : 0.0);
         }
     }
 }
@@ -391,7 +440,7 @@ cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
     };
     std::map<Key, int> index;
     std::vector<OzOperand> ops;
-    std::vector<int> opA(h.size()), opB(h.size());
+    std::vector<int> opA(h.size(), -1), opB(h.size(), -1);
     auto add = [&](const Key &k) -> int {
         auto it = index.find(k);
         if (it != index.end()) return it->second;
@@ -409,62 +458,134 @@ cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
     };
     for (size_t i = 0; i < h.size(); ++i) {
         const GemmDesc &g = h[i];
-        if (g.M <= 0 || g.N <= 0) {
-            opA[i] = opB[i] = -1;
-            continue;
-        }
+        if (g.M <= 0 || g.N <= 0) continue;
         opA[i] = add(Key{g.A, g.lda, g.transA == 0 ? g.a_rows : nullptr, g.k_idx_a, g.M, g.K, g.transA == 0 ? 1 : 0});
         opB[i] = add(Key{g.B, g.ldb, g.n_idx_b, g.k_idx_b, g.N, g.K, g.transB == 1 ? 1 : 0});
     }
-    // scale arrays, slice regions and job prefixes per operand
+    // row packing: problems of fewer than BM rows that read the same B operand (hence the same K and N) fill
+    // shared BM-row tiles, first fit in decreasing row count, when that saves tiles
+    std::vector<int> packed_in(h.size(), -1);   // packed tile of each problem
+    std::vector<std::vector<OzRow>> ptab;       // row tables
+    std::vector<int> pB;                        // B operand of each packed tile
+    {
+        std::map<int, std::vector<int>> byB;
+        for (size_t i = 0; i < h.size(); ++i)
+            if (opB[i] >= 0 && h[i].M < BM) byB[opB[i]].push_back((int)i);
+        for (auto &kv : byB) {
+            std::vector<int> &v = kv.second;
+            if (v.size() < 2) continue;
+            std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return h[x].M > h[y].M; });
+            std::vector<int> fill;   // rows used per new tile
+            std::vector<int> bin(v.size());
+            for (size_t u = 0; u < v.size(); ++u) {
+                size_t t = 0;
+                while (t < fill.size() && fill[t] + h[v[u]].M > BM) ++t;
+                if (t == fill.size()) fill.push_back(0);
+                bin[u] = (int)t;
+                fill[t] += h[v[u]].M;
+            }
+            if (fill.size() >= v.size()) continue;
+            const int base = (int)ptab.size();
+            for (size_t t = 0; t < fill.size(); ++t) {
+                ptab.emplace_back(BM, OzRow{-1, -1, 0});
+                pB.push_back(kv.first);
+            }
+            std::vector<int> used(fill.size(), 0);
+            for (size_t u = 0; u < v.size(); ++u) {
+                const int p = v[u], t = bin[u];
+                packed_in[p] = base + t;
+                for (int m = 0; m < h[p].M; ++m) ptab[base + t][used[t] + m] = OzRow{p, opA[p], m};
+                used[t] += h[p].M;
+            }
+        }
+    }
+    // operands that are sliced on their own: every B operand and the A operands of unpacked problems
+    std::vector<char> sliced(ops.size(), 0);
+    for (size_t i = 0; i < h.size(); ++i) {
+        if (opB[i] < 0) continue;
+        sliced[opB[i]] = 1;
+        if (packed_in[i] < 0) sliced[opA[i]] = 1;
+    }
+    // scale arrays (all operands), slice images and jobs
     long long nexp = 0, bytes = 0;
-    std::vector<long long> j0(ops.size() + 1, 0), s0(ops.size() + 1, 0), eoff(ops.size());
+    std::vector<long long> s0(ops.size() + 1, 0), eoff(ops.size());
+    std::vector<OzJob> jobs;
     for (size_t q = 0; q < ops.size(); ++q) {
         OzOperand &o = ops[q];
-        const long long nkt = (o.K + BK - 1) / BK, rt = (o.R + BM - 1) / BM;
         eoff[q] = nexp;
         nexp += o.R;
-        o.soff = bytes;
-        bytes += rt * nkt * TILE_BYTES;
-        j0[q + 1] = j0[q] + rt * nkt;
         s0[q + 1] = s0[q] + (o.R + SROWS - 1) / SROWS;
+        o.soff = -1;
+        if (!sliced[q]) continue;
+        const int nkt = (o.K + BK - 1) / BK, rt = (o.R + BM - 1) / BM;
+        o.soff = bytes;
+        for (int r = 0; r < rt; ++r)
+            for (int k = 0; k < nkt; ++k) jobs.push_back(OzJob{bytes + ((long long)r * nkt + k) * TILE_BYTES, (int)q, r, k, -1});
+        bytes += (long long)rt * nkt * TILE_BYTES;
+    }
+    std::vector<long long> poff(ptab.size());
+    for (size_t t = 0; t < ptab.size(); ++t) {
+        const int nkt = (ops[pB[t]].K + BK - 1) / BK;
+        poff[t] = bytes;
+        for (int k = 0; k < nkt; ++k) jobs.push_back(OzJob{bytes + (long long)k * TILE_BYTES, -1, 0, k, (int)t});
+        bytes += (long long)nkt * TILE_BYTES;
     }
     cudaError_t e = cudaMalloc(&tt.d_exps, (size_t)std::max<long long>(nexp, 1) * sizeof(int));
     if (e != cudaSuccess) return e;
     for (size_t q = 0; q < ops.size(); ++q) ops[q].exps = tt.d_exps + eoff[q];
-    std::vector<long long> t0(h.size() + 1, 0), so(2 * h.size(), 0);
+    // output tiles: unpacked problems (M tiles x N tiles), then packed tiles (x N tiles); longest K first
+    std::vector<OzTile> tiles;
     for (size_t i = 0; i < h.size(); ++i) {
+        if (opB[i] < 0) continue;
         GemmDesc &g = h[i];
-        long long tiles = 0;
-        if (opA[i] >= 0) {
-            g.ea = ops[opA[i]].exps;
-            g.eb = ops[opB[i]].exps;
-            so[2 * i] = ops[opA[i]].soff;
-            so[2 * i + 1] = ops[opB[i]].soff;
-            tiles = (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
-        }
-        t0[i + 1] = t0[i] + tiles;
+        g.ea = ops[opA[i]].exps;
+        g.eb = ops[opB[i]].exps;
+        if (packed_in[i] >= 0) continue;
+        const int nkt = (g.K + BK - 1) / BK;
+        for (int mt = 0; mt < (g.M + BM - 1) / BM; ++mt)
+            for (int nt = 0; nt < (g.N + BN - 1) / BN; ++nt)
+                tiles.push_back(OzTile{ops[opA[i]].soff + (long long)mt * nkt * TILE_BYTES,
+                                       ops[opB[i]].soff + (long long)nt * nkt * TILE_BYTES, (int)i, mt * BM, nt * BN, nkt, -1});
     }
-    tt.tiles = t0.back();
-    tt.jobs = j0.back();
+    std::vector<OzRow> rows;
+    for (size_t t = 0; t < ptab.size(); ++t) {
+        const OzOperand &ob = ops[pB[t]];
+        const int nkt = (ob.K + BK - 1) / BK;
+        for (int nt = 0; nt < (ob.R + BN - 1) / BN; ++nt)
+            tiles.push_back(OzTile{poff[t], ob.soff + (long long)nt * nkt * TILE_BYTES, ptab[t][0].p, 0, nt * BN, nkt, (int)t});
+        rows.insert(rows.end(), ptab[t].begin(), ptab[t].end());
+    }
+    std::stable_sort(tiles.begin(), tiles.end(), [](const OzTile &x, const OzTile &y) { return x.nkt > y.nkt; });
+    tt.tiles = (long long)tiles.size();
+    tt.jobs = (long long)jobs.size();
     tt.sjobs = s0.back();
     tt.scratch_bytes = bytes;
     tt.nprob = (int)h.size();
     tt.nops = (int)ops.size();
+    tt.packed_tiles = (long long)ptab.size();
     auto up = [](auto *&dst, const auto &v) -> cudaError_t {
         cudaError_t ee = cudaMalloc(&dst, std::max<size_t>(v.size(), 1) * sizeof(v[0]));
         if (ee != cudaSuccess || v.empty()) return ee;
         return cudaMemcpy(dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice);
     };
     if ((e = up(tt.d_desc, h)) != cudaSuccess) return e;
-    if ((e = up(tt.d_tile0, t0)) != cudaSuccess) return e;
-    if ((e = up(tt.d_soff, so)) != cudaSuccess) return e;
-    if ((e = up(tt.d_jobs0, j0)) != cudaSuccess) return e;
     if ((e = up(tt.d_sjobs0, s0)) != cudaSuccess) return e;
     OzOperand *dops = nullptr;
-    if ((e = up(dops, ops)) != cudaSuccess) return e;
+    OzJob *djobs = nullptr;
+    OzTile *dtiles = nullptr;
+    OzRow *drows = nullptr;
+    e = up(dops, ops);
     tt.d_ops = dops;
-    return cudaSuccess;
+    if (e != cudaSuccess) return e;
+    e = up(djobs, jobs);
+    tt.d_jobs = djobs;
+    if (e != cudaSuccess) return e;
+    e = up(dtiles, tiles);
+    tt.d_otiles = dtiles;
+    if (e != cudaSuccess) return e;
+    e = up(drows, rows);
+    tt.d_rows = drows;
+    return e;
 }
 
 cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err, cudaStream_t s) {
@@ -478,6 +599,7 @@ cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err
     }
     cudaError_t e;
     const OzOperand *ops = static_cast<const OzOperand *>(tt.d_ops);
+    const OzRow *rows = static_cast<const OzRow *>(tt.d_rows);
     if (tt.sjobs > 0) {
         count_launch();
         k_oz_scales<<<(unsigned)tt.sjobs, 256, 0, s>>>(ops, tt.d_sjobs0, tt.nops);
@@ -485,11 +607,11 @@ cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err
     }
     if (tt.jobs > 0) {
         count_launch();
-        k_oz_slice<<<(unsigned)tt.jobs, NT, 0, s>>>(ops, tt.d_jobs0, tt.nops, scratch);
+        k_oz_slice<<<(unsigned)tt.jobs, NT, 0, s>>>(ops, static_cast<const OzJob *>(tt.d_jobs), rows, scratch);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     count_launch();
-    k_oz_gemm<<<(unsigned)tt.tiles, NT, SMEM, s>>>(tt.d_desc, tt.d_tile0, tt.d_soff, tt.nprob, scratch, err);
+    k_oz_gemm<<<(unsigned)tt.tiles, NT, SMEM, s>>>(tt.d_desc, static_cast<const OzTile *>(tt.d_otiles), rows, scratch, err);
     return cudaGetLastError();
 }
 
