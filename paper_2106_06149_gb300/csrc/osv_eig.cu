@@ -20,11 +20,15 @@
 #include <cfloat>
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "jacobi.cuh"
 #include "kernels.cuh"
 #include "osv_eig.h"
 
 namespace osv {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -58,27 +62,42 @@ __device__ __forceinline__ R warp_sum_t(R v) {
 // forms v_k from it; (b) one pass over rows r > k applies the pending update and accumulates p = tau A v_k;
 // (c) p -= (tau/2)(p.v) v; (v_k, p) become the pending update A <- A - v p^T - p v^T.  Below-diagonal column k
 // is not updated (it is never read again).
-template <class R>
+template <class R, int CL>
 __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__ descs) {
-    const TriDescT<R> D = descs[blockIdx.x];
+    static_assert(CL == 1 || CL == 2, "one CTA or a pair of CTAs per matrix");
+    const unsigned rank = CL == 2 ? cg::this_cluster().block_rank() : 0u;
+    const TriDescT<R> D = descs[blockIdx.x / CL];
     const int n = D.n;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *v = reinterpret_cast<R *>(smem_raw), *p = v + n, *vo = p + n, *po = vo + n;   // global indices
-    R *nx = po + n;   // row k + 1 as pass (b) of step k leaves it (read by step k + 1 instead of global memory)
+    const int ns = (n + 3) & ~3;   // vector stride: 16-byte aligned starts
+    R *v = reinterpret_cast<R *>(smem_raw), *p = v + ns, *vo = p + ns, *po = vo + ns;   // global indices
+    R *nx = po + ns;   // row k + 1 as pass (b) of step k leaves it (read by step k + 1 instead of global memory)
     __shared__ R part[kTT / 32];   // in the working precision: FP64 conversions and adds are slow on GB300
-    __shared__ R s_beta, s_kc;
+    __shared__ R s_beta[2], s_kc, s_pv[2];
+    // cluster of two: the peer CTA's copy of a shared-memory location
+    auto remote = [&](R *x) -> R * {
+        if constexpr (CL == 2) return cg::this_cluster().map_shared_rank(x, rank ^ 1u);
+        return x;
+    };
+    auto cluster_sync = [&]() {
+        if constexpr (CL == 2) cg::this_cluster().sync();
+    };
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     constexpr int NW = kTT / 32;
     R *A = D.A;
     const long long lda = D.lda;
+    const bool vec = (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;   // 16-byte aligned rows
     for (int i = tid; i < n; i += kTT) {
         vo[i] = 0;
         po[i] = 0;
     }
     __syncthreads();
+    cluster_sync();   // both CTAs resident before the first remote store
     for (int k = 0; k + 2 < n; ++k) {
-        // (a) row k with the pending update; reflector from its entries right of the diagonal
-        if (wid == 0) {
+        // (a) row k with the pending update; reflector from its entries right of the diagonal (formed by the CTA
+        // that owns row k and copied into the peer's shared memory)
+        if (wid == 0 && (CL == 1 || (unsigned)(k & 1) == rank)) {
+            R *vr_ = remote(v);
             R *row = A + (long long)k * lda;
             const R *src = k == 0 ? row : nx;
             const R vk = vo[k], pk = po[k];
@@ -86,6 +105,7 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
             for (int c = k + 1 + lane; c < n; c += 32) {
                 const R x = src[c] - vk * po[c] - pk * vo[c];
                 v[c] = x;
+                if (CL == 2 && c > k + 1) vr_[c] = x;
                 ss = fma(x, x, ss);
             }
             ss = warp_sum_t(ss);
@@ -103,30 +123,97 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
                     beta = (R)1 / (alpha * (alpha + fabs(x0)));
                 }
                 D.tau[k] = beta;
-                s_beta = beta;
+                s_beta[k & 1] = beta;
+                if constexpr (CL == 2) {
+                    vr_[k + 1] = v[k + 1];
+                    *remote(&s_beta[k & 1]) = beta;
+                }
             }
             __syncwarp();
             for (int c = k + 1 + lane; c < n; c += 32) row[c] = v[c];   // reflector into row k
         }
         __syncthreads();
-        const R beta = s_beta;
+        cluster_sync();
+        const R beta = s_beta[k & 1];
         // (b) pending update of rows r > k (columns > k) fused with p = beta A v; a warp takes four rows at a
         // time so that several independent loads are in flight per lane
+        // (rows r = rank (mod CL): warp w takes the rows rstart + CL (w + NW q), q < 4, per pass)
         R pv = 0;
-        for (int r0 = k + 1 + wid; r0 < n; r0 += 4 * NW) {
+        R *pr_ = remote(p);
+        const int rstart = k + 1 + (int)((rank ^ (unsigned)(k + 1)) & (CL - 1));
+        for (int r0 = rstart + CL * wid; r0 < n; r0 += 4 * CL * NW) {
             R *row[4];
             R vr[4], pr[4], acc[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int r = r0 + q * NW;
+                const int r = r0 + q * CL * NW;
                 const bool ok = r < n;
                 row[q] = A + (long long)(ok ? r : r0) * lda;
                 vr[q] = ok ? vo[r] : (R)0;
                 pr[q] = ok ? po[r] : (R)0;
                 acc[q] = 0;
             }
-            const int nr = min(4, (n - 1 - r0) / NW + 1);
+            const int nr = min(4, (n - 1 - r0) / (CL * NW) + 1);
             const bool stash = r0 == k + 1;   // warp 0's first row is row k + 1
+            auto col = [&](int c) {           // one column of the (up to) four rows
+                const R poc = po[c], voc = vo[c], vc = v[c];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < nr) {
+                        const R x = row[q][c] - vr[q] * poc - pr[q] * voc;
+                        row[q][c] = x;
+                        acc[q] = fma(x, vc, acc[q]);
+                        if (q == 0 && stash) nx[c] = x;
+                    }
+            };
+            bool vdone = false;
+            if constexpr (sizeof(R) == 4) {
+                if (vec) {
+                    // 16-byte column groups [cb, ce), UV groups of four rows per lane in flight; the ragged head
+                    // [k + 1, cb) and tail [max(ce, cb), n) (three columns at most each) column by column
+                    const int cb = min((k + 4) & ~3, n), ce = n & ~3;
+                    if (lane < 3 && k + 1 + lane < cb) col(k + 1 + lane);
+                    if (lane < 3 && max(ce, cb) + lane < n) col(max(ce, cb) + lane);
+                    const int nch = ce > cb ? (ce - cb) >> 2 : 0;
+                    constexpr int UV = 3;
+                    for (int j0 = lane; j0 < nch; j0 += 32 * UV) {
+                        float4 a[UV][4];
+#pragma unroll
+                        for (int u = 0; u < UV; ++u) {
+                            const int j = j0 + 32 * u;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (q < nr && j < nch) a[u][q] = *reinterpret_cast<const float4 *>(row[q] + cb + 4 * j);
+                        }
+#pragma unroll
+                        for (int u = 0; u < UV; ++u) {
+                            const int j = j0 + 32 * u;
+                            if (j >= nch) break;
+                            const int c = cb + 4 * j;
+                            const float4 poc = *reinterpret_cast<const float4 *>(po + c);
+                            const float4 voc = *reinterpret_cast<const float4 *>(vo + c);
+                            const float4 vc = *reinterpret_cast<const float4 *>(v + c);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (q < nr) {
+                                    float4 x = a[u][q];
+                                    x.x = x.x - vr[q] * poc.x - pr[q] * voc.x;
+                                    x.y = x.y - vr[q] * poc.y - pr[q] * voc.y;
+                                    x.z = x.z - vr[q] * poc.z - pr[q] * voc.z;
+                                    x.w = x.w - vr[q] * poc.w - pr[q] * voc.w;
+                                    *reinterpret_cast<float4 *>(row[q] + c) = x;
+                                    acc[q] = fma(x.x, vc.x, acc[q]);
+                                    acc[q] = fma(x.y, vc.y, acc[q]);
+                                    acc[q] = fma(x.z, vc.z, acc[q]);
+                                    acc[q] = fma(x.w, vc.w, acc[q]);
+                                    if (q == 0 && stash) *reinterpret_cast<float4 *>(nx + c) = x;
+                                }
+                        }
+                    }
+                    vdone = true;
+                }
+            }
+            if (!vdone) {
             // U column groups of four rows: every load of a group is issued before its first store
             constexpr int U = sizeof(R) == 4 ? 4 : 2;
             for (int c0 = k + 1 + lane; c0 < n; c0 += 32 * U) {
@@ -153,25 +240,36 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
                     if (stash) nx[c] = a[u][0];
                 }
             }
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (q >= nr) break;
                 const R sum = warp_sum_t(acc[q]) * beta;
                 if (lane == 0) {
-                    p[r0 + q * NW] = sum;
-                    pv = fma(sum, v[r0 + q * NW], pv);
+                    p[r0 + q * CL * NW] = sum;
+                    if (CL == 2) pr_[r0 + q * CL * NW] = sum;
+                    pv = fma(sum, v[r0 + q * CL * NW], pv);
                 }
             }
         }
         if (lane == 0) part[wid] = pv;
         __syncthreads();
-        // (c) p -= (beta/2)(p.v) v (the partial sums reduced by warp 0); swap the pending-update buffers
+        // (c) p -= (beta/2)(p.v) v (the partial sums reduced by warp 0, then over the pair in rank order); swap
+        // the pending-update buffers
         if (wid == 0) {
             const R t = warp_sum_t(lane < NW ? part[lane] : (R)0);
-            if (lane == 0) s_kc = (R)0.5 * beta * t;
+            if (lane == 0) {
+                if constexpr (CL == 2) {
+                    s_pv[rank] = t;
+                    *remote(&s_pv[rank]) = t;
+                } else {
+                    s_kc = (R)0.5 * beta * t;
+                }
+            }
         }
         __syncthreads();
-        const R kc = s_kc;
+        cluster_sync();
+        const R kc = CL == 2 ? (R)0.5 * beta * (s_pv[0] + s_pv[1]) : s_kc;
         for (int r = k + 1 + tid; r < n; r += kTT) p[r] -= kc * v[r];
         __syncthreads();
         R *t = vo;
@@ -181,7 +279,8 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
         po = p;
         p = t;
     }
-    if (tid == 0) {
+    cluster_sync();   // no remote access after this point; the peer's last row updates are visible
+    if (tid == 0 && rank == 0) {
         if (n >= 2) {
             const int a = n - 2, b = n - 1;
             D.d[a] = A[(long long)a * lda + a] - 2 * vo[a] * po[a];
@@ -899,12 +998,31 @@ size_t jacobi_smem_bytes(int n) {
 template <class R>
 cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
-    const size_t sh = 5 * (size_t)n * sizeof(R);
+    const size_t sh = 5 * (size_t)((n + 3) & ~3) * sizeof(R);
     cudaError_t e;
-    if ((e = smem_attr(k_tridiag<R>, sh)) != cudaSuccess) return e;
-    count_launch();
-    k_tridiag<R><<<batch, kTT, sh, s>>>(d);
-    return cudaGetLastError();
+    if constexpr (sizeof(R) == 4) {
+        // FP32: a pair of CTAs (thread-block cluster) per matrix, each owning every other row
+        if ((e = smem_attr(k_tridiag<R, 2>, sh)) != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2 * (unsigned)batch);
+        cfg.blockDim = dim3(kTT);
+        cfg.dynamicSmemBytes = sh;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        count_launch();
+        return cudaLaunchKernelEx(&cfg, k_tridiag<R, 2>, d);
+    } else {
+        if ((e = smem_attr(k_tridiag<R, 1>, sh)) != cudaSuccess) return e;
+        count_launch();
+        k_tridiag<R, 1><<<batch, kTT, sh, s>>>(d);
+        return cudaGetLastError();
+    }
 }
 
 template <class R>
