@@ -85,6 +85,15 @@ __device__ __forceinline__ void two_sum_f32(float &hi, float &lo, float x) {
     lo = __fadd_rn(lo, err);
 }
 
+// d 2^(-8 i) for an integer |d| < 2^22 with one integer add and one FP32 subtraction, both exact: the bit pattern
+// of 1.5 2^(23 - 8 i) plus d is the float 1.5 2^(23 - 8 i) + d 2^(-8 i) (its unit in the last place is 2^(-8 i)).
+// Keeps the integer-to-float conversion off the reduced-rate conversion path.
+template <int I>
+__device__ __forceinline__ float digit_to_float(int d) {
+    constexpr int kBits = 0x4B400000 - ((8 * I) << 23);   // 1.5 2^(23 - 8 I)
+    return __fsub_rn(__int_as_float(kBits + d), __int_as_float(kBits));
+}
+
 // x = N 2^(e-31) + rounding (|x| <= 2^e), N cut into four signed base-256 digits; slice i returned as s_i 2^(-8 i)
 // (exact BF16 values).  Inf / NaN propagate as NaN; zero and subnormal inputs slice to zero.
 __device__ __forceinline__ void slice4_exact(double x, int e, float *s) {
@@ -107,10 +116,10 @@ __device__ __forceinline__ void slice4_exact(double x, int e, float *s) {
     r -= s1 << 16;
     const int s2 = (r + (1 << 7)) >> 8;
     const int s3 = r - (s2 << 8);
-    s[0] = (float)s0;
-    s[1] = (float)s1 * 3.90625e-3f;
-    s[2] = (float)s2 * 1.52587890625e-5f;
-    s[3] = (float)s3 * 5.9604644775390625e-8f;
+    s[0] = digit_to_float<0>(s0);
+    s[1] = digit_to_float<1>(s1);
+    s[2] = digit_to_float<2>(s2);
+    s[3] = digit_to_float<3>(s3);
 }
 
 // |x| as its bit pattern (integer order = numeric order for finite values): maxima on the integer ALU
