@@ -12,7 +12,9 @@
 //   acc3: i + j = 3, 4   (7 products) rounded in FP32 (the tensor core may truncate): an error of a few 2^-24 of
 //                        a term that is itself <= 2^-24 of the result, so below 2^-40 relative even if biased.
 // Products with i + j >= 5 (weight <= 2^-40) are not formed.  After each chunk the accumulators are drained
-// into FP64 registers (exactly for acc0..acc2); the epilogue restores 2^(e_m + e_n - 14).
+// into double-float register pairs (hi, lo): acc0..acc2 by an error-free two-sum, acc3 (at most 2^-20 of the
+// scale) added to the low word, a rounding below 2^-43 of the scale per chunk.  The epilogue restores
+// 2^(e_m + e_n - 14).
 //
 // Two kernels per batch: (1) the row scales, then every operand tile (128 rows x 32 K) is sliced once into four
 // 8 KB images already in the canonical no-swizzle K-major shared-memory layout (8 rows x 16 bytes per core
@@ -258,9 +260,8 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
     const uint32_t taddr = s_taddr;
 
     // drain targets: TMEM lanes of warp % 4 (rows), columns 64 * (warp / 4) .. + 63.  The chunk sums are added
-    // into FP32 double-float pairs (hi, lo) with an error-free two-sum: FP32 ALU only (an FP64 add runs at 1/64 of
-    // the FP32 rate on this part and made the drain the bottleneck); ~48 significant bits, ample for the
-    // ~31-bit products.
+    // into FP32 double-float pairs (hi, lo) on the FP32 ALU only (an FP64 add runs at 1/64 of the FP32 rate on
+    // this part and made the drain the bottleneck); well beyond the ~31 significant bits of the products.
     float chi[64], clo[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) {
@@ -296,7 +297,9 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
                 s_fail = 1;
             } else {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t a0 = smem_u32(smem + st * STAGE), b0 = a0 + TILE_BYTES;
+                // descriptors of the stage's images: the start-address field (address / 16, 14 bits) of the base
+                // descriptor plus the image offset / 16 (no carry: shared addresses are below 256 KB)
+                const uint64_t da = sdesc(smem_u32(smem + st * STAGE)), db = da + (uint64_t)(TILE_BYTES >> 4);
 #pragma unroll
                 for (int ks = 0; ks < BK / 16; ++ks) {
                     const uint32_t off = ks * 256;
@@ -310,8 +313,8 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
                             const int d = i + j;
                             if (d > 4) continue;
                             const int a = d < 3 ? d : 3;
-                            tc_mma_bf16(taddr + (uint32_t)(a * BN), sdesc(a0 + i * IMG + off), sdesc(b0 + j * IMG + off),
-                                        kIdesc, !fresh[a]);
+                            tc_mma_bf16(taddr + (uint32_t)(a * BN), da + (uint64_t)((i * IMG + off) >> 4),
+                                        db + (uint64_t)((j * IMG + off) >> 4), kIdesc, !fresh[a]);
                             fresh[a] = false;
                         }
                 }
@@ -349,10 +352,18 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
                     tc_ld16(lbase + a * BN + c, v0);
                     tc_ld16(lbase + a * BN + c + 16, v1);
                     asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (a < 3) {   // acc0..acc2: error-free two-sum into (hi, lo)
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        two_sum_f32(chi[c + i], clo[c + i], v0[i]);
-                        two_sum_f32(chi[c + 16 + i], clo[c + 16 + i], v1[i]);
+                        for (int i = 0; i < 16; ++i) {
+                            two_sum_f32(chi[c + i], clo[c + i], v0[i]);
+                            two_sum_f32(chi[c + 16 + i], clo[c + 16 + i], v1[i]);
+                        }
+                    } else {       // acc3 (below 2^-20 of the scale): into the low word
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            clo[c + i] = __fadd_rn(clo[c + i], v0[i]);
+                            clo[c + 16 + i] = __fadd_rn(clo[c + 16 + i], v1[i]);
+                        }
                     }
                 }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -376,50 +387,131 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr));
     }
     if (!ok) return;
-    // epilogue through shared memory (the stage buffers are idle): the (hi, lo) pairs of the row-major 128 x 128
-    // tile, then coalesced stores; the only FP64 operations are one add and one or two multiplies per element
+    // Epilogue.  The per-row destinations (the tile's own problem, or a packed tile's row table) and the per-column
+    // scale exponents are fetched first, one load per thread, so that the element loop reads shared memory only
+    // (a chain of dependent global loads per row made this phase longer than the main loop).  The (hi, lo) sums
+    // then pass through shared memory (the stage buffers are idle) for row-wise coalesced stores.  alpha = +-2^k
+    // folds into the exponent; the FP64 value is assembled with integer operations (df_to_double).
+    __shared__ double *s_crow[BM];
+    __shared__ const int *s_nmap[BM];
+    __shared__ double s_alpha[BM], s_beta[BM];
+    __shared__ int s_em[BM], s_rf[BM], s_eb[BN];
+    if (tid < BM) {
+        const int r = tid;
+        int p = T.p, m = m0 + r;
+        bool valid;
+        if (T.rt >= 0) {
+            const OzRow x = rows[(long long)T.rt * BM + r];
+            valid = x.p >= 0;
+            p = x.p;
+            m = x.m;
+        } else {
+            valid = m < descs[p].M;
+        }
+        s_crow[r] = nullptr;
+        s_em[r] = 0;
+        s_rf[r] = 0;
+        s_alpha[r] = 1.0;
+        s_beta[r] = 0.0;
+        s_nmap[r] = nullptr;
+        if (valid) {
+            const GemmDesc &g = descs[p];
+            const double alpha = g.alpha;
+            const unsigned long long abits = (unsigned long long)__double_as_longlong(alpha);
+            const int aexp = (int)((abits >> 52) & 0x7FF);
+            const bool alpha_p2 = (abits & 0xFFFFFFFFFFFFFULL) == 0 && aexp > 0 && aexp < 0x7FF;
+            s_em[r] = g.ea[m] - 14 + (alpha_p2 ? aexp - 1023 : 0);
+            s_rf[r] = (g.atomic ? 1 : 0) | (alpha_p2 ? 2 : 0) | ((alpha_p2 && (abits >> 63)) ? 4 : 0);
+            s_alpha[r] = alpha;
+            s_beta[r] = g.beta;
+            s_nmap[r] = g.n_idx_c;
+            s_crow[r] = g.C + (long long)m * g.ldc;
+        }
+    } else if (tid < BM + BN) {
+        const int c = tid - BM, n = n0 + c;
+        const GemmDesc &g0 = descs[T.p];   // every row of the tile reads the same B operand
+        s_eb[c] = n < g0.N ? g0.eb[n] : 0;
+    }
+    // row stride of 130 elements: every row starts on a 16-byte boundary (bulk copies below)
     float2 *sC = reinterpret_cast<float2 *>(smem);
-    constexpr int LDC = BN + 1;
+    double *sD = reinterpret_cast<double *>(smem);   // the same storage after the in-place conversion
+    constexpr int LDC = BN + 2;
     {
         const int r = (warp & 3) * 32 + lane;
 #pragma unroll
         for (int j = 0; j < 64; ++j) sC[r * LDC + (warp >> 2) * 64 + j] = make_float2(chi[j], clo[j]);
     }
     __syncthreads();
-    // each row's problem: the tile's own, or the packed tile's row table.  alpha = +-2^k folds into the exponent
-    // (no FP64 multiply); the value itself is assembled with integer operations (df_to_double)
+    const int N = descs[T.p].N;
+    const int nvalid = max(0, min(BN, N - n0));
+    // (hi, lo) -> alpha times the FP64 value, in place (each element read and written by the same thread)
     for (int r = warp; r < BM; r += NT / 32) {
-        int p = T.p, m = m0 + r;
-        if (T.rt >= 0) {
-            const OzRow x = rows[(long long)T.rt * BM + r];
-            if (x.p < 0) continue;
-            p = x.p;
-            m = x.m;
-        }
-        const GemmDesc &g = descs[p];
-        if (m >= g.M) break;
-        const double alpha = g.alpha, beta = g.beta;
-        const unsigned long long abits = (unsigned long long)__double_as_longlong(alpha);
-        const int aexp = (int)((abits >> 52) & 0x7FF);
-        const bool alpha_p2 = (abits & 0xFFFFFFFFFFFFFULL) == 0 && aexp > 0 && aexp < 0x7FF;
-        const int ashift = alpha_p2 ? aexp - 1023 : 0;
-        const unsigned long long asign = alpha_p2 ? (abits & 0x8000000000000000ULL) : 0ULL;
-        const int em = g.ea[m] - 14 + ashift;
-        const int N = g.N, atomic = g.atomic;
-        const int *__restrict__ eb = g.eb;
-        const int *__restrict__ nmap = g.n_idx_c;
-        double *crow = g.C + (long long)m * g.ldc;
-        for (int c = lane; c < BN; c += 32) {
-            const int n = n0 + c;
-            if (n >= N) break;
-            const float2 hl = sC[r * LDC + c];
-            double val = __longlong_as_double(__double_as_longlong(df_to_double(hl.x, hl.y, em + eb[n])) ^ (long long)asign);
-            if (!alpha_p2) val *= alpha;
-            double *cp = crow + (nmap ? nmap[n] : n);
-            if (atomic) atomicAdd(cp, val);
-            else *cp = val + (beta != 0.0 ? beta * *cp : 0.0);
+        if (!s_crow[r]) continue;
+        const int em = s_em[r], rf = s_rf[r];
+        const double alpha = s_alpha[r];
+        const long long asign = (rf & 4) ? (long long)0x8000000000000000ULL : 0LL;
+#pragma unroll
+        for (int u = 0; u < BN / 32; ++u) {
+            const int c = lane + 32 * u;
+            if (c < nvalid) {
+                const float2 hl = sC[r * LDC + c];
+                const double v = __longlong_as_double(__double_as_longlong(df_to_double(hl.x, hl.y, em + s_eb[c])) ^ asign);
+                sD[r * LDC + c] = (rf & 2) ? v : v * alpha;
+            }
         }
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy writes -> bulk-copy reads
+    __syncthreads();
+    // rows with a contiguous, 16-byte aligned destination leave by one bulk copy each: a store (C = alpha AB) or
+    // an element-wise atomic add (accumulating rows, and beta = 1); the others take the element path below
+    __shared__ int s_slow[BM];
+    bool issued_bulk = false;
+    if (tid < BM) {
+        const int r = tid;
+        double *crow = s_crow[r];
+        int slow = 0;
+        if (crow && nvalid > 0) {
+            const int rf = s_rf[r];
+            const double beta = s_beta[r];
+            double *dst = crow + n0;
+            const uint32_t bytes = (uint32_t)nvalid * 8u;
+            const bool fits = !s_nmap[r] && (bytes & 15u) == 0 && ((uintptr_t)dst & 15u) == 0;
+            const bool store = !(rf & 1) && beta == 0.0, add = (rf & 1) || beta == 1.0;
+            if (fits && (store || add)) {
+                const uint32_t src = smem_u32(sD + r * LDC);
+                if (store)
+                    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),
+                                 "r"(bytes)
+                                 : "memory");
+                else
+                    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(dst),
+                                 "r"(src), "r"(bytes)
+                                 : "memory");
+                issued_bulk = true;
+            } else {
+                slow = 1;
+            }
+        }
+        s_slow[r] = slow;
+        if (issued_bulk) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+    __syncthreads();
+    for (int r = warp; r < BM; r += NT / 32) {
+        if (!s_slow[r]) continue;
+        double *crow = s_crow[r];
+        const int rf = s_rf[r];
+        const double beta = s_beta[r];
+        const int *__restrict__ nmap = s_nmap[r];
+        for (int c = lane; c < nvalid; c += 32) {
+            const int n = n0 + c;
+            const double v = sD[r * LDC + c];
+            double *cp = crow + (nmap ? nmap[n] : n);
+            if (rf & 1) atomicAdd(cp, v);
+            else *cp = v + (beta != 0.0 ? beta * *cp : 0.0);
+        }
+    }
+    // the bulk copies read shared memory until they complete: wait before the CTA exits
+    if (issued_bulk) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
 
 }  // namespace
