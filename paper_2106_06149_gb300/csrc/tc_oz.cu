@@ -16,12 +16,13 @@
 // scale) added to the low word, a rounding below 2^-43 of the scale per chunk.  The epilogue restores
 // 2^(e_m + e_n - 14).
 //
-// Two kernels per batch: (1) the row scales, then every operand tile (128 rows x 32 K) is sliced once into four
-// 8 KB images already in the canonical no-swizzle K-major shared-memory layout (8 rows x 16 bytes per core
-// matrix; K-adjacent core matrices 128 B apart, 8-row groups 512 B apart); (2) the GEMM: one CTA (256 threads)
-// per 128 x 128 output tile, a three-stage pipeline of 64 KB stages filled by bulk asynchronous copies
-// (cp.async.bulk + mbarrier transaction counts), thread 0 issuing 2 x 13 tcgen05.mma.kind::f16 (M = 128,
-// N = 128, K = 16) per stage into four TMEM accumulators (512 columns).  Every wait is bounded: on expiry the
+// Two kernels per batch: (1) the row scales, then every operand tile (128 rows x 16 K) is sliced once into four
+// 4 KB images already in the canonical no-swizzle K-major shared-memory layout (8 rows x 16 bytes per core
+// matrix; K-adjacent core matrices 128 B apart, 8-row groups 256 B apart), two tiles per slicing job; (2) the
+// GEMM: one CTA (256 threads) per 128 x 128 output tile, a six-stage pipeline of 32 KB stages filled by bulk
+// asynchronous copies (cp.async.bulk + mbarrier transaction counts; five stages of copies in flight hide the
+// load latency), thread 0 issuing 13 tcgen05.mma.kind::f16 (M = 128, N = 128, K = 16) per stage into four TMEM
+// accumulators (512 columns).  Every wait is bounded: on expiry the
 // error word is set, in-flight MMAs are waited for (bounded), TMEM is freed and the CTA returns.
 #include <cuda_bf16.h>
 
@@ -39,14 +40,18 @@ namespace osv {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32, NT = 256;
+constexpr int BM = 128, BN = 128, BK = 16, NT = 256;
+constexpr int SK = 32;                            // K extent of one slicing job: SK / BK image tiles
 constexpr int NSLICE = 4;
-constexpr int IMG = BM * BK * 2;                  // 8 KB: one slice of one 128 x 32 tile
-constexpr int TILE_BYTES = NSLICE * IMG;          // 32 KB: the four slices of one operand tile
+constexpr int IMG = BM * BK * 2;                  // 4 KB: one slice of one 128 x 16 tile
+constexpr int TILE_BYTES = NSLICE * IMG;          // 16 KB: the four slices of one operand tile
 constexpr int STAGE = 2 * TILE_BYTES;             // A and B
-constexpr int NSTAGE = 3;
+constexpr int NSTAGE = 6;                         // five stages of copies in flight ahead of the MMAs
 constexpr int SMEM = NSTAGE * STAGE + 1024;
-constexpr int CHUNK_KT = 8;                       // 256 K per exact chunk
+constexpr int CHUNK_KT = 256 / BK;                // 256 K per exact chunk
+constexpr int KT_PER_JOB = SK / BK;
+// image tiles per operand row tile: whole slicing jobs (the padding tile, if any, holds zeros)
+__host__ __device__ constexpr int padded_nkt(int K) { return ((K + SK - 1) / SK) * KT_PER_JOB; }
 constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
 
 __device__ __forceinline__ uint32_t koff(int r, int k) { return kmajor_off(r, k, BK); }
@@ -143,7 +148,8 @@ struct OzTile {
 struct OzRow {
     int p, q, m;
 };
-// Slicing job: the 128 x 32 tile kt of operand q, row tile rt (packed < 0), or of packed tile `packed`.
+// Slicing job: the 128 x 32 block kt (two 16-K image tiles) of operand q, row tile rt (packed < 0), or of packed
+// tile `packed`.
 struct OzJob {
     long long dst;
     int q, rt, kt, packed;
@@ -154,14 +160,14 @@ struct OzJob {
 // triples, so a packed tile gathers the rows of several problems.
 __global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ ops, const OzJob *__restrict__ jobs,
                                                  const OzRow *__restrict__ rows, unsigned char *__restrict__ scratch) {
-    __shared__ double xs[BK][BM + 1];
+    __shared__ double xs[SK][BM + 1];
     __shared__ int es[BM], kn[BM];
     __shared__ const double *rbase[BM];
     __shared__ const int *rkmap[BM];
     __shared__ long long rks[BM];
     __shared__ int s_along_k;
     const OzJob J = jobs[blockIdx.x];
-    const int k0 = J.kt * BK;
+    const int k0 = J.kt * SK;
     const int tid = threadIdx.x;
     for (int r = tid; r < BM; r += NT) {
         int q = -1, m = 0;
@@ -198,24 +204,25 @@ __global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ o
         return rbase[r][kc * rks[r]];
     };
     if (s_along_k) {
-        for (int idx = tid; idx < BM * BK; idx += NT) {   // lanes along k
-            const int r = idx / BK, k = idx % BK;
+        for (int idx = tid; idx < BM * SK; idx += NT) {   // lanes along k
+            const int r = idx / SK, k = idx % SK;
             xs[k][r] = elem(r, k);
         }
     } else {
-        for (int idx = tid; idx < BM * BK; idx += NT) {   // lanes along rows
+        for (int idx = tid; idx < BM * SK; idx += NT) {   // lanes along rows
             const int k = idx / BM, r = idx % BM;
             xs[k][r] = elem(r, k);
         }
     }
     __syncthreads();
     unsigned char *img = scratch + J.dst;
-    for (int c = tid; c < BM * (BK / 8); c += NT) {   // one core-matrix row (8 K of one row) per step
+    for (int c = tid; c < BM * (SK / 8); c += NT) {   // one core-matrix row (8 K of one row) per step
         const int r = c % BM, kg = c / BM;
+        const int sub = kg / (BK / 8), kgl = kg % (BK / 8);   // image tile of the job, 8-K group inside it
         float sl[8][NSLICE];
 #pragma unroll
         for (int q = 0; q < 8; ++q) slice4_exact(xs[kg * 8 + q][r], es[r], sl[q]);
-        const uint32_t off = koff(r, kg * 8);
+        const uint32_t off = (uint32_t)sub * TILE_BYTES + koff(r, kgl * 8);
 #pragma unroll
         for (int i = 0; i < NSLICE; ++i) {
             __nv_bfloat162 h[4];
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], dbar;
     __shared__ uint32_t s_taddr;
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_issued, s_loaded;
 
     const OzTile T = tiles[blockIdx.x];
     const int m0 = T.m0, n0 = T.n0, nkt = T.nkt;
@@ -249,6 +256,8 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&dbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
+        s_issued = 0;
+        s_loaded = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_taddr)));
@@ -269,8 +278,14 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         clo[j] = 0.f;
     }
 
-    int loaded = 0;   // k-tiles whose copies were issued (thread 0's view)
-    auto load_stage = [&](int kt) {   // thread 0 only
+    // Roles: thread 32 (warp 1) copies k tile j into stage j % NSTAGE as soon as the MMAs of tile j - NSTAGE are
+    // done; thread 0 waits for each tile's data and issues its MMAs, and never waits for MMA completion inside a
+    // chunk.  All threads drain the accumulators after each 256-K chunk; the copies of the next chunk's first
+    // stages are in flight meanwhile.
+    volatile int *fail = &s_fail;
+    int loaded = 0;   // k tiles whose copies were issued (thread 32)
+    int issued = 0;   // MMA groups committed (thread 0)
+    auto load_stage = [&](int kt) {
         const int st = kt % NSTAGE;
         ++loaded;
         unsigned char *sA = smem + st * STAGE;
@@ -281,31 +296,41 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
             bulk_g2s(sA + TILE_BYTES + i * IMG, Bimg + (long long)kt * TILE_BYTES + i * IMG, IMG, &full[st]);
         }
     };
-
-    int issued = 0;   // MMA groups committed (thread 0's view)
     bool ok = true;
-    if (tid == 0)
-        for (int kt = 0; kt < nkt && kt < NSTAGE - 1; ++kt) load_stage(kt);
-    int chunk = 0;
-    for (int kt = 0; kt < nkt; ++kt) {
-        const int st = kt % NSTAGE;
-        const bool first_of_chunk = (kt % CHUNK_KT) == 0;
-        const bool last_of_chunk = (kt % CHUNK_KT) == CHUNK_KT - 1 || kt == nkt - 1;
-        if (tid == 0 && !s_fail) {
-            if (!tc_wait(&full[st], (uint32_t)((kt / NSTAGE) & 1))) {
-                raise_err(err, kDevTimeout);
-                s_fail = 1;
-            } else {
+    const int nchunk = (nkt + CHUNK_KT - 1) / CHUNK_KT;
+    for (int chunk = 0; chunk < nchunk; ++chunk) {
+        const int kt0 = chunk * CHUNK_KT, kt1 = min(nkt, kt0 + CHUNK_KT);
+        if (tid == 32) {
+            const int jend = min(nkt, kt1 + NSTAGE - 1);
+            while (loaded < jend && !*fail) {
+                const int j = loaded;
+                if (j >= NSTAGE && !tc_wait(&empty[j % NSTAGE], (uint32_t)((j / NSTAGE - 1) & 1))) {
+                    raise_err(err, kDevTimeout);
+                    *fail = 1;
+                    break;
+                }
+                load_stage(j);
+            }
+            s_loaded = loaded;
+        } else if (tid == 0) {
+            for (int kt = kt0; kt < kt1 && !*fail; ++kt) {
+                const int st = kt % NSTAGE;
+                if (!tc_wait(&full[st], (uint32_t)((kt / NSTAGE) & 1))) {
+                    raise_err(err, kDevTimeout);
+                    *fail = 1;
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 // descriptors of the stage's images: the start-address field (address / 16, 14 bits) of the base
                 // descriptor plus the image offset / 16 (no carry: shared addresses are below 256 KB)
                 const uint64_t da = sdesc(smem_u32(smem + st * STAGE)), db = da + (uint64_t)(TILE_BYTES >> 4);
+                const bool first = kt == kt0;
 #pragma unroll
                 for (int ks = 0; ks < BK / 16; ++ks) {
                     const uint32_t off = ks * 256;
                     bool fresh[NACC];
 #pragma unroll
-                    for (int a = 0; a < NACC; ++a) fresh[a] = first_of_chunk && ks == 0;
+                    for (int a = 0; a < NACC; ++a) fresh[a] = first && ks == 0;
 #pragma unroll
                     for (int i = 0; i < NSLICE; ++i)
 #pragma unroll
@@ -320,65 +345,54 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
                 }
                 tc_commit(&empty[st]);
                 ++issued;
-                // refill the stage that kt - 1 used with kt + 2, once its MMAs are done
-                const int nk = kt + NSTAGE - 1;
-                if (nk < nkt) {
-                    if (kt >= 1 && !tc_wait(&empty[(kt - 1) % NSTAGE], (uint32_t)(((kt - 1) / NSTAGE) & 1))) {
-                        raise_err(err, kDevTimeout);
-                        s_fail = 1;
-                    } else {
-                        load_stage(nk);
+            }
+            s_issued = issued;
+            if (!*fail) tc_commit(&dbar);
+        }
+        __syncthreads();
+        if (*fail) { ok = false; break; }
+        if (!tc_wait(&dbar, (uint32_t)(chunk & 1))) {
+            raise_err(err, kDevTimeout);
+            *fail = 1;
+        }
+        __syncthreads();
+        if (*fail) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t lbase = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
+#pragma unroll
+        for (int a = 0; a < NACC; ++a)
+#pragma unroll
+            for (int c = 0; c < 64; c += 32) {
+                float v0[16], v1[16];
+                tc_ld16(lbase + a * BN + c, v0);
+                tc_ld16(lbase + a * BN + c + 16, v1);
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (a < 3) {   // acc0..acc2: error-free two-sum into (hi, lo)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        two_sum_f32(chi[c + i], clo[c + i], v0[i]);
+                        two_sum_f32(chi[c + 16 + i], clo[c + 16 + i], v1[i]);
+                    }
+                } else {       // acc3 (below 2^-20 of the scale): into the low word
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        clo[c + i] = __fadd_rn(clo[c + i], v0[i]);
+                        clo[c + 16 + i] = __fadd_rn(clo[c + 16 + i], v1[i]);
                     }
                 }
             }
-        }
-        if (last_of_chunk) {
-            if (tid == 0) tc_commit(&dbar);
-            __syncthreads();
-            if (s_fail) { ok = false; break; }
-            if (!tc_wait(&dbar, (uint32_t)(chunk & 1))) {
-                raise_err(err, kDevTimeout);
-                s_fail = 1;
-            }
-            __syncthreads();
-            if (s_fail) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t lbase = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
-#pragma unroll
-            for (int a = 0; a < NACC; ++a)
-#pragma unroll
-                for (int c = 0; c < 64; c += 32) {
-                    float v0[16], v1[16];
-                    tc_ld16(lbase + a * BN + c, v0);
-                    tc_ld16(lbase + a * BN + c + 16, v1);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-                    if (a < 3) {   // acc0..acc2: error-free two-sum into (hi, lo)
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            two_sum_f32(chi[c + i], clo[c + i], v0[i]);
-                            two_sum_f32(chi[c + 16 + i], clo[c + 16 + i], v1[i]);
-                        }
-                    } else {       // acc3 (below 2^-20 of the scale): into the low word
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            clo[c + i] = __fadd_rn(clo[c + i], v0[i]);
-                            clo[c + 16 + i] = __fadd_rn(clo[c + 16 + i], v1[i]);
-                        }
-                    }
-                }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            ++chunk;
-        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
     }
     if (!ok && tid == 0) {
         // let every committed MMA group finish before TMEM is released, and every issued copy land before the
         // shared memory is given up (both bounded)
+        const int iss = s_issued, ld = s_loaded;
         for (int s = 0; s < NSTAGE; ++s) {
-            const int uses = issued / NSTAGE + (s < issued % NSTAGE ? 1 : 0);
+            const int uses = iss / NSTAGE + (s < iss % NSTAGE ? 1 : 0);
             if (uses > 0) tc_wait(&empty[s], (uint32_t)((uses - 1) & 1));
         }
-        for (int kt = issued; kt < loaded; ++kt) tc_wait(&full[kt % NSTAGE], (uint32_t)((kt / NSTAGE) & 1));
+        for (int kt = iss; kt < ld; ++kt) tc_wait(&full[kt % NSTAGE], (uint32_t)((kt / NSTAGE) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -609,18 +623,20 @@ cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
         s0[q + 1] = s0[q] + (o.R + SROWS - 1) / SROWS;
         o.soff = -1;
         if (!sliced[q]) continue;
-        const int nkt = (o.K + BK - 1) / BK, rt = (o.R + BM - 1) / BM;
+        const int nkp = padded_nkt(o.K), rt = (o.R + BM - 1) / BM;
         o.soff = bytes;
         for (int r = 0; r < rt; ++r)
-            for (int k = 0; k < nkt; ++k) jobs.push_back(OzJob{bytes + ((long long)r * nkt + k) * TILE_BYTES, (int)q, r, k, -1});
-        bytes += (long long)rt * nkt * TILE_BYTES;
+            for (int k = 0; k < nkp / KT_PER_JOB; ++k)
+                jobs.push_back(OzJob{bytes + ((long long)r * nkp + k * KT_PER_JOB) * TILE_BYTES, (int)q, r, k, -1});
+        bytes += (long long)rt * nkp * TILE_BYTES;
     }
     std::vector<long long> poff(ptab.size());
     for (size_t t = 0; t < ptab.size(); ++t) {
-        const int nkt = (ops[pB[t]].K + BK - 1) / BK;
+        const int nkp = padded_nkt(ops[pB[t]].K);
         poff[t] = bytes;
-        for (int k = 0; k < nkt; ++k) jobs.push_back(OzJob{bytes + (long long)k * TILE_BYTES, -1, 0, k, (int)t});
-        bytes += (long long)nkt * TILE_BYTES;
+        for (int k = 0; k < nkp / KT_PER_JOB; ++k)
+            jobs.push_back(OzJob{bytes + (long long)k * KT_PER_JOB * TILE_BYTES, -1, 0, k, (int)t});
+        bytes += (long long)nkp * TILE_BYTES;
     }
     cudaError_t e = cudaMalloc(&tt.d_exps, (size_t)std::max<long long>(nexp, 1) * sizeof(int));
     if (e != cudaSuccess) return e;
@@ -633,18 +649,18 @@ cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
         g.ea = ops[opA[i]].exps;
         g.eb = ops[opB[i]].exps;
         if (packed_in[i] >= 0) continue;
-        const int nkt = (g.K + BK - 1) / BK;
+        const int nkt = (g.K + BK - 1) / BK, nkp = padded_nkt(g.K);
         for (int mt = 0; mt < (g.M + BM - 1) / BM; ++mt)
             for (int nt = 0; nt < (g.N + BN - 1) / BN; ++nt)
-                tiles.push_back(OzTile{ops[opA[i]].soff + (long long)mt * nkt * TILE_BYTES,
-                                       ops[opB[i]].soff + (long long)nt * nkt * TILE_BYTES, (int)i, mt * BM, nt * BN, nkt, -1});
+                tiles.push_back(OzTile{ops[opA[i]].soff + (long long)mt * nkp * TILE_BYTES,
+                                       ops[opB[i]].soff + (long long)nt * nkp * TILE_BYTES, (int)i, mt * BM, nt * BN, nkt, -1});
     }
     std::vector<OzRow> rows;
     for (size_t t = 0; t < ptab.size(); ++t) {
         const OzOperand &ob = ops[pB[t]];
-        const int nkt = (ob.K + BK - 1) / BK;
+        const int nkt = (ob.K + BK - 1) / BK, nkp = padded_nkt(ob.K);
         for (int nt = 0; nt < (ob.R + BN - 1) / BN; ++nt)
-            tiles.push_back(OzTile{poff[t], ob.soff + (long long)nt * nkt * TILE_BYTES, ptab[t][0].p, 0, nt * BN, nkt, (int)t});
+            tiles.push_back(OzTile{poff[t], ob.soff + (long long)nt * nkp * TILE_BYTES, ptab[t][0].p, 0, nt * BN, nkt, (int)t});
         rows.insert(rows.end(), ptab[t].begin(), ptab[t].end());
     }
     std::stable_sort(tiles.begin(), tiles.end(), [](const OzTile &x, const OzTile &y) { return x.nkt > y.nkt; });
