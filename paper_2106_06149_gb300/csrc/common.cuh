@@ -185,6 +185,46 @@ __host__ __device__ __forceinline__ double df_to_double(float hi, float lo, int 
 #endif
 }
 
+// df_to_double without branches for the common case: finite hi and lo, hi zero or normal, lo zero or normal, the
+// result exponent in the normal FP64 range.  special is set otherwise; the caller then takes df_to_double.
+// The lo contribution is ((m_lo << 29) >> d) with d = e_hi - e_lo >= 24 after the renormalisation (one shift for
+// both directions: exact for d <= 29, truncated beyond), so independent conversions interleave freely.
+__host__ __device__ __forceinline__ double df_to_double_nb(float hi, float lo, int E, bool &special) {
+#ifdef __CUDA_ARCH__
+    const float s = __fadd_rn(hi, lo);
+    const float bp = __fsub_rn(s, hi);
+    const float l = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(lo, bp));
+    const unsigned bh = __float_as_uint(s), bl = __float_as_uint(l);
+#else
+    const float s = hi + lo;
+    const float bp = s - hi;
+    const float l = (hi - (s - bp)) + (lo - bp);
+    unsigned bh, bl;
+    memcpy(&bh, &s, 4);
+    memcpy(&bl, &l, 4);
+#endif
+    const int eh = (int)((bh >> 23) & 0xFFu), el = (int)((bl >> 23) & 0xFFu);
+    int e = eh - 127 + 1023 + E;
+    const unsigned long long mh = (unsigned long long)((bh & 0x7FFFFFu) | 0x800000u) << 29;
+    const unsigned long long ml = el != 0 ? (unsigned long long)((bl & 0x7FFFFFu) | 0x800000u) << 29 : 0ULL;
+    const int d = max(0, min(eh - el, 63));
+    const unsigned long long lv = ml >> d;
+    unsigned long long M = ((bh ^ bl) >> 31) ? mh - lv : mh + lv;
+    const bool low = M < (1ULL << 52);   // hi a power of two, lo of the other sign
+    M = low ? M << 1 : M;
+    e = low ? e - 1 : e;
+    special = eh == 255 || el == 255 || (el == 0 && (bl & 0x7FFFFFu)) || (eh != 0 && (e <= 1 || e >= 2046));
+    const unsigned long long sign = (unsigned long long)(bh >> 31) << 63;
+    const unsigned long long bits = eh == 0 ? sign : sign | ((unsigned long long)e << 52) | (M & ((1ULL << 52) - 1));
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)bits);
+#else
+    double r;
+    memcpy(&r, &bits, 8);
+    return r;
+#endif
+}
+
 // (h + l) g 2^E for a double-float g: the product in double-float on the FP32 pipe, then integer assembly
 __device__ __forceinline__ double df_to_double_mul(float h, float l, float2 g, int E) {
     float ph = 0.f, pl = 0.f;

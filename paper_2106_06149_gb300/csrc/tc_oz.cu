@@ -19,11 +19,12 @@
 // Two kernels per batch: (1) the row scales, then every operand tile (128 rows x 16 K) is sliced once into four
 // 4 KB images already in the canonical no-swizzle K-major shared-memory layout (8 rows x 16 bytes per core
 // matrix; K-adjacent core matrices 128 B apart, 8-row groups 256 B apart), two tiles per slicing job; (2) the
-// GEMM: one CTA (256 threads) per 128 x 128 output tile, a six-stage pipeline of 32 KB stages filled by bulk
-// asynchronous copies (cp.async.bulk + mbarrier transaction counts; five stages of copies in flight hide the
-// load latency), thread 0 issuing 13 tcgen05.mma.kind::f16 (M = 128, N = 128, K = 16) per stage into four TMEM
-// accumulators (512 columns).  Every wait is bounded: on expiry the
-// error word is set, in-flight MMAs are waited for (bounded), TMEM is freed and the CTA returns.
+// GEMM: one CTA (256 threads) per 128 x 128 output tile, a six-stage pipeline of 32 KB stages filled by four
+// producer warps with 16-byte asynchronous copies (completion counted per thread on the stage's mbarrier; five
+// stages in flight), thread 0 issuing 13 tcgen05.mma.kind::f16 (M = 128, N = 128, K = 16) per stage into four
+// TMEM accumulators (512 columns), and rows of the result leaving by bulk stores or bulk add-reductions.  Every
+// wait is bounded: on expiry the error word is set, in-flight MMAs are waited for (bounded), TMEM is freed and
+// the CTA returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -47,6 +48,7 @@ constexpr int IMG = BM * BK * 2;                  // 4 KB: one slice of one 128 
 constexpr int TILE_BYTES = NSLICE * IMG;          // 16 KB: the four slices of one operand tile
 constexpr int STAGE = 2 * TILE_BYTES;             // A and B
 constexpr int NSTAGE = 6;                         // five stages of copies in flight ahead of the MMAs
+constexpr int kProducers = 128;                   // copy threads (warps 4..7)
 constexpr int SMEM = NSTAGE * STAGE + 1024;
 constexpr int CHUNK_KT = 256 / BK;                // 256 K per exact chunk
 constexpr int KT_PER_JOB = SK / BK;
@@ -57,19 +59,6 @@ constexpr uint32_t kIdesc = idesc_bf16(BM, BN);
 __device__ __forceinline__ uint32_t koff(int r, int k) { return kmajor_off(r, k, BK); }
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) { return smem_desc(saddr, 16 * BK); }
 constexpr int NACC = 4;
-
-
-__device__ __forceinline__ void expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// bulk asynchronous copy global -> shared, completion counted on bar (16-byte aligned, size % 16 == 0)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
 
 
 __device__ __forceinline__ int find_prob(const long long *__restrict__ pre, int nprob, long long t) {
@@ -240,7 +229,7 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], dbar;
     __shared__ uint32_t s_taddr;
-    __shared__ int s_fail, s_issued, s_loaded;
+    __shared__ int s_fail, s_issued;
 
     const OzTile T = tiles[blockIdx.x];
     const int m0 = T.m0, n0 = T.n0, nkt = T.nkt;
@@ -250,14 +239,13 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
 
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(kProducers));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&dbar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
         s_issued = 0;
-        s_loaded = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_taddr)));
@@ -278,29 +266,33 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         clo[j] = 0.f;
     }
 
-    // Roles: thread 32 (warp 1) copies k tile j into stage j % NSTAGE as soon as the MMAs of tile j - NSTAGE are
-    // done; thread 0 waits for each tile's data and issues its MMAs, and never waits for MMA completion inside a
-    // chunk.  All threads drain the accumulators after each 256-K chunk; the copies of the next chunk's first
-    // stages are in flight meanwhile.
+    // Roles: warps 4..7 copy k tile j into stage j % NSTAGE (16-byte asynchronous copies, 16 per thread, each
+    // thread's completion counted on the stage's mbarrier) as soon as the MMAs of tile j - NSTAGE are done; thread
+    // 0 waits for each tile's data and issues its MMAs, and never waits for MMA completion inside a chunk.  All
+    // threads drain the accumulators after each 256-K chunk; the copies of the next chunk's first stages are in
+    // flight meanwhile.
     volatile int *fail = &s_fail;
-    int loaded = 0;   // k tiles whose copies were issued (thread 32)
+    int loaded = 0;   // k tiles whose copies were issued (producer threads)
     int issued = 0;   // MMA groups committed (thread 0)
+    const int ptid = tid - (NT - kProducers);   // producer index, or negative
     auto load_stage = [&](int kt) {
         const int st = kt % NSTAGE;
         ++loaded;
-        unsigned char *sA = smem + st * STAGE;
-        expect_tx(&full[st], STAGE);
+        const uint32_t dst = smem_u32(smem + st * STAGE);
+        const unsigned char *srcA = Aimg + (long long)kt * TILE_BYTES, *srcB = Bimg + (long long)kt * TILE_BYTES;
 #pragma unroll
-        for (int i = 0; i < NSLICE; ++i) {   // one copy per slice image keeps several requests in flight
-            bulk_g2s(sA + i * IMG, Aimg + (long long)kt * TILE_BYTES + i * IMG, IMG, &full[st]);
-            bulk_g2s(sA + TILE_BYTES + i * IMG, Bimg + (long long)kt * TILE_BYTES + i * IMG, IMG, &full[st]);
+        for (int q = 0; q < STAGE / 16 / kProducers; ++q) {
+            const int ch = ptid + q * kProducers;   // 16-byte chunk of the stage: A images, then B images
+            const unsigned char *src = ch < TILE_BYTES / 16 ? srcA + ch * 16 : srcB + (ch - TILE_BYTES / 16) * 16;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + ch * 16), "l"(src) : "memory");
         }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st])) : "memory");
     };
     bool ok = true;
     const int nchunk = (nkt + CHUNK_KT - 1) / CHUNK_KT;
     for (int chunk = 0; chunk < nchunk; ++chunk) {
         const int kt0 = chunk * CHUNK_KT, kt1 = min(nkt, kt0 + CHUNK_KT);
-        if (tid == 32) {
+        if (ptid >= 0) {
             const int jend = min(nkt, kt1 + NSTAGE - 1);
             while (loaded < jend && !*fail) {
                 const int j = loaded;
@@ -311,7 +303,6 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
                 }
                 load_stage(j);
             }
-            s_loaded = loaded;
         } else if (tid == 0) {
             for (int kt = kt0; kt < kt1 && !*fail; ++kt) {
                 const int st = kt % NSTAGE;
@@ -320,6 +311,8 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
                     *fail = 1;
                     break;
                 }
+                // the stage was written through the generic proxy: order it before the tensor core's reads
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 // descriptors of the stage's images: the start-address field (address / 16, 14 bits) of the base
                 // descriptor plus the image offset / 16 (no carry: shared addresses are below 256 KB)
@@ -384,15 +377,14 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
     }
+    if (ptid >= 0) asm volatile("cp.async.wait_all;" ::: "memory");   // every copy of this thread has landed
     if (!ok && tid == 0) {
-        // let every committed MMA group finish before TMEM is released, and every issued copy land before the
-        // shared memory is given up (both bounded)
-        const int iss = s_issued, ld = s_loaded;
+        // let every committed MMA group finish before TMEM is released (bounded)
+        const int iss = s_issued;
         for (int s = 0; s < NSTAGE; ++s) {
             const int uses = iss / NSTAGE + (s < iss % NSTAGE ? 1 : 0);
             if (uses > 0) tc_wait(&empty[s], (uint32_t)((uses - 1) & 1));
         }
-        for (int kt = iss; kt < ld; ++kt) tc_wait(&full[kt % NSTAGE], (uint32_t)((kt / NSTAGE) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -404,8 +396,9 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
     // Epilogue.  The per-row destinations (the tile's own problem, or a packed tile's row table) and the per-column
     // scale exponents are fetched first, one load per thread, so that the element loop reads shared memory only
     // (a chain of dependent global loads per row made this phase longer than the main loop).  The (hi, lo) sums
-    // then pass through shared memory (the stage buffers are idle) for row-wise coalesced stores.  alpha = +-2^k
-    // folds into the exponent; the FP64 value is assembled with integer operations (df_to_double).
+    // then pass through shared memory (the stage buffers are idle), are converted there in place, and rows leave
+    // as wholes.  alpha = +-2^k folds into the exponent; the FP64 value is assembled with integer operations
+    // (df_to_double_nb).
     __shared__ double *s_crow[BM];
     __shared__ const int *s_nmap[BM];
     __shared__ double s_alpha[BM], s_beta[BM];
@@ -455,7 +448,7 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
 #pragma unroll
         for (int j = 0; j < 64; ++j) sC[r * LDC + (warp >> 2) * 64 + j] = make_float2(chi[j], clo[j]);
     }
-    __syncthreads();
+    __syncthreads();   // the (hi, lo) tile, row constants and column exponents in shared memory
     const int N = descs[T.p].N;
     const int nvalid = max(0, min(BN, N - n0));
     // (hi, lo) -> alpha times the FP64 value, in place (each element read and written by the same thread)
@@ -464,13 +457,38 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         const int em = s_em[r], rf = s_rf[r];
         const double alpha = s_alpha[r];
         const long long asign = (rf & 4) ? (long long)0x8000000000000000ULL : 0LL;
+        // the lane's four conversions branch-free (they interleave), then the rare special cases
+        constexpr int CU = BN / 32;
+        double v[CU];
+        bool sp[CU], any = false;
 #pragma unroll
-        for (int u = 0; u < BN / 32; ++u) {
+        for (int u = 0; u < CU; ++u) {
             const int c = lane + 32 * u;
-            if (c < nvalid) {
-                const float2 hl = sC[r * LDC + c];
-                const double v = __longlong_as_double(__double_as_longlong(df_to_double(hl.x, hl.y, em + s_eb[c])) ^ asign);
-                sD[r * LDC + c] = (rf & 2) ? v : v * alpha;
+            const float2 hl = sC[r * LDC + c];
+            v[u] = df_to_double_nb(hl.x, hl.y, em + s_eb[c], sp[u]);
+            sp[u] = sp[u] && c < nvalid;
+            any |= sp[u];
+        }
+        if (any) {
+#pragma unroll
+            for (int u = 0; u < CU; ++u)
+                if (sp[u]) {
+                    const int c = lane + 32 * u;
+                    const float2 hl = sC[r * LDC + c];
+                    v[u] = df_to_double(hl.x, hl.y, em + s_eb[c]);
+                }
+        }
+        if (rf & 2) {   // alpha = +-2^k, already in the exponent (uniform per row: no FP64 multiply issued)
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const int c = lane + 32 * u;
+                if (c < nvalid) sD[r * LDC + c] = __longlong_as_double(__double_as_longlong(v[u]) ^ asign);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const int c = lane + 32 * u;
+                if (c < nvalid) sD[r * LDC + c] = v[u] * alpha;
             }
         }
     }
