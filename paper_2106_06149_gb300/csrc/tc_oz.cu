@@ -186,22 +186,28 @@ __global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ o
         if (r == 0) s_along_k = q >= 0 ? ops[q].kcontig : 1;
     }
     __syncthreads();
-    auto elem = [&](int r, int k) -> double {
+    // all of a thread's element addresses first, then all its loads, then the shared-memory stores: sixteen
+    // loads in flight per thread instead of one (the loop with a load, a store and a branch per element was
+    // latency-bound)
+    constexpr int PER = BM * SK / NT;
+    const bool along_k = s_along_k;
+    const double *src[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int idx = tid + q * NT;
+        const int r = along_k ? idx / SK : idx % BM, k = along_k ? idx % SK : idx / BM;
         const int kk = k0 + k;
-        if (kk >= kn[r]) return 0.0;
-        const long long kc = rkmap[r] ? rkmap[r][kk] : kk;
-        return rbase[r][kc * rks[r]];
-    };
-    if (s_along_k) {
-        for (int idx = tid; idx < BM * SK; idx += NT) {   // lanes along k
-            const int r = idx / SK, k = idx % SK;
-            xs[k][r] = elem(r, k);
-        }
-    } else {
-        for (int idx = tid; idx < BM * SK; idx += NT) {   // lanes along rows
-            const int k = idx / BM, r = idx % BM;
-            xs[k][r] = elem(r, k);
-        }
+        const int *km = rkmap[r];
+        src[q] = kk < kn[r] ? rbase[r] + (km ? (long long)km[kk] : (long long)kk) * rks[r] : nullptr;
+    }
+    double val[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) val[q] = src[q] ? __ldg(src[q]) : 0.0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int idx = tid + q * NT;
+        const int r = along_k ? idx / SK : idx % BM, k = along_k ? idx % SK : idx / BM;
+        xs[k][r] = val[q];
     }
     __syncthreads();
     unsigned char *img = scratch + J.dst;
