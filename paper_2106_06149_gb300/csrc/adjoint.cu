@@ -531,6 +531,10 @@ cudaError_t AdjointPlan::plan(osv_ctx &c) {
     AL(dB64, c.aux_ptr[n] * (long long)nv);
     AL(dF64, (long long)n * n);
     AL(A1, (long long)n * nv * nm);
+    if (2 * nm <= kAdjTcMaxOrder) {   // (either precision: the plan outlives a change of mode)
+        AL(TbS, std::max<long long>(c.slot_mat, 1));
+        AL(ebS, std::max<size_t>(c.slots.h.size(), 1));
+    }
     grid = (int)std::min<size_t>(c.cl.size(), 152 * 4);
     pstride = 4LL * nm * nm;
     AL(scratch, (long long)std::max(grid, 1) * 5 * pstride);
@@ -790,8 +794,8 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
         const int ld = 2 * nm + 1;
         const size_t sh = 4 * (size_t)ld * ld * sizeof(float2);
         const AdjArgsS as{c.cinfo.d, c.order.d, c.slots.d, c.terms.d, c.pinfo.d, c.rdim, c.focc, c.pe, c.Tslot,
-                          c.Stil, n, (int)c.cl.size(), ld, GS, GF, GSc, dF64};
-        if (c.osv_mixed && !c.cl.empty() && 2 * nm <= kAdjTcMaxOrder) {
+                          c.Stil, n, (int)c.cl.size(), ld, GS, GF, GSc, dF64, TbS, ebS};
+        if (c.osv_mixed && !c.cl.empty() && 2 * nm <= kAdjTcMaxOrder && TbS && ebS) {
             // mixed modes, pair orders <= 80: exact BF16 slices on the tensor cores
             CK(launch_cluster_adjoint_tc(as, (int)c.cl.size(), c.derr, s));
         } else if (c.osv_mixed && !c.cl.empty() && sh <= 216 * 1024) {

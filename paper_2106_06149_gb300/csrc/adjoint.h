@@ -24,6 +24,8 @@ struct AdjArgsS {
     const double *focc, *e, *Tslot, *Stil;
     int n_occ, ncl, ld;
     double *GS, *GF, *GSc, *dF;
+    double *TbS;   // tensor-core kernel: Tb = 2T - T^T per slot (slot amplitude layout), formed by its slot phase
+    int *ebS;      // and the scale exponent of each slot's Tb
 };
 
 // The same partials on the tensor cores (exact BF16 slices of every operand, tcgen05 with the sums in tensor
@@ -39,6 +41,8 @@ struct AdjointPlan {
            *ptmp = nullptr, *GSc = nullptr, *GSco = nullptr, *ctmp = nullptr, *HS = nullptr, *HF = nullptr;
     // chain to W, Q, B and the OSV relaxation
     double *Z = nullptr, *dQ = nullptr, *dB64 = nullptr, *dF64 = nullptr, *A1 = nullptr;
+    double *TbS = nullptr;   // Tb per cluster slot (tensor-core adjoint)
+    int *ebS = nullptr;
     double *scratch = nullptr;
     int *zrows = nullptr;   // per off-diagonal pair: W row maps of its two stacked-K products into Z
     long long pstride = 0;

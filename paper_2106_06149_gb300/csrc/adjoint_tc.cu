@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
             }
             const int eT = scale_exp_of_bits(block_max_bits(mt, s_red));
             const int eB = scale_exp_of_bits(block_max_bits(mb, s_red));
+            if (tid == 0) A.ebS[s] = eB;
             // slot 0: Tb (A), slot 1: T^T (A), slot 2: T (B), slot 3: Tb^T (B): at (a, k) they hold Tb(a, k),
             // T(k, a), T(a, k), Tb(k, a) = 2 T(k, a) - T(a, k)
             for (int it = tid; it < kItems; it += kTC) {
@@ -236,6 +237,10 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                 load(it, a, k0, x, xt);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) v[j] = 2.0 * x[j] - xt[j];
+                if (a < r)   // kept for the coupling terms of this destination slot
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (k0 + j < r) A.TbS[S.t_off + (long long)a * np + k0 + j] = v[j];
                 put8(c.img[0], a, k0, v, eB);
                 put8(c.img[1], a, k0, xt, eT);
                 put8(c.img[2], a, k0, x, eT);
@@ -310,7 +315,7 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
             const double f = A.focc[(long long)Tm.fx * A.n_occ + Tm.fy];
             const double *Sb = A.Stil + Tm.sblk;
             const long long lds = Tm.s_trans ? np : nq;
-            const double *Tq = A.Tslot + Ssl.t_off, *Tp = A.Tslot + Sd.t_off;
+            const double *Tq = A.Tslot + Ssl.t_off;
             const double wm = w * Sd.mult;
             auto sval = [&](int c_, int b_) -> double {   // S~(c, b), zero outside rp x rq
                 return (c_ < rp && b_ < rq) ? (Tm.s_trans ? Sb[(long long)b_ * lds + c_] : Sb[(long long)c_ * lds + b_]) : 0.0;
@@ -318,21 +323,19 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
             auto tqval = [&](int x_, int y_) -> double {   // T'(x, y), zero outside rq x rq
                 return (x_ < rq && y_ < rq) ? (Tm.t_trans ? Tq[(long long)y_ * nq + x_] : Tq[(long long)x_ * nq + y_]) : 0.0;
             };
-            // scales: Tb_p, S~, T'
-            unsigned long long mb = 0, ms = 0, mq = 0;
+            // scales: S~, T' (Tb's, and Tb itself, from the destination slot's pass above: no FP64 work here)
+            const double *Tbp = A.TbS + Sd.t_off;
+            unsigned long long ms = 0, mq = 0;
             for (int it = tid; it < kItems; it += kTC) {
                 const int a = it % kR, k0 = (it / kR) * 8;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int k = k0 + j;
-                    const bool in = a < rp && k < rp;
-                    const double xb = in ? 2.0 * Tp[(long long)a * np + k] - Tp[(long long)k * np + a] : 0.0;
-                    mb = max(mb, abs_bits64(xb));
                     ms = max(ms, abs_bits64(sval(k, a)));
                     mq = max(mq, abs_bits64(tqval(a, k)));
                 }
             }
-            const int eTb = scale_exp_of_bits(block_max_bits(mb, s_red));
+            const int eTb = A.ebS[Tm.dst];
             const int eS = scale_exp_of_bits(block_max_bits(ms, s_red));
             const int eTq = scale_exp_of_bits(block_max_bits(mq, s_red));
             // slot 0: Tb (A), slot 1: Tb^T (A), slot 2: B[b][c] = S~(c, b), slot 3: B[b][c] = T'(c, b)
@@ -343,9 +346,8 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                 for (int j = 0; j < 8; ++j) {
                     const int k = k0 + j;
                     const bool in = a < rp && k < rp;
-                    const double x = in ? Tp[(long long)a * np + k] : 0.0, xt = in ? Tp[(long long)k * np + a] : 0.0;
-                    v0[j] = 2.0 * x - xt;
-                    v1[j] = 2.0 * xt - x;
+                    v0[j] = in ? Tbp[(long long)a * np + k] : 0.0;
+                    v1[j] = in ? Tbp[(long long)k * np + a] : 0.0;
                 }
                 put8(c.img[0], a, k0, v0, eTb);
                 put8(c.img[1], a, k0, v1, eTb);
