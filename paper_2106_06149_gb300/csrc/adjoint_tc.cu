@@ -207,6 +207,10 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                     xt[j] = in ? T[(long long)(k0 + j) * np + a] : 0.0;
                 }
             };
+            double *Tbs = A.TbS + S.t_off;
+            auto tbval = [&](int x_, int y_) -> double {   // Tb(x, y), zero outside r x r
+                return (x_ < r && y_ < r) ? Tbs[(long long)x_ * np + y_] : 0.0;
+            };
             unsigned long long mt = 0, mb = 0;
             double tt = 0.0;
             for (int it = tid; it < kItems; it += kTC) {
@@ -219,6 +223,8 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                     tt = fma(x[j], xb, tt);
                     mt = max(mt, abs_bits64(x[j]));
                     mb = max(mb, abs_bits64(xb));
+                    // kept for the passes below and the coupling terms of this destination slot
+                    if (a < r && k0 + j < r) Tbs[(long long)a * np + k0 + j] = xb;
                 }
             }
             tt = block_sum(tt, s_dred);
@@ -236,16 +242,12 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
                 double x[8], xt[8], v[8];
                 load(it, a, k0, x, xt);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = 2.0 * x[j] - xt[j];
-                if (a < r)   // kept for the coupling terms of this destination slot
-#pragma unroll
-                    for (int j = 0; j < 8; ++j)
-                        if (k0 + j < r) A.TbS[S.t_off + (long long)a * np + k0 + j] = v[j];
+                for (int j = 0; j < 8; ++j) v[j] = tbval(a, k0 + j);
                 put8(c.img[0], a, k0, v, eB);
                 put8(c.img[1], a, k0, xt, eT);
                 put8(c.img[2], a, k0, x, eT);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = 2.0 * xt[j] - x[j];
+                for (int j = 0; j < 8; ++j) v[j] = tbval(k0 + j, a);
                 put8(c.img[3], a, k0, v, eB);
             }
             // M2 = Tb T^T + T^T Tb (columns kColA)
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const double ep = s_ep[k0 + j];
-                    m3 = max(m3, abs_bits64((2.0 * x[j] - xt[j]) * ep));
+                    m3 = max(m3, abs_bits64(tbval(a, k0 + j) * ep));
                     m4 = max(m4, abs_bits64(ep * xt[j]));
                 }
             }
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const double ep = s_ep[k0 + j];
-                    v3[j] = (2.0 * x[j] - xt[j]) * ep;
+                    v3[j] = tbval(a, k0 + j) * ep;
                     v4[j] = ep * xt[j];
                 }
                 put8(c.img[0], a, k0, v3, e3);
