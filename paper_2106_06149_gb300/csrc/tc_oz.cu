@@ -73,14 +73,15 @@ __device__ __forceinline__ int find_prob(const long long *__restrict__ pre, int 
 // One GEMM operand as the slicing passes see it: R rows over K, element (r, k) = ptr[row(r) ld + kk(k)] when the
 // rows are K-contiguous (A, transA = 0; B, transB = 1), ptr[kk(k) ld + row(r)] otherwise, with optional row and
 // K index maps.  Problems that read the same operand (same pointer, layout, maps and sizes) share one entry: its
-// row scales and slice images are computed once per batch.
+// row scales and slice images are computed once per batch.  An A operand read only by row-packed problems gets its
+// scales but no images of its own (its rows are sliced into the packed tiles).
 struct OzOperand {
     const double *ptr;
     long long ld;
     const int *rowmap, *kmap;
     int R, K, kcontig;
     int *exps;         // row scale exponents (R)
-    long long soff;    // byte offset of its slice images in the scratch
+    long long soff;    // byte offset of its slice images in the scratch (-1: not sliced on its own)
 };
 
 // Row scales: exps[r] = e with max_k |X(r,k)| = f 2^e, f in [0.5, 1) (0 for a zero row).  One CTA per block of
