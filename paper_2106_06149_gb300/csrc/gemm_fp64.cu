@@ -266,7 +266,8 @@ cudaError_t gemm_batch_upload(GemmBatch &b) {
     gemm_batch_free(b);
     if (b.h.empty()) return cudaSuccess;
     // 64 x 64 tile offsets (FP64 kernel) and the double-float kernel's tile shape: the one with the least
-    // max(1, waves of two CTAs per SM) x (tile area), i.e. the least padded work on the critical path
+    // ceil(tiles / SMs) x (tile area), the padded work of the busiest SM (the kernel is FP32-throughput bound, so
+    // an SM's co-resident tiles share its pipes; a near-empty last round still costs a whole tile)
     constexpr int kShapes = 5;
     const int sm[kShapes] = {64, 80, 48, 80, 48}, sn[kShapes] = {64, 80, 80, 48, 48};
     std::vector<long long> t[kShapes];
@@ -281,8 +282,8 @@ cudaError_t gemm_batch_upload(GemmBatch &b) {
     int best = 0;
     double best_cost = 0.0;
     for (int c = 0; c < kShapes; ++c) {
-        const double waves = std::max(1.0, (double)t[c].back() / (2 * 152));
-        const double cost = waves * sm[c] * sn[c];
+        const double per_sm = (double)((t[c].back() + 151) / 152);
+        const double cost = per_sm * sm[c] * sn[c];
         if (c == 0 || cost < best_cost) {
             best = c;
             best_cost = cost;
