@@ -34,6 +34,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "oz_pack.h"
 #include "tc_common.cuh"
 #include "tc_gemm.h"
 
@@ -593,40 +594,22 @@ cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
         opA[i] = add(Key{g.A, g.lda, g.transA == 0 ? g.a_rows : nullptr, g.k_idx_a, g.M, g.K, g.transA == 0 ? 1 : 0});
         opB[i] = add(Key{g.B, g.ldb, g.n_idx_b, g.k_idx_b, g.N, g.K, g.transB == 1 ? 1 : 0});
     }
-    // row packing: problems of fewer than BM rows that read the same B operand (hence the same K and N) fill
-    // shared BM-row tiles, first fit in decreasing row count, when that saves tiles
+    // row packing (oz_pack.h): problems of fewer than BM rows that read the same B operand (hence the same K and N)
+    // share BM-row tiles
     std::vector<int> packed_in(h.size(), -1);   // packed tile of each problem
     std::vector<std::vector<OzRow>> ptab;       // row tables
     std::vector<int> pB;                        // B operand of each packed tile
     {
-        std::map<int, std::vector<int>> byB;
-        for (size_t i = 0; i < h.size(); ++i)
-            if (opB[i] >= 0 && h[i].M < BM) byB[opB[i]].push_back((int)i);
-        for (auto &kv : byB) {
-            std::vector<int> &v = kv.second;
-            if (v.size() < 2) continue;
-            std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return h[x].M > h[y].M; });
-            std::vector<int> fill;   // rows used per new tile
-            std::vector<int> bin(v.size());
-            for (size_t u = 0; u < v.size(); ++u) {
-                size_t t = 0;
-                while (t < fill.size() && fill[t] + h[v[u]].M > BM) ++t;
-                if (t == fill.size()) fill.push_back(0);
-                bin[u] = (int)t;
-                fill[t] += h[v[u]].M;
-            }
-            if (fill.size() >= v.size()) continue;
-            const int base = (int)ptab.size();
-            for (size_t t = 0; t < fill.size(); ++t) {
-                ptab.emplace_back(BM, OzRow{-1, -1, 0});
-                pB.push_back(kv.first);
-            }
-            std::vector<int> used(fill.size(), 0);
-            for (size_t u = 0; u < v.size(); ++u) {
-                const int p = v[u], t = bin[u];
-                packed_in[p] = base + t;
-                for (int m = 0; m < h[p].M; ++m) ptab[base + t][used[t] + m] = OzRow{p, opA[p], m};
-                used[t] += h[p].M;
+        std::vector<int> rows(h.size());
+        for (size_t i = 0; i < h.size(); ++i) rows[i] = opB[i] >= 0 ? h[i].M : 0;
+        for (const OzPackTile &pt : oz_pack_rows(rows, opB, BM)) {
+            const int t = (int)ptab.size();
+            ptab.emplace_back(BM, OzRow{-1, -1, 0});
+            pB.push_back(pt.key);
+            for (const auto &mb : pt.members) {
+                const int p = mb.first;
+                packed_in[p] = t;
+                for (int m = 0; m < h[p].M; ++m) ptab[t][mb.second + m] = OzRow{p, opA[p], m};
             }
         }
     }

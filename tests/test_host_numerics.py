@@ -1,4 +1,4 @@
-"""Host-compiled checks of device arithmetic helpers that have a host path (no GPU needed)."""
+"""Host-compiled checks of the device helpers and host planners that run without a GPU."""
 import os
 import shutil
 import subprocess
@@ -27,3 +27,16 @@ def test_df_to_double_branch_free_matches_reference(tmp_path):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "mismatch=0" in r.stdout and "beyond_2^-51=0" in r.stdout
+
+
+def test_row_packing_plan(tmp_path):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path / "pack_rows")
+    src = os.path.join(HERE, "host", "pack_rows.cpp")
+    r = subprocess.run([cxx, "-O2", "-std=c++17", src, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "fails=0" in r.stdout
