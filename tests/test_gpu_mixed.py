@@ -36,10 +36,14 @@ def run(m, p, prm, grad=True):
     return out
 
 
-@pytest.mark.parametrize("local", [False, True])
-def test_bf16x4_small_matches_fp64_and_oracle(osvmbe, local):
-    if local:
+@pytest.mark.parametrize("case", ["full", "local", "odd"])
+def test_bf16x4_small_matches_fp64_and_oracle(osvmbe, case):
+    # "odd": n_vir = 30 (rows not a multiple of four: the FP32 tridiagonalisation's scalar column path) and odd
+    # GEMM row lengths (the exact-slice epilogue's element path next to its bulk copies)
+    if case == "local":
         p = make_problem(6, 24, 90, geometry="cube", box=7.0, dmin=1.4, radius=4.5, seed=51)
+    elif case == "odd":
+        p = make_problem(6, 30, 110, seed=53)
     else:
         p = make_problem(6, 40, 150, seed=52)
     base = dict(n_osv_fixed=6, mbe_order=3, r2b=6.0, r3b=5.0, tol=1e-11)
