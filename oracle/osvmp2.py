@@ -27,7 +27,9 @@ Readings of points where the paper is silent (each listed in the design doc):
   * convergence: max over ordered pairs of ||V^T R V||_F <= tol;
   * OSV count: eigenvalues > l_osv, capped at n_osv_max, at least one; or exactly n_osv_fixed;
   * clusters: pair kept iff distance <= r2b, triple kept iff its three pairs are kept and all three
-    distances <= r3b (distance cutoffs in place of the OSV-overlap metric of Eqs. 26-27).
+    distances <= r3b (distance cutoffs in place of the OSV-overlap metric of Eqs. 26-27);
+  * with the OSV-overlap metric (select_clusters_osv): "exceeding" read as strictly greater, and a triple kept only
+    if its three pairs are kept 2b clusters (the metric of Eq. 3bscreen averages the pairs' 2b metrics).
 """
 from __future__ import annotations
 
@@ -40,7 +42,7 @@ DT = torch.float64
 
 __all__ = [
     "tkk", "osv_decompose", "n_osv_select", "select_clusters", "mbe_weights", "pair_domain",
-    "ClusterSolver", "energy", "gradient", "dense_B",
+    "ClusterSolver", "energy", "gradient", "dense_B", "osv_overlap_metric", "select_clusters_osv",
 ]
 
 
@@ -98,6 +100,42 @@ def select_clusters(centres, r2b, r3b, mbe_order):
                         continue
                     for k in range(j + 1, n):
                         if (i, k) in keep and (j, k) in keep and max(d[i, j], d[i, k], d[j, k]) <= r3b:
+                            out.append((i, j, k))
+    return out
+
+
+def osv_overlap_metric(Q):
+    """Pairwise OSV-overlap metric of Sec. 2.2.1, Eq. 2bscreen: s_ij = sum over (mu, nu) of <mu_i|nu_j>^2 divided by
+    sqrt(n_i n_j), with <mu_i|nu_j> the entries of Q_i^T Q_j and n_i the number of OSVs of LMO i.  Q is a list of
+    n_v x n_i blocks with orthonormal columns; then 0 <= s_ij <= 1 and s_ii = 1."""
+    n = len(Q)
+    s = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            O = torch.as_tensor(Q[i], dtype=DT).T @ torch.as_tensor(Q[j], dtype=DT)
+            s[i, j] = float((O * O).sum()) / math.sqrt(Q[i].shape[1] * Q[j].shape[1])
+    return s
+
+
+def select_clusters_osv(s2b, l2b, l3b, mbe_order):
+    """1b/2b/3b clusters by the OSV-overlap metrics of Sec. 2.2.1: a pair ij is a 2b cluster when s2b_ij exceeds
+    l2b; a triple ijk is a 3b cluster when its three pairs are 2b clusters and s3b_ijk = (s_ij + s_ik + s_jk) / 3
+    (Eq. 3bscreen) exceeds l3b.  mbe_order 0 returns one cluster holding every LMO."""
+    s2b = np.asarray(s2b, dtype=np.float64)
+    n = s2b.shape[0]
+    if mbe_order == 0:
+        return [tuple(range(n))]
+    out = [(i,) for i in range(n)]
+    if mbe_order >= 2:
+        pairs = [(i, j) for i in range(n) for j in range(i + 1, n) if s2b[i, j] > l2b]
+        out += pairs
+        if mbe_order >= 3:
+            keep = set(pairs)
+            for i in range(n):
+                for j in range(i + 1, n):
+                    for k in range(j + 1, n):
+                        if (i, j) in keep and (i, k) in keep and (j, k) in keep and \
+                                (s2b[i, j] + s2b[i, k] + s2b[j, k]) / 3.0 > l3b:
                             out.append((i, j, k))
     return out
 

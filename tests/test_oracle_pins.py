@@ -304,3 +304,66 @@ def test_euler_identity():
     g = oracle.gradient(p, prm)
     s = sum(float(np.sum(p.B_block(i) * g["dB"][i])) for i in range(p.n_occ))
     assert abs(s - 4.0 * g["E"]) <= 1e-12 * max(1.0, abs(g["E"])) * 100
+
+
+# ------------------------------------------------------------------ OSV-overlap cluster metric (Sec. 2.2.1)
+def _orthonormal(nv, k, rng):
+    q, _ = np.linalg.qr(rng.standard_normal((nv, k)))
+    return q
+
+
+def test_osv_overlap_metric_bounds_and_closed_forms():
+    """Eq. 2bscreen: s_ii = 1 and 0 <= s_ij <= 1 for orthonormal OSV blocks (the paper's Cauchy-Schwarz remark);
+    closed forms: identical spans give 1 whatever the basis inside them and the block sizes, orthogonal spans give
+    0, single OSVs give cos^2 of their angle, and a span half inside another (n_i = 2, n_j = 1) gives 1/sqrt(2)."""
+    rng = np.random.default_rng(5)
+    nv = 12
+    Q = [_orthonormal(nv, k, rng) for k in (1, 2, 3, 4, 2)]
+    s = oracle.osv_overlap_metric(Q)
+    assert np.allclose(np.diag(s), 1.0, atol=1e-13)
+    assert np.all(s >= -1e-15) and np.all(s <= 1.0 + 1e-13)
+    assert np.allclose(s, s.T, atol=1e-14)
+    # same span, another orthonormal basis of it (rotation inside the span)
+    R, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    assert abs(oracle.osv_overlap_metric([Q[2], Q[2] @ R])[0, 1] - 1.0) < 1e-13
+    # orthogonal spans
+    E = np.eye(nv)
+    assert abs(oracle.osv_overlap_metric([E[:, :3], E[:, 3:7]])[0, 1]) < 1e-15
+    # one OSV each: (q_i . q_j)^2
+    a, b = rng.standard_normal(nv), rng.standard_normal(nv)
+    a /= np.linalg.norm(a)
+    b /= np.linalg.norm(b)
+    assert abs(oracle.osv_overlap_metric([a[:, None], b[:, None]])[0, 1] - (a @ b) ** 2) < 1e-14
+    # n_i = 2 spanning e0, e1; n_j = 1 along e0: sum of squares 1, normalisation sqrt(2)
+    assert abs(oracle.osv_overlap_metric([E[:, :2], E[:, :1]])[0, 1] - 1.0 / np.sqrt(2.0)) < 1e-15
+
+
+def test_osv_metric_cluster_selection_bruteforce():
+    """2b clusters: s_ij exceeding l2b; 3b clusters: all three pairs kept and the mean of their s exceeding l3b
+    (Eq. 3bscreen).  Checked against a brute-force enumeration on random symmetric metrics, plus hand cases at
+    the thresholds (equality does not exceed)."""
+    s = np.array([[1.0, 0.5, 0.3, 1e-3],
+                  [0.5, 1.0, 0.01, 0.4],
+                  [0.3, 0.01, 1.0, 0.25],
+                  [1e-3, 0.4, 0.25, 1.0]])
+    got = oracle.select_clusters_osv(s, 0.01, 0.2, 3)
+    assert got == [(0,), (1,), (2,), (3,), (0, 1), (0, 2), (1, 3), (2, 3)]   # (1, 2) at l2b exactly: out
+    s2 = s.copy()
+    s2[1, 2] = s2[2, 1] = 0.0100001
+    got2 = oracle.select_clusters_osv(s2, 0.01, 0.2, 3)
+    assert (0, 1, 2) in got2 and (1, 2, 3) in got2 and (0, 1, 3) not in got2
+    assert oracle.select_clusters_osv(s, 0.01, 0.2, 1) == [(0,), (1,), (2,), (3,)]
+    assert oracle.select_clusters_osv(s, 0.01, 0.2, 0) == [(0, 1, 2, 3)]
+    rng = np.random.default_rng(9)
+    for _ in range(200):
+        n = int(rng.integers(1, 8))
+        m = rng.random((n, n)) ** 3
+        m = (m + m.T) / 2
+        np.fill_diagonal(m, 1.0)
+        l2, l3 = float(rng.random() * 0.2), float(rng.random() * 0.5)
+        want = [(i,) for i in range(n)]
+        want += [c for c in itertools.combinations(range(n), 2) if m[c] > l2]
+        want += [c for c in itertools.combinations(range(n), 3)
+                 if all(m[p] > l2 for p in itertools.combinations(c, 2))
+                 and sum(m[p] for p in itertools.combinations(c, 2)) / 3 > l3]
+        assert oracle.select_clusters_osv(m, l2, l3, 3) == want
