@@ -43,6 +43,7 @@ DT = torch.float64
 __all__ = [
     "tkk", "osv_decompose", "n_osv_select", "select_clusters", "mbe_weights", "pair_domain",
     "ClusterSolver", "energy", "gradient", "dense_B", "osv_overlap_metric", "select_clusters_osv",
+    "weak_pair_one_block",
 ]
 
 
@@ -259,6 +260,58 @@ class ClusterSolver:
             R = self.residual(p, T)
             E = E + torch.sum((self.b.K(p) + R) * (2.0 * T[p] - T[p].T))
         return E
+
+
+# ------------------------------------------------------------------------------- weak 2b clusters
+def weak_pair_one_block(problem, params, i, j, n_osv=None, tol=1e-12, max_iter=500):
+    """One-block amplitudes of a weak 2b cluster {i, j} (Sec. 2.2.2).
+
+    The pair amplitudes T_(ij,ij) of the 2b cluster are restricted to their upper-right block X (rows: the OSVs of
+    i, columns: the OSVs of j; the direct-dispersion excitations), T_(ij,ij) = E_i X E_j^T, and X solves the
+    upper-right block of the 2b cluster residual of Eq. 4, R^{i,j}_(i,j) = E_i^T R_(ij,ij) E_j = 0.  The diagonal
+    pairs keep their 1b cluster amplitudes T^i_(ii,ii), T^j_(jj,jj) in the f_ij coupling terms.  Iterations:
+    X <- X - U_i [(U_i^T R U_j) / (e_i + e_j - f_ii - f_jj)] U_j^T with F_(i,i) = U_i diag(e_i) U_i^T.
+
+    Returns X, the weak pair's energy E_w (the Hylleraas terms <K + R, 2T - T^T> of Eq. 3 for the ordered pairs
+    (i, j) and (j, i), T_(ji,ji) = E_j X^T E_i^T), the iteration count and the final max |R^{i,j}_(i,j)|."""
+    assert i != j
+    eps, F, Bd = _inputs(problem, False)
+    Q, _ = _osvs(Bd, eps, F, params, n_osv)
+    b = _Blocks(Q, Bd, eps)
+    T = {}
+    for k in (i, j):   # 1b cluster amplitudes of the diagonal pairs
+        Tk, _, _, _ = ClusterSolver((k,), b, F, params.tau_red).solve(params.tol, params.max_iter)
+        T[(k, k)] = Tk[(k, k)]
+    ni, nj = Q[i].shape[1], Q[j].shape[1]
+    cs = ClusterSolver((i, j), b, F, params.tau_red)
+    p, pt = (i, j), (j, i)
+    ei, Ui = torch.linalg.eigh(b.F((i, i), (i, i)))
+    ej, Uj = torch.linalg.eigh(b.F((j, j), (j, j)))
+    D = ei[:, None] + ej[None, :] - F[i, i] - F[j, j]
+    X = torch.zeros(ni, nj, dtype=DT)
+
+    def embed(Xb):
+        Tp = torch.zeros(ni + nj, ni + nj, dtype=DT)
+        Tp[:ni, ni:] = Xb
+        return Tp
+
+    it, rn = 0, float("inf")
+    for it in range(max_iter + 1):
+        T[p] = embed(X)
+        Rb = cs.residual(p, T)[:ni, ni:]
+        rn = float(Rb.abs().max())
+        if rn <= tol or it == max_iter:
+            break
+        X = X - Ui @ ((Ui.T @ Rb @ Uj) / D) @ Uj.T
+    T[p] = embed(X)
+    Tt = torch.zeros(ni + nj, ni + nj, dtype=DT)   # (j, i): rows the OSVs of j, columns those of i
+    Tt[:nj, nj:] = X.T
+    T[pt] = Tt
+    Ew = torch.zeros((), dtype=DT)
+    for q in (p, pt):
+        R = cs.residual(q, T)
+        Ew = Ew + torch.sum((b.K(q) + R) * (2.0 * T[q] - T[q].T))
+    return X, float(Ew), it, rn
 
 
 # ------------------------------------------------------------------------------------------- top level

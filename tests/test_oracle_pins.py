@@ -367,3 +367,78 @@ def test_osv_metric_cluster_selection_bruteforce():
                  if all(m[p] > l2 for p in itertools.combinations(c, 2))
                  and sum(m[p] for p in itertools.combinations(c, 2)) / 3 > l3]
         assert oracle.select_clusters_osv(m, l2, l3, 3) == want
+
+
+# ------------------------------------------------------------------ weak 2b clusters, one-block scheme (Sec. 2.2.2)
+def _osv_blocks_numpy(p, n_osv):
+    """Q_k of every LMO with numpy (eigenvectors of Eq. 6's T_kk, largest first), independent of the oracle."""
+    Q = []
+    for k in range(p.n_occ):
+        Bk = p.B_dense(k)
+        den = p.eps_vir[:, None] + p.eps_vir[None, :] - 2.0 * p.f_occ[k, k]
+        w, U = np.linalg.eigh((Bk @ Bk.T) / den)
+        Q.append(U[:, np.argsort(-w, kind="stable")[:n_osv]])
+    return Q
+
+
+def test_weak_pair_one_block_is_a_sylvester_solve():
+    """With orthonormal OSVs per LMO, the upper-right block of Eq. 4 for a 2b cluster is the Sylvester equation
+    (F_ii - f_ii) X + X (F_jj - f_jj) = -K_(i,j) + f_ij (T_ii S_ij + S_ij T_jj), with F_xy = Q_x^T diag(eps) Q_y,
+    S_ij = Q_i^T Q_j, K_(i,j) = Q_i^T B_i B_j^T Q_j and T_ii, T_jj the 1b cluster amplitudes.  Solved here with
+    scipy's Sylvester solver on blocks built with numpy (a transposed block or a misplaced shift fails)."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    p = make_problem(4, 18, 40, seed=31)
+    p.f_occ = p.f_occ.copy()
+    p.f_occ[0, 3] = p.f_occ[3, 0] = -0.03      # a visible coupling
+    n_osv = 5
+    prm = Params(n_osv_fixed=n_osv, mbe_order=3, tol=1e-12)
+    i, j = 0, 3
+    X, Ew, it, rn = oracle.weak_pair_one_block(p, prm, i, j)
+    assert rn <= 1e-12
+    Q = _osv_blocks_numpy(p, n_osv)
+    # the oracle's OSVs may differ by column signs: compare in the sign convention of the numpy blocks
+    Qo = [oracle.osv_decompose(oracle.tkk(oracle.dense_B(p, k), torch.as_tensor(p.eps_vir), torch.tensor(p.f_occ[k, k])))[1][:, :n_osv].numpy()
+          for k in range(p.n_occ)]
+    sg = [np.sign(np.sum(Q[k] * Qo[k], axis=0)) for k in range(p.n_occ)]
+    Xo = (sg[i][:, None] * X.numpy()) * sg[j][None, :]
+    eps = p.eps_vir
+    Fii, Fjj = Q[i].T @ (eps[:, None] * Q[i]), Q[j].T @ (eps[:, None] * Q[j])
+    Sij = Q[i].T @ Q[j]
+    Kij = Q[i].T @ p.B_dense(i) @ p.B_dense(j).T @ Q[j]
+    Tii = {}
+    for k in (i, j):
+        Tk, _, _, _ = oracle.ClusterSolver((k,), oracle.osvmp2._Blocks(
+            [torch.as_tensor(q) for q in Q], [oracle.dense_B(p, m) for m in range(p.n_occ)],
+            torch.as_tensor(eps)), torch.as_tensor(p.f_occ), 1e-8).solve(1e-13, 500)
+        Tii[k] = Tk[(k, k)].numpy()
+    fij = p.f_occ[i, j]
+    rhs = -Kij + fij * (Tii[i] @ Sij + Sij @ Tii[j])
+    Xs = scipy_linalg.solve_sylvester(Fii - p.f_occ[i, i] * np.eye(n_osv), Fjj - p.f_occ[j, j] * np.eye(n_osv), rhs)
+    assert np.abs(Xo - Xs).max() <= 1e-10 * np.abs(Xs).max()
+
+
+def test_weak_pair_one_block_equals_full_2b_when_decoupled():
+    """If the OSV spans of i and j sit on disjoint canonical virtuals (S_ij = 0, F_ij = 0) and f_ij = 0, every block
+    of the 2b cluster's equations decouples: the one-block amplitudes equal the upper-right block of the full 2b
+    solution, and the weak pair's energy equals the 2b increment E^{ij} - E^i - E^j of the MBE energy."""
+    p = make_problem(2, 16, 30, seed=33)
+    nv = p.n_vir
+    B = p.B.copy()
+    for k, rows in ((0, slice(nv // 2, nv)), (1, slice(0, nv // 2))):
+        a = p.a(k)
+        blk = B[p.aux_ptr[k] * nv:p.aux_ptr[k + 1] * nv].reshape(nv, a)
+        blk[rows, :] = 0.0
+    q = Problem(**{**p.__dict__, "B": B, "f_occ": np.diag(np.diag(p.f_occ))})
+    prm = Params(n_osv_fixed=4, mbe_order=3, tol=1e-12)
+    X, Ew, it, rn = oracle.weak_pair_one_block(q, prm, 0, 1)
+    full = oracle.energy(q, prm, clusters=[(0,), (1,), (0, 1)])
+    mono = oracle.energy(q, prm, clusters=[(0,), (1,)])
+    assert abs(Ew - (full["E"] - mono["E"])) <= 1e-12 * abs(full["E"])
+    # the full cluster's (0, 1) amplitudes: zero outside the upper-right block, equal to X inside
+    eps, F, Bd = oracle.osvmp2._inputs(q, False)
+    Qo, _ = oracle.osvmp2._osvs(Bd, eps, F, prm, None)
+    Tf, _, _, _ = oracle.ClusterSolver((0, 1), oracle.osvmp2._Blocks(Qo, Bd, eps), F, prm.tau_red).solve(1e-13, 500)
+    T01 = Tf[(0, 1)].numpy()
+    n0 = Qo[0].shape[1]
+    assert np.abs(T01[:n0, n0:] - X.numpy()).max() <= 1e-10 * np.abs(X.numpy()).max()
+    assert np.abs(T01[:n0, :n0]).max() <= 1e-12 and np.abs(T01[n0:, :]).max() <= 1e-12
