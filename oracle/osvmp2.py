@@ -43,7 +43,7 @@ DT = torch.float64
 __all__ = [
     "tkk", "osv_decompose", "n_osv_select", "select_clusters", "mbe_weights", "pair_domain",
     "ClusterSolver", "energy", "gradient", "dense_B", "osv_overlap_metric", "select_clusters_osv",
-    "weak_pair_one_block",
+    "weak_pair_one_block", "energy_osv_screened",
 ]
 
 
@@ -375,6 +375,24 @@ def energy(problem, params, n_osv=None, clusters=None):
     with torch.no_grad():
         _, out, _ = _run(problem, params, n_osv, grad=False, clusters=clusters)
     return out
+
+
+def energy_osv_screened(problem, params, l2b, l3b, l_discard=1e-7, n_osv=None):
+    """MBE energy under the paper's screening (Sec. 2.2.1-2.2.2): strong 2b and 3b clusters by the OSV-overlap
+    metrics (select_clusters_osv), every weak pair (l_discard <= s2b_ij <= l2b) added through its one-block energy
+    (weak_pair_one_block), pairs with s2b_ij below l_discard dropped.  Weak pairs exist from mbe_order 2 on."""
+    with torch.no_grad():
+        eps, F, Bd = _inputs(problem, False)
+        Q, _ = _osvs(Bd, eps, F, params, n_osv)
+        s = osv_overlap_metric([q.numpy() for q in Q])
+        clusters = select_clusters_osv(s, l2b, l3b, params.mbe_order)
+        strong = energy(problem, params, n_osv, clusters=clusters)
+        n = problem.n_occ
+        weak = [(i, j) for i in range(n) for j in range(i + 1, n)
+                if params.mbe_order >= 2 and l_discard <= s[i, j] <= l2b]
+        Ew = sum(weak_pair_one_block(problem, params, i, j, n_osv)[1] for i, j in weak)
+    return dict(E=strong["E"] + Ew, E_strong=strong["E"], E_weak=float(Ew), clusters=clusters, weak_pairs=weak,
+                s2b=s)
 
 
 def gradient(problem, params, n_osv=None, clusters=None):

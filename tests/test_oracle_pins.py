@@ -442,3 +442,30 @@ def test_weak_pair_one_block_equals_full_2b_when_decoupled():
     n0 = Qo[0].shape[1]
     assert np.abs(T01[:n0, n0:] - X.numpy()).max() <= 1e-10 * np.abs(X.numpy()).max()
     assert np.abs(T01[:n0, :n0]).max() <= 1e-12 and np.abs(T01[n0:, :]).max() <= 1e-12
+
+
+def test_screened_energy_limits():
+    """The screened MBE energy (strong clusters by the OSV metric + one-block weak pairs - discarded pairs) in its
+    limits: every pair strong and no triple -> the MBE(2) energy of all pairs; every pair below the discard
+    threshold -> the sum of the 1b cluster energies; two decoupled LMOs (disjoint virtual spans, f_ij = 0) whose
+    pair is weak -> exactly the full 2b energy (the one-block scheme misses nothing there)."""
+    p = make_problem(4, 16, 30, seed=35)
+    prm = Params(n_osv_fixed=4, mbe_order=3, tol=1e-12)
+    scr = oracle.energy_osv_screened(p, prm, l2b=-1.0, l3b=2.0)
+    pairs = [c for c in itertools.combinations(range(4), 2)]
+    ref = oracle.energy(p, prm, clusters=[(i,) for i in range(4)] + pairs)
+    assert scr["weak_pairs"] == [] and abs(scr["E"] - ref["E"]) <= 1e-13 * abs(ref["E"])
+    scr0 = oracle.energy_osv_screened(p, prm, l2b=2.0, l3b=2.0, l_discard=2.0)
+    mono = oracle.energy(p, prm, clusters=[(i,) for i in range(4)])
+    assert scr0["weak_pairs"] == [] and abs(scr0["E"] - mono["E"]) <= 1e-13 * abs(mono["E"])
+    q = make_problem(2, 16, 30, seed=33)
+    nv = q.n_vir
+    B = q.B.copy()
+    for k, rows in ((0, slice(nv // 2, nv)), (1, slice(0, nv // 2))):
+        blk = B[q.aux_ptr[k] * nv:q.aux_ptr[k + 1] * nv].reshape(nv, q.a(k))
+        blk[rows, :] = 0.0
+    q = Problem(**{**q.__dict__, "B": B, "f_occ": np.diag(np.diag(q.f_occ))})
+    scrw = oracle.energy_osv_screened(q, prm, l2b=0.5, l3b=2.0, l_discard=-1.0)   # s_01 = 0: weak, kept
+    full = oracle.energy(q, prm, clusters=[(0,), (1,), (0, 1)])
+    assert scrw["weak_pairs"] == [(0, 1)]
+    assert abs(scrw["E"] - full["E"]) <= 1e-12 * abs(full["E"])
