@@ -18,6 +18,9 @@ Method (arXiv 2106.06149, Liang & Yang):
   * Gradient: amplitudes are variational (Sec. 2.1, Eq. 9 and the text before it), so dE/dx is the partial
     derivative of the weighted cluster Hylleraas functionals at fixed amplitudes.  It is taken here by torch
     autograd through the plain steps above, including the full OSV eigenvector derivative of eigh.
+  * Screening (Sec. 2.2.1): the OSV-overlap metric of Eq. 2bscreen and the 2b/3b selection of Eq. 3bscreen.
+  * Weak 2b clusters (Sec. 2.2.2): one-block amplitudes (the upper-right block of the 2b pair amplitudes, from the
+    upper-right block of Eq. 4) and their energy; the screened MBE energy that adds them to the strong clusters.
 
 Readings of points where the paper is silent (each listed in the design doc):
   * ordered pairs (i, j) and (j, i) are separate pair equations; the pair ii uses the domain Q_i only;
