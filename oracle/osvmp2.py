@@ -21,6 +21,7 @@ Method (arXiv 2106.06149, Liang & Yang):
   * Screening (Sec. 2.2.1): the OSV-overlap metric of Eq. 2bscreen and the 2b/3b selection of Eq. 3bscreen.
   * Weak 2b clusters (Sec. 2.2.2): one-block amplitudes (the upper-right block of the 2b pair amplitudes, from the
     upper-right block of Eq. 4) and their energy; the screened MBE energy that adds them to the strong clusters.
+  * Posterior correction (Sec. 3): Eq. 4 at the collective amplitudes over each pair's cluster LMOs, one step.
 
 Readings of points where the paper is silent (each listed in the design doc):
   * ordered pairs (i, j) and (j, i) are separate pair equations; the pair ii uses the domain Q_i only;
@@ -46,7 +47,7 @@ DT = torch.float64
 __all__ = [
     "tkk", "osv_decompose", "n_osv_select", "select_clusters", "mbe_weights", "pair_domain",
     "ClusterSolver", "energy", "gradient", "dense_B", "osv_overlap_metric", "select_clusters_osv",
-    "weak_pair_one_block", "energy_osv_screened",
+    "weak_pair_one_block", "energy_osv_screened", "posterior_correction",
 ]
 
 
@@ -396,6 +397,49 @@ def energy_osv_screened(problem, params, l2b, l3b, l_discard=1e-7, n_osv=None):
         Ew = sum(weak_pair_one_block(problem, params, i, j, n_osv)[1] for i, j in weak)
     return dict(E=strong["E"] + Ew, E_strong=strong["E"], E_weak=float(Ew), clusters=clusters, weak_pairs=weak,
                 s2b=s)
+
+
+def posterior_correction(problem, params, n_osv=None, clusters=None):
+    """One-step posterior correction over the MBE collective amplitudes (Sec. 3, the MBE(n > 3) estimate).
+
+    With the converged collective amplitudes T (Eqs. 28-32), every ordered pair ij that has them gets the residual
+    dR_(ij,ij) of Eq. 4 with k running over the union of the LMOs of the selected clusters that contain both i and
+    j (pairs without collective amplitudes count as zero), and one preconditioned step
+    dT = -V [(V^T dR V) / D] V^T in the pair's pseudo-canonical basis (the cluster solver's update).  Returns the
+    MBE energy, the same pair functional sum over pairs of <K + R(T'), 2T' - T'^T> (Eq. 3) at T' = T (E_global)
+    and at T' = T + dT (E_corrected), and the largest ||V^T dR V||_F."""
+    with torch.no_grad():
+        out = energy(problem, params, n_osv, clusters=clusters)
+        b, coll, cl = out["blocks"], out["collective"], out["clusters"]
+        F = torch.as_tensor(problem.f_occ, dtype=DT)
+        T = {p: t.clone() for p, t in coll.items()}
+        ks = {}
+        for p in T:
+            i, j = p
+            ks[p] = sorted({k for c in cl if i in c and j in c for k in c})
+        dT, rmax = {}, 0.0
+        for p in T:
+            cs = ClusterSolver(tuple(ks[p]), b, F, params.tau_red)
+            Tz = {q: T.get(q, torch.zeros(b.dom(q).shape[1], b.dom(q).shape[1], dtype=DT))
+                  for q in [(x, y) for x in ks[p] for y in ks[p]]}
+            R = cs.residual(p, Tz)
+            V, D = cs.precond(p)
+            Rt = V.T @ R @ V
+            rmax = max(rmax, float(torch.linalg.norm(Rt)))
+            dT[p] = -V @ (Rt / D) @ V.T
+        def functional(A):
+            E = torch.zeros((), dtype=DT)
+            for p in A:
+                cs = ClusterSolver(tuple(ks[p]), b, F, params.tau_red)
+                Tz = {q: A.get(q, torch.zeros(b.dom(q).shape[1], b.dom(q).shape[1], dtype=DT))
+                      for q in [(x, y) for x in ks[p] for y in ks[p]]}
+                R = cs.residual(p, Tz)
+                E = E + torch.sum((b.K(p) + R) * (2.0 * A[p] - A[p].T))
+            return float(E)
+
+        Eg = functional(T)
+        Ec = functional({p: T[p] + dT[p] for p in T})
+    return dict(E=out["E"], E_global=Eg, E_corrected=Ec, dR_max=rmax, k_sets=ks)
 
 
 def gradient(problem, params, n_osv=None, clusters=None):

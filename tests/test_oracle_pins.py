@@ -469,3 +469,21 @@ def test_screened_energy_limits():
     full = oracle.energy(q, prm, clusters=[(0,), (1,), (0, 1)])
     assert scrw["weak_pairs"] == [(0, 1)]
     assert abs(scrw["E"] - full["E"]) <= 1e-12 * abs(full["E"])
+
+
+def test_posterior_correction_vanishes_where_mbe_is_exact():
+    """The one-step posterior correction (Sec. 3) evaluates Eq. 4 at the collective amplitudes over the LMOs of the
+    pair's clusters.  Where MBE(3) is exact (three LMOs, every cluster kept; or one full cluster) the collective
+    amplitudes solve those equations: the residual vanishes, the step is zero and the pair functional equals the
+    MBE energy.  A k range missing an LMO of the cluster, or a mis-indexed pair, leaves a residual here."""
+    p = make_problem(3, 16, 40, seed=4)
+    for order, extra in ((3, dict(r2b=99.0, r3b=99.0)), (0, {})):
+        r = oracle.posterior_correction(p, Params(n_osv_fixed=4, mbe_order=order, tol=1e-12, **extra))
+        assert r["dR_max"] <= 1e-10
+        assert abs(r["E_corrected"] - r["E"]) <= 1e-12 * abs(r["E"])
+        assert abs(r["E_global"] - r["E"]) <= 1e-12 * abs(r["E"])
+        assert all(ks == [0, 1, 2] for ks in r["k_sets"].values())
+    # truncated MBE(3) on six LMOs: a nonzero residual and a finite step
+    q = make_problem(6, 16, 40, seed=3)
+    r = oracle.posterior_correction(q, Params(n_osv_fixed=4, mbe_order=3, r2b=6.0, r3b=5.0, tol=1e-12))
+    assert r["dR_max"] > 1e-8 and np.isfinite(r["E_corrected"])
