@@ -487,3 +487,130 @@ def test_posterior_correction_vanishes_where_mbe_is_exact():
     q = make_problem(6, 16, 40, seed=3)
     r = oracle.posterior_correction(q, Params(n_osv_fixed=4, mbe_order=3, r2b=6.0, r3b=5.0, tol=1e-12))
     assert r["dR_max"] > 1e-8 and np.isfinite(r["E_corrected"])
+
+
+# ------------------------------------------------------------------------------------------- OSV count
+def test_osv_count_rule_on_hand_built_spectra():
+    """Sec. 2.1 keeps the OSVs whose eigenvalues are greater than l_osv; the reading adds a cap n_osv_max (0 = no
+    cap), a floor of one OSV, and an exact count n_osv_fixed that overrides both.  Expected counts written by hand
+    from that rule: an eigenvalue equal to l_osv is not kept, the cap applies after the threshold, the floor after
+    the cap."""
+    w = torch.tensor([0.5, 0.3, 0.2, 1e-4, 1e-4, 5e-5, 0.0], dtype=DT)
+    sel = oracle.n_osv_select
+    assert sel(w, 1e-4, 0, 0) == 3            # 1e-4 itself is not "greater than" 1e-4
+    assert sel(w, 9.9e-5, 0, 0) == 5          # just below: the two eigenvalues at 1e-4 are kept
+    assert sel(w, 1e-4, 2, 0) == 2            # cap below the count
+    assert sel(w, 1e-4, 3, 0) == 3            # cap equal to the count
+    assert sel(w, 1e-4, 10, 0) == 3           # cap above the count
+    assert sel(w, 1.0, 10, 0) == 1            # nothing above the threshold: at least one OSV
+    assert sel(w, 1.0, 0, 0) == 1
+    assert sel(w, -1.0, 0, 0) == 7            # everything kept, the zero eigenvalue included
+    assert sel(w, -1.0, 4, 0) == 4
+    assert sel(w, 1e-4, 2, 6) == 6            # an exact count ignores threshold and cap
+    assert sel(w, 1e-4, 2, 99) == 7           # ... but cannot exceed the virtual space
+    # the rule counts eigenvalues, not leading positions: the oracle's spectra are sorted, so both agree there
+    ws = torch.sort(torch.tensor([3e-4, 2e-5, 8e-4, 1.5e-4, 9e-5], dtype=DT), descending=True).values
+    assert sel(ws, 1e-4, 0, 0) == 3
+
+
+# ------------------------------------------------------------------------------------- posterior step
+def _posterior_numpy(problem, out, ks, tau_red):
+    """Independent restatement of the one-step posterior correction in the canonical virtual space (numpy only).
+
+    With t_p = P_p T_p P_p^T (P_p the pair domain of the oracle's OSVs, T_p its collective amplitudes, zero where
+    a pair has none), Eq. 4 for the ordered pair ij over the LMOs k of ks[ij] is the projection onto range(P_ij) of
+        r_ij = (ia|jb) + eps t_ij + t_ij eps - sum_k (f_kj t_ik + f_ik t_kj).
+    In an orthonormal basis U_ij = Phi W of range(P_ij) that diagonalises eps (U^T eps U = diag(e)), the step is
+    dt_ij = -U [(U^T r_ij U) / (e_a + e_b - f_ii - f_jj)] U^T, and the pair functional (Eq. 3) is
+    sum_ij <(ia|jb) + r_ij, 2 t_ij - t_ij^T>."""
+    n, nv = problem.n_occ, problem.n_vir
+    Bd = [problem.B_dense(i) for i in range(n)]
+    f, eps = problem.f_occ, problem.eps_vir
+    Q = [q.numpy() for q in out["Q"]]
+    P = {}
+    for i in range(n):
+        for j in range(n):
+            P[(i, j)] = Q[i] if i == j else np.concatenate([Q[i], Q[j]], axis=1)
+    t = {p: P[p] @ T.numpy() @ P[p].T for p, T in out["collective"].items()}
+    zero = np.zeros((nv, nv))
+
+    def resid(tt, p):
+        i, j = p
+        r = Bd[i] @ Bd[j].T + eps[:, None] * tt[p] + tt[p] * eps[None, :]
+        for k in ks[p]:
+            r = r - f[k, j] * tt.get((i, k), zero) - f[i, k] * tt.get((k, j), zero)
+        return r
+
+    def functional(tt):
+        return sum(float(np.sum((Bd[p[0]] @ Bd[p[1]].T + resid(tt, p)) * (2.0 * tt[p] - tt[p].T))) for p in tt)
+
+    dt, rmax = {}, 0.0
+    for p in t:
+        i, j = p
+        u, s, _ = np.linalg.svd(P[p], full_matrices=False)
+        Phi = u[:, s * s > tau_red]                 # S = P^T P: its eigenvalues are the squared singular values
+        e, W = np.linalg.eigh(Phi.T @ (eps[:, None] * Phi))
+        U = Phi @ W
+        rho = U.T @ resid(t, p) @ U
+        rmax = max(rmax, float(np.linalg.norm(rho)))
+        dt[p] = -U @ (rho / (e[:, None] + e[None, :] - f[i, i] - f[j, j])) @ U.T
+    return functional(t), functional({p: t[p] + dt[p] for p in t}), rmax
+
+
+def _k_ranges(centres, r2b, r3b):
+    """For every ordered pair ij inside a selected cluster: the union of the LMOs of the clusters holding i and j
+    (pairs within r2b; triples whose three distances are within r3b), written from the distance rule."""
+    n = len(centres)
+    d = np.linalg.norm(centres[:, None, :] - centres[None, :, :], axis=-1)
+    cl = [{i} for i in range(n)] + [{i, j} for i, j in itertools.combinations(range(n), 2) if d[i, j] <= r2b]
+    cl += [{i, j, k} for i, j, k in itertools.combinations(range(n), 3)
+           if max(d[i, j], d[i, k], d[j, k]) <= min(r2b, r3b)]
+    out = {}
+    for i in range(n):
+        for j in range(n):
+            members = [c for c in cl if i in c and j in c]
+            if members:
+                out[(i, j)] = sorted(set().union(*members))
+    return out
+
+
+def test_posterior_correction_on_a_truncated_expansion():
+    """Truncated MBE(3) on six LMOs (Sec. 3): the collective amplitudes leave a residual over the k ranges of the
+    pairs' clusters.  The oracle's residual norm, global pair functional and corrected functional must equal the
+    numpy restatement above (a wrong sign, denominator, k range or transposed block in the oracle fails here).
+    The change made by the step is second order in the residual (one preconditioned step on a quadratic
+    functional): halving the off-diagonal Fock couplings scales the change like the squared residual norm.  With
+    every pair and triple kept, each pair's k range is all six LMOs, so the residual is that of the untruncated
+    OSV-MP2 equations: the global functional and then the corrected one come closer to the untruncated energy than
+    the MBE(3) energy (the higher-order estimate of Sec. 3)."""
+    base = make_problem(6, 16, 40, seed=3)
+    prm = Params(n_osv_fixed=4, mbe_order=3, r2b=6.0, r3b=5.0, tol=1e-12, max_iter=500)
+    rows = []
+    for lam in (1.0, 0.5, 0.25):
+        f = base.f_occ.copy()
+        off = ~np.eye(6, dtype=bool)
+        f[off] *= lam
+        q = Problem(**{**base.__dict__, "f_occ": f})
+        r = oracle.posterior_correction(q, prm)
+        out = oracle.energy(q, prm)
+        ks = _k_ranges(q.centres, prm.r2b, prm.r3b)
+        assert {p: r["k_sets"][p] for p in ks} == ks and set(r["k_sets"]) == set(ks)
+        Eg, Ec, rmax = _posterior_numpy(q, out, ks, prm.tau_red)
+        assert r["dR_max"] > 1e-8
+        assert abs(r["dR_max"] - rmax) <= 1e-9 * rmax
+        assert abs(r["E_global"] - Eg) <= 1e-11 * abs(Eg)
+        assert abs(r["E_corrected"] - Ec) <= 1e-11 * abs(Ec)
+        # the step's own energy change (~|dR|^2 / D, far below E): a wrong denominator or k range shows here
+        dEo, dEn = r["E_corrected"] - r["E_global"], Ec - Eg
+        assert abs(dEo - dEn) <= 5e-4 * abs(dEn) + 2e-16, (dEo, dEn)
+        rows.append((rmax, abs(r["E_corrected"] - r["E_global"])))
+    for (r0, d0), (r1, d1) in zip(rows, rows[1:]):
+        slope = np.log(d0 / d1) / np.log(r0 / r1)
+        assert 1.8 <= slope <= 2.2, rows
+    allk = Params(n_osv_fixed=4, mbe_order=3, r2b=99.0, r3b=99.0, tol=1e-12, max_iter=500)
+    r = oracle.posterior_correction(base, allk)
+    full = oracle.energy(base, Params(n_osv_fixed=4, mbe_order=0, tol=1e-12, max_iter=500))["E"]
+    assert all(ks == list(range(6)) for ks in r["k_sets"].values())
+    err = [abs(r[key] - full) for key in ("E", "E_global", "E_corrected")]
+    assert err[0] > 1e-8 and err[2] < err[1] < err[0], err
+    assert err[2] <= 1e-3 * err[0], err
