@@ -39,16 +39,20 @@ typedef enum {
 } osv_status;
 
 typedef enum {
-    OSV_FP64 = 0,          /* every contraction in FP64                                                    */
-    OSV_MIXED_TF32X3 = 1,  /* dense DF contractions (T_kk Gram, half transform, K blocks, adjoint products) in
-                              split TF32 (hi*hi + hi*lo + lo*hi) on tcgen05 tensor cores with FP32 accumulation
-                              in tensor memory; that accumulation is biased over long K (E error ~1e-5
-                              relative): the fast mode                                                     */
-    OSV_MIXED_BF16X4 = 2   /* the same contractions on tcgen05 with each FP64 operand cut into four signed
-                              8-bit integer slices (exact BF16) under per-row power-of-two scales, all sixteen
-                              slice products accumulated exactly per 128-K chunk: unbiased, ~31 significant
-                              bits.  Eigensolves, pair orthonormalisation, residual iterations, norms, energy
-                              and gradient accumulation stay FP64                                           */
+    OSV_FP64 = 0,          /* every step in FP64 on the CUDA cores                                         */
+    OSV_MIXED_TF32X3 = 1,  /* reserved, rejected with OSV_ERR_INVALID: split TF32 (hi*hi + hi*lo + lo*hi)
+                              with FP32 accumulation over the full K is biased (E error ~1e-5 relative) and
+                              misses the 1e-6 Eh bar                                                         */
+    OSV_MIXED_BF16X4 = 2   /* dense DF contractions (T_kk Gram, half transforms, K blocks and the adjoint's
+                              dense products) on tcgen05 tensor cores: each FP64 operand row gets a
+                              power-of-two scale, is rounded to 32 bits and cut into four signed 8-bit digits
+                              (exact BF16); the 13 digit products of order i + j <= 4 are accumulated in tensor
+                              memory per 256-K chunk (orders 0-2 exactly, orders 3-4 rounded below 2^-40 of the
+                              result) and drained into double-float sums: unbiased, ~31 significant bits of the
+                              row scales.  OSV and pair-basis eigensolves run in FP32 and are refined to FP64
+                              accuracy (Rayleigh-Ritz, double-float Jacobi polish); the residual iterates in
+                              FP32 with FP64-accurate (double-float) evaluations and corrections; norms, energy
+                              and gradient accumulation are FP64-accurate                                    */
 } osv_precision;
 
 /* Method parameters.  l_osv: OSV cut on the eigenvalues of T_kk (Sec. 2.1, Eq. 6).  r2b/r3b: distance
@@ -98,8 +102,10 @@ const char *osv_last_error(const osv_ctx *ctx);
 osv_status clusters_build(osv_ctx *ctx, const osv_problem *prob, const osv_params *params, int *n_clusters);
 
 /* Build orbital-specific virtuals and all pair quantities for the selected clusters (steps on the device):
- *   T_kk = (ka|kb) / (eps_a + eps_b - 2 f_kk), eigendecomposition in FP64, Q_k = eigenvectors of the n_k
- *   largest eigenvalues (Sec. 2.1, Eqs. 5-6; discarded eigenpairs are kept for the OSV relaxation);
+ *   T_kk = (ka|kb) / (eps_a + eps_b - 2 f_kk), eigenpairs to FP64 accuracy (FP64 tridiagonal route, or FP32
+ *   with FP64 Rayleigh-Ritz refinement in OSV_MIXED_BF16X4), Q_k = eigenvectors of the n_k largest eigenvalues
+ *   (Sec. 2.1, Eqs. 5-6; the discarded space enters the OSV relaxation of Eq. 8 only through the resolvent of
+ *   T_kk restricted to it, so its eigenvectors are never formed);
  *   S, F and K blocks A_(ij,kl) = (Q_i Q_j)^T A (Q_k Q_l) (Eq. 7) with K over the common fitting domain;
  *   per pair an orthonormal pseudo-canonical basis of (Q_i Q_j).
  * n_osv_out: HOST n_occ ints receiving n_k (may be NULL; non-NULL synchronises the stream). */
@@ -110,7 +116,7 @@ osv_status osv_build(osv_ctx *ctx, const osv_problem *prob, const osv_params *pa
  * n_iter_out: HOST int receiving the largest iteration count over clusters (may be NULL; non-NULL
  * synchronises).  cluster_status: DEVICE int32 per cluster (may be NULL): iterations used, or -1 where the
  * cluster did not converge.  Returns OSV_ERR_NOCONV (after a synchronisation) if any cluster did not
- * converge and n_iter_out is non-NULL. */
+ * converge and n_iter_out is non-NULL; otherwise the failure is reported by the next energy() call. */
 osv_status cluster_residual_solve(osv_ctx *ctx, int *n_iter_out, int32_t *cluster_status);
 
 /* Collective pair amplitudes T_(ij,ij) = sum over clusters c containing i, j of w_c T^c_(ij,ij)
@@ -119,7 +125,8 @@ osv_status mbe3_combine(osv_ctx *ctx);
 
 /* E = sum_c w_c E^c_Hylleraas (Eq. 3 per cluster, MBE-combined) into *E_out (HOST);
  * E_linear_out (HOST, may be NULL) = sum_ij <K_(ij,ij), 2T - T^T> with the collective amplitudes.
- * Synchronises the stream.  Returns OSV_ERR_NUMERIC if E is not finite. */
+ * Synchronises the stream.  Returns OSV_ERR_NOCONV if any cluster of the last cluster_residual_solve hit
+ * max_iter (E and E_linear are still written), OSV_ERR_NUMERIC if E is not finite. */
 osv_status energy(osv_ctx *ctx, double *E_out, double *E_linear_out);
 
 /* Adjoint of the energy (amplitudes are variational, Sec. 2.1): accumulate dE_scale * dE/dB into dE_dB
@@ -127,8 +134,17 @@ osv_status energy(osv_ctx *ctx, double *E_out, double *E_linear_out);
  * float64, entrywise derivative with F used as given).  Includes the OSV relaxation through the discarded
  * eigenvectors of T_kk (Sec. 2.1, Eq. 8) and the MBE(3) combination of the pair densities (Eqs. 33-34).
  * The buffers are added to (+=), not overwritten; either may be NULL to skip it.  Half-transformed
- * integrals are recomputed, not stored. */
+ * integrals are recomputed, not stored.  Synchronises the stream and returns OSV_ERR_TIMEOUT or
+ * OSV_ERR_NUMERIC if a device step of the build, the solve or the adjoint reported one. */
 osv_status gradient_backward(osv_ctx *ctx, double dE_scale, void *dE_dB, double *dE_dFocc);
+
+/* Failure detection (no counterpart in the paper): every wait of the tensor-core kernels on their pipeline
+ * barriers is bounded; when a wait runs out the kernel raises OSV_ERR_TIMEOUT in the context's error word, lets
+ * the work it already committed finish, frees its tensor memory and returns.  osv_set_wait_budget sets the bound
+ * of those waits for this context's later calls, in SM clock cycles (cycles <= 0 restores the default of 2^32,
+ * about two seconds).  A tiny budget makes the waits run out on purpose, which is how the timeout path is tested;
+ * results computed under an expired wait are meaningless and the call that reads the error word reports it. */
+osv_status osv_set_wait_budget(osv_ctx *ctx, long long cycles);
 
 /* Diagnostics (all synchronise; HOST outputs):
  *   osv_cluster_count: number of clusters (all orders).
@@ -138,6 +154,11 @@ osv_status gradient_backward(osv_ctx *ctx, double dE_scale, void *dE_dB, double 
 osv_status osv_cluster_count(osv_ctx *ctx, int *n_clusters);
 osv_status osv_cluster_info(osv_ctx *ctx, int32_t *members, int32_t *weight, double *energy, int32_t *iters);
 osv_status osv_eigenvalues(osv_ctx *ctx, int k, double *w_out);
+/* Collective amplitudes of the ordered pair (i, j) after mbe3_combine (Eqs. 28-32), in the canonical virtual
+ * space: t_out (HOST n_vir x n_vir) = (Q_i Q_j) T_(ij,ij) (Q_i Q_j)^T, rows indexed by the virtuals of i's
+ * side; t_ji = t_ij^T.  The pair must lie in a selected cluster (OSV_ERR_INVALID otherwise).  Formed on the
+ * host from the device's OSVs, pair basis and amplitudes (a diagnostic, not part of the hot path). */
+osv_status osv_pair_amplitudes(osv_ctx *ctx, int i, int j, double *t_out);
 
 /* Per-stage timing: osv_profile_enable(ctx, 1) clears previous records and makes every later call record a
  * pair of CUDA events around each of its stages on the context's stream; (ctx, 0) stops and clears.
@@ -191,8 +212,9 @@ osv_status osv_syev_batched(const double *A, int n, int batch, double *w, double
  *   - limits: batch <= 1024 and batch*n*n + 3*batch*n <= 1048576; larger requests return OSV_ERR_INVALID with
  *     the numbers in osv_last_error(NULL);
  *   - Zt doubles as the working matrix (A may equal Zt for an in-place call);
- *   - the first call on each device looks up the static array's device address (cudaGetSymbolAddress with that
- *     device current); make that first call before any stream capture;
+ *   - every call looks up the static array's device address (cudaGetSymbolAddress with the calling thread's
+ *     current device); the first call on each device also loads the library's device code there, so make that
+ *     first call before any stream capture;
  *   - every call shares the one static array (the error word is cleared on each call): calls that overlap on
  *     the GPU, from several host threads or streams, race and must be serialised by the caller.
  * Synchronises the stream. */

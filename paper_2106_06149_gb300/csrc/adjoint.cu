@@ -489,7 +489,7 @@ void AdjointPlan::release() {
         gemm_batch_free(*g);
         g->h.clear();
     }
-    for (TcTiles *t : {&tc_z, &tc_db, &tc_dq, &tc_gt, &tc_rb, &oz_z, &oz_db, &oz_dq, &oz_gt, &oz_rb}) tc_tiles_free(*t);
+    for (TcTiles *t : {&oz_z, &oz_db, &oz_dq, &oz_gt, &oz_rb}) tc_tiles_free(*t);
     bc_hs.h.clear();
     bc_hs.d = nullptr;
     planned = false;
@@ -733,9 +733,7 @@ cudaError_t AdjointPlan::plan(osv_ctx &c) {
     for (GemmBatch *g : {&gb_kc1, &gb_kc2, &gb_f1, &gb_f2, &gb_k1, &gb_k2, &gb_c1, &gb_c2, &gb_z, &gb_db, &gb_dq,
                          &gb_gt, &gb_rb, &gb_at})
         if ((e = gemm_batch_upload(*g)) != cudaSuccess) return e;
-    if ((e = tc_batch_prepare(gb_z, tc_z)) != cudaSuccess || (e = tc_batch_prepare(gb_db, tc_db)) != cudaSuccess ||
-        (e = tc_batch_prepare(gb_dq, tc_dq)) != cudaSuccess || (e = tc_batch_prepare(gb_gt, tc_gt)) != cudaSuccess ||
-        (e = tc_batch_prepare(gb_rb, tc_rb)) != cudaSuccess || (e = bf16x4_batch_prepare(gb_z, oz_z)) != cudaSuccess ||
+    if ((e = bf16x4_batch_prepare(gb_z, oz_z)) != cudaSuccess ||
         (e = bf16x4_batch_prepare(gb_db, oz_db)) != cudaSuccess || (e = bf16x4_batch_prepare(gb_dq, oz_dq)) != cudaSuccess ||
         (e = bf16x4_batch_prepare(gb_gt, oz_gt)) != cudaSuccess || (e = bf16x4_batch_prepare(gb_rb, oz_rb)) != cudaSuccess)
         return e;
@@ -797,7 +795,7 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
                           c.Stil, n, (int)c.cl.size(), ld, GS, GF, GSc, dF64, TbS, ebS};
         if (c.osv_mixed && !c.cl.empty() && 2 * nm <= kAdjTcMaxOrder && TbS && ebS) {
             // mixed modes, pair orders <= 80: exact BF16 slices on the tensor cores
-            CK(launch_cluster_adjoint_tc(as, (int)c.cl.size(), c.derr, s));
+            CK(launch_cluster_adjoint_tc(as, (int)c.cl.size(), c.derr, c.wait_budget, s));
         } else if (c.osv_mixed && !c.cl.empty() && sh <= 216 * 1024) {
             // mixed modes: double-float products on the FP32 pipe
             CK(cudaFuncSetAttribute(k_cluster_adjoint_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
@@ -818,9 +816,9 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
     }
     {
         StageTimer t(c, "adj_half_transform");
-        CK(c.run_dense(gb_z, tc_z, oz_z));
-        CK(c.run_dense(gb_db, tc_db, oz_db));
-        CK(c.run_dense(gb_dq, tc_dq, oz_dq));
+        CK(c.run_dense(gb_z, oz_z));
+        CK(c.run_dense(gb_db, oz_db));
+        CK(c.run_dense(gb_dq, oz_dq));
     }
     StageTimer trelax(c, "adj_osv_relax");
     // A1 = (omega_mu - T)^{-1} P_perp dE/dQ on the discarded space.  FP64: P_perp -> tridiagonal basis ->
@@ -836,14 +834,14 @@ cudaError_t AdjointPlan::run(osv_ctx &c, double scale, void *dB, double *dF, std
         CK(osv_project_out<double>(c.nosv, c.Ytri, A1, n, nv, nm, s));
         CK(osv_reflect<double>(c.tri_osv.d, n, nv, nm, c.nosv, A1, 0, s));
     }
-    CK(c.run_dense(gb_gt, tc_gt, oz_gt));
+    CK(c.run_dense(gb_gt, oz_gt));
     {
         const int bx = (int)std::min<long long>(((long long)nv * nv + kThreads - 1) / kThreads, 64);
         count_launch();
         k_relax_sym<<<dim3(bx, n), kThreads, 0, s>>>(c.Zc, c.Tkk, c.eps, c.focc, n, nv, dF64);
         CK(cudaGetLastError());
     }
-    CK(c.run_dense(gb_rb, tc_rb, oz_rb));
+    CK(c.run_dense(gb_rb, oz_rb));
     const long long nb = c.aux_ptr[n] * (long long)nv;
     if (dB) {
         const int blocks = (int)std::min<long long>((nb + 255) / 256, 152LL * 16);

@@ -31,7 +31,7 @@ struct AdjArgsS {
 // The same partials on the tensor cores (exact BF16 slices of every operand, tcgen05 with the sums in tensor
 // memory) for pair orders <= kAdjTcMaxOrder; err receives kDevTimeout if a bounded wait expires.
 constexpr int kAdjTcMaxOrder = 80;
-cudaError_t launch_cluster_adjoint_tc(const AdjArgsS &a, int ncl, int *err, cudaStream_t s);
+cudaError_t launch_cluster_adjoint_tc(const AdjArgsS &a, int ncl, int *err, long long budget, cudaStream_t s);
 
 struct AdjointPlan {
     bool planned = false;
@@ -53,7 +53,6 @@ struct AdjointPlan {
     } bc_hs;
     GemmBatch gb_kc1, gb_kc2, gb_f1, gb_f2, gb_k1, gb_k2, gb_c1, gb_c2, gb_z, gb_db, gb_dq, gb_gt, gb_rb;
     GemmBatch gb_at;                            // mixed relaxation: A1 T (FP64 residual of the resolvent solve)
-    TcTiles tc_z, tc_db, tc_dq, tc_gt, tc_rb;   // tensor-core tilings, TF32x3
     TcTiles oz_z, oz_db, oz_dq, oz_gt, oz_rb;   // tensor-core tilings, exact BF16x4
 
     void release();

@@ -81,6 +81,7 @@ struct Tc {
     uint32_t taddr;
     int *fail;
     unsigned long long *red;   // kTC / 32 words
+    long long budget;          // clock cycles of a product wait (<= 0: the default)
 };
 
 // largest |x| over the CTA (bit patterns), broadcast
@@ -125,7 +126,7 @@ __device__ bool run_mma(Tc &c, F issue, int *err) {
         issue(c);
         tc_commit(c.bar);
     }
-    const bool done = tc_wait(c.bar, c.phase);
+    const bool done = tc_wait(c.bar, c.phase, c.budget);
     if (done) c.phase ^= 1u;   // on expiry the pending phase is waited for once more before tensor memory is freed
     if (!done && threadIdx.x == 0) {
         raise_err(err, kDevTimeout);
@@ -153,7 +154,7 @@ __device__ __forceinline__ void read8(const Tc &c, uint32_t col, float *hi, floa
     }
 }
 
-__global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *err) {
+__global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *err, long long budget) {
     extern __shared__ __align__(16) unsigned char tc_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t s_bar;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    Tc c{{smem, smem + kImg, smem + 2 * kImg, smem + 3 * kImg}, &s_bar, 0u, s_taddr, &s_fail, s_red};
+    Tc c{{smem, smem + kImg, smem + 2 * kImg, smem + 3 * kImg}, &s_bar, 0u, s_taddr, &s_fail, s_red, budget};
     // tensor-memory reads: warp w reads lane quarter w & 3 (rows 32 (w & 3) + lane) and the 8-column chunks
     // w >> 2, w >> 2 + 4, ... of an 80-column accumulator
     const int row = (warp & 3) * 32 + lane, ch0 = warp >> 2;
@@ -452,12 +453,12 @@ __global__ void __launch_bounds__(kTC, 1) k_cluster_adjoint_tc(AdjArgsS A, int *
 
 }  // namespace
 
-cudaError_t launch_cluster_adjoint_tc(const AdjArgsS &a, int ncl, int *err, cudaStream_t s) {
+cudaError_t launch_cluster_adjoint_tc(const AdjArgsS &a, int ncl, int *err, long long budget, cudaStream_t s) {
     if (ncl <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_cluster_adjoint_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_cluster_adjoint_tc<<<std::min(ncl, 152), kTC, kSmem, s>>>(a, err);
+    k_cluster_adjoint_tc<<<std::min(ncl, 152), kTC, kSmem, s>>>(a, err, budget);
     return cudaGetLastError();
 }
 

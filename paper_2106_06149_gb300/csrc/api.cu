@@ -33,7 +33,10 @@ osv_status check_params(osv_ctx *c, const osv_params *p) {
     if (p->mbe_order < 0 || p->mbe_order > 3) return c->fail(OSV_ERR_INVALID, "mbe_order must be 0..3");
     if (!(p->tau_red >= 0.0) || !(p->r2b >= 0.0) || !(p->r3b >= 0.0) || !std::isfinite(p->l_osv))
         return c->fail(OSV_ERR_INVALID, "tau_red, r2b, r3b must be >= 0 and l_osv finite");
-    if (p->precision != OSV_FP64 && p->precision != OSV_MIXED_TF32X3 && p->precision != OSV_MIXED_BF16X4)
+    if (p->precision == OSV_MIXED_TF32X3)
+        return c->fail(OSV_ERR_INVALID, "OSV_MIXED_TF32X3 is reserved: split TF32 with FP32 accumulation misses the "
+                                        "1e-6 Eh bar; use OSV_MIXED_BF16X4");
+    if (p->precision != OSV_FP64 && p->precision != OSV_MIXED_BF16X4)
         return c->fail(OSV_ERR_INVALID, "unknown precision");
     return OSV_OK;
 }
@@ -473,7 +476,9 @@ osv_status build_plan(osv_ctx *c) {
         ALLOC(r.AT, blk);
         ALLOC(r.RS, blk);
         ALLOC(r.nm_all, n);
-        ALLOC(r.Twy, (long long)osv_wy_floats(n, nv));
+        // compact-WY factors only where the blocked reflector product fits shared memory (n_vir up to ~1700);
+        // larger orders apply the reflectors one by one
+        if (osv_reflect_wy_fits(nv)) ALLOC(r.Twy, (long long)osv_wy_floats(n, nv));
         std::vector<int> all(n, nm);
         if ((e = cudaMemcpy(r.nm_all, all.data(), n * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
             return c->cuda_fail(e, "upload n_max");
@@ -669,8 +674,7 @@ osv_status build_plan(osv_ctx *c) {
         for (int x = 0; x < 2; ++x)
             for (GemmBatch *g : {&c->refine.gb_w[x], &c->refine.gb_gh[x], &c->refine.gb_rot[x], &c->refine.gb_fin[x]})
                 if ((e = gemm_batch_upload(*g)) != cudaSuccess) return c->cuda_fail(e, "upload refine batch");
-    if ((e = tc_batch_prepare(c->gb_gram, c->tc_gram)) != cudaSuccess || (e = tc_batch_prepare(c->gb_w, c->tc_w)) != cudaSuccess ||
-        (e = tc_batch_prepare(c->gb_k, c->tc_k)) != cudaSuccess || (e = bf16x4_batch_prepare(c->gb_gram, c->oz_gram)) != cudaSuccess ||
+    if ((e = bf16x4_batch_prepare(c->gb_gram, c->oz_gram)) != cudaSuccess ||
         (e = bf16x4_batch_prepare(c->gb_w, c->oz_w)) != cudaSuccess || (e = bf16x4_batch_prepare(c->gb_k, c->oz_k)) != cudaSuccess)
         return c->cuda_fail(e, "tensor-core tiling");
     if (c->prm.precision == OSV_MIXED_BF16X4 &&
@@ -695,7 +699,7 @@ osv_status run_osv_build(osv_ctx *c) {
     }
     {
         StageTimer t(*c, "tkk_gram");
-        CK(c->run_dense(c->gb_gram, c->tc_gram, c->oz_gram), "gram");
+        CK(c->run_dense(c->gb_gram, c->oz_gram), "gram");
         if (c->osv_mixed) {
             CK(launch_tkk_scale<float>(c->Tkk, c->refine.A32, c->eps, c->focc, n, nv, c->derr, s), "tkk");
         } else {
@@ -725,11 +729,11 @@ osv_status run_osv_build(osv_ctx *c) {
     }
     {
         StageTimer t(*c, "half_transform");
-        CK(c->run_dense(c->gb_w, c->tc_w, c->oz_w), "half transform");
+        CK(c->run_dense(c->gb_w, c->oz_w), "half transform");
     }
     {
         StageTimer t(*c, "k_blocks");
-        CK(c->run_dense(c->gb_k, c->tc_k, c->oz_k), "K blocks");
+        CK(c->run_dense(c->gb_k, c->oz_k), "K blocks");
     }
     {
         StageTimer t(*c, "pair_basis");
@@ -878,6 +882,7 @@ osv_status cluster_residual_solve(osv_ctx *c, int *n_iter_out, int32_t *cluster_
             return c->cuda_fail(e, "status copy");
     }
     c->solved = true;
+    c->combined = false;
     if (n_iter_out) {
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "residual");
         osv_status st = device_error(c);
@@ -905,6 +910,53 @@ osv_status mbe3_combine(osv_ctx *c) {
     cudaError_t e = launch_combine(c->pinfo.d, (int)c->pairs.size(), c->comb_ptr.d, c->comb_src.d, c->comb_w.d,
                                    c->Tslot, c->Tc, c->stream);
     if (e != cudaSuccess) return c->cuda_fail(e, "combine");
+    c->combined = true;
+    return OSV_OK;
+}
+
+osv_status osv_pair_amplitudes(osv_ctx *c, int i, int j, double *t_out) {
+    if (!c || !t_out) return OSV_ERR_INVALID;
+    if (!c->combined) return c->fail(OSV_ERR_INVALID, "mbe3_combine must precede osv_pair_amplitudes");
+    if (i < 0 || j < 0 || i >= c->n_occ || j >= c->n_occ) return c->fail(OSV_ERR_INVALID, "LMO index out of range");
+    const int p = c->pid(i, j);
+    if (p < 0) return c->fail(OSV_ERR_INVALID, "the pair belongs to no selected cluster");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "sync");
+    const PairInfo &P = c->pinfo.h[p];
+    const int nv = c->n_vir, nm = c->nmax, np = P.np;
+    const int dom[2] = {P.i, P.j};
+    const int nd = P.i == P.j ? 1 : 2;
+    // domain rows (OSVs of the pair's LMOs; rows beyond n_k are zero), basis V (columns) and collective T~
+    std::vector<double> Pr((size_t)np * nv), V((size_t)np * np), T((size_t)np * np);
+    for (int x = 0; x < nd; ++x)
+        if ((e = cudaMemcpy(Pr.data() + (size_t)x * nm * nv, c->Q + (long long)dom[x] * nm * nv,
+                            (size_t)nm * nv * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return c->cuda_fail(e, "copy Q");
+    if ((e = cudaMemcpy(V.data(), c->V + P.off, V.size() * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(T.data(), c->Tc + P.off, T.size() * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy pair");
+    // U = V^T P (np x nv): the orthonormal pair basis in the virtual space; t = U^T T~ U
+    std::vector<double> U((size_t)np * nv, 0.0), TU((size_t)np * nv, 0.0);
+    for (int a = 0; a < np; ++a)
+        for (int r = 0; r < np; ++r) {
+            const double v = V[(size_t)r * np + a];
+            if (v == 0.0) continue;
+            for (int x = 0; x < nv; ++x) U[(size_t)a * nv + x] += v * Pr[(size_t)r * nv + x];
+        }
+    for (int a = 0; a < np; ++a)
+        for (int b = 0; b < np; ++b) {
+            const double v = T[(size_t)a * np + b];
+            if (v == 0.0) continue;
+            for (int x = 0; x < nv; ++x) TU[(size_t)a * nv + x] += v * U[(size_t)b * nv + x];
+        }
+    const bool swap = i > j;   // stored pair (j, i): t_ij = t_ji^T
+    for (int x = 0; x < nv; ++x)
+        for (int y = 0; y < nv; ++y) {
+            double acc = 0.0;
+            for (int a = 0; a < np; ++a) acc += U[(size_t)a * nv + x] * TU[(size_t)a * nv + y];
+            t_out[swap ? (size_t)y * nv + x : (size_t)x * nv + y] = acc;
+        }
     return OSV_OK;
 }
 
@@ -928,6 +980,12 @@ osv_status energy(osv_ctx *c, double *E_out, double *E_linear_out) {
     *E_out = h[0];
     if (E_linear_out) *E_linear_out = h[1];
     if (!std::isfinite(h[0])) return c->fail(OSV_ERR_NUMERIC, "energy is not finite");
+    // clusters that hit max_iter carry iters = -1 (whether or not cluster_residual_solve was asked to check)
+    std::vector<int> it(c->cl.size());
+    if ((e = cudaMemcpy(it.data(), c->iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "iters");
+    const long long bad = std::count_if(it.begin(), it.end(), [](int v) { return v < 0; });
+    if (bad) return c->fail(OSV_ERR_NOCONV, std::to_string(bad) + " clusters did not converge within max_iter");
     return OSV_OK;
 }
 
@@ -993,6 +1051,14 @@ osv_status gradient_backward(osv_ctx *c, double dE_scale, void *dE_dB, double *d
     std::string msg;
     cudaError_t e = c->adj.run(*c, dE_scale, dE_dB, dE_dFocc, msg);
     if (e != cudaSuccess) return c->cuda_fail(e, msg.c_str());
+    // a bounded wait that gave up, or a non-finite value, leaves its mark in the device error word
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "gradient_backward");
+    return device_error(c);
+}
+
+osv_status osv_set_wait_budget(osv_ctx *c, long long cycles) {
+    if (!c) return OSV_ERR_INVALID;
+    c->wait_budget = cycles > 0 ? cycles : 0;
     return OSV_OK;
 }
 

@@ -51,7 +51,7 @@ struct osv_ctx {
     const double *B64 = nullptr;   // fp64 DF blocks (caller's buffer or the internal copy)
 
     // clusters (host)
-    bool have_clusters = false, built = false, solved = false;
+    bool have_clusters = false, built = false, solved = false, combined = false;
     std::vector<std::vector<int>> cl;
     std::vector<int> cl_w;
     int ncl_order[3] = {0, 0, 0};
@@ -103,10 +103,10 @@ struct osv_ctx {
     HostDev<int> rows_w;                   // a_rows maps for the half transforms
     HostDev<int> kidx;                     // common-fitting-domain position lists
     GemmBatch gb_gram, gb_sf, gb_w, gb_k, gb_fx1, gb_fx2, gb_v, gb_kt1, gb_kt2, gb_c1, gb_c2;
-    osv::TcTiles tc_gram, tc_w, tc_k;          // tensor-core tilings of the dense DF contractions (TF32x3)
     osv::TcTiles oz_gram, oz_w, oz_k;          // exact-slice BF16x4 tilings
 
     osv::AdjointPlan adj;
+    long long wait_budget = 0;             // tensor-core main-loop wait budget in clock cycles (0 = default)
 
     // per-stage CUDA-event profiling (osv_profile_enable / osv_profile_read)
     bool prof = false;
@@ -139,11 +139,9 @@ struct osv_ctx {
         if (e == cudaSuccess) allocs.push_back((void *)p);
         return e;
     }
-    // dense DF contractions: FP64 CUDA cores, split TF32 (biased FP32 accumulation) or exact BF16 slices on the
-    // tcgen05 tensor cores
-    cudaError_t run_dense(const GemmBatch &b, const osv::TcTiles &t, const osv::TcTiles &oz) {
-        if (prm.precision == OSV_MIXED_TF32X3) return osv::tc_batch_run(b, t, derr, stream);
-        if (prm.precision == OSV_MIXED_BF16X4) return osv::bf16x4_batch_run(oz, oz_scratch, derr, stream);
+    // dense DF contractions: FP64 CUDA cores or exact BF16 slices on the tcgen05 tensor cores
+    cudaError_t run_dense(const GemmBatch &b, const osv::TcTiles &oz) {
+        if (prm.precision == OSV_MIXED_BF16X4) return osv::bf16x4_batch_run(oz, oz_scratch, derr, wait_budget, stream);
         return osv::gemm_batch_run(b, stream);
     }
     // the small FP64-accurate GEMM batches (pair and refinement blocks): FP64 CUDA cores, or double-float on the
@@ -189,9 +187,9 @@ struct osv_ctx {
         if (oz_scratch) cudaFree(oz_scratch);
         oz_scratch = nullptr;
         oz_cap = 0;
-        for (osv::TcTiles *t : {&tc_gram, &tc_w, &tc_k, &oz_gram, &oz_w, &oz_k}) osv::tc_tiles_free(*t);
+        for (osv::TcTiles *t : {&oz_gram, &oz_w, &oz_k}) osv::tc_tiles_free(*t);
         adj.release();
-        built = solved = false;
+        built = solved = combined = false;
     }
     int pid(int i, int j) const {
         auto it = pair_id.find((long long)std::min(i, j) * n_occ + std::max(i, j));

@@ -4,7 +4,6 @@
 // pool), and latency-sensitive callers that cannot afford the implicit device-wide synchronisation of
 // cudaFree.  Its scratch lives in file-scope __device__ arrays that every GPU loading this library holds until
 // the process exits.
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -20,39 +19,25 @@ namespace {
 // Scratch: eigenvector accumulation (batch * n * n) and the tridiagonal vectors (3 * batch * n), in doubles.
 constexpr long long kScratchDoubles = 1LL << 20;   // 8 MiB per device
 constexpr int kMaxBatch = 1024;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 static __device__ __align__(256) osv::EighDesc g_desc[kMaxBatch];
 static __device__ __align__(256) int g_err[64];
 
 struct DeviceAddrs {
-    bool ready = false;
     double *scratch = nullptr;
     osv::EighDesc *desc = nullptr;
     int *err = nullptr;
 };
 
-std::mutex g_mu;
-DeviceAddrs g_addrs[kMaxDevices];
-
-// Device addresses of the static arrays for the current device (looked up once per device).  In host code
-// the names g_scratch / g_desc / g_err are host-side stand-ins, never device addresses.
-cudaError_t device_addrs(DeviceAddrs &out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    DeviceAddrs &a = g_addrs[dev];
-    if (!a.ready) {
-        if ((e = cudaGetSymbolAddress((void **)&a.scratch, g_scratch)) != cudaSuccess) return e;
-        if ((e = cudaGetSymbolAddress((void **)&a.desc, g_desc)) != cudaSuccess) return e;
-        if ((e = cudaGetSymbolAddress((void **)&a.err, g_err)) != cudaSuccess) return e;
-        a.ready = true;
-    }
-    out = a;
-    return cudaSuccess;
+// Device addresses of the static arrays for the current device, looked up on every call: a cached address would
+// go stale if the caller tears the primary context down (cudaDeviceReset) and a later call runs in a new one.  In
+// host code the names g_scratch / g_desc / g_err are host-side stand-ins, never device addresses.
+cudaError_t device_addrs(DeviceAddrs &a) {
+    cudaError_t e;
+    if ((e = cudaGetSymbolAddress((void **)&a.scratch, g_scratch)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&a.desc, g_desc)) != cudaSuccess) return e;
+    return cudaGetSymbolAddress((void **)&a.err, g_err);
 }
 
 }  // namespace

@@ -48,8 +48,11 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// wait for the given phase parity of bar, bounded: false when the budget ran out
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
+// wait for the given phase parity of bar, bounded by `budget` clock cycles (<= 0: kTcWaitBudget): false when the
+// budget ran out.  Main-loop waits take the caller's budget; the tear-down waits for work already committed (MMAs
+// and copies that complete on their own) always take the full kTcWaitBudget.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, long long budget = kTcWaitBudget) {
+    if (budget <= 0) budget = kTcWaitBudget;
     const long long t0 = clock64();
     uint32_t done = 0;
     while (true) {
@@ -60,7 +63,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
             : "r"(smem_u32(bar)), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > kTcWaitBudget) return false;
+        if (clock64() - t0 > budget) return false;
     }
 }
 

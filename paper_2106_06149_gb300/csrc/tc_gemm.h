@@ -1,12 +1,14 @@
-// Grouped split-TF32 GEMM on tcgen05 tensor cores (same GemmDesc batches as the FP64 grouped GEMM).
+// Grouped exact-slice GEMM on tcgen05 tensor cores (tc_oz.cu): tilings of the same GemmDesc batches as the FP64
+// grouped GEMM.
 #pragma once
+#include <vector>
+
 #include "kernels.cuh"
 
 namespace osv {
 
 struct TcTiles {
-    long long *d_tile0 = nullptr;
-    long long tiles = 0;
+    long long tiles = 0;          // output tiles of the GEMM launch
     GemmDesc *d_desc = nullptr;   // exact-slice GEMM: descriptors with scale arrays attached
     int *d_exps = nullptr;
     int nprob = 0;
@@ -18,18 +20,16 @@ struct TcTiles {
     void *d_jobs = nullptr, *d_otiles = nullptr, *d_rows = nullptr;
     int nops = 0;
     long long packed_tiles = 0;                         // output tiles whose rows come from several problems
+    std::vector<TcTiles> parts;                         // non-empty: the batch runs as these consecutive parts
 };
 
-// per-problem 128 x 64 tile offsets of an uploaded batch
-cudaError_t tc_batch_prepare(GemmBatch &b, TcTiles &tt);
-// err: device int set to kDevTimeout if a bounded mbarrier wait expires
-cudaError_t tc_batch_run(const GemmBatch &b, const TcTiles &tt, int *err, cudaStream_t s);
 void tc_tiles_free(TcTiles &tt);
 
 // Exact-slice BF16x4 GEMM (unbiased, ~31 significant bits, tc_oz.cu): 128 x 128 tiling, per-row scale arrays,
 // operands pre-sliced into scratch (tt.scratch_bytes, 16-byte aligned, shared by batches run one after another).
 // Problems of fewer than 128 rows that read the same B operand share output tiles (row packing).
 cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt);
-cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err, cudaStream_t s);
+// budget: clock cycles of each main-loop wait before the tile gives up and raises kDevTimeout (<= 0: the default)
+cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err, long long budget, cudaStream_t s);
 
 }  // namespace osv

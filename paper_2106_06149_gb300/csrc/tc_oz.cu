@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(NT) k_oz_slice(const OzOperand *__restrict__ o
 
 __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ descs, const OzTile *__restrict__ tiles,
                                                   const OzRow *__restrict__ rows,
-                                                  const unsigned char *__restrict__ scratch, int *err) {
+                                                  const unsigned char *__restrict__ scratch, int *err, long long budget) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[NSTAGE], empty[NSTAGE], dbar;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
             const int jend = min(nkt, kt1 + NSTAGE - 1);
             while (loaded < jend && !*fail) {
                 const int j = loaded;
-                if (j >= NSTAGE && !tc_wait(&empty[j % NSTAGE], (uint32_t)((j / NSTAGE - 1) & 1))) {
+                if (j >= NSTAGE && !tc_wait(&empty[j % NSTAGE], (uint32_t)((j / NSTAGE - 1) & 1), budget)) {
                     raise_err(err, kDevTimeout);
                     *fail = 1;
                     break;
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         } else if (tid == 0) {
             for (int kt = kt0; kt < kt1 && !*fail; ++kt) {
                 const int st = kt % NSTAGE;
-                if (!tc_wait(&full[st], (uint32_t)((kt / NSTAGE) & 1))) {
+                if (!tc_wait(&full[st], (uint32_t)((kt / NSTAGE) & 1), budget)) {
                     raise_err(err, kDevTimeout);
                     *fail = 1;
                     break;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
         }
         __syncthreads();
         if (*fail) { ok = false; break; }
-        if (!tc_wait(&dbar, (uint32_t)(chunk & 1))) {
+        if (!tc_wait(&dbar, (uint32_t)(chunk & 1), budget)) {
             raise_err(err, kDevTimeout);
             *fail = 1;
         }
@@ -556,10 +556,22 @@ __global__ void __launch_bounds__(NT, 1) k_oz_gemm(const GemmDesc *__restrict__ 
 
 }  // namespace
 
-cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
-    tc_tiles_free(tt);
-    if (b.h.empty()) return cudaSuccess;
-    std::vector<GemmDesc> h = b.h;
+void tc_tiles_free(TcTiles &tt) {
+    for (TcTiles &p : tt.parts) tc_tiles_free(p);
+    if (tt.d_desc) cudaFree(tt.d_desc);
+    if (tt.d_exps) cudaFree(tt.d_exps);
+    if (tt.d_jobs) cudaFree(tt.d_jobs);
+    if (tt.d_otiles) cudaFree(tt.d_otiles);
+    if (tt.d_rows) cudaFree(tt.d_rows);
+    if (tt.d_sjobs0) cudaFree(tt.d_sjobs0);
+    if (tt.d_ops) cudaFree(tt.d_ops);
+    tt = TcTiles{};
+}
+
+namespace {
+
+// One launch group: the problems h (a consecutive range of a batch), their operands, slicing jobs and tiles.
+cudaError_t prepare_part(std::vector<GemmDesc> h, TcTiles &tt) {
     // distinct operands (A of every problem, B of every problem), identified by pointer, layout, maps and sizes
     struct Key {
         const double *ptr;
@@ -704,7 +716,63 @@ cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
     return e;
 }
 
-cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err, cudaStream_t s) {
+// Slice-image bytes of one problem's operands on their own (an upper bound: problems of a part may share them).
+long long problem_image_bytes(const GemmDesc &g) {
+    if (g.M <= 0 || g.N <= 0) return 0;
+    const long long nkp = padded_nkt(g.K);
+    return ((long long)(g.M + BM - 1) / BM + (g.N + BN - 1) / BN) * nkp * TILE_BYTES;
+}
+
+cudaError_t run_part(const TcTiles &tt, unsigned char *scratch, int *err, long long budget, cudaStream_t s);
+
+}  // namespace
+
+// Batches whose slice images exceed kOzPartBytes run as consecutive parts (ranges of problems, in batch order),
+// each sliced into the same scratch after the previous part's GEMM: the scratch is bounded by the largest part
+// instead of growing with the batch (the relaxation products at n_vir = 3000 would need ~60 GB at once).
+constexpr long long kOzPartBytes = 8LL << 30;
+
+cudaError_t bf16x4_batch_prepare(GemmBatch &b, TcTiles &tt) {
+    tc_tiles_free(tt);
+    if (b.h.empty()) return cudaSuccess;
+    std::vector<std::pair<size_t, size_t>> ranges;
+    size_t first = 0;
+    long long acc = 0;
+    for (size_t i = 0; i < b.h.size(); ++i) {
+        const long long x = problem_image_bytes(b.h[i]);
+        if (i > first && acc + x > kOzPartBytes) {
+            ranges.push_back({first, i});
+            first = i;
+            acc = 0;
+        }
+        acc += x;
+    }
+    ranges.push_back({first, b.h.size()});
+    if (ranges.size() == 1) return prepare_part(b.h, tt);
+    tt.parts.resize(ranges.size());
+    for (size_t q = 0; q < ranges.size(); ++q) {
+        std::vector<GemmDesc> h(b.h.begin() + ranges[q].first, b.h.begin() + ranges[q].second);
+        cudaError_t e = prepare_part(h, tt.parts[q]);
+        if (e != cudaSuccess) return e;
+        tt.scratch_bytes = std::max(tt.scratch_bytes, tt.parts[q].scratch_bytes);
+        tt.tiles += tt.parts[q].tiles;
+        tt.packed_tiles += tt.parts[q].packed_tiles;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err, long long budget, cudaStream_t s) {
+    if (tt.parts.empty()) return run_part(tt, scratch, err, budget, s);
+    for (const TcTiles &p : tt.parts) {
+        cudaError_t e = run_part(p, scratch, err, budget, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+namespace {
+
+cudaError_t run_part(const TcTiles &tt, unsigned char *scratch, int *err, long long budget, cudaStream_t s) {
     if (tt.tiles == 0) return cudaSuccess;
     if (!scratch) return cudaErrorInvalidValue;
     static bool attr = false;
@@ -727,8 +795,11 @@ cudaError_t bf16x4_batch_run(const TcTiles &tt, unsigned char *scratch, int *err
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     count_launch();
-    k_oz_gemm<<<(unsigned)tt.tiles, NT, SMEM, s>>>(tt.d_desc, static_cast<const OzTile *>(tt.d_otiles), rows, scratch, err);
+    k_oz_gemm<<<(unsigned)tt.tiles, NT, SMEM, s>>>(tt.d_desc, static_cast<const OzTile *>(tt.d_otiles), rows, scratch, err,
+                                                   budget);
     return cudaGetLastError();
 }
+
+}  // namespace
 
 }  // namespace osv

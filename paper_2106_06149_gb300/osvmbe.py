@@ -22,7 +22,8 @@ EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv
            "mbe3_combine", "energy", "gradient_backward", "osv_cluster_count", "osv_cluster_info",
            "osv_eigenvalues", "osv_syev_batched", "osv_profile_enable", "osv_profile_read",
            "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops",
-           "osv_solve_counts", "osv_residual_work"]
+           "osv_solve_counts", "osv_residual_work", "osv_set_wait_budget",
+           "osv_pair_amplitudes"]
 
 
 class OsvParams(ctypes.Structure):
@@ -73,6 +74,8 @@ def load(path=LIB_PATH):
         "osv_adjoint_flops": ([V, P(D)], I),
         "osv_solve_counts": ([V, P(ctypes.c_longlong), P(ctypes.c_longlong), P(I)], I),
         "osv_residual_work": ([V, P(D), P(D)], I),
+        "osv_set_wait_budget": ([V, ctypes.c_longlong], I),
+        "osv_pair_amplitudes": ([V, I, I, V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +221,10 @@ class Context:
         _check(load().gradient_backward(self.h, float(scale), _ptr(dB) if dB is not None else None,
                                         _ptr(dF) if dF is not None else None), self.h)
 
+    def set_wait_budget(self, cycles):
+        """Bound (SM clock cycles) of the tensor-core kernels' pipeline waits; <= 0 restores the default."""
+        _check(load().osv_set_wait_budget(self.h, int(cycles)), self.h)
+
     # --- diagnostics
     def cluster_info(self):
         n = ctypes.c_int()
@@ -265,6 +272,12 @@ class Context:
         f32, f64 = ctypes.c_double(), ctypes.c_double()
         _check(load().osv_residual_work(self.h, ctypes.byref(f32), ctypes.byref(f64)), self.h)
         return f32.value, f64.value
+
+    def pair_amplitudes(self, i, j, n_vir):
+        """Collective amplitudes t_ij of the ordered pair (i, j) in the canonical virtual space (n_vir x n_vir)."""
+        out = np.zeros((n_vir, n_vir), np.float64)
+        _check(load().osv_pair_amplitudes(self.h, int(i), int(j), _ptr(out)), self.h)
+        return out
 
     def eigenvalues(self, k, n_vir):
         out = np.zeros(n_vir, np.float64)

@@ -34,7 +34,7 @@ class Params:
     tau_red: float = 1e-8     # drop pair-overlap eigenvalues below this (redundant pair space)
     tol: float = 1e-8         # residual convergence: max_ij ||R~_ij||_F <= tol
     max_iter: int = 100       # residual iteration cap
-    precision: int = 0        # 0 = FP64, 1 = split-TF32 tensor-core GEMMs, 2 = exact BF16x4 tensor-core GEMMs
+    precision: int = 0        # 0 = FP64, 2 = exact BF16x4 tensor-core GEMMs (1, split TF32, is rejected)
 
     def as_dict(self):
         return dataclasses.asdict(self)

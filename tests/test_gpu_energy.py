@@ -139,3 +139,25 @@ def test_invalid_inputs_are_rejected(osvmbe):
     assert ei.value.status == osvmbe.OSV_ERR_INVALID
     with pytest.raises(osvmbe.OsvError):
         ctx.cluster_residual_solve()
+
+
+def test_collective_amplitudes_and_linear_energy_match_oracle(osvmbe):
+    """mbe3_combine (Eqs. 28-32) on a truncated MBE(3) case, where the cluster weights are not trivial: for every
+    ordered pair of a selected cluster, the collective amplitudes in the canonical virtual space,
+    t_ij = (Q_i Q_j) T_(ij,ij) (Q_i Q_j)^T (independent of the OSV signs and of the pair basis), equal the
+    oracle's; and E_linear = sum_ij <K_(ij,ij), 2T - T^T> over the collective amplitudes equals the oracle's.  A
+    wrong weight, sign or pair index in the combination fails here even where the total energy would not."""
+    p = make_problem(7, 18, 40, seed=12)
+    prm = Params(n_osv_fixed=5, mbe_order=3, r2b=5.0, r3b=3.5, tol=1e-12, max_iter=400)
+    g = gpu_run(osvmbe, p, prm)
+    o = oracle.energy(p, prm)
+    assert sorted(set(o["weights"].values())) != [1]          # truncated: some weights differ from one
+    assert abs(g["E_linear"] - o["E_linear"]) <= 1e-9, (g["E_linear"], o["E_linear"])
+    worst = 0.0
+    for (i, j), T in o["collective"].items():
+        P = torch.cat([o["Q"][i], o["Q"][j]], dim=1) if i != j else o["Q"][i]
+        t_ref = (P @ T @ P.T).numpy()
+        t_gpu = g["ctx"].pair_amplitudes(i, j, p.n_vir)
+        worst = max(worst, float(np.abs(t_gpu - t_ref).max()))
+        assert np.abs(t_gpu - t_ref).max() <= 1e-10 * max(1.0, np.abs(t_ref).max()), (i, j)
+    print(f"\nmax |t_gpu - t_oracle| over {len(o['collective'])} ordered pairs: {worst:.2e}")
