@@ -2,9 +2,10 @@
 //
 // Only the n_k kept eigenvectors of T_kk enter the energy, and the OSV relaxation of Eq. 8 needs the discarded
 // eigenvectors only through the restricted resolvent sum_nu q'_nu q'_nu^T / (omega_mu - omega'_nu).  So:
-//   1. Householder tridiagonalisation T = H Tri H^T (one CTA per LMO; reflector k kept contiguous in row k).
-//      One pass over the trailing matrix per step: the rank-2 update of step k-1 is applied lazily in the same
-//      pass that forms the product A v_k of step k (warp per row, coalesced, division free);
+//   1. Householder tridiagonalisation T = H Tri H^T (one CTA per LMO, or a pair of CTAs in FP32; reflector k
+//      kept contiguous in row k).  One pass over the lower triangle of the trailing matrix per step: the rank-2
+//      update of step k-1 is applied lazily in the same pass that forms the product A v_k of step k from the row
+//      and column sums of the stored triangle (warp per row, coalesced, division free);
 //   2. the n_max largest eigenvalues of Tri by 32-point multisection of the Sturm count (one warp per
 //      eigenvalue, FP64 arithmetic): ~11 rounds instead of ~60 bisection steps, each a chain of n dependent
 //      multiply-adds (on GB300 a dependent FP64 operation costs ~64 cycles and a division ~430);
@@ -57,11 +58,16 @@ __device__ __forceinline__ R warp_sum_t(R v) {
 }
 
 // ---------------------------------------------------------------------- 1. Householder tridiagonalisation
-// A (n x n, lda, both triangles stored) overwritten; d, e (n), tau (n); reflector k stored in row k, columns
-// k+1 .. n-1 (H_k = I - tau_k v v^T).  Step k: (a) warp 0 applies the pending update of step k-1 to row k and
-// forms v_k from it; (b) one pass over rows r > k applies the pending update and accumulates p = tau A v_k;
-// (c) p -= (tau/2)(p.v) v; (v_k, p) become the pending update A <- A - v p^T - p v^T.  Below-diagonal column k
-// is not updated (it is never read again).
+// A (n x n, lda; both triangles stored on input) overwritten; d, e (n), tau (n); reflector k stored in row k,
+// columns k+1 .. n-1 (H_k = I - tau_k v v^T).  Only the lower triangle of the trailing matrix is read and written:
+// the symmetric product A v takes every below-diagonal element twice, for its row sum (p_r) and for its column
+// sum (p_c), which halves the memory traffic of the reduction.  Step k: (a) warp 0 of the owner of row k applies
+// the pending update of step k-1 to column k of the trailing matrix (stashed by the previous pass; row 0 read
+// directly at step 0) and forms v_k from it; (b) one pass over rows r > k, columns k+1 .. r, applies the pending
+// update, accumulates the row sums of A v_k and scatters the column sums (one shared-memory add per column and
+// group of four rows), and stashes column k+1; (c) p = tau (row + column sums), p -= (tau/2)(p.v) v; (v_k, p)
+// become the pending update A <- A - v p^T - p v^T.  The upper part of row k holds the reflector: no later step
+// reads it.
 template <class R, int CL>
 __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__ descs) {
     static_assert(CL == 1 || CL == 2, "one CTA or a pair of CTAs per matrix");
@@ -71,7 +77,9 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int ns = (n + 3) & ~3;   // vector stride: 16-byte aligned starts
     R *v = reinterpret_cast<R *>(smem_raw), *p = v + ns, *vo = p + ns, *po = vo + ns;   // global indices
-    R *nx = po + ns;   // row k + 1 as pass (b) of step k leaves it (read by step k + 1 instead of global memory)
+    R *nx = po + ns;   // column k + 1 of the trailing matrix as pass (b) of step k leaves it (rows >= k + 1)
+    R *cs = nx + ns;   // column sums of A v over this CTA's rows
+    R *cq = cs + ns;   // (pair of CTAs) the peer's column sums for this CTA's rows
     __shared__ R part[kTT / 32];   // in the working precision: FP64 conversions and adds are slow on GB300
     __shared__ R s_beta[2], s_kc, s_pv[2];
     // cluster of two: the peer CTA's copy of a shared-memory location
@@ -90,27 +98,27 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
     for (int i = tid; i < n; i += kTT) {
         vo[i] = 0;
         po[i] = 0;
+        cs[i] = 0;
     }
     __syncthreads();
     cluster_sync();   // both CTAs resident before the first remote store
     for (int k = 0; k + 2 < n; ++k) {
-        // (a) row k with the pending update; reflector from its entries right of the diagonal (formed by the CTA
+        // (a) column k with the pending update; reflector from its entries below the diagonal (formed by the CTA
         // that owns row k and copied into the peer's shared memory)
         if (wid == 0 && (CL == 1 || (unsigned)(k & 1) == rank)) {
             R *vr_ = remote(v);
             R *row = A + (long long)k * lda;
-            const R *src = k == 0 ? row : nx;
             const R vk = vo[k], pk = po[k];
             R ss = 0;
             for (int c = k + 1 + lane; c < n; c += 32) {
-                const R x = src[c] - vk * po[c] - pk * vo[c];
+                const R x = (k == 0 ? row[c] : nx[c]) - vk * po[c] - pk * vo[c];
                 v[c] = x;
                 if (CL == 2 && c > k + 1) vr_[c] = x;
                 ss = fma(x, x, ss);
             }
             ss = warp_sum_t(ss);
             if (lane == 0) {
-                D.d[k] = src[k] - 2 * vk * pk;
+                D.d[k] = (k == 0 ? row[0] : nx[k]) - 2 * vk * pk;
                 const R x0 = v[k + 1];
                 const R alpha = sqrt(ss);
                 R beta = 0;
@@ -135,45 +143,54 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
         __syncthreads();
         cluster_sync();
         const R beta = s_beta[k & 1];
-        // (b) pending update of rows r > k (columns > k) fused with p = beta A v; a warp takes four rows at a
-        // time so that several independent loads are in flight per lane
-        // (rows r = rank (mod CL): warp w takes the rows rstart + CL (w + NW q), q < 4, per pass)
-        R pv = 0;
-        R *pr_ = remote(p);
+        // (b) pending update of the lower triangle of rows r > k fused with the row and column sums of A v; a warp
+        // takes four rows at a time so that several independent loads are in flight per lane (rows r = rank
+        // (mod CL): warp w takes the rows rstart + CL (w + NW q), q < 4, per pass)
+        R *nxr = remote(nx);
         const int rstart = k + 1 + (int)((rank ^ (unsigned)(k + 1)) & (CL - 1));
         for (int r0 = rstart + CL * wid; r0 < n; r0 += 4 * CL * NW) {
             R *row[4];
-            R vr[4], pr[4], acc[4];
+            R vr[4], pr[4], vq[4], acc[4];
+            int rq[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int r = r0 + q * CL * NW;
                 const bool ok = r < n;
+                rq[q] = ok ? r : -1;   // columns c <= rq[q] belong to row q
                 row[q] = A + (long long)(ok ? r : r0) * lda;
                 vr[q] = ok ? vo[r] : (R)0;
                 pr[q] = ok ? po[r] : (R)0;
+                vq[q] = ok ? v[r] : (R)0;
                 acc[q] = 0;
             }
             const int nr = min(4, (n - 1 - r0) / (CL * NW) + 1);
-            const bool stash = r0 == k + 1;   // warp 0's first row is row k + 1
-            auto col = [&](int c) {           // one column of the (up to) four rows
+            const int hi = rq[nr - 1];   // the group's longest row
+            auto col = [&](int c) {      // one column of the (up to) four rows
                 const R poc = po[c], voc = vo[c], vc = v[c];
+                R cl = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (q < nr) {
+                    if (q < nr && c <= rq[q]) {
                         const R x = row[q][c] - vr[q] * poc - pr[q] * voc;
                         row[q][c] = x;
                         acc[q] = fma(x, vc, acc[q]);
-                        if (q == 0 && stash) nx[c] = x;
+                        if (c < rq[q]) cl = fma(x, vq[q], cl);
+                        if (c == k + 1) {
+                            nx[rq[q]] = x;
+                            if (CL == 2) nxr[rq[q]] = x;
+                        }
                     }
+                if (c < hi) atomicAdd(cs + c, cl);
             };
             bool vdone = false;
             if constexpr (sizeof(R) == 4) {
                 if (vec) {
-                    // 16-byte column groups [cb, ce), UV groups of four rows per lane in flight; the ragged head
-                    // [k + 1, cb) and tail [max(ce, cb), n) (three columns at most each) column by column
-                    const int cb = min((k + 4) & ~3, n), ce = n & ~3;
+                    // 16-byte column groups [cb, ce) inside [k + 1, hi], UV groups of four rows per lane in flight;
+                    // the ragged head [k + 1, cb) and tail [max(ce, cb), hi] (three columns at most each) column by
+                    // column.  A group that reaches past a shorter row stores that row's elements back unchanged.
+                    const int cb = min((k + 4) & ~3, hi + 1), ce = (hi + 1) & ~3;
                     if (lane < 3 && k + 1 + lane < cb) col(k + 1 + lane);
-                    if (lane < 3 && max(ce, cb) + lane < n) col(max(ce, cb) + lane);
+                    if (lane < 3 && max(ce, cb) + lane <= hi) col(max(ce, cb) + lane);
                     const int nch = ce > cb ? (ce - cb) >> 2 : 0;
                     constexpr int UV = 3;
                     for (int j0 = lane; j0 < nch; j0 += 32 * UV) {
@@ -183,7 +200,8 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
                             const int j = j0 + 32 * u;
 #pragma unroll
                             for (int q = 0; q < 4; ++q)
-                                if (q < nr && j < nch) a[u][q] = *reinterpret_cast<const float4 *>(row[q] + cb + 4 * j);
+                                if (q < nr && j < nch && cb + 4 * j <= rq[q])
+                                    a[u][q] = *reinterpret_cast<const float4 *>(row[q] + cb + 4 * j);
                         }
 #pragma unroll
                         for (int u = 0; u < UV; ++u) {
@@ -193,69 +211,81 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
                             const float4 poc = *reinterpret_cast<const float4 *>(po + c);
                             const float4 voc = *reinterpret_cast<const float4 *>(vo + c);
                             const float4 vc = *reinterpret_cast<const float4 *>(v + c);
+                            float4 cl = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                             for (int q = 0; q < 4; ++q)
-                                if (q < nr) {
+                                if (q < nr && c <= rq[q]) {
                                     float4 x = a[u][q];
+                                    const int lim = rq[q] - c;   // elements c + e with e <= lim belong to the row
                                     x.x = x.x - vr[q] * poc.x - pr[q] * voc.x;
-                                    x.y = x.y - vr[q] * poc.y - pr[q] * voc.y;
-                                    x.z = x.z - vr[q] * poc.z - pr[q] * voc.z;
-                                    x.w = x.w - vr[q] * poc.w - pr[q] * voc.w;
-                                    *reinterpret_cast<float4 *>(row[q] + c) = x;
                                     acc[q] = fma(x.x, vc.x, acc[q]);
-                                    acc[q] = fma(x.y, vc.y, acc[q]);
-                                    acc[q] = fma(x.z, vc.z, acc[q]);
-                                    acc[q] = fma(x.w, vc.w, acc[q]);
-                                    if (q == 0 && stash) *reinterpret_cast<float4 *>(nx + c) = x;
+                                    if (lim > 0) cl.x = fma(x.x, vq[q], cl.x);
+                                    if (lim >= 1) {
+                                        x.y = x.y - vr[q] * poc.y - pr[q] * voc.y;
+                                        acc[q] = fma(x.y, vc.y, acc[q]);
+                                        if (lim > 1) cl.y = fma(x.y, vq[q], cl.y);
+                                    }
+                                    if (lim >= 2) {
+                                        x.z = x.z - vr[q] * poc.z - pr[q] * voc.z;
+                                        acc[q] = fma(x.z, vc.z, acc[q]);
+                                        if (lim > 2) cl.z = fma(x.z, vq[q], cl.z);
+                                    }
+                                    if (lim >= 3) {
+                                        x.w = x.w - vr[q] * poc.w - pr[q] * voc.w;
+                                        acc[q] = fma(x.w, vc.w, acc[q]);
+                                        if (lim > 3) cl.w = fma(x.w, vq[q], cl.w);
+                                    }
+                                    *reinterpret_cast<float4 *>(row[q] + c) = x;
+                                    if (c == k + 1) {
+                                        nx[rq[q]] = x.x;
+                                        if (CL == 2) nxr[rq[q]] = x.x;
+                                    }
                                 }
+                            // columns at or beyond the longest row's diagonal take no column sum
+                            if (c < hi) atomicAdd(cs + c, cl.x);
+                            if (c + 1 < hi) atomicAdd(cs + c + 1, cl.y);
+                            if (c + 2 < hi) atomicAdd(cs + c + 2, cl.z);
+                            if (c + 3 < hi) atomicAdd(cs + c + 3, cl.w);
                         }
                     }
                     vdone = true;
                 }
             }
             if (!vdone) {
-            // U column groups of four rows: every load of a group is issued before its first store
-            constexpr int U = sizeof(R) == 4 ? 4 : 2;
-            for (int c0 = k + 1 + lane; c0 < n; c0 += 32 * U) {
-                R a[U][4];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int c = c0 + 32 * u;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q < nr && c < n) a[u][q] = row[q][c];
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int c = c0 + 32 * u;
-                    if (c >= n) break;
-                    const R poc = po[c], voc = vo[c], vc = v[c];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (q < nr) {
-                            a[u][q] = a[u][q] - vr[q] * poc - pr[q] * voc;
-                            row[q][c] = a[u][q];
-                            acc[q] = fma(a[u][q], vc, acc[q]);
-                        }
-                    if (stash) nx[c] = a[u][0];
-                }
-            }
+                for (int c = k + 1 + lane; c <= hi; c += 32) col(c);
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (q >= nr) break;
-                const R sum = warp_sum_t(acc[q]) * beta;
-                if (lane == 0) {
-                    p[r0 + q * CL * NW] = sum;
-                    if (CL == 2) pr_[r0 + q * CL * NW] = sum;
-                    pv = fma(sum, v[r0 + q * CL * NW], pv);
-                }
+                const R sum = warp_sum_t(acc[q]);
+                if (lane == 0) p[rq[q]] = sum;   // the row sum; the column sums are added below
             }
         }
+        __syncthreads();
+        // (c) the peer's column sums for this CTA's rows, then p = beta (row + column sums) for this CTA's rows
+        // (copied into the peer), p.v, and p -= (beta/2)(p.v) v over the whole vector
+        if constexpr (CL == 2) {
+            R *cqr = remote(cq);
+            for (int c = k + 1 + tid; c < n; c += kTT)
+                if ((unsigned)(c & 1) != rank) cqr[c] = cs[c];
+            cluster_sync();
+        }
+        R pv = 0;
+        {
+            R *pr_ = remote(p);
+            for (int c = k + 1 + tid; c < n; c += kTT) {
+                if (CL == 1 || (unsigned)(c & 1) == rank) {
+                    const R pc = beta * (p[c] + cs[c] + (CL == 2 ? cq[c] : (R)0));
+                    p[c] = pc;
+                    if (CL == 2) pr_[c] = pc;
+                    pv = fma(pc, v[c], pv);
+                }
+                cs[c] = 0;   // ready for the next pass (the peer has its copy)
+            }
+        }
+        pv = warp_sum_t(pv);
         if (lane == 0) part[wid] = pv;
         __syncthreads();
-        // (c) p -= (beta/2)(p.v) v (the partial sums reduced by warp 0, then over the pair in rank order); swap
-        // the pending-update buffers
         if (wid == 0) {
             const R t = warp_sum_t(lane < NW ? part[lane] : (R)0);
             if (lane == 0) {
@@ -998,7 +1028,8 @@ size_t jacobi_smem_bytes(int n) {
 template <class R>
 cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
-    const size_t sh = 5 * (size_t)((n + 3) & ~3) * sizeof(R);
+    // v, p, vo, po, the column stash and the column sums; the pair of CTAs adds the peer's column sums
+    const size_t sh = (sizeof(R) == 4 ? 7 : 6) * (size_t)((n + 3) & ~3) * sizeof(R);
     cudaError_t e;
     if constexpr (sizeof(R) == 4) {
         // FP32: a pair of CTAs (thread-block cluster) per matrix, each owning every other row
