@@ -101,6 +101,22 @@ const char *osv_last_error(const osv_ctx *ctx);
  * (mbe_order 0: n_clusters[0] = 1 full cluster, others 0).  Must precede osv_build. */
 osv_status clusters_build(osv_ctx *ctx, const osv_problem *prob, const osv_params *params, int *n_clusters);
 
+/* OSV-overlap screening (Sec. 2.2.1; the paper's cluster selection, in place of the distance cutoffs):
+ *   osv_overlap_metric builds the OSVs of every LMO with `params` (as osv_build does; mbe_order is ignored) and
+ *   writes the metric of Eq. 2bscreen for every pair of LMOs, s2b_ij = sum_{mu in i, nu in j} <mu|nu>^2 /
+ *   sqrt(n_i n_j), <mu|nu> the entries of Q_i^T Q_j, into s2b_out (HOST n_occ x n_occ, row-major; 0 <= s2b <= 1,
+ *   s2b_ii = 1).  The Gram of the OSVs runs on the precision mode's dense back end (exact BF16 slices on the
+ *   tensor cores in OSV_MIXED_BF16X4).  Synchronises.  It replaces any earlier plan on ctx: call
+ *   clusters_build_osv next.
+ *   clusters_build_osv is clusters_build with the selection rule of Eqs. 2bscreen and 3bscreen: pair ij (i < j)
+ *   is a 2b cluster iff s2b[i][j] > l2b; triple ijk is a 3b cluster iff its three pairs are 2b clusters and
+ *   (s2b_ij + s2b_ik + s2b_jk) / 3 > l3b (entries read at i < j); r2b and r3b of params are not used.  MBE
+ *   weights, mbe_order and the rest of the plan as in clusters_build.  OSV_ERR_INVALID for a NULL or non-finite
+ *   s2b. */
+osv_status osv_overlap_metric(osv_ctx *ctx, const osv_problem *prob, const osv_params *params, double *s2b_out);
+osv_status clusters_build_osv(osv_ctx *ctx, const osv_problem *prob, const osv_params *params, const double *s2b,
+                              double l2b, double l3b, int *n_clusters);
+
 /* Build orbital-specific virtuals and all pair quantities for the selected clusters (steps on the device):
  *   T_kk = (ka|kb) / (eps_a + eps_b - 2 f_kk), eigenpairs to FP64 accuracy (FP64 tridiagonal route, or FP32
  *   with FP64 Rayleigh-Ritz refinement in OSV_MIXED_BF16X4), Q_k = eigenvectors of the n_k largest eigenvalues
@@ -122,6 +138,15 @@ osv_status cluster_residual_solve(osv_ctx *ctx, int *n_iter_out, int32_t *cluste
 /* Collective pair amplitudes T_(ij,ij) = sum over clusters c containing i, j of w_c T^c_(ij,ij)
  * (MBE(3), Eqs. 28-32). */
 osv_status mbe3_combine(osv_ctx *ctx);
+
+/* One-step posterior correction over the collective amplitudes (Sec. 3, the estimate beyond MBE(3)), after
+ * mbe3_combine.  For every pair ij of a selected cluster, Eq. 4 is evaluated at the collective amplitudes T with
+ * k running over the LMOs of every selected cluster that holds both i and j, and one step of the cluster
+ * solver's preconditioned update is taken, T' = T - R~ / (e_a + e_b - f_ii - f_jj) in the pair's
+ * pseudo-canonical basis.  HOST outputs: *E_global = sum over ordered pairs of <K + R(T), 2T - T^T>, *E_corrected
+ * the same functional at T', *dR_max (may be NULL) = max over pairs of ||R~(T)||_F.  FP64 evaluations (double-
+ * float in OSV_MIXED_BF16X4).  Synchronises; OSV_ERR_NUMERIC for a non-finite result. */
+osv_status posterior_correction(osv_ctx *ctx, double *E_global, double *E_corrected, double *dR_max);
 
 /* E = sum_c w_c E^c_Hylleraas (Eq. 3 per cluster, MBE-combined) into *E_out (HOST);
  * E_linear_out (HOST, may be NULL) = sum_ij <K_(ij,ij), 2T - T^T> with the collective amplitudes.

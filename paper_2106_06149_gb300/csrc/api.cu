@@ -63,8 +63,10 @@ osv_status check_problem(osv_ctx *c, const osv_problem *pb) {
     return OSV_OK;
 }
 
-// clusters: sorted member lists; selection rule of clusters_build
-void select_clusters(osv_ctx *c) {
+// clusters: sorted member lists.  Distance rule of clusters_build, or (s2b != NULL) the OSV-overlap rule of
+// clusters_build_osv (Sec. 2.2.1, Eqs. 2bscreen and 3bscreen): pair ij kept iff s2b_ij > l2b, triple ijk kept iff
+// its three pairs are kept and (s2b_ij + s2b_ik + s2b_jk) / 3 > l3b (s2b read at i < j).
+void select_clusters(osv_ctx *c, const double *s2b = nullptr, double l2b = 0.0, double l3b = 0.0) {
     const int n = c->n_occ;
     const osv_params &p = c->prm;
     c->cl.clear();
@@ -87,6 +89,28 @@ void select_clusters(osv_ctx *c) {
     for (int i = 0; i < n; ++i) c->cl.push_back({i});
     c->ncl_order[0] = n;
     if (p.mbe_order < 2) return;
+    if (s2b) {
+        auto s = [&](int i, int j) { return s2b[(size_t)i * n + j]; };
+        std::vector<char> kp((size_t)n * n, 0);
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j)
+                if (s(i, j) > l2b) {
+                    kp[(size_t)i * n + j] = 1;
+                    c->cl.push_back({i, j});
+                    ++c->ncl_order[1];
+                }
+        if (p.mbe_order < 3) return;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                if (!kp[(size_t)i * n + j]) continue;
+                for (int k = j + 1; k < n; ++k)
+                    if (kp[(size_t)i * n + k] && kp[(size_t)j * n + k] && (s(i, j) + s(i, k) + s(j, k)) / 3.0 > l3b) {
+                        c->cl.push_back({i, j, k});
+                        ++c->ncl_order[2];
+                    }
+            }
+        return;
+    }
     std::vector<char> keep((size_t)n * n, 0);
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j)
@@ -130,6 +154,58 @@ void mbe_weights(osv_ctx *c) {
     }
 }
 
+osv_status clusters_setup(osv_ctx *c, const osv_problem *pb, const osv_params *prm, int *n_clusters,
+                          const double *s2b, double l2b, double l3b) {
+    if (!c) return OSV_ERR_INVALID;
+    osv_status st;
+    if ((st = check_params(c, prm)) != OSV_OK) return st;
+    if ((st = check_problem(c, pb)) != OSV_OK) return st;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->release();
+    c->prm = *prm;
+    c->n_occ = pb->n_occ;
+    c->n_vir = pb->n_vir;
+    c->n_aux = pb->n_aux;
+    c->centres.assign(pb->centres, pb->centres + 3 * pb->n_occ);
+    c->aux_ptr.assign(pb->aux_ptr, pb->aux_ptr + pb->n_occ + 1);
+    c->aux_idx.assign(pb->aux_idx, pb->aux_idx + pb->aux_ptr[pb->n_occ]);
+    select_clusters(c, s2b, l2b, l3b);
+    mbe_weights(c);
+    const int n = c->n_occ;
+    // stored pairs i <= j: every diagonal pair and every pair inside a cluster
+    c->pairs.clear();
+    c->pair_id.clear();
+    for (int i = 0; i < n; ++i) {
+        c->pair_id[(long long)i * n + i] = (int)c->pairs.size();
+        c->pairs.push_back({i, i});
+    }
+    for (const auto &m : c->cl)
+        for (size_t a = 0; a < m.size(); ++a)
+            for (size_t b = a + 1; b < m.size(); ++b) {
+                const long long key = (long long)m[a] * n + m[b];
+                if (!c->pair_id.count(key)) {
+                    c->pair_id[key] = (int)c->pairs.size();
+                    c->pairs.push_back({m[a], m[b]});
+                }
+            }
+    c->nb.assign(n, {});
+    for (int i = 0; i < n; ++i) c->nb[i].push_back(i);
+    for (const auto &pr : c->pairs)
+        if (pr.first != pr.second) {
+            c->nb[pr.first].push_back(pr.second);
+            c->nb[pr.second].push_back(pr.first);
+        }
+    for (auto &v : c->nb) std::sort(v.begin(), v.end());
+    c->have_clusters = true;
+    if (n_clusters) {
+        n_clusters[0] = c->ncl_order[0];
+        n_clusters[1] = c->ncl_order[1];
+        n_clusters[2] = c->ncl_order[2];
+    }
+    return OSV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -168,54 +244,18 @@ osv_status osv_destroy(osv_ctx *ctx) {
 }
 
 osv_status clusters_build(osv_ctx *c, const osv_problem *pb, const osv_params *prm, int *n_clusters) {
+    return clusters_setup(c, pb, prm, n_clusters, nullptr, 0.0, 0.0);
+}
+
+osv_status clusters_build_osv(osv_ctx *c, const osv_problem *pb, const osv_params *prm, const double *s2b, double l2b,
+                              double l3b, int *n_clusters) {
     if (!c) return OSV_ERR_INVALID;
-    osv_status st;
-    if ((st = check_params(c, prm)) != OSV_OK) return st;
-    if ((st = check_problem(c, pb)) != OSV_OK) return st;
-    cudaSetDevice(c->device);
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    c->release();
-    c->prm = *prm;
-    c->n_occ = pb->n_occ;
-    c->n_vir = pb->n_vir;
-    c->n_aux = pb->n_aux;
-    c->centres.assign(pb->centres, pb->centres + 3 * pb->n_occ);
-    c->aux_ptr.assign(pb->aux_ptr, pb->aux_ptr + pb->n_occ + 1);
-    c->aux_idx.assign(pb->aux_idx, pb->aux_idx + pb->aux_ptr[pb->n_occ]);
-    select_clusters(c);
-    mbe_weights(c);
-    const int n = c->n_occ;
-    // stored pairs i <= j: every diagonal pair and every pair inside a cluster
-    c->pairs.clear();
-    c->pair_id.clear();
-    for (int i = 0; i < n; ++i) {
-        c->pair_id[(long long)i * n + i] = (int)c->pairs.size();
-        c->pairs.push_back({i, i});
-    }
-    for (const auto &m : c->cl)
-        for (size_t a = 0; a < m.size(); ++a)
-            for (size_t b = a + 1; b < m.size(); ++b) {
-                const long long key = (long long)m[a] * n + m[b];
-                if (!c->pair_id.count(key)) {
-                    c->pair_id[key] = (int)c->pairs.size();
-                    c->pairs.push_back({m[a], m[b]});
-                }
-            }
-    c->nb.assign(n, {});
-    for (int i = 0; i < n; ++i) c->nb[i].push_back(i);
-    for (const auto &pr : c->pairs)
-        if (pr.first != pr.second) {
-            c->nb[pr.first].push_back(pr.second);
-            c->nb[pr.second].push_back(pr.first);
-        }
-    for (auto &v : c->nb) std::sort(v.begin(), v.end());
-    c->have_clusters = true;
-    if (n_clusters) {
-        n_clusters[0] = c->ncl_order[0];
-        n_clusters[1] = c->ncl_order[1];
-        n_clusters[2] = c->ncl_order[2];
-    }
-    return OSV_OK;
+    if (!s2b || !std::isfinite(l2b) || !std::isfinite(l3b))
+        return c->fail(OSV_ERR_INVALID, "s2b must be non-NULL and l2b, l3b finite");
+    if (pb && pb->n_occ > 0)
+        for (long long q = 0; q < (long long)pb->n_occ * pb->n_occ; ++q)
+            if (!std::isfinite(s2b[q])) return c->fail(OSV_ERR_INVALID, "non-finite s2b entry");
+    return clusters_setup(c, pb, prm, n_clusters, s2b, l2b, l3b);
 }
 
 }  // extern "C"
@@ -832,6 +872,47 @@ osv_status osv_build(osv_ctx *c, const osv_problem *pb, const osv_params *prm, i
     return OSV_OK;
 }
 
+osv_status osv_overlap_metric(osv_ctx *c, const osv_problem *pb, const osv_params *prm, double *s2b_out) {
+    if (!c) return OSV_ERR_INVALID;
+    if (!s2b_out) return c->fail(OSV_ERR_INVALID, "s2b_out is NULL");
+    if (!prm) return c->fail(OSV_ERR_INVALID, "params is NULL");
+    // the OSVs of every LMO: a plan of the 1b clusters alone (the cluster list is chosen afterwards)
+    osv_params p1 = *prm;
+    p1.mbe_order = 1;
+    osv_status st;
+    if ((st = clusters_setup(c, pb, &p1, nullptr, nullptr, 0.0, 0.0)) != OSV_OK) return st;
+    if ((st = osv_build(c, pb, &p1, nullptr)) != OSV_OK) return st;
+    const int n = c->n_occ, nm = c->nmax, nv = c->n_vir;
+    const long long nr = (long long)n * nm;
+    double *G = nullptr, *s = nullptr;
+    cudaError_t e;
+    if ((e = c->dalloc(G, (size_t)(nr * nr))) != cudaSuccess || (e = c->dalloc(s, (size_t)n * n)) != cudaSuccess)
+        return c->cuda_fail(e, "cudaMalloc metric");
+    // G = Q Q^T over all OSV rows, one problem per LMO's rows (the dense back end of the precision mode)
+    GemmBatch gb;
+    for (int i = 0; i < n; ++i)
+        gb.add(gemm(nm, (int)nr, nv, c->Q + (long long)i * nm * nv, nv, 0, c->Q, nv, 1, G + (long long)i * nm * nr, nr));
+    osv::TcTiles oz;
+    e = gemm_batch_upload(gb);
+    if (e == cudaSuccess && c->prm.precision == OSV_MIXED_BF16X4) {
+        e = bf16x4_batch_prepare(gb, oz);
+        if (e == cudaSuccess) e = c->oz_reserve((size_t)oz.scratch_bytes);
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(*c, "osv_metric");
+        e = c->run_dense(gb, oz);
+        if (e == cudaSuccess) e = launch_s2b(G, c->nosv, n, nm, s, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    gemm_batch_free(gb);
+    osv::tc_tiles_free(oz);
+    if (e != cudaSuccess) return c->cuda_fail(e, "overlap metric");
+    if ((st = device_error(c)) != OSV_OK) return st;
+    if ((e = cudaMemcpy(s2b_out, s, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "copy s2b");
+    return OSV_OK;
+}
+
 osv_status cluster_residual_solve(osv_ctx *c, int *n_iter_out, int32_t *cluster_status) {
     if (!c) return OSV_ERR_INVALID;
     if (!c->built) return c->fail(OSV_ERR_INVALID, "osv_build must precede cluster_residual_solve");
@@ -911,6 +992,123 @@ osv_status mbe3_combine(osv_ctx *c) {
                                    c->Tslot, c->Tc, c->stream);
     if (e != cudaSuccess) return c->cuda_fail(e, "combine");
     c->combined = true;
+    return OSV_OK;
+}
+
+namespace {
+
+// Posterior plan: for every stored pair p = (i, j), the LMOs k of the clusters that hold both i and j, and the terms
+// of Eq. 4 over them (the same coupling blocks as the cluster solves, which hold every such k with i and j).
+osv_status build_posterior_plan(osv_ctx *c) {
+    const int np_ = (int)c->pairs.size();
+    std::vector<std::vector<int>> ks(np_);
+    for (const auto &m : c->cl)
+        for (size_t a = 0; a < m.size(); ++a)
+            for (size_t b = a; b < m.size(); ++b) {
+                auto &v = ks[c->pid(m[a], m[b])];
+                v.insert(v.end(), m.begin(), m.end());
+            }
+    c->post_slots.h.clear();
+    c->post_cl.h.clear();
+    c->post_terms.h.clear();
+    for (int p = 0; p < np_; ++p) {
+        auto &v = ks[p];
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        const PairInfo &P = c->pinfo.h[p];
+        Slot S{};
+        S.pair = p;
+        S.cluster = p;
+        S.t_off = P.off;
+        S.mult = P.i == P.j ? 1 : 2;
+        c->post_slots.h.push_back(S);
+        ClusterInfo C{};
+        C.slot0 = p;
+        C.slot1 = p + 1;
+        C.term0 = (int)c->post_terms.h.size();
+        C.weight = 1;
+        C.size = (int)v.size();
+        auto add = [&](int x, int y, int fx, int fy) -> bool {
+            const int q = c->pid(x, y);
+            if (q < 0) return false;
+            const long long key = (long long)std::min(p, q) * (long long)np_ + std::max(p, q);
+            auto it = c->coupling_id.find(key);
+            if (it == c->coupling_id.end()) return false;
+            Term T{};
+            T.dst = p;
+            T.src = q;
+            T.fx = fx;
+            T.fy = fy;
+            T.t_trans = x > y ? 1 : 0;
+            T.s_trans = p > q ? 1 : 0;
+            T.coupling = it->second;
+            T.sblk = c->coup_off[it->second];
+            c->post_terms.h.push_back(T);
+            return true;
+        };
+        for (int k : v) {
+            if (k != P.j && !add(P.i, k, k, P.j)) return c->fail(OSV_ERR_INVALID, "posterior: missing coupling block");
+            if (k != P.i && !add(k, P.j, P.i, k)) return c->fail(OSV_ERR_INVALID, "posterior: missing coupling block");
+        }
+        C.term1 = (int)c->post_terms.h.size();
+        c->post_cl.h.push_back(C);
+    }
+    cudaError_t e;
+    if ((e = c->upload(c->post_slots)) != cudaSuccess || (e = c->upload(c->post_cl)) != cudaSuccess ||
+        (e = c->upload(c->post_terms)) != cudaSuccess || (e = c->dalloc(c->post_R1, c->pair_mat)) != cudaSuccess ||
+        (e = c->dalloc(c->post_T2, c->pair_mat)) != cudaSuccess || (e = c->dalloc(c->post_R2, c->pair_mat)) != cudaSuccess ||
+        (e = c->dalloc(c->post_rn, 2LL * np_)) != cudaSuccess || (e = c->dalloc(c->post_E, 2LL * np_)) != cudaSuccess ||
+        (e = c->dalloc(c->post_G1, (long long)np_ * c->gstride)) != cudaSuccess)
+        return c->cuda_fail(e, "posterior plan");
+    c->post_built = true;
+    return OSV_OK;
+}
+
+}  // namespace
+
+osv_status posterior_correction(osv_ctx *c, double *E_global, double *E_corrected, double *dR_max) {
+    if (!c || !E_global || !E_corrected) return c ? c->fail(OSV_ERR_INVALID, "NULL output") : OSV_ERR_INVALID;
+    if (!c->combined) return c->fail(OSV_ERR_INVALID, "mbe3_combine must precede posterior_correction");
+    cudaSetDevice(c->device);
+    osv_status st;
+    if (!c->post_built && (st = build_posterior_plan(c)) != OSV_OK) return st;
+    const int np_ = (int)c->pairs.size();
+    SolveArgs a{};
+    a.clusters = c->post_cl.d;
+    a.slots = c->post_slots.d;
+    a.terms = c->post_terms.d;
+    a.pairs = c->pinfo.d;
+    a.rdim = c->rdim;
+    a.e = c->pe;
+    a.Kt = c->Kt;
+    a.sblk = c->Stil;
+    a.focc = c->focc;
+    a.n_occ = c->n_occ;
+    a.G1 = c->post_G1;
+    a.gstride = c->gstride;
+    a.np_max = 2 * c->nmax;
+    cudaError_t e;
+    {
+        StageTimer t(*c, "posterior");
+        e = launch_posterior(a, np_, c->Tc, c->post_R1, c->post_T2, c->post_R2, c->post_rn, c->post_E,
+                             c->post_E + np_, c->prm.precision != OSV_FP64, c->stream);
+    }
+    if (e != cudaSuccess) return c->cuda_fail(e, "posterior");
+    std::vector<double> rn(np_), E(2LL * np_);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess ||
+        (e = cudaMemcpy(rn.data(), c->post_rn, np_ * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(E.data(), c->post_E, 2LL * np_ * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return c->cuda_fail(e, "posterior copy");
+    double e1 = 0.0, e2 = 0.0, r = 0.0;
+    for (int p = 0; p < np_; ++p) {
+        e1 += E[p];
+        e2 += E[np_ + p];
+        r = std::max(r, rn[p]);
+    }
+    *E_global = e1;
+    *E_corrected = e2;
+    if (dR_max) *dR_max = r;
+    if (!std::isfinite(e1) || !std::isfinite(e2)) return c->fail(OSV_ERR_NUMERIC, "posterior energy is not finite");
     return OSV_OK;
 }
 

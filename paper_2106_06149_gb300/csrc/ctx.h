@@ -106,6 +106,13 @@ struct osv_ctx {
     osv::TcTiles oz_gram, oz_w, oz_k;          // exact-slice BF16x4 tilings
 
     osv::AdjointPlan adj;
+    // one-step posterior correction (built on first use after a solve): one pseudo-cluster per stored pair
+    bool post_built = false;
+    HostDev<Slot> post_slots;
+    HostDev<ClusterInfo> post_cl;
+    HostDev<Term> post_terms;
+    double *post_R1 = nullptr, *post_T2 = nullptr, *post_R2 = nullptr, *post_rn = nullptr, *post_E = nullptr,
+           *post_G1 = nullptr;
     long long wait_budget = 0;             // tensor-core main-loop wait budget in clock cycles (0 = default)
 
     // per-stage CUDA-event profiling (osv_profile_enable / osv_profile_read)
@@ -189,7 +196,7 @@ struct osv_ctx {
         oz_cap = 0;
         for (osv::TcTiles *t : {&oz_gram, &oz_w, &oz_k}) osv::tc_tiles_free(*t);
         adj.release();
-        built = solved = combined = false;
+        built = solved = combined = post_built = false;
     }
     int pid(int i, int j) const {
         auto it = pair_id.find((long long)std::min(i, j) * n_occ + std::max(i, j));

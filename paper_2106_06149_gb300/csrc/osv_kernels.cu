@@ -103,7 +103,31 @@ __global__ void k_clean_w(const PairInfo *__restrict__ pairs, const int *__restr
     for (int a = r + threadIdx.x; a < np; a += blockDim.x) e[P.e_off + a] = 0.0;
 }
 
+// OSV-overlap metric of Sec. 2.2.1, Eq. 2bscreen, from the Gram G of all OSV rows (row i*nm + mu is OSV mu of
+// LMO i, zero beyond n_i): s_ij = sum over the n_i x n_j block of G^2 / sqrt(n_i n_j).  One CTA per (i, j).
+__global__ void k_s2b(const double *__restrict__ G, const int *__restrict__ nosv, int n, int nm,
+                      double *__restrict__ s) {
+    const int i = blockIdx.y, j = blockIdx.x;
+    const long long ld = (long long)n * nm;
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < nm * nm; idx += blockDim.x) {
+        const int mu = idx / nm, nu = idx % nm;
+        const double g = G[(long long)(i * nm + mu) * ld + (long long)j * nm + nu];
+        acc = fma(g, g, acc);
+    }
+    __shared__ double red[32];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) s[(long long)i * n + j] = acc / sqrt((double)nosv[i] * (double)nosv[j]);
+}
+
 }  // namespace
+
+cudaError_t launch_s2b(const double *G, const int *nosv, int n, int nm, double *s, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    count_launch();
+    k_s2b<<<dim3(n, n), 128, 0, st>>>(G, nosv, n, nm, s);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_f32_to_f64(const float *in, double *out, long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;

@@ -559,7 +559,76 @@ __global__ void k_energy_final(const double *__restrict__ Ec, const ClusterInfo 
     }
 }
 
+// One-step posterior correction over the collective amplitudes (Sec. 3): every stored pair p is a pseudo-cluster
+// whose single slot is p and whose terms run over the LMOs k of the clusters that hold both LMOs of p (the slots
+// and the amplitudes are those of the pairs: t_off = the pair's offset into Tsrc / Rdst).  One CTA per pair: R~_p of
+// Eq. 4 at Tsrc and its Frobenius norm, FP64 (df = false) or double-float on the FP32 pipe (df = true).
+__global__ void __launch_bounds__(kThreads) k_posterior_eval(SolveArgs A, const double *__restrict__ Tsrc,
+                                                             double *__restrict__ Rdst, double *__restrict__ rnorm,
+                                                             bool df) {
+    const int p = blockIdx.x;
+    const ClusterInfo C = A.clusters[p];
+    __shared__ double red[kThreads / 32];
+    extern __shared__ __align__(16) float stage[];
+    View<double> v{A.e, A.Kt, false, A.sblk, const_cast<double *>(Tsrc), Rdst, A.G1 + (long long)blockIdx.x * A.gstride,
+                   stage, A.np_max + 1, df};
+    const double rn = residual_eval<double>(A, C, v, red);
+    if (threadIdx.x == 0) rnorm[p] = rn;
+}
+
+// T' = T - R~ / (e_a + e_b - f_ii - f_jj) on the r_p x r_p block of every pair (the cluster solver's preconditioned
+// step); zero elsewhere.
+__global__ void k_posterior_step(const PairInfo *__restrict__ pairs, const int *__restrict__ rdim,
+                                 const double *__restrict__ e, const double *__restrict__ focc, int n_occ,
+                                 const double *__restrict__ T, const double *__restrict__ R, double *__restrict__ T2) {
+    const int p = blockIdx.x;
+    const PairInfo P = pairs[p];
+    const int r = rdim[p], np = P.np;
+    const double fii = focc[(long long)P.i * n_occ + P.i], fjj = focc[(long long)P.j * n_occ + P.j];
+    for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x) {
+        const int a = idx / np, b = idx % np;
+        const long long o = P.off + idx;
+        T2[o] = (a < r && b < r) ? T[o] - R[o] / (e[P.e_off + a] + e[P.e_off + b] - fii - fjj) : 0.0;
+    }
+}
+
+// Per pair: mult_p <K~_p + R~_p, 2T~_p - T~_p^T> (Eq. 3 over the ordered pairs ij and ji, which are transposes).
+__global__ void k_pair_functional(const PairInfo *__restrict__ pairs, const int *__restrict__ rdim,
+                                  const double *__restrict__ Kt, const double *__restrict__ T,
+                                  const double *__restrict__ R, double *__restrict__ out) {
+    const int p = blockIdx.x;
+    const PairInfo P = pairs[p];
+    const int r = rdim[p], np = P.np;
+    __shared__ double red[kThreads / 32];
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+        const int a = idx / r, b = idx % r;
+        const long long o = P.off + (long long)a * np + b;
+        acc += (Kt[o] + R[o]) * (2.0 * T[o] - T[P.off + (long long)b * np + a]);
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) out[p] = (P.i == P.j ? 1.0 : 2.0) * acc;
+}
+
 }  // namespace
+
+cudaError_t launch_posterior(const SolveArgs &a, int npairs, const double *Tc, double *R1, double *T2, double *R2,
+                             double *rnorm, double *E1, double *E2, bool df, cudaStream_t s) {
+    if (npairs <= 0) return cudaSuccess;
+    const int ld = a.np_max + 1;
+    const size_t sh = df ? 2 * (size_t)ld * ld * sizeof(float2) : 0;
+    cudaError_t e;
+    if (sh > 48 * 1024 && (e = cudaFuncSetAttribute(k_posterior_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)sh)) != cudaSuccess)
+        return e;
+    count_launch(5);
+    k_posterior_eval<<<npairs, kThreads, sh, s>>>(a, Tc, R1, rnorm, df);
+    k_posterior_step<<<npairs, kThreads, 0, s>>>(a.pairs, a.rdim, a.e, a.focc, a.n_occ, Tc, R1, T2);
+    k_posterior_eval<<<npairs, kThreads, sh, s>>>(a, T2, R2, rnorm + npairs, df);
+    k_pair_functional<<<npairs, kThreads, 0, s>>>(a.pairs, a.rdim, a.Kt, Tc, R1, E1);
+    k_pair_functional<<<npairs, kThreads, 0, s>>>(a.pairs, a.rdim, a.Kt, T2, R2, E2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_residual(const SolveArgs &a, int nclusters, bool mixed, cudaStream_t s) {
     if (nclusters <= 0) return cudaSuccess;

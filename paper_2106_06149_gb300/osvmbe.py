@@ -23,7 +23,8 @@ EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv
            "osv_eigenvalues", "osv_syev_batched", "osv_profile_enable", "osv_profile_read",
            "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops",
            "osv_solve_counts", "osv_residual_work", "osv_set_wait_budget",
-           "osv_pair_amplitudes"]
+           "osv_pair_amplitudes", "osv_overlap_metric", "clusters_build_osv",
+           "posterior_correction"]
 
 
 class OsvParams(ctypes.Structure):
@@ -76,6 +77,9 @@ def load(path=LIB_PATH):
         "osv_residual_work": ([V, P(D), P(D)], I),
         "osv_set_wait_budget": ([V, ctypes.c_longlong], I),
         "osv_pair_amplitudes": ([V, I, I, V], I),
+        "osv_overlap_metric": ([V, P(OsvProblem), P(OsvParams), V], I),
+        "clusters_build_osv": ([V, P(OsvProblem), P(OsvParams), V, D, D, V], I),
+        "posterior_correction": ([V, P(D), P(D), P(D)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -192,6 +196,24 @@ class Context:
         _check(load().clusters_build(self.h, ctypes.byref(ps), ctypes.byref(self._prm), n), self.h)
         return [n[0], n[1], n[2]]
 
+    def osv_overlap_metric(self, prob: DeviceProblem, params):
+        """OSV-overlap metric s2b (n_occ x n_occ) of Eq. 2bscreen from the OSVs of every LMO."""
+        self._prm = params_struct(params)
+        ps = prob.struct()
+        out = np.zeros((prob.n_occ, prob.n_occ), np.float64)
+        _check(load().osv_overlap_metric(self.h, ctypes.byref(ps), ctypes.byref(self._prm), _ptr(out)), self.h)
+        return out
+
+    def clusters_build_osv(self, prob: DeviceProblem, params, s2b, l2b, l3b):
+        """clusters_build with the 2b/3b selection of Eqs. 2bscreen and 3bscreen on the metric s2b."""
+        self._prm = params_struct(params)
+        ps = prob.struct()
+        s = np.ascontiguousarray(s2b, dtype=np.float64)
+        n = (ctypes.c_int * 3)()
+        _check(load().clusters_build_osv(self.h, ctypes.byref(ps), ctypes.byref(self._prm), _ptr(s), float(l2b),
+                                         float(l3b), n), self.h)
+        return [n[0], n[1], n[2]]
+
     def osv_build(self, prob: DeviceProblem, params=None, want_counts=False, B=None, f_occ=None):
         if params is not None:
             self._prm = params_struct(params)
@@ -216,6 +238,12 @@ class Context:
         el = ctypes.c_double()
         _check(load().energy(self.h, ctypes.byref(e), ctypes.byref(el)), self.h)
         return e.value, el.value
+
+    def posterior_correction(self):
+        """One-step posterior correction (Sec. 3): dict(E_global, E_corrected, dR_max)."""
+        eg, ec, r = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().posterior_correction(self.h, ctypes.byref(eg), ctypes.byref(ec), ctypes.byref(r)), self.h)
+        return dict(E_global=eg.value, E_corrected=ec.value, dR_max=r.value)
 
     def gradient_backward(self, scale, dB=None, dF=None):
         _check(load().gradient_backward(self.h, float(scale), _ptr(dB) if dB is not None else None,
