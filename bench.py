@@ -1,20 +1,25 @@
 """Benchmark of the MBE(3)-OSV-MP2 hot path on GB300: one step = one geometry's energy AND gradient
-(osv_build -> cluster_residual_solve -> mbe3_combine -> energy -> gradient_backward) on the 64-LMO chain
-workload (n_vir 400, n_aux 1600, l_osv 1e-4 capped at 40 OSVs, 8/6 A pair/triple cutoffs).
+(osv_build -> cluster_residual_solve -> mbe3_combine -> energy -> gradient_backward) on a synthetic workload of
+paper_2106_06149_gb300.synth.WORKLOADS, by default workload 2: 256 LMOs in a 20 A cube, n_vir 1500, n_aux 6000,
+7 A fitting domains, B in FP32, l_osv 1e-4 capped at 40 OSVs, 8/6 A pair/triple cutoffs (256 + 5212 + 8872
+clusters), the mixed-precision and batching workload the metric is quoted on.
 
 Metric: cluster pair-residual TFLOP/s = algorithmic residual FLOPs of the step (coupling products of Eq. 4,
-2 (r_p r_q^2 + r_p^2 r_q) per term and residual evaluation) / step wall time.  Also reported: gradient
-seconds per geometry (= ms_per_step / 1000), residual-solve-only TFLOP/s, and the roofline of the dominant
-kernel from per-stage CUDA events taken over the timed region.
+2 (r_p r_q^2 + r_p^2 r_q) per term and residual evaluation, counted over the iterations the FP64 solve needs) /
+step wall time.  Also reported: gradient seconds per geometry (= ms_per_step / 1000), the FP64 GPU path's step
+time beside it (mixed_vs_fp64), the residual kernel's roofline (algorithmic FLOPs / its CUDA-event time / the
+measured dense BF16 peak) and per-stage times from CUDA events taken over the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--workload 1|2|3|4]
+                  [--precision fp64|bf16x4] [--fp64-steps S] [--no-cpu-baseline]
 Multi-GPU (torchrun, one rank per GPU): each rank solves its own geometry (different seed); no collective on
 the data path; value = all ranks' residual FLOPs / max-over-ranks time ("scaling": "weak").
---impl reference times the CPU oracle (the reference implementation of this path) on a bounded sample.
+--impl reference times the CPU oracle (the reference implementation of this path) on a bounded cluster sample.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -28,10 +33,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cluster pair-residual TFLOP/s, gradient s/geometry: mixed vs FP64 GPU @1e-6 Eh"
-WORKLOAD = 1
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM (1.25 TFLOP/s nominal)
 FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12  # 152 SMs x 2.07 GHz x 128 FP32 lanes x 2 (FMA) = 80.5 TFLOP/s
 DF_OPS_PER_FMA = 12                            # FP32 instructions of one double-float multiply-add (df_fma)
+WHY_NOT_4 = ("workload 4 (512 LMOs, n_vir 3000) also fits one GPU, but one step takes several seconds, so the "
+             "driver's step counts would exceed the minute-scale timed budget; it is measured with --workload 4")
+
+# DRAM traffic per launch of the residual kernel (dram__bytes_read.sum + dram__bytes_write.sum), from the ncu capture
+# summarised in profiles/, keyed by workload and by the SHA-256 prefix of the kernel's source file at capture time:
+# a kernel changed since the capture reports null.
+NCU_TRAFFIC = {
+    # profiles/residual_mixed_full_cube48.md: 5.54 GB over 1585 clusters, scaled to workload 2's 14340 clusters
+    (2, 2, "8fa4e15ceb0a99f1"): (3.107834e9 + 2.431217e9) * 14340 / 1585,
+}
 
 
 def parse():
@@ -40,8 +54,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", default="bf16x4", choices=["fp64", "tf32x3", "bf16x4"],
+    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--precision", default="bf16x4", choices=["fp64", "bf16x4"],
                     help="path whose throughput is the headline value; the FP64 path is always timed beside it")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the FP64 comparison path (after one warm-up step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -53,13 +70,18 @@ def dist_env():
     return r, w, lr
 
 
-def workload_config(prm, p):
-    return {"workload": f"MBE(3) energy+gradient, {p.n_occ} LMOs on a 1.5 A chain, n_vir={p.n_vir}, "
-                        f"n_aux={p.n_aux}, l_osv=1e-4 capped at {prm.n_osv_max} OSVs, pair/triple cutoffs "
-                        f"{prm.r2b}/{prm.r3b} A",
-            "n_occ": p.n_occ, "n_vir": p.n_vir, "n_aux": p.n_aux, "mbe_order": prm.mbe_order,
-            "precision": {0: "fp64", 1: "tf32x3", 2: "bf16x4"}[prm.precision],
-            "l2": f"inputs larger than L2 (B = {p.B.nbytes / 1e6:.0f} MB > 129 MB)"}
+def workload_config(k, prm, p):
+    from paper_2106_06149_gb300.synth import WORKLOADS
+    desc = WORKLOADS[k][0]
+    cfg = {"workload": f"workload {k}: {desc}; MBE(3) energy+gradient per step, l_osv {prm.l_osv:g} capped at "
+                       f"{prm.n_osv_max} OSVs, pair/triple cutoffs {prm.r2b}/{prm.r3b} A",
+           "n_occ": p.n_occ, "n_vir": p.n_vir, "n_aux": p.n_aux, "mean_fitting_domain": float(np.diff(p.aux_ptr).mean()),
+           "mbe_order": prm.mbe_order, "precision": {0: "fp64", 2: "bf16x4"}[prm.precision],
+           "B_dtype": str(p.B.dtype),
+           "l2": f"inputs larger than L2 (B = {p.B.nbytes / 1e6:.0f} MB > 129 MB)"}
+    if k != 4:
+        cfg["why_not_workload_4"] = WHY_NOT_4
+    return cfg
 
 
 # ------------------------------------------------------------------------------------------ clocks
@@ -126,11 +148,15 @@ def run_gpu(args):
     if world > 1:
         torch.distributed.barrier()
     osvmbe.load()
-    p, prm = workload(WORKLOAD)
+    p, prm = workload(args.workload)
     if rank > 0:   # each rank: an independent geometry of the same workload (own seed)
-        _, pk, _ = WORKLOADS[WORKLOAD]
+        _, pk, _ = WORKLOADS[args.workload]
+        pk = dict(pk)
+        if pk.get("radius") == "mean2000":
+            from paper_2106_06149_gb300.synth import _radius_for_mean_domain
+            pk["radius"] = _radius_for_mean_domain(pk["seed"], pk["n_occ"], pk["box"], 1.4, pk["n_aux"], 2000.0)
         p = make_problem(**{**pk, "seed": pk["seed"] + 1000 * rank})
-    prec = {"fp64": 0, "tf32x3": 1, "bf16x4": 2}[args.precision]
+    prec = {"fp64": 0, "bf16x4": 2}[args.precision]
     stream = torch.cuda.current_stream()
     dp = osvmbe.DeviceProblem.from_host(p)
     ctx = osvmbe.Context(stream)
@@ -159,20 +185,20 @@ def run_gpu(args):
         return t0.elapsed_time(t1) / k
 
     warm = max(args.warmup, 3)
-    # ---- the plain FP64 GPU path (reference point of the mixed path)
+    # ---- the plain FP64 GPU path (reference point of the mixed path): one warm-up step, then fp64_steps timed
     prm.precision = 0
-    for _ in range(warm):
-        step()
-    fp64_ms = timed_steps(args.steps)
+    step()
+    fp64_ms = timed_steps(max(args.fp64_steps, 1))
     E64, _ = ctx.energy()
     flops64 = ctx.residual_flops()
     dB.zero_()
+    dF.zero_()
     ctx.profile(True)
     step()
     torch.cuda.synchronize()
     stages64 = ctx.profile_read()
     ctx.profile(False)
-    dB64 = dB.clone()
+    dB64, dF64 = dB.clone(), dF.clone()
     # ---- the headline path
     prm.precision = prec
     for _ in range(warm):
@@ -185,9 +211,12 @@ def run_gpu(args):
     flops_step = flops64
     E, E_lin = ctx.energy()
     dB.zero_()
+    dF.zero_()
     step()
     torch.cuda.synchronize()
-    grad_diff = float((dB - dB64).abs().max())
+    grad_diff = float((dB.double() - dB64.double()).abs().max())
+    gradF_diff = float((dF - dF64).abs().max())
+    del dB64, dF64
 
     # ---- timed region (device-resident inputs)
     ctx.profile(True)
@@ -228,17 +257,17 @@ def run_gpu(args):
     h2d = hB.numel() * hB.element_size() + hF.numel() * 8 + he.numel() * 8
     d2h = 8 + odB.numel() * odB.element_size() + odF.numel() * 8
 
-    # ---- roofline of the dominant stage
+    # ---- roofline of the residual kernel (the metric's work) and the stage table
     total_stage = sum(v[0] for v in stages.values())
-    dom = max(stages.items(), key=lambda kv: kv[1][0])
-    roof = roofline(dom, stages, flops_step, p, prm, ctx.adjoint_flops(), prec, ctx.residual_work())
+    roof = residual_roofline(stages, flops_step, prec, ctx.residual_work(), args.workload)
     roof_tc = tensor_roofline(stages, p, prm) if prec > 0 else None
+    dom = max(stages.items(), key=lambda kv: kv[1][0])
 
     out = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {0: "f64", 1: "tf32x3+f64", 2: "bf16x4+f64"}[prec], "data": "synthetic",
-        "config": workload_config(prm, p),
+        "warmup": warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {0: "f64", 2: "bf16x4+f32+f64"}[prec], "data": "synthetic",
+        "config": workload_config(args.workload, prm, p),
         "gradient_s_per_geometry": ms / 1e3,
         "residual_solve_tflops": flops_step / (stages["residual"][0] / stages["residual"][1] * 1e-3) / 1e12
         if "residual" in stages else None,
@@ -248,10 +277,12 @@ def run_gpu(args):
                                 "clusters": len(ctx.cluster_info()[0])},
         "fp64_stage_ms": {k: v[0] for k, v in stages64.items()},
         "energy_Eh": E, "energy_linear_Eh": E_lin,
-        "fp64_ms_per_step": fp64_ms, "mixed_vs_fp64": fp64_ms / ms, "energy_fp64_Eh": E64,
-        "abs_dE_vs_fp64_Eh": abs(E - E64), "max_abs_dgradB_vs_fp64": grad_diff,
+        "fp64_ms_per_step": fp64_ms, "fp64_steps_timed": max(args.fp64_steps, 1), "mixed_vs_fp64": fp64_ms / ms,
+        "energy_fp64_Eh": E64, "abs_dE_vs_fp64_Eh": abs(E - E64), "max_abs_dgradB_vs_fp64": grad_diff,
+        "max_abs_dgradF_vs_fp64": gradF_diff,
         "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
         "stage_share": {k: v[0] / total_stage for k, v in stages.items()},
+        "dominant_stage": dom[0],
         "roofline": roof,
         "roofline_tensor_gemm": roof_tc,
         "e2e": {"value": flops_all / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
@@ -260,7 +291,7 @@ def run_gpu(args):
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(sample_every=4, repeats=1)
+        out["cpu_baseline"] = cpu_baseline(args.workload)
     if world > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
@@ -288,134 +319,136 @@ def ctypes_launches(osvmbe):
     return n.value
 
 
-def stage_flops(name, p, prm, flops_step, adj_flops=None):
-    """Algorithmic FLOPs of one launch of a stage (FP64 work of the method, padding excluded)."""
-    nv, na, n, nm = p.n_vir, p.n_aux, p.n_occ, prm.n_osv_max if prm.n_osv_fixed <= 0 else prm.n_osv_fixed
-    d = np.linalg.norm(p.centres[:, None, :] - p.centres[None, :, :], axis=-1)
-    nb = (d <= prm.r2b).sum(axis=1)            # |{i} U N(i)| of the half transforms
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except Exception:
+        return fallback, "fallback"
+
+
+def source_sha(rel):
+    with open(os.path.join(ROOT, "paper_2106_06149_gb300", "csrc", rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def residual_roofline(stages, flops_step, prec, work, wl):
+    """The residual kernel (one launch per step: k_residual_mixed, or k_residual on the FP64 path) against the
+    dense BF16 tensor peak measured on this machine, sustained figure (the kernel runs inside a long step):
+    achieved = algorithmic residual FLOPs of the step / the kernel's average CUDA-event duration over the timed
+    region.  The FP32-pipe view of the mixed kernel (its FP32 evaluations plus 12 FP32 instructions per
+    double-float multiply-add of its FP64-accurate evaluations, against 152 SMs x 128 lanes x 2 x 2.07 GHz) is
+    kept beside it."""
+    if "residual" not in stages:
+        return None
+    ms_total, calls = stages["residual"]
+    avg_ms = ms_total / calls
+    peak, src = measured_peak("bf16_tflops_sustained", 1700.0)
+    ach = flops_step / (avg_ms * 1e-3) / 1e12
+    sha = source_sha("residual.cu")
+    traffic = NCU_TRAFFIC.get((wl, prec, sha))
+    out = {"bound": "tensor", "kernel": "k_residual_mixed" if prec else "k_residual", "stage": "residual",
+           "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+           "avg_launch_ms": avg_ms, "launches": calls, "algorithmic_flops_per_launch": flops_step,
+           "peak_note": f"dense BF16, {src} (MEASURED_PEAKS.json bf16_tflops_sustained)",
+           "algorithmic_note": "sum over clusters of (FP64 solve's residual evaluations) x sum over coupling terms "
+                               "of 2 (r_p r_q^2 + r_p^2 r_q); padding and the mixed solve's extra FP32 "
+                               "iterations are not counted",
+           "kernel_source_sha": sha}
+    if prec and work is not None:
+        f32, f64 = work
+        pipe = f32 + DF_OPS_PER_FMA * f64
+        out["fp32_pipe_view"] = {"achieved": pipe / (avg_ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                                 "frac": pipe / (avg_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                                 "fp32_evaluation_flops": f32, "fp64_accurate_evaluation_flops": f64,
+                                 "note": "FP32 pipe peak from unit counts and the 2.07 GHz maximum clock"}
+    elif not prec:
+        out["fp64_pipe_view"] = {"achieved": ach, "peak": FP64_PEAK_TFLOPS, "frac": ach / FP64_PEAK_TFLOPS,
+                                 "note": "FP64 units, 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    return out
+
+
+def stage_flops(name, p, prm):
+    """Algorithmic FLOPs of one launch of a dense stage (FP64 work of the method, padding excluded)."""
+    nv = p.n_vir
     a = np.diff(p.aux_ptr)
-    if name == "residual":
-        return flops_step
-    if name == "adj_clusters":
-        return adj_flops
     if name == "tkk_gram":
         return float(np.sum(2.0 * nv * nv * a))
-    if name == "half_transform":
-        return float(np.sum(2.0 * nb * nm * nv * a))
-    if name == "osv_eigh":
-        return n * (4.0 / 3.0) * nv ** 3                 # Householder tridiagonalisation (bisection and kept-vector work are O(n^2))
     return None
 
 
 def tensor_roofline(stages, p, prm):
-    """The tcgen05 GEMM of the T_kk Gram products: issued tensor FLOPs vs the measured dense BF16 peak (each useful
-    multiply-add costs 13 BF16 slice products in the exact-slice mode, 3 TF32 products (at half the BF16 rate)
-    in the split-TF32 mode); useful FLOPs reported beside it.  The stage time includes the slicing passes."""
+    """The tcgen05 exact-slice GEMM of the T_kk Gram products: useful FLOPs (2 n_vir^2 a_k per LMO) per stage
+    launch against the measured dense BF16 peak (burst: the stage is one batch), with the issued slice products
+    (13 BF16 products per useful multiply-add) beside it.  The stage time includes the slicing passes."""
     if "tkk_gram" not in stages:
         return None
     ms_total, calls = stages["tkk_gram"]
     avg = ms_total / calls
-    useful = stage_flops("tkk_gram", p, prm, 0.0)
-    mult = 13.0 if prm.precision == 2 else 6.0
-    peak = measured_peak("bf16_tflops", 1900.0)
-    issued = useful * mult / (avg * 1e-3) / 1e12
-    return {"bound": "tensor", "stage": "tkk_gram", "kernel": "k_oz_gemm" if prm.precision == 2 else "k_gemm_tf32x3",
-            "achieved": issued, "peak": peak, "unit": "TFLOP/s", "frac": issued / peak, "traffic": None,
-            "useful_tflops": useful / (avg * 1e-3) / 1e12, "avg_launch_ms": avg,
-            "peak_note": "measured dense bf16 (burst); achieved counts issued BF16-equivalent slice products"}
-
-
-def measured_peak(key, fallback):
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)[key])
-    except Exception:
-        return fallback
-
-
-def roofline(dom, stages, flops_step, p, prm, adj_flops=None, prec=0, work=None):
-    """ALU roofline of the dominant stage.  FP64 path: algorithmic FLOPs against the FP64 units.  Mixed paths:
-    the FP32-pipe work those FLOPs become (FP32 residual evaluations as they are; every FP64-accurate multiply-add
-    as a double-float one, DF_OPS_PER_FMA FP32 instructions) against the FP32 pipe; both from unit counts and the
-    2.07 GHz maximum clock.  Index arithmetic, loads and conversions are not counted, so the issue-slot use is
-    higher than frac."""
-    name, (ms_total, calls) = dom
-    avg_ms = ms_total / calls
-    flops = stage_flops(name, p, prm, flops_step, adj_flops)
-    base = {"bound": "alu", "stage": name, "unit": "TFLOP/s", "traffic": None, "avg_launch_ms": avg_ms}
-    if not flops:
-        return dict(base, achieved=None, peak=FP64_PEAK_TFLOPS if prec == 0 else FP32_PEAK_TFLOPS, frac=None)
-    if prec == 0:
-        ach = flops / (avg_ms * 1e-3) / 1e12
-        return dict(base, achieved=ach, peak=FP64_PEAK_TFLOPS, frac=ach / FP64_PEAK_TFLOPS,
-                    algorithmic_flops_per_launch=flops,
-                    peak_note="FP64 CUDA cores, 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal 1.25 TFLOP/s)")
-    nm = prm.n_osv_max if prm.n_osv_fixed <= 0 else prm.n_osv_fixed
-    if name == "adj_clusters" and 2 * nm <= 80:
-        # tensor-core partials: 13 BF16 digit products per FP64-accurate product, M = 128 rows issued for <= 80
-        issued = 13.0 * flops * 128.0 / 80.0
-        ach = issued / (avg_ms * 1e-3) / 1e12
-        peak = measured_peak("bf16_tflops", 1900.0)
-        return dict(base, bound="tensor", achieved=ach, peak=peak, frac=ach / peak, algorithmic_flops_per_launch=flops,
-                    issued_bf16_flops_per_launch=issued, fp64_equivalent_tflops=flops / (avg_ms * 1e-3) / 1e12,
-                    peak_note="measured dense BF16 (MEASURED_PEAKS.json, burst); achieved counts the issued digit "
-                              "products (13 per FP64-accurate product, M padded to 128)")
-    if name == "residual" and work is not None:
-        f32, f64 = work
-        pipe = f32 + DF_OPS_PER_FMA * f64
-        detail = {"fp32_evaluation_flops": f32, "fp64_accurate_evaluation_flops": f64}
-    else:
-        pipe = DF_OPS_PER_FMA * flops   # every other dominant candidate (the cluster adjoint) is double-float
-        detail = {}
-    ach = pipe / (avg_ms * 1e-3) / 1e12
-    return dict(base, achieved=ach, peak=FP32_PEAK_TFLOPS, frac=ach / FP32_PEAK_TFLOPS,
-                algorithmic_flops_per_launch=flops, fp32_pipe_flops_per_launch=pipe,
-                fp64_equivalent_tflops=flops / (avg_ms * 1e-3) / 1e12,
-                peak_note="FP32 pipe, 152 SMs x 128 lanes x 2 flop x 2.07 GHz; double-float multiply-add = "
-                          f"{DF_OPS_PER_FMA} FP32 instructions", **detail)
+    useful = stage_flops("tkk_gram", p, prm)
+    peak, src = measured_peak("bf16_tflops", 1900.0)
+    ach = useful / (avg * 1e-3) / 1e12
+    return {"bound": "tensor", "stage": "tkk_gram", "kernel": "k_oz_gemm (+ k_oz_scales, k_oz_slice)",
+            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "issued_bf16_tflops": 13.0 * ach, "avg_launch_ms": avg,
+            "peak_note": f"dense BF16 burst, {src}; achieved counts useful FP64-accurate FLOPs"}
 
 
 # ------------------------------------------------------------------------------------- CPU baseline
-def oracle_sample(sample_every):
-    """Oracle energy + gradient of every `sample_every`-th cluster of the bench workload (OSVs for all LMOs)."""
+def _sample_clusters(k, n):
+    """n clusters of workload k spread over the orders (triples, pairs, singles in turn), deterministic."""
+    import oracle
+    from paper_2106_06149_gb300.synth import workload
+    p, prm = workload(k)
+    cl = oracle.select_clusters(p.centres, prm.r2b, prm.r3b, prm.mbe_order)
+    by = [[c for c in cl if len(c) == m] for m in (1, 2, 3)]
+    pick = []
+    for t in range(n):
+        lst = by[2 - t % 3] or by[0]
+        pick.append(lst[(t * 7919) % len(lst)])
+    return p, prm, pick, len(cl)
+
+
+def oracle_sample(p, prm, sample):
+    """Oracle energy + gradient of each sampled cluster on its own restricted problem (OSVs of its LMOs only), and
+    the residual model FLOPs of the sample (same formula as the library: stored pairs, r = kept OSV dims)."""
     import torch
 
     import oracle
-    from paper_2106_06149_gb300.synth import workload
+    from oracle.subproblem import restrict
 
-    p, prm = workload(WORKLOAD)
-    cl = oracle.select_clusters(p.centres, prm.r2b, prm.r3b, prm.mbe_order)
-    sample = cl[::sample_every]
     t0 = time.perf_counter()
-    g = oracle.gradient(p, prm, clusters=sample)
-    dt = time.perf_counter() - t0
-    # residual model FLOPs of the sample, same formula as the library (stored pairs, r = kept dims)
     flops = 0.0
     for c in sample:
+        q = restrict(p, c)
+        m = len(c)
+        g = oracle.gradient(q, prm, clusters=[tuple(range(m))])
+        it = g["iters"][tuple(range(m))]
         r = {}
-        for a in c:
-            for b in c:
-                if a <= b:
-                    r[(a, b)] = g["n_osv"][a] + (g["n_osv"][b] if a != b else 0)
+        for a in range(m):
+            for b in range(a, m):
+                r[(a, b)] = g["n_osv"][a] + (g["n_osv"][b] if a != b else 0)
         per = 0.0
         for (i, j), rp in r.items():
-            for k in c:
-                if k != j:
-                    rq = r[(min(i, k), max(i, k))]
+            for kk in range(m):
+                if kk != j:
+                    rq = r[(min(i, kk), max(i, kk))]
                     per += 2.0 * (rp * rq * rq + rp * rp * rq)
-                if k != i:
-                    rq = r[(min(k, j), max(k, j))]
+                if kk != i:
+                    rq = r[(min(kk, j), max(kk, j))]
                     per += 2.0 * (rp * rq * rq + rp * rp * rq)
-        flops += per * (g["iters"][c] + 1)
-    return flops, dt, len(sample), len(cl), torch.get_num_threads()
+        flops += per * (it + 1)
+    return flops, time.perf_counter() - t0, torch.get_num_threads()
 
 
-def cpu_baseline(sample_every=4, repeats=1):
-    flops, dt, ns, nc, cores = oracle_sample(sample_every)
-    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-            "seconds": dt,
-            "sample": f"oracle energy+gradient of every {sample_every}th cluster ({ns} of {nc}) of the bench "
-                      f"workload, OSVs of all LMOs, FP64, torch CPU with {cores} threads"}
+def cpu_baseline(k, n=3):
+    import torch
+    torch.set_num_threads(len(os.sched_getaffinity(0)))
+    p, prm, sample, ncl = _sample_clusters(k, n)
+    flops, dt, cores = oracle_sample(p, prm, sample)
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "seconds": dt,
+            "sample": f"oracle energy+gradient of {len(sample)} clusters of the {ncl} of workload {k} (one per order, "
+                      f"each on its own LMOs: OSVs of those LMOs only), FP64, torch CPU with {cores} threads"}
 
 
 def run_reference(args):
@@ -424,22 +457,24 @@ def run_reference(args):
         return
     import torch
     torch.set_num_threads(len(os.sched_getaffinity(0)))
-    for _ in range(args.warmup):
-        oracle_sample(32)
+    k = args.workload
+    p, prm, sample, ncl = _sample_clusters(k, args.warmup + args.steps)
+    for t in range(args.warmup):
+        oracle_sample(p, prm, [sample[t]])
     tot_f, tot_t = 0.0, 0.0
-    for _ in range(args.steps):
-        f, dt, ns, nc, cores = oracle_sample(32)
+    for t in range(args.steps):
+        f, dt, cores = oracle_sample(p, prm, [sample[args.warmup + t]])
         tot_f += f
         tot_t += dt
     value = tot_f / tot_t / 1e12
-    from paper_2106_06149_gb300.synth import workload
-    p, prm = workload(WORKLOAD)
+    prm.precision = {"fp64": 0, "bf16x4": 2}[args.precision]   # the GPU arm's config, precision field included
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(prm, p),
+           "config": workload_config(k, prm, p),
            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "kind": "oracle", "cores": cores,
-                            "sample": f"oracle energy+gradient of every 32nd cluster ({ns} of {nc}) per step"},
+                            "sample": f"per step, the oracle energy+gradient of one cluster of the {ncl} of workload "
+                                      f"{k} (triples, pairs and singles in turn), on its own LMOs"},
            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 

@@ -23,7 +23,7 @@ Method (arXiv 2106.06149, Liang & Yang):
     upper-right block of Eq. 4) and their energy; the screened MBE energy that adds them to the strong clusters.
   * Posterior correction (Sec. 3): Eq. 4 at the collective amplitudes over each pair's cluster LMOs, one step.
 
-Readings of points where the paper is silent (each listed in the design doc):
+Readings of points where the paper is silent:
   * ordered pairs (i, j) and (j, i) are separate pair equations; the pair ii uses the domain Q_i only;
   * each pair inside a cluster uses its own domain (Q_i Q_j), never the union over the cluster;
   * the OSV-basis residual is preconditioned in an orthonormal pseudo-canonical basis of the pair domain,

@@ -29,7 +29,8 @@ def test_reference_arm_prints_the_contract_line():
         assert isinstance(d[k], t), k
     assert d["impl"] == "reference" and d["value"] > 0 and d["vs_baseline"] is None
     assert d["steps"] == 1 and d["n_gpus"] == 1 and d["data"] == "synthetic"
-    assert "workload" in d["config"] and "64 LMOs" in d["config"]["workload"]
+    assert "workload" in d["config"] and "256 LMOs" in d["config"]["workload"]
+    assert d["config"]["precision"] == "bf16x4"        # the GPU arm's config, field for field
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     e2e = d["e2e"]
