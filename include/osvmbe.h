@@ -139,6 +139,17 @@ osv_status cluster_residual_solve(osv_ctx *ctx, int *n_iter_out, int32_t *cluste
  * (MBE(3), Eqs. 28-32). */
 osv_status mbe3_combine(osv_ctx *ctx);
 
+/* Weak 2b clusters by the one-block scheme (Sec. 2.2.2), after cluster_residual_solve: every pair ij (i < j) with
+ * l_discard <= s2b[i][j] <= l2b that belongs to no selected cluster is a weak pair.  Its amplitudes are the upper-
+ * right block X of T_(ij,ij) (rows: the OSVs of i, columns: those of j), solving the upper-right block of the 2b
+ * cluster's Eq. 4 with the pairs ii and jj held at their 1b cluster amplitudes (directly, in the pseudo-canonical
+ * bases of ii and jj); its energy is the Hylleraas functional (Eq. 3) of the ordered pairs ij and ji.
+ * *E_weak (HOST) = the sum over weak pairs, to be added to energy()'s E (the strong clusters); *n_weak (HOST, may
+ * be NULL) = their number.  Pairs with s2b below l_discard are dropped.  No weak pairs below mbe_order 2.  The
+ * cross half transforms Q_j B_i, Q_i B_j run on the dense back end, the per-pair blocks in FP64.  Synchronises. */
+osv_status weak_pairs_energy(osv_ctx *ctx, const double *s2b, double l2b, double l_discard, double *E_weak,
+                             int *n_weak);
+
 /* One-step posterior correction over the collective amplitudes (Sec. 3, the estimate beyond MBE(3)), after
  * mbe3_combine.  For every pair ij of a selected cluster, Eq. 4 is evaluated at the collective amplitudes T with
  * k running over the LMOs of every selected cluster that holds both i and j, and one step of the cluster

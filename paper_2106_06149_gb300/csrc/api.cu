@@ -1112,6 +1112,141 @@ osv_status posterior_correction(osv_ctx *c, double *E_global, double *E_correcte
     return OSV_OK;
 }
 
+osv_status weak_pairs_energy(osv_ctx *c, const double *s2b, double l2b, double l_discard, double *E_weak,
+                             int *n_weak) {
+    if (!c || !E_weak) return c ? c->fail(OSV_ERR_INVALID, "E_weak is NULL") : OSV_ERR_INVALID;
+    if (!s2b || !std::isfinite(l2b) || !std::isfinite(l_discard))
+        return c->fail(OSV_ERR_INVALID, "s2b must be non-NULL and l2b, l_discard finite");
+    if (!c->solved) return c->fail(OSV_ERR_INVALID, "cluster_residual_solve must precede weak_pairs_energy");
+    const int n = c->n_occ, nm = c->nmax, nv = c->n_vir;
+    *E_weak = 0.0;
+    if (n_weak) *n_weak = 0;
+    if (c->prm.mbe_order < 2 || c->prm.mbe_order > 3) return OSV_OK;   // no weak 2b clusters below MBE(2)
+    // weak pairs: l_discard <= s2b_ij <= l2b (i < j), not a pair of a selected cluster
+    std::vector<std::pair<int, int>> wl;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const double x = s2b[(size_t)i * n + j];
+            if (!std::isfinite(x)) return c->fail(OSV_ERR_INVALID, "non-finite s2b entry");
+            if (x >= l_discard && x <= l2b && c->pid(i, j) < 0) wl.push_back({i, j});
+        }
+    const int nw = (int)wl.size();
+    if (n_weak) *n_weak = nw;
+    if (nw == 0) return OSV_OK;
+    cudaSetDevice(c->device);
+    const bool full = full_domains(c);
+    const long long nn = (long long)nm * nm;
+    // device memory of this call: the cross half transforms Q_j B_i and Q_i B_j, the blocks and the workspaces
+    std::vector<long long> yoff(nw + 1, 0);
+    for (int w = 0; w < nw; ++w) yoff[w + 1] = yoff[w] + (long long)nm * (c->a_of(wl[w].first) + c->a_of(wl[w].second));
+    std::vector<int> kmap;
+    std::vector<std::pair<size_t, int>> kref(nw);
+    if (!full) {
+        std::vector<int> pi, pj;
+        for (int w = 0; w < nw; ++w) {
+            common_domain(c, wl[w].first, wl[w].second, pi, pj);
+            kref[w] = {kmap.size(), (int)pi.size()};
+            kmap.insert(kmap.end(), pi.begin(), pi.end());
+            kmap.insert(kmap.end(), pj.begin(), pj.end());
+        }
+    }
+    double *Y = nullptr, *blk = nullptr, *work = nullptr, *E = nullptr;
+    int *dmap = nullptr;
+    WeakPair *dwp = nullptr;
+    GemmBatch gy, gk, gsf;
+    osv::TcTiles oy, ok;
+    auto cleanup = [&]() {
+        for (void *p : {(void *)Y, (void *)blk, (void *)work, (void *)E, (void *)dmap, (void *)dwp})
+            if (p) cudaFree(p);
+        gemm_batch_free(gy);
+        gemm_batch_free(gk);
+        gemm_batch_free(gsf);
+        osv::tc_tiles_free(oy);
+        osv::tc_tiles_free(ok);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&Y, std::max<long long>(yoff[nw], 1) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&blk, 4 * nw * nn * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&work, 7 * nw * nn * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&E, nw * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&dmap, std::max<size_t>(kmap.size(), 1) * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&dwp, nw * sizeof(WeakPair))) != cudaSuccess) {
+        cleanup();
+        return c->cuda_fail(e, "weak pairs");
+    }
+    if (!kmap.empty() && (e = cudaMemcpy(dmap, kmap.data(), kmap.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cleanup();
+        return c->cuda_fail(e, "weak pairs");
+    }
+    std::vector<WeakPair> h(nw);
+    for (int w = 0; w < nw; ++w) {
+        const int i = wl[w].first, j = wl[w].second;
+        const long long ai = c->a_of(i), aj = c->a_of(j);
+        double *Yij = Y + yoff[w], *Yji = Yij + (long long)nm * ai;   // Q_j B_i (nm x a_i), Q_i B_j (nm x a_j)
+        const double *Qi = c->Q + (long long)i * nm * nv, *Qj = c->Q + (long long)j * nm * nv;
+        gy.add(gemm(nm, (int)ai, nv, Qj, nv, 0, c->B64 + c->b_off(i), ai, 0, Yij, ai));
+        gy.add(gemm(nm, (int)aj, nv, Qi, nv, 0, c->B64 + c->b_off(j), aj, 0, Yji, aj));
+        double *Kur = blk + 4 * w * nn, *Kll = Kur + nn, *S = Kll + nn, *F = S + nn;
+        const double *Xi = c->W + c->w_off[i] + (long long)c->slot_of(i, i) * nm * ai;   // Q_i B_i
+        const double *Xj = c->W + c->w_off[j] + (long long)c->slot_of(j, j) * nm * aj;   // Q_j B_j
+        GemmDesc g1 = gemm(nm, nm, full ? c->n_aux : 0, Xi, ai, 0, Xj, aj, 1, Kur, nm);
+        GemmDesc g2 = gemm(nm, nm, full ? c->n_aux : 0, Yij, ai, 0, Yji, aj, 1, Kll, nm);
+        if (!full) {
+            g1.K = g2.K = kref[w].second;
+            g1.k_idx_a = g2.k_idx_a = dmap + kref[w].first;
+            g1.k_idx_b = g2.k_idx_b = dmap + kref[w].first + kref[w].second;
+        }
+        gk.add(g1);
+        gk.add(g2);
+        gsf.add(gemm(nm, nm, nv, Qi, nv, 0, Qj, nv, 1, S, nm));
+        gsf.add(gemm(nm, nm, nv, Qi, nv, 0, c->Qe + (long long)j * nm * nv, nv, 1, F, nm));
+        const PairInfo &Pi = c->pinfo.h[c->pid(i, i)], &Pj = c->pinfo.h[c->pid(j, j)];
+        WeakPair &W = h[w];
+        W.i = i;
+        W.j = j;
+        W.Kur = Kur;
+        W.Kll = Kll;
+        W.S = S;
+        W.F = F;
+        W.Vi = c->V + Pi.off;
+        W.Vj = c->V + Pj.off;
+        W.ei = c->pe + Pi.e_off;
+        W.ej = c->pe + Pj.e_off;
+        W.ri = c->rdim + c->pid(i, i);
+        W.rj = c->rdim + c->pid(j, j);
+        W.Ti = c->Tslot + c->slots.h[c->cinfo.h[i].slot0].t_off;   // the 1b cluster {i} is cluster i
+        W.Tj = c->Tslot + c->slots.h[c->cinfo.h[j].slot0].t_off;
+        W.work = work + 7 * w * nn;
+    }
+    const bool mixed = c->prm.precision == OSV_MIXED_BF16X4;
+    e = cudaMemcpy(dwp, h.data(), nw * sizeof(WeakPair), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = gemm_batch_upload(gy);
+    if (e == cudaSuccess) e = gemm_batch_upload(gk);
+    if (e == cudaSuccess) e = gemm_batch_upload(gsf);
+    if (e == cudaSuccess && mixed) {
+        if ((e = bf16x4_batch_prepare(gy, oy)) == cudaSuccess && (e = bf16x4_batch_prepare(gk, ok)) == cudaSuccess)
+            e = c->oz_reserve((size_t)std::max(oy.scratch_bytes, ok.scratch_bytes));
+    }
+    if (e == cudaSuccess) {
+        StageTimer t(*c, "weak_pairs");
+        if ((e = c->run_dense(gy, oy)) == cudaSuccess && (e = c->run_dense(gk, ok)) == cudaSuccess &&
+            (e = c->run_small(gsf)) == cudaSuccess)
+            e = launch_weak_pairs(dwp, nw, nm, c->focc, c->n_occ, E, c->stream);
+    }
+    std::vector<double> Eh(nw);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(Eh.data(), E, nw * sizeof(double), cudaMemcpyDeviceToHost);
+    cleanup();
+    if (e != cudaSuccess) return c->cuda_fail(e, "weak pairs");
+    osv_status st = device_error(c);
+    if (st != OSV_OK) return st;
+    double sum = 0.0;
+    for (double x : Eh) sum += x;
+    *E_weak = sum;
+    if (!std::isfinite(sum)) return c->fail(OSV_ERR_NUMERIC, "weak-pair energy is not finite");
+    return OSV_OK;
+}
+
 osv_status osv_pair_amplitudes(osv_ctx *c, int i, int j, double *t_out) {
     if (!c || !t_out) return OSV_ERR_INVALID;
     if (!c->combined) return c->fail(OSV_ERR_INVALID, "mbe3_combine must precede osv_pair_amplitudes");

@@ -49,6 +49,18 @@ struct ClusterInfo {
     int size;               // number of LMOs
 };
 
+// One weak pair ij (one-block scheme, Sec. 2.2.2): its n_max x n_max blocks (row-major, leading dimension n_max)
+// and a 7 n_max^2 workspace.  S = Q_i Q_j^T, F = Q_i diag(eps) Q_j^T (rows of Q = OSVs), K_ur = Q_i (ia|jb) Q_j^T,
+// K_ll = Q_j (ia|jb) Q_i^T; V, e, r: the pseudo-canonical bases of the pairs ii and jj; Ti, Tj: the 1b cluster
+// amplitudes of ii and jj in those bases.
+struct WeakPair {
+    int i, j;
+    const double *Kur, *Kll, *S, *F;
+    const double *Vi, *Vj, *ei, *ej, *Ti, *Tj;
+    const int *ri, *rj;
+    double *work;
+};
+
 // Everything the residual / adjoint kernels read.
 struct SolveArgs {
     const ClusterInfo *clusters;

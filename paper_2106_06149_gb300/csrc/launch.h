@@ -21,6 +21,9 @@ cudaError_t launch_pair_x(const PairInfo *pairs, int npairs, const double *Ut, c
 cudaError_t launch_clean_w(const PairInfo *pairs, int npairs, const int *rdim, double *Wt, double *e,
                            cudaStream_t s);
 cudaError_t launch_residual(const SolveArgs &a, int nclusters, bool mixed, cudaStream_t s);
+// one-block amplitudes and energies of weak pairs (E per pair)
+cudaError_t launch_weak_pairs(const WeakPair *wp, int nweak, int nm, const double *focc, int n_occ, double *E,
+                              cudaStream_t s);
 // one-step posterior correction: R1 = R(Tc), T2 = Tc - R1 / D, R2 = R(T2), per-pair norms (rnorm[0, np) of R1,
 // rnorm[np, 2np) of R2) and pair functionals E1 (at Tc), E2 (at T2)
 cudaError_t launch_posterior(const SolveArgs &a, int npairs, const double *Tc, double *R1, double *T2, double *R2,

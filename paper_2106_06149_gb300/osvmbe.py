@@ -24,7 +24,7 @@ EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv
            "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops",
            "osv_solve_counts", "osv_residual_work", "osv_set_wait_budget",
            "osv_pair_amplitudes", "osv_overlap_metric", "clusters_build_osv",
-           "posterior_correction"]
+           "posterior_correction", "weak_pairs_energy"]
 
 
 class OsvParams(ctypes.Structure):
@@ -80,6 +80,7 @@ def load(path=LIB_PATH):
         "osv_overlap_metric": ([V, P(OsvProblem), P(OsvParams), V], I),
         "clusters_build_osv": ([V, P(OsvProblem), P(OsvParams), V, D, D, V], I),
         "posterior_correction": ([V, P(D), P(D), P(D)], I),
+        "weak_pairs_energy": ([V, V, D, D, P(D), P(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -238,6 +239,14 @@ class Context:
         el = ctypes.c_double()
         _check(load().energy(self.h, ctypes.byref(e), ctypes.byref(el)), self.h)
         return e.value, el.value
+
+    def weak_pairs_energy(self, s2b, l2b, l_discard=1e-7):
+        """One-block energies of the weak pairs (Sec. 2.2.2): (E_weak, number of weak pairs)."""
+        s = np.ascontiguousarray(s2b, dtype=np.float64)
+        e, n = ctypes.c_double(), ctypes.c_int()
+        _check(load().weak_pairs_energy(self.h, _ptr(s), float(l2b), float(l_discard), ctypes.byref(e),
+                                        ctypes.byref(n)), self.h)
+        return e.value, n.value
 
     def posterior_correction(self):
         """One-step posterior correction (Sec. 3): dict(E_global, E_corrected, dR_max)."""
