@@ -206,6 +206,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     flops_exec = ctx.residual_flops()
     upd32, ev64, uncv = ctx.solve_counts()
+    tuned = ctx.autotune_report()   # launch shapes picked when the mixed plan was built (first warm-up step)
     # the metric's work per step: the residual FLOPs of the FP64 solve to tol (the iterations the problem
     # needs); the mixed solve's own count (FP32 iterations + FP64 evaluations) is reported beside it
     flops_step = flops64
@@ -289,6 +290,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        "autotune": tuned,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload)

@@ -174,6 +174,18 @@ osv_status energy(osv_ctx *ctx, double *E_out, double *E_linear_out);
  * OSV_ERR_NUMERIC if a device step of the build, the solve or the adjoint reported one. */
 osv_status gradient_backward(osv_ctx *ctx, double dE_scale, void *dE_dB, double *dE_dFocc);
 
+/* Autotuner of the launch shapes (no counterpart in the paper).  When a context plans a problem in the mixed
+ * precision (the first osv_build of a new shape), it times on the device, with CUDA events, the candidate launch
+ * shapes of its tunable kernels and keeps the fastest: the FP32 Householder tridiagonalisation (a pair of CTAs per
+ * matrix, or one CTA per matrix and two per SM) and the tile shape of every double-float GEMM batch whose problems
+ * all overwrite their outputs.  Results do not depend on the choice beyond rounding order.  osv_autotune(ctx, 0)
+ * turns it off for later plans (the fixed rules then apply); it is on by default.  osv_autotune_report writes the
+ * last plan's choices as a NUL-terminated JSON object into buf (HOST, len bytes, may be NULL), with the fixed
+ * rule's choice, the tuned one and the timings per item, and *needed (HOST, may be NULL) = the bytes the whole
+ * report takes; "" when nothing was tuned. */
+osv_status osv_autotune(osv_ctx *ctx, int on);
+osv_status osv_autotune_report(osv_ctx *ctx, char *buf, int len, int *needed);
+
 /* Failure detection (no counterpart in the paper): every wait of the tensor-core kernels on their pipeline
  * barriers is bounded; when a wait runs out the kernel raises OSV_ERR_TIMEOUT in the context's error word, lets
  * the work it already committed finish, frees its tensor memory and returns.  osv_set_wait_budget sets the bound

@@ -4,7 +4,9 @@
 // and padded pair-basis columns are dropped by the overlap eigenvalue test.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <numeric>
 #include <string>
@@ -724,6 +726,94 @@ osv_status build_plan(osv_ctx *c) {
     return OSV_OK;
 }
 
+// Plan-time autotuner (mixed precision): launch shapes are timed on the device with CUDA events and the fastest
+// is kept.  Timed runs read the plan's own buffers whatever they hold (the work of these kernels does not depend on
+// the values) and write only outputs that the build overwrites afterwards.
+//   - the FP32 Householder tridiagonalisation: a pair of CTAs per matrix, or one CTA per matrix and two per SM;
+//   - the double-float GEMM tile shape (64x64, 80x80, 48x80, 80x48, 48x48) of every batch of the build whose
+//     problems all have beta = 0 and no atomic accumulation (re-running such a batch is harmless).
+// The report (osv_autotune_report) lists, per item, the rule's choice, the tuned choice and the timings.
+osv_status autotune_plan(osv_ctx *c) {
+    c->tune_report.clear();
+    if (!c->autotune || !c->osv_mixed) return OSV_OK;
+    cudaStream_t s = c->stream;
+    cudaEvent_t a = c->take_event(), b = c->take_event();
+    cudaError_t e = cudaSuccess;
+    auto timed = [&](const std::function<cudaError_t()> &run, int reps) -> double {
+        if (e != cudaSuccess) return 0.0;
+        if ((e = cudaEventRecord(a, s)) != cudaSuccess) return 0.0;
+        for (int q = 0; q < reps && e == cudaSuccess; ++q) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        return ms / reps;
+    };
+    const char *shape_name[5] = {"64x64", "80x80", "48x80", "80x48", "48x48"};
+    std::string js = "{";
+    double gain = 0.0, spent = 0.0;
+    // 1. tridiagonalisation launch shape
+    {
+        const int n = c->n_occ, nv = c->n_vir;
+        double t[2];
+        for (int v = 0; v < 2; ++v) t[v] = timed([&] { return osv_tridiag<float>(c->refine.tri_d, n, nv, s, v); }, 1);
+        const int best = t[1] < t[0] ? 1 : 0;
+        c->refine.tri_variant = best;
+        gain += t[0] - t[best];
+        spent += t[0] + t[1];
+        char buf[256];
+        snprintf(buf, sizeof buf, "\"tridiag\": {\"rule\": \"cta_pair\", \"choice\": \"%s\", \"ms\": {\"cta_pair\": %.3f, "
+                 "\"single_cta_2_per_sm\": %.3f}}", best ? "single_cta_2_per_sm" : "cta_pair", t[0], t[1]);
+        js += buf;
+    }
+    // 2. double-float GEMM tile shapes
+    std::vector<std::pair<std::string, GemmBatch *>> batches = {
+        {"sf_blocks", &c->gb_sf}, {"pair_fx1", &c->gb_fx1}, {"pair_fx2", &c->gb_fx2}, {"pair_v", &c->gb_v},
+        {"pair_kt1", &c->gb_kt1}, {"pair_kt2", &c->gb_kt2}, {"coupling_c1", &c->gb_c1}, {"coupling_c2", &c->gb_c2}};
+    for (int x = 0; x < 2; ++x) {
+        const std::string k = std::to_string(x);
+        batches.push_back({"refine_w" + k, &c->refine.gb_w[x]});
+        batches.push_back({"refine_gh" + k, &c->refine.gb_gh[x]});
+        batches.push_back({"refine_rot" + k, &c->refine.gb_rot[x]});
+        batches.push_back({"refine_fin" + k, &c->refine.gb_fin[x]});
+    }
+    js += ", \"gemm_df\": {";
+    bool first = true;
+    for (auto &nb : batches) {
+        GemmBatch &g = *nb.second;
+        if (g.h.empty() || g.tiles == 0) continue;
+        bool ok = true;
+        for (const GemmDesc &d : g.h) ok = ok && d.beta == 0.0 && !d.atomic;
+        if (!ok) continue;
+        double t[5];
+        for (int sh = 0; sh < 5; ++sh) {
+            if ((e = gemm_batch_set_df_shape(g, sh)) != cudaSuccess) break;
+            gemm_batch_run_df(g, s);   // warm-up
+            t[sh] = timed([&] { return gemm_batch_run_df(g, s); }, 3);
+            spent += 4 * t[sh];
+        }
+        if (e != cudaSuccess) break;
+        int best = 0;
+        for (int sh = 1; sh < 5; ++sh)
+            if (t[sh] < t[best]) best = sh;
+        if ((e = gemm_batch_set_df_shape(g, best)) != cudaSuccess) break;
+        gain += t[g.df_rule] - t[best];
+        char buf[512];
+        snprintf(buf, sizeof buf, "%s\"%s\": {\"rule\": \"%s\", \"choice\": \"%s\", \"ms\": [%.4f, %.4f, %.4f, %.4f, %.4f]}",
+                 first ? "" : ", ", nb.first.c_str(), shape_name[g.df_rule], shape_name[best], t[0], t[1], t[2], t[3], t[4]);
+        js += buf;
+        first = false;
+    }
+    c->pool.push_back(a);
+    c->pool.push_back(b);
+    if (e != cudaSuccess) return c->cuda_fail(e, "autotune");
+    char buf[160];
+    snprintf(buf, sizeof buf, "}, \"gain_ms_per_build\": %.3f, \"tuning_ms\": %.1f}", gain, spent);
+    js += buf;
+    c->tune_report = js;
+    return OSV_OK;
+}
+
 osv_status run_osv_build(osv_ctx *c) {
     cudaError_t e;
     cudaStream_t s = c->stream;
@@ -854,7 +944,7 @@ osv_status osv_build(osv_ctx *c, const osv_problem *pb, const osv_params *prm, i
         c->B_in = pb->B;
         c->B_dtype = pb->B_dtype;
         plan_clusters(c);
-        if ((st = build_plan(c)) != OSV_OK) {
+        if ((st = build_plan(c)) != OSV_OK || (st = autotune_plan(c)) != OSV_OK) {
             c->release();
             return st;
         }
@@ -1387,6 +1477,23 @@ osv_status gradient_backward(osv_ctx *c, double dE_scale, void *dE_dB, double *d
     // a bounded wait that gave up, or a non-finite value, leaves its mark in the device error word
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "gradient_backward");
     return device_error(c);
+}
+
+osv_status osv_autotune(osv_ctx *c, int on) {
+    if (!c) return OSV_ERR_INVALID;
+    c->autotune = on != 0;
+    return OSV_OK;
+}
+
+osv_status osv_autotune_report(osv_ctx *c, char *buf, int len, int *needed) {
+    if (!c) return OSV_ERR_INVALID;
+    const int n = (int)c->tune_report.size() + 1;
+    if (needed) *needed = n;
+    if (buf && len > 0) {
+        strncpy(buf, c->tune_report.c_str(), (size_t)len - 1);
+        buf[len - 1] = 0;
+    }
+    return OSV_OK;
 }
 
 osv_status osv_set_wait_budget(osv_ctx *c, long long cycles) {

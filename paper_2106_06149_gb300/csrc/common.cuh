@@ -280,10 +280,13 @@ struct GemmBatch {
     long long *d_tile0_df = nullptr;   // tile offsets of the double-float kernel's shape
     long long tiles_df = 0;
     int df_shape = 0;                  // 0: 64 x 64, 1: 80 x 80, 2: 48 x 80, 3: 80 x 48, 4: 48 x 48
+    int df_rule = 0;                   // the shape the padded-work rule chose at upload
     void add(const GemmDesc &g) { h.push_back(g); }
 };
 
 cudaError_t gemm_batch_upload(GemmBatch &b);
+// the double-float kernel's tile shape of an uploaded batch: 0 64x64, 1 80x80, 2 48x80, 3 80x48, 4 48x48
+cudaError_t gemm_batch_set_df_shape(GemmBatch &b, int shape);
 cudaError_t gemm_batch_run(const GemmBatch &b, cudaStream_t s);
 // the same batch in double-float arithmetic on the FP32 pipe (~2^-44 relative)
 cudaError_t gemm_batch_run_df(const GemmBatch &b, cudaStream_t s);

@@ -114,6 +114,9 @@ struct osv_ctx {
     double *post_R1 = nullptr, *post_T2 = nullptr, *post_R2 = nullptr, *post_rn = nullptr, *post_E = nullptr,
            *post_G1 = nullptr;
     long long wait_budget = 0;             // tensor-core main-loop wait budget in clock cycles (0 = default)
+    // plan-time autotuner (mixed precision): launch shapes timed on the device, the fastest kept
+    bool autotune = true;
+    std::string tune_report;               // JSON: per tuned item the rule's choice, the tuned choice, timings
 
     // per-stage CUDA-event profiling (osv_profile_enable / osv_profile_read)
     bool prof = false;

@@ -291,6 +291,7 @@ cudaError_t gemm_batch_upload(GemmBatch &b) {
     }
     b.tiles = t[0].back();
     b.df_shape = best;
+    b.df_rule = best;
     b.tiles_df = t[best].back();
     cudaError_t e = cudaMalloc(&b.d_desc, b.h.size() * sizeof(GemmDesc));
     if (e != cudaSuccess) return e;
@@ -314,6 +315,25 @@ cudaError_t gemm_batch_run(const GemmBatch &b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t gemm_batch_set_df_shape(GemmBatch &b, int shape) {
+    if (b.h.empty() || shape == b.df_shape) return cudaSuccess;
+    if (shape < 0 || shape > 4) return cudaErrorInvalidValue;
+    const int sm[5] = {64, 80, 48, 80, 48}, sn[5] = {64, 80, 80, 48, 48};
+    std::vector<long long> t(b.h.size() + 1, 0);
+    for (size_t i = 0; i < b.h.size(); ++i) {
+        const GemmDesc &g = b.h[i];
+        const bool live = g.M > 0 && g.N > 0;
+        t[i + 1] = t[i] + (live ? (long long)((g.M + sm[shape] - 1) / sm[shape]) * ((g.N + sn[shape] - 1) / sn[shape]) : 0);
+    }
+    if (b.d_tile0_df) cudaFree(b.d_tile0_df);
+    b.d_tile0_df = nullptr;
+    cudaError_t e = cudaMalloc(&b.d_tile0_df, t.size() * sizeof(long long));
+    if (e != cudaSuccess) return e;
+    b.df_shape = shape;
+    b.tiles_df = t.back();
+    return cudaMemcpy(b.d_tile0_df, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice);
+}
+
 void gemm_batch_free(GemmBatch &b) {
     if (b.d_desc) cudaFree(b.d_desc);
     if (b.d_tile0) cudaFree(b.d_tile0);
@@ -322,7 +342,7 @@ void gemm_batch_free(GemmBatch &b) {
     b.d_tile0 = nullptr;
     b.d_tile0_df = nullptr;
     b.tiles = b.tiles_df = 0;
-    b.df_shape = 0;
+    b.df_shape = b.df_rule = 0;
 }
 
 }  // namespace osv

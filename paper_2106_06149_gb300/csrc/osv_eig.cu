@@ -68,8 +68,8 @@ __device__ __forceinline__ R warp_sum_t(R v) {
 // group of four rows), and stashes column k+1; (c) p = tau (row + column sums), p -= (tau/2)(p.v) v; (v_k, p)
 // become the pending update A <- A - v p^T - p v^T.  The upper part of row k holds the reflector: no later step
 // reads it.
-template <class R, int CL>
-__global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__ descs) {
+template <class R, int CL, int MINB>
+__global__ void __launch_bounds__(kTT, MINB) k_tridiag(const TriDescT<R> *__restrict__ descs) {
     static_assert(CL == 1 || CL == 2, "one CTA or a pair of CTAs per matrix");
     const unsigned rank = CL == 2 ? cg::this_cluster().block_rank() : 0u;
     const TriDescT<R> D = descs[blockIdx.x / CL];
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kTT) k_tridiag(const TriDescT<R> *__restrict__
                     if (lane < 3 && k + 1 + lane < cb) col(k + 1 + lane);
                     if (lane < 3 && max(ce, cb) + lane <= hi) col(max(ce, cb) + lane);
                     const int nch = ce > cb ? (ce - cb) >> 2 : 0;
-                    constexpr int UV = 3;
+                    constexpr int UV = MINB == 2 ? 1 : 3;   // two CTAs per SM: a 64-register budget
                     for (int j0 = lane; j0 < nch; j0 += 32 * UV) {
                         float4 a[UV][4];
 #pragma unroll
@@ -1026,14 +1026,22 @@ size_t jacobi_smem_bytes(int n) {
 }
 
 template <class R>
-cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s) {
+cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, int variant) {
     if (batch <= 0) return cudaSuccess;
-    // v, p, vo, po, the column stash and the column sums; the pair of CTAs adds the peer's column sums
-    const size_t sh = (sizeof(R) == 4 ? 7 : 6) * (size_t)((n + 3) & ~3) * sizeof(R);
     cudaError_t e;
     if constexpr (sizeof(R) == 4) {
-        // FP32: a pair of CTAs (thread-block cluster) per matrix, each owning every other row
-        if ((e = smem_attr(k_tridiag<R, 2>, sh)) != cudaSuccess) return e;
+        if (variant == 1) {
+            // FP32, one CTA per matrix and two CTAs per SM (no cluster barriers; more warps per SM)
+            const size_t sh = 6 * (size_t)((n + 3) & ~3) * sizeof(R);
+            if ((e = smem_attr(k_tridiag<R, 1, 2>, sh)) != cudaSuccess) return e;
+            count_launch();
+            k_tridiag<R, 1, 2><<<batch, kTT, sh, s>>>(d);
+            return cudaGetLastError();
+        }
+        // FP32: a pair of CTAs (thread-block cluster) per matrix, each owning every other row; v, p, vo, po, the
+        // column stash, the column sums and the peer's column sums in shared memory
+        const size_t sh = 7 * (size_t)((n + 3) & ~3) * sizeof(R);
+        if ((e = smem_attr(k_tridiag<R, 2, 1>, sh)) != cudaSuccess) return e;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(2 * (unsigned)batch);
         cfg.blockDim = dim3(kTT);
@@ -1047,11 +1055,13 @@ cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s) 
         cfg.attrs = at;
         cfg.numAttrs = 1;
         count_launch();
-        return cudaLaunchKernelEx(&cfg, k_tridiag<R, 2>, d);
+        return cudaLaunchKernelEx(&cfg, k_tridiag<R, 2, 1>, d);
     } else {
-        if ((e = smem_attr(k_tridiag<R, 1>, sh)) != cudaSuccess) return e;
+        (void)variant;
+        const size_t sh = 6 * (size_t)((n + 3) & ~3) * sizeof(R);
+        if ((e = smem_attr(k_tridiag<R, 1, 1>, sh)) != cudaSuccess) return e;
         count_launch();
-        k_tridiag<R, 1><<<batch, kTT, sh, s>>>(d);
+        k_tridiag<R, 1, 1><<<batch, kTT, sh, s>>>(d);
         return cudaGetLastError();
     }
 }
@@ -1131,7 +1141,7 @@ cudaError_t osv_tri_shift_solve(const TriDescT<R> *d, int batch, int n, int nmax
 }
 
 #define OSV_EIG_INST(R)                                                                                            \
-    template cudaError_t osv_tridiag<R>(const TriDescT<R> *, int, int, cudaStream_t);                              \
+    template cudaError_t osv_tridiag<R>(const TriDescT<R> *, int, int, cudaStream_t, int);                         \
     template cudaError_t osv_tri_eigvals<R>(const TriDescT<R> *, int, int, int, cudaStream_t);                     \
     template cudaError_t osv_tri_kept_vectors<R>(const TriDescT<R> *, int, int, int, const int *, R *, R *,        \
                                                  cudaStream_t);                                                    \

@@ -19,8 +19,9 @@ struct TriDescT {
 using TriDesc = TriDescT<double>;
 using TriDesc32 = TriDescT<float>;
 
+// variant (FP32 only): 0 = a pair of CTAs per matrix (thread-block cluster), 1 = one CTA per matrix, two per SM
 template <class R>
-cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s);
+cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, int variant = 0);
 // The cnt largest eigenvalues of every tridiagonal (decreasing, into w[0..cnt)), by 32-point multisection in
 // FP64 arithmetic (one warp per eigenvalue).
 template <class R>

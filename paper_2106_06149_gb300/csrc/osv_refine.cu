@@ -262,7 +262,7 @@ cudaError_t osv_mixed_eigh(const OsvRefine &r, int n, int nv, int nm, double *Q,
     } while (0)
     const long long per = (long long)nm * nv, tot = per * n;
     const int grid = grid_for(tot);
-    CK(osv_tridiag<float>(r.tri_d, n, nv, s));
+    CK(osv_tridiag<float>(r.tri_d, n, nv, s, r.tri_variant));
     if (r.Twy) CK(osv_wy_prepare(r.tri_d, n, nv, r.Twy, s));
     CK(osv_tri_eigvals<float>(r.tri_d, n, nv, nm, s));
     CK(osv_tri_kept_vectors<float>(r.tri_d, n, nv, nm, r.nm_all, r.Y32, r.work32, s));

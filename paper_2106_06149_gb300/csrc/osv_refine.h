@@ -26,6 +26,7 @@ struct OsvRefine {
     double *AT = nullptr, *RS = nullptr;   // relaxation: a T and the FP64 residual (nm x n_vir per LMO)
     int *nm_all = nullptr;                 // n_max for every LMO (rows refined)
     float *Twy = nullptr;                  // compact-WY T factors of the FP32 reflectors (osv_wy_floats)
+    int tri_variant = 0;                   // FP32 tridiagonalisation launch shape (osv_tridiag), set by the autotuner
     GemmBatch gb_w[2], gb_gh[2], gb_rot[2], gb_fin[2];
 };
 

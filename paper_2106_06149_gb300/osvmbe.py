@@ -24,7 +24,7 @@ EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv
            "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops",
            "osv_solve_counts", "osv_residual_work", "osv_set_wait_budget",
            "osv_pair_amplitudes", "osv_overlap_metric", "clusters_build_osv",
-           "posterior_correction", "weak_pairs_energy"]
+           "posterior_correction", "weak_pairs_energy", "osv_autotune", "osv_autotune_report"]
 
 
 class OsvParams(ctypes.Structure):
@@ -81,6 +81,8 @@ def load(path=LIB_PATH):
         "clusters_build_osv": ([V, P(OsvProblem), P(OsvParams), V, D, D, V], I),
         "posterior_correction": ([V, P(D), P(D), P(D)], I),
         "weak_pairs_energy": ([V, V, D, D, P(D), P(I)], I),
+        "osv_autotune": ([V, I], I),
+        "osv_autotune_report": ([V, V, I, P(I)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -257,6 +259,19 @@ class Context:
     def gradient_backward(self, scale, dB=None, dF=None):
         _check(load().gradient_backward(self.h, float(scale), _ptr(dB) if dB is not None else None,
                                         _ptr(dF) if dF is not None else None), self.h)
+
+    def autotune(self, on=True):
+        """Plan-time autotuning of launch shapes (mixed precision); on by default."""
+        _check(load().osv_autotune(self.h, 1 if on else 0), self.h)
+
+    def autotune_report(self):
+        """The last plan's tuned launch shapes (dict; empty when nothing was tuned)."""
+        import json
+        n = ctypes.c_int()
+        _check(load().osv_autotune_report(self.h, None, 0, ctypes.byref(n)), self.h)
+        buf = ctypes.create_string_buffer(max(n.value, 1))
+        _check(load().osv_autotune_report(self.h, buf, n.value, ctypes.byref(n)), self.h)
+        return json.loads(buf.value.decode()) if buf.value else {}
 
     def set_wait_budget(self, cycles):
         """Bound (SM clock cycles) of the tensor-core kernels' pipeline waits; <= 0 restores the default."""

@@ -125,3 +125,29 @@ def test_bf16x4_adjoint_kernels_match_fp64(osvmbe, nosv):
     print(f"\nn_osv {nosv}: dE = {x['E'] - f['E']:.3e}; max|d dB| = {gb:.3e}; max|d dF| = {gf:.3e}")
     assert abs(x["E"] - f["E"]) <= 1e-6
     assert gb <= 1e-6 and gf <= 1e-6
+
+
+def test_autotuner_reports_its_choices_and_keeps_the_results(osvmbe):
+    """The plan-time autotuner times the candidate launch shapes (FP32 tridiagonalisation, double-float GEMM tiles)
+    and keeps the fastest; its report names the fixed rule's choice, the tuned one and the timings.  Launch shapes
+    change only the rounding order, so the energy with and without tuning agrees to far below the 1e-6 bar."""
+    p = make_problem(6, 40, 150, seed=52)
+    prm = Params(n_osv_fixed=6, mbe_order=3, r2b=6.0, r3b=5.0, tol=1e-11, precision=2)
+    out = {}
+    for on in (True, False):
+        dp = osvmbe.DeviceProblem.from_host(p)
+        ctx = osvmbe.Context()
+        ctx.autotune(on)
+        ctx.clusters_build(dp, prm)
+        out[on] = (osvmbe.run_energy(ctx, dp, prm)[0], ctx.autotune_report())
+        ctx.close()
+    (E_on, rep), (E_off, rep_off) = out[True], out[False]
+    assert rep_off == {}
+    assert rep["tridiag"]["choice"] in ("cta_pair", "single_cta_2_per_sm") and len(rep["tridiag"]["ms"]) == 2
+    shapes = {"64x64", "80x80", "48x80", "80x48", "48x48"}
+    assert rep["gemm_df"] and all(v["rule"] in shapes and v["choice"] in shapes and len(v["ms"]) == 5
+                                  for v in rep["gemm_df"].values())
+    for v in rep["gemm_df"].values():   # the choice is the fastest timed shape
+        assert min(v["ms"]) == v["ms"][["64x64", "80x80", "48x80", "80x48", "48x48"].index(v["choice"])]
+    print(f"\nautotuner: {rep}")
+    assert abs(E_on - E_off) <= 1e-9
