@@ -34,8 +34,27 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __host__ __device__ __forceinline__ int wy_blocks(int n) { return n < 3 ? 0 : (n - 2 + kNB - 1) / kNB; }
 
+// The reflectors of block j stream through shared memory in chunks of kCH columns (chunk rows padded to an odd
+// stride, kCH + 1, so that lane i reading reflector i's column c hits bank (i + c) mod 32): the blocks of any order up
+// to 4096 fit, not only those whose kNB x n reflector block fits at once.
+constexpr int kCH = 256;
+constexpr int kLdc = kCH + 1;
+
+// reflector i of block j (k0 = j kNB, kb reflectors), columns [c0 + cbeg, c0 + cbeg + cw) relative to c0 = k0 + 1,
+// into Vs (kNB x kLdc): row k0 + i of A from column k0 + 1 + i on, zeros before (and for i >= kb)
+__device__ __forceinline__ void load_v_chunk(const TriDesc32 &D, int k0, int kb, int cbeg, int cw, float *Vs) {
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const int c0 = k0 + 1;
+    for (int i = wid; i < kNB; i += kT / 32) {
+        const float *src = D.A + (long long)min(k0 + i, D.n - 1) * D.lda + c0 + cbeg;
+        for (int c = lane; c < cw; c += 32)
+            cp_async_zfill(Vs + i * kLdc + c, src + c, 4, (i < kb && cbeg + c >= i) ? 4 : 0);
+    }
+}
+
 // T_j of every block j of every matrix (kNB x kNB row-major, zero outside the upper triangle of the block's kb
-// reflectors).  With G = V^T V, the columns follow T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i], T[i][i] = tau_i.
+// reflectors).  With G = V^T V (accumulated over column chunks), the columns follow
+// T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i], T[i][i] = tau_i.
 __global__ void __launch_bounds__(kT) k_wy_t(const TriDesc32 *__restrict__ descs, float *__restrict__ Tall, int J) {
     const int b = blockIdx.x, j = blockIdx.y;
     const TriDesc32 D = descs[b];
@@ -48,30 +67,38 @@ __global__ void __launch_bounds__(kT) k_wy_t(const TriDesc32 *__restrict__ descs
         for (int i = tid; i < kNB * kNB; i += kT) T[i] = 0.f;
         return;
     }
-    const int m0 = n - k0 - 1, ld = m0 | 1;
+    const int m0 = n - k0 - 1;
     extern __shared__ __align__(16) float wsm[];
-    float *Vs = wsm;                      // kb x ld: reflector i at columns k0+1+c, zero for c < i
-    float *Gs = Vs + (long long)kNB * ld;  // kNB x (kNB + 1)
+    float *Vs = wsm;                       // kNB x kLdc: one column chunk of the block's reflectors
+    float *Gs = Vs + kNB * kLdc;           // kNB x (kNB + 1)
     float *Ts = Gs + kNB * (kNB + 1);      // kNB x (kNB + 1)
-    for (int idx = tid; idx < kb * m0; idx += kT) {
-        const int i = idx / m0, c = idx - i * m0;
-        Vs[i * ld + c] = c >= i ? D.A[(long long)(k0 + i) * D.lda + k0 + 1 + c] : 0.f;
-    }
     for (int idx = tid; idx < kNB * (kNB + 1); idx += kT) Ts[idx] = 0.f;
-    __syncthreads();
-    for (int p = tid; p < kb * kb; p += kT) {
-        const int l = p / kb, i = p - l * kb;
-        if (l < i) {
-            const float *vl = Vs + l * ld, *vi = Vs + i * ld;
-            float s0 = 0.f, s1 = 0.f;
-            int c = i;
-            for (; c + 1 < m0; c += 2) {
-                s0 = fmaf(vl[c], vi[c], s0);
-                s1 = fmaf(vl[c + 1], vi[c + 1], s1);
+    // G[l][i], l < i, one thread per (l, i), accumulated over the chunks (registers)
+    constexpr int kPairs = kNB * kNB / kT;   // 4 pairs per thread
+    float gacc[kPairs];
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) gacc[q] = 0.f;
+    for (int cbeg = 0; cbeg < m0; cbeg += kCH) {
+        const int cw = min(kCH, m0 - cbeg);
+        __syncthreads();   // the previous chunk is no longer read
+        load_v_chunk(D, k0, kb, cbeg, cw, Vs);
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q) {
+            const int pidx = tid + q * kT, l = pidx / kNB, i = pidx % kNB;
+            if (l < i && i < kb) {
+                const float *vl = Vs + l * kLdc, *vi = Vs + i * kLdc;
+                float s = 0.f;
+                for (int c = 0; c < cw; ++c) s = fmaf(vl[c], vi[c], s);
+                gacc[q] += s;
             }
-            if (c < m0) s0 = fmaf(vl[c], vi[c], s0);
-            Gs[l * (kNB + 1) + i] = s0 + s1;
         }
+    }
+#pragma unroll
+    for (int q = 0; q < kPairs; ++q) {
+        const int pidx = tid + q * kT, l = pidx / kNB, i = pidx % kNB;
+        if (l < i && i < kb) Gs[l * (kNB + 1) + i] = gacc[q];
     }
     __syncthreads();
     for (int i = 0; i < kb; ++i) {
@@ -92,8 +119,8 @@ __global__ void __launch_bounds__(kT) k_wy_t(const TriDesc32 *__restrict__ descs
 }
 
 // rows mu < nrow[b] of V (nmax x n per matrix) <- H V (forward = 0: B_{J-1} first) or H^T V (forward = 1:
-// B_0^T first).  Per block: W = V_j^T y (lane i: reflector i), Z = T_j W or T_j^T W through warp shuffles,
-// y -= V_j Z; the block's reflectors and T_j are shared by the CTA's kWyRows rows.
+// B_0^T first).  Per block: W = V_j^T y (lane i: reflector i) over the column chunks, Z = T_j W or T_j^T W through
+// warp shuffles, then y -= V_j Z over the chunks again; the chunks and T_j are shared by the CTA's kWyRows rows.
 __global__ void __launch_bounds__(kT) k_reflect_wy(const TriDesc32 *__restrict__ descs, const float *__restrict__ Tall,
                                                    int J, const int *__restrict__ nrow, float *__restrict__ V, int nmax,
                                                    int forward) {
@@ -106,54 +133,69 @@ __global__ void __launch_bounds__(kT) k_reflect_wy(const TriDesc32 *__restrict__
     if (g0 >= nr || Jb == 0) return;
     const int rows = min(kWyRows, nr - g0);
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    const int ldv = (n - 1) | 1;
     extern __shared__ __align__(16) float wsm[];
     float *Ys = wsm;                             // kWyRows x n
-    float *Vs = Ys + (long long)kWyRows * n;     // kNB x ldv
-    float *Ts = Vs + (long long)kNB * ldv;       // kNB x (kNB + 1)
+    float *Vs = Ys + (long long)kWyRows * n;     // kNB x kLdc: one column chunk of the block
+    float *Ts = Vs + kNB * kLdc;                 // kNB x (kNB + 1)
     float *Vg = V + ((long long)b * nmax + g0) * n;
     for (int i = tid; i < rows * n; i += kT) cp_async_zfill(Ys + i, Vg + i, 4, 4);
     for (int s = 0; s < Jb; ++s) {
         const int j = forward ? s : Jb - 1 - s;
         const int k0 = j * kNB, kb = min(kNB, n - 2 - k0), m0 = n - k0 - 1, c0 = k0 + 1;
         __syncthreads();   // previous block fully applied
-        // reflector i of the block: row k0 + i of A from column k0 + 1 + i on, zeros before (and for i >= kb)
-        for (int i = wid; i < kNB; i += kT / 32) {
-            const float *src = D.A + (long long)min(k0 + i, n - 1) * D.lda + c0;
-            for (int c = lane; c < m0; c += 32) cp_async_zfill(Vs + i * ldv + c, src + c, 4, (i < kb && c >= i) ? 4 : 0);
-        }
         const float *Tg = Tall + ((long long)b * J + j) * kNB * kNB;
         for (int idx = tid; idx < kNB * kNB; idx += kT) {
             const int i = idx >> 5, l = idx & 31;
             cp_async_zfill(Ts + i * (kNB + 1) + l, Tg + idx, 4, 4);
         }
-        cp_async_wait_all();
-        __syncthreads();
-        if (wid < rows) {
-            float *y = Ys + (long long)wid * n + c0;
-            const float *vr = Vs + lane * ldv;
-            float w0 = 0.f, w1 = 0.f;
-            int c = 0;
-            for (; c + 1 < m0; c += 2) {
-                w0 = fmaf(y[c], vr[c], w0);
-                w1 = fmaf(y[c + 1], vr[c + 1], w1);
+        float w = 0.f;   // lane i: reflector i . this warp's row
+        for (int cbeg = 0; cbeg < m0; cbeg += kCH) {
+            const int cw = min(kCH, m0 - cbeg);
+            __syncthreads();
+            load_v_chunk(D, k0, kb, cbeg, cw, Vs);
+            cp_async_wait_all();
+            __syncthreads();
+            if (wid < rows) {
+                const float *y = Ys + (long long)wid * n + c0 + cbeg;
+                const float *vr = Vs + lane * kLdc;
+                float w0 = 0.f, w1 = 0.f;
+                int c = 0;
+                for (; c + 1 < cw; c += 2) {
+                    w0 = fmaf(y[c], vr[c], w0);
+                    w1 = fmaf(y[c + 1], vr[c + 1], w1);
+                }
+                if (c < cw) w0 = fmaf(y[c], vr[c], w0);
+                w += w0 + w1;
             }
-            if (c < m0) w0 = fmaf(y[c], vr[c], w0);
-            const float w = w0 + w1;
-            float z = 0.f;
+        }
+        float z = 0.f;
+        if (wid < rows) {
 #pragma unroll
             for (int l = 0; l < kNB; ++l) {
                 const float wl = __shfl_sync(0xffffffffu, w, l);
                 z = fmaf(wl, forward ? Ts[l * (kNB + 1) + lane] : Ts[lane * (kNB + 1) + l], z);
             }
-            float zr[kNB];
+        }
+        float zr[kNB];
 #pragma unroll
-            for (int i = 0; i < kNB; ++i) zr[i] = __shfl_sync(0xffffffffu, z, i);
-            for (int cc = lane; cc < m0; cc += 32) {
-                float acc = y[cc];
+        for (int i = 0; i < kNB; ++i) zr[i] = __shfl_sync(0xffffffffu, z, i);
+        for (int cbeg = 0; cbeg < m0; cbeg += kCH) {
+            const int cw = min(kCH, m0 - cbeg);
+            // a block of one chunk is still in Vs from the first pass; otherwise every chunk is loaded again
+            if (cbeg > 0 || m0 > kCH) {
+                __syncthreads();
+                load_v_chunk(D, k0, kb, cbeg, cw, Vs);
+                cp_async_wait_all();
+                __syncthreads();
+            }
+            if (wid < rows) {
+                float *y = Ys + (long long)wid * n + c0 + cbeg;
+                for (int cc = lane; cc < cw; cc += 32) {
+                    float acc = y[cc];
 #pragma unroll
-                for (int i = 0; i < kNB; ++i) acc = fmaf(-zr[i], Vs[i * ldv + cc], acc);
-                y[cc] = acc;
+                    for (int i = 0; i < kNB; ++i) acc = fmaf(-zr[i], Vs[i * kLdc + cc], acc);
+                    y[cc] = acc;
+                }
             }
         }
     }
@@ -341,7 +383,7 @@ cudaError_t smem_attr(K kernel, size_t sh) {
 constexpr size_t kSmemCap = 227 * 1024;
 
 size_t reflect_wy_smem(int n) {
-    return ((size_t)kWyRows * n + (size_t)kNB * ((n - 1) | 1) + (size_t)kNB * (kNB + 1)) * sizeof(float);
+    return ((size_t)kWyRows * n + (size_t)kNB * kLdc + (size_t)kNB * (kNB + 1)) * sizeof(float);
 }
 
 template <class P>
@@ -356,7 +398,7 @@ size_t osv_wy_floats(int batch, int n) { return (size_t)batch * std::max(wy_bloc
 cudaError_t osv_wy_prepare(const TriDesc32 *d, int batch, int n, float *T, cudaStream_t s) {
     const int J = wy_blocks(n);
     if (batch <= 0 || J == 0) return cudaSuccess;
-    const size_t sh = ((size_t)kNB * ((n - 1) | 1) + 2 * (size_t)kNB * (kNB + 1)) * sizeof(float);
+    const size_t sh = ((size_t)kNB * kLdc + 2 * (size_t)kNB * (kNB + 1)) * sizeof(float);
     if (sh > kSmemCap) return cudaErrorInvalidValue;
     cudaError_t e;
     if ((e = smem_attr(k_wy_t, sh)) != cudaSuccess) return e;
