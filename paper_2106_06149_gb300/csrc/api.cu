@@ -463,6 +463,7 @@ osv_status build_plan(osv_ctx *c) {
     ALLOC(c->G1_32, (long long)c->cl.size() * c->gstride);
     ALLOC(c->evals64, c->cl.size());
     ALLOC(c->evals32, c->cl.size());
+    ALLOC(c->work_next, 1);
     if (c->B_dtype == 1) {
         ALLOC(c->B64own, c->aux_ptr[n] * (long long)nv);
         c->B64 = c->B64own;
@@ -1038,6 +1039,8 @@ osv_status cluster_residual_solve(osv_ctx *c, int *n_iter_out, int32_t *cluster_
     a.evals64 = c->evals64;
     a.evals32 = c->evals32;
     a.np_max = 2 * c->nmax;
+    a.next = c->work_next;
+    a.ncl = (int)c->cl.size();
     if ((e = cudaMemsetAsync(c->Tslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)
         return c->cuda_fail(e, "memset T");
     if ((e = cudaMemsetAsync(c->Rslot, 0, c->slot_mat * sizeof(double), c->stream)) != cudaSuccess)

@@ -84,6 +84,7 @@ struct osv_ctx {
     int *evals64 = nullptr;
     int *evals32 = nullptr;
     int *iters = nullptr;
+    int *work_next = nullptr;             // work counter of the persistent residual launch
     long long slot_mat = 0, gstride = 0;
 
     HostDev<PairInfo> pinfo;

@@ -89,6 +89,8 @@ struct SolveArgs {
     int *evals64;             // per cluster: FP64 residual evaluations used
     int *evals32;             // per cluster: FP32 residual evaluations (mixed solve)
     int np_max;               // largest padded pair order (shared-memory staging of the FP32 terms)
+    int *next;                // work counter of the persistent cluster solve (zeroed per launch)
+    int ncl;                  // clusters in the order list
 };
 
 }  // namespace osv

@@ -361,8 +361,7 @@ __device__ double hylleraas(const SolveArgs &A, const ClusterInfo &C, double *re
 }
 
 // Plain FP64 cluster solve: Jacobi iterations from T~ = 0 until max ||R~||_F <= tol.
-__global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
-    const int c = A.order[blockIdx.x];
+__device__ void solve_cluster_fp64(const SolveArgs &A, int c) {
     const ClusterInfo C = A.clusters[c];
     __shared__ double red[kThreads / 32];
     View<double> v{A.e, A.Kt, false, A.sblk, A.T, A.R, A.G1 + (long long)blockIdx.x * A.gstride, nullptr, 0, false};
@@ -428,11 +427,9 @@ __device__ double promote_residual(const SolveArgs &A, const ClusterInfo &C, dou
 // Mixed cluster solve: FP32 Jacobi to the FP32 floor, then FP64 iterative refinement (FP64 residual, FP32
 // correction solve with the FP64 residual as right-hand side, FP64 update) until max ||R~||_F <= tol in FP64.
 // The energy uses the last FP64 residual, so its error is second order in the amplitude error (Eq. 3).
-__global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
-    const int c = A.order[blockIdx.x];
+__device__ void solve_cluster_mixed(const SolveArgs &A, int c, float *stage32) {
     const ClusterInfo C = A.clusters[c];
     __shared__ double red[kThreads / 32];
-    extern __shared__ __align__(16) float stage32[];
     const int ld = A.np_max + 1;
     View<float> v32{A.e32, A.Kt32, false, A.sblk32, A.T32, A.R32, A.G1_32 + (long long)blockIdx.x * A.gstride, stage32, ld,
                     false};
@@ -509,6 +506,24 @@ __global__ void __launch_bounds__(kThreads) k_residual_mixed(SolveArgs A) {
         A.iters[c] = conv ? total + evals - 1 : -1;
         if (A.evals64) A.evals64[c] = evals;
         if (A.evals32) A.evals32[c] = ev32;
+    }
+}
+
+// One persistent grouped launch over every cluster: each CTA takes the next cluster of the cost-sorted order
+// (most expensive first) from a device counter until none is left, so uneven clusters balance over the resident
+// CTAs without a launch per cluster.
+template <bool MIXED>
+__global__ void __launch_bounds__(kThreads) k_residual(SolveArgs A) {
+    __shared__ int s_q;
+    extern __shared__ __align__(16) float stage32[];
+    for (;;) {
+        __syncthreads();   // every thread has read the previous index
+        if (threadIdx.x == 0) s_q = atomicAdd(A.next, 1);
+        __syncthreads();
+        const int q = s_q;
+        if (q >= A.ncl) break;
+        if constexpr (MIXED) solve_cluster_mixed(A, A.order[q], stage32);
+        else solve_cluster_fp64(A, A.order[q]);
     }
 }
 
@@ -632,18 +647,22 @@ cudaError_t launch_posterior(const SolveArgs &a, int npairs, const double *Tc, d
 
 cudaError_t launch_residual(const SolveArgs &a, int nclusters, bool mixed, cudaStream_t s) {
     if (nclusters <= 0) return cudaSuccess;
+    const int ld = a.np_max + 1;
+    const size_t sh = mixed ? std::max(3 * (size_t)ld * ld * sizeof(float), 2 * (size_t)ld * ld * sizeof(float2)) : 0;
+    auto kern = mixed ? k_residual<true> : k_residual<false>;
+    cudaError_t e;
+    if (sh > 48 * 1024 && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh)) != cudaSuccess)
+        return e;
+    // resident CTAs: occupancy x SMs, at most one per cluster (the per-CTA scratch G1 has nclusters slots)
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sh)) != cudaSuccess)
+        return e;
+    const int grid = std::max(1, std::min(nclusters, std::max(per_sm, 1) * sms));
+    if ((e = cudaMemsetAsync(a.next, 0, sizeof(int), s)) != cudaSuccess) return e;
     count_launch();
-    if (mixed) {
-        const int ld = a.np_max + 1;
-        const size_t sh = std::max(3 * (size_t)ld * ld * sizeof(float), 2 * (size_t)ld * ld * sizeof(float2));
-        if (sh > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_residual_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-            if (e != cudaSuccess) return e;
-        }
-        k_residual_mixed<<<nclusters, kThreads, sh, s>>>(a);
-    } else {
-        k_residual<<<nclusters, kThreads, 0, s>>>(a);
-    }
+    kern<<<grid, kThreads, sh, s>>>(a);
     return cudaGetLastError();
 }
 
