@@ -1,5 +1,6 @@
 """Benchmark of the MBE(3)-OSV-MP2 hot path on GB300: one step = one geometry's energy AND gradient
-(osv_build -> cluster_residual_solve -> mbe3_combine -> energy -> gradient_backward) on a synthetic workload of
+(osv_build -> cluster_residual_solve -> mbe3_combine -> energy -> gradient_backward, recorded once as a CUDA graph by
+osv_graph_capture and replayed by osv_graph_launch, one replay per step) on a synthetic workload of
 paper_2106_06149_gb300.synth.WORKLOADS, by default workload 2: 256 LMOs in a 20 A cube, n_vir 1500, n_aux 6000,
 7 A fitting domains, B in FP32, l_osv 1e-4 capped at 40 OSVs, 8/6 A pair/triple cutoffs (256 + 5212 + 8872
 clusters), the mixed-precision and batching workload the metric is quoted on.
@@ -164,9 +165,10 @@ def run_gpu(args):
     dB = torch.zeros_like(dp.B)
     dF = torch.zeros_like(dp.f_occ)
 
-    def step():
-        osvmbe.run_energy(ctx, dp, prm)
-        ctx.gradient_backward(1.0, dB, dF)
+    res = {}
+
+    def step():   # one replay of the recorded step: build, solves, combination, energy, adjoint into dB/dF
+        res["E"] = ctx.graph_launch()
 
     def barrier():
         if world > 1:
@@ -185,41 +187,36 @@ def run_gpu(args):
         return t0.elapsed_time(t1) / k
 
     warm = max(args.warmup, 3)
-    # ---- the plain FP64 GPU path (reference point of the mixed path): one warm-up step, then fp64_steps timed
+    # ---- the plain FP64 GPU path (reference point of the mixed path): one eager step and its recording as a CUDA
+    # graph, then fp64_steps timed replays (with their stage events)
     prm.precision = 0
-    step()
-    fp64_ms = timed_steps(max(args.fp64_steps, 1))
-    E64, _ = ctx.energy()
-    flops64 = ctx.residual_flops()
-    dB.zero_()
-    dF.zero_()
+    ctx.graph_capture(dp, prm, 1.0, dB, dF)
     ctx.profile(True)
-    step()
-    torch.cuda.synchronize()
+    fp64_ms = timed_steps(max(args.fp64_steps, 1))
     stages64 = ctx.profile_read()
     ctx.profile(False)
+    E64 = res["E"][0]
+    flops64 = ctx.residual_flops()
     dB64, dF64 = dB.clone(), dF.clone()
-    # ---- the headline path
+    # ---- the headline path: re-plan (and tune) for the mixed precision, record, warm up
     prm.precision = prec
+    ctx.graph_capture(dp, prm, 1.0, dB, dF)
+    graph_kernels = ctx.graph_kernels()
     for _ in range(warm):
         step()
     torch.cuda.synchronize()
     flops_exec = ctx.residual_flops()
     upd32, ev64, uncv = ctx.solve_counts()
-    tuned = ctx.autotune_report()   # launch shapes picked when the mixed plan was built (first warm-up step)
+    tuned = ctx.autotune_report()   # launch shapes picked when the mixed plan was built
     # the metric's work per step: the residual FLOPs of the FP64 solve to tol (the iterations the problem
     # needs); the mixed solve's own count (FP32 iterations + FP64 evaluations) is reported beside it
     flops_step = flops64
-    E, E_lin = ctx.energy()
-    dB.zero_()
-    dF.zero_()
-    step()
-    torch.cuda.synchronize()
+    E, E_lin = res["E"]
     grad_diff = float((dB.double() - dB64.double()).abs().max())
     gradF_diff = float((dF - dF64).abs().max())
     del dB64, dF64
 
-    # ---- timed region (device-resident inputs)
+    # ---- timed region (device-resident inputs; graph replays, each read back E on the host)
     ctx.profile(True)
     l0 = ctypes_launches(osvmbe)
     with ClockSampler(local) as clk:
@@ -230,7 +227,8 @@ def run_gpu(args):
     ms, flops_all = reduce_over_ranks(ms, flops_step, world, "cuda")
     value = flops_all / (ms * 1e-3) / 1e12
 
-    # ---- end to end through the C ABI with host buffers: h2d of B, F, eps; d2h of E, dB, dF
+    # ---- end to end through the C ABI with host buffers: h2d of B, F, eps into the recorded step's input buffers;
+    # the replay (E back to the host); d2h of dB, dF
     hB = torch.from_numpy(np.ascontiguousarray(p.B)).pin_memory()
     hF = torch.from_numpy(np.ascontiguousarray(p.f_occ)).pin_memory()
     he = torch.from_numpy(np.ascontiguousarray(p.eps_vir)).pin_memory()
@@ -241,10 +239,7 @@ def run_gpu(args):
         dp.B.copy_(hB, non_blocking=True)
         dp.f_occ.copy_(hF, non_blocking=True)
         dp.eps_vir.copy_(he, non_blocking=True)
-        dB.zero_()
-        dF.zero_()
-        osvmbe.run_energy(ctx, dp, prm)        # energy() reads E back to the host
-        ctx.gradient_backward(1.0, dB, dF)
+        ctx.graph_launch()
         odB.copy_(dB, non_blocking=True)
         odF.copy_(dF, non_blocking=True)
 
@@ -289,6 +284,8 @@ def run_gpu(args):
         "e2e": {"value": flops_all / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
+        "graph": {"kernels_per_step": int(graph_kernels),
+                  "note": "each step is one replay of the whole step recorded as a CUDA graph (osv_graph_capture)"},
         "clocks": clk.summary(),
         "autotune": tuned,
     }

@@ -174,6 +174,26 @@ osv_status energy(osv_ctx *ctx, double *E_out, double *E_linear_out);
  * OSV_ERR_NUMERIC if a device step of the build, the solve or the adjoint reported one. */
 osv_status gradient_backward(osv_ctx *ctx, double dE_scale, void *dE_dB, double *dE_dFocc);
 
+/* One whole step recorded as a CUDA graph (no counterpart in the paper; the per-geometry loop of an energy and
+ * gradient calculation).  osv_graph_capture first runs one eager step (osv_build -> cluster_residual_solve ->
+ * mbe3_combine -> energy, and gradient_backward when dE_dB or dE_dFocc is non-NULL), which plans and tunes a new
+ * shape and reports any failure of the step itself; it then records the same step, from the T_kk Gram to the
+ * gradient outputs, as one graph: every launch, the zeroing of dE_dB and dE_dFocc (DEVICE, as in
+ * gradient_backward, but OVERWRITTEN by the step rather than added to) and the copies of E, E_linear, the error
+ * word and the per-cluster iteration counts into a pinned host block.  clusters_build must precede it.  The graph
+ * holds the device addresses of prob (B, f_occ, eps_vir), of dE_dB and of dE_dFocc and the parameters as given:
+ * change their VALUES in place between launches (a new geometry), never their addresses, sizes or the parameters
+ * (capture again instead).  osv_graph_launch replays the step on the context's stream, synchronises and returns E
+ * and E_linear (HOST, either may be NULL) with energy()'s and gradient_backward()'s error rules (OSV_ERR_NOCONV,
+ * OSV_ERR_NUMERIC, OSV_ERR_TIMEOUT).  Any call that re-plans (clusters_build, osv_build of another shape or
+ * precision, osv_overlap_metric) drops the graph; osv_graph_launch then returns OSV_ERR_INVALID.
+ * osv_graph_kernels: the kernels one replay launches (0 without a graph); the launch counter of
+ * osv_kernel_launches grows by that much per replay and not at all while recording. */
+osv_status osv_graph_capture(osv_ctx *ctx, const osv_problem *prob, const osv_params *params, double dE_scale,
+                             void *dE_dB, double *dE_dFocc);
+osv_status osv_graph_launch(osv_ctx *ctx, double *E_out, double *E_linear_out);
+osv_status osv_graph_kernels(osv_ctx *ctx, long long *count);
+
 /* Autotuner of the launch shapes (no counterpart in the paper).  When a context plans a problem in the mixed
  * precision (the first osv_build of a new shape), it times on the device, with CUDA events, the candidate launch
  * shapes of its tunable kernels and keeps the fastest: the FP32 Householder tridiagonalisation (a pair of CTAs per
@@ -209,7 +229,9 @@ osv_status osv_eigenvalues(osv_ctx *ctx, int k, double *w_out);
 osv_status osv_pair_amplitudes(osv_ctx *ctx, int i, int j, double *t_out);
 
 /* Per-stage timing: osv_profile_enable(ctx, 1) clears previous records and makes every later call record a
- * pair of CUDA events around each of its stages on the context's stream; (ctx, 0) stops and clears.
+ * pair of CUDA events around each of its stages on the context's stream; (ctx, 0) stops and clears.  A recorded
+ * step (osv_graph_capture) carries its own stage events, and each osv_graph_launch made while profiling is on adds
+ * their times.
  * osv_profile_read (synchronises) returns the stages in first-seen order: names[32*q] (NUL-terminated, up to
  * 31 chars), summed milliseconds ms[q] and number of records calls[q] for q < min(max_stages, *n_stages);
  * names, ms, calls may be NULL.  Profiling adds event records; leave it off when capturing a CUDA graph. */

@@ -236,6 +236,7 @@ osv_status osv_destroy(osv_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     ctx->release();
+    if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
     for (auto &e : ctx->pev) {
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
@@ -903,14 +904,18 @@ osv_status run_osv_build(osv_ctx *c) {
     return OSV_OK;
 }
 
-osv_status device_error(osv_ctx *c) {
-    int h = 0;
-    cudaError_t e = cudaMemcpy(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return c->cuda_fail(e, "read error word");
+osv_status error_word_status(osv_ctx *c, int h) {
     if (h == kDevEighNoConv) return c->fail(OSV_ERR_TIMEOUT, "eigensolver hit its iteration cap");
     if (h == kDevNonFinite) return c->fail(OSV_ERR_NUMERIC, "non-finite value in T_kk (check B, eps, f_occ)");
     if (h == kDevTimeout) return c->fail(OSV_ERR_TIMEOUT, "a bounded tensor-core wait expired");
     return OSV_OK;
+}
+
+osv_status device_error(osv_ctx *c) {
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return c->cuda_fail(e, "read error word");
+    return error_word_status(c, h);
 }
 
 }  // namespace
@@ -1482,6 +1487,157 @@ osv_status gradient_backward(osv_ctx *c, double dE_scale, void *dE_dB, double *d
     return device_error(c);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Pinned host block the recorded step copies its results into: E and E_linear, the error word, per-cluster
+// iteration counts.
+constexpr size_t kPinE = 0, kPinErr = 16, kPinIters = 24;
+
+// Enqueue one step on c->stream with the plan already in place (nothing allocates, uploads or synchronises):
+// osv_build's device steps, the cluster solves, the MBE(3) combination, the energy and, when grad, the adjoint into
+// zeroed dB/dF; then the results are copied into the pinned block.
+osv_status record_step(osv_ctx *c, bool grad, double scale, void *dB, double *dF, size_t nb, size_t nf) {
+    osv_status st;
+    cudaError_t e;
+    if ((st = run_osv_build(c)) != OSV_OK) return st;
+    if ((st = cluster_residual_solve(c, nullptr, nullptr)) != OSV_OK) return st;
+    if ((st = mbe3_combine(c)) != OSV_OK) return st;
+    {
+        StageTimer t(*c, "energy");
+        e = launch_energy(c->pinfo.d, c->rdim, c->Kt, c->Tc, (int)c->pairs.size(), c->lin, c->Ecl, c->cinfo.d,
+                          (int)c->cl.size(), c->Eout, c->stream);
+    }
+    if (e != cudaSuccess) return c->cuda_fail(e, "energy");
+    if (grad) {
+        if (dB && (e = cudaMemsetAsync(dB, 0, nb, c->stream)) != cudaSuccess) return c->cuda_fail(e, "memset dE_dB");
+        if (dF && (e = cudaMemsetAsync(dF, 0, nf, c->stream)) != cudaSuccess) return c->cuda_fail(e, "memset dE_dF");
+        std::string msg;
+        if ((e = c->adj.run(*c, scale, dB, dF, msg)) != cudaSuccess) return c->cuda_fail(e, msg.c_str());
+    }
+    char *h = (char *)c->gpin;
+    if ((e = cudaMemcpyAsync(h + kPinE, c->Eout, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(h + kPinErr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h + kPinIters, c->iters, c->cl.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                             c->stream)) != cudaSuccess)
+        return c->cuda_fail(e, "result copies");
+    return OSV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+osv_status osv_graph_capture(osv_ctx *c, const osv_problem *pb, const osv_params *prm, double dE_scale,
+                             void *dE_dB, double *dE_dFocc) {
+    if (!c) return OSV_ERR_INVALID;
+    cudaSetDevice(c->device);
+    c->graph_release();
+    const bool grad = dE_dB || dE_dFocc;
+    osv_status st;
+    cudaError_t e;
+    // one eager step: plans (and tunes) a new shape, checks the inputs and leaves this step's results in place
+    if ((st = osv_build(c, pb, prm, nullptr)) != OSV_OK || (st = cluster_residual_solve(c, nullptr, nullptr)) != OSV_OK ||
+        (st = mbe3_combine(c)) != OSV_OK)
+        return st;
+    double E0, El0;
+    if ((st = energy(c, &E0, &El0)) != OSV_OK) return st;
+    const size_t nb = (size_t)c->aux_ptr[c->n_occ] * c->n_vir * (c->B_dtype == 0 ? sizeof(double) : sizeof(float));
+    const size_t nf = (size_t)c->n_occ * c->n_occ * sizeof(double);
+    if (grad) {
+        if (dE_dB && (e = cudaMemsetAsync(dE_dB, 0, nb, c->stream)) != cudaSuccess) return c->cuda_fail(e, "memset");
+        if (dE_dFocc && (e = cudaMemsetAsync(dE_dFocc, 0, nf, c->stream)) != cudaSuccess)
+            return c->cuda_fail(e, "memset");
+        if ((st = gradient_backward(c, dE_scale, dE_dB, dE_dFocc)) != OSV_OK) return st;
+    }
+    if ((e = cudaMallocHost(&c->gpin, kPinIters + std::max<size_t>(c->cl.size(), 1) * sizeof(int))) != cudaSuccess) {
+        c->gpin = nullptr;
+        return c->cuda_fail(e, "pinned result block");
+    }
+    if (!c->gstream && (e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)) != cudaSuccess) {
+        c->gstream = nullptr;
+        return c->cuda_fail(e, "capture stream");
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "graph capture");
+    // record the same step on the capture stream; the launches it counts are recorded, not run
+    cudaStream_t user = c->stream;
+    c->capturing = true;
+    c->stream = c->gstream;
+    const long long l0 = g_launches.load();
+    cudaGraph_t g = nullptr;
+    if ((e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+        st = c->cuda_fail(e, "begin capture");
+    } else {
+        st = record_step(c, grad, dE_scale, dE_dB, dE_dFocc, nb, nf);
+        const cudaError_t e2 = cudaStreamEndCapture(c->gstream, &g);
+        if (st == OSV_OK && e2 != cudaSuccess) st = c->cuda_fail(e2, "end capture");
+    }
+    g_launches.fetch_sub(g_launches.load() - l0);
+    c->stream = user;
+    c->capturing = false;
+    if (st == OSV_OK) {
+        size_t nn = 0;
+        if ((e = cudaGraphGetNodes(g, nullptr, &nn)) == cudaSuccess) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if ((e = cudaGraphGetNodes(g, nodes.data(), &nn)) == cudaSuccess)
+                for (cudaGraphNode_t x : nodes) {
+                    cudaGraphNodeType t;
+                    if ((e = cudaGraphNodeGetType(x, &t)) != cudaSuccess) break;
+                    if (t == cudaGraphNodeTypeKernel) ++c->graph_kernels;
+                }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            st = c->cuda_fail(e, "graph instantiate");
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    if (st != OSV_OK) {
+        c->graph_release();
+        return st;
+    }
+    c->graph_grad = grad;
+    return OSV_OK;
+}
+
+osv_status osv_graph_launch(osv_ctx *c, double *E_out, double *E_linear_out) {
+    if (!c) return OSV_ERR_INVALID;
+    if (!c->gexec) return c->fail(OSV_ERR_INVALID, "no recorded step: osv_graph_capture (again after a re-plan)");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+    if (e != cudaSuccess) return c->cuda_fail(e, "graph launch");
+    count_launch(c->graph_kernels);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return c->cuda_fail(e, "graph launch");
+    c->solved = c->combined = true;
+    if (c->prof)
+        for (auto &ev : c->gev) {
+            float t = 0.f;
+            if ((e = cudaEventElapsedTime(&t, ev.a, ev.b)) != cudaSuccess) return c->cuda_fail(e, "stage event time");
+            c->gtimes.push_back({ev.name, t});
+        }
+    const char *h = (const char *)c->gpin;
+    osv_status st = error_word_status(c, *(const int *)(h + kPinErr));
+    if (st != OSV_OK) return st;
+    double E[2];
+    memcpy(E, h + kPinE, sizeof(E));
+    if (E_out) *E_out = E[0];
+    if (E_linear_out) *E_linear_out = E[1];
+    if (!std::isfinite(E[0])) return c->fail(OSV_ERR_NUMERIC, "energy is not finite");
+    const int *it = (const int *)(h + kPinIters);
+    const long long bad = std::count_if(it, it + c->cl.size(), [](int v) { return v < 0; });
+    if (bad) return c->fail(OSV_ERR_NOCONV, std::to_string(bad) + " clusters did not converge within max_iter");
+    return OSV_OK;
+}
+
+osv_status osv_graph_kernels(osv_ctx *c, long long *count) {
+    if (!c || !count) return OSV_ERR_INVALID;
+    *count = c->gexec ? c->graph_kernels : 0;
+    return OSV_OK;
+}
+
 osv_status osv_autotune(osv_ctx *c, int on) {
     if (!c) return OSV_ERR_INVALID;
     c->autotune = on != 0;
@@ -1520,6 +1676,7 @@ osv_status osv_profile_enable(osv_ctx *c, int on) {
         c->pool.push_back(e.b);
     }
     c->pev.clear();
+    c->gtimes.clear();
     c->prof = on != 0;
     return OSV_OK;
 }
@@ -1537,6 +1694,11 @@ osv_status osv_profile_read(osv_ctx *c, int max_stages, char *names, double *ms,
         if (!acc.count(ev.name)) order.push_back(ev.name);
         acc[ev.name].first += t;
         acc[ev.name].second += 1;
+    }
+    for (auto &gt : c->gtimes) {
+        if (!acc.count(gt.first)) order.push_back(gt.first);
+        acc[gt.first].first += gt.second;
+        acc[gt.first].second += 1;
     }
     *n_stages = (int)order.size();
     for (int q = 0; q < (int)order.size() && q < max_stages; ++q) {

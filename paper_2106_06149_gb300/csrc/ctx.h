@@ -118,6 +118,27 @@ struct osv_ctx {
     // plan-time autotuner (mixed precision): launch shapes timed on the device, the fastest kept
     bool autotune = true;
     std::string tune_report;               // JSON: per tuned item the rule's choice, the tuned choice, timings
+    // one whole step recorded as a CUDA graph (osv_graph_capture / osv_graph_launch)
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;        // non-blocking stream the step is recorded on
+    long long graph_kernels = 0;           // kernel nodes of the recorded step
+    bool graph_grad = false;
+    void *gpin = nullptr;                  // pinned host: E, E_linear, error word, per-cluster iterations
+    bool capturing = false;                // recording: stage timers become event-record nodes of the graph
+    std::vector<osv::ProfEvent> gev;       // the stage events recorded in the graph
+    std::vector<std::pair<const char *, float>> gtimes;   // stage times of the replays run while profiling
+    void graph_release() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        for (auto &e : gev) {
+            pool.push_back(e.a);
+            pool.push_back(e.b);
+        }
+        gev.clear();
+        if (gpin) cudaFreeHost(gpin);
+        gpin = nullptr;
+        graph_kernels = 0;
+    }
 
     // per-stage CUDA-event profiling (osv_profile_enable / osv_profile_read)
     bool prof = false;
@@ -200,6 +221,7 @@ struct osv_ctx {
         oz_cap = 0;
         for (osv::TcTiles *t : {&oz_gram, &oz_w, &oz_k}) osv::tc_tiles_free(*t);
         adj.release();
+        graph_release();
         built = solved = combined = post_built = false;
     }
     int pid(int i, int j) const {
@@ -220,15 +242,19 @@ struct StageTimer {
     osv_ctx &c;
     osv::ProfEvent e{};
     StageTimer(osv_ctx &ctx, const char *name) : c(ctx) {
-        if (!c.prof) return;
+        if (!c.prof && !c.capturing) return;
         e.name = name;
         e.a = c.take_event();
         e.b = c.take_event();
-        cudaEventRecord(e.a, c.stream);
+        record(e.a);
+    }
+    void record(cudaEvent_t ev) {
+        if (c.capturing) cudaEventRecordWithFlags(ev, c.stream, cudaEventRecordExternal);
+        else cudaEventRecord(ev, c.stream);
     }
     ~StageTimer() {
-        if (!c.prof || !e.a) return;
-        cudaEventRecord(e.b, c.stream);
-        c.pev.push_back(e);
+        if (!e.a) return;
+        record(e.b);
+        (c.capturing ? c.gev : c.pev).push_back(e);
     }
 };

@@ -24,7 +24,8 @@ EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv
            "osv_residual_flops", "osv_kernel_launches", "osv_syev_batched_noalloc", "osv_adjoint_flops",
            "osv_solve_counts", "osv_residual_work", "osv_set_wait_budget",
            "osv_pair_amplitudes", "osv_overlap_metric", "clusters_build_osv",
-           "posterior_correction", "weak_pairs_energy", "osv_autotune", "osv_autotune_report"]
+           "posterior_correction", "weak_pairs_energy", "osv_autotune", "osv_autotune_report",
+           "osv_graph_capture", "osv_graph_launch", "osv_graph_kernels"]
 
 
 class OsvParams(ctypes.Structure):
@@ -83,6 +84,9 @@ def load(path=LIB_PATH):
         "weak_pairs_energy": ([V, V, D, D, P(D), P(I)], I),
         "osv_autotune": ([V, I], I),
         "osv_autotune_report": ([V, V, I, P(I)], I),
+        "osv_graph_capture": ([V, P(OsvProblem), P(OsvParams), D, V, V], I),
+        "osv_graph_launch": ([V, P(D), P(D)], I),
+        "osv_graph_kernels": ([V, P(ctypes.c_longlong)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -260,6 +264,30 @@ class Context:
         _check(load().gradient_backward(self.h, float(scale), _ptr(dB) if dB is not None else None,
                                         _ptr(dF) if dF is not None else None), self.h)
 
+    def graph_capture(self, prob: DeviceProblem, params=None, scale=1.0, dB=None, dF=None, B=None, f_occ=None):
+        """Run one eager step, then record the whole step (build, solves, combination, energy and, with dB or dF,
+        the adjoint into those buffers, which each replay overwrites) as a CUDA graph.  The graph keeps the device
+        addresses of the problem arrays and of dB/dF: update their values in place between graph_launch calls."""
+        if params is not None:
+            self._prm = params_struct(params)
+        ps = prob.struct(B=B, f_occ=f_occ)
+        self._keep = (prob, B, f_occ)
+        self._graph_keep = (prob, B, f_occ, dB, dF)
+        _check(load().osv_graph_capture(self.h, ctypes.byref(ps), ctypes.byref(self._prm), float(scale),
+                                        _ptr(dB) if dB is not None else None, _ptr(dF) if dF is not None else None),
+               self.h)
+
+    def graph_launch(self):
+        """Replay the recorded step; returns (E, E_linear)."""
+        E, El = ctypes.c_double(), ctypes.c_double()
+        _check(load().osv_graph_launch(self.h, ctypes.byref(E), ctypes.byref(El)), self.h)
+        return E.value, El.value
+
+    def graph_kernels(self):
+        n = ctypes.c_longlong()
+        _check(load().osv_graph_kernels(self.h, ctypes.byref(n)), self.h)
+        return n.value
+
     def autotune(self, on=True):
         """Plan-time autotuning of launch shapes (mixed precision); on by default."""
         _check(load().osv_autotune(self.h, 1 if on else 0), self.h)
@@ -345,6 +373,13 @@ def syev_batched(A: torch.Tensor, stream=None):
     Zt = torch.empty(b, n, n, dtype=torch.float64, device=A.device)
     _check(load().osv_syev_batched(_ptr(A), n, b, _ptr(w), _ptr(Zt), _stream_handle(stream)))
     return w, Zt
+
+
+def kernel_launches():
+    """Kernels the library has launched in this process (osv_kernel_launches)."""
+    n = ctypes.c_longlong()
+    _check(load().osv_kernel_launches(ctypes.byref(n)))
+    return n.value
 
 
 def run_energy(ctx: Context, prob: DeviceProblem, params, B=None, f_occ=None):
