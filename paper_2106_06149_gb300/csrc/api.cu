@@ -737,6 +737,7 @@ osv_status build_plan(osv_ctx *c) {
 // The report (osv_autotune_report) lists, per item, the rule's choice, the tuned choice and the timings.
 osv_status autotune_plan(osv_ctx *c) {
     c->tune_report.clear();
+    if (c->osv_mixed && c->tri_force >= 0) c->refine.tri_variant = c->tri_force;
     if (!c->autotune || !c->osv_mixed) return OSV_OK;
     cudaStream_t s = c->stream;
     cudaEvent_t a = c->take_event(), b = c->take_event();
@@ -754,19 +755,46 @@ osv_status autotune_plan(osv_ctx *c) {
     const char *shape_name[5] = {"64x64", "80x80", "48x80", "80x48", "48x48"};
     std::string js = "{";
     double gain = 0.0, spent = 0.0;
-    // 1. tridiagonalisation launch shape
-    {
-        const int n = c->n_occ, nv = c->n_vir;
-        double t[2];
-        for (int v = 0; v < 2; ++v) t[v] = timed([&] { return osv_tridiag<float>(c->refine.tri_d, n, nv, s, v); }, 1);
-        const int best = t[1] < t[0] ? 1 : 0;
-        c->refine.tri_variant = best;
-        gain += t[0] - t[best];
-        spent += t[0] + t[1];
-        char buf[256];
-        snprintf(buf, sizeof buf, "\"tridiag\": {\"rule\": \"cta_pair\", \"choice\": \"%s\", \"ms\": {\"cta_pair\": %.3f, "
-                 "\"single_cta_2_per_sm\": %.3f}}", best ? "single_cta_2_per_sm" : "cta_pair", t[0], t[1]);
-        js += buf;
+    // 1. tridiagonalisation launch shape (unless fixed by osv_set_tridiag_variant), timed on the first
+    // min(n_occ, 2 x 152) matrices (a full wave of the widest variant); a variant this GPU cannot launch (no room
+    // for its cluster) is skipped
+    if (c->tri_force >= 0) {
+        js += "\"tridiag\": {\"choice\": \"fixed\"}";
+    } else {
+        const char *tri_name[kTriVariants] = {"cta_pair", "single_cta_2_per_sm", "cluster_4", "cluster_8", "cluster_16"};
+        const int m = std::min(c->n_occ, 2 * 152), nv = c->n_vir;
+        double t[kTriVariants];
+        int best = 0;
+        for (int v = 0; v < kTriVariants; ++v) {
+            t[v] = -1.0;
+            if (e != cudaSuccess) break;
+            t[v] = timed([&] { return osv_tridiag<float>(c->refine.tri_d, m, nv, s, v); }, 1);
+            if (e == cudaErrorNotSupported) {
+                e = cudaSuccess;
+                t[v] = -1.0;
+                continue;
+            }
+            if (e == cudaSuccess && t[v] < t[best]) best = v;
+        }
+        if (e == cudaSuccess) {
+            c->refine.tri_variant = best;
+            gain += (t[0] - t[best]) * c->n_occ / m;
+            std::string ms = "{";
+            for (int v = 0; v < kTriVariants; ++v) {
+                char b2[64];
+                if (t[v] >= 0.0) {
+                    spent += t[v];
+                    snprintf(b2, sizeof b2, "%s\"%s\": %.3f", ms.size() > 1 ? ", " : "", tri_name[v], t[v]);
+                } else {
+                    snprintf(b2, sizeof b2, "%s\"%s\": null", ms.size() > 1 ? ", " : "", tri_name[v]);
+                }
+                ms += b2;
+            }
+            char buf[160];
+            snprintf(buf, sizeof buf, "\"tridiag\": {\"rule\": \"cta_pair\", \"choice\": \"%s\", \"matrices_timed\": %d, \"ms\": ",
+                     tri_name[best], m);
+            js += buf + ms + "}}";
+        }
     }
     // 2. double-float GEMM tile shapes
     std::vector<std::pair<std::string, GemmBatch *>> batches = {
@@ -1652,6 +1680,13 @@ osv_status osv_autotune_report(osv_ctx *c, char *buf, int len, int *needed) {
         strncpy(buf, c->tune_report.c_str(), (size_t)len - 1);
         buf[len - 1] = 0;
     }
+    return OSV_OK;
+}
+
+osv_status osv_set_tridiag_variant(osv_ctx *c, int variant) {
+    if (!c) return OSV_ERR_INVALID;
+    if (variant < -1 || variant >= kTriVariants) return c->fail(OSV_ERR_INVALID, "tridiagonalisation variant out of range");
+    c->tri_force = variant;
     return OSV_OK;
 }
 

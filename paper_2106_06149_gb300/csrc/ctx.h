@@ -117,6 +117,7 @@ struct osv_ctx {
     long long wait_budget = 0;             // tensor-core main-loop wait budget in clock cycles (0 = default)
     // plan-time autotuner (mixed precision): launch shapes timed on the device, the fastest kept
     bool autotune = true;
+    int tri_force = -1;                    // FP32 tridiagonalisation launch shape fixed by the caller (-1: tuned)
     std::string tune_report;               // JSON: per tuned item the rule's choice, the tuned choice, timings
     // one whole step recorded as a CUDA graph (osv_graph_capture / osv_graph_launch)
     cudaGraphExec_t gexec = nullptr;

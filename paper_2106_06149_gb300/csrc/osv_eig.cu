@@ -57,6 +57,126 @@ __device__ __forceinline__ R warp_sum_t(R v) {
     return v;
 }
 
+// Pass (b) of step k of the Householder reduction over one CTA's rows: the rows rstart + RS j (j >= 0) of the lower
+// triangle of the trailing matrix, warp w taking the rows rstart + RS (w + NW q), q < 4, per round so that several
+// independent loads are in flight per lane.  Applies the pending update of step k-1 (vo, po) to columns k+1 .. r of
+// each row, writes the row sum of A v into p[r], scatters the column sums into cs (one shared-memory add per column
+// and group of four rows) and hands the updated element of column k+1 of each row to stash(r, x).  UV: groups of
+// four rows per lane in flight in the 16-byte path (two CTAs per SM leave a 64-register budget: UV = 1).
+template <class R, int UV, class Stash>
+__device__ __forceinline__ void tri_rows_pass(R *__restrict__ A, long long lda, bool vec, int k, int n, int rstart,
+                                              int RS, const R *__restrict__ vo, const R *__restrict__ po,
+                                              const R *__restrict__ v, R *cs, R *p, Stash stash) {
+    constexpr int NW = kTT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int r0 = rstart + RS * wid; r0 < n; r0 += 4 * RS * NW) {
+        R *row[4];
+        R vr[4], pr[4], vq[4], acc[4];
+        int rq[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = r0 + q * RS * NW;
+            const bool ok = r < n;
+            rq[q] = ok ? r : -1;   // columns c <= rq[q] belong to row q
+            row[q] = A + (long long)(ok ? r : r0) * lda;
+            vr[q] = ok ? vo[r] : (R)0;
+            pr[q] = ok ? po[r] : (R)0;
+            vq[q] = ok ? v[r] : (R)0;
+            acc[q] = 0;
+        }
+        const int nr = min(4, (n - 1 - r0) / (RS * NW) + 1);
+        const int hi = rq[nr - 1];   // the group's longest row
+        auto col = [&](int c) {      // one column of the (up to) four rows
+            const R poc = po[c], voc = vo[c], vc = v[c];
+            R cl = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nr && c <= rq[q]) {
+                    const R x = row[q][c] - vr[q] * poc - pr[q] * voc;
+                    row[q][c] = x;
+                    acc[q] = fma(x, vc, acc[q]);
+                    if (c < rq[q]) cl = fma(x, vq[q], cl);
+                    if (c == k + 1) stash(rq[q], x);
+                }
+            if (c < hi) atomicAdd(cs + c, cl);
+        };
+        bool vdone = false;
+        if constexpr (sizeof(R) == 4) {
+            if (vec) {
+                // 16-byte column groups [cb, ce) inside [k + 1, hi], UV groups of four rows per lane in flight;
+                // the ragged head [k + 1, cb) and tail [max(ce, cb), hi] (three columns at most each) column by
+                // column.  A group that reaches past a shorter row stores that row's elements back unchanged.
+                const int cb = min((k + 4) & ~3, hi + 1), ce = (hi + 1) & ~3;
+                if (lane < 3 && k + 1 + lane < cb) col(k + 1 + lane);
+                if (lane < 3 && max(ce, cb) + lane <= hi) col(max(ce, cb) + lane);
+                const int nch = ce > cb ? (ce - cb) >> 2 : 0;
+                for (int j0 = lane; j0 < nch; j0 += 32 * UV) {
+                    float4 a[UV][4];
+#pragma unroll
+                    for (int u = 0; u < UV; ++u) {
+                        const int j = j0 + 32 * u;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (q < nr && j < nch && cb + 4 * j <= rq[q])
+                                a[u][q] = *reinterpret_cast<const float4 *>(row[q] + cb + 4 * j);
+                    }
+#pragma unroll
+                    for (int u = 0; u < UV; ++u) {
+                        const int j = j0 + 32 * u;
+                        if (j >= nch) break;
+                        const int c = cb + 4 * j;
+                        const float4 poc = *reinterpret_cast<const float4 *>(po + c);
+                        const float4 voc = *reinterpret_cast<const float4 *>(vo + c);
+                        const float4 vc = *reinterpret_cast<const float4 *>(v + c);
+                        float4 cl = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (q < nr && c <= rq[q]) {
+                                float4 x = a[u][q];
+                                const int lim = rq[q] - c;   // elements c + e with e <= lim belong to the row
+                                x.x = x.x - vr[q] * poc.x - pr[q] * voc.x;
+                                acc[q] = fma(x.x, vc.x, acc[q]);
+                                if (lim > 0) cl.x = fma(x.x, vq[q], cl.x);
+                                if (lim >= 1) {
+                                    x.y = x.y - vr[q] * poc.y - pr[q] * voc.y;
+                                    acc[q] = fma(x.y, vc.y, acc[q]);
+                                    if (lim > 1) cl.y = fma(x.y, vq[q], cl.y);
+                                }
+                                if (lim >= 2) {
+                                    x.z = x.z - vr[q] * poc.z - pr[q] * voc.z;
+                                    acc[q] = fma(x.z, vc.z, acc[q]);
+                                    if (lim > 2) cl.z = fma(x.z, vq[q], cl.z);
+                                }
+                                if (lim >= 3) {
+                                    x.w = x.w - vr[q] * poc.w - pr[q] * voc.w;
+                                    acc[q] = fma(x.w, vc.w, acc[q]);
+                                    if (lim > 3) cl.w = fma(x.w, vq[q], cl.w);
+                                }
+                                *reinterpret_cast<float4 *>(row[q] + c) = x;
+                                if (c == k + 1) stash(rq[q], x.x);
+                            }
+                        // columns at or beyond the longest row's diagonal take no column sum
+                        if (c < hi) atomicAdd(cs + c, cl.x);
+                        if (c + 1 < hi) atomicAdd(cs + c + 1, cl.y);
+                        if (c + 2 < hi) atomicAdd(cs + c + 2, cl.z);
+                        if (c + 3 < hi) atomicAdd(cs + c + 3, cl.w);
+                    }
+                }
+                vdone = true;
+            }
+        }
+        if (!vdone) {
+            for (int c = k + 1 + lane; c <= hi; c += 32) col(c);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (q >= nr) break;
+            const R sum = warp_sum_t(acc[q]);
+            if (lane == 0) p[rq[q]] = sum;   // the row sum; the column sums are added below
+        }
+    }
+}
+
 // ---------------------------------------------------------------------- 1. Householder tridiagonalisation
 // A (n x n, lda; both triangles stored on input) overwritten; d, e (n), tau (n); reflector k stored in row k,
 // columns k+1 .. n-1 (H_k = I - tau_k v v^T).  Only the lower triangle of the trailing matrix is read and written:
@@ -146,120 +266,13 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag(const TriDescT<R> *__rest
         // (b) pending update of the lower triangle of rows r > k fused with the row and column sums of A v; a warp
         // takes four rows at a time so that several independent loads are in flight per lane (rows r = rank
         // (mod CL): warp w takes the rows rstart + CL (w + NW q), q < 4, per pass)
-        R *nxr = remote(nx);
         const int rstart = k + 1 + (int)((rank ^ (unsigned)(k + 1)) & (CL - 1));
-        for (int r0 = rstart + CL * wid; r0 < n; r0 += 4 * CL * NW) {
-            R *row[4];
-            R vr[4], pr[4], vq[4], acc[4];
-            int rq[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int r = r0 + q * CL * NW;
-                const bool ok = r < n;
-                rq[q] = ok ? r : -1;   // columns c <= rq[q] belong to row q
-                row[q] = A + (long long)(ok ? r : r0) * lda;
-                vr[q] = ok ? vo[r] : (R)0;
-                pr[q] = ok ? po[r] : (R)0;
-                vq[q] = ok ? v[r] : (R)0;
-                acc[q] = 0;
-            }
-            const int nr = min(4, (n - 1 - r0) / (CL * NW) + 1);
-            const int hi = rq[nr - 1];   // the group's longest row
-            auto col = [&](int c) {      // one column of the (up to) four rows
-                const R poc = po[c], voc = vo[c], vc = v[c];
-                R cl = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < nr && c <= rq[q]) {
-                        const R x = row[q][c] - vr[q] * poc - pr[q] * voc;
-                        row[q][c] = x;
-                        acc[q] = fma(x, vc, acc[q]);
-                        if (c < rq[q]) cl = fma(x, vq[q], cl);
-                        if (c == k + 1) {
-                            nx[rq[q]] = x;
-                            if (CL == 2) nxr[rq[q]] = x;
-                        }
-                    }
-                if (c < hi) atomicAdd(cs + c, cl);
-            };
-            bool vdone = false;
-            if constexpr (sizeof(R) == 4) {
-                if (vec) {
-                    // 16-byte column groups [cb, ce) inside [k + 1, hi], UV groups of four rows per lane in flight;
-                    // the ragged head [k + 1, cb) and tail [max(ce, cb), hi] (three columns at most each) column by
-                    // column.  A group that reaches past a shorter row stores that row's elements back unchanged.
-                    const int cb = min((k + 4) & ~3, hi + 1), ce = (hi + 1) & ~3;
-                    if (lane < 3 && k + 1 + lane < cb) col(k + 1 + lane);
-                    if (lane < 3 && max(ce, cb) + lane <= hi) col(max(ce, cb) + lane);
-                    const int nch = ce > cb ? (ce - cb) >> 2 : 0;
-                    constexpr int UV = MINB == 2 ? 1 : 3;   // two CTAs per SM: a 64-register budget
-                    for (int j0 = lane; j0 < nch; j0 += 32 * UV) {
-                        float4 a[UV][4];
-#pragma unroll
-                        for (int u = 0; u < UV; ++u) {
-                            const int j = j0 + 32 * u;
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                if (q < nr && j < nch && cb + 4 * j <= rq[q])
-                                    a[u][q] = *reinterpret_cast<const float4 *>(row[q] + cb + 4 * j);
-                        }
-#pragma unroll
-                        for (int u = 0; u < UV; ++u) {
-                            const int j = j0 + 32 * u;
-                            if (j >= nch) break;
-                            const int c = cb + 4 * j;
-                            const float4 poc = *reinterpret_cast<const float4 *>(po + c);
-                            const float4 voc = *reinterpret_cast<const float4 *>(vo + c);
-                            const float4 vc = *reinterpret_cast<const float4 *>(v + c);
-                            float4 cl = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                if (q < nr && c <= rq[q]) {
-                                    float4 x = a[u][q];
-                                    const int lim = rq[q] - c;   // elements c + e with e <= lim belong to the row
-                                    x.x = x.x - vr[q] * poc.x - pr[q] * voc.x;
-                                    acc[q] = fma(x.x, vc.x, acc[q]);
-                                    if (lim > 0) cl.x = fma(x.x, vq[q], cl.x);
-                                    if (lim >= 1) {
-                                        x.y = x.y - vr[q] * poc.y - pr[q] * voc.y;
-                                        acc[q] = fma(x.y, vc.y, acc[q]);
-                                        if (lim > 1) cl.y = fma(x.y, vq[q], cl.y);
-                                    }
-                                    if (lim >= 2) {
-                                        x.z = x.z - vr[q] * poc.z - pr[q] * voc.z;
-                                        acc[q] = fma(x.z, vc.z, acc[q]);
-                                        if (lim > 2) cl.z = fma(x.z, vq[q], cl.z);
-                                    }
-                                    if (lim >= 3) {
-                                        x.w = x.w - vr[q] * poc.w - pr[q] * voc.w;
-                                        acc[q] = fma(x.w, vc.w, acc[q]);
-                                        if (lim > 3) cl.w = fma(x.w, vq[q], cl.w);
-                                    }
-                                    *reinterpret_cast<float4 *>(row[q] + c) = x;
-                                    if (c == k + 1) {
-                                        nx[rq[q]] = x.x;
-                                        if (CL == 2) nxr[rq[q]] = x.x;
-                                    }
-                                }
-                            // columns at or beyond the longest row's diagonal take no column sum
-                            if (c < hi) atomicAdd(cs + c, cl.x);
-                            if (c + 1 < hi) atomicAdd(cs + c + 1, cl.y);
-                            if (c + 2 < hi) atomicAdd(cs + c + 2, cl.z);
-                            if (c + 3 < hi) atomicAdd(cs + c + 3, cl.w);
-                        }
-                    }
-                    vdone = true;
-                }
-            }
-            if (!vdone) {
-                for (int c = k + 1 + lane; c <= hi; c += 32) col(c);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (q >= nr) break;
-                const R sum = warp_sum_t(acc[q]);
-                if (lane == 0) p[rq[q]] = sum;   // the row sum; the column sums are added below
-            }
+        {
+            R *nxr = remote(nx);
+            tri_rows_pass<R, MINB == 2 ? 1 : 3>(A, lda, vec, k, n, rstart, CL, vo, po, v, cs, p, [&](int r, R x) {
+                nx[r] = x;
+                if (CL == 2) nxr[r] = x;
+            });
         }
         __syncthreads();
         // (c) the peer's column sums for this CTA's rows, then p = beta (row + column sums) for this CTA's rows
@@ -318,6 +331,147 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag(const TriDescT<R> *__rest
             D.d[b] = A[(long long)b * lda + b] - 2 * vo[b] * po[b];
             D.tau[a] = 0;
             A[(long long)a * lda + b] = 0;   // no reflector for the last two rows
+        } else if (n == 1) {
+            D.d[0] = A[0];
+        }
+        D.e[n - 1] = 0;
+        D.tau[n - 1] = 0;
+    }
+}
+
+// FP32 Householder reduction by a cluster of CL CTAs per matrix (CL = 4, 8 or 16; one CTA per SM).  Fewer matrices
+// are in flight at once than with one CTA or a pair per matrix, so their trailing triangles fit in L2 and the pass
+// of every step streams from L2 instead of HBM.  Row r belongs to CTA r mod CL.  Every CTA keeps full copies of v,
+// p, vo, po and of the stashed column and forms the reflector itself from its copy: the same operations in the same
+// order on the same values, hence the same bits on every CTA, so no reflector is sent.  The exchanges are the stash
+// (each row's owner writes its element into every CTA), the column sums (each CTA gathers its peers' partial sums for
+// its own rows), p (the owner of each entry writes it into every CTA) and the partial dot products p.v: two cluster
+// barriers per step.  The stash is double-buffered by the parity of k, since a CTA may start the next pass while a
+// peer still reads the previous column.  Results equal those of k_tridiag up to the order of the column sums.
+template <int CL>
+__global__ void __launch_bounds__(kTT, 1) k_tridiag_cl(const TriDescT<float> *__restrict__ descs) {
+    using R = float;
+    static_assert(CL == 4 || CL == 8 || CL == 16, "clusters of 4, 8 or 16 CTAs");
+    cg::cluster_group cluster = cg::this_cluster();
+    const unsigned rank = cluster.block_rank();
+    const TriDescT<R> D = descs[blockIdx.x / CL];
+    const int n = D.n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ns = (n + 3) & ~3;
+    R *v = reinterpret_cast<R *>(smem_raw), *p = v + ns, *vo = p + ns, *po = vo + ns;
+    R *nxb = po + ns;        // two stashes: column k + 1 as pass (b) of step k leaves it, in nxb + (k & 1) ns
+    R *cs = nxb + 2 * ns;    // column sums of A v over this CTA's rows
+    __shared__ R part[kTT / 32];
+    __shared__ R s_pv[CL];   // every CTA's partial p.v
+    __shared__ R s_beta;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int NW = kTT / 32;
+    // the same shared-memory location in CTA q of the cluster
+    auto at = [&](R *x, unsigned q) -> R * { return cluster.map_shared_rank(x, q); };
+    R *A = D.A;
+    const long long lda = D.lda;
+    const bool vec = (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+    for (int i = tid; i < n; i += kTT) {
+        vo[i] = 0;
+        po[i] = 0;
+        cs[i] = 0;
+    }
+    __syncthreads();
+    cluster.sync();   // every CTA resident and initialised before the first remote store
+    for (int k = 0; k + 2 < n; ++k) {
+        const bool own_k = (unsigned)(k & (CL - 1)) == rank;
+        R *nx = nxb + (k & 1) * ns, *nxp = nxb + ((k + 1) & 1) * ns;   // written now, written by the last step
+        // (a) column k with the pending update, from the stash (row 0 from memory at step 0), and the reflector;
+        // every CTA alike, the owner of row k writes d, e and tau
+        if (wid == 0) {
+            const R *row = A + (long long)k * lda;
+            const R vk = vo[k], pk = po[k];
+            R ss = 0;
+            for (int c = k + 1 + lane; c < n; c += 32) {
+                const R x = (k == 0 ? row[c] : nxp[c]) - vk * po[c] - pk * vo[c];
+                v[c] = x;
+                ss = fma(x, x, ss);
+            }
+            ss = warp_sum_t(ss);
+            if (lane == 0) {
+                const R dk = (k == 0 ? row[0] : nxp[k]) - 2 * vk * pk;
+                const R x0 = v[k + 1];
+                const R alpha = sqrt(ss);
+                R beta = 0, ek = 0;
+                if (alpha != (R)0) {
+                    const R sgn = x0 >= (R)0 ? (R)1 : (R)-1;
+                    v[k + 1] = x0 + sgn * alpha;
+                    ek = -sgn * alpha;
+                    beta = (R)1 / (alpha * (alpha + fabs(x0)));
+                }
+                s_beta = beta;
+                if (own_k) {
+                    D.d[k] = dk;
+                    D.e[k] = ek;
+                    D.tau[k] = beta;
+                }
+            }
+        }
+        __syncthreads();
+        const R beta = s_beta;
+        // (b) this CTA's rows: pending update, row and column sums of A v, the new stash
+        const int rstart = k + 1 + (((int)rank - (k + 1)) & (CL - 1));
+        tri_rows_pass<R, 3>(A, lda, vec, k, n, rstart, CL, vo, po, v, cs, p, [&](int r, R x) { nx[r] = x; });
+        __syncthreads();
+        for (int r = rstart + CL * tid; r < n; r += CL * kTT) {
+            const R x = nx[r];
+#pragma unroll
+            for (unsigned q = 1; q < CL; ++q) *at(nx + r, (rank + q) & (CL - 1)) = x;
+        }
+        cluster.sync();   // the column sums and the stash complete in every CTA; every (a) of step k done
+        // (c) the owner of row k writes the reflector (no CTA reads row k any more); p = beta (row + column sums)
+        // for this CTA's rows, into every CTA; the partial p.v into every CTA
+        if (own_k)
+            for (int c = k + 1 + tid; c < n; c += kTT) A[(long long)k * lda + c] = v[c];
+        R pv = 0;
+        for (int c = rstart + CL * tid; c < n; c += CL * kTT) {
+            R t = p[c] + cs[c];
+#pragma unroll
+            for (unsigned q = 1; q < CL; ++q) t += *at(cs + c, (rank + q) & (CL - 1));
+            const R pc = beta * t;
+            p[c] = pc;
+#pragma unroll
+            for (unsigned q = 1; q < CL; ++q) *at(p + c, (rank + q) & (CL - 1)) = pc;
+            pv = fma(pc, v[c], pv);
+        }
+        pv = warp_sum_t(pv);
+        if (lane == 0) part[wid] = pv;
+        __syncthreads();
+        if (wid == 0) {
+            const R t = warp_sum_t(lane < NW ? part[lane] : (R)0);
+            if (lane < CL) *at(s_pv + rank, (unsigned)lane) = t;
+        }
+        cluster.sync();   // p and the partial dot products complete in every CTA; no peer reads cs any more
+        R tpv = 0;
+#pragma unroll
+        for (int q = 0; q < CL; ++q) tpv += s_pv[q];   // the same order in every CTA
+        const R kc = (R)0.5 * beta * tpv;
+        for (int r = k + 1 + tid; r < n; r += kTT) {
+            p[r] -= kc * v[r];
+            cs[r] = 0;
+        }
+        __syncthreads();
+        R *t = vo;
+        vo = v;
+        v = t;
+        t = po;
+        po = p;
+        p = t;
+    }
+    cluster.sync();   // the last row updates of every CTA visible
+    if (tid == 0 && rank == 0) {
+        if (n >= 2) {
+            const int a = n - 2, b = n - 1;
+            D.d[a] = A[(long long)a * lda + a] - 2 * vo[a] * po[a];
+            D.e[a] = A[(long long)b * lda + a] - vo[b] * po[a] - po[b] * vo[a];
+            D.d[b] = A[(long long)b * lda + b] - 2 * vo[b] * po[b];
+            D.tau[a] = 0;
+            A[(long long)a * lda + b] = 0;
         } else if (n == 1) {
             D.d[0] = A[0];
         }
@@ -1037,6 +1191,34 @@ cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, 
             count_launch();
             k_tridiag<R, 1, 2><<<batch, kTT, sh, s>>>(d);
             return cudaGetLastError();
+        }
+        if (variant >= 2 && variant <= 4) {
+            // FP32, a cluster of 4, 8 or 16 CTAs per matrix, one CTA per SM (16 is a non-portable cluster size)
+            const int cl = 2 << variant;
+            const size_t sh = 7 * (size_t)((n + 3) & ~3) * sizeof(R);
+            void (*kern)(const TriDescT<float> *) =
+                cl == 4 ? k_tridiag_cl<4> : cl == 8 ? k_tridiag_cl<8> : k_tridiag_cl<16>;
+            if ((e = smem_attr(kern, sh)) != cudaSuccess) return e;
+            if (cl == 16 && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+                                cudaSuccess)
+                return e;
+            cudaLaunchConfig_t cfg{};
+            cfg.gridDim = dim3((unsigned)cl * (unsigned)batch);
+            cfg.blockDim = dim3(kTT);
+            cfg.dynamicSmemBytes = sh;
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)cl;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if ((e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg)) != cudaSuccess) return e;
+            if (nclusters < 1) return cudaErrorNotSupported;   // this GPU cannot hold one such cluster
+            count_launch();
+            return cudaLaunchKernelEx(&cfg, kern, d);
         }
         // FP32: a pair of CTAs (thread-block cluster) per matrix, each owning every other row; v, p, vo, po, the
         // column stash, the column sums and the peer's column sums in shared memory

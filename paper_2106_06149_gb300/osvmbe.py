@@ -25,7 +25,7 @@ EXPORTS = ["osv_create", "osv_destroy", "osv_last_error", "clusters_build", "osv
            "osv_solve_counts", "osv_residual_work", "osv_set_wait_budget",
            "osv_pair_amplitudes", "osv_overlap_metric", "clusters_build_osv",
            "posterior_correction", "weak_pairs_energy", "osv_autotune", "osv_autotune_report",
-           "osv_graph_capture", "osv_graph_launch", "osv_graph_kernels"]
+           "osv_graph_capture", "osv_graph_launch", "osv_graph_kernels", "osv_set_tridiag_variant"]
 
 
 class OsvParams(ctypes.Structure):
@@ -87,6 +87,7 @@ def load(path=LIB_PATH):
         "osv_graph_capture": ([V, P(OsvProblem), P(OsvParams), D, V, V], I),
         "osv_graph_launch": ([V, P(D), P(D)], I),
         "osv_graph_kernels": ([V, P(ctypes.c_longlong)], I),
+        "osv_set_tridiag_variant": ([V, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -287,6 +288,10 @@ class Context:
         n = ctypes.c_longlong()
         _check(load().osv_graph_kernels(self.h, ctypes.byref(n)), self.h)
         return n.value
+
+    def set_tridiag_variant(self, variant):
+        """Fix the FP32 tridiagonalisation's launch shape for later plans (0-4), or -1 to tune it."""
+        _check(load().osv_set_tridiag_variant(self.h, int(variant)), self.h)
 
     def autotune(self, on=True):
         """Plan-time autotuning of launch shapes (mixed precision); on by default."""

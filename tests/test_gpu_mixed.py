@@ -111,6 +111,43 @@ def test_mixed_osv_eigenpairs_match_fp64(osvmbe, fixed):
     assert rest <= 1e-5
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [(8, 120, 300, 61), (5, 37, 90, 62), (3, 5, 20, 63)])
+def test_every_tridiagonalisation_launch_shape(osvmbe, variant, shape):
+    """Each launch shape of the FP32 Householder reduction (a pair of CTAs, one CTA with two per SM, clusters of 4, 8
+    and 16 CTAs per matrix), fixed with osv_set_tridiag_variant: the eigenvalues of every T_kk against the FP64
+    route, leading ones after the FP64 refinement, the rest straight from the FP32 tridiagonal.  Shapes: rows a
+    multiple of four (16-byte passes), an odd order (column-by-column passes), and an order below the cluster
+    size (CTAs that own no row)."""
+    n_occ, n_vir, n_aux, seed = shape
+    p = make_problem(n_occ, n_vir, n_aux, seed=seed)
+    nm = min(6, n_vir)
+    prm = dict(n_osv_fixed=nm, mbe_order=2, r2b=6.0)
+    out = {}
+    for prec in (0, 2):
+        dp = osvmbe.DeviceProblem.from_host(p)
+        ctx = osvmbe.Context()
+        if prec:
+            ctx.set_tridiag_variant(variant)
+        ctx.clusters_build(dp, Params(**prm, precision=prec))
+        try:
+            ctx.osv_build(dp, Params(**prm, precision=prec), want_counts=True)
+        except osvmbe.OsvError as err:   # a cluster size this GPU cannot hold is refused before any launch
+            ctx.close()
+            if prec and variant == 4 and err.status == osvmbe.OSV_ERR_CUDA and "not supported" in str(err):
+                pytest.skip("this GPU holds no cluster of 16 CTAs of this kernel")
+            raise
+        out[prec] = np.array([ctx.eigenvalues(k, p.n_vir) for k in range(p.n_occ)])
+        if prec:
+            assert ctx.autotune_report().get("tridiag", {}).get("choice") == "fixed"
+        ctx.close()
+    scale = np.abs(out[0]).max()
+    lead = np.abs(out[2][:, :nm] - out[0][:, :nm]).max() / scale
+    rest = np.abs(out[2][:, nm:] - out[0][:, nm:]).max() / scale if n_vir > nm else 0.0
+    print(f"\nvariant {variant}, n_vir {n_vir}: leading rel diff {lead:.2e}; rest {rest:.2e}")
+    assert lead <= 2e-9 and rest <= 1e-5
+
+
 @pytest.mark.parametrize("nosv", [6, 41])
 def test_bf16x4_adjoint_kernels_match_fp64(osvmbe, nosv):
     """The mixed cluster partials take the tensor-core kernel for pair orders <= 80 (6 OSVs per LMO: orders <= 12)
@@ -143,7 +180,12 @@ def test_autotuner_reports_its_choices_and_keeps_the_results(osvmbe):
         ctx.close()
     (E_on, rep), (E_off, rep_off) = out[True], out[False]
     assert rep_off == {}
-    assert rep["tridiag"]["choice"] in ("cta_pair", "single_cta_2_per_sm") and len(rep["tridiag"]["ms"]) == 2
+    tri = rep["tridiag"]
+    names = ["cta_pair", "single_cta_2_per_sm", "cluster_4", "cluster_8", "cluster_16"]
+    assert set(tri["ms"]) == set(names) and tri["choice"] in names
+    timed = {k: v for k, v in tri["ms"].items() if v is not None}   # a cluster size the GPU cannot hold is null
+    assert {"cta_pair", "single_cta_2_per_sm", "cluster_4", "cluster_8"} <= set(timed)
+    assert timed[tri["choice"]] == min(timed.values())
     shapes = {"64x64", "80x80", "48x80", "80x48", "48x48"}
     assert rep["gemm_df"] and all(v["rule"] in shapes and v["choice"] in shapes and len(v["ms"]) == 5
                                   for v in rep["gemm_df"].values())
