@@ -44,8 +44,8 @@ WHY_NOT_4 = ("workload 4 (512 LMOs, n_vir 3000) also fits one GPU, but one step 
 # summarised in profiles/, keyed by workload and by the SHA-256 prefix of the kernel's source file at capture time:
 # a kernel changed since the capture reports null.
 NCU_TRAFFIC = {
-    # profiles/residual_mixed_full_cube48.md: 5.54 GB over 1585 clusters, scaled to workload 2's 14340 clusters
-    (2, 2, "8fa4e15ceb0a99f1"): (3.107834e9 + 2.431217e9) * 14340 / 1585,
+    # profiles/residual_mixed_full_cube48.md: 5.53 GB over 1585 clusters, scaled to workload 2's 14340 clusters
+    (2, 2, "0bb875668c9dc2db"): (3.106020e9 + 2.425234e9) * 14340 / 1585,
 }
 
 
@@ -332,8 +332,9 @@ def source_sha(rel):
 
 
 def residual_roofline(stages, flops_step, prec, work, wl):
-    """The residual kernel (one launch per step: k_residual_mixed, or k_residual on the FP64 path) against the
-    dense BF16 tensor peak measured on this machine, sustained figure (the kernel runs inside a long step):
+    """The residual kernel (one persistent launch per step: k_residual<true> in the mixed path, k_residual<false> in
+    the FP64 path) against the dense BF16 tensor peak measured on this machine, sustained figure (the kernel runs
+    inside a long step):
     achieved = algorithmic residual FLOPs of the step / the kernel's average CUDA-event duration over the timed
     region.  The FP32-pipe view of the mixed kernel (its FP32 evaluations plus 12 FP32 instructions per
     double-float multiply-add of its FP64-accurate evaluations, against 152 SMs x 128 lanes x 2 x 2.07 GHz) is
@@ -346,7 +347,7 @@ def residual_roofline(stages, flops_step, prec, work, wl):
     ach = flops_step / (avg_ms * 1e-3) / 1e12
     sha = source_sha("residual.cu")
     traffic = NCU_TRAFFIC.get((wl, prec, sha))
-    out = {"bound": "tensor", "kernel": "k_residual_mixed" if prec else "k_residual", "stage": "residual",
+    out = {"bound": "tensor", "kernel": "k_residual<true>" if prec else "k_residual<false>", "stage": "residual",
            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
            "avg_launch_ms": avg_ms, "launches": calls, "algorithmic_flops_per_launch": flops_step,
            "peak_note": f"dense BF16, {src} (MEASURED_PEAKS.json bf16_tflops_sustained)",
