@@ -197,7 +197,8 @@ osv_status osv_graph_kernels(osv_ctx *ctx, long long *count);
 /* Autotuner of the launch shapes (no counterpart in the paper).  When a context plans a problem in the mixed
  * precision (the first osv_build of a new shape), it times on the device, with CUDA events, the candidate launch
  * shapes of its tunable kernels and keeps the fastest: the FP32 Householder tridiagonalisation (a pair of CTAs per
- * matrix, one CTA per matrix and two per SM, or a cluster of 4, 8 or 16 CTAs per matrix) and the tile shape of every double-float GEMM batch whose problems
+ * matrix, one CTA per matrix and two per SM, a cluster of 4, 8 or 16 CTAs per matrix, or one CTA per matrix with
+ * delayed updates) and the tile shape of every double-float GEMM batch whose problems
  * all overwrite their outputs.  Results do not depend on the choice beyond rounding order.  osv_autotune(ctx, 0)
  * turns it off for later plans (the fixed rules then apply); it is on by default.  osv_autotune_report writes the
  * last plan's choices as a NUL-terminated JSON object into buf (HOST, len bytes, may be NULL), with the fixed
@@ -207,8 +208,9 @@ osv_status osv_autotune(osv_ctx *ctx, int on);
 osv_status osv_autotune_report(osv_ctx *ctx, char *buf, int len, int *needed);
 /* Fix the launch shape of the FP32 tridiagonalisation for this context's later plans instead of tuning it:
  * 0 = a pair of CTAs per matrix, 1 = one CTA per matrix and two per SM, 2 / 3 / 4 = a cluster of 4 / 8 / 16 CTAs
- * per matrix (one per SM; fewer matrices in flight, so their trailing matrices stay in L2); -1 = tuned again (the
- * default).  The results differ only in rounding order.  OSV_ERR_INVALID out of range; a later osv_build reports
+ * per matrix (one per SM; fewer matrices in flight, so their trailing matrices stay in L2), 5 / 6 / 7 = one CTA per
+ * matrix that writes the rank-2 updates of 2 / 2 / 4 steps into the trailing matrix together (6: two CTAs per SM;
+ * fewer bytes written); -1 = tuned again (the default).  The results differ only in rounding order.  OSV_ERR_INVALID out of range; a later osv_build reports
  * OSV_ERR_CUDA if the GPU cannot hold one cluster of the chosen size. */
 osv_status osv_set_tridiag_variant(osv_ctx *ctx, int variant);
 

@@ -480,6 +480,285 @@ __global__ void __launch_bounds__(kTT, 1) k_tridiag_cl(const TriDescT<float> *__
     }
 }
 
+// FP32 Householder reduction with delayed updates (one CTA per matrix).  The rank-2 updates
+// A <- A - v_s p_s^T - p_s v_s^T of NB consecutive steps are written into the stored lower triangle together, by the
+// pass of every NB-th step (a flush pass, which applies them element by element while it forms A v).  The passes in
+// between only read the stored triangle and correct its product with v for the updates still pending:
+// A v = A_stored v - sum_s [v_s (p_s . v) + p_s (v_s . v)].  Every element is still read once per step but written
+// once per NB steps, so the bytes moved fall to (NB + 1) / 2NB of the reduction above.  The last NB + 1 pairs
+// (v_s, p_s) live in a ring in shared memory (slot s mod (NB + 1)); column k + 1 as the pass leaves it in memory is
+// stashed, and step k + 1 applies to it the updates not yet written.
+struct TriPend {   // the pending pairs a flush pass applies
+    const float *v[4], *p[4];
+};
+
+__device__ __forceinline__ float &f4c(float4 &x, int e) { return e == 0 ? x.x : e == 1 ? x.y : e == 2 ? x.z : x.w; }
+
+template <int UV, int NP, bool WRITE>
+__device__ __forceinline__ void tri_rows_pass_d(float *__restrict__ A, long long lda, bool vec, int k, int n,
+                                                const TriPend &P, const float *__restrict__ v, float *cs, float *p,
+                                                float *nx) {
+    constexpr int NW = kTT / 32;
+    constexpr int NX = NP > 0 ? NP : 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int r0 = k + 1 + wid; r0 < n; r0 += 4 * NW) {
+        // rows r0 + q NW, q < nr (row q's columns c <= r0 + q NW)
+        float *row0 = A + (long long)r0 * lda;
+        const long long rstep = (long long)NW * lda;
+        const int nr = min(4, (n - 1 - r0) / NW + 1);
+        float vq[4], acc[4], vr[4][NX], pr[4][NX];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = q < nr ? r0 + q * NW : r0;
+            vq[q] = q < nr ? v[r] : 0.f;
+            acc[q] = 0.f;
+#pragma unroll
+            for (int s = 0; s < NX; ++s) {
+                vr[q][s] = NP > 0 && q < nr ? P.v[s][r] : 0.f;
+                pr[q][s] = NP > 0 && q < nr ? P.p[s][r] : 0.f;
+            }
+        }
+        const int hi = r0 + (nr - 1) * NW;   // the group's longest row
+        // element (row q, column c): the pending updates applied, the row and column sums taken
+        auto elem = [&](float x, int q, int c, const float *pce, const float *wce, float vce, float &cl) -> float {
+#pragma unroll
+            for (int s = 0; s < NP; ++s) x = x - vr[q][s] * pce[s] - pr[q][s] * wce[s];
+            acc[q] = fma(x, vce, acc[q]);
+            if (c < r0 + q * NW) cl = fma(x, vq[q], cl);
+            return x;
+        };
+        auto col = [&](int c) {   // one column of the (up to) four rows
+            float pce[NX], wce[NX];
+#pragma unroll
+            for (int s = 0; s < NX; ++s) {
+                pce[s] = NP > 0 ? P.p[s][c] : 0.f;
+                wce[s] = NP > 0 ? P.v[s][c] : 0.f;
+            }
+            const float vce = v[c];
+            float cl = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nr && c <= r0 + q * NW) {
+                    float *rp = row0 + q * rstep + c;
+                    const float x = elem(*rp, q, c, pce, wce, vce, cl);
+                    if (WRITE) *rp = x;
+                    if (c == k + 1) nx[r0 + q * NW] = x;
+                }
+            if (c < hi) atomicAdd(cs + c, cl);
+        };
+        if (vec) {
+            // 16-byte column groups [cb, ce) inside [k + 1, hi]; the ragged head and tail column by column
+            const int cb = min((k + 4) & ~3, hi + 1), ce = (hi + 1) & ~3;
+            if (lane < 3 && k + 1 + lane < cb) col(k + 1 + lane);
+            if (lane < 3 && max(ce, cb) + lane <= hi) col(max(ce, cb) + lane);
+            const int nch = ce > cb ? (ce - cb) >> 2 : 0;
+            for (int j0 = lane; j0 < nch; j0 += 32 * UV) {
+                float4 a[UV][4];
+#pragma unroll
+                for (int u = 0; u < UV; ++u) {
+                    const int j = j0 + 32 * u;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nr && j < nch && cb + 4 * j <= r0 + q * NW)
+                            a[u][q] = *reinterpret_cast<const float4 *>(row0 + q * rstep + cb + 4 * j);
+                }
+#pragma unroll
+                for (int u = 0; u < UV; ++u) {
+                    const int j = j0 + 32 * u;
+                    if (j >= nch) break;
+                    const int c = cb + 4 * j;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {   // column c + e
+                        float pce[NX], wce[NX];
+#pragma unroll
+                        for (int s = 0; s < NX; ++s) {
+                            pce[s] = NP > 0 ? P.p[s][c + e] : 0.f;
+                            wce[s] = NP > 0 ? P.v[s][c + e] : 0.f;
+                        }
+                        const float vce = v[c + e];
+                        float cl = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (q < nr && c + e <= r0 + q * NW) f4c(a[u][q], e) = elem(f4c(a[u][q], e), q, c + e, pce, wce, vce, cl);
+                        // columns at or beyond the longest row's diagonal take no column sum
+                        if (c + e < hi) atomicAdd(cs + c + e, cl);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (q < nr && c <= r0 + q * NW) {
+                            if (WRITE) *reinterpret_cast<float4 *>(row0 + q * rstep + c) = a[u][q];
+                            if (c == k + 1) nx[r0 + q * NW] = a[u][q].x;
+                        }
+                }
+            }
+        } else {
+            for (int c = k + 1 + lane; c <= hi; c += 32) col(c);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (q >= nr) break;
+            const float sum = warp_sum_t(acc[q]);
+            if (lane == 0) p[r0 + q * NW] = sum;   // the row sum; the column sums are added below
+        }
+    }
+}
+
+template <int NB, int MINB>
+__global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<float> *__restrict__ descs) {
+    static_assert(NB >= 2 && NB <= 4, "two to four updates per flush");
+    constexpr int NS = NB + 1;                     // ring slots
+    constexpr int UVF = 1, UVR = MINB == 2 ? 1 : (NB == 4 ? 2 : 3);   // register budgets without spills (NB = 2, one CTA per SM)
+    const TriDescT<float> D = descs[blockIdx.x];
+    const int n = D.n;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ns = (n + 3) & ~3;
+    float *Vr = reinterpret_cast<float *>(smem_raw);   // v_s of the ring
+    float *Pr = Vr + NS * ns;                          // p_s of the ring
+    float *nx = Pr + NS * ns;                          // column k + 1 as the pass of step k leaves it in memory
+    float *cs = nx + ns;                               // column sums of A v
+    __shared__ float part[kTT / 32][2 * NB];
+    __shared__ float s_dot[2 * NB];
+    __shared__ float s_beta, s_kc;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int NW = kTT / 32;
+    auto vs = [&](int s) -> float * { return Vr + (((s % NS) + NS) % NS) * ns; };
+    auto ps = [&](int s) -> float * { return Pr + (((s % NS) + NS) % NS) * ns; };
+    float *A = D.A;
+    const long long lda = D.lda;
+    const bool vec = (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+    for (int i = tid; i < (2 * NS + 2) * ns; i += kTT) Vr[i] = 0.f;   // the ring, the stash and the column sums
+    __syncthreads();
+    for (int k = 0; k + 2 < n; ++k) {
+        float *v = vs(k), *p = ps(k);
+        const int mc = k == 0 ? 0 : (k - 1) % NB + 1;   // updates of steps k - mc .. k - 1 not yet in the stash
+        // (a) column k with the updates not yet written, and its reflector (warp 0)
+        if (wid == 0) {
+            float *row = A + (long long)k * lda;
+            float ss = 0.f;
+            for (int c = k + 1 + lane; c < n; c += 32) {
+                float x = k == 0 ? row[c] : nx[c];
+                for (int t = 1; t <= mc; ++t) {
+                    const float *vv = vs(k - t), *pp = ps(k - t);
+                    x = x - vv[k] * pp[c] - pp[k] * vv[c];
+                }
+                v[c] = x;
+                ss = fma(x, x, ss);
+            }
+            ss = warp_sum_t(ss);
+            if (lane == 0) {
+                float dk = k == 0 ? row[0] : nx[k];
+                for (int t = 1; t <= mc; ++t) dk -= 2.f * vs(k - t)[k] * ps(k - t)[k];
+                D.d[k] = dk;
+                const float x0 = v[k + 1];
+                const float alpha = sqrtf(ss);
+                float beta = 0.f;
+                if (alpha == 0.f) {
+                    D.e[k] = 0.f;
+                } else {
+                    const float sgn = x0 >= 0.f ? 1.f : -1.f;
+                    v[k + 1] = x0 + sgn * alpha;
+                    D.e[k] = -sgn * alpha;
+                    beta = 1.f / (alpha * (alpha + fabsf(x0)));
+                }
+                D.tau[k] = beta;
+                s_beta = beta;
+            }
+            __syncwarp();
+            for (int c = k + 1 + lane; c < n; c += 32) row[c] = v[c];   // reflector into row k
+        }
+        __syncthreads();
+        const float beta = s_beta;
+        const bool flush = k % NB == 0;
+        const int m = flush ? 0 : k % NB;   // updates of steps k - m .. k - 1 missing from the stored triangle
+        // (b) one pass over the rows r > k: a flush applies and writes the updates of steps k - NB .. k - 1
+        if (flush) {
+            TriPend P{};
+#pragma unroll
+            for (int s = 0; s < NB; ++s) {
+                P.v[s] = vs(k - 1 - s);
+                P.p[s] = ps(k - 1 - s);
+            }
+            tri_rows_pass_d<UVF, NB, true>(A, lda, vec, k, n, P, v, cs, p, nx);
+        } else {
+            const TriPend P{};
+            tri_rows_pass_d<UVR, 0, false>(A, lda, vec, k, n, P, v, cs, p, nx);
+            // the dot products p_s . v and v_s . v of the missing updates
+            float dl[2 * NB];
+#pragma unroll
+            for (int t = 0; t < 2 * NB; ++t) dl[t] = 0.f;
+            for (int c = k + 1 + tid; c < n; c += kTT) {
+                const float vc = v[c];
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+                    if (t < m) {
+                        dl[2 * t] = fma(ps(k - 1 - t)[c], vc, dl[2 * t]);
+                        dl[2 * t + 1] = fma(vs(k - 1 - t)[c], vc, dl[2 * t + 1]);
+                    }
+            }
+#pragma unroll
+            for (int t = 0; t < 2 * NB; ++t) {
+                const float x = warp_sum_t(dl[t]);
+                if (lane == 0) part[wid][t] = x;
+            }
+        }
+        __syncthreads();
+        if (!flush) {
+            if (wid == 0)
+                for (int t = 0; t < 2 * m; ++t) {
+                    const float x = warp_sum_t(lane < NW ? part[lane][t] : 0.f);
+                    if (lane == 0) s_dot[t] = x;
+                }
+            __syncthreads();
+        }
+        // (c) p = beta (A v) with the correction for the missing updates, p.v, p -= (beta/2)(p.v) v
+        float pv = 0.f;
+        for (int c = k + 1 + tid; c < n; c += kTT) {
+            float y = p[c] + cs[c];
+            for (int t = 0; t < m; ++t) y -= vs(k - 1 - t)[c] * s_dot[2 * t] + ps(k - 1 - t)[c] * s_dot[2 * t + 1];
+            const float pc = beta * y;
+            p[c] = pc;
+            pv = fma(pc, v[c], pv);
+            cs[c] = 0.f;   // ready for the next pass
+        }
+        pv = warp_sum_t(pv);
+        if (lane == 0) part[wid][0] = pv;
+        __syncthreads();
+        if (wid == 0) {
+            const float t = warp_sum_t(lane < NW ? part[lane][0] : 0.f);
+            if (lane == 0) s_kc = 0.5f * beta * t;
+        }
+        __syncthreads();
+        const float kc = s_kc;
+        for (int r = k + 1 + tid; r < n; r += kTT) p[r] -= kc * v[r];
+        __syncthreads();
+    }
+    // the last two rows: their stored values and the updates not yet written (steps kl - kl % NB .. kl, kl = n - 3)
+    if (tid == 0) {
+        if (n >= 2) {
+            const int a = n - 2, b = n - 1;
+            float da = A[(long long)a * lda + a], ea = A[(long long)b * lda + a], db = A[(long long)b * lda + b];
+            if (n >= 3) {
+                const int kl = n - 3;
+                for (int s = kl - kl % NB; s <= kl; ++s) {
+                    const float *vv = vs(s), *pp = ps(s);
+                    da -= 2.f * vv[a] * pp[a];
+                    ea -= vv[b] * pp[a] + pp[b] * vv[a];
+                    db -= 2.f * vv[b] * pp[b];
+                }
+            }
+            D.d[a] = da;
+            D.e[a] = ea;
+            D.d[b] = db;
+            D.tau[a] = 0.f;
+            A[(long long)a * lda + b] = 0.f;   // no reflector for the last two rows
+        } else if (n == 1) {
+            D.d[0] = A[0];
+        }
+        D.e[n - 1] = 0.f;
+        D.tau[n - 1] = 0.f;
+    }
+}
+
 // ------------------------------------------------------------------------------------- 2. multisection
 // Number of eigenvalues below x: sign changes of the leading principal minors p_i = det(T_0..i - x), computed by
 // the three-term recurrence p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2} (no division).  Every four steps both
@@ -1190,6 +1469,18 @@ cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, 
             if ((e = smem_attr(k_tridiag<R, 1, 2>, sh)) != cudaSuccess) return e;
             count_launch();
             k_tridiag<R, 1, 2><<<batch, kTT, sh, s>>>(d);
+            return cudaGetLastError();
+        }
+        if (variant >= 5 && variant <= 7) {
+            // FP32, one CTA per matrix, the updates of two (variants 5, 6) or four (7) steps written together;
+            // variant 6 two CTAs per SM
+            const int nb = variant == 7 ? 4 : 2;
+            const size_t sh = (size_t)(2 * (nb + 1) + 2) * ((n + 3) & ~3) * sizeof(R);
+            void (*kern)(const TriDescT<float> *) =
+                variant == 5 ? k_tridiag_delayed<2, 1> : variant == 6 ? k_tridiag_delayed<2, 2> : k_tridiag_delayed<4, 1>;
+            if ((e = smem_attr(kern, sh)) != cudaSuccess) return e;
+            count_launch();
+            kern<<<batch, kTT, sh, s>>>(d);
             return cudaGetLastError();
         }
         if (variant >= 2 && variant <= 4) {
