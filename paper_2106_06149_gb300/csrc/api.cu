@@ -777,6 +777,19 @@ osv_status autotune_plan(osv_ctx *c) {
             }
             if (e == cudaSuccess && t[v] < t[best]) best = v;
         }
+        // a larger batch: the two fastest on the subset again on the whole batch (waves of different sizes)
+        double tf[2] = {-1.0, -1.0};
+        int fin[2] = {best, -1};
+        if (e == cudaSuccess && m < c->n_occ) {
+            for (int v = 0; v < kTriVariants; ++v)
+                if (v != best && t[v] >= 0.0 && (fin[1] < 0 || t[v] < t[fin[1]])) fin[1] = v;
+            for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+                if (fin[f] >= 0) {
+                    tf[f] = timed([&] { return osv_tridiag<float>(c->refine.tri_d, c->n_occ, nv, s, fin[f]); }, 1);
+                    spent += tf[f];
+                }
+            if (e == cudaSuccess && fin[1] >= 0 && tf[1] < tf[0]) best = fin[1];
+        }
         if (e == cudaSuccess) {
             c->refine.tri_variant = best;
             gain += (t[0] - t[best]) * c->n_occ / m;
@@ -794,7 +807,14 @@ osv_status autotune_plan(osv_ctx *c) {
             char buf[160];
             snprintf(buf, sizeof buf, "\"tridiag\": {\"rule\": \"cta_pair\", \"choice\": \"%s\", \"matrices_timed\": %d, \"ms\": ",
                      tri_name[best], m);
-            js += buf + ms + "}}";
+            js += buf + ms + "}";
+            if (fin[1] >= 0 && tf[1] >= 0.0) {
+                char b3[160];
+                snprintf(b3, sizeof b3, ", \"ms_whole_batch\": {\"%s\": %.3f, \"%s\": %.3f}", tri_name[fin[0]], tf[0],
+                         tri_name[fin[1]], tf[1]);
+                js += b3;
+            }
+            js += "}";
         }
     }
     // 2. double-float GEMM tile shapes

@@ -494,21 +494,21 @@ struct TriPend {   // the pending pairs a flush pass applies
 
 __device__ __forceinline__ float &f4c(float4 &x, int e) { return e == 0 ? x.x : e == 1 ? x.y : e == 2 ? x.z : x.w; }
 
-template <int UV, int NP, bool WRITE>
+template <int UV, int NP, bool WRITE, int RW = 4>
 __device__ __forceinline__ void tri_rows_pass_d(float *__restrict__ A, long long lda, bool vec, int k, int n,
                                                 const TriPend &P, const float *__restrict__ v, float *cs, float *p,
                                                 float *nx) {
     constexpr int NW = kTT / 32;
     constexpr int NX = NP > 0 ? NP : 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int r0 = k + 1 + wid; r0 < n; r0 += 4 * NW) {
-        // rows r0 + q NW, q < nr (row q's columns c <= r0 + q NW)
+    for (int r0 = k + 1 + wid; r0 < n; r0 += RW * NW) {
+        // rows r0 + q NW, q < nr <= RW (row q's columns c <= r0 + q NW)
         float *row0 = A + (long long)r0 * lda;
         const long long rstep = (long long)NW * lda;
-        const int nr = min(4, (n - 1 - r0) / NW + 1);
-        float vq[4], acc[4], vr[4][NX], pr[4][NX];
+        const int nr = min(RW, (n - 1 - r0) / NW + 1);
+        float vq[RW], acc[RW], vr[RW][NX], pr[RW][NX];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RW; ++q) {
             const int r = q < nr ? r0 + q * NW : r0;
             vq[q] = q < nr ? v[r] : 0.f;
             acc[q] = 0.f;
@@ -537,7 +537,7 @@ __device__ __forceinline__ void tri_rows_pass_d(float *__restrict__ A, long long
             const float vce = v[c];
             float cl = 0.f;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < RW; ++q)
                 if (q < nr && c <= r0 + q * NW) {
                     float *rp = row0 + q * rstep + c;
                     const float x = elem(*rp, q, c, pce, wce, vce, cl);
@@ -553,12 +553,12 @@ __device__ __forceinline__ void tri_rows_pass_d(float *__restrict__ A, long long
             if (lane < 3 && max(ce, cb) + lane <= hi) col(max(ce, cb) + lane);
             const int nch = ce > cb ? (ce - cb) >> 2 : 0;
             for (int j0 = lane; j0 < nch; j0 += 32 * UV) {
-                float4 a[UV][4];
+                float4 a[UV][RW];
 #pragma unroll
                 for (int u = 0; u < UV; ++u) {
                     const int j = j0 + 32 * u;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
+                    for (int q = 0; q < RW; ++q)
                         if (q < nr && j < nch && cb + 4 * j <= r0 + q * NW)
                             a[u][q] = *reinterpret_cast<const float4 *>(row0 + q * rstep + cb + 4 * j);
                 }
@@ -578,13 +578,13 @@ __device__ __forceinline__ void tri_rows_pass_d(float *__restrict__ A, long long
                         const float vce = v[c + e];
                         float cl = 0.f;
 #pragma unroll
-                        for (int q = 0; q < 4; ++q)
+                        for (int q = 0; q < RW; ++q)
                             if (q < nr && c + e <= r0 + q * NW) f4c(a[u][q], e) = elem(f4c(a[u][q], e), q, c + e, pce, wce, vce, cl);
                         // columns at or beyond the longest row's diagonal take no column sum
                         if (c + e < hi) atomicAdd(cs + c + e, cl);
                     }
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
+                    for (int q = 0; q < RW; ++q)
                         if (q < nr && c <= r0 + q * NW) {
                             if (WRITE) *reinterpret_cast<float4 *>(row0 + q * rstep + c) = a[u][q];
                             if (c == k + 1) nx[r0 + q * NW] = a[u][q].x;
@@ -595,7 +595,7 @@ __device__ __forceinline__ void tri_rows_pass_d(float *__restrict__ A, long long
             for (int c = k + 1 + lane; c <= hi; c += 32) col(c);
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < RW; ++q) {
             if (q >= nr) break;
             const float sum = warp_sum_t(acc[q]);
             if (lane == 0) p[r0 + q * NW] = sum;   // the row sum; the column sums are added below
@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
                 P.v[s] = vs(k - 1 - s);
                 P.p[s] = ps(k - 1 - s);
             }
-            tri_rows_pass_d<UVF, NB, true>(A, lda, vec, k, n, P, v, cs, p, nx);
+            tri_rows_pass_d<UVF, NB, true, MINB == 2 ? 2 : 4>(A, lda, vec, k, n, P, v, cs, p, nx);
         } else {
             const TriPend P{};
             tri_rows_pass_d<UVR, 0, false>(A, lda, vec, k, n, P, v, cs, p, nx);

@@ -187,7 +187,8 @@ def test_autotuner_reports_its_choices_and_keeps_the_results(osvmbe):
     assert set(tri["ms"]) == set(names) and tri["choice"] in names
     timed = {k: v for k, v in tri["ms"].items() if v is not None}   # a cluster size the GPU cannot hold is null
     assert set(names) - {"cluster_16"} <= set(timed)
-    assert timed[tri["choice"]] == min(timed.values())
+    whole = tri.get("ms_whole_batch")   # batches above 304 matrices: the two fastest re-timed on the whole batch
+    assert (min(whole, key=whole.get) if whole else min(timed, key=timed.get)) == tri["choice"]
     shapes = {"64x64", "80x80", "48x80", "80x48", "48x48"}
     assert rep["gemm_df"] and all(v["rule"] in shapes and v["choice"] in shapes and len(v["ms"]) == 5
                                   for v in rep["gemm_df"].values())
