@@ -616,6 +616,16 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
     float *Pr = Vr + NS * ns;                          // p_s of the ring
     float *nx = Pr + NS * ns;                          // column k + 1 as the pass of step k leaves it in memory
     float *cs = nx + ns;                               // column sums of A v
+    {
+        // launched with less dynamic shared memory than the ring needs: report a non-finite tridiagonal instead of
+        // touching memory past the allocation (the whole block returns before any barrier)
+        unsigned dsm;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+        if ((size_t)dsm < (size_t)(2 * NS + 2) * ns * sizeof(float)) {
+            if (threadIdx.x == 0) D.d[0] = __int_as_float(0x7fc00000);
+            return;
+        }
+    }
     __shared__ float part[kTT / 32][2 * NB];
     __shared__ float s_dot[2 * NB];
     __shared__ float s_beta, s_kc;
@@ -1458,6 +1468,17 @@ size_t jacobi_smem_bytes(int n) {
            (size_t)ne * sizeof(int) + 64;
 }
 
+// k_tridiag_delayed<NB, MINB>: the ring of NB + 1 pairs (v_s, p_s), the stash and the column sums in shared memory
+template <int NB, int MINB>
+cudaError_t launch_tridiag_delayed(const TriDescT<float> *d, int batch, int n, cudaStream_t s) {
+    const size_t sh = (size_t)(2 * (NB + 1) + 2) * ((n + 3) & ~3) * sizeof(float);
+    cudaError_t e = smem_attr(k_tridiag_delayed<NB, MINB>, sh);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_tridiag_delayed<NB, MINB><<<batch, kTT, sh, s>>>(d);
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, int variant) {
     if (batch <= 0) return cudaSuccess;
@@ -1474,14 +1495,9 @@ cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, 
         if (variant >= 5 && variant <= 7) {
             // FP32, one CTA per matrix, the updates of two (variants 5, 6) or four (7) steps written together;
             // variant 6 two CTAs per SM
-            const int nb = variant == 7 ? 4 : 2;
-            const size_t sh = (size_t)(2 * (nb + 1) + 2) * ((n + 3) & ~3) * sizeof(R);
-            void (*kern)(const TriDescT<float> *) =
-                variant == 5 ? k_tridiag_delayed<2, 1> : variant == 6 ? k_tridiag_delayed<2, 2> : k_tridiag_delayed<4, 1>;
-            if ((e = smem_attr(kern, sh)) != cudaSuccess) return e;
-            count_launch();
-            kern<<<batch, kTT, sh, s>>>(d);
-            return cudaGetLastError();
+            if (variant == 5) return launch_tridiag_delayed<2, 1>(d, batch, n, s);
+            if (variant == 6) return launch_tridiag_delayed<2, 2>(d, batch, n, s);
+            return launch_tridiag_delayed<4, 1>(d, batch, n, s);
         }
         if (variant >= 2 && variant <= 4) {
             // FP32, a cluster of 4, 8 or 16 CTAs per matrix, one CTA per SM (16 is a non-portable cluster size)
