@@ -522,7 +522,7 @@ osv_status build_plan(osv_ctx *c) {
         ALLOC(r.nm_all, n);
         // compact-WY factors only where the blocked reflector product fits shared memory (n_vir up to ~1700);
         // larger orders apply the reflectors one by one
-        if (osv_reflect_wy_fits(nv)) ALLOC(r.Twy, (long long)osv_wy_floats(n, nv));
+        ALLOC(r.Twy, (long long)osv_wy_floats(n, nv));
         std::vector<int> all(n, nm);
         if ((e = cudaMemcpy(r.nm_all, all.data(), n * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
             return c->cuda_fail(e, "upload n_max");

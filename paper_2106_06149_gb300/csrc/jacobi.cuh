@@ -155,8 +155,11 @@ __device__ __forceinline__ void df_rot_sel(float2 &x, float2 &y, const float2 c,
     else df_rot(x, y, c, sn);
 }
 
-// Cyclic round-robin Jacobi sweeps in double-float (A, V: ne x ne pairs in shared memory; same pairing and
-// stopping rule as jacobi_sweeps, the rotation angle from FP64 values of the three entries).
+// Cyclic round-robin Jacobi sweeps in double-float (A, V: ne x ne pairs in shared memory; same pairing as
+// jacobi_sweeps, the rotation angle from FP64 values of the three entries).  Stops when off <= tol2 fro, or at the
+// arithmetic's floor: double-float rotations leave about 2^-48 |A| of rounding in every off-diagonal entry, a sum of
+// squares near ne 2^-96 fro (5e-28 fro at ne = 41), which can sit above tol2 fro; once off <= 1e-26 fro and a sweep
+// no longer halves it, further sweeps change nothing and the matrix counts as diagonal.
 __device__ inline bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, float2 *cs, float2 *sn, int *pp, int *qq,
                                  double *red, int *flag, int max_sweeps, double tol2) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -168,6 +171,7 @@ __device__ inline bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, fl
     fro = block_sum(fro, red);
     const int half = ne / 2;
     bool conv = false;
+    double prev = -1.0;
     for (int sweep = 0;; ++sweep) {
         double off = 0.0;
         for (int idx = tid; idx < ne * ne; idx += nt) {
@@ -178,7 +182,8 @@ __device__ inline bool jacobi_sweeps_df(float2 *A, float2 *V, int ne, int ld, fl
             }
         }
         off = block_sum(off, red);
-        if (tid == 0) *flag = off <= tol2 * fro || off == 0.0;
+        if (tid == 0) *flag = off <= tol2 * fro || off == 0.0 || (prev >= 0.0 && off <= 1e-26 * fro && off > 0.5 * prev);
+        prev = off;
         __syncthreads();
         conv = *flag;
         __syncthreads();

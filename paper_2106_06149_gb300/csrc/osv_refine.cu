@@ -213,10 +213,10 @@ __global__ void __launch_bounds__(kT) k_osv_finish(const double *__restrict__ la
 
 // X (FP32 rows, virtual basis) -> Z = M(shift) X: H^T, remove the FP32 kept vectors, (shift - Tri)^{-1},
 // remove them again, H.  Rows >= nkeep[b] of Z are zero.
-// H or H^T on FP32 rows: blocked (compact WY) when its shared-memory tiles fit, else reflector by reflector
+// H or H^T on FP32 rows: blocked (compact WY) when the plan holds the T factors, else reflector by reflector
 cudaError_t reflect32(const OsvRefine &r, int n, int nv, int nm, const int *nrow, float *V, int forward,
                       cudaStream_t s) {
-    if (r.Twy && osv_reflect_wy_fits(nv)) return osv_reflect_wy(r.tri_d, r.Twy, n, nv, nm, nrow, V, forward, s);
+    if (r.Twy) return osv_reflect_wy(r.tri_d, r.Twy, n, nv, nm, nrow, V, forward, s);
     return osv_reflect<float>(r.tri_d, n, nv, nm, nrow, V, forward, s);
 }
 

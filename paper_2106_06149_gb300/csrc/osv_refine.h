@@ -45,7 +45,6 @@ cudaError_t osv_mixed_relax(const OsvRefine &r, const GemmBatch &gb_at, int n_oc
 // then rows mu < nrow[b] of V <- H V (forward = 0) or H^T V (forward = 1), same contract as osv_reflect<float>.
 size_t osv_wy_floats(int batch, int n);
 cudaError_t osv_wy_prepare(const TriDesc32 *d, int batch, int n, float *T, cudaStream_t s);
-bool osv_reflect_wy_fits(int n);
 cudaError_t osv_reflect_wy(const TriDesc32 *d, const float *T, int batch, int n, int nmax, const int *nrow, float *V,
                            int forward, cudaStream_t s);
 // Same contract as osv_project_out, for nmax <= 64: FP32 arithmetic for float, double-float for double.

@@ -19,7 +19,6 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kNB = 32;       // reflectors per compact-WY block (one per lane)
-constexpr int kWyRows = 8;    // rows of V per CTA of the blocked product (one warp each)
 constexpr int kPoRows = 8;    // rows of X per CTA of the projection (one warp each)
 constexpr int kPoCW = 64;     // Y column chunk of the projection
 constexpr int kPoMaxY = 64;   // projection onto at most 64 rows (two per lane)
@@ -118,89 +117,142 @@ __global__ void __launch_bounds__(kT) k_wy_t(const TriDesc32 *__restrict__ descs
     }
 }
 
-// rows mu < nrow[b] of V (nmax x n per matrix) <- H V (forward = 0: B_{J-1} first) or H^T V (forward = 1:
-// B_0^T first).  Per block: W = V_j^T y (lane i: reflector i) over the column chunks, Z = T_j W or T_j^T W through
-// warp shuffles, then y -= V_j Z over the chunks again; the chunks and T_j are shared by the CTA's kWyRows rows.
-__global__ void __launch_bounds__(kT) k_reflect_wy(const TriDesc32 *__restrict__ descs, const float *__restrict__ Tall,
-                                                   int J, const int *__restrict__ nrow, float *__restrict__ V, int nmax,
-                                                   int forward) {
+constexpr int kTR = 64;          // rows of V per CTA of the tiled product: every kept row of a matrix (n_max <= 64)
+constexpr int kTCW = 64;         // column chunk
+constexpr int kTLd = kTCW + 4;   // chunk row stride in floats: 16-byte rows; rows r and r + 1 four banks apart
+
+// rows mu < nrow[b] of V (nmax <= 64 rows of n per matrix) <- H V (forward = 0: B_{J-1} first) or H^T V
+// (forward = 1: B_0^T first); one CTA per matrix.  Per block j: W = V_j Y^T (32 reflectors x the rows) over column
+// chunks of V_j and Y staged in shared memory (thread tile: 4 reflectors x rows {r, r + 32}, float4 along the
+// columns, so 6 shared loads feed 32 FMAs), Z = T_j^T W or T_j W, then Y -= Z^T V_j chunk by chunk (thread tile:
+// rows {2q, 2q + 1} x columns {4p .. 4p + 3, 32 + 4p .. 35 + 4p}).  Y lives in global memory (L2) between chunks, so
+// the CTA's shared memory does not grow with n and several CTAs share an SM.
+__global__ void __launch_bounds__(kT, 4) k_reflect_wy_tiled(const TriDesc32 *__restrict__ descs,
+                                                         const float *__restrict__ Tall, int J,
+                                                         const int *__restrict__ nrow, float *__restrict__ V, int nmax,
+                                                         int forward) {
     const int b = blockIdx.x;
     const TriDesc32 D = descs[b];
     const int n = D.n;
-    const int nr = nrow ? nrow[b] : nmax;
-    const int g0 = blockIdx.y * kWyRows;
+    const int R = min(nrow ? nrow[b] : nmax, min(nmax, kTR));
     const int Jb = wy_blocks(n);
-    if (g0 >= nr || Jb == 0) return;
-    const int rows = min(kWyRows, nr - g0);
-    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
-    extern __shared__ __align__(16) float wsm[];
-    float *Ys = wsm;                             // kWyRows x n
-    float *Vs = Ys + (long long)kWyRows * n;     // kNB x kLdc: one column chunk of the block
-    float *Ts = Vs + kNB * kLdc;                 // kNB x (kNB + 1)
-    float *Vg = V + ((long long)b * nmax + g0) * n;
-    for (int i = tid; i < rows * n; i += kT) cp_async_zfill(Ys + i, Vg + i, 4, 4);
+    if (R <= 0 || Jb == 0) return;
+    __shared__ __align__(16) float Vc[kNB * kTLd];   // reflector chunk (32 x kTCW)
+    __shared__ __align__(16) float Yc[kTR * kTLd];   // row chunk (64 x kTCW)
+    __shared__ float Ws[kNB * (kTR + 1)];             // W, then Z
+    __shared__ float Ts[kNB * (kNB + 1)];
+    const int tid = threadIdx.x;
+    const int ti = tid >> 5, tr = tid & 31;            // pass 1 / Z: reflectors 4 ti .. 4 ti + 3, rows tr, tr + 32
+    const int pq = 2 * (tid >> 3), pp = 4 * (tid & 7);   // pass 2: rows pq, pq + 1; columns pp.., 32 + pp..
+    float *Yg = V + (long long)b * nmax * n;
     for (int s = 0; s < Jb; ++s) {
         const int j = forward ? s : Jb - 1 - s;
         const int k0 = j * kNB, kb = min(kNB, n - 2 - k0), m0 = n - k0 - 1, c0 = k0 + 1;
-        __syncthreads();   // previous block fully applied
+        __syncthreads();   // the previous block is done with Ts and Ws
         const float *Tg = Tall + ((long long)b * J + j) * kNB * kNB;
-        for (int idx = tid; idx < kNB * kNB; idx += kT) {
-            const int i = idx >> 5, l = idx & 31;
-            cp_async_zfill(Ts + i * (kNB + 1) + l, Tg + idx, 4, 4);
-        }
-        float w = 0.f;   // lane i: reflector i . this warp's row
-        for (int cbeg = 0; cbeg < m0; cbeg += kCH) {
-            const int cw = min(kCH, m0 - cbeg);
+        for (int idx = tid; idx < kNB * kNB; idx += kT) Ts[(idx >> 5) * (kNB + 1) + (idx & 31)] = Tg[idx];
+        // chunk [cbeg, cbeg + cw) of the block's columns c0 .. n - 1 into Vc (reflector i: zero before column
+        // k0 + 1 + i and for i >= kb) and Yc (rows >= R zero)
+        auto load_chunk = [&](int cbeg, int cw) {
+#pragma unroll
+            for (int t = 0; t < kNB * kTCW / kT; ++t) {
+                const int idx = tid + t * kT, i = idx / kTCW, cc = idx % kTCW;
+                float x = 0.f;
+                if (i < kb && cc < cw && cbeg + cc >= i) x = D.A[(long long)(k0 + i) * D.lda + c0 + cbeg + cc];
+                Vc[i * kTLd + cc] = x;
+            }
+#pragma unroll
+            for (int t = 0; t < kTR * kTCW / kT; ++t) {
+                const int idx = tid + t * kT, r = idx / kTCW, cc = idx % kTCW;
+                Yc[r * kTLd + cc] = (r < R && cc < cw) ? Yg[(long long)r * n + c0 + cbeg + cc] : 0.f;
+            }
+        };
+        // pass 1: W = V_j Y^T
+        float w[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) w[a][0] = w[a][1] = 0.f;
+        for (int cbeg = 0; cbeg < m0; cbeg += kTCW) {
+            const int cw = min(kTCW, m0 - cbeg);
             __syncthreads();
-            load_v_chunk(D, k0, kb, cbeg, cw, Vs);
-            cp_async_wait_all();
+            load_chunk(cbeg, cw);
             __syncthreads();
-            if (wid < rows) {
-                const float *y = Ys + (long long)wid * n + c0 + cbeg;
-                const float *vr = Vs + lane * kLdc;
-                float w0 = 0.f, w1 = 0.f;
-                int c = 0;
-                for (; c + 1 < cw; c += 2) {
-                    w0 = fmaf(y[c], vr[c], w0);
-                    w1 = fmaf(y[c + 1], vr[c + 1], w1);
+#pragma unroll 4
+            for (int cc = 0; cc < kTCW; cc += 4) {
+                const float4 y0 = *reinterpret_cast<const float4 *>(Yc + tr * kTLd + cc);
+                const float4 y1 = *reinterpret_cast<const float4 *>(Yc + (tr + 32) * kTLd + cc);
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float4 v = *reinterpret_cast<const float4 *>(Vc + (4 * ti + a) * kTLd + cc);
+                    w[a][0] = fmaf(v.x, y0.x, fmaf(v.y, y0.y, fmaf(v.z, y0.z, fmaf(v.w, y0.w, w[a][0]))));
+                    w[a][1] = fmaf(v.x, y1.x, fmaf(v.y, y1.y, fmaf(v.z, y1.z, fmaf(v.w, y1.w, w[a][1]))));
                 }
-                if (c < cw) w0 = fmaf(y[c], vr[c], w0);
-                w += w0 + w1;
             }
         }
-        float z = 0.f;
-        if (wid < rows) {
 #pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            Ws[(4 * ti + a) * (kTR + 1) + tr] = w[a][0];
+            Ws[(4 * ti + a) * (kTR + 1) + tr + 32] = w[a][1];
+        }
+        __syncthreads();
+        // Z = T_j^T W (forward) or T_j W
+        float z[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = 4 * ti + a;
+            float z0 = 0.f, z1 = 0.f;
+#pragma unroll 8
             for (int l = 0; l < kNB; ++l) {
-                const float wl = __shfl_sync(0xffffffffu, w, l);
-                z = fmaf(wl, forward ? Ts[l * (kNB + 1) + lane] : Ts[lane * (kNB + 1) + l], z);
+                const float t = forward ? Ts[l * (kNB + 1) + i] : Ts[i * (kNB + 1) + l];
+                z0 = fmaf(t, Ws[l * (kTR + 1) + tr], z0);
+                z1 = fmaf(t, Ws[l * (kTR + 1) + tr + 32], z1);
             }
+            z[a][0] = z0;
+            z[a][1] = z1;
         }
-        float zr[kNB];
+        __syncthreads();   // every W read
 #pragma unroll
-        for (int i = 0; i < kNB; ++i) zr[i] = __shfl_sync(0xffffffffu, z, i);
-        for (int cbeg = 0; cbeg < m0; cbeg += kCH) {
-            const int cw = min(kCH, m0 - cbeg);
-            // a block of one chunk is still in Vs from the first pass; otherwise every chunk is loaded again
-            if (cbeg > 0 || m0 > kCH) {
-                __syncthreads();
-                load_v_chunk(D, k0, kb, cbeg, cw, Vs);
-                cp_async_wait_all();
-                __syncthreads();
-            }
-            if (wid < rows) {
-                float *y = Ys + (long long)wid * n + c0 + cbeg;
-                for (int cc = lane; cc < cw; cc += 32) {
-                    float acc = y[cc];
+        for (int a = 0; a < 4; ++a) {
+            Ws[(4 * ti + a) * (kTR + 1) + tr] = z[a][0];
+            Ws[(4 * ti + a) * (kTR + 1) + tr + 32] = z[a][1];
+        }
+        // pass 2: Y -= Z^T V_j
+        for (int cbeg = 0; cbeg < m0; cbeg += kTCW) {
+            const int cw = min(kTCW, m0 - cbeg);
+            __syncthreads();   // Z complete; the previous chunk's reads done
+            load_chunk(cbeg, cw);
+            __syncthreads();
+            if (pq < R) {
+                float y[2][8];
 #pragma unroll
-                    for (int i = 0; i < kNB; ++i) acc = fmaf(-zr[i], Vs[i * kLdc + cc], acc);
-                    y[cc] = acc;
+                for (int q = 0; q < 2; ++q) {
+                    const float4 lo = *reinterpret_cast<const float4 *>(Yc + (pq + q) * kTLd + pp);
+                    const float4 hi = *reinterpret_cast<const float4 *>(Yc + (pq + q) * kTLd + 32 + pp);
+                    y[q][0] = lo.x; y[q][1] = lo.y; y[q][2] = lo.z; y[q][3] = lo.w;
+                    y[q][4] = hi.x; y[q][5] = hi.y; y[q][6] = hi.z; y[q][7] = hi.w;
                 }
+#pragma unroll 4
+                for (int i = 0; i < kNB; ++i) {
+                    const float z0 = Ws[i * (kTR + 1) + pq], z1 = Ws[i * (kTR + 1) + pq + 1];
+                    const float4 lo = *reinterpret_cast<const float4 *>(Vc + i * kTLd + pp);
+                    const float4 hi = *reinterpret_cast<const float4 *>(Vc + i * kTLd + 32 + pp);
+                    const float ve[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        y[0][e] = fmaf(-z0, ve[e], y[0][e]);
+                        y[1][e] = fmaf(-z1, ve[e], y[1][e]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    if (pq + q < R)
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int cc = (e < 4 ? pp : 32 + pp) + (e & 3);
+                            if (cc < cw) Yg[(long long)(pq + q) * n + c0 + cbeg + cc] = y[q][e];
+                        }
             }
         }
     }
-    __syncthreads();
-    for (int i = tid; i < rows * n; i += kT) Vg[i] = Ys[i];
 }
 
 // Arithmetic of the projection: FP32, or double-float for FP64 data.
@@ -382,10 +434,6 @@ cudaError_t smem_attr(K kernel, size_t sh) {
 
 constexpr size_t kSmemCap = 227 * 1024;
 
-size_t reflect_wy_smem(int n) {
-    return ((size_t)kWyRows * n + (size_t)kNB * kLdc + (size_t)kNB * (kNB + 1)) * sizeof(float);
-}
-
 template <class P>
 size_t project_rows_smem(int n) {
     return ((size_t)kPoRows * n + (size_t)kPoMaxY * (kPoCW + 1) + (size_t)kPoRows * kPoMaxY) * sizeof(typename P::S);
@@ -407,18 +455,12 @@ cudaError_t osv_wy_prepare(const TriDesc32 *d, int batch, int n, float *T, cudaS
     return cudaGetLastError();
 }
 
-bool osv_reflect_wy_fits(int n) { return reflect_wy_smem(n) <= kSmemCap; }
-
 cudaError_t osv_reflect_wy(const TriDesc32 *d, const float *T, int batch, int n, int nmax, const int *nrow, float *V,
                            int forward, cudaStream_t s) {
     if (batch <= 0 || nmax <= 0 || wy_blocks(n) == 0) return cudaSuccess;
-    const size_t sh = reflect_wy_smem(n);
-    if (sh > kSmemCap) return cudaErrorInvalidValue;
-    cudaError_t e;
-    if ((e = smem_attr(k_reflect_wy, sh)) != cudaSuccess) return e;
+    if (nmax > kTR) return cudaErrorInvalidValue;
     count_launch();
-    k_reflect_wy<<<dim3(batch, (nmax + kWyRows - 1) / kWyRows), kT, sh, s>>>(d, T, wy_blocks(n), nrow, V, nmax,
-                                                                             forward);
+    k_reflect_wy_tiled<<<batch, kT, 0, s>>>(d, T, wy_blocks(n), nrow, V, nmax, forward);
     return cudaGetLastError();
 }
 
