@@ -29,6 +29,8 @@ def main():
     ap.add_argument("--params", default="{}", help="Params fields (JSON)")
     ap.add_argument("--what", default="egrad", choices=["build", "energy", "egrad"])
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--tridiag-variant", type=int, default=-1,
+                    help="fix the FP32 tridiagonalisation's launch shape (osv_set_tridiag_variant); -1 = tuned")
     a = ap.parse_args()
     build.build()
     osvmbe.load()
@@ -45,6 +47,7 @@ def main():
         setattr(prm, k, v)
     dp = osvmbe.DeviceProblem.from_host(p)
     ctx = osvmbe.Context()
+    ctx.set_tridiag_variant(a.tridiag_variant)
     print("clusters", ctx.clusters_build(dp, prm), flush=True)
     dB = torch.zeros_like(dp.B)
     dF = torch.zeros_like(dp.f_occ)
