@@ -120,14 +120,23 @@ __global__ void __launch_bounds__(kT) k_wy_t(const TriDesc32 *__restrict__ descs
 constexpr int kTR = 64;          // rows of V per CTA of the tiled product: every kept row of a matrix (n_max <= 64)
 constexpr int kTCW = 64;         // column chunk
 constexpr int kTLd = kTCW + 4;   // chunk row stride in floats: 16-byte rows; rows r and r + 1 four banks apart
+constexpr int kTBuf = (kNB + kTR) * kTLd;   // one chunk buffer: the 32 reflector rows, then the 64 row chunks
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // rows mu < nrow[b] of V (nmax <= 64 rows of n per matrix) <- H V (forward = 0: B_{J-1} first) or H^T V
 // (forward = 1: B_0^T first); one CTA per matrix.  Per block j: W = V_j Y^T (32 reflectors x the rows) over column
 // chunks of V_j and Y staged in shared memory (thread tile: 4 reflectors x rows {r, r + 32}, float4 along the
 // columns, so 6 shared loads feed 32 FMAs), Z = T_j^T W or T_j W, then Y -= Z^T V_j chunk by chunk (thread tile:
 // rows {2q, 2q + 1} x columns {4p .. 4p + 3, 32 + 4p .. 35 + 4p}).  Y lives in global memory (L2) between chunks, so
-// the CTA's shared memory does not grow with n and several CTAs share an SM.
-__global__ void __launch_bounds__(kT, 4) k_reflect_wy_tiled(const TriDesc32 *__restrict__ descs,
+// the CTA's shared memory does not grow with n and several CTAs share an SM.  A block's chunks (pass 1, then the
+// same columns again for pass 2) run as one sequence through two buffers: the copies of chunk t + 1 are in flight
+// while chunk t is consumed.  Pass 1 leaves Y unchanged and pass 2 writes only the chunk it has consumed, so
+// every prefetched chunk holds current data; the sequence restarts at each block, whose columns the previous
+// block's pass 2 has just written.
+__global__ void __launch_bounds__(kT, 3) k_reflect_wy_tiled(const TriDesc32 *__restrict__ descs,
                                                          const float *__restrict__ Tall, int J,
                                                          const int *__restrict__ nrow, float *__restrict__ V, int nmax,
                                                          int forward) {
@@ -137,10 +146,10 @@ __global__ void __launch_bounds__(kT, 4) k_reflect_wy_tiled(const TriDesc32 *__r
     const int R = min(nrow ? nrow[b] : nmax, min(nmax, kTR));
     const int Jb = wy_blocks(n);
     if (R <= 0 || Jb == 0) return;
-    __shared__ __align__(16) float Vc[kNB * kTLd];   // reflector chunk (32 x kTCW)
-    __shared__ __align__(16) float Yc[kTR * kTLd];   // row chunk (64 x kTCW)
-    __shared__ float Ws[kNB * (kTR + 1)];             // W, then Z
-    __shared__ float Ts[kNB * (kNB + 1)];
+    extern __shared__ __align__(16) float wsm[];
+    float *Buf = wsm;                        // two chunk buffers
+    float *Ws = Buf + 2 * kTBuf;             // W, then Z (32 x (kTR + 1))
+    float *Ts = Ws + kNB * (kTR + 1);        // T_j (32 x 33)
     const int tid = threadIdx.x;
     const int ti = tid >> 5, tr = tid & 31;            // pass 1 / Z: reflectors 4 ti .. 4 ti + 3, rows tr, tr + 32
     const int pq = 2 * (tid >> 3), pp = 4 * (tid & 7);   // pass 2: rows pq, pq + 1; columns pp.., 32 + pp..
@@ -148,80 +157,88 @@ __global__ void __launch_bounds__(kT, 4) k_reflect_wy_tiled(const TriDesc32 *__r
     for (int s = 0; s < Jb; ++s) {
         const int j = forward ? s : Jb - 1 - s;
         const int k0 = j * kNB, kb = min(kNB, n - 2 - k0), m0 = n - k0 - 1, c0 = k0 + 1;
-        __syncthreads();   // the previous block is done with Ts and Ws
+        const int nch = (m0 + kTCW - 1) / kTCW;   // chunks per pass
+        __syncthreads();   // the previous block is done with Ts, Ws and both buffers; its writes of Y are visible
         const float *Tg = Tall + ((long long)b * J + j) * kNB * kNB;
         for (int idx = tid; idx < kNB * kNB; idx += kT) Ts[(idx >> 5) * (kNB + 1) + (idx & 31)] = Tg[idx];
-        // chunk [cbeg, cbeg + cw) of the block's columns c0 .. n - 1 into Vc (reflector i: zero before column
-        // k0 + 1 + i and for i >= kb) and Yc (rows >= R zero)
-        auto load_chunk = [&](int cbeg, int cw) {
+        // copies of chunk t (columns [cbeg, cbeg + cw) of the block's c0 .. n - 1, cbeg = (t mod nch) kTCW) into
+        // buffer t & 1: reflector i zero before column k0 + 1 + i and for i >= kb, rows >= R zero
+        auto issue = [&](int t) {
+            const int cbeg = (t % nch) * kTCW, cw = min(kTCW, m0 - cbeg);
+            float *Vb = Buf + (t & 1) * kTBuf, *Yb = Vb + kNB * kTLd;
 #pragma unroll
-            for (int t = 0; t < kNB * kTCW / kT; ++t) {
-                const int idx = tid + t * kT, i = idx / kTCW, cc = idx % kTCW;
-                float x = 0.f;
-                if (i < kb && cc < cw && cbeg + cc >= i) x = D.A[(long long)(k0 + i) * D.lda + c0 + cbeg + cc];
-                Vc[i * kTLd + cc] = x;
+            for (int u = 0; u < kNB * kTCW / kT; ++u) {
+                const int idx = tid + u * kT, i = idx / kTCW, cc = idx % kTCW;
+                const bool ok = i < kb && cc < cw && cbeg + cc >= i;
+                cp_async_zfill(Vb + i * kTLd + cc, ok ? D.A + (long long)(k0 + i) * D.lda + c0 + cbeg + cc : D.A, 4,
+                               ok ? 4 : 0);
             }
 #pragma unroll
-            for (int t = 0; t < kTR * kTCW / kT; ++t) {
-                const int idx = tid + t * kT, r = idx / kTCW, cc = idx % kTCW;
-                Yc[r * kTLd + cc] = (r < R && cc < cw) ? Yg[(long long)r * n + c0 + cbeg + cc] : 0.f;
+            for (int u = 0; u < kTR * kTCW / kT; ++u) {
+                const int idx = tid + u * kT, r = idx / kTCW, cc = idx % kTCW;
+                const bool ok = r < R && cc < cw;
+                cp_async_zfill(Yb + r * kTLd + cc, ok ? Yg + (long long)r * n + c0 + cbeg + cc : Yg, 4, ok ? 4 : 0);
             }
+            cp_async_commit();
         };
-        // pass 1: W = V_j Y^T
         float w[4][2];
 #pragma unroll
         for (int a = 0; a < 4; ++a) w[a][0] = w[a][1] = 0.f;
-        for (int cbeg = 0; cbeg < m0; cbeg += kTCW) {
-            const int cw = min(kTCW, m0 - cbeg);
-            __syncthreads();
-            load_chunk(cbeg, cw);
-            __syncthreads();
+        issue(0);
+        for (int t = 0; t < 2 * nch; ++t) {
+            if (t + 1 < 2 * nch) {
+                issue(t + 1);
+                cp_async_wait_group<1>();
+            } else {
+                cp_async_wait_group<0>();
+            }
+            __syncthreads();   // chunk t complete for every thread
+            const float *Vc = Buf + (t & 1) * kTBuf, *Yc = Vc + kNB * kTLd;
+            if (t < nch) {
+                // pass 1: W += V_j Y^T over this chunk
 #pragma unroll 4
-            for (int cc = 0; cc < kTCW; cc += 4) {
-                const float4 y0 = *reinterpret_cast<const float4 *>(Yc + tr * kTLd + cc);
-                const float4 y1 = *reinterpret_cast<const float4 *>(Yc + (tr + 32) * kTLd + cc);
+                for (int cc = 0; cc < kTCW; cc += 4) {
+                    const float4 y0 = *reinterpret_cast<const float4 *>(Yc + tr * kTLd + cc);
+                    const float4 y1 = *reinterpret_cast<const float4 *>(Yc + (tr + 32) * kTLd + cc);
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float4 v = *reinterpret_cast<const float4 *>(Vc + (4 * ti + a) * kTLd + cc);
-                    w[a][0] = fmaf(v.x, y0.x, fmaf(v.y, y0.y, fmaf(v.z, y0.z, fmaf(v.w, y0.w, w[a][0]))));
-                    w[a][1] = fmaf(v.x, y1.x, fmaf(v.y, y1.y, fmaf(v.z, y1.z, fmaf(v.w, y1.w, w[a][1]))));
+                    for (int a = 0; a < 4; ++a) {
+                        const float4 v = *reinterpret_cast<const float4 *>(Vc + (4 * ti + a) * kTLd + cc);
+                        w[a][0] = fmaf(v.x, y0.x, fmaf(v.y, y0.y, fmaf(v.z, y0.z, fmaf(v.w, y0.w, w[a][0]))));
+                        w[a][1] = fmaf(v.x, y1.x, fmaf(v.y, y1.y, fmaf(v.z, y1.z, fmaf(v.w, y1.w, w[a][1]))));
+                    }
                 }
-            }
-        }
+                if (t == nch - 1) {
+                    // Z = T_j^T W (forward) or T_j W, into Ws
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            Ws[(4 * ti + a) * (kTR + 1) + tr] = w[a][0];
-            Ws[(4 * ti + a) * (kTR + 1) + tr + 32] = w[a][1];
-        }
-        __syncthreads();
-        // Z = T_j^T W (forward) or T_j W
-        float z[4][2];
+                    for (int a = 0; a < 4; ++a) {
+                        Ws[(4 * ti + a) * (kTR + 1) + tr] = w[a][0];
+                        Ws[(4 * ti + a) * (kTR + 1) + tr + 32] = w[a][1];
+                    }
+                    __syncthreads();
+                    float z[4][2];
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int i = 4 * ti + a;
-            float z0 = 0.f, z1 = 0.f;
+                    for (int a = 0; a < 4; ++a) {
+                        const int i = 4 * ti + a;
+                        float z0 = 0.f, z1 = 0.f;
 #pragma unroll 8
-            for (int l = 0; l < kNB; ++l) {
-                const float t = forward ? Ts[l * (kNB + 1) + i] : Ts[i * (kNB + 1) + l];
-                z0 = fmaf(t, Ws[l * (kTR + 1) + tr], z0);
-                z1 = fmaf(t, Ws[l * (kTR + 1) + tr + 32], z1);
-            }
-            z[a][0] = z0;
-            z[a][1] = z1;
-        }
-        __syncthreads();   // every W read
+                        for (int l = 0; l < kNB; ++l) {
+                            const float tt = forward ? Ts[l * (kNB + 1) + i] : Ts[i * (kNB + 1) + l];
+                            z0 = fmaf(tt, Ws[l * (kTR + 1) + tr], z0);
+                            z1 = fmaf(tt, Ws[l * (kTR + 1) + tr + 32], z1);
+                        }
+                        z[a][0] = z0;
+                        z[a][1] = z1;
+                    }
+                    __syncthreads();   // every W read
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            Ws[(4 * ti + a) * (kTR + 1) + tr] = z[a][0];
-            Ws[(4 * ti + a) * (kTR + 1) + tr + 32] = z[a][1];
-        }
-        // pass 2: Y -= Z^T V_j
-        for (int cbeg = 0; cbeg < m0; cbeg += kTCW) {
-            const int cw = min(kTCW, m0 - cbeg);
-            __syncthreads();   // Z complete; the previous chunk's reads done
-            load_chunk(cbeg, cw);
-            __syncthreads();
-            if (pq < R) {
+                    for (int a = 0; a < 4; ++a) {
+                        Ws[(4 * ti + a) * (kTR + 1) + tr] = z[a][0];
+                        Ws[(4 * ti + a) * (kTR + 1) + tr + 32] = z[a][1];
+                    }
+                }
+            } else if (pq < R) {
+                // pass 2: Y -= Z^T V_j over this chunk (Z complete: the barrier after the next chunk's wait)
+                const int cbeg = (t - nch) * kTCW, cw = min(kTCW, m0 - cbeg);
                 float y[2][8];
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
@@ -251,6 +268,7 @@ __global__ void __launch_bounds__(kT, 4) k_reflect_wy_tiled(const TriDesc32 *__r
                             if (cc < cw) Yg[(long long)(pq + q) * n + c0 + cbeg + cc] = y[q][e];
                         }
             }
+            __syncthreads();   // chunk t consumed before its buffer takes chunk t + 2
         }
     }
 }
@@ -459,8 +477,11 @@ cudaError_t osv_reflect_wy(const TriDesc32 *d, const float *T, int batch, int n,
                            int forward, cudaStream_t s) {
     if (batch <= 0 || nmax <= 0 || wy_blocks(n) == 0) return cudaSuccess;
     if (nmax > kTR) return cudaErrorInvalidValue;
+    const size_t sh = (2 * (size_t)kTBuf + (size_t)kNB * (kTR + 1) + (size_t)kNB * (kNB + 1)) * sizeof(float);
+    cudaError_t e;
+    if ((e = smem_attr(k_reflect_wy_tiled, sh)) != cudaSuccess) return e;
     count_launch();
-    k_reflect_wy_tiled<<<batch, kT, 0, s>>>(d, T, wy_blocks(n), nrow, V, nmax, forward);
+    k_reflect_wy_tiled<<<batch, kT, sh, s>>>(d, T, wy_blocks(n), nrow, V, nmax, forward);
     return cudaGetLastError();
 }
 
