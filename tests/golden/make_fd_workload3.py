@@ -1,6 +1,7 @@
-"""Writes fd_workload3.json: central finite differences (step 1e-5) of the oracle's MBE(3)-OSV-MP2 energy with
-respect to 200 random entries of B and F_occ of workload 3 (128 LMOs in a 14 A cube, n_vir 800, n_aux 3200, 7 A
-fitting domains, l_osv 1e-4 capped at 40 OSVs, 8/6 A cutoffs).  Calls only oracle/ (and the seeded generator).
+"""Writes fd_workload3.json: central finite differences of the oracle's MBE(3)-OSV-MP2 energy with respect to 200
+random entries of B and F_occ of workload 3 (128 LMOs in a 14 A cube, n_vir 800, n_aux 3200, 7 A fitting domains,
+l_osv 1e-4 capped at 40 OSVs, 8/6 A cutoffs), at two steps: h = 1e-5 and h = 1e-4.  Calls only oracle/ (and the
+seeded generator).
 
 An entry of B_i changes only the clusters that hold LMO i; an entry f_xy only those that hold x and y (and f_xx
 those that hold x).  Every superset of such a cluster holds the same LMOs, so the MBE weights of these clusters
@@ -8,10 +9,14 @@ are the same in the full cluster list and in the list of the clusters that hold 
 that of the oracle run on the restricted problem (oracle/subproblem.py) with that cluster list.  OSV counts
 are frozen at the base point (the finite differences of a step function are meaningless).
 
-Two stencils are stored: the second-order one, (E(h) - E(-h)) / 2h, and the fourth-order one,
-(8 [E(h) - E(-h)] - [E(2h) - E(-2h)]) / 12h (the value the tests compare against).  Where the kept and
-discarded OSV eigenvalues of an LMO lie close, the second-order truncation error h^2 E'''/6 reaches 1e-6
-(a 0.65 % gap at LMO 83 gives 1.1e-6 on one B entry); the fourth-order error is O(h^4).
+Per step h, the second-order stencil (E(h) - E(-h)) / 2h and the fourth-order one
+(8 [E(h) - E(-h)] - [E(2h) - E(-2h)]) / 12h.  Why two steps: each energy carries FP64 rounding noise of about
+1e-14 |E| (the eigensolves, the iterations and the sums over hundreds of clusters), and a finite difference at
+step h inherits about that divided by h.  The energy an entry reaches is up to 1.6e3 Eh (82 LMOs and 421 clusters
+around LMO 83), so at h = 1e-5 the noise is about 1e-6, the size of the gradient bar itself (there the oracle's
+own autograd agrees with the analytic GPU gradient to 4e-12 while the differences scatter by 1e-6 from one step
+to the next).  At h = 1e-4 the noise is ten times smaller and the fourth-order truncation O(h^4) still far below
+it.  E_reached = (E(h) + E(-h)) / 2 at h = 1e-5 is stored to size the noise.
 
     python tests/golden/make_fd_workload3.py [workers]
 """
@@ -30,7 +35,7 @@ sys.path.insert(0, HERE)
 
 import numpy as np  # noqa: E402
 
-STEP = 1e-5
+STEPS = (1e-5, 1e-4)
 SEED = 3003
 N_LMO, N_B_PER_LMO, N_F_OFF = 5, 30, 9
 TOL = 1e-10
@@ -95,9 +100,15 @@ def _task(args):
     import torch
     torch.set_num_threads(1)
     k, e, n_osv = args
-    d1 = energy_part(e, STEP, n_osv)[0] - energy_part(e, -STEP, n_osv)[0]
-    d2 = energy_part(e, 2.0 * STEP, n_osv)[0] - energy_part(e, -2.0 * STEP, n_osv)[0]
-    return k, (d1 / (2.0 * STEP), (8.0 * d1 - d2) / (12.0 * STEP))
+    out = {}
+    for h in STEPS:
+        ep, em = energy_part(e, h, n_osv)[0], energy_part(e, -h, n_osv)[0]
+        d1 = ep - em
+        d2 = energy_part(e, 2.0 * h, n_osv)[0] - energy_part(e, -2.0 * h, n_osv)[0]
+        out[h] = (d1 / (2.0 * h), (8.0 * d1 - d2) / (12.0 * h))
+        if h == STEPS[0]:
+            out["E"] = 0.5 * (ep + em)
+    return k, out
 
 
 def main(workers):
@@ -132,14 +143,17 @@ def main(workers):
             done = sum(x is not None for x in vals)
             if done % 10 == 0:
                 print(f"{done}/{len(ents)} entries, {time.time() - t0:.0f} s", flush=True)
-    rec = {"workload": 3, "step": STEP, "seed": SEED, "tol": TOL,
+    rec = {"workload": 3, "steps": list(STEPS), "seed": SEED, "tol": TOL,
            "params": {"l_osv": prm.l_osv, "n_osv_max": prm.n_osv_max, "r2b": prm.r2b, "r3b": prm.r3b,
                       "mbe_order": prm.mbe_order, "tau_red": prm.tau_red},
            "n_osv": {str(k): v for k, v in sorted(n_base.items())},
            "note": "central differences of the oracle energy (oracle/osvmp2.py) restricted to the clusters each "
-                   "entry reaches: fd = fourth-order stencil on +-h, +-2h; fd2 = second-order stencil on +-h; "
+                   "entry reaches: fd4_h / fd2_h = fourth-order stencil on +-h, +-2h / second-order stencil on "
+                   "+-h, for h = 1e-5 and 1e-4; E_reached = the restricted energy at the base point (to O(h^2)); "
                    "B entries index LMO i's local block (virtual a, local fitting function P)",
-           "entries": [{"kind": e[0], "idx": list(e[1:]), "fd": v[1], "fd2": v[0]} for e, v in zip(ents, vals)]}
+           "entries": [{"kind": e[0], "idx": list(e[1:]), "fd4_1e-5": v[STEPS[0]][1], "fd2_1e-5": v[STEPS[0]][0],
+                        "fd4_1e-4": v[STEPS[1]][1], "fd2_1e-4": v[STEPS[1]][0], "E_reached": v["E"]}
+                       for e, v in zip(ents, vals)]}
     with open(os.path.join(HERE, "fd_workload3.json"), "w") as f:
         json.dump(rec, f, indent=1)
     print(f"wrote fd_workload3.json in {time.time() - t0:.0f} s")

@@ -4,9 +4,10 @@ thousands of uneven clusters), against the FP64 GPU path and the oracle:
 * workload 2 (mixed precision + batching): mixed vs FP64 energy and gradient at |dE| <= 1e-6 Eh and
   max |d grad| <= 1e-6 (plus one FP32 unit in the last place where B, hence dE/dB, is FP32); cluster counts; MBE weights of every cluster against the oracle's; OSV eigenvalues and
   cluster energies of sampled LMOs and clusters against the oracle at FP64 accuracy;
-* workload 3 (gradient): dE/dB and dE/dF_occ of the FP64 and mixed paths against central finite differences
-  (step 1e-5) of the oracle energy on 200 random entries (tests/golden/fd_workload3.json, written by
-  tests/golden/make_fd_workload3.py from oracle/ only), at max |d| <= 1e-6;
+* workload 3 (gradient): dE/dB and dE/dF_occ of the FP64 and mixed paths against central finite differences of
+  the oracle energy on 200 random entries (tests/golden/fd_workload3.json, written by
+  tests/golden/make_fd_workload3.py from oracle/ only): max |d| <= 1e-6 against the fourth-order stencil at step
+  1e-4, and <= 1e-6 plus the stencil's rounding-noise floor against the one at step 1e-5;
 * workload 4 (large energy + gradient): mixed vs FP64 energy and gradient at the same bars, and the FP64 energy of
   a sampled triple cluster against the oracle.
 
@@ -114,11 +115,16 @@ def test_workload2_mixed_vs_fp64_and_oracle_samples(m):
     assert xb <= 0.0 and xf <= 0.0
 
 
+# Rounding noise of a finite difference at step h: each oracle energy is known to about 1e-14 |E| (eigensolves,
+# iterations and sums over hundreds of clusters), and the fourth-order stencil divides about that by h.
+FD_NOISE_REL = 2e-14
+
+
 def test_workload3_gradients_vs_oracle_finite_differences(m):
     with open(os.path.join(HERE, "golden", "fd_workload3.json")) as f:
         gold = json.load(f)
     p, prm = workload(3)
-    assert gold["workload"] == 3 and gold["params"]["n_osv_max"] == prm.n_osv_max
+    assert gold["workload"] == 3 and gold["params"]["n_osv_max"] == prm.n_osv_max and gold["steps"] == [1e-5, 1e-4]
     dp = m.DeviceProblem.from_host(p)
     worst = {}
     for prec in (0, 2):
@@ -129,7 +135,7 @@ def test_workload3_gradients_vs_oracle_finite_differences(m):
         dB = r["dB"].cpu().numpy()
         dF = r["dF"].cpu().numpy()
         ctx.close()
-        err = 0.0
+        err = [0.0, 0.0]
         for e in gold["entries"]:
             if e["kind"] == "B":
                 i, a, P = e["idx"]
@@ -137,10 +143,13 @@ def test_workload3_gradients_vs_oracle_finite_differences(m):
             else:
                 x, y = e["idx"]
                 g = dF[x, y]
-            err = max(err, abs(g - e["fd"]))
-            assert abs(g - e["fd"]) <= TOL_GRAD, (prec, e, g)
+            d4, d5 = abs(g - e["fd4_1e-4"]), abs(g - e["fd4_1e-5"])
+            err = [max(err[0], d4), max(err[1], d5)]
+            assert d4 <= TOL_GRAD, (prec, e, g)
+            assert d5 <= TOL_GRAD + FD_NOISE_REL * abs(e["E_reached"]) / 1e-5, (prec, e, g)
         worst[prec] = err
-    print(f"\nworkload 3: max |grad - FD| over {len(gold['entries'])} entries: FP64 {worst[0]:.2e}, mixed {worst[2]:.2e}")
+    print(f"\nworkload 3: max |grad - FD| over {len(gold['entries'])} entries, step 1e-4 / 1e-5: "
+          f"FP64 {worst[0][0]:.2e} / {worst[0][1]:.2e}, mixed {worst[2][0]:.2e} / {worst[2][1]:.2e}")
 
 
 def test_workload4_mixed_vs_fp64_energy_and_gradient(m):
