@@ -603,7 +603,164 @@ __device__ __forceinline__ void tri_rows_pass_d(float *__restrict__ A, long long
     }
 }
 
-template <int NB, int MINB>
+// Geometry of one row group of pass (b): rows r0 + q NW (q < nr), the group's longest row hi, its 16-byte column
+// groups [cb, ce) (nch of them) and their chunks of 32 (one per lane: njb chunks).
+struct TriGroup {
+    int nr, hi, cb, ce, nch, njb;
+};
+__device__ __forceinline__ TriGroup tri_group(int r0, int k, int n, int rw, int nw) {
+    TriGroup g;
+    g.nr = min(rw, (n - 1 - r0) / nw + 1);
+    g.hi = r0 + (g.nr - 1) * nw;
+    g.cb = min((k + 4) & ~3, g.hi + 1);
+    g.ce = (g.hi + 1) & ~3;
+    g.nch = g.ce > g.cb ? (g.ce - g.cb) >> 2 : 0;
+    g.njb = (g.nch + 31) >> 5;
+    return g;
+}
+
+// 16-byte global -> shared copy in flight (src_bytes = 0: zero fill, nothing read)
+__device__ __forceinline__ void tri_cp16(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tri_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void tri_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// tri_rows_pass_d with the 16-byte row chunks staged through shared memory: every lane copies its next chunk of
+// the RW rows (cp.async, into a two-slot ring of its own) while it works on the current one, so a second set of
+// loads is in flight without registers to hold it.  The copy cursor walks the warp's row groups and chunks in the
+// order of the work; the chunk being copied is never one the pass writes before it is consumed.  16-byte aligned
+// rows only (vec); stage: this warp's 2 x RW x 32 float4.
+template <int NP, bool WRITE, int RW>
+__device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long long lda, int k, int n,
+                                                     const TriPend &P, const float *__restrict__ v, float *cs,
+                                                     float *p, float *nx, float4 *stage) {
+    constexpr int NW = kTT / 32;
+    constexpr int NX = NP > 0 ? NP : 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gstep = RW * NW;
+    // copy cursor: group pr0, chunk pjb (past the end once pr0 >= n)
+    int pr0 = k + 1 + wid, pjb = 0;
+    TriGroup pg = pr0 < n ? tri_group(pr0, k, n, RW, NW) : TriGroup{0, 0, 0, 0, 0, 0};
+    auto skip_empty = [&]() {
+        while (pr0 < n && pjb >= pg.njb) {
+            pr0 += gstep;
+            pjb = 0;
+            if (pr0 < n) pg = tri_group(pr0, k, n, RW, NW);
+        }
+    };
+    skip_empty();
+    auto issue = [&](int slot) {   // the cursor's chunk into this lane's slot (an empty group past the end)
+        if (pr0 < n) {
+            const int j = pjb * 32 + lane;
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+                const int r = pr0 + q * NW;
+                const bool ok = q < pg.nr && j < pg.nch && pg.cb + 4 * j <= r;
+                tri_cp16(stage + (slot * RW + q) * 32 + lane, ok ? A + (long long)r * lda + pg.cb + 4 * j : A,
+                         ok ? 16 : 0);
+            }
+            ++pjb;
+            skip_empty();
+        }
+        tri_cp_commit();
+    };
+    int slot = 0;
+    issue(0);
+    for (int r0 = k + 1 + wid; r0 < n; r0 += gstep) {
+        const TriGroup g = tri_group(r0, k, n, RW, NW);
+        float *row0 = A + (long long)r0 * lda;
+        const long long rstep = (long long)NW * lda;
+        const int nr = g.nr, hi = g.hi;
+        float vq[RW], acc[RW], vr[RW][NX], pr[RW][NX];
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+            const int r = q < nr ? r0 + q * NW : r0;
+            vq[q] = q < nr ? v[r] : 0.f;
+            acc[q] = 0.f;
+#pragma unroll
+            for (int s = 0; s < NX; ++s) {
+                vr[q][s] = NP > 0 && q < nr ? P.v[s][r] : 0.f;
+                pr[q][s] = NP > 0 && q < nr ? P.p[s][r] : 0.f;
+            }
+        }
+        auto elem = [&](float x, int q, int c, const float *pce, const float *wce, float vce, float &cl) -> float {
+#pragma unroll
+            for (int s = 0; s < NP; ++s) x = x - vr[q][s] * pce[s] - pr[q][s] * wce[s];
+            acc[q] = fma(x, vce, acc[q]);
+            if (c < r0 + q * NW) cl = fma(x, vq[q], cl);
+            return x;
+        };
+        auto col = [&](int c) {   // one column of the (up to) RW rows, straight from memory
+            float pce[NX], wce[NX];
+#pragma unroll
+            for (int s = 0; s < NX; ++s) {
+                pce[s] = NP > 0 ? P.p[s][c] : 0.f;
+                wce[s] = NP > 0 ? P.v[s][c] : 0.f;
+            }
+            const float vce = v[c];
+            float cl = 0.f;
+#pragma unroll
+            for (int q = 0; q < RW; ++q)
+                if (q < nr && c <= r0 + q * NW) {
+                    float *rp = row0 + q * rstep + c;
+                    const float x = elem(*rp, q, c, pce, wce, vce, cl);
+                    if (WRITE) *rp = x;
+                    if (c == k + 1) nx[r0 + q * NW] = x;
+                }
+            if (c < hi) atomicAdd(cs + c, cl);
+        };
+        // the ragged head [k + 1, cb) and tail [max(ce, cb), hi] column by column (outside every staged chunk)
+        if (lane < 3 && k + 1 + lane < g.cb) col(k + 1 + lane);
+        if (lane < 3 && max(g.ce, g.cb) + lane <= hi) col(max(g.ce, g.cb) + lane);
+        for (int jb = 0; jb < g.njb; ++jb) {
+            issue(slot ^ 1);
+            tri_cp_wait<1>();   // this lane's copies of the current chunk have landed
+            const int j = jb * 32 + lane;
+            if (j < g.nch) {
+                const int c = g.cb + 4 * j;
+                float4 a[RW];
+#pragma unroll
+                for (int q = 0; q < RW; ++q) a[q] = stage[(slot * RW + q) * 32 + lane];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {   // column c + e
+                    float pce[NX], wce[NX];
+#pragma unroll
+                    for (int s = 0; s < NX; ++s) {
+                        pce[s] = NP > 0 ? P.p[s][c + e] : 0.f;
+                        wce[s] = NP > 0 ? P.v[s][c + e] : 0.f;
+                    }
+                    const float vce = v[c + e];
+                    float cl = 0.f;
+#pragma unroll
+                    for (int q = 0; q < RW; ++q)
+                        if (q < nr && c + e <= r0 + q * NW) f4c(a[q], e) = elem(f4c(a[q], e), q, c + e, pce, wce, vce, cl);
+                    // columns at or beyond the longest row's diagonal take no column sum
+                    if (c + e < hi) atomicAdd(cs + c + e, cl);
+                }
+#pragma unroll
+                for (int q = 0; q < RW; ++q)
+                    if (q < nr && c <= r0 + q * NW) {
+                        if (WRITE) *reinterpret_cast<float4 *>(row0 + q * rstep + c) = a[q];
+                        if (c == k + 1) nx[r0 + q * NW] = a[q].x;
+                    }
+            }
+            slot ^= 1;
+        }
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+            if (q >= nr) break;
+            const float sum = warp_sum_t(acc[q]);
+            if (lane == 0) p[r0 + q * NW] = sum;   // the row sum; the column sums are added below
+        }
+    }
+    tri_cp_wait<0>();   // nothing in flight past the pass
+}
+
+template <int NB, int MINB, bool STAGE = false>
 __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<float> *__restrict__ descs) {
     static_assert(NB >= 2 && NB <= 4, "two to four updates per flush");
     constexpr int NS = NB + 1;                     // ring slots
@@ -616,12 +773,14 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
     float *Pr = Vr + NS * ns;                          // p_s of the ring
     float *nx = Pr + NS * ns;                          // column k + 1 as the pass of step k leaves it in memory
     float *cs = nx + ns;                               // column sums of A v
+    // (STAGE) each warp's two-slot ring of row chunks, 2 x 4 x 32 float4
+    float4 *stage = reinterpret_cast<float4 *>(cs + ns) + (threadIdx.x >> 5) * (2 * 4 * 32);
     {
         // launched with less dynamic shared memory than the ring needs: report a non-finite tridiagonal instead of
         // touching memory past the allocation (the whole block returns before any barrier)
         unsigned dsm;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
-        if ((size_t)dsm < (size_t)(2 * NS + 2) * ns * sizeof(float)) {
+        if ((size_t)dsm < (size_t)(2 * NS + 2) * ns * sizeof(float) + (STAGE ? (size_t)(kTT / 32) * 2 * 4 * 32 * 16 : 0)) {
             if (threadIdx.x == 0) D.d[0] = __int_as_float(0x7fc00000);
             return;
         }
@@ -688,10 +847,12 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
                 P.v[s] = vs(k - 1 - s);
                 P.p[s] = ps(k - 1 - s);
             }
-            tri_rows_pass_d<UVF, NB, true, MINB == 2 ? 2 : 4>(A, lda, vec, k, n, P, v, cs, p, nx);
+            if (STAGE && vec) tri_rows_pass_staged<NB, true, MINB == 2 ? 2 : 4>(A, lda, k, n, P, v, cs, p, nx, stage);
+            else tri_rows_pass_d<UVF, NB, true, MINB == 2 ? 2 : 4>(A, lda, vec, k, n, P, v, cs, p, nx);
         } else {
             const TriPend P{};
-            tri_rows_pass_d<UVR, 0, false>(A, lda, vec, k, n, P, v, cs, p, nx);
+            if (STAGE && vec) tri_rows_pass_staged<0, false, 4>(A, lda, k, n, P, v, cs, p, nx, stage);
+            else tri_rows_pass_d<UVR, 0, false>(A, lda, vec, k, n, P, v, cs, p, nx);
             // the dot products p_s . v and v_s . v of the missing updates
             float dl[2 * NB];
 #pragma unroll
@@ -1469,13 +1630,14 @@ size_t jacobi_smem_bytes(int n) {
 }
 
 // k_tridiag_delayed<NB, MINB>: the ring of NB + 1 pairs (v_s, p_s), the stash and the column sums in shared memory
-template <int NB, int MINB>
+template <int NB, int MINB, bool STAGE = false>
 cudaError_t launch_tridiag_delayed(const TriDescT<float> *d, int batch, int n, cudaStream_t s) {
-    const size_t sh = (size_t)(2 * (NB + 1) + 2) * ((n + 3) & ~3) * sizeof(float);
-    cudaError_t e = smem_attr(k_tridiag_delayed<NB, MINB>, sh);
+    const size_t sh = (size_t)(2 * (NB + 1) + 2) * ((n + 3) & ~3) * sizeof(float) +
+                      (STAGE ? (size_t)(kTT / 32) * 2 * 4 * 32 * sizeof(float4) : 0);
+    cudaError_t e = smem_attr(k_tridiag_delayed<NB, MINB, STAGE>, sh);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_tridiag_delayed<NB, MINB><<<batch, kTT, sh, s>>>(d);
+    k_tridiag_delayed<NB, MINB, STAGE><<<batch, kTT, sh, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -1492,6 +1654,8 @@ cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, 
             k_tridiag<R, 1, 2><<<batch, kTT, sh, s>>>(d);
             return cudaGetLastError();
         }
+        if (variant == 8) return launch_tridiag_delayed<2, 2, true>(d, batch, n, s);
+        if (variant == 9) return launch_tridiag_delayed<2, 1, true>(d, batch, n, s);
         if (variant >= 5 && variant <= 7) {
             // FP32, one CTA per matrix, the updates of two (variants 5, 6) or four (7) steps written together;
             // variant 6 two CTAs per SM

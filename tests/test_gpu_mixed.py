@@ -111,12 +111,12 @@ def test_mixed_osv_eigenpairs_match_fp64(osvmbe, fixed):
     assert rest <= 1e-5
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", list(range(10)))
 @pytest.mark.parametrize("shape", [(8, 120, 300, 61), (5, 37, 90, 62), (3, 5, 20, 63)])
 def test_every_tridiagonalisation_launch_shape(osvmbe, variant, shape):
     """Each launch shape of the FP32 Householder reduction (a pair of CTAs, one CTA with two per SM, clusters of 4, 8
-    and 16 CTAs per matrix, one CTA with the updates of two or four steps written together), fixed with
-    osv_set_tridiag_variant: the eigenvalues of every T_kk against the FP64
+    and 16 CTAs per matrix, one CTA with the updates of two or four steps written together, with or without row
+    chunks staged through shared memory), fixed with osv_set_tridiag_variant: the eigenvalues of every T_kk against the FP64
     route, leading ones after the FP64 refinement, the rest straight from the FP32 tridiagonal.  Shapes: rows a
     multiple of four (16-byte passes), an odd order (column-by-column passes), and an order below the cluster
     size (CTAs that own no row)."""
@@ -183,7 +183,7 @@ def test_autotuner_reports_its_choices_and_keeps_the_results(osvmbe):
     assert rep_off == {}
     tri = rep["tridiag"]
     names = ["cta_pair", "single_cta_2_per_sm", "cluster_4", "cluster_8", "cluster_16", "delayed_2",
-             "delayed_2_2_per_sm", "delayed_4"]
+             "delayed_2_2_per_sm", "delayed_4", "staged_2_2_per_sm", "staged_2"]
     assert set(tri["ms"]) == set(names) and tri["choice"] in names
     timed = {k: v for k, v in tri["ms"].items() if v is not None}   # a cluster size the GPU cannot hold is null
     assert set(names) - {"cluster_16"} <= set(timed)
