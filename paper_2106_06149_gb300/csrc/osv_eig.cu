@@ -629,12 +629,12 @@ __device__ __forceinline__ void tri_cp_commit() { asm volatile("cp.async.commit_
 template <int N>
 __device__ __forceinline__ void tri_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// tri_rows_pass_d with the 16-byte row chunks staged through shared memory: every lane copies its next chunk of
-// the RW rows (cp.async, into a two-slot ring of its own) while it works on the current one, so a second set of
-// loads is in flight without registers to hold it.  The copy cursor walks the warp's row groups and chunks in the
-// order of the work; the chunk being copied is never one the pass writes before it is consumed.  16-byte aligned
-// rows only (vec); stage: this warp's 2 x RW x 32 float4.
-template <int NP, bool WRITE, int RW>
+// tri_rows_pass_d with the 16-byte row chunks staged through shared memory: every lane copies its next NSL - 1
+// chunks of the RW rows (cp.async, into an NSL-slot ring of its own) while it works on the current one, so more
+// loads are in flight without registers to hold them.  The copy cursor walks the warp's row groups and chunks in the
+// order of the work; a chunk being copied is never one the pass writes before it is consumed.  16-byte aligned
+// rows only (vec); stage: this warp's NSL x 4 x 32 float4.
+template <int NP, bool WRITE, int RW, int NSL>
 __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long long lda, int k, int n,
                                                      const TriPend &P, const float *__restrict__ v, float *cs,
                                                      float *p, float *nx, float4 *stage) {
@@ -660,7 +660,7 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
             for (int q = 0; q < RW; ++q) {
                 const int r = pr0 + q * NW;
                 const bool ok = q < pg.nr && j < pg.nch && pg.cb + 4 * j <= r;
-                tri_cp16(stage + (slot * RW + q) * 32 + lane, ok ? A + (long long)r * lda + pg.cb + 4 * j : A,
+                tri_cp16(stage + (slot * 4 + q) * 32 + lane, ok ? A + (long long)r * lda + pg.cb + 4 * j : A,
                          ok ? 16 : 0);
             }
             ++pjb;
@@ -668,8 +668,9 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
         }
         tri_cp_commit();
     };
-    int slot = 0;
-    issue(0);
+    int slot = 0, islot = NSL - 1;   // the slot consumed next, the slot filled next
+#pragma unroll
+    for (int t = 0; t < NSL - 1; ++t) issue(t);
     for (int r0 = k + 1 + wid; r0 < n; r0 += gstep) {
         const TriGroup g = tri_group(r0, k, n, RW, NW);
         float *row0 = A + (long long)r0 * lda;
@@ -717,14 +718,15 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
         if (lane < 3 && k + 1 + lane < g.cb) col(k + 1 + lane);
         if (lane < 3 && max(g.ce, g.cb) + lane <= hi) col(max(g.ce, g.cb) + lane);
         for (int jb = 0; jb < g.njb; ++jb) {
-            issue(slot ^ 1);
-            tri_cp_wait<1>();   // this lane's copies of the current chunk have landed
+            issue(islot);       // the slot consumed one chunk ago
+            islot = islot + 1 == NSL ? 0 : islot + 1;
+            tri_cp_wait<NSL - 1>();   // this lane's copies of the current chunk have landed
             const int j = jb * 32 + lane;
             if (j < g.nch) {
                 const int c = g.cb + 4 * j;
                 float4 a[RW];
 #pragma unroll
-                for (int q = 0; q < RW; ++q) a[q] = stage[(slot * RW + q) * 32 + lane];
+                for (int q = 0; q < RW; ++q) a[q] = stage[(slot * 4 + q) * 32 + lane];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {   // column c + e
                     float pce[NX], wce[NX];
@@ -748,7 +750,7 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
                         if (c == k + 1) nx[r0 + q * NW] = a[q].x;
                     }
             }
-            slot ^= 1;
+            slot = slot + 1 == NSL ? 0 : slot + 1;
         }
 #pragma unroll
         for (int q = 0; q < RW; ++q) {
@@ -760,7 +762,7 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
     tri_cp_wait<0>();   // nothing in flight past the pass
 }
 
-template <int NB, int MINB, bool STAGE = false>
+template <int NB, int MINB, int NSL = 0>
 __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<float> *__restrict__ descs) {
     static_assert(NB >= 2 && NB <= 4, "two to four updates per flush");
     constexpr int NS = NB + 1;                     // ring slots
@@ -773,14 +775,14 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
     float *Pr = Vr + NS * ns;                          // p_s of the ring
     float *nx = Pr + NS * ns;                          // column k + 1 as the pass of step k leaves it in memory
     float *cs = nx + ns;                               // column sums of A v
-    // (STAGE) each warp's two-slot ring of row chunks, 2 x 4 x 32 float4
-    float4 *stage = reinterpret_cast<float4 *>(cs + ns) + (threadIdx.x >> 5) * (2 * 4 * 32);
+    // (NSL > 0) each warp's ring of row chunks, NSL x 4 x 32 float4
+    float4 *stage = reinterpret_cast<float4 *>(cs + ns) + (threadIdx.x >> 5) * (NSL * 4 * 32);
     {
         // launched with less dynamic shared memory than the ring needs: report a non-finite tridiagonal instead of
         // touching memory past the allocation (the whole block returns before any barrier)
         unsigned dsm;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
-        if ((size_t)dsm < (size_t)(2 * NS + 2) * ns * sizeof(float) + (STAGE ? (size_t)(kTT / 32) * 2 * 4 * 32 * 16 : 0)) {
+        if ((size_t)dsm < (size_t)(2 * NS + 2) * ns * sizeof(float) + (size_t)(kTT / 32) * NSL * 4 * 32 * 16) {
             if (threadIdx.x == 0) D.d[0] = __int_as_float(0x7fc00000);
             return;
         }
@@ -847,11 +849,11 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
                 P.v[s] = vs(k - 1 - s);
                 P.p[s] = ps(k - 1 - s);
             }
-            if (STAGE && vec) tri_rows_pass_staged<NB, true, MINB == 2 ? 2 : 4>(A, lda, k, n, P, v, cs, p, nx, stage);
+            if (NSL > 0 && vec) tri_rows_pass_staged<NB, true, MINB == 2 ? 2 : 4, NSL>(A, lda, k, n, P, v, cs, p, nx, stage);
             else tri_rows_pass_d<UVF, NB, true, MINB == 2 ? 2 : 4>(A, lda, vec, k, n, P, v, cs, p, nx);
         } else {
             const TriPend P{};
-            if (STAGE && vec) tri_rows_pass_staged<0, false, 4>(A, lda, k, n, P, v, cs, p, nx, stage);
+            if (NSL > 0 && vec) tri_rows_pass_staged<0, false, 4, NSL>(A, lda, k, n, P, v, cs, p, nx, stage);
             else tri_rows_pass_d<UVR, 0, false>(A, lda, vec, k, n, P, v, cs, p, nx);
             // the dot products p_s . v and v_s . v of the missing updates
             float dl[2 * NB];
@@ -1630,14 +1632,15 @@ size_t jacobi_smem_bytes(int n) {
 }
 
 // k_tridiag_delayed<NB, MINB>: the ring of NB + 1 pairs (v_s, p_s), the stash and the column sums in shared memory
-template <int NB, int MINB, bool STAGE = false>
+template <int NB, int MINB, int NSL = 0>
 cudaError_t launch_tridiag_delayed(const TriDescT<float> *d, int batch, int n, cudaStream_t s) {
     const size_t sh = (size_t)(2 * (NB + 1) + 2) * ((n + 3) & ~3) * sizeof(float) +
-                      (STAGE ? (size_t)(kTT / 32) * 2 * 4 * 32 * sizeof(float4) : 0);
-    cudaError_t e = smem_attr(k_tridiag_delayed<NB, MINB, STAGE>, sh);
+                      (size_t)(kTT / 32) * NSL * 4 * 32 * sizeof(float4);
+    if (sh > 227 * 1024) return cudaErrorNotSupported;   // the ring does not fit beside the vectors at this order
+    cudaError_t e = smem_attr(k_tridiag_delayed<NB, MINB, NSL>, sh);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_tridiag_delayed<NB, MINB, STAGE><<<batch, kTT, sh, s>>>(d);
+    k_tridiag_delayed<NB, MINB, NSL><<<batch, kTT, sh, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -1654,8 +1657,10 @@ cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, 
             k_tridiag<R, 1, 2><<<batch, kTT, sh, s>>>(d);
             return cudaGetLastError();
         }
-        if (variant == 8) return launch_tridiag_delayed<2, 2, true>(d, batch, n, s);
-        if (variant == 9) return launch_tridiag_delayed<2, 1, true>(d, batch, n, s);
+        if (variant == 8) return launch_tridiag_delayed<2, 2, 2>(d, batch, n, s);
+        if (variant == 9) return launch_tridiag_delayed<2, 1, 2>(d, batch, n, s);
+        if (variant == 10) return launch_tridiag_delayed<2, 1, 3>(d, batch, n, s);
+        if (variant == 11) return launch_tridiag_delayed<2, 1, 4>(d, batch, n, s);
         if (variant >= 5 && variant <= 7) {
             // FP32, one CTA per matrix, the updates of two (variants 5, 6) or four (7) steps written together;
             // variant 6 two CTAs per SM
