@@ -634,7 +634,7 @@ __device__ __forceinline__ void tri_cp_wait() { asm volatile("cp.async.wait_grou
 // loads are in flight without registers to hold them.  The copy cursor walks the warp's row groups and chunks in the
 // order of the work; a chunk being copied is never one the pass writes before it is consumed.  16-byte aligned
 // rows only (vec); stage: this warp's NSL x 4 x 32 float4.
-template <int NP, bool WRITE, int RW, int NSL>
+template <int NP, bool WRITE, int RW, int NSL, bool V4>
 __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long long lda, int k, int n,
                                                      const TriPend &P, const float *__restrict__ v, float *cs,
                                                      float *p, float *nx, float4 *stage) {
@@ -727,15 +727,26 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
                 float4 a[RW];
 #pragma unroll
                 for (int q = 0; q < RW; ++q) a[q] = stage[(slot * 4 + q) * 32 + lane];
+                // V4: the group's four entries of v and of the pending pairs as one 16-byte load each (lanes' groups
+                // are 16 bytes apart: no bank conflicts; column-wise scalar loads would collide four ways)
+                float4 v4, p4[NX], w4[NX];
+                if constexpr (V4) {
+                    v4 = *reinterpret_cast<const float4 *>(v + c);
+#pragma unroll
+                    for (int s = 0; s < NX; ++s) {
+                        p4[s] = NP > 0 ? *reinterpret_cast<const float4 *>(P.p[s] + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        w4[s] = NP > 0 ? *reinterpret_cast<const float4 *>(P.v[s] + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {   // column c + e
                     float pce[NX], wce[NX];
 #pragma unroll
                     for (int s = 0; s < NX; ++s) {
-                        pce[s] = NP > 0 ? P.p[s][c + e] : 0.f;
-                        wce[s] = NP > 0 ? P.v[s][c + e] : 0.f;
+                        pce[s] = NP > 0 ? (V4 ? f4c(p4[s], e) : P.p[s][c + e]) : 0.f;
+                        wce[s] = NP > 0 ? (V4 ? f4c(w4[s], e) : P.v[s][c + e]) : 0.f;
                     }
-                    const float vce = v[c + e];
+                    const float vce = V4 ? f4c(v4, e) : v[c + e];
                     float cl = 0.f;
 #pragma unroll
                     for (int q = 0; q < RW; ++q)
@@ -849,11 +860,12 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
                 P.v[s] = vs(k - 1 - s);
                 P.p[s] = ps(k - 1 - s);
             }
-            if (NSL > 0 && vec) tri_rows_pass_staged<NB, true, MINB == 2 ? 2 : 4, NSL>(A, lda, k, n, P, v, cs, p, nx, stage);
+            if (NSL > 0 && vec)
+                tri_rows_pass_staged<NB, true, MINB == 2 ? 2 : 4, NSL, MINB == 1>(A, lda, k, n, P, v, cs, p, nx, stage);
             else tri_rows_pass_d<UVF, NB, true, MINB == 2 ? 2 : 4>(A, lda, vec, k, n, P, v, cs, p, nx);
         } else {
             const TriPend P{};
-            if (NSL > 0 && vec) tri_rows_pass_staged<0, false, 4, NSL>(A, lda, k, n, P, v, cs, p, nx, stage);
+            if (NSL > 0 && vec) tri_rows_pass_staged<0, false, 4, NSL, MINB == 1>(A, lda, k, n, P, v, cs, p, nx, stage);
             else tri_rows_pass_d<UVR, 0, false>(A, lda, vec, k, n, P, v, cs, p, nx);
             // the dot products p_s . v and v_s . v of the missing updates
             float dl[2 * NB];
