@@ -164,6 +164,12 @@ def run_gpu(args):
     ctx.clusters_build(dp, prm)
     dB = torch.zeros_like(dp.B)
     dF = torch.zeros_like(dp.f_occ)
+    # pinned host buffers of the end-to-end leg, allocated before any plan
+    hB = torch.from_numpy(np.ascontiguousarray(p.B)).pin_memory()
+    hF = torch.from_numpy(np.ascontiguousarray(p.f_occ)).pin_memory()
+    he = torch.from_numpy(np.ascontiguousarray(p.eps_vir)).pin_memory()
+    odB = torch.empty(dB.shape, dtype=dB.dtype).pin_memory()
+    odF = torch.empty(dF.shape, dtype=dF.dtype).pin_memory()
 
     res = {}
 
@@ -214,12 +220,6 @@ def run_gpu(args):
 
     # ---- end to end through the C ABI with host buffers: h2d of B, F, eps into the recorded step's input buffers;
     # the replay (E back to the host); d2h of dB, dF
-    hB = torch.from_numpy(np.ascontiguousarray(p.B)).pin_memory()
-    hF = torch.from_numpy(np.ascontiguousarray(p.f_occ)).pin_memory()
-    he = torch.from_numpy(np.ascontiguousarray(p.eps_vir)).pin_memory()
-    odB = torch.empty(dB.shape, dtype=dB.dtype).pin_memory()
-    odF = torch.empty(dF.shape, dtype=dF.dtype).pin_memory()
-
     def e2e_step():
         dp.B.copy_(hB, non_blocking=True)
         dp.f_occ.copy_(hF, non_blocking=True)
