@@ -210,8 +210,9 @@ osv_status osv_autotune_report(osv_ctx *ctx, char *buf, int len, int *needed);
  * 0 = a pair of CTAs per matrix, 1 = one CTA per matrix and two per SM, 2 / 3 / 4 = a cluster of 4 / 8 / 16 CTAs
  * per matrix (one per SM; fewer matrices in flight, so their trailing matrices stay in L2), 5 / 6 / 7 = one CTA per
  * matrix that writes the rank-2 updates of 2 / 2 / 4 steps into the trailing matrix together (6: two CTAs per SM;
- * fewer bytes written), 8 / 9 = variants 6 / 5 with the row chunks staged through shared memory; -1 = tuned again
- * (the default).  The results differ only in rounding order.  OSV_ERR_INVALID out of range; a later osv_build reports
+ * fewer bytes written), 8 / 9 = variants 6 / 5 with the row chunks staged through shared memory, 10 / 11 = variant
+ * 9 with two / three chunks in flight ahead, 12 = variant 9 with eight rows per warp group; -1 = tuned again (the
+ * default).  The results differ only in rounding order.  OSV_ERR_INVALID out of range; a later osv_build reports
  * OSV_ERR_CUDA if the GPU cannot hold one cluster of the chosen size. */
 osv_status osv_set_tridiag_variant(osv_ctx *ctx, int variant);
 

@@ -763,7 +763,7 @@ osv_status autotune_plan(osv_ctx *c) {
     } else {
         const char *tri_name[kTriVariants] = {"cta_pair", "single_cta_2_per_sm", "cluster_4", "cluster_8", "cluster_16",
                                               "delayed_2", "delayed_2_2_per_sm", "delayed_4", "staged_2_2_per_sm",
-                                              "staged_2", "staged_2_depth_2", "staged_2_depth_3"};
+                                              "staged_2", "staged_2_depth_2", "staged_2_depth_3", "staged_2_8_rows"};
         const int m = std::min(c->n_occ, 2 * 152), nv = c->n_vir;
         double t[kTriVariants];
         int best = 0;

@@ -634,7 +634,7 @@ __device__ __forceinline__ void tri_cp_wait() { asm volatile("cp.async.wait_grou
 // loads are in flight without registers to hold them.  The copy cursor walks the warp's row groups and chunks in the
 // order of the work; a chunk being copied is never one the pass writes before it is consumed.  16-byte aligned
 // rows only (vec); stage: this warp's NSL x 4 x 32 float4.
-template <int NP, bool WRITE, int RW, int NSL, bool V4>
+template <int NP, bool WRITE, int RW, int NSL, bool V4, int SR = 4>
 __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long long lda, int k, int n,
                                                      const TriPend &P, const float *__restrict__ v, float *cs,
                                                      float *p, float *nx, float4 *stage) {
@@ -660,7 +660,7 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
             for (int q = 0; q < RW; ++q) {
                 const int r = pr0 + q * NW;
                 const bool ok = q < pg.nr && j < pg.nch && pg.cb + 4 * j <= r;
-                tri_cp16(stage + (slot * 4 + q) * 32 + lane, ok ? A + (long long)r * lda + pg.cb + 4 * j : A,
+                tri_cp16(stage + (slot * SR + q) * 32 + lane, ok ? A + (long long)r * lda + pg.cb + 4 * j : A,
                          ok ? 16 : 0);
             }
             ++pjb;
@@ -726,7 +726,7 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
                 const int c = g.cb + 4 * j;
                 float4 a[RW];
 #pragma unroll
-                for (int q = 0; q < RW; ++q) a[q] = stage[(slot * 4 + q) * 32 + lane];
+                for (int q = 0; q < RW; ++q) a[q] = stage[(slot * SR + q) * 32 + lane];
                 // V4: the group's four entries of v and of the pending pairs as one 16-byte load each (lanes' groups
                 // are 16 bytes apart: no bank conflicts; column-wise scalar loads would collide four ways)
                 float4 v4, p4[NX], w4[NX];
@@ -773,7 +773,7 @@ __device__ __forceinline__ void tri_rows_pass_staged(float *__restrict__ A, long
     tri_cp_wait<0>();   // nothing in flight past the pass
 }
 
-template <int NB, int MINB, int NSL = 0>
+template <int NB, int MINB, int NSL = 0, int RWS = 4>
 __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<float> *__restrict__ descs) {
     static_assert(NB >= 2 && NB <= 4, "two to four updates per flush");
     constexpr int NS = NB + 1;                     // ring slots
@@ -786,14 +786,14 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
     float *Pr = Vr + NS * ns;                          // p_s of the ring
     float *nx = Pr + NS * ns;                          // column k + 1 as the pass of step k leaves it in memory
     float *cs = nx + ns;                               // column sums of A v
-    // (NSL > 0) each warp's ring of row chunks, NSL x 4 x 32 float4
-    float4 *stage = reinterpret_cast<float4 *>(cs + ns) + (threadIdx.x >> 5) * (NSL * 4 * 32);
+    // (NSL > 0) each warp's ring of row chunks, NSL x RWS x 32 float4
+    float4 *stage = reinterpret_cast<float4 *>(cs + ns) + (threadIdx.x >> 5) * (NSL * RWS * 32);
     {
         // launched with less dynamic shared memory than the ring needs: report a non-finite tridiagonal instead of
         // touching memory past the allocation (the whole block returns before any barrier)
         unsigned dsm;
         asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
-        if ((size_t)dsm < (size_t)(2 * NS + 2) * ns * sizeof(float) + (size_t)(kTT / 32) * NSL * 4 * 32 * 16) {
+        if ((size_t)dsm < (size_t)(2 * NS + 2) * ns * sizeof(float) + (size_t)(kTT / 32) * NSL * RWS * 32 * 16) {
             if (threadIdx.x == 0) D.d[0] = __int_as_float(0x7fc00000);
             return;
         }
@@ -861,11 +861,12 @@ __global__ void __launch_bounds__(kTT, MINB) k_tridiag_delayed(const TriDescT<fl
                 P.p[s] = ps(k - 1 - s);
             }
             if (NSL > 0 && vec)
-                tri_rows_pass_staged<NB, true, MINB == 2 ? 2 : 4, NSL, MINB == 1>(A, lda, k, n, P, v, cs, p, nx, stage);
+                tri_rows_pass_staged<NB, true, MINB == 2 ? 2 : (RWS > 4 ? 4 : RWS), NSL, MINB == 1, RWS>(A, lda, k, n, P, v, cs, p, nx,
+                                                                                       stage);
             else tri_rows_pass_d<UVF, NB, true, MINB == 2 ? 2 : 4>(A, lda, vec, k, n, P, v, cs, p, nx);
         } else {
             const TriPend P{};
-            if (NSL > 0 && vec) tri_rows_pass_staged<0, false, 4, NSL, MINB == 1>(A, lda, k, n, P, v, cs, p, nx, stage);
+            if (NSL > 0 && vec) tri_rows_pass_staged<0, false, RWS, NSL, MINB == 1, RWS>(A, lda, k, n, P, v, cs, p, nx, stage);
             else tri_rows_pass_d<UVR, 0, false>(A, lda, vec, k, n, P, v, cs, p, nx);
             // the dot products p_s . v and v_s . v of the missing updates
             float dl[2 * NB];
@@ -1644,15 +1645,15 @@ size_t jacobi_smem_bytes(int n) {
 }
 
 // k_tridiag_delayed<NB, MINB>: the ring of NB + 1 pairs (v_s, p_s), the stash and the column sums in shared memory
-template <int NB, int MINB, int NSL = 0>
+template <int NB, int MINB, int NSL = 0, int RWS = 4>
 cudaError_t launch_tridiag_delayed(const TriDescT<float> *d, int batch, int n, cudaStream_t s) {
     const size_t sh = (size_t)(2 * (NB + 1) + 2) * ((n + 3) & ~3) * sizeof(float) +
-                      (size_t)(kTT / 32) * NSL * 4 * 32 * sizeof(float4);
+                      (size_t)(kTT / 32) * NSL * RWS * 32 * sizeof(float4);
     if (sh > 227 * 1024) return cudaErrorNotSupported;   // the ring does not fit beside the vectors at this order
-    cudaError_t e = smem_attr(k_tridiag_delayed<NB, MINB, NSL>, sh);
+    cudaError_t e = smem_attr(k_tridiag_delayed<NB, MINB, NSL, RWS>, sh);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_tridiag_delayed<NB, MINB, NSL><<<batch, kTT, sh, s>>>(d);
+    k_tridiag_delayed<NB, MINB, NSL, RWS><<<batch, kTT, sh, s>>>(d);
     return cudaGetLastError();
 }
 
@@ -1673,6 +1674,7 @@ cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, 
         if (variant == 9) return launch_tridiag_delayed<2, 1, 2>(d, batch, n, s);
         if (variant == 10) return launch_tridiag_delayed<2, 1, 3>(d, batch, n, s);
         if (variant == 11) return launch_tridiag_delayed<2, 1, 4>(d, batch, n, s);
+        if (variant == 12) return launch_tridiag_delayed<2, 1, 2, 8>(d, batch, n, s);
         if (variant >= 5 && variant <= 7) {
             // FP32, one CTA per matrix, the updates of two (variants 5, 6) or four (7) steps written together;
             // variant 6 two CTAs per SM

@@ -23,8 +23,9 @@ using TriDesc32 = TriDescT<float>;
 // 2 / 3 / 4 = a cluster of 4 / 8 / 16 CTAs per matrix (cudaErrorNotSupported when the GPU cannot hold one),
 // 5 / 6 / 7 = one CTA per matrix with the updates of 2 / 2 / 4 steps written together (6: two CTAs per SM),
 // 8 / 9 = variants 6 / 5 with the row chunks staged through shared memory (a second set of loads in flight),
-// 10 / 11 = variant 9 with two / three chunks in flight ahead (cudaErrorNotSupported where the ring does not fit)
-constexpr int kTriVariants = 12;
+// 10 / 11 = variant 9 with two / three chunks in flight ahead (cudaErrorNotSupported where the ring does not fit),
+// 12 = variant 9 with eight rows per warp group instead of four
+constexpr int kTriVariants = 13;
 template <class R>
 cudaError_t osv_tridiag(const TriDescT<R> *d, int batch, int n, cudaStream_t s, int variant = 0);
 // The cnt largest eigenvalues of every tridiagonal (decreasing, into w[0..cnt)), by 32-point multisection in

@@ -111,7 +111,7 @@ def test_mixed_osv_eigenpairs_match_fp64(osvmbe, fixed):
     assert rest <= 1e-5
 
 
-@pytest.mark.parametrize("variant", list(range(12)))
+@pytest.mark.parametrize("variant", list(range(13)))
 @pytest.mark.parametrize("shape", [(8, 120, 300, 61), (5, 37, 90, 62), (3, 5, 20, 63)])
 def test_every_tridiagonalisation_launch_shape(osvmbe, variant, shape):
     """Each launch shape of the FP32 Householder reduction (a pair of CTAs, one CTA with two per SM, clusters of 4, 8
@@ -184,7 +184,7 @@ def test_autotuner_reports_its_choices_and_keeps_the_results(osvmbe):
     tri = rep["tridiag"]
     names = ["cta_pair", "single_cta_2_per_sm", "cluster_4", "cluster_8", "cluster_16", "delayed_2",
              "delayed_2_2_per_sm", "delayed_4", "staged_2_2_per_sm", "staged_2", "staged_2_depth_2",
-             "staged_2_depth_3"]
+             "staged_2_depth_3", "staged_2_8_rows"]
     assert set(tri["ms"]) == set(names) and tri["choice"] in names
     timed = {k: v for k, v in tri["ms"].items() if v is not None}   # a cluster size the GPU cannot hold is null
     assert set(names) - {"cluster_16"} <= set(timed)
