@@ -47,7 +47,7 @@ DT = torch.float64
 __all__ = [
     "tkk", "osv_decompose", "n_osv_select", "select_clusters", "mbe_weights", "pair_domain",
     "ClusterSolver", "energy", "gradient", "dense_B", "osv_overlap_metric", "select_clusters_osv",
-    "weak_pair_one_block", "energy_osv_screened", "posterior_correction",
+    "weak_pair_one_block", "gradient_weak_pairs", "energy_osv_screened", "posterior_correction",
 ]
 
 
@@ -249,7 +249,7 @@ class ClusterSolver:
         for it in range(max_iter + 1):
             R = {p: self.residual(p, T) for p in self.pairs}
             Rt = {p: pc[p][0].T @ R[p] @ pc[p][0] for p in self.pairs}
-            rn = max(float(torch.linalg.norm(Rt[p])) for p in self.pairs)
+            rn = max(float(torch.linalg.norm(Rt[p]).detach()) for p in self.pairs)
             if rn <= tol or it == max_iter:
                 break
             for p in self.pairs:
@@ -267,20 +267,10 @@ class ClusterSolver:
 
 
 # ------------------------------------------------------------------------------- weak 2b clusters
-def weak_pair_one_block(problem, params, i, j, n_osv=None, tol=1e-12, max_iter=500):
-    """One-block amplitudes of a weak 2b cluster {i, j} (Sec. 2.2.2).
-
-    The pair amplitudes T_(ij,ij) of the 2b cluster are restricted to their upper-right block X (rows: the OSVs of
-    i, columns: the OSVs of j; the direct-dispersion excitations), T_(ij,ij) = E_i X E_j^T, and X solves the
-    upper-right block of the 2b cluster residual of Eq. 4, R^{i,j}_(i,j) = E_i^T R_(ij,ij) E_j = 0.  The diagonal
-    pairs keep their 1b cluster amplitudes T^i_(ii,ii), T^j_(jj,jj) in the f_ij coupling terms.  Iterations:
-    X <- X - U_i [(U_i^T R U_j) / (e_i + e_j - f_ii - f_jj)] U_j^T with F_(i,i) = U_i diag(e_i) U_i^T.
-
-    Returns X, the weak pair's energy E_w (the Hylleraas terms <K + R, 2T - T^T> of Eq. 3 for the ordered pairs
-    (i, j) and (j, i), T_(ji,ji) = E_j X^T E_i^T), the iteration count and the final max |R^{i,j}_(i,j)|."""
-    assert i != j
-    eps, F, Bd = _inputs(problem, False)
-    Q, _ = _osvs(Bd, eps, F, params, n_osv)
+def _weak_pair(i, j, Q, Bd, eps, F, params, tol, max_iter):
+    """Core of weak_pair_one_block on given OSVs Q, DF blocks Bd and Fock matrix F (torch tensors; every step is a
+    torch operation, so the energy can be differentiated through the 1b solves and the one-block iterations).
+    Returns X, E_w (a tensor), the iteration count and the final max |R^{i,j}_(i,j)|."""
     b = _Blocks(Q, Bd, eps)
     T = {}
     for k in (i, j):   # 1b cluster amplitudes of the diagonal pairs
@@ -303,7 +293,7 @@ def weak_pair_one_block(problem, params, i, j, n_osv=None, tol=1e-12, max_iter=5
     for it in range(max_iter + 1):
         T[p] = embed(X)
         Rb = cs.residual(p, T)[:ni, ni:]
-        rn = float(Rb.abs().max())
+        rn = float(Rb.detach().abs().max())
         if rn <= tol or it == max_iter:
             break
         X = X - Ui @ ((Ui.T @ Rb @ Uj) / D) @ Uj.T
@@ -315,7 +305,49 @@ def weak_pair_one_block(problem, params, i, j, n_osv=None, tol=1e-12, max_iter=5
     for q in (p, pt):
         R = cs.residual(q, T)
         Ew = Ew + torch.sum((b.K(q) + R) * (2.0 * T[q] - T[q].T))
+    return X, Ew, it, rn
+
+
+def weak_pair_one_block(problem, params, i, j, n_osv=None, tol=1e-12, max_iter=500):
+    """One-block amplitudes of a weak 2b cluster {i, j} (Sec. 2.2.2).
+
+    The pair amplitudes T_(ij,ij) of the 2b cluster are restricted to their upper-right block X (rows: the OSVs of
+    i, columns: the OSVs of j; the direct-dispersion excitations), T_(ij,ij) = E_i X E_j^T, and X solves the
+    upper-right block of the 2b cluster residual of Eq. 4, R^{i,j}_(i,j) = E_i^T R_(ij,ij) E_j = 0.  The diagonal
+    pairs keep their 1b cluster amplitudes T^i_(ii,ii), T^j_(jj,jj) in the f_ij coupling terms.  Iterations:
+    X <- X - U_i [(U_i^T R U_j) / (e_i + e_j - f_ii - f_jj)] U_j^T with F_(i,i) = U_i diag(e_i) U_i^T.
+
+    Returns X, the weak pair's energy E_w (the Hylleraas terms <K + R, 2T - T^T> of Eq. 3 for the ordered pairs
+    (i, j) and (j, i), T_(ji,ji) = E_j X^T E_i^T), the iteration count and the final max |R^{i,j}_(i,j)|."""
+    assert i != j
+    eps, F, Bd = _inputs(problem, False)
+    Q, _ = _osvs(Bd, eps, F, params, n_osv)
+    X, Ew, it, rn = _weak_pair(i, j, Q, Bd, eps, F, params, tol, max_iter)
     return X, float(Ew), it, rn
+
+
+def gradient_weak_pairs(problem, params, pairs, n_osv=None, tol=1e-12, max_iter=500):
+    """The weak pairs' energy sum_w E_w (weak_pair_one_block) and its derivative with respect to the stored DF
+    entries B (list of (n_vir, a_i) arrays in each LMO's local aux order) and every entry of F_occ.
+
+    E_w holds only the ordered pairs (i, j) and (j, i) of the 2b cluster, with T_ii, T_jj frozen at their 1b
+    solutions, so it is not stationary in X, T_ii or T_jj: the derivative takes their responses.  It is the
+    derivative of the computed energy, by automatic differentiation through the OSV eigendecompositions, the 1b
+    solves and the one-block iterations (converged to tol).  OSV counts are frozen (n_osv, else the counts at B)."""
+    eps, F, Bd = _inputs(problem, True)
+    Q, info = _osvs(Bd, eps, F, params, n_osv)
+    E = torch.zeros((), dtype=DT)
+    for i, j in pairs:
+        assert i != j
+        E = E + _weak_pair(i, j, Q, Bd, eps, F, params, tol, max_iter)[1]
+    E.backward()
+    dB = []
+    for i in range(problem.n_occ):
+        idx = problem.aux_idx[problem.aux_ptr[i]:problem.aux_ptr[i + 1]].astype(np.int64)
+        g = Bd[i].grad
+        dB.append(g[:, idx].numpy().copy() if g is not None else np.zeros((Bd[i].shape[0], len(idx))))
+    return dict(E=float(E.detach()), dB=dB, dF=F.grad.numpy().copy() if F.grad is not None else
+                np.zeros_like(problem.f_occ), n_osv=[n for _, n in info])
 
 
 # ------------------------------------------------------------------------------------------- top level

@@ -444,6 +444,45 @@ def test_weak_pair_one_block_equals_full_2b_when_decoupled():
     assert np.abs(T01[:n0, :n0]).max() <= 1e-12 and np.abs(T01[n0:, :]).max() <= 1e-12
 
 
+def test_weak_pair_gradient_matches_finite_differences():
+    """gradient_weak_pairs (the derivative of the weak pairs' one-block energy, Sec. 2.2.2) against fourth-order
+    central differences of weak_pair_one_block's E_w, on B entries of both LMOs of each weak pair and on
+    diagonal and off-diagonal entries of F_occ (entrywise: f_03 and f_30 apart).  E_w is not stationary in the
+    one-block amplitudes or the frozen 1b amplitudes, so a derivative that drops their responses fails here."""
+    p = make_problem(4, 18, 40, seed=31)
+    p.f_occ = p.f_occ.copy()
+    p.f_occ[0, 3] = p.f_occ[3, 0] = -0.03
+    prm = Params(n_osv_fixed=5, mbe_order=3, tol=1e-13, max_iter=500)
+    pairs = [(0, 3), (1, 2)]
+    g = oracle.gradient_weak_pairs(p, prm, pairs)
+
+    def ew(q):
+        return sum(oracle.weak_pair_one_block(q, prm, i, j)[1] for i, j in pairs)
+
+    def moved(kind, idx, h):
+        q = Problem(**p.__dict__)
+        if kind == "B":
+            i, a, P = idx
+            q.B = p.B.copy()
+            q.B[int(p.aux_ptr[i]) * p.n_vir + a * p.a(i) + P] += h
+        else:
+            q.f_occ = p.f_occ.copy()
+            q.f_occ[idx] += h
+        return q
+
+    rng = np.random.default_rng(7)
+    entries = [("B", (i, int(rng.integers(p.n_vir)), int(rng.integers(p.a(i))))) for i in (0, 3, 1, 2) for _ in range(2)]
+    entries += [("F", (0, 0)), ("F", (0, 3)), ("F", (3, 0)), ("F", (1, 2))]
+    h = 1e-4
+    for kind, idx in entries:
+        d1 = ew(moved(kind, idx, h)) - ew(moved(kind, idx, -h))
+        d2 = ew(moved(kind, idx, 2 * h)) - ew(moved(kind, idx, -2 * h))
+        fd = (8 * d1 - d2) / (12 * h)
+        an = g["dB"][idx[0]][idx[1], idx[2]] if kind == "B" else g["dF"][idx]
+        assert abs(an - fd) <= 1e-8 + 1e-6 * abs(fd), (kind, idx, an, fd)
+    assert abs(g["E"] - ew(p)) <= 1e-14
+
+
 def test_screened_energy_limits():
     """The screened MBE energy (strong clusters by the OSV metric + one-block weak pairs - discarded pairs) in its
     limits: every pair strong and no triple -> the MBE(2) energy of all pairs; every pair below the discard
