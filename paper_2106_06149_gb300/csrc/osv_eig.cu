@@ -2,10 +2,14 @@
 //
 // Only the n_k kept eigenvectors of T_kk enter the energy, and the OSV relaxation of Eq. 8 needs the discarded
 // eigenvectors only through the restricted resolvent sum_nu q'_nu q'_nu^T / (omega_mu - omega'_nu).  So:
-//   1. Householder tridiagonalisation T = H Tri H^T (one CTA per LMO, or a pair of CTAs in FP32; reflector k
-//      kept contiguous in row k).  One pass over the lower triangle of the trailing matrix per step: the rank-2
-//      update of step k-1 is applied lazily in the same pass that forms the product A v_k of step k from the row
-//      and column sums of the stored triangle (warp per row, coalesced, division free);
+//   1. Householder tridiagonalisation T = H Tri H^T (reflector k kept contiguous in row k).  One pass over the
+//      lower triangle of the trailing matrix per step: the rank-2 update of step k-1 is applied lazily in the
+//      same pass that forms the product A v_k of step k from the row and column sums of the stored triangle
+//      (warp per row, coalesced, division free).  FP64: one CTA per LMO.  FP32 (a first stage, refined to FP64
+//      accuracy afterwards), launch shapes picked by the plan's autotuner: a pair of CTAs per matrix, one CTA
+//      (two per SM), clusters of 4 / 8 / 16 CTAs (k_tridiag_cl), and delayed updates (k_tridiag_delayed: the
+//      rank-2 updates of NB steps written together, read-only passes in between, optionally with the row chunks
+//      staged through a per-lane cp.async ring in shared memory);
 //   2. the n_max largest eigenvalues of Tri by 32-point multisection of the Sturm count (one warp per
 //      eigenvalue, FP64 arithmetic): ~11 rounds instead of ~60 bisection steps, each a chain of n dependent
 //      multiply-adds (on GB300 a dependent FP64 operation costs ~64 cycles and a division ~430);
