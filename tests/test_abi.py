@@ -45,3 +45,12 @@ def test_null_and_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.clusters_build(None, None, None, None) == osvmbe.OSV_ERR_INVALID
     assert lib.energy(None, None, None) == osvmbe.OSV_ERR_INVALID
     assert lib.osv_syev_batched(None, 4, 1, None, None, None) == osvmbe.OSV_ERR_INVALID
+    # the recorded step, the launch-shape and failure-detection settings, the counters
+    assert lib.osv_graph_capture(None, None, None, 1.0, None, None) == osvmbe.OSV_ERR_INVALID
+    assert lib.osv_graph_launch(None, None, None) == osvmbe.OSV_ERR_INVALID
+    n = ctypes.c_longlong()
+    assert lib.osv_graph_kernels(None, ctypes.byref(n)) == osvmbe.OSV_ERR_INVALID
+    assert lib.osv_set_tridiag_variant(None, 0) == osvmbe.OSV_ERR_INVALID
+    assert lib.osv_set_wait_budget(None, 1) == osvmbe.OSV_ERR_INVALID
+    assert lib.osv_autotune(None, 1) == osvmbe.OSV_ERR_INVALID
+    assert lib.osv_kernel_launches(None) == osvmbe.OSV_ERR_INVALID
