@@ -37,8 +37,8 @@ METRIC = "cluster pair-residual TFLOP/s, gradient s/geometry: mixed vs FP64 GPU 
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 2 DFMA/clk/SM (1.25 TFLOP/s nominal)
 FP32_PEAK_TFLOPS = 152 * 2.07e9 * 256 / 1e12  # 152 SMs x 2.07 GHz x 128 FP32 lanes x 2 (FMA) = 80.5 TFLOP/s
 DF_OPS_PER_FMA = 12                            # FP32 instructions of one double-float multiply-add (df_fma)
-WHY_NOT_4 = ("workload 4 (512 LMOs, n_vir 3000) also fits one GPU, but one step takes several seconds, so the "
-             "driver's step counts would exceed the minute-scale timed budget; it is measured with --workload 4")
+WHY_NOT_4 = ("workload 4 (512 LMOs, n_vir 3000) also fits one GPU, but one step takes about 6 s, so 20 timed steps "
+             "would run past a minute-scale timed region; it is measured with --workload 4")
 
 # DRAM traffic per launch of the residual kernel (dram__bytes_read.sum + dram__bytes_write.sum), from the ncu capture
 # summarised in profiles/, keyed by workload and by the SHA-256 prefix of the kernel's source file at capture time:
